@@ -1,0 +1,802 @@
+/*
+ * ibm_oracle.c -- plain, slow, FP64 CPU oracle of the sharp-interface IBM
+ * fractional step (Vagnoli, Scarpolini, Verzicco, Viola, arXiv 2606.09799).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path links, loads or
+ * calls this file: only the test-suite, the smoke check and the CPU-baseline
+ * leg of the benchmark do.  It shares no code, header, table or constant
+ * with the CUDA library.
+ *
+ * Every function below follows one passage of the paper, cited in its
+ * comment.  Loops are written in the plainest order; there is no blocking,
+ * fusion or reordering beyond what the cited equation or algorithm states.
+ * The discrete Fourier transform of the Poisson solve is done in Python
+ * (numpy.fft) by oracle.py; this file holds everything else.
+ *
+ * Conventions (shared with the CUDA path only through the paper's text and
+ * the documented data format, never through code):
+ *   - grid nx*ny*nz cells, box [0,lx]x[0,ly]x[0,lz]; x and z periodic,
+ *     y bounded by walls at y=0 and y=ly (the paper's x3, Section 2).
+ *   - u on x-faces  (i*dx, (j+.5)*dy, (k+.5)*dz), j in [0,ny)
+ *     v on y-faces  ((i+.5)*dx, j*dy, (k+.5)*dz), j in [0,ny], walls j=0,ny
+ *     w on z-faces  ((i+.5)*dx, (j+.5)*dy, k*dz), j in [0,ny)
+ *     p, phi at cell centres.  Arrays are [k][j][i], i fastest; v has ny+1
+ *     planes.
+ *   - Compile with -ffp-contract=off: the tagging predicates must round
+ *     exactly as written (no fused multiply-add).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef struct {
+  int nx, ny, nz;
+  int ybc;              /* 0: no-slip walls, 1: free-slip walls (tests) */
+  double lx, ly, lz;
+  double dx, dy, dz;
+} orc_grid;
+
+/* ------------------------------------------------------------------ */
+/* grid helpers                                                        */
+/* ------------------------------------------------------------------ */
+
+int orc_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+void orc_grid_init(orc_grid* g, int nx, int ny, int nz, double lx, double ly, double lz, int ybc) {
+  g->nx = nx; g->ny = ny; g->nz = nz; g->ybc = ybc;
+  g->lx = lx; g->ly = ly; g->lz = lz;
+  g->dx = lx / (double)nx;
+  g->dy = ly / (double)ny;
+  g->dz = lz / (double)nz;
+}
+
+/* number of y-planes stored for component c (v carries both wall planes) */
+static int planes(const orc_grid* g, int c) { return c == 1 ? g->ny + 1 : g->ny; }
+
+static long fidx(const orc_grid* g, int c, long i, long j, long k) {
+  return (k * planes(g, c) + j) * (long)g->nx + i;
+}
+
+static long cidx(const orc_grid* g, long i, long j, long k) {
+  return (k * g->ny + j) * (long)g->nx + i;
+}
+
+static long wrap(long i, long n) {
+  long r = i % n;
+  return r < 0 ? r + n : r;
+}
+
+/* Staggered node position of component c with (possibly unwrapped) lattice
+ * indices (i,j,k): Fig. problem_and_grid(b), Section 2. */
+static void node_xyz(const orc_grid* g, int c, long i, long j, long k, double x[3]) {
+  x[0] = (c == 0) ? (double)i * g->dx : ((double)i + 0.5) * g->dx;
+  x[1] = (c == 1) ? (double)j * g->dy : ((double)j + 0.5) * g->dy;
+  x[2] = (c == 2) ? (double)k * g->dz : ((double)k + 0.5) * g->dz;
+}
+
+/* Offsets of component c's lattice in units of the spacing. */
+static void node_offset(int c, double off[3]) {
+  off[0] = (c == 0) ? 0.0 : 0.5;
+  off[1] = (c == 1) ? 0.0 : 0.5;
+  off[2] = (c == 2) ? 0.0 : 0.5;
+}
+
+/* Range of y indices that hold unknowns of component c. */
+static void jrange(const orc_grid* g, int c, long* jlo, long* jhi) {
+  if (c == 1) { *jlo = 1; *jhi = g->ny - 1; }
+  else        { *jlo = 0; *jhi = g->ny - 1; }
+}
+
+static double dot3(const double a[3], const double b[3]) {
+  return (a[0] * b[0] + a[1] * b[1]) + a[2] * b[2];
+}
+
+/* ------------------------------------------------------------------ */
+/* Closest point on a triangle (Algorithm 1, step "closest point",     */
+/* which cites Ericson 2004).  Voronoi-region classification of p      */
+/* against the vertex, edge and face regions of triangle (a,b,c).       */
+/* Returns X and its barycentric weights w (w[0]+w[1]+w[2]=1).         */
+/* ------------------------------------------------------------------ */
+void orc_closest_point(const double p[3], const double a[3], const double b[3], const double c[3],
+                       double X[3], double w[3]) {
+  double ab[3], ac[3], ap[3], bp[3], cp[3];
+  for (int d = 0; d < 3; ++d) {
+    ab[d] = b[d] - a[d];
+    ac[d] = c[d] - a[d];
+    ap[d] = p[d] - a[d];
+  }
+  double d1 = dot3(ab, ap);
+  double d2 = dot3(ac, ap);
+  if (d1 <= 0.0 && d2 <= 0.0) {                         /* vertex a region */
+    for (int d = 0; d < 3; ++d) X[d] = a[d];
+    w[0] = 1.0; w[1] = 0.0; w[2] = 0.0;
+    return;
+  }
+  for (int d = 0; d < 3; ++d) bp[d] = p[d] - b[d];
+  double d3 = dot3(ab, bp);
+  double d4 = dot3(ac, bp);
+  if (d3 >= 0.0 && d4 <= d3) {                          /* vertex b region */
+    for (int d = 0; d < 3; ++d) X[d] = b[d];
+    w[0] = 0.0; w[1] = 1.0; w[2] = 0.0;
+    return;
+  }
+  double vc = d1 * d4 - d3 * d2;
+  if (vc <= 0.0 && d1 >= 0.0 && d3 <= 0.0) {           /* edge ab region */
+    double t = d1 / (d1 - d3);
+    for (int d = 0; d < 3; ++d) X[d] = a[d] + t * ab[d];
+    w[0] = 1.0 - t; w[1] = t; w[2] = 0.0;
+    return;
+  }
+  for (int d = 0; d < 3; ++d) cp[d] = p[d] - c[d];
+  double d5 = dot3(ab, cp);
+  double d6 = dot3(ac, cp);
+  if (d6 >= 0.0 && d5 <= d6) {                          /* vertex c region */
+    for (int d = 0; d < 3; ++d) X[d] = c[d];
+    w[0] = 0.0; w[1] = 0.0; w[2] = 1.0;
+    return;
+  }
+  double vb = d5 * d2 - d1 * d6;
+  if (vb <= 0.0 && d2 >= 0.0 && d6 <= 0.0) {           /* edge ac region */
+    double t = d2 / (d2 - d6);
+    for (int d = 0; d < 3; ++d) X[d] = a[d] + t * ac[d];
+    w[0] = 1.0 - t; w[1] = 0.0; w[2] = t;
+    return;
+  }
+  double va = d3 * d6 - d5 * d4;
+  if (va <= 0.0 && (d4 - d3) >= 0.0 && (d5 - d6) >= 0.0) { /* edge bc region */
+    double t = (d4 - d3) / ((d4 - d3) + (d5 - d6));
+    for (int d = 0; d < 3; ++d) X[d] = b[d] + t * (c[d] - b[d]);
+    w[0] = 0.0; w[1] = 1.0 - t; w[2] = t;
+    return;
+  }
+  double s = 1.0 / ((va + vb) + vc);                    /* face region */
+  double v = vb * s;
+  double u = vc * s;
+  for (int d = 0; d < 3; ++d) X[d] = (a[d] + ab[d] * v) + ac[d] * u;
+  w[0] = (1.0 - v) - u; w[1] = v; w[2] = u;
+}
+
+/* ------------------------------------------------------------------ */
+/* Algorithm 1, body of the inner loop: decide whether node x (lattice  */
+/* indices i,j,k of component c, unwrapped) is a forcing node for the   */
+/* triangle (a,b,c3).  Returns 1 and |N|^2 if so.                       */
+/*   |N| <= diagonal of the local cell (compared squared);             */
+/*   forcing iff some scalar product N . (x^{k,n} - X) < 0 over the six */
+/*   lattice neighbours x^{k,n}.  A node lying on the surface (N = 0)   */
+/*   has no defined side and is tagged, with alpha = 0 in Eq. new_IB.  */
+/* ------------------------------------------------------------------ */
+static int tag_test(const orc_grid* g, int c, long i, long j, long k, const double x[3],
+                    const double* a, const double* b, const double* c3, double diag2, double* n2_out) {
+  double X[3], w[3], N[3];
+  orc_closest_point(x, a, b, c3, X, w);
+  for (int d = 0; d < 3; ++d) N[d] = x[d] - X[d];
+  double n2 = dot3(N, N);
+  if (!(n2 <= diag2)) return 0;
+  *n2_out = n2;
+  if (n2 == 0.0) return 1;
+  for (int d = 0; d < 3; ++d) {
+    for (int s = -1; s <= 1; s += 2) {
+      long ni = i + (d == 0 ? s : 0);
+      long nj = j + (d == 1 ? s : 0);
+      long nk = k + (d == 2 ? s : 0);
+      double xn[3], vn[3];
+      node_xyz(g, c, ni, nj, nk, xn);
+      for (int e = 0; e < 3; ++e) vn[e] = xn[e] - X[e];
+      if (dot3(N, vn) < 0.0) return 1;
+    }
+  }
+  return 0;
+}
+
+static void tri_vertices(const double* xyz, const int* tri, long t, const double** a, const double** b,
+                         const double** c) {
+  *a = xyz + 3 * (long)tri[3 * t + 0];
+  *b = xyz + 3 * (long)tri[3 * t + 1];
+  *c = xyz + 3 * (long)tri[3 * t + 2];
+}
+
+static double diag2_of(const orc_grid* g) {
+  return (g->dx * g->dx + g->dy * g->dy) + g->dz * g->dz;
+}
+
+/* Owner rule when several triangles tag the same node: the one with the
+ * smallest |N|^2, ties to the smallest triangle index. */
+static void claim(int32_t* owner, double* d2, long idx, int32_t t, double n2) {
+  if (owner[idx] < 0 || n2 < d2[idx] || (n2 == d2[idx] && t < owner[idx])) {
+    owner[idx] = t;
+    d2[idx] = n2;
+  }
+}
+
+/* Algorithm 1 as printed: loop over triangles, build the Cartesian box
+ * min - dx < x < max + dx (strict), visit the Eulerian points of component c
+ * inside it, and classify each.  owner[] (size of component c's array) must
+ * be -1 on entry; d2[] is scratch of the same size.  Indices that leave the
+ * box in x or z wrap periodically (the point keeps its unwrapped coordinate). */
+void orc_tag_alg1(const orc_grid* g, int c, const double* xyz, int ntri, const int* tri,
+                  int32_t* owner, double* d2) {
+  double off[3], del[3] = {g->dx, g->dy, g->dz};
+  node_offset(c, off);
+  double diag2 = diag2_of(g);
+  long jlo, jhi;
+  jrange(g, c, &jlo, &jhi);
+  for (long t = 0; t < ntri; ++t) {
+    const double *a, *b, *c3;
+    tri_vertices(xyz, tri, t, &a, &b, &c3);
+    double lo[3], hi[3];
+    long ilo[3], ihi[3];
+    for (int d = 0; d < 3; ++d) {
+      double mn = fmin(a[d], fmin(b[d], c3[d]));
+      double mx = fmax(a[d], fmax(b[d], c3[d]));
+      lo[d] = mn - del[d];
+      hi[d] = mx + del[d];
+      ilo[d] = (long)floor(lo[d] / del[d] - off[d]) - 1;
+      ihi[d] = (long)ceil(hi[d] / del[d] - off[d]) + 1;
+    }
+    if (ilo[1] < jlo) ilo[1] = jlo;
+    if (ihi[1] > jhi) ihi[1] = jhi;
+    for (long k = ilo[2]; k <= ihi[2]; ++k)
+      for (long j = ilo[1]; j <= ihi[1]; ++j)
+        for (long i = ilo[0]; i <= ihi[0]; ++i) {
+          double x[3];
+          node_xyz(g, c, i, j, k, x);
+          int inside = 1;
+          for (int d = 0; d < 3; ++d)
+            if (!(lo[d] < x[d] && x[d] < hi[d])) inside = 0;
+          if (!inside) continue;
+          double n2;
+          if (tag_test(g, c, i, j, k, x, a, b, c3, diag2, &n2)) {
+            long idx = fidx(g, c, wrap(i, g->nx), j, wrap(k, g->nz));
+            claim(owner, d2, idx, (int32_t)t, n2);
+          }
+        }
+  }
+}
+
+/* Brute force counterpart of Algorithm 1: every node of component c (and
+ * its periodic images one box away in x and z) against every triangle, with
+ * the bounding box applied as a predicate.  Tiny grids only. */
+void orc_tag_brute(const orc_grid* g, int c, const double* xyz, int ntri, const int* tri,
+                   int32_t* owner, double* d2) {
+  double del[3] = {g->dx, g->dy, g->dz};
+  double diag2 = diag2_of(g);
+  long jlo, jhi;
+  jrange(g, c, &jlo, &jhi);
+  for (long k = 0; k < g->nz; ++k)
+    for (long j = jlo; j <= jhi; ++j)
+      for (long i = 0; i < g->nx; ++i) {
+        long idx = fidx(g, c, i, j, k);
+        for (int mk = -1; mk <= 1; ++mk)
+          for (int mi = -1; mi <= 1; ++mi) {
+            long ii = i + mi * (long)g->nx, kk = k + mk * (long)g->nz;
+            double x[3];
+            node_xyz(g, c, ii, j, kk, x);
+            for (long t = 0; t < ntri; ++t) {
+              const double *a, *b, *c3;
+              tri_vertices(xyz, tri, t, &a, &b, &c3);
+              int inside = 1;
+              for (int d = 0; d < 3; ++d) {
+                double mn = fmin(a[d], fmin(b[d], c3[d]));
+                double mx = fmax(a[d], fmax(b[d], c3[d]));
+                if (!((mn - del[d]) < x[d] && x[d] < (mx + del[d]))) inside = 0;
+              }
+              if (!inside) continue;
+              double n2;
+              if (tag_test(g, c, ii, j, kk, x, a, b, c3, diag2, &n2)) claim(owner, d2, idx, (int32_t)t, n2);
+            }
+          }
+      }
+}
+
+/* ------------------------------------------------------------------ */
+/* Trilinear interpolation of component c at point P from the 8        */
+/* surrounding nodes of the same staggered lattice (Section 3.1, the   */
+/* interpolation of u^e).  x and z wrap; in y the 8 nodes must lie in  */
+/* the stored planes (u,w: 0..ny-1, v: 0..ny incl. the wall values),    */
+/* otherwise returns -1 (probe left the domain).                        */
+/* ------------------------------------------------------------------ */
+static int trilinear(const orc_grid* g, int c, const double* f, const double P[3], double* out) {
+  double off[3], del[3] = {g->dx, g->dy, g->dz};
+  node_offset(c, off);
+  long i0[3];
+  double t[3];
+  for (int d = 0; d < 3; ++d) {
+    double s = P[d] / del[d] - off[d];
+    double fl = floor(s);
+    i0[d] = (long)fl;
+    t[d] = s - fl;
+  }
+  long jmax = planes(g, c) - 1;
+  if (i0[1] < 0 || i0[1] + 1 > jmax) return -1;
+  double acc = 0.0;
+  for (int dk = 0; dk <= 1; ++dk)
+    for (int dj = 0; dj <= 1; ++dj)
+      for (int di = 0; di <= 1; ++di) {
+        double wgt = (di ? t[0] : 1.0 - t[0]) * (dj ? t[1] : 1.0 - t[1]) * (dk ? t[2] : 1.0 - t[2]);
+        long ii = wrap(i0[0] + di, g->nx), jj = i0[1] + dj, kk = wrap(i0[2] + dk, g->nz);
+        acc += wgt * f[fidx(g, c, ii, jj, kk)];
+      }
+  *out = acc;
+  return 0;
+}
+
+/* Lattice position of stored node (i,j,k) taken at the periodic image
+ * nearest to the owning triangle's centroid (the image Algorithm 1 visited). */
+static void node_near(const orc_grid* g, int c, long i, long j, long k, const double* a, const double* b,
+                      const double* c3, double x[3]) {
+  double cen[3];
+  for (int d = 0; d < 3; ++d) cen[d] = (a[d] + b[d] + c3[d]) / 3.0;
+  node_xyz(g, c, i, j, k, x);
+  long mi = lround((cen[0] - x[0]) / g->lx);
+  long mk = lround((cen[2] - x[2]) / g->lz);
+  node_xyz(g, c, i + mi * (long)g->nx, j, k + mk * (long)g->nz, x);
+}
+
+/* ------------------------------------------------------------------ */
+/* Two-sided IB forcing, Eqs. probe and new_IB: for every forcing node */
+/* x^f of component c, X^f = closest point on its triangle, N = x^f-X, */
+/* n = N/|N|, x^e = X^f + h n, u^e trilinear from the snapshot `src`,  */
+/* U = wall velocity at X^f (barycentric from the vertex velocities),  */
+/* alpha = |N|/h, u^f = (1-alpha) U + alpha u^e.  Writes u^f into dst  */
+/* at the forcing nodes only.  Returns the number of probes that left  */
+/* the domain (0 on success).                                           */
+/* ------------------------------------------------------------------ */
+int orc_force(const orc_grid* g, int c, const double* src, double* dst, const int32_t* owner,
+              const double* xyz, const double* vel, const int* tri, double h) {
+  long n = (long)g->nz * planes(g, c) * g->nx;
+  int bad = 0;
+  for (long idx = 0; idx < n; ++idx) {
+    int32_t t = owner[idx];
+    if (t < 0) continue;
+    long i = idx % g->nx, j = (idx / g->nx) % planes(g, c), k = idx / ((long)g->nx * planes(g, c));
+    const double *a, *b, *c3;
+    tri_vertices(xyz, tri, t, &a, &b, &c3);
+    double x[3], X[3], w[3], N[3];
+    node_near(g, c, i, j, k, a, b, c3, x);
+    orc_closest_point(x, a, b, c3, X, w);
+    for (int d = 0; d < 3; ++d) N[d] = x[d] - X[d];
+    double U = w[0] * vel[3 * (long)tri[3 * t + 0] + c] + w[1] * vel[3 * (long)tri[3 * t + 1] + c] +
+               w[2] * vel[3 * (long)tri[3 * t + 2] + c];
+    double n2 = dot3(N, N);
+    if (n2 == 0.0) { dst[idx] = U; continue; }
+    double nl = sqrt(n2);
+    double xe[3];
+    for (int d = 0; d < 3; ++d) xe[d] = X[d] + h * (N[d] / nl);
+    double ue;
+    if (trilinear(g, c, src, xe, &ue) != 0) { bad++; continue; }
+    double alpha = nl / h;
+    dst[idx] = (1.0 - alpha) * U + alpha * ue;
+  }
+  return bad;
+}
+
+/* ------------------------------------------------------------------ */
+/* No-slip error on the forcing points of component c (Section 4.4,   */
+/* heaving plate): the flow is interpolated on the surface with the     */
+/* interpolator of Eq. new_IB, u_w = (u(x^f) - alpha u(x^e))/(1-alpha), */
+/* eps = u_w - U.  Returns sum |eps| and the count through pointers.   */
+/* ------------------------------------------------------------------ */
+int orc_slip(const orc_grid* g, int c, const double* f, const int32_t* owner, const double* xyz,
+             const double* vel, const int* tri, double h, double* sum_abs, long* count) {
+  long n = (long)g->nz * planes(g, c) * g->nx;
+  double s = 0.0;
+  long cnt = 0;
+  int bad = 0;
+  for (long idx = 0; idx < n; ++idx) {
+    int32_t t = owner[idx];
+    if (t < 0) continue;
+    long i = idx % g->nx, j = (idx / g->nx) % planes(g, c), k = idx / ((long)g->nx * planes(g, c));
+    const double *a, *b, *c3;
+    tri_vertices(xyz, tri, t, &a, &b, &c3);
+    double x[3], X[3], w[3], N[3];
+    node_near(g, c, i, j, k, a, b, c3, x);
+    orc_closest_point(x, a, b, c3, X, w);
+    for (int d = 0; d < 3; ++d) N[d] = x[d] - X[d];
+    double U = w[0] * vel[3 * (long)tri[3 * t + 0] + c] + w[1] * vel[3 * (long)tri[3 * t + 1] + c] +
+               w[2] * vel[3 * (long)tri[3 * t + 2] + c];
+    double n2 = dot3(N, N);
+    double uw;
+    if (n2 == 0.0) {
+      uw = f[idx];
+    } else {
+      double nl = sqrt(n2);
+      double xe[3];
+      for (int d = 0; d < 3; ++d) xe[d] = X[d] + h * (N[d] / nl);
+      double ue;
+      if (trilinear(g, c, f, xe, &ue) != 0) { bad++; continue; }
+      double alpha = nl / h;
+      uw = (f[idx] - alpha * ue) / (1.0 - alpha);
+    }
+    s += fabs(uw - U);
+    cnt++;
+  }
+  *sum_abs = s;
+  *count = cnt;
+  return bad;
+}
+
+/* ------------------------------------------------------------------ */
+/* Explicit part of Eq. NS_prov on the fluid nodes:                    */
+/*   R = dt [ gamma H^s + rho H^{s-1} - alpha G p^s + alpha/Re L u^s   */
+/*            + alpha f ]                                               */
+/* (the CN half alpha/(2Re) L(uhat+u^s) written in delta form adds     */
+/*  alpha/Re L u^s here; the other half is the implicit operator).      */
+/* H is the conservative non-linear term -div(u u) on the staggered     */
+/* grid with arithmetic face/edge averages (Section 2, "conservative    */
+/* form", second-order centred).  R = 0 on forcing nodes.  H is          */
+/* returned on every node.  Hprev may be NULL when rho == 0.            */
+/* Tangential wall condition: ghost u_{-1} = -u_0 (no-slip, wall at     */
+/* rest) or u_{-1} = u_0 (free-slip); v = 0 on the walls.               */
+/* ------------------------------------------------------------------ */
+void orc_rhs(const orc_grid* g, const double* u, const double* v, const double* w, const double* p,
+             const double* Hu_prev, const double* Hv_prev, const double* Hw_prev,
+             const int32_t* own_u, const int32_t* own_v, const int32_t* own_w,
+             double gam, double rho, double alp, double dt, double re, const double fb[3],
+             double* Ru, double* Rv, double* Rw, double* Hu, double* Hv, double* Hw) {
+  const int nx = g->nx, ny = g->ny, nz = g->nz;
+  const double dx = g->dx, dy = g->dy, dz = g->dz;
+  const double gs = (g->ybc == 0) ? -1.0 : 1.0; /* ghost sign for tangential components */
+#define U(i, j, k) u[fidx(g, 0, wrap(i, nx), j, wrap(k, nz))]
+#define V(i, j, k) v[fidx(g, 1, wrap(i, nx), j, wrap(k, nz))]
+#define W(i, j, k) w[fidx(g, 2, wrap(i, nx), j, wrap(k, nz))]
+#define P(i, j, k) p[cidx(g, wrap(i, nx), j, wrap(k, nz))]
+#pragma omp parallel for schedule(static)
+  for (long k = 0; k < nz; ++k)
+    for (long j = 0; j < ny; ++j)
+      for (long i = 0; i < nx; ++i) {
+        /* ---- u at (i dx, (j+.5) dy, (k+.5) dz) ---- */
+        {
+          double uc_p = 0.5 * (U(i, j, k) + U(i + 1, j, k));
+          double uc_m = 0.5 * (U(i - 1, j, k) + U(i, j, k));
+          double duu = (uc_p * uc_p - uc_m * uc_m) / dx;
+          double vt = 0.5 * (V(i - 1, j + 1, k) + V(i, j + 1, k));
+          double ut = (j + 1 < ny) ? 0.5 * (U(i, j, k) + U(i, j + 1, k)) : 0.0;
+          double vb = 0.5 * (V(i - 1, j, k) + V(i, j, k));
+          double ub = (j > 0) ? 0.5 * (U(i, j - 1, k) + U(i, j, k)) : 0.0;
+          double dvu = (vt * ut - vb * ub) / dy;
+          double wf = 0.5 * (W(i - 1, j, k + 1) + W(i, j, k + 1));
+          double uf = 0.5 * (U(i, j, k) + U(i, j, k + 1));
+          double wb = 0.5 * (W(i - 1, j, k) + W(i, j, k));
+          double ubk = 0.5 * (U(i, j, k - 1) + U(i, j, k));
+          double dwu = (wf * uf - wb * ubk) / dz;
+          double H = -(duu + dvu + dwu);
+          double c0 = U(i, j, k);
+          double ujm = (j > 0) ? U(i, j - 1, k) : gs * c0;
+          double ujp = (j + 1 < ny) ? U(i, j + 1, k) : gs * c0;
+          double L = (U(i + 1, j, k) - 2.0 * c0 + U(i - 1, j, k)) / (dx * dx) +
+                     (ujp - 2.0 * c0 + ujm) / (dy * dy) +
+                     (U(i, j, k + 1) - 2.0 * c0 + U(i, j, k - 1)) / (dz * dz);
+          double G = (P(i, j, k) - P(i - 1, j, k)) / dx;
+          long id = fidx(g, 0, i, j, k);
+          double r = gam * H - alp * G + (alp / re) * L + alp * fb[0];
+          if (rho != 0.0) r += rho * Hu_prev[id];
+          Hu[id] = H;
+          Ru[id] = own_u[id] >= 0 ? 0.0 : dt * r;
+        }
+        /* ---- w at ((i+.5) dx, (j+.5) dy, k dz) ---- */
+        {
+          double ur = 0.5 * (U(i + 1, j, k - 1) + U(i + 1, j, k));
+          double wr = 0.5 * (W(i, j, k) + W(i + 1, j, k));
+          double ul = 0.5 * (U(i, j, k - 1) + U(i, j, k));
+          double wl = 0.5 * (W(i - 1, j, k) + W(i, j, k));
+          double duw = (ur * wr - ul * wl) / dx;
+          double vt = 0.5 * (V(i, j + 1, k - 1) + V(i, j + 1, k));
+          double wt = (j + 1 < ny) ? 0.5 * (W(i, j, k) + W(i, j + 1, k)) : 0.0;
+          double vb = 0.5 * (V(i, j, k - 1) + V(i, j, k));
+          double wbj = (j > 0) ? 0.5 * (W(i, j - 1, k) + W(i, j, k)) : 0.0;
+          double dvw = (vt * wt - vb * wbj) / dy;
+          double wc_p = 0.5 * (W(i, j, k) + W(i, j, k + 1));
+          double wc_m = 0.5 * (W(i, j, k - 1) + W(i, j, k));
+          double dww = (wc_p * wc_p - wc_m * wc_m) / dz;
+          double H = -(duw + dvw + dww);
+          double c0 = W(i, j, k);
+          double wjm = (j > 0) ? W(i, j - 1, k) : gs * c0;
+          double wjp = (j + 1 < ny) ? W(i, j + 1, k) : gs * c0;
+          double L = (W(i + 1, j, k) - 2.0 * c0 + W(i - 1, j, k)) / (dx * dx) +
+                     (wjp - 2.0 * c0 + wjm) / (dy * dy) +
+                     (W(i, j, k + 1) - 2.0 * c0 + W(i, j, k - 1)) / (dz * dz);
+          double G = (P(i, j, k) - P(i, j, k - 1)) / dz;
+          long id = fidx(g, 2, i, j, k);
+          double r = gam * H - alp * G + (alp / re) * L + alp * fb[2];
+          if (rho != 0.0) r += rho * Hw_prev[id];
+          Hw[id] = H;
+          Rw[id] = own_w[id] >= 0 ? 0.0 : dt * r;
+        }
+        /* ---- v at ((i+.5) dx, j dy, (k+.5) dz), interior faces only ---- */
+        if (j >= 1) {
+          double ur = 0.5 * (U(i + 1, j - 1, k) + U(i + 1, j, k));
+          double vr = 0.5 * (V(i, j, k) + V(i + 1, j, k));
+          double ul = 0.5 * (U(i, j - 1, k) + U(i, j, k));
+          double vl = 0.5 * (V(i - 1, j, k) + V(i, j, k));
+          double duv = (ur * vr - ul * vl) / dx;
+          double vc_p = 0.5 * (V(i, j, k) + V(i, j + 1, k));
+          double vc_m = 0.5 * (V(i, j - 1, k) + V(i, j, k));
+          double dvv = (vc_p * vc_p - vc_m * vc_m) / dy;
+          double wf = 0.5 * (W(i, j - 1, k + 1) + W(i, j, k + 1));
+          double vf = 0.5 * (V(i, j, k) + V(i, j, k + 1));
+          double wb = 0.5 * (W(i, j - 1, k) + W(i, j, k));
+          double vbk = 0.5 * (V(i, j, k - 1) + V(i, j, k));
+          double dwv = (wf * vf - wb * vbk) / dz;
+          double H = -(duv + dvv + dwv);
+          double c0 = V(i, j, k);
+          double L = (V(i + 1, j, k) - 2.0 * c0 + V(i - 1, j, k)) / (dx * dx) +
+                     (V(i, j + 1, k) - 2.0 * c0 + V(i, j - 1, k)) / (dy * dy) +
+                     (V(i, j, k + 1) - 2.0 * c0 + V(i, j, k - 1)) / (dz * dz);
+          double G = (P(i, j, k) - P(i, j - 1, k)) / dy;
+          long id = fidx(g, 1, i, j, k);
+          double r = gam * H - alp * G + (alp / re) * L + alp * fb[1];
+          if (rho != 0.0) r += rho * Hv_prev[id];
+          Hv[id] = H;
+          Rv[id] = own_v[id] >= 0 ? 0.0 : dt * r;
+        }
+      }
+  /* wall planes of v carry no unknown */
+  for (long k = 0; k < nz; ++k)
+    for (long i = 0; i < nx; ++i) {
+      Rv[fidx(g, 1, i, 0, k)] = 0.0;  Hv[fidx(g, 1, i, 0, k)] = 0.0;
+      Rv[fidx(g, 1, i, ny, k)] = 0.0; Hv[fidx(g, 1, i, ny, k)] = 0.0;
+    }
+#undef U
+#undef V
+#undef W
+#undef P
+}
+
+/* ------------------------------------------------------------------ */
+/* Tridiagonal solvers (Thomas algorithm, and its periodic variant by   */
+/* the Sherman-Morrison correction).  a = sub, b = diag, c = super.     */
+/* ------------------------------------------------------------------ */
+static void thomas(int n, const double* a, const double* b, const double* c, double* x, double* cw) {
+  /* solves in place: x holds the right-hand side on entry */
+  cw[0] = c[0] / b[0];
+  x[0] = x[0] / b[0];
+  for (int i = 1; i < n; ++i) {
+    double den = b[i] - a[i] * cw[i - 1];
+    cw[i] = c[i] / den;
+    x[i] = (x[i] - a[i] * x[i - 1]) / den;
+  }
+  for (int i = n - 2; i >= 0; --i) x[i] = x[i] - cw[i] * x[i + 1];
+}
+
+/* periodic system: a[0] couples row 0 to x[n-1], c[n-1] couples row n-1 to x[0] */
+static void thomas_periodic(int n, const double* a, const double* b, const double* c, double* x,
+                            double* bb, double* z, double* cw) {
+  double gam = -b[0];
+  for (int i = 0; i < n; ++i) bb[i] = b[i];
+  bb[0] = b[0] - gam;
+  bb[n - 1] = b[n - 1] - c[n - 1] * a[0] / gam;
+  thomas(n, a, bb, c, x, cw);
+  for (int i = 0; i < n; ++i) z[i] = 0.0;
+  z[0] = gam;
+  z[n - 1] = c[n - 1];
+  thomas(n, a, bb, c, z, cw);
+  double fact = (x[0] + a[0] * x[n - 1] / gam) / (1.0 + z[0] + a[0] * z[n - 1] / gam);
+  for (int i = 0; i < n; ++i) x[i] -= fact * z[i];
+}
+
+/* ------------------------------------------------------------------ */
+/* Approximate factorisation of the CN operator (Section 2, after Eq.  */
+/* NS_prov): (1 - beta L_x)(1 - beta L_z)(1 - beta L_y) du = R, solved */
+/* one direction at a time, x first, then z, then y; beta =            */
+/* alpha dt / (2 Re).  Forcing nodes are identity rows (the equation is */
+/* solved on all points but the forcing points).  x and z periodic; in  */
+/* y the tangential components use the wall ghost of orc_rhs and v has  */
+/* du = 0 on the wall planes.  In-place on `f` (component c).           */
+/* ------------------------------------------------------------------ */
+void orc_sweep(const orc_grid* g, int c, int dir, double* f, const int32_t* owner, double beta) {
+  const int nx = g->nx, ny = g->ny, nz = g->nz;
+  const long pl = planes(g, c);
+  if (dir == 0 || dir == 2) {
+    const int n = dir == 0 ? nx : nz;
+    const double dd = dir == 0 ? g->dx : g->dz;
+    const double off = beta / (dd * dd);
+    const int nl1 = dir == 0 ? (int)pl : (int)pl;   /* j planes */
+    const int nl2 = dir == 0 ? nz : nx;
+#pragma omp parallel for schedule(static)
+    for (int l2 = 0; l2 < nl2; ++l2) {
+      double *a = malloc(sizeof(double) * n * 7), *b = a + n, *cc = b + n, *x = cc + n, *bb = x + n, *z = bb + n,
+             *cw = z + n;
+      for (int j = 0; j < nl1; ++j) {
+        if (c == 1 && (j == 0 || j == ny)) continue;
+        for (int m = 0; m < n; ++m) {
+          long id = dir == 0 ? fidx(g, c, m, j, l2) : fidx(g, c, l2, j, m);
+          if (owner[id] >= 0) { a[m] = 0.0; b[m] = 1.0; cc[m] = 0.0; }
+          else { a[m] = -off; b[m] = 1.0 + 2.0 * off; cc[m] = -off; }
+          x[m] = f[id];
+        }
+        thomas_periodic(n, a, b, cc, x, bb, z, cw);
+        for (int m = 0; m < n; ++m) {
+          long id = dir == 0 ? fidx(g, c, m, j, l2) : fidx(g, c, l2, j, m);
+          f[id] = x[m];
+        }
+      }
+      free(a);
+    }
+  } else {
+    const double off = beta / (g->dy * g->dy);
+    const double gs = (g->ybc == 0) ? -1.0 : 1.0;
+    const int j0 = (c == 1) ? 1 : 0, j1 = (c == 1) ? ny - 1 : ny - 1;
+    const int n = j1 - j0 + 1;
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < nz; ++k) {
+      double *a = malloc(sizeof(double) * n * 5), *b = a + n, *cc = b + n, *x = cc + n, *cw = x + n;
+      for (int i = 0; i < nx; ++i) {
+        for (int m = 0; m < n; ++m) {
+          long id = fidx(g, c, i, j0 + m, k);
+          if (owner[id] >= 0) { a[m] = 0.0; b[m] = 1.0; cc[m] = 0.0; }
+          else {
+            a[m] = -off; b[m] = 1.0 + 2.0 * off; cc[m] = -off;
+            if (c != 1) {
+              /* ghost du_{-1} = gs du_0 folds into the diagonal of the wall rows */
+              if (m == 0) { b[m] -= gs * off; a[m] = 0.0; }
+              if (m == n - 1) { b[m] -= gs * off; cc[m] = 0.0; }
+            } else {
+              if (m == 0) a[m] = 0.0;
+              if (m == n - 1) cc[m] = 0.0;
+            }
+          }
+          x[m] = f[id];
+        }
+        thomas(n, a, b, cc, x, cw);
+        for (int m = 0; m < n; ++m) f[fidx(g, c, i, j0 + m, k)] = x[m];
+      }
+      free(a);
+    }
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* Discrete divergence (Eq. discrete_div) at every cell centre.        */
+/* ------------------------------------------------------------------ */
+void orc_divergence(const orc_grid* g, const double* u, const double* v, const double* w, double* div) {
+  const int nx = g->nx, ny = g->ny, nz = g->nz;
+#pragma omp parallel for schedule(static)
+  for (long k = 0; k < nz; ++k)
+    for (long j = 0; j < ny; ++j)
+      for (long i = 0; i < nx; ++i) {
+        double du = (u[fidx(g, 0, wrap(i + 1, nx), j, k)] - u[fidx(g, 0, i, j, k)]) / g->dx;
+        double dv = (v[fidx(g, 1, i, j + 1, k)] - v[fidx(g, 1, i, j, k)]) / g->dy;
+        double dw = (w[fidx(g, 2, i, j, wrap(k + 1, nz))] - w[fidx(g, 2, i, j, k)]) / g->dz;
+        div[cidx(g, i, j, k)] = du + dv + dw;
+      }
+}
+
+/* Boundary-cell flags (Section 3.2, Fig. fluid_and_boundary_cells): a cell
+ * is a boundary cell when every one of its six faces holds a forcing node
+ * of the velocity component living there. */
+void orc_boundary_cells(const orc_grid* g, const int32_t* own_u, const int32_t* own_v, const int32_t* own_w,
+                        uint8_t* isb) {
+  const int nx = g->nx, ny = g->ny, nz = g->nz;
+  for (long k = 0; k < nz; ++k)
+    for (long j = 0; j < ny; ++j)
+      for (long i = 0; i < nx; ++i) {
+        int all = own_u[fidx(g, 0, i, j, k)] >= 0 && own_u[fidx(g, 0, wrap(i + 1, nx), j, k)] >= 0 &&
+                  own_v[fidx(g, 1, i, j, k)] >= 0 && own_v[fidx(g, 1, i, j + 1, k)] >= 0 &&
+                  own_w[fidx(g, 2, i, j, k)] >= 0 && own_w[fidx(g, 2, i, j, wrap(k + 1, nz))] >= 0;
+        isb[cidx(g, i, j, k)] = (uint8_t)all;
+      }
+}
+
+/* Consistent mass correction and right-hand side of Eq. elliptic_mod:
+ *   q_B = D uhat on boundary cells (Eq. q_boundary),
+ *   q_F = -(1/|C_F|) sum_{C_B} D uhat dV, uniform on fluid cells,
+ *   rhs = (D uhat - q) / (alpha dt)  (zero on C_B by construction).
+ * With use_q = 0, q = 0 everywhere (the standard Eq. elliptic).  Returns
+ * q_F; A = sum_{C_B} D uhat dV and V_F = |C_F| through pointers.  The sums
+ * run in plain index order. */
+double orc_rhs_poisson(const orc_grid* g, const double* div, const uint8_t* isb, int use_q, double adt,
+                       double* rhs, double* A_out, double* VF_out) {
+  const long n = (long)g->nx * g->ny * g->nz;
+  const double dV = (g->dx * g->dy) * g->dz;
+  double A = 0.0, VF = 0.0;
+  for (long id = 0; id < n; ++id) {
+    if (isb[id]) A += div[id] * dV;
+    else VF += dV;
+  }
+  double qF = (use_q && VF > 0.0) ? -A / VF : 0.0;
+  for (long id = 0; id < n; ++id) {
+    double q = use_q ? (isb[id] ? div[id] : qF) : 0.0;
+    rhs[id] = (div[id] - q) / adt;
+  }
+  *A_out = A;
+  *VF_out = VF;
+  return qF;
+}
+
+/* ------------------------------------------------------------------ */
+/* Wall-normal solve of the Poisson equation per Fourier mode (Eq.     */
+/* elliptic, solved with FFTs in x and z and the Thomas algorithm in   */
+/* y).  spec is [kz][j][kx] complex (re,im interleaved), nkx = nx/2+1; */
+/* in place.  Row j: (phi_{j+1} - 2 phi_j + phi_{j-1})/dy^2            */
+/*   - (lx + lz) phi_j = r_j, homogeneous Neumann at both walls, with    */
+/* lx = (2 - 2 cos(2 pi kx / nx))/dx^2 (modified wavenumber of the      */
+/* second difference), lz likewise.  Mode (0,0) is singular: phi_0 is   */
+/* pinned to 0 and the mean over j is then removed (zero-mean gauge).   */
+/* ------------------------------------------------------------------ */
+void orc_poisson_y(const orc_grid* g, double* spec) {
+  const int nx = g->nx, ny = g->ny, nz = g->nz, nkx = nx / 2 + 1;
+  const double pi = 3.14159265358979323846;
+  const double idy2 = 1.0 / (g->dy * g->dy);
+#pragma omp parallel for schedule(static)
+  for (int kz = 0; kz < nz; ++kz) {
+    double *a = malloc(sizeof(double) * ny * 6), *b = a + ny, *c = b + ny, *xr = c + ny, *xi = xr + ny,
+           *cw = xi + ny;
+    for (int kx = 0; kx < nkx; ++kx) {
+      double lam = (2.0 - 2.0 * cos(2.0 * pi * kx / nx)) / (g->dx * g->dx) +
+                   (2.0 - 2.0 * cos(2.0 * pi * kz / nz)) / (g->dz * g->dz);
+      for (int j = 0; j < ny; ++j) {
+        a[j] = (j > 0) ? idy2 : 0.0;
+        c[j] = (j < ny - 1) ? idy2 : 0.0;
+        b[j] = -a[j] - c[j] - lam;
+        long id = ((long)kz * ny + j) * nkx + kx;
+        xr[j] = spec[2 * id];
+        xi[j] = spec[2 * id + 1];
+      }
+      int singular = (kx == 0 && kz == 0);
+      if (singular) { b[0] = 1.0; c[0] = 0.0; xr[0] = 0.0; xi[0] = 0.0; }
+      thomas(ny, a, b, c, xr, cw);
+      thomas(ny, a, b, c, xi, cw);
+      if (singular) {
+        double mr = 0.0, mi = 0.0;
+        for (int j = 0; j < ny; ++j) { mr += xr[j]; mi += xi[j]; }
+        mr /= ny; mi /= ny;
+        for (int j = 0; j < ny; ++j) { xr[j] -= mr; xi[j] -= mi; }
+      }
+      for (int j = 0; j < ny; ++j) {
+        long id = ((long)kz * ny + j) * nkx + kx;
+        spec[2 * id] = xr[j];
+        spec[2 * id + 1] = xi[j];
+      }
+    }
+    free(a);
+  }
+}
+
+/* L_c = D G on the pressure grid with homogeneous Neumann walls (Eq. elliptic). */
+void orc_lap_c(const orc_grid* g, const double* phi, double* out) {
+  const int nx = g->nx, ny = g->ny, nz = g->nz;
+#pragma omp parallel for schedule(static)
+  for (long k = 0; k < nz; ++k)
+    for (long j = 0; j < ny; ++j)
+      for (long i = 0; i < nx; ++i) {
+        double c0 = phi[cidx(g, i, j, k)];
+        double lx = (phi[cidx(g, wrap(i + 1, nx), j, k)] - 2.0 * c0 + phi[cidx(g, wrap(i - 1, nx), j, k)]) /
+                    (g->dx * g->dx);
+        double lz = (phi[cidx(g, i, j, wrap(k + 1, nz))] - 2.0 * c0 + phi[cidx(g, i, j, wrap(k - 1, nz))]) /
+                    (g->dz * g->dz);
+        double up = (j + 1 < ny) ? (phi[cidx(g, i, j + 1, k)] - c0) : 0.0;
+        double dn = (j > 0) ? (c0 - phi[cidx(g, i, j - 1, k)]) : 0.0;
+        double ly = (up - dn) / (g->dy * g->dy);
+        out[cidx(g, i, j, k)] = lx + ly + lz;
+      }
+}
+
+/* Projection (Eq. projection) and pressure update (Eq. update_pressure):
+ *   u^{s+1} = uhat - alpha dt G phi   (v on the wall planes untouched)
+ *   p^{s+1} = p^s + phi - alpha dt / (2 Re) L_c phi.
+ * lapphi is L_c phi from orc_lap_c. */
+void orc_project(const orc_grid* g, double* u, double* v, double* w, double* p, const double* phi,
+                 const double* lapphi, double adt, double re) {
+  const int nx = g->nx, ny = g->ny, nz = g->nz;
+#pragma omp parallel for schedule(static)
+  for (long k = 0; k < nz; ++k)
+    for (long j = 0; j < ny; ++j)
+      for (long i = 0; i < nx; ++i) {
+        double c0 = phi[cidx(g, i, j, k)];
+        u[fidx(g, 0, i, j, k)] -= adt * (c0 - phi[cidx(g, wrap(i - 1, nx), j, k)]) / g->dx;
+        w[fidx(g, 2, i, j, k)] -= adt * (c0 - phi[cidx(g, i, j, wrap(k - 1, nz))]) / g->dz;
+        if (j >= 1) v[fidx(g, 1, i, j, k)] -= adt * (c0 - phi[cidx(g, i, j - 1, k)]) / g->dy;
+        p[cidx(g, i, j, k)] += c0 - adt / (2.0 * re) * lapphi[cidx(g, i, j, k)];
+      }
+}

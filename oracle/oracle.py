@@ -1,0 +1,330 @@
+"""Plain FP64 CPU oracle of the sharp-interface IBM fractional step.
+
+TEST INFRASTRUCTURE ONLY: imported by the test-suite, by the smoke check and
+by the CPU-baseline leg of the benchmark, never by the product path.  It
+shares no code with the CUDA library; the two meet only through the data
+format (arrays [k][j][i], i fastest) and the seeded input generators.
+
+The time step follows the paper's order (Section 2 and Section 3):
+
+  once per step   Algorithm 1 tagging of the three staggered grids
+  per sub-stage   IB step on the forcing nodes (Eqs. IB_step, probe, new_IB)
+                  explicit right-hand side of Eq. NS_prov
+                  approximate factorisation: x, then z, then y sweeps
+                  divergence, boundary cells and q (Eqs. q_boundary, q_F)
+                  Poisson solve of Eq. elliptic_mod: FFT in x and z
+                  (numpy.fft, the one library step), Thomas in y
+                  projection (Eq. projection), pressure (Eq. update_pressure)
+  after the step  no-slip error on the forcing points (Section 4.4)
+
+The C kernels live in ibm_oracle.c; this module compiles it on first use.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ibm_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_SO = os.path.join(_OUT_DIR, "libibm_oracle.so")
+_LIB = None
+_LOCK = threading.Lock()
+
+RK2_CN = "rk2"
+AB_CN = "ab"
+# (gamma, rho, alpha) per sub-stage, Section 2 after Eq. NS_prov
+SCHEMES = {
+    RK2_CN: ((0.5, 0.0, 0.5), (1.0, -0.5, 0.5)),
+    AB_CN: ((1.5, -0.5, 1.0),),
+}
+
+
+def build(force: bool = False) -> str:
+    """Compile ibm_oracle.c into a shared library (no FMA contraction)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+               "-fopenmp", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _SO)
+    return _SO
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("ybc", ctypes.c_int),
+                ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double)]
+
+
+_P = ctypes.c_void_p
+_D = ctypes.c_double
+_I = ctypes.c_int
+_GP = ctypes.POINTER(Grid)
+
+
+def lib():
+    global _LIB
+    with _LOCK:
+        if _LIB is None:
+            build()
+            L = ctypes.CDLL(_SO)
+            L.orc_threads.restype = _I
+            L.orc_grid_init.argtypes = [_GP, _I, _I, _I, _D, _D, _D, _I]
+            L.orc_closest_point.argtypes = [_P] * 6
+            L.orc_tag_alg1.argtypes = [_GP, _I, _P, _I, _P, _P, _P]
+            L.orc_tag_brute.argtypes = [_GP, _I, _P, _I, _P, _P, _P]
+            L.orc_force.argtypes = [_GP, _I, _P, _P, _P, _P, _P, _P, _D]
+            L.orc_force.restype = _I
+            L.orc_slip.argtypes = [_GP, _I, _P, _P, _P, _P, _P, _D, _P, _P]
+            L.orc_slip.restype = _I
+            L.orc_rhs.argtypes = [_GP] + [_P] * 10 + [_D] * 5 + [_P] * 7
+            L.orc_sweep.argtypes = [_GP, _I, _I, _P, _P, _D]
+            L.orc_divergence.argtypes = [_GP, _P, _P, _P, _P]
+            L.orc_boundary_cells.argtypes = [_GP, _P, _P, _P, _P]
+            L.orc_rhs_poisson.argtypes = [_GP, _P, _P, _I, _D, _P, _P, _P]
+            L.orc_rhs_poisson.restype = _D
+            L.orc_poisson_y.argtypes = [_GP, _P]
+            L.orc_lap_c.argtypes = [_GP, _P, _P]
+            L.orc_project.argtypes = [_GP, _P, _P, _P, _P, _P, _P, _D, _D]
+            _LIB = L
+    return _LIB
+
+
+def _p(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def threads() -> int:
+    return int(lib().orc_threads())
+
+
+def make_grid(nx, ny, nz, lx=1.0, ly=1.0, lz=1.0, ybc=0) -> Grid:
+    g = Grid()
+    lib().orc_grid_init(ctypes.byref(g), nx, ny, nz, lx, ly, lz, ybc)
+    return g
+
+
+def field_shape(g: Grid, c: int):
+    return (g.nz, g.ny + 1 if c == 1 else g.ny, g.nx)
+
+
+def closest_point(p, a, b, c):
+    """Closest point X on triangle (a,b,c) to p and its barycentric weights."""
+    arrs = [np.ascontiguousarray(x, dtype=np.float64) for x in (p, a, b, c)]
+    X = np.zeros(3)
+    w = np.zeros(3)
+    lib().orc_closest_point(*[_p(x) for x in arrs], _p(X), _p(w))
+    return X, w
+
+
+def tag(g: Grid, xyz: np.ndarray, tri: np.ndarray, brute: bool = False):
+    """Algorithm 1 on the three staggered grids.  Returns (owner, d2) lists;
+    owner = -1 on fluid nodes, else the owning triangle index."""
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    tri = np.ascontiguousarray(tri, dtype=np.int32)
+    owners, d2s = [], []
+    fn = lib().orc_tag_brute if brute else lib().orc_tag_alg1
+    for c in range(3):
+        own = np.full(field_shape(g, c), -1, dtype=np.int32)
+        d2 = np.full(field_shape(g, c), np.inf)
+        fn(ctypes.byref(g), c, _p(xyz), int(tri.shape[0]), _p(tri), _p(own), _p(d2))
+        owners.append(own)
+        d2s.append(d2)
+    return owners, d2s
+
+
+def boundary_cells(g: Grid, owners):
+    isb = np.zeros((g.nz, g.ny, g.nx), dtype=np.uint8)
+    lib().orc_boundary_cells(ctypes.byref(g), _p(owners[0]), _p(owners[1]), _p(owners[2]), _p(isb))
+    return isb
+
+
+def divergence(g: Grid, u, v, w):
+    d = np.zeros((g.nz, g.ny, g.nx))
+    lib().orc_divergence(ctypes.byref(g), _p(u), _p(v), _p(w), _p(d))
+    return d
+
+
+def lap_c(g: Grid, phi):
+    out = np.zeros_like(phi)
+    lib().orc_lap_c(ctypes.byref(g), _p(phi), _p(out))
+    return out
+
+
+def poisson(g: Grid, rhs: np.ndarray) -> np.ndarray:
+    """Solve L_c phi = rhs (Eq. elliptic): FFT in x and z, Thomas in y per
+    mode, zero-mean gauge."""
+    spec = np.ascontiguousarray(np.fft.rfft2(rhs, axes=(0, 2)))
+    buf = spec.view(np.float64)
+    lib().orc_poisson_y(ctypes.byref(g), _p(buf))
+    return np.ascontiguousarray(np.fft.irfft2(spec, s=(g.nz, g.nx), axes=(0, 2)))
+
+
+def sweep(g: Grid, c: int, direction: int, f: np.ndarray, owner: np.ndarray, beta: float):
+    lib().orc_sweep(ctypes.byref(g), c, direction, _p(f), _p(owner), beta)
+
+
+def no_tags(g: Grid):
+    return [np.full(field_shape(g, c), -1, dtype=np.int32) for c in range(3)]
+
+
+def rhs(g: Grid, u, v, w, p, owners, gam, rho, alp, dt, re, fb=(0.0, 0.0, 0.0), Hprev=None):
+    """Explicit right-hand side of Eq. NS_prov; returns (R, H) lists."""
+    if Hprev is None:
+        Hprev = [np.zeros(field_shape(g, c)) for c in range(3)]
+    fb = np.ascontiguousarray(fb, dtype=np.float64)
+    R = [np.zeros(field_shape(g, c)) for c in range(3)]
+    H = [np.zeros(field_shape(g, c)) for c in range(3)]
+    lib().orc_rhs(ctypes.byref(g), _p(u), _p(v), _p(w), _p(p), _p(Hprev[0]), _p(Hprev[1]), _p(Hprev[2]),
+                  _p(owners[0]), _p(owners[1]), _p(owners[2]), gam, rho, alp, dt, re, _p(fb),
+                  _p(R[0]), _p(R[1]), _p(R[2]), _p(H[0]), _p(H[1]), _p(H[2]))
+    return R, H
+
+
+def force(g: Grid, c, src, dst, owner, xyz, vel, tri, h):
+    """Eq. new_IB on the forcing nodes of component c (dst updated in place)."""
+    bad = lib().orc_force(ctypes.byref(g), c, _p(src), _p(dst), _p(owner),
+                          _p(np.ascontiguousarray(xyz, dtype=np.float64)),
+                          _p(np.ascontiguousarray(vel, dtype=np.float64)),
+                          _p(np.ascontiguousarray(tri, dtype=np.int32)), h)
+    return int(bad)
+
+
+def rhs_poisson(g: Grid, div, isb, use_q, adt):
+    out = np.zeros_like(div)
+    A = ctypes.c_double()
+    VF = ctypes.c_double()
+    qF = lib().orc_rhs_poisson(ctypes.byref(g), _p(div), _p(isb), int(use_q), adt, _p(out),
+                               ctypes.byref(A), ctypes.byref(VF))
+    return out, qF, A.value, VF.value
+
+
+def project(g: Grid, u, v, w, p, phi, adt, re):
+    lp = lap_c(g, phi)
+    lib().orc_project(ctypes.byref(g), _p(u), _p(v), _p(w), _p(p), _p(phi), _p(lp), adt, re)
+
+
+class OracleSim:
+    """One simulation instance advanced by the plain FP64 oracle."""
+
+    def __init__(self, nx, ny, nz, lx=1.0, ly=1.0, lz=1.0, re=100.0, dt=1e-3, scheme=RK2_CN, ybc=0,
+                 use_q=True):
+        self.g = make_grid(nx, ny, nz, lx, ly, lz, ybc)
+        self.re, self.dt, self.scheme, self.use_q = float(re), float(dt), scheme, bool(use_q)
+        g = self.g
+        self.u = np.zeros(field_shape(g, 0))
+        self.v = np.zeros(field_shape(g, 1))
+        self.w = np.zeros(field_shape(g, 2))
+        self.p = np.zeros((nz, ny, nx))
+        self.H = [np.zeros(field_shape(g, c)) for c in range(3)]
+        self.fb = np.zeros(3)
+        self.xyz = np.zeros((0, 3))
+        self.vel = np.zeros((0, 3))
+        self.tri = np.zeros((0, 3), dtype=np.int32)
+        diag = np.sqrt((g.dx * g.dx + g.dy * g.dy) + g.dz * g.dz)
+        self.h = 2.0 * diag                     # probe length, Section 3.1
+        self.owners = None
+        self.last = {}
+        self.nsteps = 0
+
+    # -- inputs ----------------------------------------------------------
+    def set_fields(self, u, v, w, p):
+        self.u[...] = u
+        self.v[...] = v
+        self.w[...] = w
+        self.p[...] = p
+
+    def set_surface(self, xyz, vel, tri):
+        self.xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+        self.vel = np.ascontiguousarray(vel, dtype=np.float64).reshape(-1, 3)
+        self.tri = np.ascontiguousarray(tri, dtype=np.int32).reshape(-1, 3)
+
+    def set_body_force(self, fx, fy, fz):
+        self.fb = np.array([fx, fy, fz], dtype=np.float64)
+
+    def fields(self):
+        return self.u, self.v, self.w, self.p
+
+    # -- stages ----------------------------------------------------------
+    def _tag(self):
+        if self.tri.shape[0] == 0:
+            self.owners = [np.full(field_shape(self.g, c), -1, dtype=np.int32) for c in range(3)]
+        else:
+            self.owners, _ = tag(self.g, self.xyz, self.tri)
+        self.isb = boundary_cells(self.g, self.owners)
+
+    def _force(self):
+        L, g = lib(), self.g
+        flds = [self.u, self.v, self.w]
+        snaps = [f.copy() for f in flds]          # u^e always from the snapshot of u^s
+        for c in range(3):
+            bad = L.orc_force(ctypes.byref(g), c, _p(snaps[c]), _p(flds[c]), _p(self.owners[c]),
+                              _p(self.xyz), _p(self.vel), _p(self.tri), self.h)
+            if bad:
+                raise RuntimeError(f"{bad} IB probes of component {c} left the domain")
+
+    def _substage(self, gam, rho, alp):
+        L, g = lib(), self.g
+        dt, re = self.dt, self.re
+        if self.tri.shape[0]:
+            self._force()
+        R = [np.zeros(field_shape(g, c)) for c in range(3)]
+        Hn = [np.zeros(field_shape(g, c)) for c in range(3)]
+        L.orc_rhs(ctypes.byref(g), _p(self.u), _p(self.v), _p(self.w), _p(self.p),
+                  _p(self.H[0]), _p(self.H[1]), _p(self.H[2]),
+                  _p(self.owners[0]), _p(self.owners[1]), _p(self.owners[2]),
+                  gam, rho, alp, dt, re, _p(self.fb), _p(R[0]), _p(R[1]), _p(R[2]),
+                  _p(Hn[0]), _p(Hn[1]), _p(Hn[2]))
+        beta = alp * dt / (2.0 * re)
+        for c in range(3):
+            for d in (0, 2, 1):
+                sweep(g, c, d, R[c], self.owners[c], beta)
+        self.u += R[0]
+        self.v += R[1]
+        self.w += R[2]
+        adt = alp * dt
+        div = divergence(g, self.u, self.v, self.w)
+        rhs = np.zeros_like(div)
+        A = ctypes.c_double()
+        VF = ctypes.c_double()
+        qF = L.orc_rhs_poisson(ctypes.byref(g), _p(div), _p(self.isb), int(self.use_q), adt, _p(rhs),
+                               ctypes.byref(A), ctypes.byref(VF))
+        phi = poisson(g, rhs)
+        lp = lap_c(g, phi)
+        L.orc_project(ctypes.byref(g), _p(self.u), _p(self.v), _p(self.w), _p(self.p), _p(phi), _p(lp), adt, re)
+        self.H = Hn
+        self.last.update(qF=qF, A=A.value, VF=VF.value, phi=phi, rhs=rhs, div_hat=div)
+
+    def slip(self):
+        """||eps||_1 = sum_i ||eps_i||_1 / 3, ||eps_i||_1 = mean |eps_i| over
+        the forcing points of component i (Section 4.4)."""
+        L, g = lib(), self.g
+        tot, per = 0.0, []
+        for c, f in enumerate((self.u, self.v, self.w)):
+            s = ctypes.c_double()
+            n = ctypes.c_long()
+            bad = L.orc_slip(ctypes.byref(g), c, _p(f), _p(self.owners[c]), _p(self.xyz), _p(self.vel),
+                             _p(self.tri), self.h, ctypes.byref(s), ctypes.byref(n))
+            if bad:
+                raise RuntimeError("slip probe left the domain")
+            m = s.value / n.value if n.value else 0.0
+            per.append((m, n.value))
+            tot += m
+        return tot / 3.0, per
+
+    def step(self, n: int = 1):
+        for _ in range(n):
+            self._tag()
+            for (gam, rho, alp) in SCHEMES[self.scheme]:
+                self._substage(gam, rho, alp)
+            self.nsteps += 1
+            if self.tri.shape[0]:
+                self.last["slip"], self.last["slip_per_comp"] = self.slip()
+        return self
