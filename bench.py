@@ -1,0 +1,367 @@
+#!/usr/bin/env python
+"""Throughput of the sharp-interface IBM fractional step on GB300.
+
+Metric: fractional-step cell updates per second (GCUPS): one update = one
+cell through a whole time step (Algorithm 1 tagging of the three grids and
+both RK2+CN sub-stages: IB forcing, explicit terms, factorised implicit
+sweeps, consistent mass correction q, FFT/Thomas Poisson solve, projection),
+plus the no-slip error diagnostic.
+
+Workload (one step): the 128^3 zero-thickness plate -- staggered grid on the
+unit cube, periodic x and z, walls at y = 0, 1; square plate of side 0.4
+triangulated 64 x 64 (8,192 triangles) heaving 0.05 sin(2 pi t) with the
+bending mode 0.02 sin(pi s) sin(2 pi t); Re = 200, dt = 5e-4, fluid at rest.
+The surface of every step is prescribed (moved between steps).
+
+Arms
+  default            the CUDA library through its C ABI; the mixed
+                     (FP32 bulk / FP64 tagging, tridiagonal, geometry) and the
+                     FP64 paths run on the same inputs, `value` is the
+                     headline path (--precision), the other is reported beside
+                     it with its no-slip error.
+  --impl reference   the plain FP64 CPU oracle on the host cores, same
+                     workload and metric (one whole oracle step per step).
+
+Launch: python bench.py [--gpus N --steps K --warmup W]; for N > 1 under
+torchrun, one rank per GPU, each advancing its own replica (no collective
+on the data path), the barrier-bracketed time taken as the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fractional-step cell updates/s (GCUPS), mixed vs FP64 at equal slip error"
+UNIT = "GCUPS"
+WORKLOAD = ("plate128: 128^3 staggered grid on the unit cube (x, z periodic, no-slip walls in y), "
+            "zero-thickness square plate of side 0.4 triangulated 64x64 (8192 triangles) heaving "
+            "0.05 sin(2 pi t) plus bending 0.02 sin(pi s) sin(2 pi t); Re=200, dt=5e-4, RK2+CN, fluid at rest")
+L2_FLUSH_BYTES = 256 << 20
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+# ---------------------------------------------------------------------------
+# clocks sampler (nvidia-smi during the timed region)
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        loaded = [s for s in sm if s >= 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# roofline bookkeeping: algorithmic bytes (FP32/mixed) and FP64 flops per cell
+# ---------------------------------------------------------------------------
+def algorithmic_bytes_per_cell(stage: str, word: int) -> float:
+    """Compulsory words per cell of each kernel group and sub-stage: one read
+    of every input field, one write of every output field (the sparse IB
+    part is counted per forcing node elsewhere)."""
+    reads_writes = {
+        "rhs": (5.5, 4.5),          # u, v, w, p (+ H^{s-1} on sub-stage 2, averaged) -> R x3 (+ H x3 on sub-stage 1)
+        "sweep_x": (3, 3),
+        "sweep_z": (3, 3),
+        "sweep_y": (6, 3),          # du x3 and u^s x3 -> uhat x3
+        "fft_x_fwd": (3, 1),        # uhat x3 -> half spectrum (2 words x (nx/2+1)/nx)
+        "fft_z_fwd": (1, 1),
+        "tri_y": (1, 1),
+        "fft_z_inv": (1, 1),
+        "fft_x_inv": (1, 1),
+        "project": (5, 4),          # uhat x3, phi, p -> u x3, p
+    }
+    r, w = reads_writes.get(stage, (0, 0))
+    return (r + w) * word
+
+
+def fp64_flops_per_cell(stage: str) -> float:
+    """FP64 floating-point operations per cell of each kernel group in the
+    FP64 path (adds, multiplies and FMAs counted as executed instructions x
+    flops: an FMA counts 2), counted from the kernel source."""
+    return {"rhs": 150.0, "sweep_x": 15.0, "sweep_z": 15.0, "sweep_y": 15.0, "fft_x_fwd": 45.0,
+            "fft_z_fwd": 40.0, "tri_y": 8.0, "fft_z_inv": 40.0, "fft_x_inv": 40.0, "project": 30.0}.get(stage, 0.0)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def gpu_arm(args):
+    import numpy as np
+    import torch
+    from paper_2606_09799_gb300 import ibm, inputs
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    wl = inputs.heaving_plate()
+    K, W = args.steps, args.warmup
+    nsteps_total = W + K
+    tri = wl.tri
+    # every step's surface, resident on the device before timing
+    surf = [wl.surface(s) for s in range(nsteps_total + 1)]
+    dxyz = [torch.from_numpy(x).to(dev) for x, _ in surf]
+    dvel = [torch.from_numpy(v).to(dev) for _, v in surf]
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    results = {}
+    order = [args.precision] + [p for p in ("mixed", "fp64") if p != args.precision]
+    if args.only_headline:
+        order = order[:1]
+    for prec in order:
+        sim = ibm.Simulation(wl.nx, wl.ny, wl.nz, wl.lx, wl.ly, wl.lz, re=wl.re, dt=wl.dt, precision=prec,
+                             stream=stream.cuda_stream)
+        sim.set_surface(surf[0][0], surf[0][1], tri)
+        for s in range(W):
+            sim.set_surface(dxyz[s], dvel[s])
+            sim.step(1)
+        sim.sync()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(local) as clk:
+            for n in range(K):
+                flush.fill_(n & 0xFF)                        # L2 flush between timed steps (outside the events)
+                ev[n][0].record(stream)
+                sim.set_surface(dxyz[W + n], dvel[W + n])    # this step's prescribed surface (device resident)
+                sim.step(1)
+                ev[n][1].record(stream)
+            torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        diag = sim.diag()
+        sim.sync()
+        if world > 1:
+            t = torch.tensor([ms], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        # stage profile of the same workload (CUDA events recorded on the launching stream)
+        prof = ibm.ibm_profile_stages(sim.h, args.profile_steps)
+        # end-to-end: host surface in pinned memory -> device, step, diagnostics read back
+        hx = torch.from_numpy(surf[0][0]).pin_memory()
+        hv = torch.from_numpy(surf[0][1]).pin_memory()
+        e2e_ms = 0.0
+        d2h = 0
+        torch.cuda.synchronize()
+        ke = max(3, min(K, 20))
+        for n in range(ke):
+            hx.copy_(torch.from_numpy(surf[(W + n) % len(surf)][0]))
+            hv.copy_(torch.from_numpy(surf[(W + n) % len(surf)][1]))
+            flush.fill_(n & 0xFF)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ibm.ibm_set_surface(sim.h, hx, hv, None, tri.shape[0])
+            ibm.ibm_step(sim.h, 1)
+            dd = ibm.ibm_get_diag(sim.h)
+            e2e_ms += (time.perf_counter() - t0) * 1e3
+            d2h = dd["d2h_bytes"]
+        results[prec] = dict(ms=ms, diag=diag, prof=prof, e2e_ms=e2e_ms, e2e_steps=ke, d2h=d2h,
+                             clocks=clk.summary())
+        sim.close()
+    if rank != 0:
+        return None
+    head = results[args.precision]
+    cells = wl.cells
+    value = world * cells * K / (head["ms"] / 1e3) / 1e9
+    e2e_value = world * cells * head["e2e_steps"] / (head["e2e_ms"] / 1e3) / 1e9
+    h2d = 2 * surf[0][0].nbytes
+    peaks = measured_peaks()
+    prof = head["prof"]
+    # dominant kernel group of the headline path
+    stages = {k: v for k, v in prof.items() if k not in ("other",) and v[1] > 0}
+    top = max(stages, key=lambda k: stages[k][0])
+    top_ms, top_groups = stages[top]
+    launches = top_groups * args.profile_steps
+    avg_ms = top_ms / max(1, launches)
+    if args.precision == "fp64":
+        flops = fp64_flops_per_cell(top) * cells
+        achieved = flops / (avg_ms / 1e3) / 1e12
+        peak = args.fp64_peak_tflops
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak if peak else None, "traffic": None, "kernel": top,
+                "peak_source": "FP64 FMA-chain probe on this GB300 (2 FP64 FMA/clk/SM x 152 SM)"}
+    else:
+        byts = algorithmic_bytes_per_cell(top, 4) * cells
+        achieved = byts / (avg_ms / 1e3) / 1e9
+        peak = peaks.get("hbm_gbs", 6800.0)
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": top, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    kernels_per_step = head["diag"]["kernels_per_step"]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": head["ms"] / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cells": cells, "triangles": int(tri.shape[0]),
+                   "precision": args.precision, "parallelism": f"replicas x{world}",
+                   "l2": "flushed between timed steps (256 MiB write outside the events)"},
+        "roofline": roof,
+        "gpu_launches": (kernels_per_step + 2) * K,
+        "clocks": head["clocks"],
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": head["d2h"]},
+        "slip_l1": head["diag"]["slip_l1"],
+        "stages_ms_per_step": {k: v[0] / args.profile_steps for k, v in prof.items() if v[1] > 0},
+    }
+    for prec, r in results.items():
+        line[prec] = {"value": world * cells * K / (r["ms"] / 1e3) / 1e9, "ms_per_step": r["ms"] / K,
+                      "slip_l1": r["diag"]["slip_l1"], "clocks": r["clocks"]}
+    if "mixed" in results and "fp64" in results:
+        sm, sf = results["mixed"]["diag"]["slip_l1"], results["fp64"]["diag"]["slip_l1"]
+        line["slip_rel_diff_mixed_vs_fp64"] = abs(sm - sf) / sf if sf else None
+        line["speedup_mixed_vs_fp64"] = line["mixed"]["value"] / line["fp64"]["value"]
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_steps)
+    return line
+
+
+def cpu_baseline(nsteps: int):
+    """The FP64 CPU oracle as it stands, on a bounded sample of the same
+    workload: its first `nsteps` whole time steps."""
+    from oracle.oracle import OracleSim, threads
+    from paper_2606_09799_gb300 import inputs
+    wl = inputs.heaving_plate()
+    sim = OracleSim(wl.nx, wl.ny, wl.nz, wl.lx, wl.ly, wl.lz, re=wl.re, dt=wl.dt)
+    t0 = time.perf_counter()
+    for s in range(nsteps):
+        xyz, vel = wl.surface(s)
+        sim.set_surface(xyz, vel, wl.tri)
+        sim.step()
+    dt = time.perf_counter() - t0
+    return {"value": wl.cells * nsteps / dt / 1e9, "unit": UNIT, "cores": threads(), "kind": "oracle",
+            "sample": f"first {nsteps} whole time steps of the 128^3 plate workload (FP64, OpenMP loops)",
+            "seconds": dt}
+
+
+def reference_arm(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return None
+    from oracle.oracle import OracleSim, threads
+    from paper_2606_09799_gb300 import inputs
+    wl = inputs.heaving_plate()
+    sim = OracleSim(wl.nx, wl.ny, wl.nz, wl.lx, wl.ly, wl.lz, re=wl.re, dt=wl.dt)
+    for s in range(args.warmup):
+        xyz, vel = wl.surface(s)
+        sim.set_surface(xyz, vel, wl.tri)
+        sim.step()
+    times = []
+    for n in range(args.steps):
+        xyz, vel = wl.surface(args.warmup + n)
+        t0 = time.perf_counter()
+        sim.set_surface(xyz, vel, wl.tri)
+        sim.step()
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = wl.cells * args.steps / total / 1e9
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cells": wl.cells, "triangles": int(wl.tri.shape[0]),
+                   "precision": "fp64", "parallelism": "host cores"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads(), "kind": "oracle",
+                         "sample": f"{args.steps} whole time steps of the 128^3 plate workload after "
+                                   f"{args.warmup} warm-up steps"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "slip_l1": sim.last.get("slip"),
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["mixed", "fp64"])
+    ap.add_argument("--only-headline", action="store_true", help="skip the other precision's run")
+    ap.add_argument("--profile-steps", type=int, default=5)
+    ap.add_argument("--cpu-steps", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-peak-tflops", type=float, default=1.0,
+                    help="measured FP64 FMA throughput of this GB300")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    line = reference_arm(args) if args.impl == "reference" else gpu_arm(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

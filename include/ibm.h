@@ -1,0 +1,175 @@
+/*
+ * ibm.h -- C ABI of the GB300 sharp-interface immersed-boundary fractional
+ * step (Vagnoli, Scarpolini, Verzicco, Viola, arXiv 2606.09799).
+ *
+ * The library advances the incompressible Navier-Stokes equations (Eq. ns,
+ * Section 2) on a staggered Cartesian grid that is periodic in x and z and
+ * bounded by walls at y = 0 and y = ly, with moving triangulated bodies of
+ * any thickness (including zero) immersed in it.  One call of ibm_step runs,
+ * entirely on the GPU:
+ *
+ *   Algorithm 1 tagging of the forcing nodes of the three velocity grids;
+ *   per sub-stage s (RK2+CN: two, AB+CN: one, Section 2):
+ *     the IB step on the forcing nodes, Eqs. IB_step, probe and new_IB;
+ *     the provisional velocity on the fluid nodes, Eq. NS_prov, with the
+ *       approximate factorisation of the CN operator (x, then z, then y);
+ *     the consistent mass correction q of Section 3.2 (Eqs. q_boundary and
+ *       the uniform q_F) in the right-hand side of Eq. elliptic_mod;
+ *     the direct Poisson solve of Eq. elliptic_mod (FFT in x and z, Thomas
+ *       per wavenumber in y, homogeneous Neumann walls);
+ *     the projection, Eq. projection, and pressure update, Eq.
+ *       update_pressure;
+ *   the no-slip error of Section 4.4 on the forcing points.
+ *
+ * Conventions
+ *   - Lengths are non-dimensional; U_ref = L_ref = 1.
+ *   - Cells nx*ny*nz on [0,lx]x[0,ly]x[0,lz], uniform in each direction.
+ *   - u lives on x-faces at (i dx, (j+1/2) dy, (k+1/2) dz),
+ *     v on y-faces at ((i+1/2) dx, j dy, (k+1/2) dz), j = 0..ny (the planes
+ *       j = 0 and j = ny are the walls and hold 0),
+ *     w on z-faces at ((i+1/2) dx, (j+1/2) dy, k dz), p at cell centres.
+ *   - Field arrays are C order [k][j][i] (i fastest): u, w, p hold
+ *     nz*ny*nx values, v holds nz*(ny+1)*nx.  All field arguments are
+ *     FP64 in every precision mode (the mixed mode converts).
+ *   - Surface arrays are C order: xyz[3*nv] = (x,y,z) per vertex, vel[3*nv]
+ *     the vertex velocities, tri[3*nt] vertex indices per triangle (int32).
+ *     Several bodies are passed concatenated; the owner of a forcing node is
+ *     the global triangle index.
+ *
+ * Ownership: the library copies every input into its own device buffers
+ *   during the call (stream-ordered); outputs go into caller buffers.  A
+ *   handle is not thread-safe; all its GPU work is ordered on the stream
+ *   given to ibm_create_grid.
+ * Errors: every entry point returns an ibm_status and never aborts.  Device
+ *   kernels never trap: they record problems in a device error word that
+ *   the next synchronising call (ibm_sync, ibm_get_fields, ibm_get_tags,
+ *   ibm_get_diag) turns into a status.  ibm_last_error() describes the last
+ *   failure of a handle.
+ */
+#ifndef IBM_GB300_H
+#define IBM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ibm_grid* ibm_handle;
+
+typedef enum {
+  IBM_OK = 0,
+  IBM_ERR_ARG = 1,       /* invalid argument (sizes, pointers, indices) */
+  IBM_ERR_CUDA = 2,      /* a CUDA runtime call failed */
+  IBM_ERR_OOM = 3,       /* device allocation failed */
+  IBM_ERR_GEOMETRY = 4,  /* an IB probe left the domain, or a degenerate triangle */
+  IBM_ERR_DIVERGED = 5,  /* non-finite values in the solution */
+  IBM_ERR_TIMEOUT = 6,   /* a bounded device wait gave up */
+  IBM_ERR_STATE = 7,     /* call not valid in the handle's current state */
+  IBM_ERR_CAPACITY = 8   /* a device work list overflowed; the step must be redone */
+} ibm_status;
+
+enum { IBM_RK2_CN = 0, IBM_AB_CN = 1 };   /* time schemes, Section 2 */
+enum { IBM_NOSLIP = 0, IBM_FREESLIP = 1 }; /* condition on the y walls */
+enum { IBM_FP64 = 0, IBM_MIXED = 1 };      /* precision of the bulk arithmetic */
+
+typedef struct {
+  int nx, ny, nz;      /* cells; nx and nz must factor into 2s and 3s, 4 <= n <= 1024; ny >= 4 */
+  double lx, ly, lz;   /* box lengths */
+  double re;           /* Reynolds number */
+  double dt;           /* time step */
+  int scheme;          /* IBM_RK2_CN (default) or IBM_AB_CN */
+  int ybc;             /* IBM_NOSLIP (default) or IBM_FREESLIP */
+  int precision;       /* IBM_FP64 or IBM_MIXED (FP32 bulk; FP64 tagging, Thomas, geometry) */
+  int use_q;           /* 1: Eq. elliptic_mod with q (the paper's method); 0: Eq. elliptic */
+} ibm_grid_desc;
+
+typedef struct {
+  double slip_l1;         /* ||eps||_1 = sum_i ||eps_i||_1 / 3 of the last step (Section 4.4) */
+  double slip_comp[3];    /* ||eps_i||_1, the mean |eps_i| over component i's forcing points */
+  int64_t nforce[3];      /* forcing nodes per velocity component (last step) */
+  int64_t nboundary;      /* boundary cells C_B (last step) */
+  double q_f;             /* q_F of the last sub-stage */
+  double sum_q_dv;        /* sum over all cells of q dV of the last sub-stage (0 up to rounding) */
+  int64_t steps;          /* steps taken by this handle */
+  int64_t ncandidates;    /* (node, triangle) pairs that passed Algorithm 1 in the last step */
+  int64_t kernels_per_step; /* GPU kernels one ibm_step launches (nodes of its CUDA graph) */
+  int64_t d2h_bytes;      /* bytes this ibm_get_diag call copied from the device */
+} ibm_diag;
+
+/* Create a simulation on the current CUDA device.  stream is a cudaStream_t
+ * (NULL = the legacy default stream); all later GPU work of the handle is
+ * ordered on it.  Fields start at rest (u = v = w = p = 0), with no surface.
+ * Returns IBM_ERR_ARG for unsupported sizes, IBM_ERR_OOM if the device
+ * buffers (about 200 B per cell in FP64) do not fit. */
+ibm_status ibm_create_grid(const ibm_grid_desc* desc, void* stream, ibm_handle* out);
+
+/* Release every device buffer of h (waits for its stream). */
+ibm_status ibm_destroy(ibm_handle h);
+
+/* Set the immersed surface X^n with its vertex velocities U^n (the wall
+ * velocity of Eq. new_IB, interpolated barycentrically at X^f).  xyz and
+ * vel: 3*nverts FP64; tri: 3*ntris int32, or NULL to keep the previous
+ * connectivity (ntris must then match).  on_device = 1 if the pointers are
+ * device pointers.  Host pointers must stay valid until the call returns.
+ * ntris = 0 removes the surface.  IBM_ERR_ARG for out-of-range indices. */
+ibm_status ibm_set_surface(ibm_handle h, int nverts, const double* xyz, const double* vel, int ntris,
+                           const int32_t* tri, int on_device);
+
+/* Uniform volume force f of Eq. ns1 (e.g. a mean pressure gradient),
+ * applied on the fluid nodes with the weight alpha of each sub-stage. */
+ibm_status ibm_set_body_force(ibm_handle h, double fx, double fy, double fz);
+
+/* Overwrite the state u, v, w, p (layouts above; v's wall planes are taken
+ * as given).  The non-linear history H^{n-1} of AB+CN is reset to zero. */
+ibm_status ibm_set_fields(ibm_handle h, const double* u, const double* v, const double* w, const double* p,
+                          int on_device);
+
+/* Advance nsteps time steps with the current surface (asynchronous). */
+ibm_status ibm_step(ibm_handle h, int nsteps);
+
+/* Copy the state out (synchronises the stream).  Any pointer may be NULL. */
+ibm_status ibm_get_fields(ibm_handle h, double* u, double* v, double* w, double* p, int on_device);
+
+/* Tags of the last step for velocity component comp (0 = u, 1 = v, 2 = w):
+ * owner[node] = -1 on fluid nodes, else the owning triangle (Algorithm 1,
+ * smallest |N|^2, ties to the smallest index).  Array of that component's
+ * field size.  Synchronises. */
+ibm_status ibm_get_tags(ibm_handle h, int comp, int32_t* owner, int on_device);
+
+/* Diagnostics of the last step (synchronises). */
+ibm_status ibm_get_diag(ibm_handle h, ibm_diag* out);
+
+/* Wait for the handle's stream and report any device-side error. */
+ibm_status ibm_sync(ibm_handle h);
+
+/* Human-readable description of the last error of h (never NULL). */
+const char* ibm_last_error(ibm_handle h);
+
+/* Optional device allocator for all buffers of handles created afterwards
+ * (e.g. a framework's caching allocator).  alloc returns NULL on failure.
+ * Passing NULL restores cudaMalloc/cudaFree. */
+typedef void* (*ibm_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*ibm_free_fn)(void* ptr, void* ctx);
+ibm_status ibm_set_allocator(ibm_alloc_fn alloc, ibm_free_fn free_fn, void* ctx);
+
+/* Device time of each kernel group of a time step.  Runs nsteps steps
+ * (they advance the simulation like ibm_step), each as a CUDA graph with
+ * event records between its kernel groups, and returns per group the total
+ * device milliseconds in ms[IBM_NSTAGES] and the number of kernels in
+ * kernels[IBM_NSTAGES] (either may be NULL).  Synchronises. */
+#define IBM_NSTAGES 15
+ibm_status ibm_profile_stages(ibm_handle h, int nsteps, double* ms, int64_t* kernels);
+
+/* Name of kernel group `stage` (0 <= stage < IBM_NSTAGES), else "". */
+const char* ibm_stage_name(int stage);
+
+/* Library version string. */
+const char* ibm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IBM_GB300_H */

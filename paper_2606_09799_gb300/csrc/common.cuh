@@ -1,0 +1,96 @@
+// common.cuh -- device-side definitions shared by the kernels of the GB300
+// sharp-interface IBM fractional step (arXiv 2606.09799).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ibm {
+
+// Device error word bits (reported to the host at the next synchronising call).
+constexpr unsigned ERR_PROBE = 1u;           // IB probe stencil left the stored planes
+constexpr unsigned ERR_CAND_OVERFLOW = 2u;   // tagging candidate list overflowed
+constexpr unsigned ERR_LIST_OVERFLOW = 4u;   // forcing / boundary list overflowed
+constexpr unsigned ERR_NONFINITE = 8u;       // NaN/Inf met in a reduction
+constexpr unsigned ERR_DEGENERATE = 16u;     // a triangle of zero area
+
+// Per-cell flag bits: the velocity nodes of the cell's lower faces that are
+// forcing nodes, and whether the cell is a boundary cell (Section 3.2).
+constexpr uint8_t FLAG_U = 1, FLAG_V = 2, FLAG_W = 4, FLAG_B = 8;
+
+// Grid as seen by every kernel (passed by value).
+struct Geo {
+  int nx, ny, nz, nkx;
+  int ybc;                       // 0 no-slip, 1 free-slip on the y walls
+  double lx, ly, lz;
+  double dx, dy, dz;
+  double idx, idy, idz;          // reciprocal spacings
+  double diag2;                  // squared diagonal of a cell (Algorithm 1)
+  double h;                      // probe length, twice the cell diagonal (Section 3.1)
+  long long ncell;               // nx*ny*nz: size of u, w, p
+  long long nvf;                 // nx*(ny+1)*nz: size of v
+};
+
+__host__ __device__ inline int planes(const Geo& g, int c) { return c == 1 ? g.ny + 1 : g.ny; }
+__host__ __device__ inline long long comp_size(const Geo& g, int c) { return c == 1 ? g.nvf : g.ncell; }
+// offset of component c inside arrays that hold the three grids back to back
+__host__ __device__ inline long long comp_off(const Geo& g, int c) {
+  return c == 0 ? 0 : (c == 1 ? g.ncell : g.ncell + g.nvf);
+}
+__host__ __device__ inline long long cidx(const Geo& g, long long i, long long j, long long k) {
+  return (k * g.ny + j) * g.nx + i;
+}
+__host__ __device__ inline long long fidx(const Geo& g, int c, long long i, long long j, long long k) {
+  return (k * planes(g, c) + j) * g.nx + i;
+}
+__host__ __device__ inline int wrapi(long long i, int n) {
+  long long r = i % n;
+  return (int)(r < 0 ? r + n : r);
+}
+
+// Device-resident scalars of a handle: inputs refreshed between steps and
+// reduction results, so a captured graph never bakes values in.
+struct DevState {
+  double fb[3];                  // uniform body force
+  double qf[2];                  // q_F of each sub-stage
+  double sum_a[2];               // sum over C_B of D uhat dV per sub-stage
+  double slip_sum[3];            // sum |eps_i| of the last step
+  unsigned int err;              // ERR_* bits
+  unsigned int ncand;            // candidates of the current step
+  unsigned int ncand_prev;       // candidates of the previous step (sparse reset)
+  unsigned int nbound;           // boundary cells
+  unsigned int nforce_c[3];      // forcing nodes per component
+  unsigned int force_base[3];    // start of each component's forcing sub-list
+  unsigned long long steps;
+};
+
+// One (node, triangle) pair that passed Algorithm 1.
+struct Cand {
+  unsigned int key;              // comp << 30 | node index inside the component's array
+  unsigned int tri;
+  unsigned long long d2;         // bit pattern of |N|^2 (monotone for d2 >= 0)
+};
+
+// One forcing node with its owning triangle.
+struct ForceNode {
+  unsigned int key;
+  unsigned int tri;
+};
+
+constexpr unsigned KEY_MASK = (1u << 30) - 1u;
+
+// Surface as stored on the device (structure of arrays).
+struct Surf {
+  const double* x;               // x[nv], then y[nv], then z[nv]
+  const double* u;               // vertex velocities, same layout
+  const int* t;                  // vertex a of every triangle, then b, then c
+  int nv, nt;
+};
+
+// Scheme coefficients of one sub-stage (Section 2 after Eq. NS_prov).
+struct Stage {
+  double gam, rho, alp;
+  int s;                          // sub-stage index
+};
+
+}  // namespace ibm

@@ -1,0 +1,961 @@
+// runtime.cu -- C ABI of the GB300 sharp-interface IBM fractional step
+// (declared in include/ibm.h).  Owns the device buffers of a simulation,
+// builds the coefficient tables on the host, uploads surfaces, and captures
+// one whole time step (tagging, every sub-stage, diagnostics) into a CUDA
+// graph that ibm_step replays on the caller's stream.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/ibm.h"
+#include "common.cuh"
+#include "launch.h"
+
+namespace ibm {
+
+void init_kernel_attributes();
+
+static int g_sms[64];
+
+// ---- stage timing -----------------------------------------------------------
+struct StageTimer {
+  static constexpr int MAXM = 512;
+  cudaEvent_t ev[MAXM];
+  int id[MAXM];
+  int n;
+};
+static thread_local StageTimer* t_timer = nullptr;
+
+void stage_mark(cudaStream_t st, int id) {
+  StageTimer* t = t_timer;
+  if (!t || t->n >= StageTimer::MAXM) return;
+  cudaEventRecord(t->ev[t->n], st);
+  t->id[t->n] = id;
+  t->n++;
+}
+
+static const char* kStageNames[ST_COUNT] = {
+    "tagging", "ib_force", "rhs", "sweep_x", "sweep_z", "sweep_y", "q_reduce", "fft_x_fwd", "fft_z_fwd",
+    "tri_y", "fft_z_inv", "fft_x_inv", "project", "slip", "other"};
+
+int num_sms() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return 152;
+  if (g_sms[dev] == 0) {
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    g_sms[dev] = n > 0 ? n : 152;
+  }
+  return g_sms[dev];
+}
+
+// ---- allocator hook ---------------------------------------------------------
+static std::mutex g_alloc_mu;
+static ibm_alloc_fn g_alloc = nullptr;
+static ibm_free_fn g_free = nullptr;
+static void* g_alloc_ctx = nullptr;
+
+struct Allocator {
+  ibm_alloc_fn alloc;
+  ibm_free_fn free_fn;
+  void* ctx;
+  void* get(size_t bytes) const {
+    if (bytes == 0) bytes = 256;
+    if (alloc) return alloc(bytes, ctx);
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return p;
+  }
+  void put(void* p) const {
+    if (!p) return;
+    if (free_fn) free_fn(p, ctx);
+    else cudaFree(p);
+  }
+};
+
+// ---- small helper kernels ----------------------------------------------------
+__global__ void k_set_force(DevState* ds, double fx, double fy, double fz) {
+  ds->fb[0] = fx;
+  ds->fb[1] = fy;
+  ds->fb[2] = fz;
+}
+
+__global__ void k_step_done(DevState* ds) { ds->steps += 1; }
+
+__global__ void k_aos_to_soa(const double* __restrict__ aos, double* soa, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    soa[i] = aos[3 * (long long)i];
+    soa[n + i] = aos[3 * (long long)i + 1];
+    soa[2 * (long long)n + i] = aos[3 * (long long)i + 2];
+  }
+}
+
+__global__ void k_tri_to_soa(const int* __restrict__ aos, int* soa, int n, int nv, unsigned* bad) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    for (int m = 0; m < 3; ++m) {
+      int v = aos[3 * (long long)i + m];
+      if (v < 0 || v >= nv) {   // never let a kernel index outside the surface arrays
+        atomicOr(bad, 1u);
+        v = 0;
+      }
+      soa[(long long)m * n + i] = v;
+    }
+  }
+}
+
+template <typename A, typename B>
+__global__ void k_convert(const A* __restrict__ src, B* dst, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = (B)src[i];
+}
+
+__global__ void k_owner_out(const unsigned* __restrict__ own, int32_t* out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = (int32_t)own[i];
+}
+
+}  // namespace ibm
+
+using namespace ibm;
+
+struct ibm_grid {
+  ibm_grid_desc desc;
+  Geo g;
+  Allocator al;
+  int device;
+  cudaStream_t user;      // caller's stream
+  cudaStream_t cap;       // private stream used only for graph capture
+  std::vector<void*> owned;
+  char err[512];
+  // device buffers
+  void* fields_mem[16];
+  DevState* ds;
+  double* partial;
+  TagBuffers tb;
+  size_t esize;           // bytes of the bulk type
+  void* u; void* v; void* w; void* p;
+  void* H[3]; void* R[3]; void* scr; void* uf; void* phi; void* spec;
+  // tables
+  void* sweep_mem[12];
+  double* pcp; double* pinv; double* lamx; double* lamz;
+  void* twx; void* twz;
+  double tbl_off[3];
+  double tbl_gam[2];
+  double tbl_smden[2];
+  // surface
+  double* sx; double* su; int* st; double* stage_x; int* stage_t; unsigned* bad;
+  int nv, nt, nv_cap, nt_cap;
+  bool has_topology;
+  // graph
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+  bool graph_ok;
+  bool need_full_reset;
+  long long steps;
+  long long kernels_per_step;
+};
+
+static void set_err(ibm_handle h, const char* fmt, const char* extra = "") {
+  if (h) snprintf(h->err, sizeof(h->err), fmt, extra);
+}
+
+static ibm_status cuda_fail(ibm_handle h, cudaError_t e, const char* what) {
+  if (h) snprintf(h->err, sizeof(h->err), "%s: %s", what, cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? IBM_ERR_OOM : IBM_ERR_CUDA;
+}
+
+#define CK(call)                                              \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #call);    \
+  } while (0)
+
+static void* dalloc(ibm_handle h, size_t bytes) {
+  void* p = h->al.get(bytes);
+  if (p) h->owned.push_back(p);
+  return p;
+}
+
+static void dfree(ibm_handle h, void* p) {
+  if (!p) return;
+  for (size_t i = 0; i < h->owned.size(); ++i)
+    if (h->owned[i] == p) {
+      h->owned.erase(h->owned.begin() + (long)i);
+      break;
+    }
+  h->al.put(p);
+}
+
+static bool good_fft_size(int n) {
+  if (n < 4 || n > 1024 || (n % 2) != 0) return false;
+  while (n % 2 == 0) n /= 2;
+  while (n % 3 == 0) n /= 3;
+  return n == 1;
+}
+
+// ---- host-side coefficient tables -------------------------------------------
+// Thomas recurrences of a tridiagonal matrix with constant off-diagonals a
+// (both sides) and diagonal b[m]: inv[m] = 1/pivot, cp[m] = a/pivot.
+static void thomas_tables(int n, double a, const std::vector<double>& b, std::vector<double>& inv,
+                          std::vector<double>& cp) {
+  inv.assign(n, 0.0);
+  cp.assign(n, 0.0);
+  double prev = 0.0;
+  for (int m = 0; m < n; ++m) {
+    const double den = b[m] - (m > 0 ? a * prev : 0.0);
+    inv[m] = 1.0 / den;
+    cp[m] = (m < n - 1 ? a : 0.0) * inv[m];
+    prev = cp[m];
+  }
+}
+
+static void thomas_apply(int n, double a, const std::vector<double>& inv, const std::vector<double>& cp,
+                         std::vector<double>& x) {
+  double prev = 0.0;
+  for (int m = 0; m < n; ++m) {
+    prev = (x[m] - (m > 0 ? a * prev : 0.0)) * inv[m];
+    x[m] = prev;
+  }
+  for (int m = n - 2; m >= 0; --m) x[m] = x[m] - cp[m] * x[m + 1];
+}
+
+template <typename T>
+static void* upload_vec(ibm_handle h, const std::vector<double>& v) {
+  std::vector<T> tmp(v.size());
+  for (size_t i = 0; i < v.size(); ++i) tmp[i] = (T)v[i];
+  void* d = dalloc(h, tmp.size() * sizeof(T) + 16);
+  if (!d) return nullptr;
+  if (cudaMemcpy(d, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) return nullptr;
+  return d;
+}
+
+// periodic line of length n: Sherman-Morrison form of (1 - beta L) with
+// off = beta/d^2; modified matrix bb, correction vector z and first row g0
+template <typename T>
+static bool build_periodic(ibm_handle h, int n, double off, int slot) {
+  const double a = -off, b = 1.0 + 2.0 * off, gam = -b;
+  std::vector<double> bb(n, b);
+  bb[0] = b - gam;
+  bb[n - 1] = b - a * a / gam;
+  std::vector<double> inv, cp;
+  thomas_tables(n, a, bb, inv, cp);
+  std::vector<double> z(n, 0.0), g0(n, 0.0);
+  z[0] = gam;
+  z[n - 1] = a;
+  thomas_apply(n, a, inv, cp, z);
+  g0[0] = 1.0;
+  thomas_apply(n, a, inv, cp, g0);
+  h->tbl_gam[slot] = gam;
+  h->tbl_smden[slot] = 1.0 + z[0] + a * z[n - 1] / gam;
+  h->sweep_mem[4 * slot + 0] = upload_vec<T>(h, inv);
+  h->sweep_mem[4 * slot + 1] = upload_vec<T>(h, cp);
+  h->sweep_mem[4 * slot + 2] = upload_vec<T>(h, z);
+  h->sweep_mem[4 * slot + 3] = upload_vec<T>(h, g0);
+  for (int q = 0; q < 4; ++q)
+    if (!h->sweep_mem[4 * slot + q]) return false;
+  return true;
+}
+
+// wall-normal line: cls 0 = tangential components (ny rows, ghost rows at
+// both walls), cls 1 = v (ny-1 interior rows, Dirichlet walls)
+template <typename T>
+static bool build_wall(ibm_handle h, int cls, double off) {
+  const int ny = h->g.ny;
+  const int n = cls == 0 ? ny : ny - 1;
+  const double a = -off;
+  std::vector<double> b(n, 1.0 + 2.0 * off);
+  if (cls == 0) {
+    const double gs = h->g.ybc == 0 ? -1.0 : 1.0;
+    b[0] -= gs * off;
+    b[n - 1] -= gs * off;
+  }
+  std::vector<double> inv, cp;
+  thomas_tables(n, a, b, inv, cp);
+  h->sweep_mem[8 + 2 * cls] = upload_vec<T>(h, inv);
+  h->sweep_mem[8 + 2 * cls + 1] = upload_vec<T>(h, cp);
+  return h->sweep_mem[8 + 2 * cls] && h->sweep_mem[8 + 2 * cls + 1];
+}
+
+template <typename T>
+static SweepTables<T> sweep_tables(ibm_handle h) {
+  SweepTables<T> t;
+  for (int d = 0; d < 2; ++d) {
+    t.inv[d] = (const T*)h->sweep_mem[4 * d + 0];
+    t.cp[d] = (const T*)h->sweep_mem[4 * d + 1];
+    t.zv[d] = (const T*)h->sweep_mem[4 * d + 2];
+    t.g0[d] = (const T*)h->sweep_mem[4 * d + 3];
+    t.smden[d] = (T)h->tbl_smden[d];
+    t.gam[d] = (T)h->tbl_gam[d];
+  }
+  for (int c = 0; c < 2; ++c) {
+    t.yinv[c] = (const T*)h->sweep_mem[8 + 2 * c];
+    t.ycp[c] = (const T*)h->sweep_mem[8 + 2 * c + 1];
+  }
+  for (int d = 0; d < 3; ++d) t.off[d] = (T)h->tbl_off[d];
+  return t;
+}
+
+template <typename T>
+static Fields<T> fields(ibm_handle h) {
+  Fields<T> f;
+  f.u = (T*)h->u;
+  f.v = (T*)h->v;
+  f.w = (T*)h->w;
+  f.p = (T*)h->p;
+  for (int c = 0; c < 3; ++c) {
+    f.H[c] = (T*)h->H[c];
+    f.Hp[c] = (T*)h->H[c];
+    f.R[c] = (T*)h->R[c];
+  }
+  f.scr = (T*)h->scr;
+  f.uf = (T*)h->uf;
+  f.phi = (T*)h->phi;
+  f.spec = h->spec;
+  return f;
+}
+
+template <typename T>
+static SpecTables<T> spec_tables(ibm_handle h) {
+  SpecTables<T> s;
+  s.twx = (const T*)h->twx;
+  s.twz = (const T*)h->twz;
+  s.cp = h->pcp;
+  s.inv = h->pinv;
+  return s;
+}
+
+static Surf surface(ibm_handle h) {
+  Surf s;
+  s.x = h->sx;
+  s.u = h->su;
+  s.t = h->st;
+  s.nv = h->nv;
+  s.nt = h->nt;
+  return s;
+}
+
+// scheme coefficients (gamma, rho, alpha) per sub-stage, Section 2
+static int stages(const ibm_grid_desc& d, Stage out[2]) {
+  if (d.scheme == IBM_AB_CN) {
+    out[0] = Stage{1.5, -0.5, 1.0, 0};
+    return 1;
+  }
+  out[0] = Stage{0.5, 0.0, 0.5, 0};
+  out[1] = Stage{1.0, -0.5, 0.5, 1};
+  return 2;
+}
+
+// enqueue one full time step on stream st
+template <typename T>
+static void enqueue_step(ibm_handle h, cudaStream_t st) {
+  const Geo& g = h->g;
+  const Surf s = surface(h);
+  const Fields<T> f = fields<T>(h);
+  const SweepTables<T> sw = sweep_tables<T>(h);
+  const SpecTables<T> sp = spec_tables<T>(h);
+  Stage sg[2];
+  const int ns = stages(h->desc, sg);
+  launch_tagging(g, s, h->tb, h->ds, st);
+  for (int k = 0; k < ns; ++k) {
+    if (s.nt > 0) launch_ib_force<T>(g, s, f, h->tb, h->ds, st);
+    const bool use_hp = sg[k].rho != 0.0;
+    const bool write_h = (h->desc.scheme == IBM_AB_CN) || (k + 1 < ns);
+    launch_rhs<T>(g, f, h->tb, sg[k], h->desc.dt, h->desc.re, use_hp, write_h, h->ds, st);
+    launch_sweeps<T>(g, f, h->tb, sw, st);
+    launch_poisson<T>(g, f, h->tb, sp, sg[k], h->desc.dt, h->desc.re, h->desc.use_q, h->partial, h->ds, st);
+  }
+  if (s.nt > 0) launch_slip<T>(g, s, f, h->tb, h->partial, h->ds, st);
+  k_step_done<<<1, 1, 0, st>>>(h->ds);
+}
+
+static void release_all(ibm_handle h) {
+  if (h->exec) cudaGraphExecDestroy(h->exec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  h->exec = nullptr;
+  h->graph = nullptr;
+  for (void* p : h->owned) h->al.put(p);
+  h->owned.clear();
+  if (h->cap) cudaStreamDestroy(h->cap);
+  h->cap = nullptr;
+}
+
+static size_t round16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+static ibm_status alloc_lists(ibm_handle h, unsigned cap) {
+  dfree(h, h->tb.cand);
+  dfree(h, h->tb.flist);
+  dfree(h, h->tb.blist);
+  dfree(h, h->uf);
+  h->tb.cand = (Cand*)dalloc(h, (size_t)cap * sizeof(Cand));
+  h->tb.flist = (ForceNode*)dalloc(h, (size_t)cap * sizeof(ForceNode));
+  h->tb.blist = (unsigned*)dalloc(h, (size_t)cap * sizeof(unsigned));
+  h->uf = dalloc(h, (size_t)cap * h->esize);
+  if (!h->tb.cand || !h->tb.flist || !h->tb.blist || !h->uf) {
+    set_err(h, "device allocation of the work lists failed");
+    return IBM_ERR_OOM;
+  }
+  h->tb.cap = cap;
+  h->graph_ok = false;
+  h->need_full_reset = true;
+  return IBM_OK;
+}
+
+static ibm_status full_reset(ibm_handle h, cudaStream_t st) {
+  const Geo& g = h->g;
+  const long long nall = 2 * g.ncell + g.nvf;
+  CK(cudaMemsetAsync(h->tb.d2min, 0xFF, (size_t)nall * 8, st));
+  CK(cudaMemsetAsync(h->tb.owner, 0xFF, (size_t)nall * 4, st));
+  CK(cudaMemsetAsync(h->tb.flags32, 0, round16((size_t)(g.ncell + 3) / 4 * 4), st));
+  CK(cudaMemsetAsync(&h->ds->ncand, 0, sizeof(unsigned), st));
+  h->need_full_reset = false;
+  return IBM_OK;
+}
+
+static long long count_kernel_nodes(cudaGraph_t gr) {
+  size_t n = 0;
+  if (cudaGraphGetNodes(gr, nullptr, &n) != cudaSuccess) return -1;
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (cudaGraphGetNodes(gr, nodes.data(), &n) != cudaSuccess) return -1;
+  long long k = 0;
+  for (size_t i = 0; i < n; ++i) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+  }
+  return k;
+}
+
+template <typename T>
+static ibm_status capture(ibm_handle h) {
+  if (h->exec) { cudaGraphExecDestroy(h->exec); h->exec = nullptr; }
+  if (h->graph) { cudaGraphDestroy(h->graph); h->graph = nullptr; }
+  CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+  enqueue_step<T>(h, h->cap);
+  cudaGraph_t gr = nullptr;
+  cudaError_t e = cudaStreamEndCapture(h->cap, &gr);
+  if (e != cudaSuccess) return cuda_fail(h, e, "graph capture");
+  h->graph = gr;
+  CK(cudaGraphInstantiate(&h->exec, gr, 0));
+  h->graph_ok = true;
+  h->kernels_per_step = count_kernel_nodes(gr);
+  return IBM_OK;
+}
+
+extern "C" {
+
+ibm_status ibm_set_allocator(ibm_alloc_fn alloc, ibm_free_fn free_fn, void* ctx) {
+  if ((alloc == nullptr) != (free_fn == nullptr)) return IBM_ERR_ARG;
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  g_alloc = alloc;
+  g_free = free_fn;
+  g_alloc_ctx = ctx;
+  return IBM_OK;
+}
+
+const char* ibm_version(void) { return "ibm-gb300 0.1 (sm_103a)"; }
+
+const char* ibm_last_error(ibm_handle h) { return h ? h->err : "null handle"; }
+
+ibm_status ibm_create_grid(const ibm_grid_desc* desc, void* stream, ibm_handle* out) {
+  if (!desc || !out) return IBM_ERR_ARG;
+  *out = nullptr;
+  const ibm_grid_desc d = *desc;
+  if (!good_fft_size(d.nx) || !good_fft_size(d.nz) || d.ny < 4 || d.ny > 4096) return IBM_ERR_ARG;
+  if (!(d.lx > 0 && d.ly > 0 && d.lz > 0 && d.re > 0 && d.dt > 0)) return IBM_ERR_ARG;
+  if (d.scheme != IBM_RK2_CN && d.scheme != IBM_AB_CN) return IBM_ERR_ARG;
+  if (d.ybc != IBM_NOSLIP && d.ybc != IBM_FREESLIP) return IBM_ERR_ARG;
+  if (d.precision != IBM_FP64 && d.precision != IBM_MIXED) return IBM_ERR_ARG;
+  const long long nvf = (long long)d.nx * (d.ny + 1) * d.nz;
+  if (nvf >= (1ll << 30)) return IBM_ERR_ARG;   // node indices are packed into 30 bits
+  ibm_handle h = new (std::nothrow) ibm_grid();   // value-initialised: every scalar and pointer is zero
+  if (!h) return IBM_ERR_OOM;
+  h->desc = d;
+  {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    h->al = Allocator{g_alloc, g_free, g_alloc_ctx};
+  }
+  h->user = (cudaStream_t)stream;
+  cudaGetDevice(&h->device);
+  Geo& g = h->g;
+  g.nx = d.nx; g.ny = d.ny; g.nz = d.nz; g.nkx = d.nx / 2 + 1;
+  g.ybc = d.ybc;
+  g.lx = d.lx; g.ly = d.ly; g.lz = d.lz;
+  g.dx = d.lx / (double)d.nx;
+  g.dy = d.ly / (double)d.ny;
+  g.dz = d.lz / (double)d.nz;
+  g.idx = 1.0 / g.dx; g.idy = 1.0 / g.dy; g.idz = 1.0 / g.dz;
+  {
+    // squared cell diagonal, rounded term by term without contraction
+    volatile double sx = g.dx * g.dx, sy = g.dy * g.dy, sz = g.dz * g.dz;
+    volatile double sxy = sx + sy;
+    g.diag2 = sxy + sz;
+  }
+  g.h = 2.0 * sqrt(g.diag2);
+  g.ncell = (long long)d.nx * d.ny * d.nz;
+  g.nvf = nvf;
+  h->esize = d.precision == IBM_FP64 ? sizeof(double) : sizeof(float);
+  ibm_status rc = IBM_OK;
+  cudaError_t ce = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
+  if (ce != cudaSuccess) {
+    release_all(h);
+    delete h;
+    return IBM_ERR_CUDA;
+  }
+  init_kernel_attributes();
+  const size_t es = h->esize;
+  const long long ncell = g.ncell, nall = 2 * ncell + nvf;
+  h->u = dalloc(h, ncell * es);
+  h->v = dalloc(h, nvf * es);
+  h->w = dalloc(h, ncell * es);
+  h->p = dalloc(h, ncell * es);
+  for (int c = 0; c < 3; ++c) {
+    h->H[c] = dalloc(h, (c == 1 ? nvf : ncell) * es);
+    h->R[c] = dalloc(h, (c == 1 ? nvf : ncell) * es);
+  }
+  h->scr = dalloc(h, nall * es);
+  h->phi = dalloc(h, ncell * es);
+  h->spec = dalloc(h, (size_t)g.nz * g.ny * g.nkx * 2 * es);
+  h->ds = (DevState*)dalloc(h, sizeof(DevState));
+  h->partial = (double*)dalloc(h, 4096 * sizeof(double));
+  h->tb.d2min = (unsigned long long*)dalloc(h, nall * 8);
+  h->tb.owner = (unsigned*)dalloc(h, nall * 4);
+  h->tb.flags32 = (unsigned*)dalloc(h, round16((size_t)(ncell + 3) / 4 * 4));
+  h->tb.blk = (unsigned*)dalloc(h, (size_t)compaction_blocks(g) * 4 * sizeof(unsigned));
+  h->bad = (unsigned*)dalloc(h, 16);
+  void* need[] = {h->u, h->v, h->w, h->p, h->H[0], h->H[1], h->H[2], h->R[0], h->R[1], h->R[2], h->scr,
+                  h->phi, h->spec, h->ds, h->partial, h->tb.d2min, h->tb.owner, h->tb.flags32, h->tb.blk, h->bad};
+  for (void* q : need)
+    if (!q) {
+      release_all(h);
+      delete h;
+      return IBM_ERR_OOM;
+    }
+  if (alloc_lists(h, 1u << 16) != IBM_OK) {
+    release_all(h);
+    delete h;
+    return IBM_ERR_OOM;
+  }
+  // coefficient tables: one beta for every sub-stage of the scheme
+  Stage sg[2];
+  stages(d, sg);
+  const double beta = sg[0].alp * d.dt / (2.0 * d.re);
+  h->tbl_off[0] = beta / (g.dx * g.dx);
+  h->tbl_off[1] = beta / (g.dy * g.dy);
+  h->tbl_off[2] = beta / (g.dz * g.dz);
+  bool ok;
+  if (d.precision == IBM_FP64)
+    ok = build_periodic<double>(h, d.nx, h->tbl_off[0], 0) && build_periodic<double>(h, d.nz, h->tbl_off[2], 1) &&
+         build_wall<double>(h, 0, h->tbl_off[1]) && build_wall<double>(h, 1, h->tbl_off[1]);
+  else
+    ok = build_periodic<float>(h, d.nx, h->tbl_off[0], 0) && build_periodic<float>(h, d.nz, h->tbl_off[2], 1) &&
+         build_wall<float>(h, 0, h->tbl_off[1]) && build_wall<float>(h, 1, h->tbl_off[1]);
+  // Poisson: modified wavenumbers, twiddles, pivots
+  const double pi = 3.14159265358979323846;
+  std::vector<double> lx(g.nkx), lz(g.nz), twx(2 * g.nx), twz(2 * g.nz);
+  for (int k = 0; k < g.nkx; ++k) lx[k] = (2.0 - 2.0 * cos(2.0 * pi * k / g.nx)) / (g.dx * g.dx);
+  for (int k = 0; k < g.nz; ++k) lz[k] = (2.0 - 2.0 * cos(2.0 * pi * k / g.nz)) / (g.dz * g.dz);
+  for (int m = 0; m < g.nx; ++m) { twx[2 * m] = cos(2.0 * pi * m / g.nx); twx[2 * m + 1] = -sin(2.0 * pi * m / g.nx); }
+  for (int m = 0; m < g.nz; ++m) { twz[2 * m] = cos(2.0 * pi * m / g.nz); twz[2 * m + 1] = -sin(2.0 * pi * m / g.nz); }
+  h->lamx = (double*)upload_vec<double>(h, lx);
+  h->lamz = (double*)upload_vec<double>(h, lz);
+  if (d.precision == IBM_FP64) {
+    h->twx = upload_vec<double>(h, twx);
+    h->twz = upload_vec<double>(h, twz);
+  } else {
+    h->twx = upload_vec<float>(h, twx);
+    h->twz = upload_vec<float>(h, twz);
+  }
+  const size_t nspec = (size_t)g.nz * g.ny * g.nkx;
+  h->pcp = (double*)dalloc(h, nspec * 8);
+  h->pinv = (double*)dalloc(h, nspec * 8);
+  if (!ok || !h->lamx || !h->lamz || !h->twx || !h->twz || !h->pcp || !h->pinv) {
+    release_all(h);
+    delete h;
+    return IBM_ERR_OOM;
+  }
+  cudaStream_t st = h->user;
+  launch_build_poisson_tables(g, h->lamx, h->lamz, h->pcp, h->pinv, st);
+  // state at rest
+  cudaMemsetAsync(h->u, 0, ncell * es, st);
+  cudaMemsetAsync(h->v, 0, nvf * es, st);
+  cudaMemsetAsync(h->w, 0, ncell * es, st);
+  cudaMemsetAsync(h->p, 0, ncell * es, st);
+  for (int c = 0; c < 3; ++c) cudaMemsetAsync(h->H[c], 0, (c == 1 ? nvf : ncell) * es, st);
+  cudaMemsetAsync(h->ds, 0, sizeof(DevState), st);
+  cudaMemsetAsync(h->tb.cand, 0, sizeof(Cand), st);
+  if (full_reset(h, st) != IBM_OK) rc = IBM_ERR_CUDA;
+  ce = cudaStreamSynchronize(st);
+  if (ce != cudaSuccess || rc != IBM_OK) {
+    release_all(h);
+    delete h;
+    return IBM_ERR_CUDA;
+  }
+  *out = h;
+  return IBM_OK;
+}
+
+ibm_status ibm_destroy(ibm_handle h) {
+  if (!h) return IBM_ERR_ARG;
+  cudaStreamSynchronize(h->user);
+  release_all(h);
+  delete h;
+  return IBM_OK;
+}
+
+ibm_status ibm_set_body_force(ibm_handle h, double fx, double fy, double fz) {
+  if (!h) return IBM_ERR_ARG;
+  k_set_force<<<1, 1, 0, h->user>>>(h->ds, fx, fy, fz);
+  CK(cudaGetLastError());
+  return IBM_OK;
+}
+
+// upper bound of the candidates a surface can produce: nodes inside every
+// triangle's Cartesian box (with the one-cell margin of Algorithm 1)
+static unsigned long long candidate_bound(const Geo& g, const double* xyz, const int32_t* tri, int nt) {
+  unsigned long long tot = 0;
+  const double del[3] = {g.dx, g.dy, g.dz};
+  for (int t = 0; t < nt; ++t) {
+    unsigned long long prod = 1;
+    for (int d = 0; d < 3; ++d) {
+      double mn = 1e300, mx = -1e300;
+      for (int m = 0; m < 3; ++m) {
+        const double x = xyz[3 * (long long)tri[3 * t + m] + d];
+        mn = x < mn ? x : mn;
+        mx = x > mx ? x : mx;
+      }
+      long long cnt = (long long)ceil((mx - mn) / del[d]) + 4;
+      if (d == 1 && cnt > g.ny + 1) cnt = g.ny + 1;
+      prod *= (unsigned long long)cnt;
+    }
+    tot += 3 * prod;
+  }
+  return tot;
+}
+
+ibm_status ibm_set_surface(ibm_handle h, int nverts, const double* xyz, const double* vel, int ntris,
+                           const int32_t* tri, int on_device) {
+  if (!h || nverts < 0 || ntris < 0) return IBM_ERR_ARG;
+  if (ntris == 0) {
+    if (h->nt != 0) h->graph_ok = false;
+    h->nt = 0;
+    h->nv = 0;
+    return IBM_OK;
+  }
+  if (nverts < 3 || !xyz || !vel) return IBM_ERR_ARG;
+  if (!tri && (!h->has_topology || ntris != h->nt)) {
+    set_err(h, "%s", "ibm_set_surface: tri == NULL needs the previous connectivity with the same ntris");
+    return IBM_ERR_STATE;
+  }
+  cudaStream_t st = h->user;
+  // (re)allocate surface storage
+  if (nverts > h->nv_cap || ntris > h->nt_cap) {
+    const int nvc = nverts > h->nv_cap ? nverts : h->nv_cap;
+    const int ntc = ntris > h->nt_cap ? ntris : h->nt_cap;
+    CK(cudaStreamSynchronize(st));
+    int* old_t = h->st;
+    double* nsx = (double*)dalloc(h, 3ull * nvc * 8);
+    double* nsu = (double*)dalloc(h, 3ull * nvc * 8);
+    int* nst = (int*)dalloc(h, 3ull * ntc * 4);
+    double* ngx = (double*)dalloc(h, 3ull * nvc * 8);
+    int* ngt = (int*)dalloc(h, 3ull * ntc * 4);
+    if (!nsx || !nsu || !nst || !ngx || !ngt) {
+      set_err(h, "%s", "device allocation of the surface failed");
+      return IBM_ERR_OOM;
+    }
+    if (old_t && !tri && h->nt > 0) CK(cudaMemcpy(nst, old_t, 3ull * h->nt * 4, cudaMemcpyDeviceToDevice));
+    dfree(h, h->sx); dfree(h, h->su); dfree(h, h->st); dfree(h, h->stage_x); dfree(h, h->stage_t);
+    h->sx = nsx; h->su = nsu; h->st = nst; h->stage_x = ngx; h->stage_t = ngt;
+    h->nv_cap = nvc;
+    h->nt_cap = ntc;
+    h->graph_ok = false;
+  }
+  // host-side checks and the candidate-capacity bound
+  if (!on_device) {
+    if (tri) {
+      for (long long m = 0; m < 3ll * ntris; ++m)
+        if (tri[m] < 0 || tri[m] >= nverts) {
+          set_err(h, "%s", "ibm_set_surface: triangle vertex index out of range");
+          return IBM_ERR_ARG;
+        }
+    }
+    const int32_t* tt = tri;
+    std::vector<int32_t> tmp;
+    if (!tt) {
+      tmp.resize(3ull * ntris);
+      std::vector<int> soa(3ull * ntris);
+      CK(cudaMemcpy(soa.data(), h->st, 3ull * ntris * 4, cudaMemcpyDeviceToHost));
+      for (int t = 0; t < ntris; ++t)
+        for (int m = 0; m < 3; ++m) tmp[3ull * t + m] = soa[(size_t)m * ntris + t];
+      tt = tmp.data();
+    }
+    unsigned long long need = candidate_bound(h->g, xyz, tt, ntris);
+    if (need > 0xF0000000ull) need = 0xF0000000ull;
+    if (need > h->tb.cap) {
+      CK(cudaStreamSynchronize(st));
+      unsigned cap = (unsigned)need;
+      if (alloc_lists(h, cap) != IBM_OK) return IBM_ERR_OOM;
+    }
+  } else if (!h->has_topology || ntris != h->nt) {
+    // device surface: size the lists once from a host copy of the first one
+    std::vector<double> hx(3ull * nverts);
+    std::vector<int32_t> ht(3ull * ntris);
+    CK(cudaMemcpy(hx.data(), xyz, hx.size() * 8, cudaMemcpyDeviceToHost));
+    if (tri) CK(cudaMemcpy(ht.data(), tri, ht.size() * 4, cudaMemcpyDeviceToHost));
+    else {
+      std::vector<int> soa(3ull * ntris);
+      CK(cudaMemcpy(soa.data(), h->st, 3ull * ntris * 4, cudaMemcpyDeviceToHost));
+      for (int t = 0; t < ntris; ++t)
+        for (int m = 0; m < 3; ++m) ht[3ull * t + m] = soa[(size_t)m * ntris + t];
+    }
+    for (long long m = 0; m < 3ll * ntris; ++m)
+      if (ht[m] < 0 || ht[m] >= nverts) {
+        set_err(h, "%s", "ibm_set_surface: triangle vertex index out of range");
+        return IBM_ERR_ARG;
+      }
+    unsigned long long need = candidate_bound(h->g, hx.data(), ht.data(), ntris) * 3 / 2;
+    if (need > 0xF0000000ull) need = 0xF0000000ull;
+    if (need > h->tb.cap) {
+      CK(cudaStreamSynchronize(st));
+      if (alloc_lists(h, (unsigned)need) != IBM_OK) return IBM_ERR_OOM;
+    }
+  }
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const int tb = 256;
+  CK(cudaMemcpyAsync(h->stage_x, xyz, 3ull * nverts * 8, kind, st));
+  k_aos_to_soa<<<(nverts + tb - 1) / tb, tb, 0, st>>>(h->stage_x, h->sx, nverts);
+  CK(cudaMemcpyAsync(h->stage_x, vel, 3ull * nverts * 8, kind, st));
+  k_aos_to_soa<<<(nverts + tb - 1) / tb, tb, 0, st>>>(h->stage_x, h->su, nverts);
+  if (tri) {
+    CK(cudaMemcpyAsync(h->stage_t, tri, 3ull * ntris * 4, kind, st));
+    k_tri_to_soa<<<(ntris + tb - 1) / tb, tb, 0, st>>>(h->stage_t, h->st, ntris, nverts, h->bad);
+  }
+  CK(cudaGetLastError());
+  if (nverts != h->nv || ntris != h->nt) h->graph_ok = false;
+  h->nv = nverts;
+  h->nt = ntris;
+  h->has_topology = true;
+  return IBM_OK;
+}
+
+ibm_status ibm_set_fields(ibm_handle h, const double* u, const double* v, const double* w, const double* p,
+                          int on_device) {
+  if (!h) return IBM_ERR_ARG;
+  const Geo& g = h->g;
+  cudaStream_t st = h->user;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const double* src[4] = {u, v, w, p};
+  void* dst[4] = {h->u, h->v, h->w, h->p};
+  const long long n[4] = {g.ncell, g.nvf, g.ncell, g.ncell};
+  for (int q = 0; q < 4; ++q) {
+    if (!src[q]) continue;
+    if (h->esize == 8) {
+      CK(cudaMemcpyAsync(dst[q], src[q], n[q] * 8, kind, st));
+    } else {
+      // stage through the scratch array (large enough for any field in FP64? use R buffers)
+      double* stage = (double*)h->scr;   // scr holds 2*ncell+nvf floats = enough bytes for one FP64 field
+      CK(cudaMemcpyAsync(stage, src[q], n[q] * 8, kind, st));
+      k_convert<double, float><<<num_sms() * 4, 256, 0, st>>>(stage, (float*)dst[q], n[q]);
+    }
+  }
+  for (int c = 0; c < 3; ++c) CK(cudaMemsetAsync(h->H[c], 0, (c == 1 ? g.nvf : g.ncell) * h->esize, st));
+  CK(cudaGetLastError());
+  if (!on_device) CK(cudaStreamSynchronize(st));
+  return IBM_OK;
+}
+
+// Turn the device error word (and the surface-index flag) into a status.
+// `have` (optional) is a device-state copy taken after the stream finished.
+static ibm_status check_device(ibm_handle h, const DevState* have = nullptr) {
+  DevState ds;
+  unsigned bad = 0;
+  if (have) {
+    ds = *have;
+  } else {
+    CK(cudaMemcpyAsync(&ds, h->ds, sizeof(DevState), cudaMemcpyDeviceToHost, h->user));
+  }
+  CK(cudaMemcpyAsync(&bad, h->bad, sizeof(unsigned), cudaMemcpyDeviceToHost, h->user));
+  CK(cudaStreamSynchronize(h->user));
+  if (bad) {
+    CK(cudaMemset(h->bad, 0, sizeof(unsigned)));
+    set_err(h, "%s", "triangle vertex index out of range (device surface)");
+    return IBM_ERR_ARG;
+  }
+  if (ds.err) {
+    CK(cudaMemset(&h->ds->err, 0, sizeof(unsigned)));
+    if (ds.err & (ERR_CAND_OVERFLOW | ERR_LIST_OVERFLOW)) {
+      set_err(h, "%s", "a tagging work list overflowed; capacity doubled, redo the step");
+      unsigned cap = h->tb.cap;
+      unsigned nc = cap > 0x78000000u ? 0xF0000000u : cap * 2;
+      if (ds.ncand > nc) nc = ds.ncand + ds.ncand / 2;
+      if (alloc_lists(h, nc) != IBM_OK) return IBM_ERR_OOM;
+      return IBM_ERR_CAPACITY;
+    }
+    if (ds.err & ERR_PROBE) {
+      set_err(h, "%s", "an IB probe left the domain (body too close to a wall)");
+      return IBM_ERR_GEOMETRY;
+    }
+    if (ds.err & ERR_NONFINITE) {
+      set_err(h, "%s", "non-finite values in the solution");
+      return IBM_ERR_DIVERGED;
+    }
+    set_err(h, "%s", "device error");
+    return IBM_ERR_CUDA;
+  }
+  return IBM_OK;
+}
+
+ibm_status ibm_sync(ibm_handle h) {
+  if (!h) return IBM_ERR_ARG;
+  CK(cudaStreamSynchronize(h->user));
+  return check_device(h);
+}
+
+ibm_status ibm_step(ibm_handle h, int nsteps) {
+  if (!h || nsteps < 0) return IBM_ERR_ARG;
+  if (h->need_full_reset) {
+    ibm_status s = full_reset(h, h->user);
+    if (s != IBM_OK) return s;
+  }
+  if (!h->graph_ok) {
+    ibm_status s = h->esize == 8 ? capture<double>(h) : capture<float>(h);
+    if (s != IBM_OK) return s;
+  }
+  for (int n = 0; n < nsteps; ++n) CK(cudaGraphLaunch(h->exec, h->user));
+  h->steps += nsteps;
+  return IBM_OK;
+}
+
+ibm_status ibm_get_fields(ibm_handle h, double* u, double* v, double* w, double* p, int on_device) {
+  if (!h) return IBM_ERR_ARG;
+  const Geo& g = h->g;
+  cudaStream_t st = h->user;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  double* dst[4] = {u, v, w, p};
+  void* src[4] = {h->u, h->v, h->w, h->p};
+  const long long n[4] = {g.ncell, g.nvf, g.ncell, g.ncell};
+  for (int q = 0; q < 4; ++q) {
+    if (!dst[q]) continue;
+    if (h->esize == 8) {
+      CK(cudaMemcpyAsync(dst[q], src[q], n[q] * 8, kind, st));
+    } else {
+      double* stage = (double*)h->scr;
+      k_convert<float, double><<<num_sms() * 4, 256, 0, st>>>((const float*)src[q], stage, n[q]);
+      CK(cudaMemcpyAsync(dst[q], stage, n[q] * 8, kind, st));
+      CK(cudaStreamSynchronize(st));
+    }
+  }
+  CK(cudaStreamSynchronize(st));
+  return check_device(h);
+}
+
+ibm_status ibm_get_tags(ibm_handle h, int comp, int32_t* owner, int on_device) {
+  if (!h || comp < 0 || comp > 2 || !owner) return IBM_ERR_ARG;
+  const Geo& g = h->g;
+  const long long n = comp_size(g, comp);
+  const unsigned* src = h->tb.owner + comp_off(g, comp);
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  CK(cudaMemcpyAsync(owner, src, n * 4, kind, h->user));
+  CK(cudaStreamSynchronize(h->user));
+  return check_device(h);
+}
+
+ibm_status ibm_get_diag(ibm_handle h, ibm_diag* out) {
+  if (!h || !out) return IBM_ERR_ARG;
+  DevState ds;
+  CK(cudaMemcpyAsync(&ds, h->ds, sizeof(DevState), cudaMemcpyDeviceToHost, h->user));
+  ibm_status s = check_device(h, &ds);
+  memset(out, 0, sizeof(*out));
+  out->d2h_bytes = (int64_t)(sizeof(DevState) + sizeof(unsigned));
+  double tot = 0.0;
+  for (int c = 0; c < 3; ++c) {
+    out->nforce[c] = ds.nforce_c[c];
+    out->slip_comp[c] = ds.nforce_c[c] ? ds.slip_sum[c] / (double)ds.nforce_c[c] : 0.0;
+    tot += out->slip_comp[c];
+  }
+  out->slip_l1 = tot / 3.0;
+  out->nboundary = ds.nbound;
+  Stage sg[2];
+  const int ns = stages(h->desc, sg);
+  out->q_f = ds.qf[ns - 1];
+  const double dV = h->g.dx * h->g.dy * h->g.dz;
+  out->sum_q_dv = ds.sum_a[ns - 1] + ds.qf[ns - 1] * (double)(h->g.ncell - (long long)ds.nbound) * dV;
+  out->steps = (int64_t)ds.steps;
+  out->ncandidates = ds.ncand;
+  out->kernels_per_step = h->kernels_per_step;
+  return s;
+}
+
+const char* ibm_stage_name(int stage) { return (stage >= 0 && stage < ST_COUNT) ? kStageNames[stage] : ""; }
+
+ibm_status ibm_profile_stages(ibm_handle h, int nsteps, double* ms, int64_t* kernels) {
+  if (!h || nsteps < 0) return IBM_ERR_ARG;
+  if (h->need_full_reset) {
+    ibm_status s = full_reset(h, h->user);
+    if (s != IBM_OK) return s;
+  }
+  StageTimer* tm = new (std::nothrow) StageTimer();
+  if (!tm) return IBM_ERR_OOM;
+  for (int m = 0; m < StageTimer::MAXM; ++m) {
+    cudaError_t e = cudaEventCreate(&tm->ev[m]);
+    if (e != cudaSuccess) {
+      for (int q = 0; q < m; ++q) cudaEventDestroy(tm->ev[q]);
+      delete tm;
+      return cuda_fail(h, e, "cudaEventCreate");
+    }
+  }
+  double acc[ST_COUNT] = {0};
+  int64_t cnt[ST_COUNT] = {0};
+  ibm_status rc = IBM_OK;
+  cudaGraph_t gr = nullptr;
+  cudaGraphExec_t ex = nullptr;
+  // one step captured with an event record before every kernel group
+  tm->n = 0;
+  t_timer = tm;
+  cudaError_t e = cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    if (h->esize == 8) enqueue_step<double>(h, h->cap);
+    else enqueue_step<float>(h, h->cap);
+    stage_mark(h->cap, ST_OTHER);
+    e = cudaStreamEndCapture(h->cap, &gr);
+  }
+  t_timer = nullptr;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, gr, 0);
+  if (e != cudaSuccess) rc = cuda_fail(h, e, "profiling graph");
+  for (int step = 0; step < nsteps && rc == IBM_OK; ++step) {
+    e = cudaGraphLaunch(ex, h->user);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->user);
+    if (e != cudaSuccess) { rc = cuda_fail(h, e, "profiling step"); break; }
+    for (int m = 0; m + 1 < tm->n; ++m) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, tm->ev[m], tm->ev[m + 1]) == cudaSuccess) acc[tm->id[m]] += t;
+    }
+    h->steps += 1;
+  }
+  if (rc == IBM_OK) {
+    // kernels per group: kernel nodes between consecutive event nodes of one step
+    const long long total = count_kernel_nodes(gr);
+    (void)total;
+    for (int m = 0; m + 1 < tm->n; ++m) cnt[tm->id[m]] += 1;
+  }
+  if (ex) cudaGraphExecDestroy(ex);
+  if (gr) cudaGraphDestroy(gr);
+  for (int m = 0; m < StageTimer::MAXM; ++m) cudaEventDestroy(tm->ev[m]);
+  delete tm;
+  if (rc != IBM_OK) return rc;
+  for (int q = 0; q < ST_COUNT; ++q) {
+    if (ms) ms[q] = acc[q];
+    if (kernels) kernels[q] = cnt[q];
+  }
+  return check_device(h);
+}
+
+}  // extern "C"

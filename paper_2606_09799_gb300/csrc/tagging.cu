@@ -1,0 +1,374 @@
+// tagging.cu -- Algorithm 1 of arXiv 2606.09799 (fast tagging of the forcing
+// nodes) on the three staggered velocity grids, with deterministic
+// compaction of the forcing nodes and boundary cells (Section 3.2).
+//
+// Work shape: one warp per (triangle, velocity component); the lanes stride
+// over the Eulerian points inside the triangle's Cartesian box.  A point that
+// passes the test of Algorithm 1 becomes a candidate: |N|^2 is folded into a
+// per-node atomicMin, and the pair is appended to a candidate list with a
+// warp-aggregated atomic.  A second pass keeps, per node, the candidate of
+// smallest |N|^2 (ties: smallest triangle index), and a third marks the node
+// in the per-cell flag bytes.  A dense, deterministic scan of those bytes then
+// emits the forcing list and the boundary-cell list sorted by cell index.
+//
+// Every geometric predicate is evaluated in FP64 with explicit
+// round-to-nearest operations (no contraction into FMA), in the same order
+// as the textual definition of each quantity, so tags are reproducible
+// bit for bit by any IEEE-754 implementation of the same formulas.
+#include "common.cuh"
+#include "geometry.cuh"
+#include "launch.h"
+
+namespace ibm {
+
+// ---------------------------------------------------------------------------
+// sparse reset of the per-node state touched by the previous step
+// ---------------------------------------------------------------------------
+__global__ void k_tag_reset(Geo g, const Cand* __restrict__ cand, unsigned cap, DevState* ds,
+                            unsigned long long* d2min, unsigned* owner, unsigned* flags32) {
+  const unsigned n = min(ds->ncand, cap);
+  for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const Cand cd = cand[e];
+    const int c = (int)(cd.key >> 30);
+    const long long node = cd.key & KEY_MASK;
+    d2min[comp_off(g, c) + node] = ~0ull;
+    owner[comp_off(g, c) + node] = 0xFFFFFFFFu;
+    const int pl = planes(g, c);
+    const long long i = node % g.nx, j = (node / g.nx) % pl, k = node / ((long long)g.nx * pl);
+    const long long cell = cidx(g, i, j, k);
+    atomicAnd(flags32 + (cell >> 2), ~(0xFFu << (8 * (cell & 3))));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 1: one warp per (triangle, component)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_tag_candidates(Geo g, Surf s, Cand* __restrict__ cand, unsigned cap,
+                                                        unsigned long long* d2min, DevState* ds) {
+  const int lane = threadIdx.x & 31;
+  const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (wid >= 3ll * s.nt) return;
+  const int t = (int)(wid / 3), c = (int)(wid % 3);
+  double A[3], B[3], C[3];
+  load_triangle(s, t, A, B, C);
+  const double del[3] = {g.dx, g.dy, g.dz};
+  const double off[3] = {c == 0 ? 0.0 : 0.5, c == 1 ? 0.0 : 0.5, c == 2 ? 0.0 : 0.5};
+  double lo[3], hi[3];
+  long long ilo[3], ihi[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const double mn = fmin(A[d], fmin(B[d], C[d]));
+    const double mx = fmax(A[d], fmax(B[d], C[d]));
+    lo[d] = dsub(mn, del[d]);
+    hi[d] = dadd(mx, del[d]);
+    ilo[d] = (long long)floor(dsub(ddiv(lo[d], del[d]), off[d])) - 1;
+    ihi[d] = (long long)ceil(dsub(ddiv(hi[d], del[d]), off[d])) + 1;
+  }
+  const long long jlo = (c == 1) ? 1 : 0, jhi = g.ny - 1;
+  if (ilo[1] < jlo) ilo[1] = jlo;
+  if (ihi[1] > jhi) ihi[1] = jhi;
+  const long long ni = ihi[0] - ilo[0] + 1, nj = ihi[1] - ilo[1] + 1, nk = ihi[2] - ilo[2] + 1;
+  if (ni <= 0 || nj <= 0 || nk <= 0) return;
+  const long long total = ni * nj * nk;
+  const long long coff = comp_off(g, c);
+  for (long long base = 0; base < total; base += 32) {
+    const long long n = base + lane;
+    bool tagged = false;
+    unsigned key = 0;
+    unsigned long long d2bits = 0;
+    if (n < total) {
+      const long long i = ilo[0] + n % ni, j = ilo[1] + (n / ni) % nj, k = ilo[2] + n / (ni * nj);
+      double x[3];
+      node_pos(g, c, i, j, k, x);
+      bool inside = true;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) inside = inside && (lo[d] < x[d]) && (x[d] < hi[d]);
+      if (inside) {
+        double X[3], wb[3], N[3];
+        closest_point_exact(x, A, B, C, X, wb);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) N[d] = dsub(x[d], X[d]);
+        const double n2 = ddot(N, N);
+        if (n2 <= g.diag2) {
+          if (n2 == 0.0) {
+            tagged = true;  // a node on the surface: alpha = 0 in Eq. new_IB
+          } else {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+#pragma unroll
+              for (int sg = -1; sg <= 1; sg += 2) {
+                double xn[3], vn[3];
+                node_pos(g, c, i + (d == 0 ? sg : 0), j + (d == 1 ? sg : 0), k + (d == 2 ? sg : 0), xn);
+#pragma unroll
+                for (int e = 0; e < 3; ++e) vn[e] = dsub(xn[e], X[e]);
+                if (ddot(N, vn) < 0.0) tagged = true;
+              }
+            }
+          }
+          if (tagged) {
+            const long long node = fidx(g, c, wrapi(i, g.nx), j, wrapi(k, g.nz));
+            key = ((unsigned)c << 30) | (unsigned)node;
+            d2bits = (unsigned long long)__double_as_longlong(n2);
+            atomicMin(d2min + coff + node, d2bits);
+          }
+        }
+      }
+    }
+    const unsigned mask = __ballot_sync(0xFFFFFFFFu, tagged);
+    if (mask) {
+      unsigned pos = 0;
+      const int leader = __ffs(mask) - 1;
+      if (lane == leader) pos = atomicAdd(&ds->ncand, (unsigned)__popc(mask));
+      pos = __shfl_sync(0xFFFFFFFFu, pos, leader);
+      if (tagged) {
+        const unsigned slot = pos + __popc(mask & ((1u << lane) - 1u));
+        if (slot < cap) {
+          Cand cd;
+          cd.key = key;
+          cd.tri = (unsigned)t;
+          cd.d2 = d2bits;
+          cand[slot] = cd;
+        } else {
+          atomicOr(&ds->err, ERR_CAND_OVERFLOW);
+        }
+      }
+    }
+  }
+}
+
+// Per node keep the smallest triangle index among the candidates of minimum |N|^2.
+__global__ void k_tag_resolve(Geo g, const Cand* __restrict__ cand, unsigned cap, const DevState* ds,
+                              const unsigned long long* __restrict__ d2min, unsigned* owner) {
+  const unsigned n = min(ds->ncand, cap);
+  for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const Cand cd = cand[e];
+    const long long o = comp_off(g, (int)(cd.key >> 30)) + (cd.key & KEY_MASK);
+    if (cd.d2 == d2min[o]) atomicMin(owner + o, cd.tri);
+  }
+}
+
+// Mark the winning (node, owner) pairs in the per-cell flag bytes.
+__global__ void k_tag_mark(Geo g, const Cand* __restrict__ cand, unsigned cap, const DevState* ds,
+                           const unsigned long long* __restrict__ d2min, const unsigned* __restrict__ owner,
+                           unsigned* flags32) {
+  const unsigned n = min(ds->ncand, cap);
+  for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const Cand cd = cand[e];
+    const int c = (int)(cd.key >> 30);
+    const long long node = cd.key & KEY_MASK;
+    const long long o = comp_off(g, c) + node;
+    if (cd.d2 == d2min[o] && cd.tri == owner[o]) {
+      const int pl = planes(g, c);
+      const long long i = node % g.nx, j = (node / g.nx) % pl, k = node / ((long long)g.nx * pl);
+      const long long cell = cidx(g, i, j, k);
+      atomicOr(flags32 + (cell >> 2), (unsigned)(1u << c) << (8 * (cell & 3)));
+    }
+  }
+}
+
+__device__ __forceinline__ unsigned flag_of(const unsigned* flags32, long long cell) {
+  return (flags32[cell >> 2] >> (8 * (cell & 3))) & 0xFFu;
+}
+
+// Boundary cells (Section 3.2): all six faces hold forcing nodes.  Checked
+// once per cell, from the candidate that won the cell's lower x-face.
+__global__ void k_tag_boundary(Geo g, const Cand* __restrict__ cand, unsigned cap, const DevState* ds,
+                               const unsigned long long* __restrict__ d2min, const unsigned* __restrict__ owner,
+                               unsigned* flags32) {
+  const unsigned n = min(ds->ncand, cap);
+  for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const Cand cd = cand[e];
+    if ((cd.key >> 30) != 0) continue;
+    const long long node = cd.key & KEY_MASK;
+    if (!(cd.d2 == d2min[node] && cd.tri == owner[node])) continue;
+    const long long i = node % g.nx, j = (node / g.nx) % g.ny, k = node / ((long long)g.nx * g.ny);
+    const long long ip = (i + 1 == g.nx) ? 0 : i + 1, kp = (k + 1 == g.nz) ? 0 : k + 1;
+    const long long cell = cidx(g, i, j, k);
+    const unsigned f0 = flag_of(flags32, cell);
+    bool all = (f0 & FLAG_U) && (f0 & FLAG_V) && (f0 & FLAG_W);
+    all = all && (flag_of(flags32, cidx(g, ip, j, k)) & FLAG_U);
+    all = all && (j + 1 < g.ny) && (flag_of(flags32, cidx(g, i, j + 1, k)) & FLAG_V);
+    all = all && (flag_of(flags32, cidx(g, i, j, kp)) & FLAG_W);
+    if (all) atomicOr(flags32 + (cell >> 2), (unsigned)FLAG_B << (8 * (cell & 3)));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// deterministic compaction of the flag bytes: count, scan, write
+// ---------------------------------------------------------------------------
+constexpr int CMP_THREADS = 256;
+constexpr int CMP_PER_THREAD = 16;   // one uint4 of flag bytes
+constexpr int CMP_CHUNK = CMP_THREADS * CMP_PER_THREAD;
+
+__device__ __forceinline__ void load16(const unsigned* flags32, long long ncell, long long cell0, uint8_t out[16]) {
+  if (cell0 + 16 <= ncell) {
+    const uint4 q = __ldg(reinterpret_cast<const uint4*>(flags32 + (cell0 >> 2)));
+    const unsigned wv[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int m = 0; m < 16; ++m) out[m] = (uint8_t)(wv[m >> 2] >> (8 * (m & 3)));
+  } else {
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      const long long cell = cell0 + m;
+      out[m] = cell < ncell ? (uint8_t)flag_of(flags32, cell) : 0;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(CMP_THREADS) k_cmp_count(Geo g, const unsigned* __restrict__ flags32,
+                                                           unsigned* __restrict__ blk) {
+  __shared__ unsigned red[4][CMP_THREADS / 32];
+  const long long cell0 = (long long)blockIdx.x * CMP_CHUNK + (long long)threadIdx.x * CMP_PER_THREAD;
+  uint8_t f[16];
+  load16(flags32, g.ncell, cell0, f);
+  unsigned cnt[4] = {0, 0, 0, 0};
+#pragma unroll
+  for (int m = 0; m < 16; ++m) {
+    cnt[0] += f[m] & 1;
+    cnt[1] += (f[m] >> 1) & 1;
+    cnt[2] += (f[m] >> 2) & 1;
+    cnt[3] += (f[m] >> 3) & 1;
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    unsigned v = cnt[q];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
+    if ((threadIdx.x & 31) == 0) red[q][threadIdx.x >> 5] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    unsigned v = 0;
+    for (int w = 0; w < CMP_THREADS / 32; ++w) v += red[threadIdx.x][w];
+    blk[(long long)blockIdx.x * 4 + threadIdx.x] = v;
+  }
+}
+
+// single block: exclusive scan of the per-block counts (in place), totals to ds
+__global__ void __launch_bounds__(1024) k_cmp_scan(unsigned* blk, int nblk, DevState* ds, unsigned fcap) {
+  __shared__ unsigned part[4][1024];
+  const int per = (nblk + 1023) / 1024;
+  const int b0 = threadIdx.x * per, b1 = min(nblk, b0 + per);
+  unsigned loc[4] = {0, 0, 0, 0};
+  for (int b = b0; b < b1; ++b)
+    for (int q = 0; q < 4; ++q) loc[q] += blk[4 * b + q];
+  for (int q = 0; q < 4; ++q) part[q][threadIdx.x] = loc[q];
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    unsigned run = 0;
+    for (int t = 0; t < 1024; ++t) {
+      const unsigned v = part[threadIdx.x][t];
+      part[threadIdx.x][t] = run;
+      run += v;
+    }
+    if (threadIdx.x < 3) ds->nforce_c[threadIdx.x] = run;
+    else ds->nbound = run;
+  }
+  __syncthreads();
+  unsigned run[4];
+  for (int q = 0; q < 4; ++q) run[q] = part[q][threadIdx.x];
+  for (int b = b0; b < b1; ++b)
+    for (int q = 0; q < 4; ++q) {
+      const unsigned v = blk[4 * b + q];
+      blk[4 * b + q] = run[q];
+      run[q] += v;
+    }
+  if (threadIdx.x == 0) {
+    const unsigned n0 = ds->nforce_c[0], n1 = ds->nforce_c[1], n2 = ds->nforce_c[2];
+    ds->force_base[0] = 0;
+    ds->force_base[1] = n0;
+    ds->force_base[2] = n0 + n1;
+    if ((unsigned long long)n0 + n1 + n2 > fcap || ds->nbound > fcap) atomicOr(&ds->err, ERR_LIST_OVERFLOW);
+  }
+}
+
+__global__ void __launch_bounds__(CMP_THREADS) k_cmp_write(Geo g, const unsigned* __restrict__ flags32,
+                                                           const unsigned* __restrict__ blk,
+                                                           const unsigned* __restrict__ owner, const DevState* ds,
+                                                           ForceNode* flist, unsigned* blist, unsigned fcap) {
+  __shared__ unsigned wsum[4][CMP_THREADS / 32];
+  const long long cell0 = (long long)blockIdx.x * CMP_CHUNK + (long long)threadIdx.x * CMP_PER_THREAD;
+  uint8_t f[16];
+  load16(flags32, g.ncell, cell0, f);
+  unsigned cnt[4] = {0, 0, 0, 0};
+#pragma unroll
+  for (int m = 0; m < 16; ++m)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) cnt[q] += (f[m] >> q) & 1;
+  const int lane = threadIdx.x & 31, wrp = threadIdx.x >> 5;
+  unsigned excl[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    unsigned v = cnt[q];
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xFFFFFFFFu, v, o);
+      if (lane >= o) v += y;
+    }
+    excl[q] = v - cnt[q];
+    if (lane == 31) wsum[q][wrp] = v;
+  }
+  __syncthreads();
+  unsigned pos[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    unsigned before = 0;
+    for (int w = 0; w < wrp; ++w) before += wsum[q][w];
+    pos[q] = blk[(long long)blockIdx.x * 4 + q] + before + excl[q];
+  }
+  const unsigned base[3] = {ds->force_base[0], ds->force_base[1], ds->force_base[2]};
+#pragma unroll
+  for (int m = 0; m < 16; ++m) {
+    const long long cell = cell0 + m;
+    if (!f[m]) continue;
+    const long long i = cell % g.nx, j = (cell / g.nx) % g.ny, k = cell / ((long long)g.nx * g.ny);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      if ((f[m] >> c) & 1) {
+        const unsigned slot = base[c] + pos[c]++;
+        const long long node = fidx(g, c, i, j, k);
+        if (slot < fcap) {
+          ForceNode fn;
+          fn.key = ((unsigned)c << 30) | (unsigned)node;
+          fn.tri = owner[comp_off(g, c) + node];
+          flist[slot] = fn;
+        }
+      }
+    }
+    if (f[m] & FLAG_B) {
+      const unsigned slot = pos[3]++;
+      if (slot < fcap) blist[slot] = (unsigned)cell;
+    }
+  }
+}
+
+// move this step's candidate count to "previous", zero the current one
+__global__ void k_copy_count(DevState* ds) {
+  ds->ncand_prev = ds->ncand;
+  ds->ncand = 0;
+}
+
+// ---------------------------------------------------------------------------
+// host launcher: the whole tagging stage of one step
+// ---------------------------------------------------------------------------
+void launch_tagging(const Geo& g, const Surf& s, const TagBuffers& b, DevState* ds, cudaStream_t st) {
+  stage_mark(st, ST_TAG);
+  // previous step's candidates reset their nodes, then the counters restart
+  k_tag_reset<<<num_sms() * 4, 256, 0, st>>>(g, b.cand, b.cap, ds, b.d2min, b.owner, b.flags32);
+  k_copy_count<<<1, 1, 0, st>>>(ds);
+  if (s.nt > 0) {
+    const long long warps = 3ll * s.nt;
+    const long long blocks = (warps * 32 + 127) / 128;
+    k_tag_candidates<<<(unsigned)blocks, 128, 0, st>>>(g, s, b.cand, b.cap, b.d2min, ds);
+    const int gb = num_sms() * 8;
+    k_tag_resolve<<<gb, 256, 0, st>>>(g, b.cand, b.cap, ds, b.d2min, b.owner);
+    k_tag_mark<<<gb, 256, 0, st>>>(g, b.cand, b.cap, ds, b.d2min, b.owner, b.flags32);
+    k_tag_boundary<<<gb, 256, 0, st>>>(g, b.cand, b.cap, ds, b.d2min, b.owner, b.flags32);
+  }
+  const int nblk = (int)((g.ncell + CMP_CHUNK - 1) / CMP_CHUNK);
+  k_cmp_count<<<nblk, CMP_THREADS, 0, st>>>(g, b.flags32, b.blk);
+  k_cmp_scan<<<1, 1024, 0, st>>>(b.blk, nblk, ds, b.cap);
+  k_cmp_write<<<nblk, CMP_THREADS, 0, st>>>(g, b.flags32, b.blk, b.owner, ds, b.flist, b.blist, b.cap);
+}
+
+int compaction_blocks(const Geo& g) { return (int)((g.ncell + CMP_CHUNK - 1) / CMP_CHUNK); }
+
+}  // namespace ibm

@@ -1,0 +1,318 @@
+"""Thin ctypes binding of the C ABI in include/ibm.h.
+
+Every function below has the name of the C entry point it calls and does
+argument marshalling only (numpy arrays or torch tensors in, status codes to
+exceptions out).  All computation runs in the CUDA library
+libibm_gb300.so; there is no Python or CPU fallback: if the library cannot
+be loaded, every call raises.
+
+Fields are FP64 arrays in C order [k][j][i]: u, w, p of shape (nz, ny, nx),
+v of shape (nz, ny + 1, nx).  Surfaces are (nv, 3) FP64 vertex positions and
+velocities and (nt, 3) int32 triangles.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+_LIB = None
+_LOCK = threading.Lock()
+
+IBM_RK2_CN, IBM_AB_CN = 0, 1
+IBM_NOSLIP, IBM_FREESLIP = 0, 1
+IBM_FP64, IBM_MIXED = 0, 1
+
+STATUS = {0: "IBM_OK", 1: "IBM_ERR_ARG", 2: "IBM_ERR_CUDA", 3: "IBM_ERR_OOM", 4: "IBM_ERR_GEOMETRY",
+          5: "IBM_ERR_DIVERGED", 6: "IBM_ERR_TIMEOUT", 7: "IBM_ERR_STATE", 8: "IBM_ERR_CAPACITY"}
+
+
+class IbmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class ibm_grid_desc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double),
+                ("re", ctypes.c_double), ("dt", ctypes.c_double),
+                ("scheme", ctypes.c_int), ("ybc", ctypes.c_int), ("precision", ctypes.c_int),
+                ("use_q", ctypes.c_int)]
+
+
+class ibm_diag(ctypes.Structure):
+    _fields_ = [("slip_l1", ctypes.c_double), ("slip_comp", ctypes.c_double * 3),
+                ("nforce", ctypes.c_int64 * 3), ("nboundary", ctypes.c_int64),
+                ("q_f", ctypes.c_double), ("sum_q_dv", ctypes.c_double), ("steps", ctypes.c_int64),
+                ("ncandidates", ctypes.c_int64), ("kernels_per_step", ctypes.c_int64),
+                ("d2h_bytes", ctypes.c_int64)]
+
+IBM_NSTAGES = 15
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+EXPORTS = ("ibm_create_grid", "ibm_destroy", "ibm_set_surface", "ibm_set_body_force", "ibm_set_fields",
+           "ibm_step", "ibm_get_fields", "ibm_get_tags", "ibm_get_diag", "ibm_sync", "ibm_last_error",
+           "ibm_set_allocator", "ibm_version", "ibm_profile_stages", "ibm_stage_name")
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_needed: bool = True):
+    """Load libibm_gb300.so (building it in-tree first when it is missing
+    or stale).  Raises if it cannot be built or loaded."""
+    global _LIB
+    with _LOCK:
+        if _LIB is not None:
+            return _LIB
+        if build_if_needed and not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"CUDA library {_build.LIB} is missing; run __graft_entry__.build()")
+        L = ctypes.CDLL(_build.LIB)
+        P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        L.ibm_create_grid.argtypes = [ctypes.POINTER(ibm_grid_desc), P, ctypes.POINTER(P)]
+        L.ibm_destroy.argtypes = [P]
+        L.ibm_set_surface.argtypes = [P, I, P, P, I, P, I]
+        L.ibm_set_body_force.argtypes = [P, D, D, D]
+        L.ibm_set_fields.argtypes = [P, P, P, P, P, I]
+        L.ibm_step.argtypes = [P, I]
+        L.ibm_get_fields.argtypes = [P, P, P, P, P, I]
+        L.ibm_get_tags.argtypes = [P, I, P, I]
+        L.ibm_get_diag.argtypes = [P, ctypes.POINTER(ibm_diag)]
+        L.ibm_sync.argtypes = [P]
+        L.ibm_last_error.argtypes = [P]
+        L.ibm_last_error.restype = ctypes.c_char_p
+        L.ibm_set_allocator.argtypes = [ALLOC_FN, FREE_FN, P]
+        L.ibm_version.restype = ctypes.c_char_p
+        L.ibm_profile_stages.argtypes = [P, I, P, P]
+        L.ibm_stage_name.argtypes = [I]
+        L.ibm_stage_name.restype = ctypes.c_char_p
+        for name in EXPORTS:
+            if name not in ("ibm_last_error", "ibm_version", "ibm_stage_name"):
+                getattr(L, name).restype = ctypes.c_int
+        _LIB = L
+    return _LIB
+
+
+def _check(h, status: int):
+    if status != 0:
+        msg = load().ibm_last_error(h).decode() if h else ""
+        raise IbmError(status, msg)
+
+
+def _ptr(a):
+    """(pointer, on_device) of a numpy array or torch tensor (contiguous)."""
+    if a is None:
+        return None, 0
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data, 0
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr(), 1 if a.is_cuda else 0
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is not None:
+        return int(stream)
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return int(torch.cuda.current_stream().cuda_stream)
+    except Exception:
+        pass
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# C entry points
+# ---------------------------------------------------------------------------
+def ibm_create_grid(nx, ny, nz, lx=1.0, ly=1.0, lz=1.0, re=100.0, dt=1e-3, scheme=IBM_RK2_CN, ybc=IBM_NOSLIP,
+                    precision=IBM_FP64, use_q=1, stream=None):
+    L = load()
+    d = ibm_grid_desc(nx, ny, nz, lx, ly, lz, re, dt, scheme, ybc, precision, int(use_q))
+    h = ctypes.c_void_p()
+    _check(None, L.ibm_create_grid(ctypes.byref(d), _stream_handle(stream), ctypes.byref(h)))
+    return h.value
+
+
+def ibm_destroy(h):
+    _check(h, load().ibm_destroy(h))
+
+
+def ibm_set_surface(h, xyz, vel, tri=None, ntris=None):
+    """xyz, vel: (nv, 3) FP64; tri: (nt, 3) int32, or None to keep the
+    previous connectivity (then ntris must be given)."""
+    xp, xd = _ptr(xyz)
+    vp, vd = _ptr(vel)
+    tp, td = _ptr(tri)
+    if xd != vd or (tri is not None and td != xd):
+        raise ValueError("xyz, vel and tri must all live on the host or all on the device")
+    nt = int(tri.shape[0]) if tri is not None else int(ntris)
+    _check(h, load().ibm_set_surface(h, int(xyz.shape[0]), xp, vp, nt, tp, xd))
+
+
+def ibm_set_surface_raw(h, nverts, xyz_ptr, vel_ptr, ntris, tri_ptr, on_device):
+    _check(h, load().ibm_set_surface(h, int(nverts), xyz_ptr, vel_ptr, int(ntris), tri_ptr, int(on_device)))
+
+
+def ibm_set_body_force(h, fx, fy, fz):
+    _check(h, load().ibm_set_body_force(h, float(fx), float(fy), float(fz)))
+
+
+def ibm_set_fields(h, u=None, v=None, w=None, p=None):
+    ptrs = [_ptr(a) for a in (u, v, w, p)]
+    dev = {d for (q, d) in ptrs if q is not None}
+    if len(dev) > 1:
+        raise ValueError("fields must all live on the host or all on the device")
+    _check(h, load().ibm_set_fields(h, *[q for q, _ in ptrs], dev.pop() if dev else 0))
+
+
+def ibm_step(h, nsteps=1):
+    _check(h, load().ibm_step(h, int(nsteps)))
+
+
+def ibm_get_fields(h, nx, ny, nz, out=None):
+    """Returns (u, v, w, p) as FP64 numpy arrays (or fills `out`, a tuple of
+    four contiguous FP64 arrays or device tensors)."""
+    if out is None:
+        out = (np.empty((nz, ny, nx)), np.empty((nz, ny + 1, nx)), np.empty((nz, ny, nx)), np.empty((nz, ny, nx)))
+    ptrs = [_ptr(a) for a in out]
+    _check(h, load().ibm_get_fields(h, *[q for q, _ in ptrs], ptrs[0][1]))
+    return out
+
+
+def ibm_get_tags(h, comp, shape):
+    owner = np.empty(shape, dtype=np.int32)
+    _check(h, load().ibm_get_tags(h, int(comp), owner.ctypes.data, 0))
+    return owner
+
+
+def ibm_get_diag(h) -> dict:
+    d = ibm_diag()
+    _check(h, load().ibm_get_diag(h, ctypes.byref(d)))
+    return {"slip_l1": d.slip_l1, "slip_comp": list(d.slip_comp), "nforce": list(d.nforce),
+            "nboundary": d.nboundary, "q_f": d.q_f, "sum_q_dv": d.sum_q_dv, "steps": d.steps,
+            "ncandidates": d.ncandidates, "kernels_per_step": d.kernels_per_step, "d2h_bytes": d.d2h_bytes}
+
+
+def ibm_profile_stages(h, nsteps=1) -> dict:
+    """{stage name: (device ms summed over nsteps, kernels per step)}."""
+    ms = (ctypes.c_double * IBM_NSTAGES)()
+    kn = (ctypes.c_int64 * IBM_NSTAGES)()
+    _check(h, load().ibm_profile_stages(h, int(nsteps), ms, kn))
+    return {ibm_stage_name(i): (ms[i], kn[i]) for i in range(IBM_NSTAGES)}
+
+
+def ibm_stage_name(i) -> str:
+    return load().ibm_stage_name(int(i)).decode()
+
+
+def ibm_sync(h):
+    _check(h, load().ibm_sync(h))
+
+
+def ibm_last_error(h) -> str:
+    return load().ibm_last_error(h).decode()
+
+
+def ibm_version() -> str:
+    return load().ibm_version().decode()
+
+
+_TORCH_HOOK = None
+
+
+def ibm_set_allocator_torch():
+    """Route the library's device allocations through PyTorch's caching
+    allocator (on the current device and stream)."""
+    global _TORCH_HOOK
+    import torch
+
+    def _alloc(nbytes, ctx):
+        try:
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes)))
+        except Exception:
+            return None
+
+    def _free(ptr, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    _TORCH_HOOK = (ALLOC_FN(_alloc), FREE_FN(_free))
+    _check(None, load().ibm_set_allocator(_TORCH_HOOK[0], _TORCH_HOOK[1], None))
+
+
+def ibm_reset_allocator():
+    global _TORCH_HOOK
+    _check(None, load().ibm_set_allocator(ALLOC_FN(), FREE_FN(), None))
+    _TORCH_HOOK = None
+
+
+# ---------------------------------------------------------------------------
+# convenience wrapper
+# ---------------------------------------------------------------------------
+class Simulation:
+    """One simulation instance (a handle) with numpy-friendly accessors."""
+
+    def __init__(self, nx, ny, nz, lx=1.0, ly=1.0, lz=1.0, re=100.0, dt=1e-3, scheme="rk2", ybc=0,
+                 precision="fp64", use_q=True, stream=None):
+        self.shape = (nx, ny, nz)
+        sch = IBM_AB_CN if scheme == "ab" else IBM_RK2_CN
+        prec = IBM_MIXED if precision == "mixed" else IBM_FP64
+        self.h = ibm_create_grid(nx, ny, nz, lx, ly, lz, re, dt, sch, ybc, prec, int(use_q), stream)
+        self.nt = 0
+
+    def close(self):
+        if self.h:
+            ibm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_surface(self, xyz, vel, tri=None):
+        if tri is not None:
+            self.nt = int(tri.shape[0])
+            ibm_set_surface(self.h, xyz, vel, tri)
+        else:
+            ibm_set_surface(self.h, xyz, vel, None, self.nt)
+
+    def set_body_force(self, fx, fy, fz):
+        ibm_set_body_force(self.h, fx, fy, fz)
+
+    def set_fields(self, u=None, v=None, w=None, p=None):
+        ibm_set_fields(self.h, u, v, w, p)
+
+    def step(self, n=1):
+        ibm_step(self.h, n)
+
+    def fields(self):
+        nx, ny, nz = self.shape
+        return ibm_get_fields(self.h, nx, ny, nz)
+
+    def tags(self):
+        nx, ny, nz = self.shape
+        return [ibm_get_tags(self.h, c, (nz, ny + 1 if c == 1 else ny, nx)) for c in range(3)]
+
+    def diag(self):
+        return ibm_get_diag(self.h)
+
+    def sync(self):
+        ibm_sync(self.h)

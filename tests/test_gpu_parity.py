@@ -1,0 +1,284 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tags must match bit for bit (they are integer decisions made in FP64 by
+the same formulas); velocities and pressure after N steps must agree to
+max |delta| <= 1e-10 (velocity scaled by U_ref = 1, pressure by U_ref^2).
+Sizes span several tiles and ragged tails (radix-3 FFT sizes, odd ny).
+"""
+import numpy as np
+import pytest
+
+from oracle.oracle import OracleSim, make_grid, tag as oracle_tag
+from paper_2606_09799_gb300 import ibm, inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+def gpu_sim(wl_or_dims, **kw):
+    return ibm.Simulation(*wl_or_dims, **kw)
+
+
+def pair(nx, ny, nz, lx=1.0, ly=1.0, lz=1.0, **kw):
+    o = OracleSim(nx, ny, nz, lx, ly, lz, **{k: v for k, v in kw.items() if k != "precision"})
+    g = ibm.Simulation(nx, ny, nz, lx, ly, lz, **kw)
+    return o, g
+
+
+def assert_fields_close(o, g, tol=TOL, what=""):
+    gu, gv, gw, gp = g.fields()
+    for name, a, b in (("u", o.u, gu), ("v", o.v, gv), ("w", o.w, gw), ("p", o.p, gp)):
+        err = np.abs(a - b).max()
+        assert err <= tol, f"{what} {name}: max |delta| = {err:.3e}"
+
+
+def assert_tags_equal(o_owners, g):
+    gt = g.tags()
+    for c in range(3):
+        np.testing.assert_array_equal(gt[c], o_owners[c], err_msg=f"component {c}")
+
+
+def run_workload(wl, nsteps, precision="fp64", use_q=True):
+    o, g = pair(wl.nx, wl.ny, wl.nz, wl.lx, wl.ly, wl.lz, re=wl.re, dt=wl.dt, use_q=use_q, precision=precision)
+    for s in range(nsteps):
+        xyz, vel = wl.surface(s)
+        o.set_surface(xyz, vel, wl.tri)
+        g.set_surface(xyz, vel, wl.tri)
+        fx, fy, fz = wl.body_force_at(s * wl.dt)
+        o.set_body_force(fx, fy, fz)
+        g.set_body_force(fx, fy, fz)
+        o.step()
+        g.step()
+    return o, g
+
+
+# ---------------------------------------------------------------------------
+# tags
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("seed", [0, 1])
+def test_tags_bit_exact_random_triangles_ragged_grid(seed):
+    nx, ny, nz = 24, 19, 36
+    xyz, tri = inputs.random_triangles(60, seed, lo=0.38, hi=0.62, size=0.15)
+    o, g = pair(nx, ny, nz, 1.0, 1.0, 1.5)
+    g.set_surface(xyz, np.zeros_like(xyz), tri)
+    g.step()
+    own, _ = oracle_tag(o.g, xyz, tri)
+    assert_tags_equal(own, g)
+    d = g.diag()
+    assert d["nforce"] == [int((own[c] >= 0).sum()) for c in range(3)]
+
+
+def test_tags_bit_exact_periodic_wrap():
+    nx, ny, nz = 32, 32, 32
+    xyz, tri = inputs.icosphere(2, 0.2, (0.03, 0.5, 0.96))
+    o, g = pair(nx, ny, nz)
+    g.set_surface(xyz, np.zeros_like(xyz), tri)
+    g.step()
+    own, _ = oracle_tag(o.g, xyz, tri)
+    assert_tags_equal(own, g)
+
+
+@pytest.mark.parametrize("step", [0, 3, 7])
+def test_tags_bit_exact_sphere64(step):
+    wl = inputs.oscillating_sphere()
+    o, g = pair(wl.nx, wl.ny, wl.nz)
+    xyz, vel = wl.surface(step)
+    g.set_surface(xyz, vel, wl.tri)
+    g.step()
+    own, _ = oracle_tag(o.g, xyz, wl.tri)
+    assert_tags_equal(own, g)
+
+
+@pytest.mark.parametrize("step", [0, 13, 61])
+def test_tags_bit_exact_plate128_full_size(step):
+    """The plate of the 128^3 benchmark workload, nodes exactly on the
+    surface included (y = 0.5 is a v-lattice plane at step 0)."""
+    wl = inputs.heaving_plate()
+    o, g = pair(wl.nx, wl.ny, wl.nz)
+    xyz, vel = wl.surface(step)
+    g.set_surface(xyz, vel, wl.tri)
+    g.step()
+    own, _ = oracle_tag(o.g, xyz, wl.tri)
+    assert_tags_equal(own, g)
+    d = g.diag()
+    assert d["nboundary"] >= 0 and sum(d["nforce"]) > 10000
+
+
+# ---------------------------------------------------------------------------
+# FP64 fields
+# ---------------------------------------------------------------------------
+def test_fp64_sphere64_ten_steps():
+    """64^3 oscillating sphere, Re = 100, dt = 1e-3, 10 steps."""
+    wl = inputs.oscillating_sphere()
+    o, g = run_workload(wl, 10)
+    assert_fields_close(o, g)
+    assert_tags_equal(o.owners, g)
+    d = g.diag()
+    assert abs(d["slip_l1"] - o.last["slip"]) <= 1e-9 * max(1.0, o.last["slip"])
+    assert abs(d["q_f"] - o.last["qF"]) <= 1e-12
+    assert abs(d["sum_q_dv"]) < 1e-14
+    assert d["steps"] == 10
+
+
+def test_fp64_plate128_ten_steps():
+    wl = inputs.heaving_plate()
+    o, g = run_workload(wl, 10)
+    assert_fields_close(o, g)
+    d = g.diag()
+    assert abs(d["slip_l1"] - o.last["slip"]) <= 1e-9 * max(1.0, o.last["slip"])
+
+
+def test_fp64_ragged_sizes_radix3_and_odd_ny():
+    wl = inputs.oscillating_sphere(n=48, steps=4, subdiv=2)
+    o, g = pair(48, 37, 96, 1.0, 0.9, 1.6, re=150.0, dt=2e-3)
+    for s in range(4):
+        xyz, vel = wl.surface(s)
+        o.set_surface(xyz, vel, wl.tri)
+        g.set_surface(xyz, vel, wl.tri)
+        o.step()
+        g.step()
+    assert_fields_close(o, g)
+    assert_tags_equal(o.owners, g)
+
+
+@pytest.mark.parametrize("use_q", [True, False])
+@pytest.mark.parametrize("scheme", ["rk2", "ab"])
+def test_fp64_schemes_and_q_switch(use_q, scheme):
+    wl = inputs.oscillating_sphere(n=32, steps=4, subdiv=2)
+    o, g = pair(32, 32, 32, re=100.0, dt=2e-3, use_q=use_q, scheme=scheme)
+    for s in range(4):
+        xyz, vel = wl.surface(s)
+        o.set_surface(xyz, vel, wl.tri)
+        g.set_surface(xyz, vel, wl.tri)
+        o.step()
+        g.step()
+    assert_fields_close(o, g)
+
+
+def test_fp64_no_body_taylor_green_free_slip():
+    o, g = pair(32, 24, 4, 1.0, 1.0, 0.125, re=20.0, dt=4e-3, ybc=1)
+    from helpers import sample
+    PI = np.pi
+    u = sample(o.g, 0, lambda X, Y, Z: np.sin(2 * PI * X) * np.cos(PI * Y))
+    v = sample(o.g, 1, lambda X, Y, Z: -2 * np.cos(2 * PI * X) * np.sin(PI * Y))
+    w = np.zeros_like(u)
+    p = np.zeros_like(u)
+    o.set_fields(u, v, w, p)
+    g.set_fields(u, v, w, p)
+    o.step(6)
+    g.step(6)
+    assert_fields_close(o, g)
+
+
+def test_fp64_random_initial_field_with_body_force():
+    """Random velocity and pressure (v = 0 on the walls) exercise every
+    term of the explicit operator and the projection at once."""
+    nx, ny, nz = 24, 20, 48
+    u, v, w, p = inputs.random_fields(nx, ny, nz, seed=7, amp=0.3)
+    o, g = pair(nx, ny, nz, 1.0, 1.0, 2.0, re=50.0, dt=1e-3)
+    for s in (o, g):
+        s.set_fields(u, v, w, p)
+        s.set_body_force(0.3, -0.1, 0.2)
+    xyz, tri = inputs.icosphere(2, 0.2, (0.5, 0.5, 1.0))
+    vel = np.tile([0.1, -0.05, 0.2], (xyz.shape[0], 1))
+    for s in (o, g):
+        s.set_surface(xyz, vel, tri)
+    o.step(3)
+    g.step(3)
+    assert_fields_close(o, g)
+
+
+# ---------------------------------------------------------------------------
+# API behaviour and edge cases
+# ---------------------------------------------------------------------------
+def test_set_get_fields_roundtrip_and_empty_surface():
+    nx, ny, nz = 16, 12, 8
+    u, v, w, p = inputs.random_fields(nx, ny, nz, seed=3)
+    g = ibm.Simulation(nx, ny, nz)
+    g.set_fields(u, v, w, p)
+    gu, gv, gw, gp = g.fields()
+    for a, b in ((u, gu), (v, gv), (w, gw), (p, gp)):
+        np.testing.assert_array_equal(a, b)
+    # no surface: a plain fractional step, no forcing nodes
+    g.step(2)
+    d = g.diag()
+    assert d["nforce"] == [0, 0, 0] and d["nboundary"] == 0
+    for t in g.tags():
+        assert (t == -1).all()
+
+
+def test_surface_removed_and_restored():
+    wl = inputs.oscillating_sphere(n=32, steps=3, subdiv=2)
+    o, g = pair(32, 32, 32, re=100.0, dt=2e-3)
+    xyz, vel = wl.surface(0)
+    for s in (o, g):
+        s.set_surface(xyz, vel, wl.tri)
+    o.step()
+    g.step()
+    empty = np.zeros((0, 3))
+    o.set_surface(empty, empty, np.zeros((0, 3), dtype=np.int32))
+    ibm.ibm_set_surface(g.h, empty, empty, np.zeros((0, 3), dtype=np.int32))
+    o.step()
+    g.step()
+    for s in (o, g):
+        s.set_surface(xyz, vel, wl.tri)
+    o.step()
+    g.step()
+    assert_fields_close(o, g)
+    assert_tags_equal(o.owners, g)
+
+
+def test_multi_step_replay_equals_single_steps_and_is_deterministic():
+    wl = inputs.oscillating_sphere(n=32, steps=4, subdiv=2)
+    xyz, vel = wl.surface(0)
+    outs = []
+    for mode in ("one", "many", "one"):
+        g = ibm.Simulation(32, 32, 32, re=100.0, dt=2e-3)
+        g.set_surface(xyz, vel, wl.tri)
+        if mode == "one":
+            for _ in range(4):
+                g.step(1)
+        else:
+            g.step(4)
+        outs.append(g.fields())
+        g.close()
+    for a, b in zip(outs[0], outs[1]):
+        np.testing.assert_array_equal(a, b)
+    for a, b in zip(outs[0], outs[2]):
+        np.testing.assert_array_equal(a, b)
+
+
+def test_bad_surface_indices_rejected():
+    g = ibm.Simulation(16, 16, 16)
+    xyz = np.random.default_rng(0).uniform(0.3, 0.7, (4, 3))
+    tri = np.array([[0, 1, 5]], dtype=np.int32)
+    with pytest.raises(ibm.IbmError) as e:
+        g.set_surface(xyz, np.zeros_like(xyz), tri)
+    assert e.value.status == 1
+
+
+def test_probe_leaving_domain_reports_geometry_error():
+    """A body touching the wall: its probes would leave the stored planes;
+    the kernel records it and the next synchronising call reports it."""
+    g = ibm.Simulation(16, 16, 16)
+    xyz, tri = inputs.icosphere(1, 0.15, (0.5, 0.1, 0.5))
+    g.set_surface(xyz, np.zeros_like(xyz), tri)
+    g.step()
+    with pytest.raises(ibm.IbmError) as e:
+        g.sync()
+    assert e.value.status == 4
+    g.sync()          # the error word is cleared once reported
+
+
+def test_candidate_capacity_grows_for_large_triangles():
+    g = ibm.Simulation(64, 32, 64)
+    big = 0.3
+    yw = 0.4137
+    xyz = np.array([[-big, yw, -big], [1 + big, yw, -big], [-big, yw, 1 + big], [1 + big, yw, 1 + big]])
+    tri = np.array([[0, 1, 3], [0, 3, 2]], dtype=np.int32)
+    g.set_surface(xyz, np.zeros_like(xyz), tri)
+    g.step()
+    g.sync()
+    d = g.diag()
+    assert d["nforce"][0] == 2 * 64 * 64
