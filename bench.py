@@ -145,6 +145,37 @@ def algorithmic_bytes_per_cell(stage: str, word: int) -> float:
     return (r + w) * word
 
 
+TAG_FLOPS_PER_PAIR = 100.0   # closest point ~73, N and |N|^2 8, neighbour tests up to ~36 (FP64, counted from source)
+
+
+def tag_pairs(wl, step: int) -> int:
+    """Algorithmic work of Algorithm 1 for one step: (node, triangle) pairs
+    with the node strictly inside the triangle's box min - d < x < max + d,
+    summed over the three staggered grids (nodes holding unknowns only)."""
+    import numpy as np
+    xyz, _ = wl.surface(step)
+    V = xyz[wl.tri]                                   # (nt, 3 vertices, 3 coords)
+    lo, hi = V.min(axis=1), V.max(axis=1)
+    d = np.array([wl.lx / wl.nx, wl.ly / wl.ny, wl.lz / wl.nz])
+    n = np.array([wl.nx, wl.ny, wl.nz])
+    total = 0
+    for c in range(3):
+        cnt = np.ones(len(V), dtype=np.int64)
+        for a in range(3):
+            off = 0.0 if a == c else 0.5
+            l = (lo[:, a] - d[a]) / d[a] - off
+            h = (hi[:, a] + d[a]) / d[a] - off
+            i0 = np.floor(l).astype(np.int64) + 1      # first index with coordinate > lo - d
+            i1 = np.ceil(h).astype(np.int64) - 1       # last index with coordinate < hi + d
+            if a == 1:
+                jlo = 1 if c == 1 else 0
+                i0 = np.maximum(i0, jlo)
+                i1 = np.minimum(i1, n[1] - 1)
+            cnt *= np.maximum(0, i1 - i0 + 1)
+        total += int(cnt.sum())
+    return total
+
+
 def fp64_flops_per_cell(stage: str) -> float:
     """FP64 floating-point operations per cell of each kernel group in the
     FP64 path (adds, multiplies and FMAs counted as executed instructions x
@@ -242,25 +273,36 @@ def gpu_arm(args):
     h2d = 2 * surf[0][0].nbytes
     peaks = measured_peaks()
     prof = head["prof"]
-    # dominant kernel group of the headline path
-    stages = {k: v for k, v in prof.items() if k not in ("other",) and v[1] > 0}
-    top = max(stages, key=lambda k: stages[k][0])
-    top_ms, top_groups = stages[top]
-    launches = top_groups * args.profile_steps
-    avg_ms = top_ms / max(1, launches)
-    if args.precision == "fp64":
-        flops = fp64_flops_per_cell(top) * cells
-        achieved = flops / (avg_ms / 1e3) / 1e12
-        peak = args.fp64_peak_tflops
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak if peak else None, "traffic": None, "kernel": top,
-                "peak_source": "FP64 FMA-chain probe on this GB300 (2 FP64 FMA/clk/SM x 152 SM)"}
-    else:
-        byts = algorithmic_bytes_per_cell(top, 4) * cells
-        achieved = byts / (avg_ms / 1e3) / 1e9
-        peak = peaks.get("hbm_gbs", 6800.0)
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": top, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    # roofline of every kernel group of the headline path; the dominant one is reported
+    pairs = tag_pairs(wl, W)
+    groups = {}
+    for name, (tot_ms, ngroups) in prof.items():
+        if name == "other" or ngroups == 0 or tot_ms <= 0:
+            continue
+        launches = ngroups * args.profile_steps
+        avg_ms = tot_ms / launches
+        if name == "tagging":
+            work = pairs * TAG_FLOPS_PER_PAIR
+            groups[name] = dict(bound="alu", achieved=work / (avg_ms / 1e3) / 1e12, peak=args.fp64_peak_tflops,
+                                unit="TFLOP/s", avg_ms=avg_ms, share=tot_ms)
+        elif args.precision == "fp64" and fp64_flops_per_cell(name) > 0:
+            work = fp64_flops_per_cell(name) * cells
+            groups[name] = dict(bound="alu", achieved=work / (avg_ms / 1e3) / 1e12, peak=args.fp64_peak_tflops,
+                                unit="TFLOP/s", avg_ms=avg_ms, share=tot_ms)
+        elif algorithmic_bytes_per_cell(name, 4) > 0:
+            work = algorithmic_bytes_per_cell(name, 4) * cells
+            groups[name] = dict(bound="hbm", achieved=work / (avg_ms / 1e3) / 1e9, peak=peaks.get("hbm_gbs", 6800.0),
+                                unit="GB/s", avg_ms=avg_ms, share=tot_ms)
+    tot_all = sum(g["share"] for g in groups.values())
+    for g in groups.values():
+        g["frac"] = g["achieved"] / g["peak"] if g["peak"] else None
+        g["share"] = g["share"] / tot_all
+    top = max(groups, key=lambda k: groups[k]["share"])
+    tg = groups[top]
+    roof = {"bound": tg["bound"], "achieved": tg["achieved"], "peak": tg["peak"], "unit": tg["unit"],
+            "frac": tg["frac"], "traffic": None, "kernel": top,
+            "peak_source": ("FP64 FMA-chain probe on a GB300 of this pool (of measured)" if tg["bound"] == "alu"
+                            else "MEASURED_PEAKS.json hbm_gbs (of measured)")}
     kernels_per_step = head["diag"]["kernels_per_step"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
@@ -276,6 +318,9 @@ def gpu_arm(args):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": head["d2h"]},
         "slip_l1": head["diag"]["slip_l1"],
         "stages_ms_per_step": {k: v[0] / args.profile_steps for k, v in prof.items() if v[1] > 0},
+        "stage_roofline": {k: {kk: (round(vv, 4) if isinstance(vv, float) else vv) for kk, vv in g.items()}
+                           for k, g in groups.items()},
+        "tag_pairs_per_step": pairs,
     }
     for prec, r in results.items():
         line[prec] = {"value": world * cells * K / (r["ms"] / 1e3) / 1e9, "ms_per_step": r["ms"] / K,

@@ -311,7 +311,7 @@ __global__ void k_fft_z(Geo g, Fields<T> f, const T* __restrict__ tw, FftPlan pl
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(128) k_tri_y(Geo g, Fields<T> f, const double* __restrict__ cp,
-                                               const double* __restrict__ inv) {
+                                               const double* __restrict__ inv, double2* fwd) {
   using C = typename Cplx<T>::type;
   const int nkx = g.nkx;
   const long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -319,41 +319,47 @@ __global__ void __launch_bounds__(128) k_tri_y(Geo g, Fields<T> f, const double*
   const long long kx = l % nkx, kz = l / nkx;
   const long long base = kz * (long long)g.ny * nkx + kx, stride = nkx;
   C* spec = reinterpret_cast<C*>(f.spec);
+  // forward values stay FP64: in place for the FP64 path, in an FP64 scratch
+  // spectrum for the mixed path
+  double2* F = fwd ? fwd : reinterpret_cast<double2*>(f.spec);
   const double a = g.idy * g.idy;
   const bool singular = (kx == 0 && kz == 0);
-  C z0 = spec[base];
-  double pr = singular ? 0.0 : (double)z0.x * inv[base];
-  double pi = singular ? 0.0 : (double)z0.y * inv[base];
-  spec[base].x = (T)pr;
-  spec[base].y = (T)pi;
-  // keep FP64 intermediates in a second pass: the forward values are stored
-  // in the spectrum (T) only for the mixed path; the FP64 path stores exactly.
-  for (int j = 1; j < g.ny; ++j) {
+  double pr = 0.0, pi = 0.0;
+  for (int j = 0; j < g.ny; ++j) {
     const long long id = base + (long long)j * stride;
     const C zj = spec[id];
-    pr = ((double)zj.x - a * pr) * inv[id];
-    pi = ((double)zj.y - a * pi) * inv[id];
-    spec[id].x = (T)pr;
-    spec[id].y = (T)pi;
+    if (j == 0) {
+      pr = singular ? 0.0 : (double)zj.x * inv[id];
+      pi = singular ? 0.0 : (double)zj.y * inv[id];
+    } else {
+      pr = ((double)zj.x - a * pr) * inv[id];
+      pi = ((double)zj.y - a * pi) * inv[id];
+    }
+    F[id] = make_double2(pr, pi);
   }
   double xr = pr, xi = pi;
   double sr = xr, si = xi;
+  spec[base + (long long)(g.ny - 1) * stride].x = (T)xr;
+  spec[base + (long long)(g.ny - 1) * stride].y = (T)xi;
   for (int j = g.ny - 2; j >= 0; --j) {
     const long long id = base + (long long)j * stride;
-    const C zj = spec[id];
-    xr = (double)zj.x - cp[id] * xr;
-    xi = (double)zj.y - cp[id] * xi;
+    const double2 zj = F[id];
+    xr = zj.x - cp[id] * xr;
+    xi = zj.y - cp[id] * xi;
+    if (singular) F[id] = make_double2(xr, xi);
     spec[id].x = (T)xr;
     spec[id].y = (T)xi;
     sr += xr;
     si += xi;
   }
   if (singular) {
+    // zero-mean gauge, from the FP64 values
     const double mr = sr / g.ny, mi = si / g.ny;
     for (int j = 0; j < g.ny; ++j) {
       const long long id = base + (long long)j * stride;
-      spec[id].x = (T)((double)spec[id].x - mr);
-      spec[id].y = (T)((double)spec[id].y - mi);
+      const double2 v = (j == g.ny - 1) ? make_double2(pr, pi) : F[id];
+      spec[id].x = (T)(v.x - mr);
+      spec[id].y = (T)(v.y - mi);
     }
   }
 }
@@ -461,7 +467,8 @@ void launch_poisson(const Geo& g, const Fields<T>& f, const TagBuffers& b, const
   {
     stage_mark(st, ST_TRI_Y);
     const long long lines = (long long)g.nkx * g.nz;
-    k_tri_y<T><<<(unsigned)((lines + 127) / 128), 128, 0, st>>>(g, f, tb.cp, tb.inv);
+    double2* fwd = sizeof(T) == sizeof(double) ? nullptr : reinterpret_cast<double2*>(f.scr);
+    k_tri_y<T><<<(unsigned)((lines + 127) / 128), 128, 0, st>>>(g, f, tb.cp, tb.inv, fwd);
   }
   stage_mark(st, ST_FFT_Z_INV);
   k_fft_z<T, true><<<g.ny * ntile, 256, smz, st>>>(g, f, tb.twz, pz, cols);

@@ -33,7 +33,8 @@ static thread_local StageTimer* t_timer = nullptr;
 void stage_mark(cudaStream_t st, int id) {
   StageTimer* t = t_timer;
   if (!t || t->n >= StageTimer::MAXM) return;
-  cudaEventRecord(t->ev[t->n], st);
+  // inside stream capture only an external record becomes a graph node
+  cudaEventRecordWithFlags(t->ev[t->n], st, cudaEventRecordExternal);
   t->id[t->n] = id;
   t->n++;
 }
@@ -179,6 +180,13 @@ static ibm_status cuda_fail(ibm_handle h, cudaError_t e, const char* what) {
     cudaError_t e_ = (call);                                  \
     if (e_ != cudaSuccess) return cuda_fail(h, e_, #call);    \
   } while (0)
+
+// Report (and clear) any error a launch left in the runtime's last-error
+// slot, so it never leaks into the caller's framework.
+static ibm_status launch_status(ibm_handle h, const char* what) {
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? IBM_OK : cuda_fail(h, e, what);
+}
 
 static void* dalloc(ibm_handle h, size_t bytes) {
   void* p = h->al.get(bytes);
@@ -418,7 +426,7 @@ static ibm_status full_reset(ibm_handle h, cudaStream_t st) {
   CK(cudaMemsetAsync(h->tb.flags32, 0, round16((size_t)(g.ncell + 3) / 4 * 4), st));
   CK(cudaMemsetAsync(&h->ds->ncand, 0, sizeof(unsigned), st));
   h->need_full_reset = false;
-  return IBM_OK;
+  return launch_status(h, "reset");
 }
 
 static long long count_kernel_nodes(cudaGraph_t gr) {
@@ -438,10 +446,19 @@ template <typename T>
 static ibm_status capture(ibm_handle h) {
   if (h->exec) { cudaGraphExecDestroy(h->exec); h->exec = nullptr; }
   if (h->graph) { cudaGraphDestroy(h->graph); h->graph = nullptr; }
+  {
+    const ibm_status ls = launch_status(h, "before capture");
+    if (ls != IBM_OK) return ls;
+  }
   CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
   enqueue_step<T>(h, h->cap);
+  const cudaError_t le = cudaGetLastError();
   cudaGraph_t gr = nullptr;
   cudaError_t e = cudaStreamEndCapture(h->cap, &gr);
+  if (le != cudaSuccess) {
+    if (gr) cudaGraphDestroy(gr);
+    return cuda_fail(h, le, "kernel launch during capture");
+  }
   if (e != cudaSuccess) return cuda_fail(h, e, "graph capture");
   h->graph = gr;
   CK(cudaGraphInstantiate(&h->exec, gr, 0));
@@ -614,8 +631,7 @@ ibm_status ibm_destroy(ibm_handle h) {
 ibm_status ibm_set_body_force(ibm_handle h, double fx, double fy, double fz) {
   if (!h) return IBM_ERR_ARG;
   k_set_force<<<1, 1, 0, h->user>>>(h->ds, fx, fy, fz);
-  CK(cudaGetLastError());
-  return IBM_OK;
+  return launch_status(h, "ibm_set_body_force");
 }
 
 // upper bound of the candidates a surface can produce: nodes inside every
@@ -743,7 +759,7 @@ ibm_status ibm_set_surface(ibm_handle h, int nverts, const double* xyz, const do
   h->nv = nverts;
   h->nt = ntris;
   h->has_topology = true;
-  return IBM_OK;
+  return launch_status(h, "ibm_set_surface");
 }
 
 ibm_status ibm_set_fields(ibm_handle h, const double* u, const double* v, const double* w, const double* p,
@@ -831,7 +847,7 @@ ibm_status ibm_step(ibm_handle h, int nsteps) {
   }
   for (int n = 0; n < nsteps; ++n) CK(cudaGraphLaunch(h->exec, h->user));
   h->steps += nsteps;
-  return IBM_OK;
+  return launch_status(h, "ibm_step");
 }
 
 ibm_status ibm_get_fields(ibm_handle h, double* u, double* v, double* w, double* p, int on_device) {
@@ -934,9 +950,11 @@ ibm_status ibm_profile_stages(ibm_handle h, int nsteps, double* ms, int64_t* ker
     e = cudaGraphLaunch(ex, h->user);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->user);
     if (e != cudaSuccess) { rc = cuda_fail(h, e, "profiling step"); break; }
-    for (int m = 0; m + 1 < tm->n; ++m) {
+    for (int m = 0; m + 1 < tm->n && rc == IBM_OK; ++m) {
       float t = 0.f;
-      if (cudaEventElapsedTime(&t, tm->ev[m], tm->ev[m + 1]) == cudaSuccess) acc[tm->id[m]] += t;
+      e = cudaEventElapsedTime(&t, tm->ev[m], tm->ev[m + 1]);
+      if (e != cudaSuccess) rc = cuda_fail(h, e, "cudaEventElapsedTime");
+      acc[tm->id[m]] += t;
     }
     h->steps += 1;
   }
@@ -950,7 +968,14 @@ ibm_status ibm_profile_stages(ibm_handle h, int nsteps, double* ms, int64_t* ker
   if (gr) cudaGraphDestroy(gr);
   for (int m = 0; m < StageTimer::MAXM; ++m) cudaEventDestroy(tm->ev[m]);
   delete tm;
-  if (rc != IBM_OK) return rc;
+  if (rc != IBM_OK) {
+    cudaGetLastError();
+    return rc;
+  }
+  {
+    const ibm_status ls = launch_status(h, "ibm_profile_stages");
+    if (ls != IBM_OK) return ls;
+  }
   for (int q = 0; q < ST_COUNT; ++q) {
     if (ms) ms[q] = acc[q];
     if (kernels) kernels[q] = cnt[q];

@@ -1,0 +1,97 @@
+"""Mixed path (FP32 bulk arithmetic; FP64 tagging, geometry, per-wavenumber
+Thomas solve and reductions) against the FP64 CPU oracle and the FP64 GPU
+path on the same inputs.
+
+Error budget, written here as the bar:
+  - tags bit-exact (the FP64 tagging is shared by both paths);
+  - velocity: max |u_mixed - u_oracle| <= 1e-5 U_ref after 10 steps;
+  - discrete divergence of the projected field on the fluid cells:
+    max |D u - q_F| <= 1e-7 U_ref / dx;
+  - mean no-slip error ||eps||_1 within 5% of the FP64 path's.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from oracle.oracle import OracleSim
+from paper_2606_09799_gb300 import ibm, inputs
+
+pytestmark = pytest.mark.gpu
+
+VEL_TOL = 1e-5
+DIV_TOL = 1e-7
+SLIP_REL = 0.05
+
+
+def run(wl, nsteps, precision):
+    g = ibm.Simulation(wl.nx, wl.ny, wl.nz, wl.lx, wl.ly, wl.lz, re=wl.re, dt=wl.dt, precision=precision)
+    slips = []
+    for s in range(nsteps):
+        xyz, vel = wl.surface(s)
+        g.set_surface(xyz, vel, wl.tri)
+        g.step()
+        slips.append(g.diag()["slip_l1"])
+    return g, slips
+
+
+def oracle_run(wl, nsteps):
+    o = OracleSim(wl.nx, wl.ny, wl.nz, wl.lx, wl.ly, wl.lz, re=wl.re, dt=wl.dt)
+    slips = []
+    for s in range(nsteps):
+        xyz, vel = wl.surface(s)
+        o.set_surface(xyz, vel, wl.tri)
+        o.step()
+        slips.append(o.last["slip"])
+    return o, slips
+
+
+def divergence_error(g, sim_shape, lx=1.0, ly=1.0, lz=1.0):
+    nx, ny, nz = sim_shape
+    gr = orc.make_grid(nx, ny, nz, lx, ly, lz)
+    u, v, w, p = g.fields()
+    d = orc.divergence(gr, u, v, w)
+    own = g.tags()
+    isb = orc.boundary_cells(gr, own)
+    qf = g.diag()["q_f"]
+    fluid = isb == 0
+    return np.abs(d - qf)[fluid].max() * gr.dx
+
+
+@pytest.mark.parametrize("name,nsteps", [("sphere64", 10), ("plate128", 10)])
+def test_mixed_vs_oracle(name, nsteps):
+    wl = inputs.workload(name)
+    o, oslip = oracle_run(wl, nsteps)
+    g, gslip = run(wl, nsteps, "mixed")
+    gt = g.tags()
+    for c in range(3):
+        np.testing.assert_array_equal(gt[c], o.owners[c])
+    gu, gv, gw, gp = g.fields()
+    err = max(np.abs(o.u - gu).max(), np.abs(o.v - gv).max(), np.abs(o.w - gw).max())
+    assert err <= VEL_TOL, f"velocity error {err:.3e}"
+    perr = np.abs((o.p - o.p.mean()) - (gp - gp.mean())).max()
+    assert perr <= 100 * VEL_TOL * max(1.0, np.abs(o.p).max()), f"pressure error {perr:.3e}"
+    div = divergence_error(g, (wl.nx, wl.ny, wl.nz))
+    assert div <= DIV_TOL, f"divergence {div:.3e} U/dx"
+
+
+def test_mixed_slip_error_matches_fp64_path():
+    wl = inputs.heaving_plate()
+    _, s64 = run(wl, 20, "fp64")
+    _, s32 = run(wl, 20, "mixed")
+    m64, m32 = np.mean(s64[5:]), np.mean(s32[5:])
+    assert abs(m32 - m64) <= SLIP_REL * m64, (m32, m64)
+
+
+def test_mixed_ragged_sizes():
+    wl = inputs.oscillating_sphere(n=48, steps=4, subdiv=2)
+    o = OracleSim(48, 37, 96, 1.0, 0.9, 1.6, re=150.0, dt=2e-3)
+    g = ibm.Simulation(48, 37, 96, 1.0, 0.9, 1.6, re=150.0, dt=2e-3, precision="mixed")
+    for s in range(4):
+        xyz, vel = wl.surface(s)
+        o.set_surface(xyz, vel, wl.tri)
+        g.set_surface(xyz, vel, wl.tri)
+        o.step()
+        g.step()
+    gu, gv, gw, _ = g.fields()
+    err = max(np.abs(o.u - gu).max(), np.abs(o.v - gv).max(), np.abs(o.w - gw).max())
+    assert err <= VEL_TOL, f"velocity error {err:.3e}"
