@@ -72,7 +72,17 @@ typedef enum {
 
 enum { IBM_RK2_CN = 0, IBM_AB_CN = 1 };   /* time schemes, Section 2 */
 enum { IBM_NOSLIP = 0, IBM_FREESLIP = 1 }; /* condition on the y walls */
-enum { IBM_FP64 = 0, IBM_MIXED = 1 };      /* precision of the bulk arithmetic */
+/* precision of the bulk arithmetic:
+ *   IBM_FP64        everything in FP64;
+ *   IBM_MIXED       stencils, forcing interpolation and FFTs in FP32; FP64
+ *                   tagging geometry and per-wavenumber Thomas solves; the
+ *                   velocity state kept as an unevaluated FP32 pair (hi + lo)
+ *                   and a final correction solve on the residual divergence
+ *                   computed in that pair arithmetic, so D u = q holds to
+ *                   ~1e-12 of U/dx;
+ *   IBM_MIXED_FAST  as IBM_MIXED with an FP32 velocity state and a single
+ *                   solve (divergence at the FP32 solve error, ~1e-6 U/dx). */
+enum { IBM_FP64 = 0, IBM_MIXED = 1, IBM_MIXED_FAST = 2 };
 
 typedef struct {
   int nx, ny, nz;      /* cells; nx and nz must factor into 2s and 3s, 4 <= n <= 1024; ny >= 4 */
@@ -81,7 +91,7 @@ typedef struct {
   double dt;           /* time step */
   int scheme;          /* IBM_RK2_CN (default) or IBM_AB_CN */
   int ybc;             /* IBM_NOSLIP (default) or IBM_FREESLIP */
-  int precision;       /* IBM_FP64 or IBM_MIXED (FP32 bulk; FP64 tagging, Thomas, geometry) */
+  int precision;       /* IBM_FP64, IBM_MIXED or IBM_MIXED_FAST (see above) */
   int use_q;           /* 1: Eq. elliptic_mod with q (the paper's method); 0: Eq. elliptic */
 } ibm_grid_desc;
 
@@ -159,7 +169,7 @@ ibm_status ibm_set_allocator(ibm_alloc_fn alloc, ibm_free_fn free_fn, void* ctx)
  * event records between its kernel groups, and returns per group the total
  * device milliseconds in ms[IBM_NSTAGES] and the number of kernels in
  * kernels[IBM_NSTAGES] (either may be NULL).  Synchronises. */
-#define IBM_NSTAGES 15
+#define IBM_NSTAGES 16
 ibm_status ibm_profile_stages(ibm_handle h, int nsteps, double* ms, int64_t* kernels);
 
 /* Name of kernel group `stage` (0 <= stage < IBM_NSTAGES), else "". */

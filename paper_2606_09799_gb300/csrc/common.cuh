@@ -53,6 +53,7 @@ __host__ __device__ inline int wrapi(long long i, int n) {
 struct DevState {
   double fb[3];                  // uniform body force
   double qf[2];                  // q_F of each sub-stage
+  float qf_hi[2], qf_lo[2];      // q_F as an unevaluated FP32 pair (mixed correction)
   double sum_a[2];               // sum over C_B of D uhat dV per sub-stage
   double slip_sum[3];            // sum |eps_i| of the last step
   unsigned int err;              // ERR_* bits
@@ -92,5 +93,27 @@ struct Stage {
   double gam, rho, alp;
   int s;                          // sub-stage index
 };
+
+// ---- unevaluated FP32 pairs (hi + lo): error-free transformations ----------
+// s + e == a + b exactly (Knuth's TwoSum)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+// p + e == a * b exactly (fused multiply-add residual)
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = __fmul_rn(a, b);   // rounded product, never contracted into a later add
+  e = fmaf(a, b, -p);
+}
+// (hi, lo) <- (hi, lo) + d, renormalised
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float d) {
+  float s, e;
+  two_sum(hi, d, s, e);
+  const float t = lo + e;
+  const float h2 = s + t;
+  lo = t - (h2 - s);
+  hi = h2;
+}
 
 }  // namespace ibm

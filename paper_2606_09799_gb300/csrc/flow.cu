@@ -70,7 +70,9 @@ __device__ inline void forcing_geometry(const Geo& g, const Surf& s, unsigned ke
   const long long mk = llround((cen[2] - ng.x[2]) / g.lz);
   if (mi != 0 || mk != 0) node_pos(g, c, i + mi * g.nx, j, k + mk * g.nz, ng.x);
   double wb[3];
-  closest_point_exact(ng.x, A, B, C, ng.X, wb);
+  TriConst TC;
+  tri_const(A, B, C, TC);
+  closest_point_exact(ng.x, TC, ng.X, wb);
 #pragma unroll
   for (int d = 0; d < 3; ++d) ng.N[d] = dsub(ng.x[d], ng.X[d]);
   ng.n2 = ddot(ng.N, ng.N);
@@ -112,7 +114,9 @@ __global__ void k_ib_scatter(Fields<T> f, const ForceNode* __restrict__ flist, u
   const unsigned n = min(ds->nforce_c[0] + ds->nforce_c[1] + ds->nforce_c[2], cap);
   for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
     const ForceNode fn = flist[e];
-    comp_ptr(f, (int)(fn.key >> 30))[fn.key & KEY_MASK] = f.uf[e];
+    const int c = (int)(fn.key >> 30);
+    comp_ptr(f, c)[fn.key & KEY_MASK] = f.uf[e];
+    if (f.lo[c]) f.lo[c][fn.key & KEY_MASK] = (T)0;
   }
 }
 
@@ -134,28 +138,39 @@ void launch_ib_force(const Geo& g, const Surf& s, const Fields<T>& f, const TagB
 // tangential components see the ghost value u_{-1} = gs u_0 beyond a wall
 // (gs = -1 no-slip at rest, +1 free-slip).
 // ---------------------------------------------------------------------------
+// Scalar coefficients of one sub-stage in the bulk type, formed once on the
+// host (no per-thread FP64 arithmetic in the FP32 path).
 template <typename T>
-__global__ void __launch_bounds__(256) k_rhs(Geo g, Fields<T> f, const unsigned* __restrict__ flags32, Stage sg,
-                                             double dt, double re, int use_hp, int write_h, const DevState* ds) {
+struct RhsCoef {
+  T idx, idy, idz, idx2, idy2, idz2;
+  T gs;                 // wall ghost sign of the tangential components
+  T cg, cr, ca, cv;     // gamma, rho, alpha, alpha / Re
+  T dt;
+  T fba;                // alpha, multiplying the body force read from the device state
+};
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_rhs(Geo g, Fields<T> f, const unsigned* __restrict__ flags32, RhsCoef<T> cf,
+                                             int use_hp, int write_h, const DevState* ds) {
   const int nx = g.nx, ny = g.ny, nz = g.nz;
-  const long long total = g.ncell;
-  const T idx = (T)g.idx, idy = (T)g.idy, idz = (T)g.idz;
-  const T idx2 = idx * idx, idy2 = idy * idy, idz2 = idz * idz;
-  const T gs = g.ybc == 0 ? (T)-1 : (T)1;
+  const T idx = cf.idx, idy = cf.idy, idz = cf.idz;
+  const T idx2 = cf.idx2, idy2 = cf.idy2, idz2 = cf.idz2;
+  const T gs = cf.gs;
   const T q = (T)0.25;
-  const T cg = (T)sg.gam, cr = (T)sg.rho, ca = (T)sg.alp, cv = (T)(sg.alp / re), tdt = (T)dt;
-  const T fbx = (T)(sg.alp * ds->fb[0]), fby = (T)(sg.alp * ds->fb[1]), fbz = (T)(sg.alp * ds->fb[2]);
+  const T cg = cf.cg, cr = cf.cr, ca = cf.ca, cv = cf.cv, tdt = cf.dt;
+  const T fbx = cf.fba * (T)ds->fb[0], fby = cf.fba * (T)ds->fb[1], fbz = cf.fba * (T)ds->fb[2];
   const long long pv = (long long)(ny + 1) * nx;   // v plane stride (k)
   const long long pu = (long long)ny * nx;         // u, w, p plane stride
   const T* __restrict__ U = f.u;
   const T* __restrict__ V = f.v;
   const T* __restrict__ W = f.w;
   const T* __restrict__ P = f.p;
-  for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < total;
-       cell += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(cell % nx);
-    const int j = (int)((cell / nx) % ny);
-    const int k = (int)(cell / pu);
+  {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= nx || j >= ny) return;
+    const long long cell = (long long)k * pu + (long long)j * nx + i;
     const int ip = i + 1 == nx ? 0 : i + 1, im = i == 0 ? nx - 1 : i - 1;
     const int kp = k + 1 == nz ? 0 : k + 1, km = k == 0 ? nz - 1 : k - 1;
     const long long r0 = (long long)k * pu + (long long)j * nx;      // row (j,k) of u, w, p
@@ -242,182 +257,547 @@ __global__ void __launch_bounds__(256) k_rhs(Geo g, Fields<T> f, const unsigned*
 template <typename T>
 void launch_rhs(const Geo& g, const Fields<T>& f, const TagBuffers& b, const Stage& sg, double dt, double re,
                 bool use_hp, bool write_h, DevState* ds, cudaStream_t st) {
-  const long long blocks = (g.ncell + 255) / 256;
+  RhsCoef<T> cf;
+  cf.idx = (T)g.idx; cf.idy = (T)g.idy; cf.idz = (T)g.idz;
+  cf.idx2 = (T)(g.idx * g.idx); cf.idy2 = (T)(g.idy * g.idy); cf.idz2 = (T)(g.idz * g.idz);
+  cf.gs = g.ybc == 0 ? (T)-1 : (T)1;
+  cf.cg = (T)sg.gam; cf.cr = (T)sg.rho; cf.ca = (T)sg.alp; cf.cv = (T)(sg.alp / re);
+  cf.dt = (T)dt;
+  cf.fba = (T)sg.alp;
   stage_mark(st, ST_RHS);
-  k_rhs<T><<<(unsigned)blocks, 256, 0, st>>>(g, f, b.flags32, sg, dt, re, use_hp ? 1 : 0, write_h ? 1 : 0, ds);
+  k_rhs<T><<<dim3((g.nx + 31) / 32, (g.ny + 3) / 4, g.nz), dim3(32, 4), 0, st>>>(g, f, b.flags32, cf, use_hp ? 1 : 0,
+                                                                               write_h ? 1 : 0, ds);
 }
 
 // ---------------------------------------------------------------------------
 // Approximate factorisation: (1 - beta L_x)(1 - beta L_z)(1 - beta L_y) du = R
 // Each factor is a tridiagonal system per grid line; forcing nodes are
-// identity rows (the provisional equation is not solved there).  A line
-// without forcing nodes has constant coefficients and uses tabulated
-// recurrences (no division, no scratch); a line with forcing nodes is
-// solved by Thomas with its c' kept in the scratch array.
+// identity rows (the provisional equation is not solved there).  Every
+// pivot depends only on the row's position m inside its segment (from the
+// line start or from the row after an identity row), so all lines run on
+// tabulated recurrences: no division, no scratch.  Lines without forcing
+// nodes (known from the per-line records written by the tagging) take a
+// branch-free path with batched loads.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ bool is_forcing(const unsigned* flags32, long long cell, int c) {
   return (flags32[cell >> 2] >> (8 * (cell & 3) + c)) & 1u;
 }
 
-// periodic direction dir (0 = x, 2 = z) for component blockIdx.y
-template <typename T>
-__global__ void __launch_bounds__(128) k_sweep_periodic(Geo g, Fields<T> f, const unsigned* __restrict__ flags32,
-                                                        SweepTables<T> tb, int dir) {
-  const int c = blockIdx.y;
-  const int j0 = c == 1 ? 1 : 0, nj = c == 1 ? g.ny - 1 : g.ny;
-  const int pl = planes(g, c);
-  long long nlines, n, stride, fstride;
-  if (dir == 0) { nlines = (long long)nj * g.nz; n = g.nx; stride = 1; fstride = 1; }
-  else { nlines = (long long)nj * g.nx; n = g.nz; stride = (long long)pl * g.nx; fstride = (long long)g.ny * g.nx; }
-  const long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (l >= nlines) return;
-  long long base, fbase;
-  if (dir == 0) {
-    const long long j = j0 + l % nj, k = l / nj;
-    base = fidx(g, c, 0, j, k);
-    fbase = cidx(g, 0, j, k);
-  } else {
-    const long long i = l % g.nx, j = j0 + l / g.nx;
-    base = fidx(g, c, i, j, 0);
-    fbase = cidx(g, i, j, 0);
-  }
-  T* __restrict__ R = f.R[c];
-  T* __restrict__ S = f.scr + comp_off(g, c);
-  const int d = dir == 0 ? 0 : 1;
-  const T off = dir == 0 ? tb.off[0] : tb.off[2];
-  const T a = -off;
-  long long f0 = -1;
-  for (long long m = 0; m < n; ++m)
-    if (is_forcing(flags32, fbase + m * fstride, c)) { f0 = m; break; }
-  if (f0 < 0) {
-    // Sherman-Morrison with tabulated recurrences of the modified matrix
+// Line solvers.  `E(m)` is a reference to row m of this thread's line in
+// shared memory, `F(m)` the flag byte of its cell; rows are solved in place.
+
+// periodic line (x or z) of component c; f0 = first forcing row or >= n
+template <typename T, class Elem, class Flag>
+__device__ __forceinline__ void solve_periodic(int n, int c, int f0, int d, T a, const SweepTables<T>& tb, Elem E,
+                                               Flag F) {
+  auto forcing = [&](int r) { return (F(r) >> c) & 1; };
+  if (f0 >= n) {
+    // Sherman-Morrison: y = T^-1 r by tabulated Thomas, y_0 = g0 . r, then
+    // x = y - (v.y / (1 + v.z)) z
     const T* __restrict__ inv = tb.inv[d];
     const T* __restrict__ cp = tb.cp[d];
     const T* __restrict__ zv = tb.zv[d];
     const T* __restrict__ g0 = tb.g0[d];
-    T prev = R[base] * inv[0];
-    T acc = g0[0] * R[base];
-    R[base] = prev;
-    for (long long m = 1; m < n; ++m) {
-      const T dm = R[base + m * stride];
-      acc += g0[m] * dm;
-      prev = (dm - a * prev) * inv[m];
-      R[base + m * stride] = prev;
+    T prev = (T)0, acc = (T)0;
+    for (int m = 0; m < n; ++m) {
+      const T dm = E(m);
+      acc += __ldg(g0 + m) * dm;
+      prev = (dm - a * prev) * __ldg(inv + m);
+      E(m) = prev;
     }
     const T fact = (acc + (a / tb.gam[d]) * prev) / tb.smden[d];
     T y = prev;
-    R[base + (n - 1) * stride] = y - fact * zv[n - 1];
-    for (long long m = n - 2; m >= 0; --m) {
-      y = R[base + m * stride] - cp[m] * y;
-      R[base + m * stride] = y - fact * zv[m];
+    E(n - 1) = y - fact * __ldg(zv + n - 1);
+    for (int m = n - 2; m >= 0; --m) {
+      y = E(m) - __ldg(cp + m) * y;
+      E(m) = y - fact * __ldg(zv + m);
     }
     return;
   }
-  // rotate the line to start at its first forcing row: the periodic system
-  // becomes an ordinary one whose row 0 is the identity
-  const T bf = (T)1 + (T)2 * off;
-  const long long id0 = base + f0 * stride;
-  const T x0 = R[id0];
-  S[id0] = (T)0;
-  T cprev = (T)0, dprev = x0;
-  for (long long m = 1; m < n; ++m) {
-    const long long r = (f0 + m) % n;
-    const long long id = base + r * stride;
-    T dm = R[id];
-    T am, bm, cm;
-    if (is_forcing(flags32, fbase + r * fstride, c)) { am = (T)0; bm = (T)1; cm = (T)0; }
-    else { am = a; bm = bf; cm = a; }
-    if (m == n - 1) { dm -= cm * x0; cm = (T)0; }
-    const T den = bm - am * cprev;
-    cprev = cm / den;
-    dprev = (dm - am * dprev) / den;
-    S[id] = cprev;
-    R[id] = dprev;
+  // rotated to start at the first forcing row: row 0 of the rotated system
+  // is an identity row; the periodic coupling of the last row to it moves
+  // to the right-hand side
+  const T* __restrict__ invR = tb.invR[d];
+  const T* __restrict__ cpR = tb.cpR[d];
+  auto rot = [&](int q) { const int r = f0 + q; return r >= n ? r - n : r; };
+  const T x0 = E(f0);
+  T prev = x0;
+  int m = 0;
+  for (int q = 1; q < n; ++q) {
+    const int r = rot(q);
+    if (forcing(r)) { prev = E(r); m = 0; continue; }
+    T dq = E(r);
+    if (q == n - 1) dq -= a * x0;
+    prev = (dq - a * prev) * __ldg(invR + m);
+    E(r) = prev;
+    ++m;
   }
-  T x = dprev;
-  for (long long m = n - 2; m >= 1; --m) {
-    const long long id = base + ((f0 + m) % n) * stride;
-    x = R[id] - S[id] * x;
-    R[id] = x;
+  T x = prev;
+  int mq = -1;
+  if (!forcing(rot(n - 1))) {
+    int lo = n - 2;
+    while (lo > 0 && !forcing(rot(lo))) --lo;
+    mq = (n - 1) - lo - 1;
+  }
+  for (int q = n - 2; q >= 1; --q) {
+    const int r = rot(q);
+    if (forcing(r)) { x = E(r); mq = -1; continue; }
+    if (mq < 0) {
+      int lo = q - 1;
+      while (lo > 0 && !forcing(rot(lo))) --lo;
+      mq = q - lo - 1;
+    } else {
+      --mq;
+    }
+    x = E(r) - __ldg(cpR + mq) * x;
+    E(r) = x;
   }
 }
 
-// wall-normal direction; the result du is added to the state: uhat = u^s + du
-template <typename T>
-__global__ void __launch_bounds__(128) k_sweep_y(Geo g, Fields<T> f, const unsigned* __restrict__ flags32,
-                                                 SweepTables<T> tb) {
-  const int c = blockIdx.y;
-  const int j0 = c == 1 ? 1 : 0, n = c == 1 ? g.ny - 1 : g.ny;
-  const long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (l >= (long long)g.nx * g.nz) return;
-  const long long i = l % g.nx, k = l / g.nx;
-  const long long base = fidx(g, c, i, j0, k), stride = g.nx;
-  const long long fbase = cidx(g, i, j0, k);
-  T* __restrict__ R = f.R[c];
-  T* __restrict__ S = f.scr + comp_off(g, c);
-  T* __restrict__ Uc = comp_ptr(f, c);
-  const T off = tb.off[1];
-  const T a = -off;
-  bool any = false;
-  for (int m = 0; m < n && !any; ++m) any = is_forcing(flags32, fbase + (long long)m * stride, c);
+// wall-normal line of component c (n rows); any = line holds forcing rows
+template <typename T, class Elem, class Flag>
+__device__ __forceinline__ void solve_wall(int n, int c, bool any, T a, const SweepTables<T>& tb, Elem E, Flag F) {
+  const bool tang = c != 1;
+  auto forcing = [&](int r) { return (F(r) >> c) & 1; };
   if (!any) {
-    const int cls = c == 1 ? 1 : 0;
-    const T* __restrict__ inv = tb.yinv[cls];
-    const T* __restrict__ cp = tb.ycp[cls];
-    T prev = R[base] * inv[0];
-    R[base] = prev;
-    for (int m = 1; m < n; ++m) {
-      const long long id = base + (long long)m * stride;
-      prev = (R[id] - a * prev) * inv[m];
-      R[id] = prev;
+    const T* __restrict__ inv = tang ? tb.yinvW : tb.vinvR;
+    const T* __restrict__ cp = tang ? tb.ycpW : tb.vcpR;
+    const T invlast = tang ? tb.yinvLW[n - 1] : inv[n - 1];
+    T prev = (T)0;
+    for (int m = 0; m < n; ++m) {
+      prev = (E(m) - a * prev) * (m == n - 1 ? invlast : __ldg(inv + m));
+      E(m) = prev;
     }
     T x = prev;
-    Uc[base + (long long)(n - 1) * stride] += x;
     for (int m = n - 2; m >= 0; --m) {
-      const long long id = base + (long long)m * stride;
-      x = R[id] - cp[m] * x;
-      Uc[id] += x;
+      x = E(m) - __ldg(cp + m) * x;
+      E(m) = x;
     }
     return;
   }
-  const T gs = g.ybc == 0 ? (T)-1 : (T)1;
-  const T bf = (T)1 + (T)2 * off;
-  T cprev = (T)0, dprev = (T)0;
-  for (int m = 0; m < n; ++m) {
-    const long long id = base + (long long)m * stride;
-    T am, bm, cm;
-    if (is_forcing(flags32, fbase + (long long)m * stride, c)) { am = (T)0; bm = (T)1; cm = (T)0; }
-    else {
-      am = m == 0 ? (T)0 : a;
-      cm = m == n - 1 ? (T)0 : a;
-      bm = bf;
-      if (c != 1 && (m == 0 || m == n - 1)) bm -= gs * off;
+  // W segments start at a wall (tangential components), R segments after
+  // an identity row; a tangential last row carries the wall diagonal
+  T prev = (T)0;
+  int m = 0;
+  bool segW = tang;
+  for (int j = 0; j < n; ++j) {
+    if (forcing(j)) { prev = E(j); m = 0; segW = false; continue; }
+    T iv;
+    if (!tang) iv = __ldg(tb.vinvR + m);
+    else if (j == n - 1) iv = segW ? __ldg(tb.yinvLW + m) : __ldg(tb.yinvLR + m);
+    else iv = segW ? __ldg(tb.yinvW + m) : __ldg(tb.yinvR + m);
+    prev = (E(j) - a * prev) * iv;
+    E(j) = prev;
+    ++m;
+  }
+  T x = prev;
+  int mq = -1;
+  bool qW = false;
+  auto seg_of = [&](int q, int& mpos, bool& w) {
+    int lo = q - 1;
+    while (lo >= 0 && !forcing(lo)) --lo;
+    mpos = q - lo - 1;
+    w = tang && lo < 0;
+  };
+  if (!forcing(n - 1)) seg_of(n - 1, mq, qW);
+  for (int j = n - 2; j >= 0; --j) {
+    if (forcing(j)) { x = E(j); mq = -1; continue; }
+    if (mq < 0) seg_of(j, mq, qW);
+    else --mq;
+    const T cpj = !tang ? __ldg(tb.vcpR + mq) : (qW ? __ldg(tb.ycpW + mq) : __ldg(tb.ycpR + mq));
+    x = E(j) - cpj * x;
+    E(j) = x;
+  }
+}
+
+// Asynchronous global -> shared copies (cp.async): every load of a tile is
+// issued up front and waited for once, instead of one memory latency per
+// element.
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(BYTES));
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// x-sweep: a block holds W complete x-lines (rows (j, k) of component
+// blockIdx.y) in shared memory, loaded and stored row by row (coalesced);
+// thread t solves line t.  Tile [W][nx+1] of T, then [W][nx] flag bytes.
+template <typename T>
+__global__ void __launch_bounds__(64) k_sweep_x(Geo g, Fields<T> f, const unsigned* __restrict__ flags32,
+                                                SweepTables<T> tb, const int* __restrict__ lfirst) {
+  extern __shared__ unsigned char smem_raw[];
+  const int W = blockDim.x, t = threadIdx.x;
+  const int c = blockIdx.y;
+  const int n = g.nx, ld = n + 1;
+  const int j0 = c == 1 ? 1 : 0, nj = c == 1 ? g.ny - 1 : g.ny;
+  const int nlines = nj * g.nz;
+  const int l0 = blockIdx.x * W;
+  T* tile = reinterpret_cast<T*>(smem_raw);
+  unsigned char* fl = reinterpret_cast<unsigned char*>(tile + (size_t)W * ld);
+  T* __restrict__ R = f.R[c];
+  const unsigned char* fbytes = reinterpret_cast<const unsigned char*>(flags32);
+  const bool words = (n & 3) == 0;   // flag bytes of a row copied four at a time
+  for (int r = 0; r < W; ++r) {
+    const int l = l0 + r;
+    if (l >= nlines) break;
+    const int j = j0 + l % nj, k = l / nj;
+    const long long base = fidx(g, c, 0, j, k), fb = cidx(g, 0, j, k);
+    for (int i = t; i < n; i += W) cp_async<sizeof(T)>(tile + r * ld + i, R + base + i);
+    if (words) {
+      for (int q = t; q < n / 4; q += W) cp_async<4>(fl + r * n + 4 * q, fbytes + fb + 4 * q);
+    } else {
+      for (int i = t; i < n; i += W) fl[r * n + i] = fbytes[fb + i];
     }
-    const T den = bm - am * cprev;
-    cprev = cm / den;
-    dprev = (R[id] - am * dprev) / den;
-    S[id] = cprev;
-    R[id] = dprev;
   }
-  T x = dprev;
-  Uc[base + (long long)(n - 1) * stride] += x;
-  for (int m = n - 2; m >= 0; --m) {
-    const long long id = base + (long long)m * stride;
-    x = R[id] - S[id] * x;
-    Uc[id] += x;
+  cp_async_wait_all();
+  __syncthreads();
+  const int l = l0 + t;
+  if (l < nlines) {
+    const int j = j0 + l % nj, k = l / nj;
+    T* row = tile + t * ld;
+    const unsigned char* frow = fl + t * n;
+    solve_periodic<T>(n, c, lfirst[line_x(g, c, j, k)], 0, -tb.off[0], tb, [&](int m) -> T& { return row[m]; },
+                      [&](int m) { return (int)frow[m]; });
   }
+  __syncthreads();
+  for (int r = 0; r < W; ++r) {
+    const int l2 = l0 + r;
+    if (l2 >= nlines) break;
+    const int j = j0 + l2 % nj, k = l2 / nj;
+    const long long base = fidx(g, c, 0, j, k);
+    for (int i = t; i < n; i += W) R[base + i] = tile[r * ld + i];
+  }
+}
+
+// x-sweep, one warp per line: lane l holds rows [l K, l K + K) of the line
+// (K = ceil(nx/32)) in registers, loaded coalesced.  Both Thomas passes are
+// affine recurrences y_m = A_m y_{m-1} + B_m (forward) and y_m = A_m y_{m+1}
+// + B_m (backward); each lane composes the maps of its rows, a warp shuffle
+// scan composes the lanes, and each lane then finishes its rows.  Identity
+// rows (forcing nodes) are the maps (0, d).  Used for the FP32 bulk type.
+template <typename T>
+struct AffMap {
+  T A, B;
+};
+// the map of `later` applied after `earlier`
+template <typename T>
+__device__ __forceinline__ AffMap<T> aff_then(AffMap<T> earlier, AffMap<T> later) {
+  return AffMap<T>{later.A * earlier.A, later.A * earlier.B + later.B};
+}
+// exclusive scan of lane maps in increasing lane order (lane 0: identity)
+template <typename T>
+__device__ __forceinline__ AffMap<T> scan_up_excl(AffMap<T> m, int lane) {
+  for (int o = 1; o < 32; o <<= 1) {
+    const T a = __shfl_up_sync(0xFFFFFFFFu, m.A, o), b = __shfl_up_sync(0xFFFFFFFFu, m.B, o);
+    if (lane >= o) m = aff_then(AffMap<T>{a, b}, m);
+  }
+  const T a = __shfl_up_sync(0xFFFFFFFFu, m.A, 1), b = __shfl_up_sync(0xFFFFFFFFu, m.B, 1);
+  return lane == 0 ? AffMap<T>{(T)1, (T)0} : AffMap<T>{a, b};
+}
+// exclusive scan in decreasing lane order (lane 31: identity)
+template <typename T>
+__device__ __forceinline__ AffMap<T> scan_down_excl(AffMap<T> m, int lane) {
+  for (int o = 1; o < 32; o <<= 1) {
+    const T a = __shfl_down_sync(0xFFFFFFFFu, m.A, o), b = __shfl_down_sync(0xFFFFFFFFu, m.B, o);
+    if (lane + o < 32) m = aff_then(AffMap<T>{a, b}, m);
+  }
+  const T a = __shfl_down_sync(0xFFFFFFFFu, m.A, 1), b = __shfl_down_sync(0xFFFFFFFFu, m.B, 1);
+  return lane == 31 ? AffMap<T>{(T)1, (T)0} : AffMap<T>{a, b};
+}
+
+template <typename T, int K>
+__global__ void __launch_bounds__(256) k_sweep_x_warp(Geo g, Fields<T> f, const unsigned* __restrict__ flags32,
+                                                      SweepTables<T> tb, const int* __restrict__ lfirst) {
+  const int lane = threadIdx.x & 31;
+  const int c = blockIdx.y;
+  const int n = g.nx;
+  const int j0 = c == 1 ? 1 : 0, nj = c == 1 ? g.ny - 1 : g.ny;
+  const int l = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (l >= nj * g.nz) return;
+  const int j = j0 + l % nj, k = l / nj;
+  const long long base = fidx(g, c, 0, j, k);
+  T* __restrict__ R = f.R[c];
+  const T a = -tb.off[0];
+  const int f0 = lfirst[line_x(g, c, j, k)];
+  const int q0 = lane * K;
+  T v[K];
+  if (f0 >= n) {
+    // ------------- no forcing node: Sherman-Morrison on the periodic line
+    const T* __restrict__ inv = tb.inv[0];
+    const T* __restrict__ cp = tb.cp[0];
+    const T* __restrict__ zv = tb.zv[0];
+    const T* __restrict__ g0 = tb.g0[0];
+#pragma unroll
+    for (int u = 0; u < K; ++u) v[u] = q0 + u < n ? R[base + q0 + u] : (T)0;
+    T acc = (T)0;
+    AffMap<T> mp{(T)1, (T)0};
+#pragma unroll
+    for (int u = 0; u < K; ++u)
+      if (q0 + u < n) {
+        const T iv = __ldg(inv + q0 + u);
+        acc += __ldg(g0 + q0 + u) * v[u];
+        mp = aff_then(mp, AffMap<T>{-a * iv, v[u] * iv});
+      }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+    const AffMap<T> pre = scan_up_excl(mp, lane);
+    T y = pre.B;   // y'_{q0 - 1}
+#pragma unroll
+    for (int u = 0; u < K; ++u)
+      if (q0 + u < n) {
+        y = (v[u] - a * y) * __ldg(inv + q0 + u);
+        v[u] = y;
+      }
+    const T ylast = __shfl_sync(0xFFFFFFFFu, y, (n - 1) / K);
+    const T fact = (acc + (a / tb.gam[0]) * ylast) / tb.smden[0];
+    // backward: y_m = -cp_m y_{m+1} + y'_m, row n-1: y = y'_{n-1}
+    mp = AffMap<T>{(T)1, (T)0};
+#pragma unroll
+    for (int u = K - 1; u >= 0; --u)
+      if (q0 + u < n) {
+        const AffMap<T> rm = (q0 + u == n - 1) ? AffMap<T>{(T)0, v[u]} : AffMap<T>{-__ldg(cp + q0 + u), v[u]};
+        mp = aff_then(mp, rm);
+      }
+    const AffMap<T> suf = scan_down_excl(mp, lane);
+    T yn = suf.B;  // y_{q0 + K}
+#pragma unroll
+    for (int u = K - 1; u >= 0; --u)
+      if (q0 + u < n) {
+        yn = (q0 + u == n - 1) ? v[u] : v[u] - __ldg(cp + q0 + u) * yn;
+        R[base + q0 + u] = yn - fact * __ldg(zv + q0 + u);
+      }
+    return;
+  }
+  // ------------- forcing rows: the line rotated to start at f0 (identity)
+  const T* __restrict__ invR = tb.invR[0];
+  const T* __restrict__ cpR = tb.cpR[0];
+  const long long fb = cidx(g, 0, j, k);
+  const unsigned char* fbytes = reinterpret_cast<const unsigned char*>(flags32);
+  int rr[K];
+  bool idn[K];
+#pragma unroll
+  for (int u = 0; u < K; ++u) {
+    const int q = q0 + u;
+    int r = f0 + q;
+    if (r >= n) r -= n;
+    rr[u] = r;
+    if (q < n) {
+      v[u] = R[base + r];
+      idn[u] = (fbytes[fb + r] >> c) & 1;
+    } else {
+      v[u] = (T)0;
+      idn[u] = true;
+    }
+  }
+  const T x0 = __shfl_sync(0xFFFFFFFFu, v[0], 0);   // row q = 0 is an identity row
+  // segment positions: distance from the last identity row before each row
+  int lastid = -1;
+#pragma unroll
+  for (int u = 0; u < K; ++u)
+    if (q0 + u < n && idn[u]) lastid = q0 + u;
+  int before = lastid;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t2 = __shfl_up_sync(0xFFFFFFFFu, before, o);
+    if (lane >= o && t2 > before) before = t2;
+  }
+  before = __shfl_up_sync(0xFFFFFFFFu, before, 1);
+  if (lane == 0) before = -1;
+  int mseg[K];
+  {
+    int last = before;
+#pragma unroll
+    for (int u = 0; u < K; ++u) {
+      const int q = q0 + u;
+      mseg[u] = q - last - 1;
+      if (q < n && idn[u]) last = q;
+    }
+  }
+  AffMap<T> mp{(T)1, (T)0};
+#pragma unroll
+  for (int u = 0; u < K; ++u) {
+    const int q = q0 + u;
+    if (q >= n) break;
+    if (idn[u]) { mp = AffMap<T>{(T)0, v[u]}; continue; }
+    const T iv = __ldg(invR + mseg[u]);
+    const T dq = (q == n - 1) ? v[u] - a * x0 : v[u];
+    mp = aff_then(mp, AffMap<T>{-a * iv, dq * iv});
+  }
+  const AffMap<T> pre = scan_up_excl(mp, lane);
+  T y = pre.B;
+#pragma unroll
+  for (int u = 0; u < K; ++u) {
+    const int q = q0 + u;
+    if (q >= n) break;
+    if (idn[u]) { y = v[u]; continue; }
+    const T dq = (q == n - 1) ? v[u] - a * x0 : v[u];
+    y = (dq - a * y) * __ldg(invR + mseg[u]);
+    v[u] = y;
+  }
+  // backward: fluid rows y_q = -cp_q y_{q+1} + y'_q; identity rows and the
+  // last row keep their value
+  mp = AffMap<T>{(T)1, (T)0};
+#pragma unroll
+  for (int u = K - 1; u >= 0; --u) {
+    const int q = q0 + u;
+    if (q >= n) continue;
+    const bool keep = idn[u] || q == n - 1;
+    mp = aff_then(mp, keep ? AffMap<T>{(T)0, v[u]} : AffMap<T>{-__ldg(cpR + mseg[u]), v[u]});
+  }
+  const AffMap<T> suf = scan_down_excl(mp, lane);
+  T yn = suf.B;
+#pragma unroll
+  for (int u = K - 1; u >= 0; --u) {
+    const int q = q0 + u;
+    if (q >= n) continue;
+    const bool keep = idn[u] || q == n - 1;
+    yn = keep ? v[u] : v[u] - __ldg(cpR + mseg[u]) * yn;
+    if (!idn[u]) R[base + rr[u]] = yn;
+  }
+}
+
+// z- and y-sweeps: a block holds the lines of W consecutive i (one plane
+// position each) for all n rows, tile [n][W] (row m of line t at m*W + t);
+// rows are loaded and stored coalesced.  dir 2: z-lines at fixed j
+// (blockIdx.z); dir 1: y-lines at fixed k (blockIdx.z), and the solution du
+// is added to the state (uhat = u^s + du) on the way out.
+template <typename T>
+__global__ void __launch_bounds__(64) k_sweep_zy(Geo g, Fields<T> f, const unsigned* __restrict__ flags32,
+                                                 SweepTables<T> tb, const int* __restrict__ lfirst, int dir) {
+  extern __shared__ unsigned char smem_raw[];
+  const int W = blockDim.x, t = threadIdx.x;
+  const int c = blockIdx.y;
+  const int i0 = blockIdx.x * W;
+  const int pl = planes(g, c);
+  int n;
+  long long base, stride, fbase, fstride;
+  if (dir == 2) {
+    if (c == 1 && (int)blockIdx.z >= g.ny - 1) return;   // v has ny-1 interior planes
+    const int j = (c == 1 ? 1 : 0) + blockIdx.z;     // fixed j of these z-lines
+    n = g.nz;
+    base = fidx(g, c, i0, j, 0);
+    stride = (long long)pl * g.nx;
+    fbase = cidx(g, i0, j, 0);
+    fstride = (long long)g.ny * g.nx;
+  } else {
+    const int k = blockIdx.z;
+    const int jj0 = c == 1 ? 1 : 0;
+    n = c == 1 ? g.ny - 1 : g.ny;
+    base = fidx(g, c, i0, jj0, k);
+    stride = g.nx;
+    fbase = cidx(g, i0, jj0, k);
+    fstride = g.nx;
+  }
+  const int w = min(W, g.nx - i0);
+  T* tile = reinterpret_cast<T*>(smem_raw);
+  T* ust = tile + (size_t)n * W;                        // y-sweep: the state u^s of the same lines
+  unsigned char* fl = reinterpret_cast<unsigned char*>(tile + (size_t)(dir == 1 ? 2 : 1) * n * W);
+  T* __restrict__ R = f.R[c];
+  T* __restrict__ Uc = comp_ptr(f, c);
+  const unsigned char* fbytes = reinterpret_cast<const unsigned char*>(flags32);
+  const bool words = (w & 3) == 0 && (fstride & 3) == 0 && (fbase & 3) == 0;
+  if (t < w) {
+    for (int m = 0; m < n; ++m) {
+      cp_async<sizeof(T)>(tile + m * W + t, R + base + m * stride + t);
+      if (dir == 1) cp_async<sizeof(T)>(ust + m * W + t, Uc + base + m * stride + t);
+    }
+  }
+  if (words) {
+    for (int e = t; e < n * (w / 4); e += W) {
+      const int m = e / (w / 4), q = e - m * (w / 4);
+      cp_async<4>(fl + m * W + 4 * q, fbytes + fbase + m * fstride + 4 * q);
+    }
+  } else if (t < w) {
+    for (int m = 0; m < n; ++m) fl[m * W + t] = fbytes[fbase + m * fstride + t];
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  if (t < w) {
+    const int i = i0 + t;
+    auto E = [&](int m) -> T& { return tile[m * W + t]; };
+    auto F = [&](int m) { return (int)fl[m * W + t]; };
+    if (dir == 2) {
+      const int j = (c == 1 ? 1 : 0) + blockIdx.z;
+      solve_periodic<T>(n, c, lfirst[line_z(g, c, i, j)], 1, -tb.off[2], tb, E, F);
+      for (int m = 0; m < n; ++m) R[base + m * stride + t] = tile[m * W + t];
+    } else {
+      const int k = blockIdx.z;
+      solve_wall<T>(n, c, lfirst[line_y(g, c, i, k)] < g.ny, -tb.off[1], tb, E, F);
+      if (f.lo[c]) {
+        // velocity state as a (hi, lo) pair: add du without rounding it away
+        T* __restrict__ Lc = f.lo[c];
+        for (int m = 0; m < n; ++m) {
+          const long long id = base + m * stride + t;
+          float hi = (float)ust[m * W + t], lo = (float)Lc[id];
+          ff_add(hi, lo, (float)tile[m * W + t]);
+          Uc[id] = (T)hi;
+          Lc[id] = (T)lo;
+        }
+      } else {
+        for (int m = 0; m < n; ++m) Uc[base + m * stride + t] = ust[m * W + t] + tile[m * W + t];
+      }
+    }
+  }
+}
+
+template <typename T>
+static size_t sweep_smem(int W, int n, int ld, int tiles = 1) {
+  return (size_t)tiles * W * ld * sizeof(T) + (size_t)W * n;
+}
+
+// lines per block: the largest of 64, 32, 16 whose tile fits 160 KB
+template <typename T>
+static int sweep_width(int n, int tiles = 1) {
+  for (int W = 64; W > 16; W /= 2)
+    if (sweep_smem<T>(W, n, n + 1, tiles) <= 160 * 1024) return W;
+  return 16;
 }
 
 template <typename T>
 void launch_sweeps(const Geo& g, const Fields<T>& f, const TagBuffers& b, const SweepTables<T>& tb,
                    cudaStream_t st) {
-  const long long lx = (long long)g.ny * g.nz, lz = (long long)g.ny * g.nx, ly = (long long)g.nx * g.nz;
   stage_mark(st, ST_SWEEP_X);
-  k_sweep_periodic<T><<<dim3((unsigned)((lx + 127) / 128), 3), 128, 0, st>>>(g, f, b.flags32, tb, 0);
+  if (sizeof(T) == 4 && g.nx <= 1024) {
+    const int lines = g.ny * g.nz;   // upper bound over components
+    const dim3 grid((lines + 7) / 8, 3);
+    const int K = (g.nx + 31) / 32;
+    if (K <= 1) k_sweep_x_warp<T, 1><<<grid, 256, 0, st>>>(g, f, b.flags32, tb, b.lines.x);
+    else if (K <= 2) k_sweep_x_warp<T, 2><<<grid, 256, 0, st>>>(g, f, b.flags32, tb, b.lines.x);
+    else if (K <= 3) k_sweep_x_warp<T, 3><<<grid, 256, 0, st>>>(g, f, b.flags32, tb, b.lines.x);
+    else if (K <= 4) k_sweep_x_warp<T, 4><<<grid, 256, 0, st>>>(g, f, b.flags32, tb, b.lines.x);
+    else if (K <= 8) k_sweep_x_warp<T, 8><<<grid, 256, 0, st>>>(g, f, b.flags32, tb, b.lines.x);
+    else if (K <= 16) k_sweep_x_warp<T, 16><<<grid, 256, 0, st>>>(g, f, b.flags32, tb, b.lines.x);
+    else k_sweep_x_warp<T, 32><<<grid, 256, 0, st>>>(g, f, b.flags32, tb, b.lines.x);
+  } else {
+    const int W = sweep_width<T>(g.nx);
+    const int nlines = g.ny * g.nz;     // upper bound over components (v has ny-1 rows of lines)
+    k_sweep_x<T><<<dim3((nlines + W - 1) / W, 3), W, sweep_smem<T>(W, g.nx, g.nx + 1), st>>>(g, f, b.flags32, tb,
+                                                                                          b.lines.x);
+  }
   stage_mark(st, ST_SWEEP_Z);
-  k_sweep_periodic<T><<<dim3((unsigned)((lz + 127) / 128), 3), 128, 0, st>>>(g, f, b.flags32, tb, 2);
+  {
+    const int W = sweep_width<T>(g.nz);
+    k_sweep_zy<T><<<dim3((g.nx + W - 1) / W, 3, g.ny), W, sweep_smem<T>(W, g.nz, g.nz), st>>>(g, f, b.flags32, tb,
+                                                                                          b.lines.z, 2);
+  }
   stage_mark(st, ST_SWEEP_Y);
-  k_sweep_y<T><<<dim3((unsigned)((ly + 127) / 128), 3), 128, 0, st>>>(g, f, b.flags32, tb);
+  {
+    const int W = sweep_width<T>(g.ny, 2);
+    k_sweep_zy<T><<<dim3((g.nx + W - 1) / W, 3, g.nz), W, sweep_smem<T>(W, g.ny, g.ny, 2), st>>>(g, f, b.flags32, tb,
+                                                                                             b.lines.y, 1);
+  }
+}
+
+template <typename T>
+static void sweep_attrs() {
+  cudaFuncSetAttribute(k_sweep_x<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_sweep_zy<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
+void init_sweep_attributes() {
+  sweep_attrs<double>();
+  sweep_attrs<float>();
 }
 
 // ---------------------------------------------------------------------------
@@ -443,7 +823,7 @@ __global__ void __launch_bounds__(SLIP_THREADS) k_slip_partial(Geo g, Surf s, Fi
     NodeGeom ng;
     forcing_geometry(g, s, fn.key, fn.tri, ng);
     const T* fc = comp_ptr(f, c);
-    const double ux = (double)fc[fn.key & KEY_MASK];
+    const double ux = (double)fc[fn.key & KEY_MASK] + (f.lo[c] ? (double)f.lo[c][fn.key & KEY_MASK] : 0.0);
     double uw = ux;
     if (ng.n2 != 0.0) {
       const double nl = sqrt(ng.n2);

@@ -16,11 +16,30 @@ int num_sms();
 // of each.  The order matches the stage names in runtime.cu.
 enum StageId {
   ST_TAG = 0, ST_FORCE, ST_RHS, ST_SWEEP_X, ST_SWEEP_Z, ST_SWEEP_Y, ST_QRED, ST_FFT_X_FWD, ST_FFT_Z_FWD,
-  ST_TRI_Y, ST_FFT_Z_INV, ST_FFT_X_INV, ST_PROJECT, ST_SLIP, ST_OTHER, ST_COUNT
+  ST_TRI_Y, ST_FFT_Z_INV, ST_FFT_X_INV, ST_PROJECT, ST_SLIP, ST_CORRECT, ST_OTHER, ST_COUNT
 };
 // Record the start of stage `id` on stream st when stage timing is active
 // on this thread (no-op otherwise, e.g. during graph capture).
 void stage_mark(cudaStream_t st, int id);
+
+// ---- per-line records of forcing nodes (filled by tagging, read by sweeps) -
+// x-lines are indexed (c, k, j), z-lines (c, j, i), y-lines (c, k, i); each
+// holds the smallest forcing index along the line, or a large value.
+struct LineInfo {
+  int* x;          // 3 * nz * (ny+1)
+  int* z;          // 3 * (ny+1) * nx
+  int* y;          // 3 * nz * nx
+  size_t bytes;    // of the three arrays together (x is their start)
+};
+__host__ __device__ inline long long line_x(const Geo& g, int c, long long j, long long k) {
+  return ((long long)c * g.nz + k) * (g.ny + 1) + j;
+}
+__host__ __device__ inline long long line_z(const Geo& g, int c, long long i, long long j) {
+  return ((long long)c * (g.ny + 1) + j) * g.nx + i;
+}
+__host__ __device__ inline long long line_y(const Geo& g, int c, long long i, long long k) {
+  return ((long long)c * g.nz + k) * g.nx + i;
+}
 
 // ---- tagging (tagging.cu) --------------------------------------------------
 struct TagBuffers {
@@ -32,28 +51,42 @@ struct TagBuffers {
   unsigned* blk;               // 4 counters per compaction block
   ForceNode* flist;            // forcing nodes, grouped by component, sorted by cell
   unsigned* blist;             // boundary cells, sorted
+  LineInfo lines;
 };
 void launch_tagging(const Geo& g, const Surf& s, const TagBuffers& b, DevState* ds, cudaStream_t st);
 int compaction_blocks(const Geo& g);
 
 // ---- tridiagonal coefficient tables (built on the host) -------------------
-// Fast path of the approximate-factorisation sweeps for lines without
-// forcing nodes: constant coefficients, so the Thomas recurrences are
-// tabulated once per (direction, beta).  Periodic lines use the
-// Sherman-Morrison form.
+// The factorised sweeps solve (1 - beta L_d) x = r per grid line.  Fluid rows
+// have constant coefficients, forcing nodes are identity rows, so every
+// pivot is a function of the row's distance m from the start of its segment
+// (the line start, or the row after an identity row): the Thomas recurrences
+// are tabulated once per (direction, beta) and no line divides.
 template <typename T>
 struct SweepTables {
-  // periodic directions x (0) and z (1)
-  const T* inv[2];   // 1 / pivot of the modified matrix, per row
-  const T* cp[2];    // c' of the modified matrix, per row
-  const T* zv[2];    // Sherman-Morrison correction vector
-  const T* g0[2];    // first row of the modified inverse
-  T smden[2];        // 1 + v.z
-  T gam[2];          // Sherman-Morrison gamma
-  // wall-normal direction y: tangential components (0) and v (1)
-  const T* yinv[2];
-  const T* ycp[2];
-  T off[3];          // beta / d^2 per direction x, y, z
+  // periodic x (0) and z (1), lines without forcing nodes: Sherman-Morrison
+  // form (modified tridiagonal matrix + one correction vector)
+  const T* inv[2];    // 1 / pivot of the modified matrix, per row
+  const T* cp[2];     // c' of the modified matrix, per row
+  const T* zv[2];     // correction vector
+  const T* g0[2];     // first row of the modified inverse (y_0 as a dot product)
+  T smden[2];         // 1 + v.z
+  T gam[2];           // Sherman-Morrison gamma
+  // periodic x (0) and z (1), lines with forcing nodes: segment recurrences
+  const T* invR[2];
+  const T* cpR[2];
+  // wall-normal, tangential components: segments from the wall (W) or after
+  // an identity row (R); LW / LR: pivot of a last (wall) row at position m
+  const T* yinvW;
+  const T* ycpW;
+  const T* yinvR;
+  const T* ycpR;
+  const T* yinvLW;
+  const T* yinvLR;
+  // wall-normal, v (Dirichlet walls): every segment is an R segment
+  const T* vinvR;
+  const T* vcpR;
+  T off[3];           // beta / d^2 per direction x, y, z
 };
 
 // ---- flow kernels (flow.cu) ------------------------------------------------
@@ -70,6 +103,9 @@ struct Fields {
   T* uf;        // IB values of the forcing nodes
   T* phi;       // pseudo-pressure
   void* spec;   // complex half-spectrum nz*ny*nkx
+  T* lo[3];     // low parts of the velocity state (mixed path), else null
+  T* phi2;      // pseudo-pressure of the correction solve (mixed path)
+  double idh[3][2];  // reciprocal spacings as (hi, lo) pairs, for the pair divergence
 };
 
 template <typename T>

@@ -66,7 +66,8 @@ __device__ void fft_pass(const typename Cplx<T>::type* src, typename Cplx<T>::ty
   using C = typename Cplx<T>::type;
   const int nb = n / R;
   const int scale = n / (Ns * R);
-  for (int t = threadIdx.x; t < lines * nb; t += blockDim.x) {
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
+  for (int t = tid; t < lines * nb; t += nth) {
     const int line = t / nb, j = t - line * nb;
     const C* s = src + line * n;
     C* d = dst + line * n;
@@ -176,7 +177,11 @@ __global__ void k_q_final(Geo g, const double* partial, DevState* ds, int s, int
   const double A = sum * dV;
   const double VF = (double)(g.ncell - (long long)ds->nbound) * dV;
   ds->sum_a[s] = A;
-  ds->qf[s] = (use_q && VF > 0.0) ? -A / VF : 0.0;
+  const double qf = (use_q && VF > 0.0) ? -A / VF : 0.0;
+  ds->qf[s] = qf;
+  const float qh = (float)qf;
+  ds->qf_hi[s] = qh;
+  ds->qf_lo[s] = (float)(qf - (double)qh);
   if (!isfinite(A)) atomicOr(&ds->err, ERR_NONFINITE);
 }
 
@@ -186,42 +191,84 @@ __global__ void k_q_final(Geo g, const double* partial, DevState* ds, int s, int
 // 1/(nx nz) so the inverse transforms need no normalisation.  Two real rows
 // form one complex line; the two half-spectra are separated on output.
 // ---------------------------------------------------------------------------
+// (H[a] + L[a]) - (H[b] + L[b]) times (ih + il), as a big part and a small
+// correction whose sum carries the product to ~FP32^2 relative accuracy
+template <typename T>
+__device__ __forceinline__ void pair_diff(const T* H, const T* L, long long a, long long b, float ih, float il,
+                                          float& big, float& small) {
+  float s, e, p, pe;
+  two_sum((float)H[a], -(float)H[b], s, e);
+  e += (float)L[a] - (float)L[b];
+  two_prod(s, ih, p, pe);
+  big = p;
+  small = pe + e * ih + s * il;
+}
+
+// mode 0: rhs = (D uhat - q)/(alpha dt) from the (hi part of the) state;
+// mode 1: rhs of the correction solve, (D u' - q_F)/(alpha dt) on fluid
+// cells from the projected state held as (hi, lo) pairs, in pair arithmetic
 template <typename T>
 __global__ void k_fft_x_fwd(Geo g, Fields<T> f, const unsigned* __restrict__ flags32, const T* __restrict__ tw,
                             FftPlan plan, int lines_per_block, const DevState* ds, int s, int use_q,
-                            double scale) {
+                            double scale, int mode) {
   using C = typename Cplx<T>::type;
   extern __shared__ unsigned char smem_raw[];
   C* bufa = reinterpret_cast<C*>(smem_raw);
   C* bufb = bufa + lines_per_block * g.nx;
-  const int n = g.nx;
-  const long long rows = (long long)g.ny * g.nz;
-  const long long line0 = (long long)blockIdx.x * lines_per_block;
-  const double qf = use_q ? ds->qf[s] : 0.0;
-  // load: rows 2 l and 2 l + 1 of line l
-  for (int t = threadIdx.x; t < lines_per_block * n; t += blockDim.x) {
-    const int l = t / n, i = t - l * n;
-    C z;
-    z.x = (T)0;
-    z.y = (T)0;
-    for (int h = 0; h < 2; ++h) {
-      const long long row = 2 * (line0 + l) + h;
-      if (row >= rows) continue;
-      const long long j = row % g.ny, k = row / g.ny;
-      const long long cell = cidx(g, i, j, k);
-      const unsigned fl = (flags32[cell >> 2] >> (8 * (cell & 3))) & 0xFFu;
-      double r = 0.0;
-      if (!(use_q && (fl & FLAG_B))) r = (div_at<T>(g, f.u, f.v, f.w, i, j, k) - qf) * scale;
-      if (h == 0) z.x = (T)r;
-      else z.y = (T)r;
+  const int n = g.nx, ny = g.ny;
+  const int rows = g.ny * g.nz;
+  const int line0 = blockIdx.x * lines_per_block;
+  const T qf = use_q ? (T)ds->qf[s] : (T)0;
+  const T sc = (T)scale, idx = (T)g.idx, idy = (T)g.idy, idz = (T)g.idz;
+  const long long pu = (long long)ny * n, pv = (long long)(ny + 1) * n;
+  // load: rows 2 l and 2 l + 1 of line l; divergence in the bulk type
+  for (int l = threadIdx.y; l < lines_per_block; l += blockDim.y) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      C z;
+      z.x = (T)0;
+      z.y = (T)0;
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        const int row = 2 * (line0 + l) + hh;
+        if (row >= rows) continue;
+        const int j = row % ny, k = row / ny;
+        const int ip = i + 1 == n ? 0 : i + 1, kp = k + 1 == g.nz ? 0 : k + 1;
+        const long long r0 = (long long)k * pu + (long long)j * n;
+        const long long cell = r0 + i;
+        const unsigned fl = (flags32[cell >> 2] >> (8 * (cell & 3))) & 0xFFu;
+        T r = (T)0;
+        if (mode == 1) {
+          if (!(use_q && (fl & FLAG_B))) {
+            const long long v0 = (long long)k * pv + (long long)j * n + i;
+            const long long wk = (long long)kp * pu + (long long)j * n + i;
+            float bx, sx, by, sy, bz, sz, a1, e1, a2, e2, a3, e3;
+            pair_diff(f.u, f.lo[0], r0 + ip, cell, (float)f.idh[0][0], (float)f.idh[0][1], bx, sx);
+            pair_diff(f.v, f.lo[1], v0 + n, v0, (float)f.idh[1][0], (float)f.idh[1][1], by, sy);
+            pair_diff(f.w, f.lo[2], wk, cell, (float)f.idh[2][0], (float)f.idh[2][1], bz, sz);
+            two_sum(bx, by, a1, e1);
+            two_sum(a1, bz, a2, e2);
+            const float qh = use_q ? ds->qf_hi[s] : 0.0f, ql = use_q ? ds->qf_lo[s] : 0.0f;
+            two_sum(a2, -qh, a3, e3);
+            r = (T)((a3 + (((e1 + e2) + e3) + ((sx + sy) + sz) - ql)) * (float)scale);
+          }
+        } else if (!(use_q && (fl & FLAG_B))) {
+          const long long v0 = (long long)k * pv + (long long)j * n + i;
+          const T du = (f.u[r0 + ip] - f.u[cell]) * idx;
+          const T dv = (f.v[v0 + n] - f.v[v0]) * idy;
+          const T dw = (f.w[(long long)kp * pu + (long long)j * n + i] - f.w[cell]) * idz;
+          r = (du + dv + dw - qf) * sc;
+        }
+        if (hh == 0) z.x = r;
+        else z.y = r;
+      }
+      bufa[l * n + i] = z;
     }
-    bufa[t] = z;
   }
   const int res = fft_lines<T, false>(bufa, bufb, lines_per_block, plan, reinterpret_cast<const C*>(tw));
   const C* out = res == 0 ? bufa : bufb;
   C* spec = reinterpret_cast<C*>(f.spec);
   const int nkx = g.nkx;
-  for (int t = threadIdx.x; t < lines_per_block * nkx; t += blockDim.x) {
+  for (int t = threadIdx.y * blockDim.x + threadIdx.x; t < lines_per_block * nkx; t += blockDim.x * blockDim.y) {
     const int l = t / nkx, kx = t - l * nkx;
     const C Z = out[l * n + kx];
     const C Zc = cconj(out[l * n + (kx == 0 ? 0 : n - kx)]);
@@ -239,7 +286,8 @@ __global__ void k_fft_x_fwd(Geo g, Fields<T> f, const unsigned* __restrict__ fla
 
 // inverse x transform: two half-spectra -> one complex line -> two real rows of phi
 template <typename T>
-__global__ void k_fft_x_inv(Geo g, Fields<T> f, const T* __restrict__ tw, FftPlan plan, int lines_per_block) {
+__global__ void k_fft_x_inv(Geo g, Fields<T> f, const T* __restrict__ tw, FftPlan plan, int lines_per_block,
+                            T* __restrict__ out_phi) {
   using C = typename Cplx<T>::type;
   extern __shared__ unsigned char smem_raw[];
   C* bufa = reinterpret_cast<C*>(smem_raw);
@@ -269,8 +317,8 @@ __global__ void k_fft_x_inv(Geo g, Fields<T> f, const T* __restrict__ tw, FftPla
   for (int t = threadIdx.x; t < lines_per_block * n; t += blockDim.x) {
     const int l = t / n, i = t - l * n;
     const long long ra = 2 * (line0 + l), rb = ra + 1;
-    if (ra < rows) f.phi[ra * n + i] = out[t].x;
-    if (rb < rows) f.phi[rb * n + i] = out[t].y;
+    if (ra < rows) out_phi[ra * n + i] = out[t].x;
+    if (rb < rows) out_phi[rb * n + i] = out[t].y;
   }
 }
 
@@ -311,55 +359,71 @@ __global__ void k_fft_z(Geo g, Fields<T> f, const T* __restrict__ tw, FftPlan pl
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(128) k_tri_y(Geo g, Fields<T> f, const double* __restrict__ cp,
-                                               const double* __restrict__ inv, double2* fwd) {
-  using C = typename Cplx<T>::type;
+                                               const double* __restrict__ inv, double* fwd) {
+  // one thread per real or imaginary part of a (kx, kz) system: the two
+  // share the pivots and are independent
   const int nkx = g.nkx;
   const long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (l >= (long long)nkx * g.nz) return;
-  const long long kx = l % nkx, kz = l / nkx;
+  if (l >= 2ll * nkx * g.nz) return;
+  const int part = (int)(l & 1);
+  const long long mode = l >> 1;
+  const long long kx = mode % nkx, kz = mode / nkx;
   const long long base = kz * (long long)g.ny * nkx + kx, stride = nkx;
-  C* spec = reinterpret_cast<C*>(f.spec);
+  T* __restrict__ sp = reinterpret_cast<T*>(f.spec);
   // forward values stay FP64: in place for the FP64 path, in an FP64 scratch
   // spectrum for the mixed path
-  double2* F = fwd ? fwd : reinterpret_cast<double2*>(f.spec);
+  double* __restrict__ F = fwd ? fwd : reinterpret_cast<double*>(f.spec);
   const double a = g.idy * g.idy;
   const bool singular = (kx == 0 && kz == 0);
-  double pr = 0.0, pi = 0.0;
-  for (int j = 0; j < g.ny; ++j) {
-    const long long id = base + (long long)j * stride;
-    const C zj = spec[id];
-    if (j == 0) {
-      pr = singular ? 0.0 : (double)zj.x * inv[id];
-      pi = singular ? 0.0 : (double)zj.y * inv[id];
-    } else {
-      pr = ((double)zj.x - a * pr) * inv[id];
-      pi = ((double)zj.y - a * pi) * inv[id];
-    }
-    F[id] = make_double2(pr, pi);
+  constexpr int B = 16;   // rows per batch: independent loads issued together
+  double pr = 0.0;
+  for (int j0 = 0; j0 < g.ny; j0 += B) {
+    double zb[B], ib[B];
+#pragma unroll
+    for (int u = 0; u < B; ++u)
+      if (j0 + u < g.ny) {
+        const long long id = base + (long long)(j0 + u) * stride;
+        zb[u] = (double)sp[2 * id + part];
+        ib[u] = inv[id];
+      }
+#pragma unroll
+    for (int u = 0; u < B; ++u)
+      if (j0 + u < g.ny) {
+        const int j = j0 + u;
+        pr = (j == 0) ? (singular ? 0.0 : zb[u] * ib[u]) : (zb[u] - a * pr) * ib[u];
+        F[2 * (base + (long long)j * stride) + part] = pr;
+      }
   }
-  double xr = pr, xi = pi;
-  double sr = xr, si = xi;
-  spec[base + (long long)(g.ny - 1) * stride].x = (T)xr;
-  spec[base + (long long)(g.ny - 1) * stride].y = (T)xi;
-  for (int j = g.ny - 2; j >= 0; --j) {
-    const long long id = base + (long long)j * stride;
-    const double2 zj = F[id];
-    xr = zj.x - cp[id] * xr;
-    xi = zj.y - cp[id] * xi;
-    if (singular) F[id] = make_double2(xr, xi);
-    spec[id].x = (T)xr;
-    spec[id].y = (T)xi;
-    sr += xr;
-    si += xi;
+  double xr = pr, sr = pr;
+  sp[2 * (base + (long long)(g.ny - 1) * stride) + part] = (T)xr;
+  for (int j1 = g.ny - 2; j1 >= 0; j1 -= B) {
+    double fb[B], cb[B];
+#pragma unroll
+    for (int u = 0; u < B; ++u)
+      if (j1 - u >= 0) {
+        const long long id = base + (long long)(j1 - u) * stride;
+        fb[u] = F[2 * id + part];
+        cb[u] = cp[id];
+      }
+#pragma unroll
+    for (int u = 0; u < B; ++u)
+      if (j1 - u >= 0) {
+        const long long id = base + (long long)(j1 - u) * stride;
+        xr = fb[u] - cb[u] * xr;
+        sp[2 * id + part] = (T)xr;
+        if (singular) {
+          F[2 * id + part] = xr;
+          sr += xr;
+        }
+      }
   }
   if (singular) {
     // zero-mean gauge, from the FP64 values
-    const double mr = sr / g.ny, mi = si / g.ny;
+    const double mr = sr / g.ny;
     for (int j = 0; j < g.ny; ++j) {
       const long long id = base + (long long)j * stride;
-      const double2 v = (j == g.ny - 1) ? make_double2(pr, pi) : F[id];
-      spec[id].x = (T)(v.x - mr);
-      spec[id].y = (T)(v.y - mi);
+      const double v = (j == g.ny - 1) ? pr : F[2 * id + part];
+      sp[2 * id + part] = (T)(v - mr);
     }
   }
 }
@@ -402,32 +466,64 @@ void launch_build_poisson_tables(const Geo& g, const double* lamx, const double*
 //   p <- p + phi - alpha dt / (2 Re) L_c phi,  L_c with Neumann walls
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) k_project(Geo g, Fields<T> f, double adt, double re) {
+struct ProjCoef {
+  T cx, cy, cz;          // alpha dt / d
+  T bx, by, bz;          // alpha dt / (2 Re d^2)
+};
+
+// mode 0: u <- uhat - alpha dt G phi and p <- p + phi - beta L_c phi;
+// mode 1: velocity only, state as (hi, lo) pairs (first solve of the mixed
+//         path);
+// mode 2: velocity with the correction phi2 (pairs), pressure with
+//         phi + phi2 (second solve of the mixed path)
+template <typename T>
+__global__ void __launch_bounds__(128) k_project(Geo g, Fields<T> f, ProjCoef<T> cf, int mode) {
   const int nx = g.nx, ny = g.ny, nz = g.nz;
   const long long pu = (long long)ny * nx, pv = (long long)(ny + 1) * nx;
-  const T cadt = (T)adt;
-  const T beta = (T)(adt / (2.0 * re));
-  const T idx = (T)g.idx, idy = (T)g.idy, idz = (T)g.idz;
-  const T* __restrict__ ph = f.phi;
-  for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < g.ncell;
-       cell += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(cell % nx);
-    const int j = (int)((cell / nx) % ny);
-    const int k = (int)(cell / pu);
-    const int ip = i + 1 == nx ? 0 : i + 1, im = i == 0 ? nx - 1 : i - 1;
-    const int kp = k + 1 == nz ? 0 : k + 1, km = k == 0 ? nz - 1 : k - 1;
-    const long long r0 = (long long)k * pu + (long long)j * nx;
-    const T c0 = ph[r0 + i];
-    const T pw = ph[r0 + im], pe = ph[r0 + ip];
-    const T pb = ph[(long long)km * pu + (long long)j * nx + i], pf = ph[(long long)kp * pu + (long long)j * nx + i];
-    const T up = j + 1 < ny ? ph[r0 + nx + i] - c0 : (T)0;
-    const T dn = j > 0 ? c0 - ph[r0 - nx + i] : (T)0;
-    f.u[r0 + i] -= cadt * (c0 - pw) * idx;
-    f.w[r0 + i] -= cadt * (c0 - pb) * idz;
-    if (j > 0) f.v[(long long)k * pv + (long long)j * nx + i] -= cadt * dn * idy;
-    const T lap = (pe - (T)2 * c0 + pw) * idx * idx + (up - dn) * idy * idy + (pf - (T)2 * c0 + pb) * idz * idz;
-    f.p[r0 + i] += c0 - beta * lap;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= nx || j >= ny) return;
+  const int ip = i + 1 == nx ? 0 : i + 1, im = i == 0 ? nx - 1 : i - 1;
+  const int kp = k + 1 == nz ? 0 : k + 1, km = k == 0 ? nz - 1 : k - 1;
+  const long long r0 = (long long)k * pu + (long long)j * nx;
+  const long long rkm = (long long)km * pu + (long long)j * nx, rkp = (long long)kp * pu + (long long)j * nx;
+  const T* __restrict__ ph = mode == 2 ? f.phi2 : f.phi;
+  const T c0 = ph[r0 + i];
+  const T gx = cf.cx * (c0 - ph[r0 + im]);
+  const T gz = cf.cz * (c0 - ph[rkm + i]);
+  const T gy = j > 0 ? cf.cy * (c0 - ph[r0 - nx + i]) : (T)0;
+  const long long vi = (long long)k * pv + (long long)j * nx + i;
+  if (mode == 0) {
+    f.u[r0 + i] -= gx;
+    f.w[r0 + i] -= gz;
+    if (j > 0) f.v[vi] -= gy;
+  } else {
+    float hi = (float)f.u[r0 + i], lo = (float)f.lo[0][r0 + i];
+    ff_add(hi, lo, -(float)gx);
+    f.u[r0 + i] = (T)hi;
+    f.lo[0][r0 + i] = (T)lo;
+    hi = (float)f.w[r0 + i];
+    lo = (float)f.lo[2][r0 + i];
+    ff_add(hi, lo, -(float)gz);
+    f.w[r0 + i] = (T)hi;
+    f.lo[2][r0 + i] = (T)lo;
+    if (j > 0) {
+      hi = (float)f.v[vi];
+      lo = (float)f.lo[1][vi];
+      ff_add(hi, lo, -(float)gy);
+      f.v[vi] = (T)hi;
+      f.lo[1][vi] = (T)lo;
+    }
   }
+  if (mode == 1) return;
+  // pressure update with the whole pseudo-pressure
+  auto PH = [&](long long id) { return mode == 2 ? f.phi[id] + f.phi2[id] : f.phi[id]; };
+  const T q0 = PH(r0 + i);
+  const T pw = PH(r0 + im), pe = PH(r0 + ip), pb = PH(rkm + i), pf = PH(rkp + i);
+  const T up = j + 1 < ny ? PH(r0 + nx + i) - q0 : (T)0;
+  const T dn = j > 0 ? q0 - PH(r0 - nx + i) : (T)0;
+  f.p[r0 + i] += q0 - (cf.bx * (pe - (T)2 * q0 + pw) + cf.by * (up - dn) + cf.bz * (pf - (T)2 * q0 + pb));
 }
 
 // ---------------------------------------------------------------------------
@@ -450,37 +546,52 @@ void launch_poisson(const Geo& g, const Fields<T>& f, const TagBuffers& b, const
   }
   const double scale = 1.0 / (sg.alp * dt * (double)g.nx * (double)g.nz);
   const FftPlan px = make_plan(g.nx), pz = make_plan(g.nz);
-  // x forward (fused divergence / q / rhs)
-  {
-    const int lpb = lines_for(g.nx);
-    const long long lines = ((long long)g.ny * g.nz + 1) / 2;
-    const size_t sm = 2ull * lpb * g.nx * sizeof(C);
-    stage_mark(st, ST_FFT_X_FWD);
-    k_fft_x_fwd<T><<<(unsigned)((lines + lpb - 1) / lpb), 256, sm, st>>>(g, f, b.flags32, tb.twx, px, lpb, ds, sg.s,
-                                                                        use_q, scale);
-  }
   const int cols = lines_for(g.nz) < 16 ? lines_for(g.nz) : 16;
   const int ntile = (g.nkx + cols - 1) / cols;
   const size_t smz = 2ull * cols * g.nz * sizeof(C);
-  stage_mark(st, ST_FFT_Z_FWD);
-  k_fft_z<T, false><<<g.ny * ntile, 256, smz, st>>>(g, f, tb.twz, pz, cols);
-  {
+  const int lpb = lines_for(g.nx);
+  const long long xlines = ((long long)g.ny * g.nz + 1) / 2;
+  const size_t smx = 2ull * lpb * g.nx * sizeof(C);
+  const int tx = g.nx < 128 ? g.nx : 128;
+  const long long tlines = (long long)g.nkx * g.nz;
+  double* fwd = sizeof(T) == sizeof(double) ? nullptr : reinterpret_cast<double*>(f.scr);
+  // the rest of one solve: z transform, wall-normal Thomas, inverse z and x
+  auto solve_rest = [&](T* out) {
+    stage_mark(st, ST_FFT_Z_FWD);
+    k_fft_z<T, false><<<g.ny * ntile, 256, smz, st>>>(g, f, tb.twz, pz, cols);
     stage_mark(st, ST_TRI_Y);
-    const long long lines = (long long)g.nkx * g.nz;
-    double2* fwd = sizeof(T) == sizeof(double) ? nullptr : reinterpret_cast<double2*>(f.scr);
-    k_tri_y<T><<<(unsigned)((lines + 127) / 128), 128, 0, st>>>(g, f, tb.cp, tb.inv, fwd);
-  }
-  stage_mark(st, ST_FFT_Z_INV);
-  k_fft_z<T, true><<<g.ny * ntile, 256, smz, st>>>(g, f, tb.twz, pz, cols);
-  {
+    k_tri_y<T><<<(unsigned)((2 * tlines + 127) / 128), 128, 0, st>>>(g, f, tb.cp, tb.inv, fwd);
+    stage_mark(st, ST_FFT_Z_INV);
+    k_fft_z<T, true><<<g.ny * ntile, 256, smz, st>>>(g, f, tb.twz, pz, cols);
     stage_mark(st, ST_FFT_X_INV);
-    const int lpb = lines_for(g.nx);
-    const long long lines = ((long long)g.ny * g.nz + 1) / 2;
-    const size_t sm = 2ull * lpb * g.nx * sizeof(C);
-    k_fft_x_inv<T><<<(unsigned)((lines + lpb - 1) / lpb), 256, sm, st>>>(g, f, tb.twx, px, lpb);
+    k_fft_x_inv<T><<<(unsigned)((xlines + lpb - 1) / lpb), 256, smx, st>>>(g, f, tb.twx, px, lpb, out);
+  };
+  const double adt = sg.alp * dt, bb = adt / (2.0 * re);
+  ProjCoef<T> cf;
+  cf.cx = (T)(adt * g.idx); cf.cy = (T)(adt * g.idy); cf.cz = (T)(adt * g.idz);
+  cf.bx = (T)(bb * g.idx * g.idx); cf.by = (T)(bb * g.idy * g.idy); cf.bz = (T)(bb * g.idz * g.idz);
+  const dim3 pgrid((g.nx + 31) / 32, (g.ny + 3) / 4, g.nz), pblk(32, 4);
+  stage_mark(st, ST_FFT_X_FWD);
+  k_fft_x_fwd<T><<<(unsigned)((xlines + lpb - 1) / lpb), dim3(tx, 256 / tx), smx, st>>>(g, f, b.flags32, tb.twx, px,
+                                                                                        lpb, ds, sg.s, use_q, scale, 0);
+  solve_rest(f.phi);
+  if (!f.lo[0]) {
+    stage_mark(st, ST_PROJECT);
+    k_project<T><<<pgrid, pblk, 0, st>>>(g, f, cf, 0);
+    return;
   }
+  // mixed path: project with the FP32 solve, then solve again for the
+  // residual divergence of the projected (hi, lo) state and correct
   stage_mark(st, ST_PROJECT);
-  k_project<T><<<(unsigned)((g.ncell + 255) / 256), 256, 0, st>>>(g, f, sg.alp * dt, re);
+  k_project<T><<<pgrid, pblk, 0, st>>>(g, f, cf, 1);
+  stage_mark(st, ST_CORRECT);
+  k_fft_x_fwd<T><<<(unsigned)((xlines + lpb - 1) / lpb), dim3(tx, 256 / tx), smx, st>>>(g, f, b.flags32, tb.twx, px,
+                                                                                        lpb, ds, sg.s, use_q, scale, 1);
+  k_fft_z<T, false><<<g.ny * ntile, 256, smz, st>>>(g, f, tb.twz, pz, cols);
+  k_tri_y<T><<<(unsigned)((2 * tlines + 127) / 128), 128, 0, st>>>(g, f, tb.cp, tb.inv, fwd);
+  k_fft_z<T, true><<<g.ny * ntile, 256, smz, st>>>(g, f, tb.twz, pz, cols);
+  k_fft_x_inv<T><<<(unsigned)((xlines + lpb - 1) / lpb), 256, smx, st>>>(g, f, tb.twx, px, lpb, f.phi2);
+  k_project<T><<<pgrid, pblk, 0, st>>>(g, f, cf, 2);
 }
 
 template <typename T>

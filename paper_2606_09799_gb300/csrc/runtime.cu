@@ -18,6 +18,7 @@
 namespace ibm {
 
 void init_kernel_attributes();
+void init_sweep_attributes();
 
 static int g_sms[64];
 
@@ -41,7 +42,7 @@ void stage_mark(cudaStream_t st, int id) {
 
 static const char* kStageNames[ST_COUNT] = {
     "tagging", "ib_force", "rhs", "sweep_x", "sweep_z", "sweep_y", "q_reduce", "fft_x_fwd", "fft_z_fwd",
-    "tri_y", "fft_z_inv", "fft_x_inv", "project", "slip", "other"};
+    "tri_y", "fft_z_inv", "fft_x_inv", "project", "slip", "correction", "other"};
 
 int num_sms() {
   int dev = 0;
@@ -120,6 +121,21 @@ __global__ void k_convert(const A* __restrict__ src, B* dst, long long n) {
     dst[i] = (B)src[i];
 }
 
+// FP64 value -> (hi, lo) FP32 pair and back
+__global__ void k_split(const double* __restrict__ src, float* hi, float* lo, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double x = src[i];
+    const float h = (float)x;
+    hi[i] = h;
+    lo[i] = (float)(x - (double)h);
+  }
+}
+
+__global__ void k_join(const float* __restrict__ hi, const float* __restrict__ lo, double* dst, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = (double)hi[i] + (double)lo[i];
+}
+
 __global__ void k_owner_out(const unsigned* __restrict__ own, int32_t* out, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     out[i] = (int32_t)own[i];
@@ -146,8 +162,9 @@ struct ibm_grid {
   size_t esize;           // bytes of the bulk type
   void* u; void* v; void* w; void* p;
   void* H[3]; void* R[3]; void* scr; void* uf; void* phi; void* spec;
+  void* lo[3]; void* phi2;   // mixed path: low parts of the velocity pairs, correction pseudo-pressure
   // tables
-  void* sweep_mem[12];
+  void* sweep_mem[24];
   double* pcp; double* pinv; double* lamx; double* lamz;
   void* twx; void* twz;
   double tbl_off[3];
@@ -247,8 +264,19 @@ static void* upload_vec(ibm_handle h, const std::vector<double>& v) {
   return d;
 }
 
+// Thomas recurrences of a segment of fluid rows with constant off-diagonal a
+// and diagonal b, whose first row has diagonal b0 (row after an identity
+// row: b0 = b; row at a wall: b0 = the wall diagonal)
+static void segment_tables(int n, double a, double b0, double b, std::vector<double>& inv, std::vector<double>& cp) {
+  std::vector<double> bb(n, b);
+  if (n > 0) bb[0] = b0;
+  thomas_tables(n, a, bb, inv, cp);
+}
+
 // periodic line of length n: Sherman-Morrison form of (1 - beta L) with
-// off = beta/d^2; modified matrix bb, correction vector z and first row g0
+// off = beta/d^2 (modified matrix, correction vector z, first row g0 of its
+// inverse) for lines without forcing nodes, and the segment recurrences for
+// lines with forcing nodes
 template <typename T>
 static bool build_periodic(ibm_handle h, int n, double off, int slot) {
   const double a = -off, b = 1.0 + 2.0 * off, gam = -b;
@@ -263,52 +291,63 @@ static bool build_periodic(ibm_handle h, int n, double off, int slot) {
   thomas_apply(n, a, inv, cp, z);
   g0[0] = 1.0;
   thomas_apply(n, a, inv, cp, g0);
+  std::vector<double> invR, cpR;
+  segment_tables(n, a, b, b, invR, cpR);
   h->tbl_gam[slot] = gam;
   h->tbl_smden[slot] = 1.0 + z[0] + a * z[n - 1] / gam;
-  h->sweep_mem[4 * slot + 0] = upload_vec<T>(h, inv);
-  h->sweep_mem[4 * slot + 1] = upload_vec<T>(h, cp);
-  h->sweep_mem[4 * slot + 2] = upload_vec<T>(h, z);
-  h->sweep_mem[4 * slot + 3] = upload_vec<T>(h, g0);
-  for (int q = 0; q < 4; ++q)
-    if (!h->sweep_mem[4 * slot + q]) return false;
+  const std::vector<double>* v[6] = {&inv, &cp, &z, &g0, &invR, &cpR};
+  for (int q = 0; q < 6; ++q) {
+    h->sweep_mem[6 * slot + q] = upload_vec<T>(h, *v[q]);
+    if (!h->sweep_mem[6 * slot + q]) return false;
+  }
   return true;
 }
 
-// wall-normal line: cls 0 = tangential components (ny rows, ghost rows at
-// both walls), cls 1 = v (ny-1 interior rows, Dirichlet walls)
+// wall-normal lines: tangential components (ny rows, wall diagonal in the
+// first and last rows) and v (ny-1 interior rows, Dirichlet walls)
 template <typename T>
-static bool build_wall(ibm_handle h, int cls, double off) {
+static bool build_wall(ibm_handle h, double off) {
   const int ny = h->g.ny;
-  const int n = cls == 0 ? ny : ny - 1;
-  const double a = -off;
-  std::vector<double> b(n, 1.0 + 2.0 * off);
-  if (cls == 0) {
-    const double gs = h->g.ybc == 0 ? -1.0 : 1.0;
-    b[0] -= gs * off;
-    b[n - 1] -= gs * off;
+  const double a = -off, b = 1.0 + 2.0 * off;
+  const double gs = h->g.ybc == 0 ? -1.0 : 1.0;
+  const double bw = b - gs * off;
+  std::vector<double> invW, cpW, invR, cpR, invLW(ny), invLR(ny), vinv, vcp;
+  segment_tables(ny, a, bw, b, invW, cpW);
+  segment_tables(ny, a, b, b, invR, cpR);
+  for (int m = 0; m < ny; ++m) {
+    invLW[m] = m == 0 ? 1.0 / bw : 1.0 / (bw - a * cpW[m - 1]);
+    invLR[m] = m == 0 ? 1.0 / bw : 1.0 / (bw - a * cpR[m - 1]);
   }
-  std::vector<double> inv, cp;
-  thomas_tables(n, a, b, inv, cp);
-  h->sweep_mem[8 + 2 * cls] = upload_vec<T>(h, inv);
-  h->sweep_mem[8 + 2 * cls + 1] = upload_vec<T>(h, cp);
-  return h->sweep_mem[8 + 2 * cls] && h->sweep_mem[8 + 2 * cls + 1];
+  segment_tables(ny - 1, a, b, b, vinv, vcp);
+  const std::vector<double>* v[8] = {&invW, &cpW, &invR, &cpR, &invLW, &invLR, &vinv, &vcp};
+  for (int q = 0; q < 8; ++q) {
+    h->sweep_mem[12 + q] = upload_vec<T>(h, *v[q]);
+    if (!h->sweep_mem[12 + q]) return false;
+  }
+  return true;
 }
 
 template <typename T>
 static SweepTables<T> sweep_tables(ibm_handle h) {
   SweepTables<T> t;
   for (int d = 0; d < 2; ++d) {
-    t.inv[d] = (const T*)h->sweep_mem[4 * d + 0];
-    t.cp[d] = (const T*)h->sweep_mem[4 * d + 1];
-    t.zv[d] = (const T*)h->sweep_mem[4 * d + 2];
-    t.g0[d] = (const T*)h->sweep_mem[4 * d + 3];
+    t.inv[d] = (const T*)h->sweep_mem[6 * d + 0];
+    t.cp[d] = (const T*)h->sweep_mem[6 * d + 1];
+    t.zv[d] = (const T*)h->sweep_mem[6 * d + 2];
+    t.g0[d] = (const T*)h->sweep_mem[6 * d + 3];
+    t.invR[d] = (const T*)h->sweep_mem[6 * d + 4];
+    t.cpR[d] = (const T*)h->sweep_mem[6 * d + 5];
     t.smden[d] = (T)h->tbl_smden[d];
     t.gam[d] = (T)h->tbl_gam[d];
   }
-  for (int c = 0; c < 2; ++c) {
-    t.yinv[c] = (const T*)h->sweep_mem[8 + 2 * c];
-    t.ycp[c] = (const T*)h->sweep_mem[8 + 2 * c + 1];
-  }
+  t.yinvW = (const T*)h->sweep_mem[12];
+  t.ycpW = (const T*)h->sweep_mem[13];
+  t.yinvR = (const T*)h->sweep_mem[14];
+  t.ycpR = (const T*)h->sweep_mem[15];
+  t.yinvLW = (const T*)h->sweep_mem[16];
+  t.yinvLR = (const T*)h->sweep_mem[17];
+  t.vinvR = (const T*)h->sweep_mem[18];
+  t.vcpR = (const T*)h->sweep_mem[19];
   for (int d = 0; d < 3; ++d) t.off[d] = (T)h->tbl_off[d];
   return t;
 }
@@ -329,6 +368,14 @@ static Fields<T> fields(ibm_handle h) {
   f.uf = (T*)h->uf;
   f.phi = (T*)h->phi;
   f.spec = h->spec;
+  for (int c = 0; c < 3; ++c) f.lo[c] = (T*)h->lo[c];
+  f.phi2 = (T*)h->phi2;
+  const double id[3] = {h->g.idx, h->g.idy, h->g.idz};
+  for (int d = 0; d < 3; ++d) {
+    const float hi = (float)id[d];
+    f.idh[d][0] = hi;
+    f.idh[d][1] = (float)(id[d] - (double)hi);
+  }
   return f;
 }
 
@@ -424,6 +471,7 @@ static ibm_status full_reset(ibm_handle h, cudaStream_t st) {
   CK(cudaMemsetAsync(h->tb.d2min, 0xFF, (size_t)nall * 8, st));
   CK(cudaMemsetAsync(h->tb.owner, 0xFF, (size_t)nall * 4, st));
   CK(cudaMemsetAsync(h->tb.flags32, 0, round16((size_t)(g.ncell + 3) / 4 * 4), st));
+  CK(cudaMemsetAsync(h->tb.lines.x, 0x7F, h->tb.lines.bytes, st));
   CK(cudaMemsetAsync(&h->ds->ncand, 0, sizeof(unsigned), st));
   h->need_full_reset = false;
   return launch_status(h, "reset");
@@ -490,7 +538,7 @@ ibm_status ibm_create_grid(const ibm_grid_desc* desc, void* stream, ibm_handle* 
   if (!(d.lx > 0 && d.ly > 0 && d.lz > 0 && d.re > 0 && d.dt > 0)) return IBM_ERR_ARG;
   if (d.scheme != IBM_RK2_CN && d.scheme != IBM_AB_CN) return IBM_ERR_ARG;
   if (d.ybc != IBM_NOSLIP && d.ybc != IBM_FREESLIP) return IBM_ERR_ARG;
-  if (d.precision != IBM_FP64 && d.precision != IBM_MIXED) return IBM_ERR_ARG;
+  if (d.precision != IBM_FP64 && d.precision != IBM_MIXED && d.precision != IBM_MIXED_FAST) return IBM_ERR_ARG;
   const long long nvf = (long long)d.nx * (d.ny + 1) * d.nz;
   if (nvf >= (1ll << 30)) return IBM_ERR_ARG;   // node indices are packed into 30 bits
   ibm_handle h = new (std::nothrow) ibm_grid();   // value-initialised: every scalar and pointer is zero
@@ -528,6 +576,7 @@ ibm_status ibm_create_grid(const ibm_grid_desc* desc, void* stream, ibm_handle* 
     return IBM_ERR_CUDA;
   }
   init_kernel_attributes();
+  init_sweep_attributes();
   const size_t es = h->esize;
   const long long ncell = g.ncell, nall = 2 * ncell + nvf;
   h->u = dalloc(h, ncell * es);
@@ -541,6 +590,14 @@ ibm_status ibm_create_grid(const ibm_grid_desc* desc, void* stream, ibm_handle* 
   h->scr = dalloc(h, nall * es);
   h->phi = dalloc(h, ncell * es);
   h->spec = dalloc(h, (size_t)g.nz * g.ny * g.nkx * 2 * es);
+  if (d.precision == IBM_MIXED) {
+    for (int c = 0; c < 3; ++c) {
+      h->lo[c] = dalloc(h, (c == 1 ? nvf : ncell) * es);
+      if (!h->lo[c]) { release_all(h); delete h; return IBM_ERR_OOM; }
+    }
+    h->phi2 = dalloc(h, ncell * es);
+    if (!h->phi2) { release_all(h); delete h; return IBM_ERR_OOM; }
+  }
   h->ds = (DevState*)dalloc(h, sizeof(DevState));
   h->partial = (double*)dalloc(h, 4096 * sizeof(double));
   h->tb.d2min = (unsigned long long*)dalloc(h, nall * 8);
@@ -548,8 +605,16 @@ ibm_status ibm_create_grid(const ibm_grid_desc* desc, void* stream, ibm_handle* 
   h->tb.flags32 = (unsigned*)dalloc(h, round16((size_t)(ncell + 3) / 4 * 4));
   h->tb.blk = (unsigned*)dalloc(h, (size_t)compaction_blocks(g) * 4 * sizeof(unsigned));
   h->bad = (unsigned*)dalloc(h, 16);
+  {
+    const size_t nxl = 3ull * g.nz * (g.ny + 1), nzl = 3ull * (g.ny + 1) * g.nx, nyl = 3ull * g.nz * g.nx;
+    h->tb.lines.bytes = (nxl + nzl + nyl) * sizeof(int);
+    h->tb.lines.x = (int*)dalloc(h, h->tb.lines.bytes);
+    h->tb.lines.z = h->tb.lines.x ? h->tb.lines.x + nxl : nullptr;
+    h->tb.lines.y = h->tb.lines.x ? h->tb.lines.z + nzl : nullptr;
+  }
   void* need[] = {h->u, h->v, h->w, h->p, h->H[0], h->H[1], h->H[2], h->R[0], h->R[1], h->R[2], h->scr,
-                  h->phi, h->spec, h->ds, h->partial, h->tb.d2min, h->tb.owner, h->tb.flags32, h->tb.blk, h->bad};
+                  h->phi, h->spec, h->ds, h->partial, h->tb.d2min, h->tb.owner, h->tb.flags32, h->tb.blk, h->bad,
+                  h->tb.lines.x};
   for (void* q : need)
     if (!q) {
       release_all(h);
@@ -571,10 +636,10 @@ ibm_status ibm_create_grid(const ibm_grid_desc* desc, void* stream, ibm_handle* 
   bool ok;
   if (d.precision == IBM_FP64)
     ok = build_periodic<double>(h, d.nx, h->tbl_off[0], 0) && build_periodic<double>(h, d.nz, h->tbl_off[2], 1) &&
-         build_wall<double>(h, 0, h->tbl_off[1]) && build_wall<double>(h, 1, h->tbl_off[1]);
+         build_wall<double>(h, h->tbl_off[1]);
   else
     ok = build_periodic<float>(h, d.nx, h->tbl_off[0], 0) && build_periodic<float>(h, d.nz, h->tbl_off[2], 1) &&
-         build_wall<float>(h, 0, h->tbl_off[1]) && build_wall<float>(h, 1, h->tbl_off[1]);
+         build_wall<float>(h, h->tbl_off[1]);
   // Poisson: modified wavenumbers, twiddles, pivots
   const double pi = 3.14159265358979323846;
   std::vector<double> lx(g.nkx), lz(g.nz), twx(2 * g.nx), twz(2 * g.nz);
@@ -606,7 +671,11 @@ ibm_status ibm_create_grid(const ibm_grid_desc* desc, void* stream, ibm_handle* 
   cudaMemsetAsync(h->v, 0, nvf * es, st);
   cudaMemsetAsync(h->w, 0, ncell * es, st);
   cudaMemsetAsync(h->p, 0, ncell * es, st);
-  for (int c = 0; c < 3; ++c) cudaMemsetAsync(h->H[c], 0, (c == 1 ? nvf : ncell) * es, st);
+  for (int c = 0; c < 3; ++c) {
+    cudaMemsetAsync(h->H[c], 0, (c == 1 ? nvf : ncell) * es, st);
+    if (h->lo[c]) cudaMemsetAsync(h->lo[c], 0, (c == 1 ? nvf : ncell) * es, st);
+  }
+  if (h->phi2) cudaMemsetAsync(h->phi2, 0, ncell * es, st);
   cudaMemsetAsync(h->ds, 0, sizeof(DevState), st);
   cudaMemsetAsync(h->tb.cand, 0, sizeof(Cand), st);
   if (full_reset(h, st) != IBM_OK) rc = IBM_ERR_CUDA;
@@ -779,7 +848,10 @@ ibm_status ibm_set_fields(ibm_handle h, const double* u, const double* v, const 
       // stage through the scratch array (large enough for any field in FP64? use R buffers)
       double* stage = (double*)h->scr;   // scr holds 2*ncell+nvf floats = enough bytes for one FP64 field
       CK(cudaMemcpyAsync(stage, src[q], n[q] * 8, kind, st));
-      k_convert<double, float><<<num_sms() * 4, 256, 0, st>>>(stage, (float*)dst[q], n[q]);
+      if (q < 3 && h->lo[q])
+        k_split<<<num_sms() * 4, 256, 0, st>>>(stage, (float*)dst[q], (float*)h->lo[q], n[q]);
+      else
+        k_convert<double, float><<<num_sms() * 4, 256, 0, st>>>(stage, (float*)dst[q], n[q]);
     }
   }
   for (int c = 0; c < 3; ++c) CK(cudaMemsetAsync(h->H[c], 0, (c == 1 ? g.nvf : g.ncell) * h->esize, st));
@@ -864,7 +936,10 @@ ibm_status ibm_get_fields(ibm_handle h, double* u, double* v, double* w, double*
       CK(cudaMemcpyAsync(dst[q], src[q], n[q] * 8, kind, st));
     } else {
       double* stage = (double*)h->scr;
-      k_convert<float, double><<<num_sms() * 4, 256, 0, st>>>((const float*)src[q], stage, n[q]);
+      if (q < 3 && h->lo[q])
+        k_join<<<num_sms() * 4, 256, 0, st>>>((const float*)src[q], (const float*)h->lo[q], stage, n[q]);
+      else
+        k_convert<float, double><<<num_sms() * 4, 256, 0, st>>>((const float*)src[q], stage, n[q]);
       CK(cudaMemcpyAsync(dst[q], stage, n[q] * 8, kind, st));
       CK(cudaStreamSynchronize(st));
     }

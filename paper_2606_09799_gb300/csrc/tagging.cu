@@ -41,76 +41,127 @@ __global__ void k_tag_reset(Geo g, const Cand* __restrict__ cand, unsigned cap, 
 }
 
 // ---------------------------------------------------------------------------
-// Algorithm 1: one warp per (triangle, component)
+// Algorithm 1: one warp per triangle, its lanes spread over the Eulerian
+// points of all three staggered grids inside the triangle's box
 // ---------------------------------------------------------------------------
+
+// Coordinate of lattice index i along axis a for a node offset of 0 (face)
+// or half a cell; the same formula as node_pos.
+__device__ __forceinline__ double lat(long long i, double del, int half) {
+  return half ? dmul(dadd((double)i, 0.5), del) : dmul((double)i, del);
+}
+
+// Exact index range of the lattice points strictly inside (lo, hi): start
+// from a conservative range and shrink it with the predicate itself (the
+// coordinate is monotone in the index), so the set equals that of testing
+// every point.
+__device__ __forceinline__ void exact_range(double lo, double hi, double del, double idel, int half,
+                                            long long& i0, long long& i1) {
+  const double off = half ? 0.5 : 0.0;
+  // conservative start (one index of margin absorbs the rounding of lo / del)
+  i0 = (long long)floor(lo * idel - off) - 1;
+  i1 = (long long)ceil(hi * idel - off) + 1;
+  while (i0 <= i1 && !(lo < lat(i0, del, half))) ++i0;
+  while (i1 >= i0 && !(lat(i1, del, half) < hi)) --i1;
+}
+
 __global__ void __launch_bounds__(128) k_tag_candidates(Geo g, Surf s, Cand* __restrict__ cand, unsigned cap,
                                                         unsigned long long* d2min, DevState* ds) {
   const int lane = threadIdx.x & 31;
-  const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (wid >= 3ll * s.nt) return;
-  const int t = (int)(wid / 3), c = (int)(wid % 3);
+  const long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (t >= s.nt) return;
   double A[3], B[3], C[3];
-  load_triangle(s, t, A, B, C);
+  load_triangle(s, (int)t, A, B, C);
+  TriConst TC;
+  tri_const(A, B, C, TC);
   const double del[3] = {g.dx, g.dy, g.dz};
-  const double off[3] = {c == 0 ? 0.0 : 0.5, c == 1 ? 0.0 : 0.5, c == 2 ? 0.0 : 0.5};
+  const double idel[3] = {g.idx, g.idy, g.idz};
   double lo[3], hi[3];
-  long long ilo[3], ihi[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    const double mn = fmin(A[d], fmin(B[d], C[d]));
-    const double mx = fmax(A[d], fmax(B[d], C[d]));
-    lo[d] = dsub(mn, del[d]);
-    hi[d] = dadd(mx, del[d]);
-    ilo[d] = (long long)floor(dsub(ddiv(lo[d], del[d]), off[d])) - 1;
-    ihi[d] = (long long)ceil(dsub(ddiv(hi[d], del[d]), off[d])) + 1;
+    lo[d] = dsub(fmin(A[d], fmin(B[d], C[d])), del[d]);
+    hi[d] = dadd(fmax(A[d], fmax(B[d], C[d])), del[d]);
   }
-  const long long jlo = (c == 1) ? 1 : 0, jhi = g.ny - 1;
-  if (ilo[1] < jlo) ilo[1] = jlo;
-  if (ihi[1] > jhi) ihi[1] = jhi;
-  const long long ni = ihi[0] - ilo[0] + 1, nj = ihi[1] - ilo[1] + 1, nk = ihi[2] - ilo[2] + 1;
-  if (ni <= 0 || nj <= 0 || nk <= 0) return;
-  const long long total = ni * nj * nk;
-  const long long coff = comp_off(g, c);
+  // ranges per axis for face (half = 0) and half-offset (half = 1) lattices
+  long long r0[3][2], r1[3][2];
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int hf = 0; hf < 2; ++hf) exact_range(lo[d], hi[d], del[d], idel[d], hf, r0[d][hf], r1[d][hf]);
+  long long n0[3][3], cnt[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    long long prod = 1;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int hf = (d == c) ? 0 : 1;
+      long long a0 = r0[d][hf], a1 = r1[d][hf];
+      if (d == 1) {
+        a0 = a0 < (c == 1 ? 1 : 0) ? (c == 1 ? 1 : 0) : a0;
+        a1 = a1 > g.ny - 1 ? g.ny - 1 : a1;
+      }
+      n0[c][d] = a0;
+      const long long len = a1 - a0 + 1;
+      prod *= len > 0 ? len : 0;
+    }
+    cnt[c] = prod;
+  }
+  long long ext[3][3];   // extent per component and axis
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int hf = (d == c) ? 0 : 1;
+      long long a1 = r1[d][hf];
+      if (d == 1) a1 = a1 > g.ny - 1 ? g.ny - 1 : a1;
+      ext[c][d] = a1 - n0[c][d] + 1;
+    }
+  const long long total = cnt[0] + cnt[1] + cnt[2];
   for (long long base = 0; base < total; base += 32) {
     const long long n = base + lane;
     bool tagged = false;
     unsigned key = 0;
     unsigned long long d2bits = 0;
     if (n < total) {
-      const long long i = ilo[0] + n % ni, j = ilo[1] + (n / ni) % nj, k = ilo[2] + n / (ni * nj);
+      const int c = n < cnt[0] ? 0 : (n < cnt[0] + cnt[1] ? 1 : 2);
+      const long long q = n - (c == 0 ? 0 : (c == 1 ? cnt[0] : cnt[0] + cnt[1]));
+      const long long ni = ext[c][0], nj = ext[c][1];
+      const long long idx3[3] = {n0[c][0] + q % ni, n0[c][1] + (q / ni) % nj, n0[c][2] + q / (ni * nj)};
       double x[3];
-      node_pos(g, c, i, j, k, x);
-      bool inside = true;
 #pragma unroll
-      for (int d = 0; d < 3; ++d) inside = inside && (lo[d] < x[d]) && (x[d] < hi[d]);
-      if (inside) {
-        double X[3], wb[3], N[3];
-        closest_point_exact(x, A, B, C, X, wb);
+      for (int d = 0; d < 3; ++d) x[d] = lat(idx3[d], del[d], d == c ? 0 : 1);
+      double X[3], wb[3], N[3], P[3];
+      closest_point_exact(x, TC, X, wb);
 #pragma unroll
-        for (int d = 0; d < 3; ++d) N[d] = dsub(x[d], X[d]);
-        const double n2 = ddot(N, N);
-        if (n2 <= g.diag2) {
-          if (n2 == 0.0) {
-            tagged = true;  // a node on the surface: alpha = 0 in Eq. new_IB
-          } else {
+      for (int d = 0; d < 3; ++d) {
+        N[d] = dsub(x[d], X[d]);
+        P[d] = dmul(N[d], N[d]);
+      }
+      const double n2 = dadd(dadd(P[0], P[1]), P[2]);
+      if (n2 <= g.diag2) {
+        if (n2 == 0.0) {
+          tagged = true;   // a node on the surface: alpha = 0 in Eq. new_IB
+        } else {
+          // N . (x^{k,n} - X) for the six lattice neighbours: only the
+          // neighbour's own axis differs from N, the other two products are
+          // the P[] already formed (same operands, same rounding)
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
+          for (int d = 0; d < 3 && !tagged; ++d) {
 #pragma unroll
-              for (int sg = -1; sg <= 1; sg += 2) {
-                double xn[3], vn[3];
-                node_pos(g, c, i + (d == 0 ? sg : 0), j + (d == 1 ? sg : 0), k + (d == 2 ? sg : 0), xn);
-#pragma unroll
-                for (int e = 0; e < 3; ++e) vn[e] = dsub(xn[e], X[e]);
-                if (ddot(N, vn) < 0.0) tagged = true;
-              }
+            for (int sg = -1; sg <= 1 && !tagged; sg += 2) {
+              const double vd = dsub(lat(idx3[d] + sg, del[d], d == c ? 0 : 1), X[d]);
+              const double Q = dmul(N[d], vd);
+              const double dot = d == 0 ? dadd(dadd(Q, P[1]), P[2])
+                                        : (d == 1 ? dadd(dadd(P[0], Q), P[2]) : dadd(dadd(P[0], P[1]), Q));
+              if (dot < 0.0) tagged = true;
             }
           }
-          if (tagged) {
-            const long long node = fidx(g, c, wrapi(i, g.nx), j, wrapi(k, g.nz));
-            key = ((unsigned)c << 30) | (unsigned)node;
-            d2bits = (unsigned long long)__double_as_longlong(n2);
-            atomicMin(d2min + coff + node, d2bits);
-          }
+        }
+        if (tagged) {
+          const long long node = fidx(g, c, wrapi(idx3[0], g.nx), idx3[1], wrapi(idx3[2], g.nz));
+          key = ((unsigned)c << 30) | (unsigned)node;
+          d2bits = (unsigned long long)__double_as_longlong(n2);
+          atomicMin(d2min + comp_off(g, c) + node, d2bits);
         }
       }
     }
@@ -147,10 +198,12 @@ __global__ void k_tag_resolve(Geo g, const Cand* __restrict__ cand, unsigned cap
   }
 }
 
-// Mark the winning (node, owner) pairs in the per-cell flag bytes.
+// Mark the winning (node, owner) pairs in the per-cell flag bytes, and in
+// the per-line records the sweeps use: the first forcing index of every x-
+// and z-line and of every y-line, per component.
 __global__ void k_tag_mark(Geo g, const Cand* __restrict__ cand, unsigned cap, const DevState* ds,
                            const unsigned long long* __restrict__ d2min, const unsigned* __restrict__ owner,
-                           unsigned* flags32) {
+                           unsigned* flags32, LineInfo li) {
   const unsigned n = min(ds->ncand, cap);
   for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
     const Cand cd = cand[e];
@@ -162,6 +215,9 @@ __global__ void k_tag_mark(Geo g, const Cand* __restrict__ cand, unsigned cap, c
       const long long i = node % g.nx, j = (node / g.nx) % pl, k = node / ((long long)g.nx * pl);
       const long long cell = cidx(g, i, j, k);
       atomicOr(flags32 + (cell >> 2), (unsigned)(1u << c) << (8 * (cell & 3)));
+      atomicMin(li.x + line_x(g, c, j, k), (int)i);
+      atomicMin(li.z + line_z(g, c, i, j), (int)k);
+      atomicMin(li.y + line_y(g, c, i, k), (int)j);
     }
   }
 }
@@ -351,16 +407,16 @@ __global__ void k_copy_count(DevState* ds) {
 // ---------------------------------------------------------------------------
 void launch_tagging(const Geo& g, const Surf& s, const TagBuffers& b, DevState* ds, cudaStream_t st) {
   stage_mark(st, ST_TAG);
+  cudaMemsetAsync(b.lines.x, 0x7F, b.lines.bytes, st);   // every line: "no forcing node"
   // previous step's candidates reset their nodes, then the counters restart
   k_tag_reset<<<num_sms() * 4, 256, 0, st>>>(g, b.cand, b.cap, ds, b.d2min, b.owner, b.flags32);
   k_copy_count<<<1, 1, 0, st>>>(ds);
   if (s.nt > 0) {
-    const long long warps = 3ll * s.nt;
-    const long long blocks = (warps * 32 + 127) / 128;
+    const long long blocks = ((long long)s.nt * 32 + 127) / 128;
     k_tag_candidates<<<(unsigned)blocks, 128, 0, st>>>(g, s, b.cand, b.cap, b.d2min, ds);
     const int gb = num_sms() * 8;
     k_tag_resolve<<<gb, 256, 0, st>>>(g, b.cand, b.cap, ds, b.d2min, b.owner);
-    k_tag_mark<<<gb, 256, 0, st>>>(g, b.cand, b.cap, ds, b.d2min, b.owner, b.flags32);
+    k_tag_mark<<<gb, 256, 0, st>>>(g, b.cand, b.cap, ds, b.d2min, b.owner, b.flags32, b.lines);
     k_tag_boundary<<<gb, 256, 0, st>>>(g, b.cand, b.cap, ds, b.d2min, b.owner, b.flags32);
   }
   const int nblk = (int)((g.ncell + CMP_CHUNK - 1) / CMP_CHUNK);

@@ -26,7 +26,7 @@ _LOCK = threading.Lock()
 
 IBM_RK2_CN, IBM_AB_CN = 0, 1
 IBM_NOSLIP, IBM_FREESLIP = 0, 1
-IBM_FP64, IBM_MIXED = 0, 1
+IBM_FP64, IBM_MIXED, IBM_MIXED_FAST = 0, 1, 2
 
 STATUS = {0: "IBM_OK", 1: "IBM_ERR_ARG", 2: "IBM_ERR_CUDA", 3: "IBM_ERR_OOM", 4: "IBM_ERR_GEOMETRY",
           5: "IBM_ERR_DIVERGED", 6: "IBM_ERR_TIMEOUT", 7: "IBM_ERR_STATE", 8: "IBM_ERR_CAPACITY"}
@@ -53,7 +53,7 @@ class ibm_diag(ctypes.Structure):
                 ("ncandidates", ctypes.c_int64), ("kernels_per_step", ctypes.c_int64),
                 ("d2h_bytes", ctypes.c_int64)]
 
-IBM_NSTAGES = 15
+IBM_NSTAGES = 16
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -272,7 +272,7 @@ class Simulation:
                  precision="fp64", use_q=True, stream=None):
         self.shape = (nx, ny, nz)
         sch = IBM_AB_CN if scheme == "ab" else IBM_RK2_CN
-        prec = IBM_MIXED if precision == "mixed" else IBM_FP64
+        prec = {"fp64": IBM_FP64, "mixed": IBM_MIXED, "mixed_fast": IBM_MIXED_FAST}[precision]
         self.h = ibm_create_grid(nx, ny, nz, lx, ly, lz, re, dt, sch, ybc, prec, int(use_q), stream)
         self.nt = 0
 
