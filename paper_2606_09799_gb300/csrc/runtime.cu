@@ -677,6 +677,7 @@ ibm_status ibm_create_grid(const ibm_grid_desc* desc, void* stream, ibm_handle* 
   }
   if (h->phi2) cudaMemsetAsync(h->phi2, 0, ncell * es, st);
   cudaMemsetAsync(h->ds, 0, sizeof(DevState), st);
+  cudaMemsetAsync(h->bad, 0, 16, st);   // reused device memory is not zero
   cudaMemsetAsync(h->tb.cand, 0, sizeof(Cand), st);
   if (full_reset(h, st) != IBM_OK) rc = IBM_ERR_CUDA;
   ce = cudaStreamSynchronize(st);
