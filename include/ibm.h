@@ -175,6 +175,38 @@ ibm_status ibm_profile_stages(ibm_handle h, int nsteps, double* ms, int64_t* ker
 /* Name of kernel group `stage` (0 <= stage < IBM_NSTAGES), else "". */
 const char* ibm_stage_name(int stage);
 
+/* Tagging without allocation.  The paper has no counterpart: this entry
+ * point exists for callers that must not allocate device memory at the time
+ * they need the tags -- an application that reserves all of its GPU memory
+ * at start-up and hands out nothing afterwards, code running inside another
+ * allocator's callback, or a time-critical loop that may not block on the
+ * allocator's implicit synchronisation.  It computes the forcing-node owners
+ * of Algorithm 1 for one surface on the three staggered grids, bit for bit
+ * the tags that ibm_step followed by ibm_get_tags gives for the same grid
+ * and surface, without a handle.
+ *
+ * All array arguments are device pointers owned by the caller: xyz (3*nverts
+ * FP64 vertex positions), tri (3*ntris int32 vertex indices) and the outputs
+ * owner_u (nz*ny*nx), owner_v (nz*(ny+1)*nx), owner_w (nz*ny*nx): -1 on fluid
+ * nodes, else the owning triangle.  Only desc's nx, ny, nz, lx, ly, lz and
+ * ybc are read.
+ *
+ * Its working memory is a fixed array inside the library, sized for
+ * IBM_NOALLOC_MAX_NODES nodes of the three grids together (8 MiB of device
+ * memory, held on every GPU that loads the library until the process
+ * exits); larger grids are rejected with IBM_ERR_CAPACITY before any work.
+ * The first call on a device resolves the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Every call shares the one array: calls that overlap on the GPU
+ * (on different streams, or from different threads) race and give wrong
+ * tags.  The call clears what it uses, runs on `stream`, and waits for it.
+ * Returns IBM_ERR_ARG for bad sizes or pointers, or when a triangle names a
+ * vertex outside [0, nverts) (such triangles are skipped, never read). */
+#define IBM_NOALLOC_MAX_NODES 1048576
+ibm_status ibm_tag_noalloc(const ibm_grid_desc* desc, int nverts, const double* xyz, int ntris,
+                           const int32_t* tri, int32_t* owner_u, int32_t* owner_v, int32_t* owner_w,
+                           void* stream);
+
 /* Library version string. */
 const char* ibm_version(void);
 

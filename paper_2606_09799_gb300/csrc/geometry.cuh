@@ -113,6 +113,26 @@ __device__ inline void closest_point_exact(const double p[3], const TriConst& T,
   w[0] = dsub(dsub(1.0, v), u); w[1] = v; w[2] = u;
 }
 
+// Coordinate of lattice index i along axis a for a node offset of 0 (face)
+// or half a cell; the same formula as node_pos.
+__device__ __forceinline__ double lat(long long i, double del, int half) {
+  return half ? dmul(dadd((double)i, 0.5), del) : dmul((double)i, del);
+}
+
+// Exact index range of the lattice points strictly inside (lo, hi): start
+// from a conservative range and shrink it with the predicate itself (the
+// coordinate is monotone in the index), so the set equals that of testing
+// every point.
+__device__ __forceinline__ void exact_range(double lo, double hi, double del, double idel, int half,
+                                            long long& i0, long long& i1) {
+  const double off = half ? 0.5 : 0.0;
+  // conservative start (one index of margin absorbs the rounding of lo / del)
+  i0 = (long long)floor(lo * idel - off) - 1;
+  i1 = (long long)ceil(hi * idel - off) + 1;
+  while (i0 <= i1 && !(lo < lat(i0, del, half))) ++i0;
+  while (i1 >= i0 && !(lat(i1, del, half) < hi)) --i1;
+}
+
 __device__ __forceinline__ void load_vertex(const Surf& s, int v, double out[3]) {
   out[0] = __ldg(s.x + v);
   out[1] = __ldg(s.x + s.nv + v);

@@ -45,26 +45,6 @@ __global__ void k_tag_reset(Geo g, const Cand* __restrict__ cand, unsigned cap, 
 // points of all three staggered grids inside the triangle's box
 // ---------------------------------------------------------------------------
 
-// Coordinate of lattice index i along axis a for a node offset of 0 (face)
-// or half a cell; the same formula as node_pos.
-__device__ __forceinline__ double lat(long long i, double del, int half) {
-  return half ? dmul(dadd((double)i, 0.5), del) : dmul((double)i, del);
-}
-
-// Exact index range of the lattice points strictly inside (lo, hi): start
-// from a conservative range and shrink it with the predicate itself (the
-// coordinate is monotone in the index), so the set equals that of testing
-// every point.
-__device__ __forceinline__ void exact_range(double lo, double hi, double del, double idel, int half,
-                                            long long& i0, long long& i1) {
-  const double off = half ? 0.5 : 0.0;
-  // conservative start (one index of margin absorbs the rounding of lo / del)
-  i0 = (long long)floor(lo * idel - off) - 1;
-  i1 = (long long)ceil(hi * idel - off) + 1;
-  while (i0 <= i1 && !(lo < lat(i0, del, half))) ++i0;
-  while (i1 >= i0 && !(lat(i1, del, half) < hi)) --i1;
-}
-
 __global__ void __launch_bounds__(128) k_tag_candidates(Geo g, Surf s, Cand* __restrict__ cand, unsigned cap,
                                                         unsigned long long* d2min, DevState* ds) {
   const int lane = threadIdx.x & 31;

@@ -61,7 +61,7 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
 EXPORTS = ("ibm_create_grid", "ibm_destroy", "ibm_set_surface", "ibm_set_body_force", "ibm_set_fields",
            "ibm_step", "ibm_get_fields", "ibm_get_tags", "ibm_get_diag", "ibm_sync", "ibm_last_error",
-           "ibm_set_allocator", "ibm_version", "ibm_profile_stages", "ibm_stage_name")
+           "ibm_set_allocator", "ibm_version", "ibm_profile_stages", "ibm_stage_name", "ibm_tag_noalloc")
 
 
 def library_path() -> str:
@@ -97,6 +97,7 @@ def load(build_if_needed: bool = True):
         L.ibm_version.restype = ctypes.c_char_p
         L.ibm_profile_stages.argtypes = [P, I, P, P]
         L.ibm_stage_name.argtypes = [I]
+        L.ibm_tag_noalloc.argtypes = [ctypes.POINTER(ibm_grid_desc), I, P, I, P, P, P, P, P]
         L.ibm_stage_name.restype = ctypes.c_char_p
         for name in EXPORTS:
             if name not in ("ibm_last_error", "ibm_version", "ibm_stage_name"):
@@ -216,6 +217,22 @@ def ibm_profile_stages(h, nsteps=1) -> dict:
     kn = (ctypes.c_int64 * IBM_NSTAGES)()
     _check(h, load().ibm_profile_stages(h, int(nsteps), ms, kn))
     return {ibm_stage_name(i): (ms[i], kn[i]) for i in range(IBM_NSTAGES)}
+
+
+IBM_NOALLOC_MAX_NODES = 1048576
+
+
+def ibm_tag_noalloc(nx, ny, nz, xyz, tri, owners, lx=1.0, ly=1.0, lz=1.0, ybc=IBM_NOSLIP, stream=None):
+    """Tags of one surface without any device allocation by the library (for
+    callers that must not allocate at that point).  xyz: (nv, 3) FP64 and
+    tri: (nt, 3) int32 device tensors; owners: three int32 device tensors of
+    the u, v, w field shapes, overwritten.  Returns the status code."""
+    d = ibm_grid_desc(nx, ny, nz, lx, ly, lz, 1.0, 1.0, IBM_RK2_CN, ybc, IBM_FP64, 1)
+    ptrs = [_ptr(a) for a in (xyz, tri) + tuple(owners)]
+    if any(dev != 1 for _, dev in ptrs):
+        raise ValueError("ibm_tag_noalloc takes device arrays only")
+    return load().ibm_tag_noalloc(ctypes.byref(d), int(xyz.shape[0]), ptrs[0][0], int(tri.shape[0]), ptrs[1][0],
+                                  ptrs[2][0], ptrs[3][0], ptrs[4][0], _stream_handle(stream))
 
 
 def ibm_stage_name(i) -> str:
