@@ -692,7 +692,9 @@ __global__ void __launch_bounds__(64) k_sweep_zy(Geo g, Fields<T> f, const unsig
   const int w = min(W, g.nx - i0);
   T* tile = reinterpret_cast<T*>(smem_raw);
   T* ust = tile + (size_t)n * W;                        // y-sweep: the state u^s of the same lines
-  unsigned char* fl = reinterpret_cast<unsigned char*>(tile + (size_t)(dir == 1 ? 2 : 1) * n * W);
+  const bool pair = dir == 1 && f.lo[c] != nullptr;     // y-sweep on a (hi, lo) velocity state
+  T* ulo = ust + (size_t)n * W;                         // ... and its low parts
+  unsigned char* fl = reinterpret_cast<unsigned char*>(tile + (size_t)(dir == 1 ? (pair ? 3 : 2) : 1) * n * W);
   T* __restrict__ R = f.R[c];
   T* __restrict__ Uc = comp_ptr(f, c);
   const unsigned char* fbytes = reinterpret_cast<const unsigned char*>(flags32);
@@ -701,6 +703,7 @@ __global__ void __launch_bounds__(64) k_sweep_zy(Geo g, Fields<T> f, const unsig
     for (int m = 0; m < n; ++m) {
       cp_async<sizeof(T)>(tile + m * W + t, R + base + m * stride + t);
       if (dir == 1) cp_async<sizeof(T)>(ust + m * W + t, Uc + base + m * stride + t);
+      if (pair) cp_async<sizeof(T)>(ulo + m * W + t, f.lo[c] + base + m * stride + t);
     }
   }
   if (words) {
@@ -729,7 +732,7 @@ __global__ void __launch_bounds__(64) k_sweep_zy(Geo g, Fields<T> f, const unsig
         T* __restrict__ Lc = f.lo[c];
         for (int m = 0; m < n; ++m) {
           const long long id = base + m * stride + t;
-          float hi = (float)ust[m * W + t], lo = (float)Lc[id];
+          float hi = (float)ust[m * W + t], lo = (float)ulo[m * W + t];
           ff_add(hi, lo, (float)tile[m * W + t]);
           Uc[id] = (T)hi;
           Lc[id] = (T)lo;
@@ -783,9 +786,10 @@ void launch_sweeps(const Geo& g, const Fields<T>& f, const TagBuffers& b, const 
   }
   stage_mark(st, ST_SWEEP_Y);
   {
-    const int W = sweep_width<T>(g.ny, 2);
-    k_sweep_zy<T><<<dim3((g.nx + W - 1) / W, 3, g.nz), W, sweep_smem<T>(W, g.ny, g.ny, 2), st>>>(g, f, b.flags32, tb,
-                                                                                             b.lines.y, 1);
+    const int tiles = f.lo[0] ? 3 : 2;
+    const int W = sweep_width<T>(g.ny, tiles);
+    k_sweep_zy<T><<<dim3((g.nx + W - 1) / W, 3, g.nz), W, sweep_smem<T>(W, g.ny, g.ny, tiles), st>>>(
+        g, f, b.flags32, tb, b.lines.y, 1);
   }
 }
 

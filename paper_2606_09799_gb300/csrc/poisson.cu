@@ -40,43 +40,82 @@ template <typename C>
 __device__ __forceinline__ C cconj(C a) { a.y = -a.y; return a; }
 
 // ---------------------------------------------------------------------------
-// FFT plan: radices in order of application (product = n)
+// FFT plan: radices in order of application (product = n), with the exact
+// multipliers that replace the integer divisions of each stage
 // ---------------------------------------------------------------------------
+struct FftStage {
+  int R, Ns, nb, scale;   // radix, span so far, butterflies per line, twiddle stride
+  unsigned mNs, mnb;      // ceil(2^32 / Ns), ceil(2^32 / nb)
+};
 struct FftPlan {
   int n, nst;
-  int rad[12];
+  FftStage st[12];
 };
+
+static unsigned magic_div(unsigned d) { return (unsigned)((0x100000000ull + d - 1) / d); }
+
+__device__ __forceinline__ unsigned magic_div_dev(unsigned d) {
+  return (unsigned)((0x100000000ull + d - 1) / d);
+}
+
+// q = x / d with m = ceil(2^32 / d): exact for x < 2^16 and d < 2^16, since
+// x * (m d - 2^32) < 2^32.  d = 1 has no 32-bit multiplier (2^32 wraps to
+// m = 0) and is taken as the identity.
+__device__ __forceinline__ unsigned fdiv(unsigned x, unsigned m) { return m ? __umulhi(x, m) : x; }
 
 static FftPlan make_plan(int n) {
   FftPlan p;
   p.n = n;
   p.nst = 0;
-  int m = n;
-  while (m % 4 == 0) { p.rad[p.nst++] = 4; m /= 4; }
-  while (m % 2 == 0) { p.rad[p.nst++] = 2; m /= 2; }
-  while (m % 3 == 0) { p.rad[p.nst++] = 3; m /= 3; }
+  int m = n, Ns = 1;
+  int rad[12], nr = 0;
+  while (m % 4 == 0) { rad[nr++] = 4; m /= 4; }
+  while (m % 2 == 0) { rad[nr++] = 2; m /= 2; }
+  while (m % 3 == 0) { rad[nr++] = 3; m /= 3; }
+  for (int s = 0; s < nr; ++s) {
+    FftStage& st = p.st[p.nst++];
+    st.R = rad[s];
+    st.Ns = Ns;
+    st.nb = n / st.R;
+    st.scale = n / (Ns * st.R);
+    st.mNs = magic_div((unsigned)Ns);
+    st.mnb = magic_div((unsigned)st.nb);
+    Ns *= st.R;
+  }
   return p;
 }
 
-// One Stockham pass over `lines` transforms of length n stored contiguously
-// (line-major) in src, written to dst.  tw[m] = exp(-2 pi i m / n).
+// One Stockham pass over `lines` transforms of length n; element e of line
+// l sits at l * ls + e * es (src and dst alike).  tw[m] = exp(-2 pi i m/n).
+// Threads take butterflies (line, j) with the line index fastest when
+// es > 1 (column tiles: neighbouring lines are neighbouring words) and j
+// fastest otherwise.
 template <typename T, bool INV>
-__device__ void fft_pass(const typename Cplx<T>::type* src, typename Cplx<T>::type* dst, int lines, int n, int R,
-                         int Ns, const typename Cplx<T>::type* __restrict__ tw) {
+__device__ void fft_pass(const typename Cplx<T>::type* src, typename Cplx<T>::type* dst, int lines, int n,
+                         const FftStage& S, const typename Cplx<T>::type* __restrict__ tw, int es, int ls,
+                         unsigned mlines) {
   using C = typename Cplx<T>::type;
-  const int nb = n / R;
-  const int scale = n / (Ns * R);
+  const int R = S.R, Ns = S.Ns, nb = S.nb;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
-  for (int t = tid; t < lines * nb; t += nth) {
-    const int line = t / nb, j = t - line * nb;
-    const C* s = src + line * n;
-    C* d = dst + line * n;
-    const int k = j % Ns;
+  const int total = lines * nb;
+  for (int t = tid; t < total; t += nth) {
+    int line, j;
+    if (es > 1) {
+      j = (int)fdiv((unsigned)t, mlines);
+      line = t - j * lines;
+    } else {
+      line = (int)fdiv((unsigned)t, S.mnb);
+      j = t - line * nb;
+    }
+    const C* sp = src + line * ls;
+    C* dp = dst + line * ls;
+    const int jn = (int)fdiv((unsigned)j, S.mNs);
+    const int k = j - jn * Ns;
     C v[4];
     for (int r = 0; r < R; ++r) {
-      C x = s[j + r * nb];
+      C x = sp[(j + r * nb) * es];
       if (r > 0 && k > 0) {
-        C w = __ldg(reinterpret_cast<const C*>(tw) + (r * k * scale));
+        C w = __ldg(tw + (r * k * S.scale));
         if (INV) w = cconj(w);
         x = cmul(x, w);
       }
@@ -110,22 +149,23 @@ __device__ void fft_pass(const typename Cplx<T>::type* src, typename Cplx<T>::ty
       v[1] = cadd(m, rot);
       v[2] = csub(m, rot);
     }
-    const int base = (j / Ns) * Ns * R + k;
-    for (int r = 0; r < R; ++r) d[base + r * Ns] = v[r];
+    const int dbase = jn * Ns * R + k;
+    for (int r = 0; r < R; ++r) dp[(dbase + r * Ns) * es] = v[r];
   }
 }
 
 // Full transform; returns the buffer that holds the result (0 = a, 1 = b).
 template <typename T, bool INV>
 __device__ int fft_lines(typename Cplx<T>::type* a, typename Cplx<T>::type* b, int lines, const FftPlan& p,
-                         const typename Cplx<T>::type* __restrict__ tw) {
-  int Ns = 1, cur = 0;
+                         const typename Cplx<T>::type* __restrict__ tw, int es = 1, int ls = -1,
+                         unsigned mlines = 0) {
+  if (ls < 0) ls = p.n;
+  int cur = 0;
   for (int s = 0; s < p.nst; ++s) {
     __syncthreads();
-    if (cur == 0) fft_pass<T, INV>(a, b, lines, p.n, p.rad[s], Ns, tw);
-    else fft_pass<T, INV>(b, a, lines, p.n, p.rad[s], Ns, tw);
+    if (cur == 0) fft_pass<T, INV>(a, b, lines, p.n, p.st[s], tw, es, ls, mlines);
+    else fft_pass<T, INV>(b, a, lines, p.n, p.st[s], tw, es, ls, mlines);
     cur ^= 1;
-    Ns *= p.rad[s];
   }
   __syncthreads();
   return cur;
@@ -223,16 +263,25 @@ __global__ void k_fft_x_fwd(Geo g, Fields<T> f, const unsigned* __restrict__ fla
   const long long pu = (long long)ny * n, pv = (long long)(ny + 1) * n;
   // load: rows 2 l and 2 l + 1 of line l; divergence in the bulk type
   for (int l = threadIdx.y; l < lines_per_block; l += blockDim.y) {
+    int jj[2], kk[2];
+    bool ok[2];
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh) {
+      const int row = 2 * (line0 + l) + hh;
+      ok[hh] = row < rows;
+      jj[hh] = row % ny;
+      kk[hh] = row / ny;
+    }
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       C z;
       z.x = (T)0;
       z.y = (T)0;
+      const int ip = i + 1 == n ? 0 : i + 1;
 #pragma unroll
       for (int hh = 0; hh < 2; ++hh) {
-        const int row = 2 * (line0 + l) + hh;
-        if (row >= rows) continue;
-        const int j = row % ny, k = row / ny;
-        const int ip = i + 1 == n ? 0 : i + 1, kp = k + 1 == g.nz ? 0 : k + 1;
+        if (!ok[hh]) continue;
+        const int j = jj[hh], k = kk[hh];
+        const int kp = k + 1 == g.nz ? 0 : k + 1;
         const long long r0 = (long long)k * pu + (long long)j * n;
         const long long cell = r0 + i;
         const unsigned fl = (flags32[cell >> 2] >> (8 * (cell & 3))) & 0xFFu;
@@ -268,8 +317,8 @@ __global__ void k_fft_x_fwd(Geo g, Fields<T> f, const unsigned* __restrict__ fla
   const C* out = res == 0 ? bufa : bufb;
   C* spec = reinterpret_cast<C*>(f.spec);
   const int nkx = g.nkx;
-  for (int t = threadIdx.y * blockDim.x + threadIdx.x; t < lines_per_block * nkx; t += blockDim.x * blockDim.y) {
-    const int l = t / nkx, kx = t - l * nkx;
+  for (int l = threadIdx.y; l < lines_per_block; l += blockDim.y)
+  for (int kx = threadIdx.x; kx < nkx; kx += blockDim.x) {
     const C Z = out[l * n + kx];
     const C Zc = cconj(out[l * n + (kx == 0 ? 0 : n - kx)]);
     C Xa, Xb;
@@ -296,8 +345,9 @@ __global__ void k_fft_x_inv(Geo g, Fields<T> f, const T* __restrict__ tw, FftPla
   const long long rows = (long long)g.ny * g.nz;
   const long long line0 = (long long)blockIdx.x * lines_per_block;
   const C* spec = reinterpret_cast<const C*>(f.spec);
-  for (int t = threadIdx.x; t < lines_per_block * n; t += blockDim.x) {
-    const int l = t / n, kx = t - l * n;
+  for (int l = threadIdx.y; l < lines_per_block; l += blockDim.y)
+  for (int kx = threadIdx.x; kx < n; kx += blockDim.x) {
+    const int t = l * n + kx;
     const long long ra = 2 * (line0 + l), rb = ra + 1;
     const bool mirror = kx >= nkx;
     const int q = mirror ? n - kx : kx;
@@ -314,8 +364,9 @@ __global__ void k_fft_x_inv(Geo g, Fields<T> f, const T* __restrict__ tw, FftPla
   }
   const int res = fft_lines<T, true>(bufa, bufb, lines_per_block, plan, reinterpret_cast<const C*>(tw));
   const C* out = res == 0 ? bufa : bufb;
-  for (int t = threadIdx.x; t < lines_per_block * n; t += blockDim.x) {
-    const int l = t / n, i = t - l * n;
+  for (int l = threadIdx.y; l < lines_per_block; l += blockDim.y)
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int t = l * n + i;
     const long long ra = 2 * (line0 + l), rb = ra + 1;
     if (ra < rows) out_phi[ra * n + i] = out[t].x;
     if (rb < rows) out_phi[rb * n + i] = out[t].y;
@@ -323,7 +374,10 @@ __global__ void k_fft_x_inv(Geo g, Fields<T> f, const T* __restrict__ tw, FftPla
 }
 
 // z transform of the half-spectrum, in place; a block takes `cols` adjacent
-// kx columns of one y-plane (coalesced rows of `cols` complex values).
+// kx columns of one y-plane (coalesced rows of `cols` complex values), kept
+// in shared memory in load order [k][column] and transformed as strided
+// lines (no bank conflicts on load, store or butterflies).  cols is a power
+// of two.
 template <typename T, bool INV>
 __global__ void k_fft_z(Geo g, Fields<T> f, const T* __restrict__ tw, FftPlan plan, int cols) {
   using C = typename Cplx<T>::type;
@@ -335,19 +389,21 @@ __global__ void k_fft_z(Geo g, Fields<T> f, const T* __restrict__ tw, FftPlan pl
   const int j = blockIdx.x / ntile;
   const int kx0 = (blockIdx.x - j * ntile) * cols;
   const int w = min(cols, nkx - kx0);
+  const int lc = __ffs(cols) - 1;
   C* spec = reinterpret_cast<C*>(f.spec);
   for (int t = threadIdx.x; t < n * cols; t += blockDim.x) {
-    const int k = t / cols, c = t - k * cols;
+    const int k = t >> lc, c = t & (cols - 1);
     C z;
     z.x = z.y = (T)0;
     if (c < w) z = spec[((long long)k * g.ny + j) * nkx + kx0 + c];
-    bufa[c * n + k] = z;
+    bufa[t] = z;
   }
-  const int res = fft_lines<T, INV>(bufa, bufb, cols, plan, reinterpret_cast<const C*>(tw));
+  const int res = fft_lines<T, INV>(bufa, bufb, cols, plan, reinterpret_cast<const C*>(tw), cols, 1,
+                                    magic_div_dev(cols));
   const C* out = res == 0 ? bufa : bufb;
   for (int t = threadIdx.x; t < n * cols; t += blockDim.x) {
-    const int k = t / cols, c = t - k * cols;
-    if (c < w) spec[((long long)k * g.ny + j) * nkx + kx0 + c] = out[c * n + k];
+    const int k = t >> lc, c = t & (cols - 1);
+    if (c < w) spec[((long long)k * g.ny + j) * nkx + kx0 + c] = out[t];
   }
 }
 
@@ -425,6 +481,150 @@ __global__ void __launch_bounds__(128) k_tri_y(Geo g, Fields<T> f, const double*
       const double v = (j == g.ny - 1) ? pr : F[2 * id + part];
       sp[2 * id + part] = (T)(v - mr);
     }
+  }
+}
+
+// Warp-cooperative variant: a warp holds G = 32/L consecutive kx of one kz,
+// L lanes per system, each lane Rr consecutive rows of j in registers (so a
+// warp load touches whole 32-byte sectors of G adjacent wavenumbers).  Both
+// Thomas passes are affine recurrences with real multipliers,
+//   forward  p_j = a_j p_{j-1} + b_j,  a_j = -(1/dy^2) inv_j, b_j = r_j inv_j
+//   backward x_j = -cp_j x_{j+1} + p_j,
+// composed per lane, then across the L lanes of a system by a segmented
+// shuffle scan, in FP64.  No forward values leave the registers.
+template <typename T, int L, int Rr>
+__global__ void __launch_bounds__(128) k_tri_y_warp(Geo g, Fields<T> f, const double* __restrict__ cp,
+                                                    const double* __restrict__ inv) {
+  using C = typename Cplx<T>::type;
+  constexpr int G = 32 / L;
+  const int lane = threadIdx.x & 31;
+  const int sl = lane % L;                      // lane inside its system
+  const int nkx = g.nkx, ny = g.ny;
+  const int groups_x = (nkx + G - 1) / G;
+  const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (wid >= (long long)groups_x * g.nz) return;     // whole warps only
+  const int kz = (int)(wid / groups_x);
+  const int kx = (int)(wid % groups_x) * G + lane / L;
+  const bool live = kx < nkx;
+  const long long base = (long long)kz * ny * nkx + (live ? kx : 0);
+  const long long stride = nkx;
+  C* spec = reinterpret_cast<C*>(f.spec);
+  const double a = g.idy * g.idy;
+  const bool singular = live && kx == 0 && kz == 0;
+  const int j0 = sl * Rr;
+  const unsigned FULL = 0xFFFFFFFFu;
+  // ---- forward: compose the lane's maps
+  double A = 1.0, Br = 0.0, Bi = 0.0;
+#pragma unroll
+  for (int u = 0; u < Rr; ++u) {
+    const int j = j0 + u;
+    if (!live || j >= ny) break;
+    const long long id = base + (long long)j * stride;
+    const C z = spec[id];
+    const double iv = inv[id];
+    const double al = (j == 0) ? 0.0 : -a * iv;
+    const double br = (j == 0 && singular) ? 0.0 : (double)z.x * iv;
+    const double bi = (j == 0 && singular) ? 0.0 : (double)z.y * iv;
+    A = al * A;
+    Br = fma(al, Br, br);
+    Bi = fma(al, Bi, bi);
+  }
+  for (int o = 1; o < L; o <<= 1) {
+    const double pa = __shfl_up_sync(FULL, A, o, L), pr = __shfl_up_sync(FULL, Br, o, L),
+                 pi = __shfl_up_sync(FULL, Bi, o, L);
+    if (sl >= o) {
+      Br = fma(A, pr, Br);
+      Bi = fma(A, pi, Bi);
+      A = A * pa;
+    }
+  }
+  double pr = __shfl_up_sync(FULL, Br, 1, L), pi = __shfl_up_sync(FULL, Bi, 1, L);
+  if (sl == 0) { pr = 0.0; pi = 0.0; }
+  double vr[Rr], vi[Rr];
+#pragma unroll
+  for (int u = 0; u < Rr; ++u) {
+    const int j = j0 + u;
+    vr[u] = 0.0;
+    vi[u] = 0.0;
+    if (!live || j >= ny) continue;
+    const long long id = base + (long long)j * stride;
+    const C z = spec[id];
+    const double iv = inv[id];
+    if (j == 0) {
+      pr = singular ? 0.0 : (double)z.x * iv;
+      pi = singular ? 0.0 : (double)z.y * iv;
+    } else {
+      pr = ((double)z.x - a * pr) * iv;
+      pi = ((double)z.y - a * pi) * iv;
+    }
+    vr[u] = pr;
+    vi[u] = pi;
+  }
+  // ---- backward: compose from the top row of the lane down
+  A = 1.0;
+  Br = 0.0;
+  Bi = 0.0;
+#pragma unroll
+  for (int u = Rr - 1; u >= 0; --u) {
+    const int j = j0 + u;
+    if (!live || j >= ny) continue;
+    const double al = (j == ny - 1) ? 0.0 : -cp[base + (long long)j * stride];
+    A = al * A;
+    Br = fma(al, Br, vr[u]);
+    Bi = fma(al, Bi, vi[u]);
+  }
+  for (int o = 1; o < L; o <<= 1) {
+    const double na = __shfl_down_sync(FULL, A, o, L), nr = __shfl_down_sync(FULL, Br, o, L),
+                 ni = __shfl_down_sync(FULL, Bi, o, L);
+    if (sl + o < L) {
+      Br = fma(A, nr, Br);
+      Bi = fma(A, ni, Bi);
+      A = A * na;
+    }
+  }
+  double xr = __shfl_down_sync(FULL, Br, 1, L), xi = __shfl_down_sync(FULL, Bi, 1, L);
+  if (sl == L - 1) { xr = 0.0; xi = 0.0; }
+  double sr = 0.0, si = 0.0;
+#pragma unroll
+  for (int u = Rr - 1; u >= 0; --u) {
+    const int j = j0 + u;
+    if (!live || j >= ny) continue;
+    if (j == ny - 1) {
+      xr = vr[u];
+      xi = vi[u];
+    } else {
+      const double c = cp[base + (long long)j * stride];
+      xr = vr[u] - c * xr;
+      xi = vi[u] - c * xi;
+    }
+    vr[u] = xr;
+    vi[u] = xi;
+    sr += xr;
+    si += xi;
+  }
+  if (kz == 0 && (int)(wid % groups_x) == 0) {
+    // the (0,0) system lives in the first group of kz = 0: zero-mean gauge
+    for (int o = 1; o < L; o <<= 1) {
+      sr += __shfl_xor_sync(FULL, sr, o, L);
+      si += __shfl_xor_sync(FULL, si, o, L);
+    }
+    if (singular) {
+      const double mr = sr / ny, mi = si / ny;
+#pragma unroll
+      for (int u = 0; u < Rr; ++u) {
+        vr[u] -= mr;
+        vi[u] -= mi;
+      }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < Rr; ++u) {
+    const int j = j0 + u;
+    if (!live || j >= ny) continue;
+    C o;
+    o.x = (T)vr[u];
+    o.y = (T)vi[u];
+    spec[base + (long long)j * stride] = o;
   }
 }
 
@@ -546,7 +746,8 @@ void launch_poisson(const Geo& g, const Fields<T>& f, const TagBuffers& b, const
   }
   const double scale = 1.0 / (sg.alp * dt * (double)g.nx * (double)g.nz);
   const FftPlan px = make_plan(g.nx), pz = make_plan(g.nz);
-  const int cols = lines_for(g.nz) < 16 ? lines_for(g.nz) : 16;
+  int cols = 16;
+  while (cols > 1 && cols * g.nz > 2048) cols >>= 1;
   const int ntile = (g.nkx + cols - 1) / cols;
   const size_t smz = 2ull * cols * g.nz * sizeof(C);
   const int lpb = lines_for(g.nx);
@@ -555,16 +756,29 @@ void launch_poisson(const Geo& g, const Fields<T>& f, const TagBuffers& b, const
   const int tx = g.nx < 128 ? g.nx : 128;
   const long long tlines = (long long)g.nkx * g.nz;
   double* fwd = sizeof(T) == sizeof(double) ? nullptr : reinterpret_cast<double*>(f.scr);
+  // wall-normal Thomas for every (kx, kz): warp-cooperative when the rows fit
+  // the registers (16 per lane), else one thread per real/imaginary part
+  auto tri_solve = [&](double* fwdbuf) {
+    if (g.ny <= 8 * 16) {
+      const long long warps = (long long)((g.nkx + 3) / 4) * g.nz;
+      k_tri_y_warp<T, 8, 16><<<(unsigned)((warps * 32 + 127) / 128), 128, 0, st>>>(g, f, tb.cp, tb.inv);
+    } else if (g.ny <= 32 * 16) {
+      const long long warps = (long long)g.nkx * g.nz;
+      k_tri_y_warp<T, 32, 16><<<(unsigned)((warps * 32 + 127) / 128), 128, 0, st>>>(g, f, tb.cp, tb.inv);
+    } else {
+      k_tri_y<T><<<(unsigned)((2 * tlines + 127) / 128), 128, 0, st>>>(g, f, tb.cp, tb.inv, fwdbuf);
+    }
+  };
   // the rest of one solve: z transform, wall-normal Thomas, inverse z and x
   auto solve_rest = [&](T* out) {
     stage_mark(st, ST_FFT_Z_FWD);
     k_fft_z<T, false><<<g.ny * ntile, 256, smz, st>>>(g, f, tb.twz, pz, cols);
     stage_mark(st, ST_TRI_Y);
-    k_tri_y<T><<<(unsigned)((2 * tlines + 127) / 128), 128, 0, st>>>(g, f, tb.cp, tb.inv, fwd);
+    tri_solve(fwd);
     stage_mark(st, ST_FFT_Z_INV);
     k_fft_z<T, true><<<g.ny * ntile, 256, smz, st>>>(g, f, tb.twz, pz, cols);
     stage_mark(st, ST_FFT_X_INV);
-    k_fft_x_inv<T><<<(unsigned)((xlines + lpb - 1) / lpb), 256, smx, st>>>(g, f, tb.twx, px, lpb, out);
+    k_fft_x_inv<T><<<(unsigned)((xlines + lpb - 1) / lpb), dim3(tx, 256 / tx), smx, st>>>(g, f, tb.twx, px, lpb, out);
   };
   const double adt = sg.alp * dt, bb = adt / (2.0 * re);
   ProjCoef<T> cf;
@@ -588,9 +802,10 @@ void launch_poisson(const Geo& g, const Fields<T>& f, const TagBuffers& b, const
   k_fft_x_fwd<T><<<(unsigned)((xlines + lpb - 1) / lpb), dim3(tx, 256 / tx), smx, st>>>(g, f, b.flags32, tb.twx, px,
                                                                                         lpb, ds, sg.s, use_q, scale, 1);
   k_fft_z<T, false><<<g.ny * ntile, 256, smz, st>>>(g, f, tb.twz, pz, cols);
-  k_tri_y<T><<<(unsigned)((2 * tlines + 127) / 128), 128, 0, st>>>(g, f, tb.cp, tb.inv, fwd);
+  tri_solve(fwd);
   k_fft_z<T, true><<<g.ny * ntile, 256, smz, st>>>(g, f, tb.twz, pz, cols);
-  k_fft_x_inv<T><<<(unsigned)((xlines + lpb - 1) / lpb), 256, smx, st>>>(g, f, tb.twx, px, lpb, f.phi2);
+  k_fft_x_inv<T><<<(unsigned)((xlines + lpb - 1) / lpb), dim3(tx, 256 / tx), smx, st>>>(g, f, tb.twx, px, lpb,
+                                                                                       f.phi2);
   k_project<T><<<pgrid, pblk, 0, st>>>(g, f, cf, 2);
 }
 

@@ -45,9 +45,87 @@ __global__ void k_tag_reset(Geo g, const Cand* __restrict__ cand, unsigned cap, 
 // points of all three staggered grids inside the triangle's box
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(128) k_tag_candidates(Geo g, Surf s, Cand* __restrict__ cand, unsigned cap,
-                                                        unsigned long long* d2min, DevState* ds) {
-  const int lane = threadIdx.x & 31;
+// Cheap FP32 screen of one (node, triangle) pair, in coordinates relative to
+// the triangle's first vertex (so every quantity is of the cell's size).  It
+// returns false only when the exact FP64 test certainly fails: |N|^2 above
+// diag^2 by a margin, or every neighbour's scalar product clearly positive.
+// Near the decision boundary |N| is at least del_min / sqrt(3), so the
+// margins (0.4% of |N|^2 + del |N_d|) bound the FP32 error of N relative to
+// the cell.  That error is about eps_32 * L / sin^2(theta) for a triangle of
+// edge L and smallest angle theta; the screen is used only where this stays
+// below 1e-4 of the margin's scale (sin^2 > 0.05, edges within 8 cells, cell
+// aspect ratio within 4), else every pair goes to the exact test.  Tags are
+// decided by the FP64 test alone.
+struct TriF32 {
+  float ab[3], ac[3], bc[3];
+  float aa, abac, cc, iaa, icc, ibc, iden;
+  long long ia[3][2];   // a = (ia + half) * del + fr, per axis and lattice offset
+  float fr[3][2];
+  float del[3], diag2;
+};
+
+__device__ __forceinline__ bool screen_pair(const TriF32& F, int c, const int idx3[3]) {
+  float p[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    // static indices only (a runtime index would put F in local memory)
+    const float pf = (float)((long long)idx3[d] - F.ia[d][0]) * F.del[d] - F.fr[d][0];
+    const float ph = (float)((long long)idx3[d] - F.ia[d][1]) * F.del[d] - F.fr[d][1];
+    p[d] = d == c ? pf : ph;
+  }
+  const float d1 = F.ab[0] * p[0] + F.ab[1] * p[1] + F.ab[2] * p[2];
+  const float d2 = F.ac[0] * p[0] + F.ac[1] * p[1] + F.ac[2] * p[2];
+  float X[3];
+  const float d3 = d1 - F.aa, d4 = d2 - F.abac, d5 = d1 - F.abac, d6 = d2 - F.cc;
+  const float vc = d1 * d4 - d3 * d2, vb = d5 * d2 - d1 * d6, va = d3 * d6 - d5 * d4;
+  if (d1 <= 0.f && d2 <= 0.f) {
+    X[0] = X[1] = X[2] = 0.f;
+  } else if (d3 >= 0.f && d4 <= d3) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) X[d] = F.ab[d];
+  } else if (vc <= 0.f && d1 >= 0.f && d3 <= 0.f) {
+    const float t = d1 * F.iaa;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) X[d] = t * F.ab[d];
+  } else if (d6 >= 0.f && d5 <= d6) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) X[d] = F.ac[d];
+  } else if (vb <= 0.f && d2 >= 0.f && d6 <= 0.f) {
+    const float t = d2 * F.icc;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) X[d] = t * F.ac[d];
+  } else if (va <= 0.f && (d4 - d3) >= 0.f && (d5 - d6) >= 0.f) {
+    const float t = (d4 - d3) * F.ibc;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) X[d] = F.ab[d] + t * F.bc[d];
+  } else {
+    const float v = vb * F.iden, w = vc * F.iden;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) X[d] = F.ab[d] * v + F.ac[d] * w;
+  }
+  float N[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) N[d] = p[d] - X[d];
+  const float n2 = N[0] * N[0] + N[1] * N[1] + N[2] * N[2];
+  if (n2 > F.diag2 * 1.004f) return false;
+  // N . (neighbour - X) = |N|^2 -+ del_d N_d: the smallest over the six
+  float lowest = 3.4e38f, scale = 0.f;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const float t = F.del[d] * fabsf(N[d]);
+    lowest = fminf(lowest, n2 - t);
+    scale = fmaxf(scale, t);
+  }
+  return lowest < 4e-3f * (n2 + scale) + 1e-9f * F.diag2;
+}
+
+constexpr int TAG_WARPS = 4;
+
+__global__ void __launch_bounds__(32 * TAG_WARPS) k_tag_candidates(Geo g, Surf s, Cand* __restrict__ cand,
+                                                                   unsigned cap, unsigned long long* d2min,
+                                                                   DevState* ds) {
+  __shared__ long long queue[TAG_WARPS][64];
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   const long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (t >= s.nt) return;
   double A[3], B[3], C[3];
@@ -68,7 +146,7 @@ __global__ void __launch_bounds__(128) k_tag_candidates(Geo g, Surf s, Cand* __r
   for (int d = 0; d < 3; ++d)
 #pragma unroll
     for (int hf = 0; hf < 2; ++hf) exact_range(lo[d], hi[d], del[d], idel[d], hf, r0[d][hf], r1[d][hf]);
-  long long n0[3][3], cnt[3];
+  long long n0[3][3], ext[3][3], cnt[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     long long prod = 1;
@@ -77,36 +155,104 @@ __global__ void __launch_bounds__(128) k_tag_candidates(Geo g, Surf s, Cand* __r
       const int hf = (d == c) ? 0 : 1;
       long long a0 = r0[d][hf], a1 = r1[d][hf];
       if (d == 1) {
-        a0 = a0 < (c == 1 ? 1 : 0) ? (c == 1 ? 1 : 0) : a0;
+        const long long jlo = c == 1 ? 1 : 0;
+        a0 = a0 < jlo ? jlo : a0;
         a1 = a1 > g.ny - 1 ? g.ny - 1 : a1;
       }
       n0[c][d] = a0;
-      const long long len = a1 - a0 + 1;
-      prod *= len > 0 ? len : 0;
+      ext[c][d] = a1 - a0 + 1;
+      prod *= ext[c][d] > 0 ? ext[c][d] : 0;
     }
     cnt[c] = prod;
   }
-  long long ext[3][3];   // extent per component and axis
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
+  const long long total = cnt[0] + cnt[1] + cnt[2];
+  // FP32 screen set-up; skinny or large triangles and strongly anisotropic
+  // cells (where the FP32 error bound above does not hold) skip it
+  TriF32 F;
+  const double den = dsub(dmul(TC.aa, TC.cc), dmul(TC.abac, TC.abac));
+  const double dmin = fmin(del[0], fmin(del[1], del[2])), dmax = fmax(del[0], fmax(del[1], del[2]));
+  const double lmax2 = fmax(TC.aa, fmax(TC.cc, dadd(dsub(TC.aa, 2.0 * TC.abac), TC.cc)));
+  const bool screen = den > 0.05 * TC.aa * TC.cc && lmax2 <= 64.0 * dmin * dmin && dmax <= 4.0 * dmin &&
+                      total < (1ll << 30);
+  if (screen) {
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      const int hf = (d == c) ? 0 : 1;
-      long long a1 = r1[d][hf];
-      if (d == 1) a1 = a1 > g.ny - 1 ? g.ny - 1 : a1;
-      ext[c][d] = a1 - n0[c][d] + 1;
+      F.ab[d] = (float)TC.ab[d];
+      F.ac[d] = (float)TC.ac[d];
+      F.bc[d] = (float)TC.bc[d];
+      F.del[d] = (float)del[d];
+#pragma unroll
+      for (int hf = 0; hf < 2; ++hf) {
+        const double off = hf ? 0.5 : 0.0;
+        const double q = floor(A[d] * idel[d] - off);
+        F.ia[d][hf] = (long long)q;
+        F.fr[d][hf] = (float)(A[d] - (q + off) * del[d]);
+      }
     }
-  const long long total = cnt[0] + cnt[1] + cnt[2];
-  for (long long base = 0; base < total; base += 32) {
-    const long long n = base + lane;
+    F.aa = (float)TC.aa;
+    F.abac = (float)TC.abac;
+    F.cc = (float)TC.cc;
+    F.iaa = (float)TC.iaa;
+    F.icc = (float)TC.icc;
+    F.ibc = (float)TC.ibc;
+    F.iden = (float)TC.iden;
+    F.diag2 = (float)g.diag2;
+  }
+  // pair n -> (component, lattice indices); 32-bit arithmetic (the screen
+  // runs only when the box holds fewer than 2^30 pairs; otherwise 64-bit)
+  int n0i[3][3];
+  unsigned exti[3][3], cnti[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    cnti[c] = (unsigned)min(cnt[c], (long long)0xFFFFFFFF);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      n0i[c][d] = (int)n0[c][d];
+      exti[c][d] = (unsigned)max(ext[c][d], 1ll);
+    }
+  }
+  auto decode32 = [&](unsigned n, int& c, int idx3[3]) {
+    c = n < cnti[0] ? 0 : (n < cnti[0] + cnti[1] ? 1 : 2);
+    // selects instead of runtime indices (keeps the tables in registers)
+    const unsigned q = n - (c == 0 ? 0u : (c == 1 ? cnti[0] : cnti[0] + cnti[1]));
+    const unsigned ni = c == 0 ? exti[0][0] : (c == 1 ? exti[1][0] : exti[2][0]);
+    const unsigned nj = c == 0 ? exti[0][1] : (c == 1 ? exti[1][1] : exti[2][1]);
+    const unsigned qi = q / ni, qj = qi / nj;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int b = c == 0 ? n0i[0][d] : (c == 1 ? n0i[1][d] : n0i[2][d]);
+      idx3[d] = b + (int)(d == 0 ? q - qi * ni : (d == 1 ? qi - qj * nj : qj));
+    }
+  };
+  auto decode = [&](long long n, int& c, long long idx3[3]) {
+    if (screen) {
+      int i3[3];
+      decode32((unsigned)n, c, i3);
+      idx3[0] = i3[0];
+      idx3[1] = i3[1];
+      idx3[2] = i3[2];
+      return;
+    }
+    c = n < cnt[0] ? 0 : (n < cnt[0] + cnt[1] ? 1 : 2);
+    const long long q = n - (c == 0 ? 0 : (c == 1 ? cnt[0] : cnt[0] + cnt[1]));
+    const long long ni = c == 0 ? ext[0][0] : (c == 1 ? ext[1][0] : ext[2][0]);
+    const long long nj = c == 0 ? ext[0][1] : (c == 1 ? ext[1][1] : ext[2][1]);
+    const long long qi = q / ni, qj = qi / nj;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const long long b = c == 0 ? n0[0][d] : (c == 1 ? n0[1][d] : n0[2][d]);
+      idx3[d] = b + (d == 0 ? q - qi * ni : (d == 1 ? qi - qj * nj : qj));
+    }
+  };
+  // the exact FP64 test of Algorithm 1 on `count` queued pairs, one per lane
+  auto exact_batch = [&](int count) {
     bool tagged = false;
     unsigned key = 0;
     unsigned long long d2bits = 0;
-    if (n < total) {
-      const int c = n < cnt[0] ? 0 : (n < cnt[0] + cnt[1] ? 1 : 2);
-      const long long q = n - (c == 0 ? 0 : (c == 1 ? cnt[0] : cnt[0] + cnt[1]));
-      const long long ni = ext[c][0], nj = ext[c][1];
-      const long long idx3[3] = {n0[c][0] + q % ni, n0[c][1] + (q / ni) % nj, n0[c][2] + q / (ni * nj)};
+    if (lane < count) {
+      int c;
+      long long idx3[3];
+      decode(queue[wl][lane], c, idx3);
       double x[3];
 #pragma unroll
       for (int d = 0; d < 3; ++d) x[d] = lat(idx3[d], del[d], d == c ? 0 : 1);
@@ -164,7 +310,33 @@ __global__ void __launch_bounds__(128) k_tag_candidates(Geo g, Surf s, Cand* __r
         }
       }
     }
+  };
+  int qn = 0;   // pairs waiting in this warp's queue (warp-uniform)
+  for (long long base = 0; base < total; base += 32) {
+    const long long n = base + lane;
+    bool keep = false;
+    if (n < total) {
+      if (screen) {
+        int c, idx3[3];
+        decode32((unsigned)n, c, idx3);
+        keep = screen_pair(F, c, idx3);
+      } else {
+        keep = true;
+      }
+    }
+    const unsigned km = __ballot_sync(0xFFFFFFFFu, keep);
+    if (keep) queue[wl][qn + __popc(km & ((1u << lane) - 1u))] = n;
+    qn += __popc(km);
+    __syncwarp();
+    if (qn >= 32) {
+      exact_batch(32);
+      __syncwarp();
+      if (lane < qn - 32) queue[wl][lane] = queue[wl][32 + lane];
+      qn -= 32;
+      __syncwarp();
+    }
   }
+  if (qn > 0) exact_batch(qn);
 }
 
 // Per node keep the smallest triangle index among the candidates of minimum |N|^2.
@@ -392,8 +564,8 @@ void launch_tagging(const Geo& g, const Surf& s, const TagBuffers& b, DevState* 
   k_tag_reset<<<num_sms() * 4, 256, 0, st>>>(g, b.cand, b.cap, ds, b.d2min, b.owner, b.flags32);
   k_copy_count<<<1, 1, 0, st>>>(ds);
   if (s.nt > 0) {
-    const long long blocks = ((long long)s.nt * 32 + 127) / 128;
-    k_tag_candidates<<<(unsigned)blocks, 128, 0, st>>>(g, s, b.cand, b.cap, b.d2min, ds);
+    const long long blocks = ((long long)s.nt * 32 + 32 * TAG_WARPS - 1) / (32 * TAG_WARPS);
+    k_tag_candidates<<<(unsigned)blocks, 32 * TAG_WARPS, 0, st>>>(g, s, b.cand, b.cap, b.d2min, ds);
     const int gb = num_sms() * 8;
     k_tag_resolve<<<gb, 256, 0, st>>>(g, b.cand, b.cap, ds, b.d2min, b.owner);
     k_tag_mark<<<gb, 256, 0, st>>>(g, b.cand, b.cap, ds, b.d2min, b.owner, b.flags32, b.lines);
