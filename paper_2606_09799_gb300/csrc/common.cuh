@@ -80,11 +80,14 @@ struct ForceNode {
 
 constexpr unsigned KEY_MASK = (1u << 30) - 1u;
 
+struct TriRec;
+
 // Surface as stored on the device (structure of arrays).
 struct Surf {
   const double* x;               // x[nv], then y[nv], then z[nv]
   const double* u;               // vertex velocities, same layout
   const int* t;                  // vertex a of every triangle, then b, then c
+  TriRec* rec;                   // per-triangle constants of the current step (nt)
   int nv, nt;
 };
 

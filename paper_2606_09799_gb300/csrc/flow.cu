@@ -58,20 +58,14 @@ __device__ inline void forcing_geometry(const Geo& g, const Surf& s, unsigned ke
   const int pl = planes(g, c);
   const long long i = node % g.nx, j = (node / g.nx) % pl, k = node / ((long long)g.nx * pl);
   const int va = __ldg(s.t + tri), vb = __ldg(s.t + s.nt + tri), vc = __ldg(s.t + 2 * (long long)s.nt + tri);
-  double A[3], B[3], C[3];
-  load_vertex(s, va, A);
-  load_vertex(s, vb, B);
-  load_vertex(s, vc, C);
-  double cen[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) cen[d] = (A[d] + B[d] + C[d]) / 3.0;
+  // the triangle's constants of this step (formed by the tagging set-up)
+  const TriRec* __restrict__ R = s.rec + tri;
   node_pos(g, c, i, j, k, ng.x);
-  const long long mi = llround((cen[0] - ng.x[0]) / g.lx);
-  const long long mk = llround((cen[2] - ng.x[2]) / g.lz);
+  const long long mi = llround((R->cen[0] - ng.x[0]) / g.lx);
+  const long long mk = llround((R->cen[2] - ng.x[2]) / g.lz);
   if (mi != 0 || mk != 0) node_pos(g, c, i + mi * g.nx, j, k + mk * g.nz, ng.x);
   double wb[3];
-  TriConst TC;
-  tri_const(A, B, C, TC);
+  const TriConst TC = R->tc;
   closest_point_exact(ng.x, TC, ng.X, wb);
 #pragma unroll
   for (int d = 0; d < 3; ++d) ng.N[d] = dsub(ng.x[d], ng.X[d]);

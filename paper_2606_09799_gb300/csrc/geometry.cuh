@@ -53,6 +53,33 @@ __device__ inline void tri_const(const double a[3], const double b[3], const dou
   T.iden = ddiv(1.0, den);
 }
 
+// FP32 copy of a triangle's constants for the tagging pre-screen, in
+// coordinates relative to the first vertex: position of lattice point i
+// along axis d is (i - ia[d][half]) * del[d] - fr[d][half].
+struct TriF32 {
+  float ab[3], ac[3], bc[3];
+  float aa, abac, cc, iaa, icc, ibc, iden;
+  long long ia[3][2];
+  float fr[3][2];
+  float del[3], diag2;
+};
+
+// Everything the kernels of one step derive from a triangle alone, formed
+// once per step by one thread per triangle: the closest-point constants,
+// the centroid (periodic image of a node), the lattice box of Algorithm 1
+// per velocity component (first index and extent per axis, pair counts)
+// and the FP32 screen constants (screen = 0 where the screen's error bound
+// does not hold).
+struct TriRec {
+  TriConst tc;
+  double cen[3];
+  TriF32 f;
+  int n0[3][3];
+  int ext[3][3];
+  long long cnt[3];
+  int screen;
+};
+
 // Closest point X on the triangle to p with barycentric weights (Ericson
 // 2004, Voronoi regions: three vertex regions, three edge regions, the
 // face), the six classifying scalar products formed from two per-point

@@ -491,7 +491,9 @@ __global__ void __launch_bounds__(128) k_tri_y(Geo g, Fields<T> f, const double*
 //   forward  p_j = a_j p_{j-1} + b_j,  a_j = -(1/dy^2) inv_j, b_j = r_j inv_j
 //   backward x_j = -cp_j x_{j+1} + p_j,
 // composed per lane, then across the L lanes of a system by a segmented
-// shuffle scan, in FP64.  No forward values leave the registers.
+// shuffle scan, in FP64.  A lane issues the loads of all its rows (right-
+// hand side, 1/pivot, c') before the first use, so the kernel waits for
+// memory once; no forward values leave the registers.
 template <typename T, int L, int Rr>
 __global__ void __launch_bounds__(128) k_tri_y_warp(Geo g, Fields<T> f, const double* __restrict__ cp,
                                                     const double* __restrict__ inv) {
@@ -513,18 +515,32 @@ __global__ void __launch_bounds__(128) k_tri_y_warp(Geo g, Fields<T> f, const do
   const bool singular = live && kx == 0 && kz == 0;
   const int j0 = sl * Rr;
   const unsigned FULL = 0xFFFFFFFFu;
+  // ---- every load of the lane's rows, issued together
+  double zr[Rr], zi[Rr], iv[Rr], cq[Rr];
+#pragma unroll
+  for (int u = 0; u < Rr; ++u) {
+    const int j = j0 + u;
+    zr[u] = zi[u] = 0.0;
+    iv[u] = 1.0;
+    cq[u] = 0.0;
+    if (live && j < ny) {
+      const long long id = base + (long long)j * stride;
+      const C z = spec[id];
+      zr[u] = (double)z.x;
+      zi[u] = (double)z.y;
+      iv[u] = __ldg(inv + id);
+      cq[u] = __ldg(cp + id);
+    }
+  }
   // ---- forward: compose the lane's maps
   double A = 1.0, Br = 0.0, Bi = 0.0;
 #pragma unroll
   for (int u = 0; u < Rr; ++u) {
     const int j = j0 + u;
-    if (!live || j >= ny) break;
-    const long long id = base + (long long)j * stride;
-    const C z = spec[id];
-    const double iv = inv[id];
-    const double al = (j == 0) ? 0.0 : -a * iv;
-    const double br = (j == 0 && singular) ? 0.0 : (double)z.x * iv;
-    const double bi = (j == 0 && singular) ? 0.0 : (double)z.y * iv;
+    if (!live || j >= ny) continue;
+    const double al = (j == 0) ? 0.0 : -a * iv[u];
+    const double br = (j == 0 && singular) ? 0.0 : zr[u] * iv[u];
+    const double bi = (j == 0 && singular) ? 0.0 : zi[u] * iv[u];
     A = al * A;
     Br = fma(al, Br, br);
     Bi = fma(al, Bi, bi);
@@ -547,15 +563,12 @@ __global__ void __launch_bounds__(128) k_tri_y_warp(Geo g, Fields<T> f, const do
     vr[u] = 0.0;
     vi[u] = 0.0;
     if (!live || j >= ny) continue;
-    const long long id = base + (long long)j * stride;
-    const C z = spec[id];
-    const double iv = inv[id];
     if (j == 0) {
-      pr = singular ? 0.0 : (double)z.x * iv;
-      pi = singular ? 0.0 : (double)z.y * iv;
+      pr = singular ? 0.0 : zr[u] * iv[u];
+      pi = singular ? 0.0 : zi[u] * iv[u];
     } else {
-      pr = ((double)z.x - a * pr) * iv;
-      pi = ((double)z.y - a * pi) * iv;
+      pr = (zr[u] - a * pr) * iv[u];
+      pi = (zi[u] - a * pi) * iv[u];
     }
     vr[u] = pr;
     vi[u] = pi;
@@ -568,7 +581,7 @@ __global__ void __launch_bounds__(128) k_tri_y_warp(Geo g, Fields<T> f, const do
   for (int u = Rr - 1; u >= 0; --u) {
     const int j = j0 + u;
     if (!live || j >= ny) continue;
-    const double al = (j == ny - 1) ? 0.0 : -cp[base + (long long)j * stride];
+    const double al = (j == ny - 1) ? 0.0 : -cq[u];
     A = al * A;
     Br = fma(al, Br, vr[u]);
     Bi = fma(al, Bi, vi[u]);
@@ -593,9 +606,8 @@ __global__ void __launch_bounds__(128) k_tri_y_warp(Geo g, Fields<T> f, const do
       xr = vr[u];
       xi = vi[u];
     } else {
-      const double c = cp[base + (long long)j * stride];
-      xr = vr[u] - c * xr;
-      xi = vi[u] - c * xi;
+      xr = vr[u] - cq[u] * xr;
+      xi = vi[u] - cq[u] * xi;
     }
     vr[u] = xr;
     vi[u] = xi;

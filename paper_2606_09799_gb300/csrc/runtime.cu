@@ -13,6 +13,7 @@
 
 #include "../../include/ibm.h"
 #include "common.cuh"
+#include "geometry.cuh"
 #include "launch.h"
 
 namespace ibm {
@@ -172,6 +173,7 @@ struct ibm_grid {
   double tbl_smden[2];
   // surface
   double* sx; double* su; int* st; double* stage_x; int* stage_t; unsigned* bad;
+  TriRec* trirec;         // per-triangle constants, rewritten every step
   int nv, nt, nv_cap, nt_cap;
   bool has_topology;
   // graph
@@ -394,6 +396,7 @@ static Surf surface(ibm_handle h) {
   s.x = h->sx;
   s.u = h->su;
   s.t = h->st;
+  s.rec = h->trirec;
   s.nv = h->nv;
   s.nt = h->nt;
   return s;
@@ -753,13 +756,15 @@ ibm_status ibm_set_surface(ibm_handle h, int nverts, const double* xyz, const do
     int* nst = (int*)dalloc(h, 3ull * ntc * 4);
     double* ngx = (double*)dalloc(h, 3ull * nvc * 8);
     int* ngt = (int*)dalloc(h, 3ull * ntc * 4);
-    if (!nsx || !nsu || !nst || !ngx || !ngt) {
+    TriRec* nrec = (TriRec*)dalloc(h, (size_t)ntc * sizeof(TriRec));
+    if (!nsx || !nsu || !nst || !ngx || !ngt || !nrec) {
       set_err(h, "%s", "device allocation of the surface failed");
       return IBM_ERR_OOM;
     }
     if (old_t && !tri && h->nt > 0) CK(cudaMemcpy(nst, old_t, 3ull * h->nt * 4, cudaMemcpyDeviceToDevice));
     dfree(h, h->sx); dfree(h, h->su); dfree(h, h->st); dfree(h, h->stage_x); dfree(h, h->stage_t);
-    h->sx = nsx; h->su = nsu; h->st = nst; h->stage_x = ngx; h->stage_t = ngt;
+    dfree(h, h->trirec);
+    h->sx = nsx; h->su = nsu; h->st = nst; h->stage_x = ngx; h->stage_t = ngt; h->trirec = nrec;
     h->nv_cap = nvc;
     h->nt_cap = ntc;
     h->graph_ok = false;

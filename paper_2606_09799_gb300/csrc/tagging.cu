@@ -41,6 +41,91 @@ __global__ void k_tag_reset(Geo g, const Cand* __restrict__ cand, unsigned cap, 
 }
 
 // ---------------------------------------------------------------------------
+// Per-triangle set-up, one thread per triangle: closest-point constants,
+// centroid, the exact lattice box of Algorithm 1 per component and the FP32
+// screen constants.  Every kernel of the step that needs a triangle's
+// constants reads them here, so they are formed once (FP64 is scarce on
+// this GPU: a warp-wide FP64 instruction costs about 20 SM cycles).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_tri_setup(Geo g, Surf s) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= s.nt) return;
+  double A[3], B[3], C[3];
+  load_triangle(s, t, A, B, C);
+  TriRec R;
+  tri_const(A, B, C, R.tc);
+  const TriConst& TC = R.tc;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) R.cen[d] = (A[d] + B[d] + C[d]) / 3.0;
+  const double del[3] = {g.dx, g.dy, g.dz};
+  const double idel[3] = {g.idx, g.idy, g.idz};
+  double lo[3], hi[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    lo[d] = dsub(fmin(A[d], fmin(B[d], C[d])), del[d]);
+    hi[d] = dadd(fmax(A[d], fmax(B[d], C[d])), del[d]);
+  }
+  // ranges per axis for face (half = 0) and half-offset (half = 1) lattices
+  long long r0[3][2], r1[3][2];
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int hf = 0; hf < 2; ++hf) exact_range(lo[d], hi[d], del[d], idel[d], hf, r0[d][hf], r1[d][hf]);
+  long long total = 0;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    long long prod = 1;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const int hf = (d == c) ? 0 : 1;
+      long long a0 = r0[d][hf], a1 = r1[d][hf];
+      if (d == 1) {
+        const long long jlo = c == 1 ? 1 : 0;
+        a0 = a0 < jlo ? jlo : a0;
+        a1 = a1 > g.ny - 1 ? g.ny - 1 : a1;
+      }
+      const long long e = a1 - a0 + 1 > 0 ? a1 - a0 + 1 : 0;
+      R.n0[c][d] = (int)a0;
+      R.ext[c][d] = (int)e;
+      prod *= e;
+    }
+    R.cnt[c] = prod;
+    total += prod;
+  }
+  // FP32 screen: skinny or large triangles and strongly anisotropic cells
+  // (where its error bound does not hold) skip it
+  const double den = dsub(dmul(TC.aa, TC.cc), dmul(TC.abac, TC.abac));
+  const double dmin = fmin(del[0], fmin(del[1], del[2])), dmax = fmax(del[0], fmax(del[1], del[2]));
+  const double lmax2 = fmax(TC.aa, fmax(TC.cc, dadd(dsub(TC.aa, 2.0 * TC.abac), TC.cc)));
+  R.screen = den > 0.05 * TC.aa * TC.cc && lmax2 <= 64.0 * dmin * dmin && dmax <= 4.0 * dmin &&
+             total < (1ll << 30);
+  TriF32& F = R.f;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    F.ab[d] = (float)TC.ab[d];
+    F.ac[d] = (float)TC.ac[d];
+    F.bc[d] = (float)TC.bc[d];
+    F.del[d] = (float)del[d];
+#pragma unroll
+    for (int hf = 0; hf < 2; ++hf) {
+      const double off = hf ? 0.5 : 0.0;
+      const double q = floor(A[d] * idel[d] - off);
+      F.ia[d][hf] = (long long)q;
+      F.fr[d][hf] = (float)(A[d] - (q + off) * del[d]);
+    }
+  }
+  F.aa = (float)TC.aa;
+  F.abac = (float)TC.abac;
+  F.cc = (float)TC.cc;
+  F.iaa = (float)TC.iaa;
+  F.icc = (float)TC.icc;
+  F.ibc = (float)TC.ibc;
+  F.iden = (float)TC.iden;
+  F.diag2 = (float)g.diag2;
+  s.rec[t] = R;
+}
+
+// ---------------------------------------------------------------------------
 // Algorithm 1: one warp per triangle, its lanes spread over the Eulerian
 // points of all three staggered grids inside the triangle's box
 // ---------------------------------------------------------------------------
@@ -56,14 +141,6 @@ __global__ void k_tag_reset(Geo g, const Cand* __restrict__ cand, unsigned cap, 
 // below 1e-4 of the margin's scale (sin^2 > 0.05, edges within 8 cells, cell
 // aspect ratio within 4), else every pair goes to the exact test.  Tags are
 // decided by the FP64 test alone.
-struct TriF32 {
-  float ab[3], ac[3], bc[3];
-  float aa, abac, cc, iaa, icc, ibc, iden;
-  long long ia[3][2];   // a = (ia + half) * del + fr, per axis and lattice offset
-  float fr[3][2];
-  float del[3], diag2;
-};
-
 __device__ __forceinline__ bool screen_pair(const TriF32& F, int c, const int idx3[3]) {
   float p[3];
 #pragma unroll
@@ -128,120 +205,45 @@ __global__ void __launch_bounds__(32 * TAG_WARPS) k_tag_candidates(Geo g, Surf s
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   const long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (t >= s.nt) return;
-  double A[3], B[3], C[3];
-  load_triangle(s, (int)t, A, B, C);
-  TriConst TC;
-  tri_const(A, B, C, TC);
+  const TriRec* __restrict__ rec = s.rec + t;
+  const long long cnt0 = rec->cnt[0], cnt1 = rec->cnt[1], cnt2 = rec->cnt[2];
+  const long long total = cnt0 + cnt1 + cnt2;
+  if (total == 0) return;
+  const bool screen = rec->screen != 0;
   const double del[3] = {g.dx, g.dy, g.dz};
-  const double idel[3] = {g.idx, g.idy, g.idz};
-  double lo[3], hi[3];
+  int n0[3][3], ext[3][3];
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    lo[d] = dsub(fmin(A[d], fmin(B[d], C[d])), del[d]);
-    hi[d] = dadd(fmax(A[d], fmax(B[d], C[d])), del[d]);
-  }
-  // ranges per axis for face (half = 0) and half-offset (half = 1) lattices
-  long long r0[3][2], r1[3][2];
-#pragma unroll
-  for (int d = 0; d < 3; ++d)
-#pragma unroll
-    for (int hf = 0; hf < 2; ++hf) exact_range(lo[d], hi[d], del[d], idel[d], hf, r0[d][hf], r1[d][hf]);
-  long long n0[3][3], ext[3][3], cnt[3];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    long long prod = 1;
+  for (int c = 0; c < 3; ++c)
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      const int hf = (d == c) ? 0 : 1;
-      long long a0 = r0[d][hf], a1 = r1[d][hf];
-      if (d == 1) {
-        const long long jlo = c == 1 ? 1 : 0;
-        a0 = a0 < jlo ? jlo : a0;
-        a1 = a1 > g.ny - 1 ? g.ny - 1 : a1;
-      }
-      n0[c][d] = a0;
-      ext[c][d] = a1 - a0 + 1;
-      prod *= ext[c][d] > 0 ? ext[c][d] : 0;
+      n0[c][d] = rec->n0[c][d];
+      ext[c][d] = max(rec->ext[c][d], 1);
     }
-    cnt[c] = prod;
-  }
-  const long long total = cnt[0] + cnt[1] + cnt[2];
-  // FP32 screen set-up; skinny or large triangles and strongly anisotropic
-  // cells (where the FP32 error bound above does not hold) skip it
-  TriF32 F;
-  const double den = dsub(dmul(TC.aa, TC.cc), dmul(TC.abac, TC.abac));
-  const double dmin = fmin(del[0], fmin(del[1], del[2])), dmax = fmax(del[0], fmax(del[1], del[2]));
-  const double lmax2 = fmax(TC.aa, fmax(TC.cc, dadd(dsub(TC.aa, 2.0 * TC.abac), TC.cc)));
-  const bool screen = den > 0.05 * TC.aa * TC.cc && lmax2 <= 64.0 * dmin * dmin && dmax <= 4.0 * dmin &&
-                      total < (1ll << 30);
-  if (screen) {
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      F.ab[d] = (float)TC.ab[d];
-      F.ac[d] = (float)TC.ac[d];
-      F.bc[d] = (float)TC.bc[d];
-      F.del[d] = (float)del[d];
-#pragma unroll
-      for (int hf = 0; hf < 2; ++hf) {
-        const double off = hf ? 0.5 : 0.0;
-        const double q = floor(A[d] * idel[d] - off);
-        F.ia[d][hf] = (long long)q;
-        F.fr[d][hf] = (float)(A[d] - (q + off) * del[d]);
-      }
-    }
-    F.aa = (float)TC.aa;
-    F.abac = (float)TC.abac;
-    F.cc = (float)TC.cc;
-    F.iaa = (float)TC.iaa;
-    F.icc = (float)TC.icc;
-    F.ibc = (float)TC.ibc;
-    F.iden = (float)TC.iden;
-    F.diag2 = (float)g.diag2;
-  }
-  // pair n -> (component, lattice indices); 32-bit arithmetic (the screen
-  // runs only when the box holds fewer than 2^30 pairs; otherwise 64-bit)
-  int n0i[3][3];
-  unsigned exti[3][3], cnti[3];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    cnti[c] = (unsigned)min(cnt[c], (long long)0xFFFFFFFF);
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      n0i[c][d] = (int)n0[c][d];
-      exti[c][d] = (unsigned)max(ext[c][d], 1ll);
-    }
-  }
-  auto decode32 = [&](unsigned n, int& c, int idx3[3]) {
-    c = n < cnti[0] ? 0 : (n < cnti[0] + cnti[1] ? 1 : 2);
-    // selects instead of runtime indices (keeps the tables in registers)
-    const unsigned q = n - (c == 0 ? 0u : (c == 1 ? cnti[0] : cnti[0] + cnti[1]));
-    const unsigned ni = c == 0 ? exti[0][0] : (c == 1 ? exti[1][0] : exti[2][0]);
-    const unsigned nj = c == 0 ? exti[0][1] : (c == 1 ? exti[1][1] : exti[2][1]);
-    const unsigned qi = q / ni, qj = qi / nj;
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const int b = c == 0 ? n0i[0][d] : (c == 1 ? n0i[1][d] : n0i[2][d]);
-      idx3[d] = b + (int)(d == 0 ? q - qi * ni : (d == 1 ? qi - qj * nj : qj));
-    }
-  };
+  // pair n -> (component, lattice indices), with selects instead of
+  // runtime indices (keeps the tables in registers); 32-bit arithmetic when
+  // the box holds fewer than 2^30 pairs (always so where the screen runs)
   auto decode = [&](long long n, int& c, long long idx3[3]) {
-    if (screen) {
-      int i3[3];
-      decode32((unsigned)n, c, i3);
-      idx3[0] = i3[0];
-      idx3[1] = i3[1];
-      idx3[2] = i3[2];
-      return;
+    c = n < cnt0 ? 0 : (n < cnt0 + cnt1 ? 1 : 2);
+    const long long q = n - (c == 0 ? 0 : (c == 1 ? cnt0 : cnt0 + cnt1));
+    const int ni = c == 0 ? ext[0][0] : (c == 1 ? ext[1][0] : ext[2][0]);
+    const int nj = c == 0 ? ext[0][1] : (c == 1 ? ext[1][1] : ext[2][1]);
+    long long qi, qj, ri, rj;
+    if (total < (1ll << 30)) {
+      const unsigned q32 = (unsigned)q, qi32 = q32 / (unsigned)ni, qj32 = qi32 / (unsigned)nj;
+      qi = qi32;
+      qj = qj32;
+      ri = q32 - qi32 * (unsigned)ni;
+      rj = qi32 - qj32 * (unsigned)nj;
+    } else {
+      qi = q / ni;
+      qj = qi / nj;
+      ri = q - qi * ni;
+      rj = qi - qj * nj;
     }
-    c = n < cnt[0] ? 0 : (n < cnt[0] + cnt[1] ? 1 : 2);
-    const long long q = n - (c == 0 ? 0 : (c == 1 ? cnt[0] : cnt[0] + cnt[1]));
-    const long long ni = c == 0 ? ext[0][0] : (c == 1 ? ext[1][0] : ext[2][0]);
-    const long long nj = c == 0 ? ext[0][1] : (c == 1 ? ext[1][1] : ext[2][1]);
-    const long long qi = q / ni, qj = qi / nj;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      const long long b = c == 0 ? n0[0][d] : (c == 1 ? n0[1][d] : n0[2][d]);
-      idx3[d] = b + (d == 0 ? q - qi * ni : (d == 1 ? qi - qj * nj : qj));
+      const int b = c == 0 ? n0[0][d] : (c == 1 ? n0[1][d] : n0[2][d]);
+      idx3[d] = b + (d == 0 ? ri : (d == 1 ? rj : qj));
     }
   };
   // the exact FP64 test of Algorithm 1 on `count` queued pairs, one per lane
@@ -250,6 +252,7 @@ __global__ void __launch_bounds__(32 * TAG_WARPS) k_tag_candidates(Geo g, Surf s
     unsigned key = 0;
     unsigned long long d2bits = 0;
     if (lane < count) {
+      const TriConst TC = rec->tc;
       int c;
       long long idx3[3];
       decode(queue[wl][lane], c, idx3);
@@ -311,14 +314,18 @@ __global__ void __launch_bounds__(32 * TAG_WARPS) k_tag_candidates(Geo g, Surf s
       }
     }
   };
+  TriF32 F;
+  if (screen) F = rec->f;
   int qn = 0;   // pairs waiting in this warp's queue (warp-uniform)
   for (long long base = 0; base < total; base += 32) {
     const long long n = base + lane;
     bool keep = false;
     if (n < total) {
       if (screen) {
-        int c, idx3[3];
-        decode32((unsigned)n, c, idx3);
+        int c;
+        long long i3[3];
+        decode(n, c, i3);
+        const int idx3[3] = {(int)i3[0], (int)i3[1], (int)i3[2]};
         keep = screen_pair(F, c, idx3);
       } else {
         keep = true;
@@ -564,6 +571,7 @@ void launch_tagging(const Geo& g, const Surf& s, const TagBuffers& b, DevState* 
   k_tag_reset<<<num_sms() * 4, 256, 0, st>>>(g, b.cand, b.cap, ds, b.d2min, b.owner, b.flags32);
   k_copy_count<<<1, 1, 0, st>>>(ds);
   if (s.nt > 0) {
+    k_tri_setup<<<(unsigned)((s.nt + 127) / 128), 128, 0, st>>>(g, s);
     const long long blocks = ((long long)s.nt * 32 + 32 * TAG_WARPS - 1) / (32 * TAG_WARPS);
     k_tag_candidates<<<(unsigned)blocks, 32 * TAG_WARPS, 0, st>>>(g, s, b.cand, b.cap, b.d2min, ds);
     const int gb = num_sms() * 8;
