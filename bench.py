@@ -220,6 +220,7 @@ def gpu_arm(args):
             sim.set_surface(dxyz[s], dvel[s])
             sim.step(1)
         sim.sync()
+        tune = sim.autotune(steps=3) if args.autotune else None   # launch shapes (state restored)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
         if world > 1:
             torch.distributed.barrier()
@@ -262,8 +263,9 @@ def gpu_arm(args):
             e2e_ms += (time.perf_counter() - t0) * 1e3
             d2h = dd["d2h_bytes"]
         results[prec] = dict(ms=ms, diag=diag, prof=prof, e2e_ms=e2e_ms, e2e_steps=ke, d2h=d2h,
-                             clocks=clk.summary())
+                             clocks=clk.summary(), tune=tune)
         sim.close()
+    batched = None if (args.only_headline or args.no_batch) else batched_leg(args, dev, stream, flush, world)
     if rank != 0:
         return None
     head = results[args.precision]
@@ -324,7 +326,9 @@ def gpu_arm(args):
     }
     for prec, r in results.items():
         line[prec] = {"value": world * cells * K / (r["ms"] / 1e3) / 1e9, "ms_per_step": r["ms"] / K,
-                      "slip_l1": r["diag"]["slip_l1"], "clocks": r["clocks"]}
+                      "slip_l1": r["diag"]["slip_l1"], "clocks": r["clocks"], "tune": r["tune"]}
+    if batched is not None:
+        line["batched"] = batched
     if "mixed" in results and "fp64" in results:
         sm, sf = results["mixed"]["diag"]["slip_l1"], results["fp64"]["diag"]["slip_l1"]
         line["slip_rel_diff_mixed_vs_fp64"] = abs(sm - sf) / sf if sf else None
@@ -332,6 +336,77 @@ def gpu_arm(args):
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_steps)
     return line
+
+
+def batched_leg(args, dev, stream, flush, world):
+    """The uneven batch (32 instances, sizes from {32, 48, 64, 96}^3, FP32
+    bulk): GCUPS of the batched step (one launch per kernel for all
+    instances, one graph per step) against the same instances stepped one
+    by one; each step's surfaces are uploaded from device-resident arrays
+    inside the timed region in both cases."""
+    import torch
+    from paper_2606_09799_gb300 import ibm, inputs
+
+    K, W = max(3, min(args.steps, args.batch_steps)), max(3, args.warmup)
+    wls = inputs.batched_instances(steps=W + K)
+    cells = sum(w.cells for w in wls)
+    surf = [[w.surface(s) for s in range(W + K)] for w in wls]
+    dsurf = [[(torch.from_numpy(x).to(dev), torch.from_numpy(v).to(dev)) for x, v in ss] for ss in surf]
+
+    def make():
+        sims = []
+        for w, ss in zip(wls, surf):
+            g = ibm.Simulation(w.nx, w.ny, w.nz, w.lx, w.ly, w.lz, re=w.re, dt=w.dt, precision="mixed",
+                               stream=stream.cuda_stream)
+            g.set_surface(ss[0][0], ss[0][1], w.tri)
+            sims.append(g)
+        return sims
+
+    def timed(sims, step_all):
+        for s in range(W):
+            for g, ds in zip(sims, dsurf):
+                g.set_surface(*ds[s])
+            step_all()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        with ClockSampler(dist_env()[2]) as clk:
+            for n in range(K):
+                flush.fill_(n & 0xFF)
+                ev[n][0].record(stream)
+                for g, ds in zip(sims, dsurf):
+                    g.set_surface(*ds[W + n])
+                step_all()
+                ev[n][1].record(stream)
+            torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev), clk.summary()
+
+    sims = make()
+    b = ibm.Batch(sims, stream=stream.cuda_stream)
+    for g, ds in zip(sims, dsurf):
+        g.set_surface(*ds[0])
+    tune = b.autotune(steps=2) if args.autotune else None
+    ms_b, clk_b = timed(sims, lambda: b.step(1))
+    b.sync()
+    info = b.info()
+    prof = b.profile_stages(1)
+    slip = sum(g.diag()["slip_l1"] for g in sims) / len(sims)
+    b.close()
+    for g in sims:
+        g.close()
+    sims = make()
+    ms_s, clk_s = timed(sims, lambda: [g.step(1) for g in sims])
+    for g in sims:
+        g.sync()
+        g.close()
+    return {"workload": f"batch32: {len(wls)} instances, nx, ny, nz each from {{32,48,64,96}} (seed 4), "
+                        f"one sphere/cube/disc each (500-5000 triangles) translating sinusoidally; "
+                        f"Re in [50,500]; FP32 bulk", "instances": len(wls), "cells": cells,
+            "steps": K, "warmup": W, "value": world * cells * K / (ms_b / 1e3) / 1e9, "unit": UNIT,
+            "ms_per_step": ms_b / K, "solo_value": world * cells * K / (ms_s / 1e3) / 1e9,
+            "solo_ms_per_step": ms_s / K, "speedup_vs_solo": ms_s / ms_b,
+            "launches_per_step": info["launches_per_step"], "launches_per_step_solo": info["launches_per_step_solo"],
+            "tune": tune, "slip_l1_mean": slip, "clocks": clk_b, "clocks_solo": clk_s,
+            "stages_ms_per_step": {k: v[0] for k, v in prof.items() if v[1] > 0}}
 
 
 def cpu_baseline(nsteps: int):
@@ -398,6 +473,10 @@ def main():
     ap.add_argument("--profile-steps", type=int, default=5)
     ap.add_argument("--cpu-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="keep the built-in launch shapes (no autotuning before timing)")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-instances leg")
+    ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--fp64-peak-tflops", type=float, default=1.0,
                     help="measured FP64 FMA throughput of this GB300")
     args = ap.parse_args()

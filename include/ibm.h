@@ -207,6 +207,83 @@ ibm_status ibm_tag_noalloc(const ibm_grid_desc* desc, int nverts, const double* 
                            const int32_t* tri, int32_t* owner_u, int32_t* owner_v, int32_t* owner_w,
                            void* stream);
 
+/* ---- launch-shape tuning ------------------------------------------------
+ * Choices of how the kernels of a step are laid out on the GPU; they change
+ * the speed, never the method (the wall-normal Thomas variants differ in
+ * rounding order only).  0 in any field means the built-in heuristic. */
+typedef struct {
+  int tri_y;          /* per-wavenumber Thomas in y: 1 warp-cooperative scan, 2 one thread per real or
+                         imaginary part */
+  int sweep_w;        /* grid lines per block of the z and y sweeps: 16, 32 or 64 */
+  int fft_lpb;        /* complex lines per block of the x transforms (capped by shared memory) */
+  int fft_cols;       /* kx columns per block of the z transforms: a power of two up to 16 */
+  double ms_per_step; /* set by the autotuners: measured time per step of the chosen shapes */
+} ibm_tune;
+
+/* Use tuning `t` from the next step on (IBM_ERR_ARG if a field is out of range). */
+ibm_status ibm_set_tune(ibm_handle h, const ibm_tune* t);
+ibm_status ibm_get_tune(ibm_handle h, ibm_tune* t);
+
+/* Autotuner: times whole steps (CUDA events, `steps` per candidate after one
+ * untimed step) for every value of one choice at a time, keeping the others
+ * at their best so far, and keeps the fastest.  The simulation state (fields,
+ * non-linear terms, device scalars) is saved before and restored after, so
+ * the trial steps leave no trace; the tagging state is rebuilt at the next
+ * step.  Writes the choice to *chosen (may be NULL).  Synchronises. */
+ibm_status ibm_autotune(ibm_handle h, int steps, ibm_tune* chosen);
+
+/* ---- batches of independent simulations ---------------------------------
+ * The paper's method advances one simulation; these entry points (no
+ * counterpart in the paper) advance many independent ones -- uneven grid
+ * sizes, each with its own bodies, Re and dt -- together: every launch of
+ * the time step becomes ONE kernel launch over all instances (the blocks of
+ * the instances' grids concatenated), and one CUDA graph holds a whole step
+ * of the batch.  Each instance computes exactly what ibm_step computes for
+ * it alone with the same launch shapes.
+ *
+ * The instances must share precision, scheme and use_q and live on one
+ * device (else IBM_ERR_ARG).  Launch shapes (tiles, FFT lines per block,
+ * Thomas variant) follow the largest extent of each axis over the batch.
+ * The batch keeps the handle pointers, not copies: destroy a batch before
+ * any of its handles.  Surfaces, fields and body forces are set per handle
+ * as usual (ibm_set_surface, ...) on the handle's own stream; the batch's
+ * stream waits for every handle's stream before a step, and every handle's
+ * stream waits for the batch after it, so per-handle calls and batch steps
+ * are ordered as issued.  A changed surface size or reallocated work list
+ * rebuilds the batch's graph at its next step.  Device errors of an
+ * instance are reported by ibm_batch_sync (or the handle's own synchronising
+ * calls). */
+typedef struct ibm_batch* ibm_batch_handle;
+
+typedef struct {
+  int64_t instances;
+  int64_t cells;                   /* sum of the instances' cells */
+  int64_t launches_per_step;       /* kernel launches of one batched step */
+  int64_t launches_per_step_solo;  /* kernel launches if each instance stepped alone */
+  int32_t shape[3];                /* nx, ny, nz that choose the launch shapes */
+} ibm_batch_info;
+
+ibm_status ibm_batch_create(const ibm_handle* hs, int n, void* stream, ibm_batch_handle* out);
+ibm_status ibm_batch_destroy(ibm_batch_handle b);
+/* nsteps steps of every instance; asynchronous on the batch's stream. */
+ibm_status ibm_batch_step(ibm_batch_handle b, int nsteps);
+/* Waits for the batch and checks every instance's device error word; on an
+ * error returns the first instance's status (ibm_batch_last_error says which). */
+ibm_status ibm_batch_sync(ibm_batch_handle b);
+ibm_status ibm_batch_get_info(ibm_batch_handle b, ibm_batch_info* out);
+/* ibm_profile_stages for the batched step (summed over the instances). */
+ibm_status ibm_batch_profile_stages(ibm_batch_handle b, int nsteps, double* ms, int64_t* kernels);
+ibm_status ibm_batch_set_tune(ibm_batch_handle b, const ibm_tune* t);
+/* ibm_autotune for the batched step (state of every instance saved and restored). */
+ibm_status ibm_batch_autotune(ibm_batch_handle b, int steps, ibm_tune* chosen);
+const char* ibm_batch_last_error(ibm_batch_handle b);
+
+/* One-call form: steps the n handles together, keeping one batch per
+ * distinct handle list (created on first use on hs[0]'s stream, released
+ * with ibm_destroy of any of its handles).  Errors are also described by
+ * ibm_last_error(hs[0]). */
+ibm_status ibm_step_batch(const ibm_handle* hs, int n, int nsteps);
+
 /* Library version string. */
 const char* ibm_version(void);
 

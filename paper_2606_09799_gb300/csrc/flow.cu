@@ -77,10 +77,10 @@ __device__ inline void forcing_geometry(const Geo& g, const Surf& s, unsigned ke
 // Eq. new_IB for every forcing node, reading u^e from the unmodified state
 // (a snapshot: the values are written by a second kernel).
 template <typename T>
-__global__ void k_ib_force(Geo g, Surf s, Fields<T> f, const ForceNode* __restrict__ flist, unsigned cap,
+__device__ __forceinline__ void ib_force(const Blk& bk, const Geo& g, const Surf& s, const Fields<T>& f, const ForceNode* __restrict__ flist, unsigned cap,
                            DevState* ds) {
   const unsigned n = min(ds->nforce_c[0] + ds->nforce_c[1] + ds->nforce_c[2], cap);
-  for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+  for (unsigned e = bk.x * blockDim.x + threadIdx.x; e < n; e += bk.gx * blockDim.x) {
     const ForceNode fn = flist[e];
     const int c = (int)(fn.key >> 30);
     NodeGeom ng;
@@ -102,25 +102,45 @@ __global__ void k_ib_force(Geo g, Surf s, Fields<T> f, const ForceNode* __restri
     f.uf[e] = (T)uf;
   }
 }
+template <typename T>
+struct IbForce {
+  static constexpr int kThreads = 128;
+  Geo g;
+  Surf s;
+  Fields<T> f;
+  const ForceNode* flist;
+  unsigned cap;
+  DevState* ds;
+  __device__ __forceinline__ void operator()(const Blk& bk) const { ib_force<T>(bk, g, s, f, flist, cap, ds); }
+};
 
 template <typename T>
-__global__ void k_ib_scatter(Fields<T> f, const ForceNode* __restrict__ flist, unsigned cap, const DevState* ds) {
+__device__ __forceinline__ void ib_scatter(const Blk& bk, const Fields<T>& f, const ForceNode* __restrict__ flist, unsigned cap, const DevState* ds) {
   const unsigned n = min(ds->nforce_c[0] + ds->nforce_c[1] + ds->nforce_c[2], cap);
-  for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+  for (unsigned e = bk.x * blockDim.x + threadIdx.x; e < n; e += bk.gx * blockDim.x) {
     const ForceNode fn = flist[e];
     const int c = (int)(fn.key >> 30);
     comp_ptr(f, c)[fn.key & KEY_MASK] = f.uf[e];
     if (f.lo[c]) f.lo[c][fn.key & KEY_MASK] = (T)0;
   }
 }
+template <typename T>
+struct IbScatter {
+  static constexpr int kThreads = 256;
+  Fields<T> f;
+  const ForceNode* flist;
+  unsigned cap;
+  const DevState* ds;
+  __device__ __forceinline__ void operator()(const Blk& bk) const { ib_scatter<T>(bk, f, flist, cap, ds); }
+};
 
 template <typename T>
 void launch_ib_force(const Geo& g, const Surf& s, const Fields<T>& f, const TagBuffers& b, DevState* ds,
-                     cudaStream_t st) {
-  const int gb = num_sms() * 4;
-  stage_mark(st, ST_FORCE);
-  k_ib_force<T><<<gb, 128, 0, st>>>(g, s, f, b.flist, b.cap, ds);
-  k_ib_scatter<T><<<gb, 256, 0, st>>>(f, b.flist, b.cap, ds);
+                     Exec& ex) {
+  const dim3 gb = grid_if(s.nt > 0, dim3(num_sms() * 4));
+  ex.mark(ST_FORCE);
+  ex.launch(gb, dim3(128), 0, IbForce<T>{g, s, f, b.flist, b.cap, ds});
+  ex.launch(gb, dim3(256), 0, IbScatter<T>{f, b.flist, b.cap, ds});
 }
 
 // ---------------------------------------------------------------------------
@@ -144,7 +164,7 @@ struct RhsCoef {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(128) k_rhs(Geo g, Fields<T> f, const unsigned* __restrict__ flags32, RhsCoef<T> cf,
+__device__ __forceinline__ void rhs(const Blk& bk, const Geo& g, const Fields<T>& f, const unsigned* __restrict__ flags32, const RhsCoef<T>& cf,
                                              int use_hp, int write_h, const DevState* ds) {
   const int nx = g.nx, ny = g.ny, nz = g.nz;
   const T idx = cf.idx, idy = cf.idy, idz = cf.idz;
@@ -160,9 +180,9 @@ __global__ void __launch_bounds__(128) k_rhs(Geo g, Fields<T> f, const unsigned*
   const T* __restrict__ W = f.w;
   const T* __restrict__ P = f.p;
   {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = blockIdx.z;
+    const int i = bk.x * blockDim.x + threadIdx.x;
+    const int j = bk.y * blockDim.y + threadIdx.y;
+    const int k = bk.z;
     if (i >= nx || j >= ny) return;
     const long long cell = (long long)k * pu + (long long)j * nx + i;
     const int ip = i + 1 == nx ? 0 : i + 1, im = i == 0 ? nx - 1 : i - 1;
@@ -247,10 +267,22 @@ __global__ void __launch_bounds__(128) k_rhs(Geo g, Fields<T> f, const unsigned*
     }
   }
 }
+template <typename T>
+struct Rhs {
+  static constexpr int kThreads = 128;
+  Geo g;
+  Fields<T> f;
+  const unsigned* flags32;
+  RhsCoef<T> cf;
+  int use_hp;
+  int write_h;
+  const DevState* ds;
+  __device__ __forceinline__ void operator()(const Blk& bk) const { rhs<T>(bk, g, f, flags32, cf, use_hp, write_h, ds); }
+};
 
 template <typename T>
 void launch_rhs(const Geo& g, const Fields<T>& f, const TagBuffers& b, const Stage& sg, double dt, double re,
-                bool use_hp, bool write_h, DevState* ds, cudaStream_t st) {
+                bool use_hp, bool write_h, DevState* ds, Exec& ex) {
   RhsCoef<T> cf;
   cf.idx = (T)g.idx; cf.idy = (T)g.idy; cf.idz = (T)g.idz;
   cf.idx2 = (T)(g.idx * g.idx); cf.idy2 = (T)(g.idy * g.idy); cf.idz2 = (T)(g.idz * g.idz);
@@ -258,9 +290,9 @@ void launch_rhs(const Geo& g, const Fields<T>& f, const TagBuffers& b, const Sta
   cf.cg = (T)sg.gam; cf.cr = (T)sg.rho; cf.ca = (T)sg.alp; cf.cv = (T)(sg.alp / re);
   cf.dt = (T)dt;
   cf.fba = (T)sg.alp;
-  stage_mark(st, ST_RHS);
-  k_rhs<T><<<dim3((g.nx + 31) / 32, (g.ny + 3) / 4, g.nz), dim3(32, 4), 0, st>>>(g, f, b.flags32, cf, use_hp ? 1 : 0,
-                                                                               write_h ? 1 : 0, ds);
+  ex.mark(ST_RHS);
+  ex.launch(dim3((g.nx + 31) / 32, (g.ny + 3) / 4, g.nz), dim3(32, 4), 0,
+            Rhs<T>{g, f, b.flags32, cf, use_hp ? 1 : 0, write_h ? 1 : 0, ds});
 }
 
 // ---------------------------------------------------------------------------
@@ -420,15 +452,15 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // blockIdx.y) in shared memory, loaded and stored row by row (coalesced);
 // thread t solves line t.  Tile [W][nx+1] of T, then [W][nx] flag bytes.
 template <typename T>
-__global__ void __launch_bounds__(64) k_sweep_x(Geo g, Fields<T> f, const unsigned* __restrict__ flags32,
-                                                SweepTables<T> tb, const int* __restrict__ lfirst) {
+__device__ __forceinline__ void sweep_x(const Blk& bk, const Geo& g, const Fields<T>& f, const unsigned* __restrict__ flags32,
+                                                const SweepTables<T>& tb, const int* __restrict__ lfirst) {
   extern __shared__ unsigned char smem_raw[];
   const int W = blockDim.x, t = threadIdx.x;
-  const int c = blockIdx.y;
+  const int c = bk.y;
   const int n = g.nx, ld = n + 1;
   const int j0 = c == 1 ? 1 : 0, nj = c == 1 ? g.ny - 1 : g.ny;
   const int nlines = nj * g.nz;
-  const int l0 = blockIdx.x * W;
+  const int l0 = bk.x * W;
   T* tile = reinterpret_cast<T*>(smem_raw);
   unsigned char* fl = reinterpret_cast<unsigned char*>(tile + (size_t)W * ld);
   T* __restrict__ R = f.R[c];
@@ -465,6 +497,16 @@ __global__ void __launch_bounds__(64) k_sweep_x(Geo g, Fields<T> f, const unsign
     for (int i = t; i < n; i += W) R[base + i] = tile[r * ld + i];
   }
 }
+template <typename T>
+struct SweepX {
+  static constexpr int kThreads = 64;
+  Geo g;
+  Fields<T> f;
+  const unsigned* flags32;
+  SweepTables<T> tb;
+  const int* lfirst;
+  __device__ __forceinline__ void operator()(const Blk& bk) const { sweep_x<T>(bk, g, f, flags32, tb, lfirst); }
+};
 
 // x-sweep, one warp per line: lane l holds rows [l K, l K + K) of the line
 // (K = ceil(nx/32)) in registers, loaded coalesced.  Both Thomas passes are
@@ -503,13 +545,13 @@ __device__ __forceinline__ AffMap<T> scan_down_excl(AffMap<T> m, int lane) {
 }
 
 template <typename T, int K>
-__global__ void __launch_bounds__(256) k_sweep_x_warp(Geo g, Fields<T> f, const unsigned* __restrict__ flags32,
-                                                      SweepTables<T> tb, const int* __restrict__ lfirst) {
+__device__ __forceinline__ void sweep_x_warp(const Blk& bk, const Geo& g, const Fields<T>& f, const unsigned* __restrict__ flags32,
+                                                      const SweepTables<T>& tb, const int* __restrict__ lfirst) {
   const int lane = threadIdx.x & 31;
-  const int c = blockIdx.y;
+  const int c = bk.y;
   const int n = g.nx;
   const int j0 = c == 1 ? 1 : 0, nj = c == 1 ? g.ny - 1 : g.ny;
-  const int l = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int l = bk.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (l >= nj * g.nz) return;
   const int j = j0 + l % nj, k = l / nj;
   const long long base = fidx(g, c, 0, j, k);
@@ -650,6 +692,16 @@ __global__ void __launch_bounds__(256) k_sweep_x_warp(Geo g, Fields<T> f, const 
     if (!idn[u]) R[base + rr[u]] = yn;
   }
 }
+template <typename T, int K>
+struct SweepXWarp {
+  static constexpr int kThreads = 256;
+  Geo g;
+  Fields<T> f;
+  const unsigned* flags32;
+  SweepTables<T> tb;
+  const int* lfirst;
+  __device__ __forceinline__ void operator()(const Blk& bk) const { sweep_x_warp<T, K>(bk, g, f, flags32, tb, lfirst); }
+};
 
 // z- and y-sweeps: a block holds the lines of W consecutive i (one plane
 // position each) for all n rows, tile [n][W] (row m of line t at m*W + t);
@@ -657,25 +709,25 @@ __global__ void __launch_bounds__(256) k_sweep_x_warp(Geo g, Fields<T> f, const 
 // (blockIdx.z); dir 1: y-lines at fixed k (blockIdx.z), and the solution du
 // is added to the state (uhat = u^s + du) on the way out.
 template <typename T>
-__global__ void __launch_bounds__(64) k_sweep_zy(Geo g, Fields<T> f, const unsigned* __restrict__ flags32,
-                                                 SweepTables<T> tb, const int* __restrict__ lfirst, int dir) {
+__device__ __forceinline__ void sweep_zy(const Blk& bk, const Geo& g, const Fields<T>& f, const unsigned* __restrict__ flags32,
+                                                 const SweepTables<T>& tb, const int* __restrict__ lfirst, int dir) {
   extern __shared__ unsigned char smem_raw[];
   const int W = blockDim.x, t = threadIdx.x;
-  const int c = blockIdx.y;
-  const int i0 = blockIdx.x * W;
+  const int c = bk.y;
+  const int i0 = bk.x * W;
   const int pl = planes(g, c);
   int n;
   long long base, stride, fbase, fstride;
   if (dir == 2) {
-    if (c == 1 && (int)blockIdx.z >= g.ny - 1) return;   // v has ny-1 interior planes
-    const int j = (c == 1 ? 1 : 0) + blockIdx.z;     // fixed j of these z-lines
+    if (c == 1 && (int)bk.z >= g.ny - 1) return;   // v has ny-1 interior planes
+    const int j = (c == 1 ? 1 : 0) + bk.z;     // fixed j of these z-lines
     n = g.nz;
     base = fidx(g, c, i0, j, 0);
     stride = (long long)pl * g.nx;
     fbase = cidx(g, i0, j, 0);
     fstride = (long long)g.ny * g.nx;
   } else {
-    const int k = blockIdx.z;
+    const int k = bk.z;
     const int jj0 = c == 1 ? 1 : 0;
     n = c == 1 ? g.ny - 1 : g.ny;
     base = fidx(g, c, i0, jj0, k);
@@ -715,11 +767,11 @@ __global__ void __launch_bounds__(64) k_sweep_zy(Geo g, Fields<T> f, const unsig
     auto E = [&](int m) -> T& { return tile[m * W + t]; };
     auto F = [&](int m) { return (int)fl[m * W + t]; };
     if (dir == 2) {
-      const int j = (c == 1 ? 1 : 0) + blockIdx.z;
+      const int j = (c == 1 ? 1 : 0) + bk.z;
       solve_periodic<T>(n, c, lfirst[line_z(g, c, i, j)], 1, -tb.off[2], tb, E, F);
       for (int m = 0; m < n; ++m) R[base + m * stride + t] = tile[m * W + t];
     } else {
-      const int k = blockIdx.z;
+      const int k = bk.z;
       solve_wall<T>(n, c, lfirst[line_y(g, c, i, k)] < g.ny, -tb.off[1], tb, E, F);
       if (f.lo[c]) {
         // velocity state as a (hi, lo) pair: add du without rounding it away
@@ -737,6 +789,17 @@ __global__ void __launch_bounds__(64) k_sweep_zy(Geo g, Fields<T> f, const unsig
     }
   }
 }
+template <typename T>
+struct SweepZY {
+  static constexpr int kThreads = 64;
+  Geo g;
+  Fields<T> f;
+  const unsigned* flags32;
+  SweepTables<T> tb;
+  const int* lfirst;
+  int dir;
+  __device__ __forceinline__ void operator()(const Blk& bk) const { sweep_zy<T>(bk, g, f, flags32, tb, lfirst, dir); }
+};
 
 template <typename T>
 static size_t sweep_smem(int W, int n, int ld, int tiles = 1) {
@@ -751,46 +814,55 @@ static int sweep_width(int n, int tiles = 1) {
   return 16;
 }
 
+template <typename T, int K>
+static void sweep_x_warp(const Geo& g, const Fields<T>& f, const TagBuffers& b, const SweepTables<T>& tb,
+                         Exec& ex) {
+  const int lines = g.ny * g.nz;   // upper bound over components
+  ex.launch(dim3((lines + 7) / 8, 3), dim3(256), 0, SweepXWarp<T, K>{g, f, b.flags32, tb, b.lines.x});
+}
+
+// Launch shapes (lines per block, registers per lane) follow ex.shape, so
+// every instance of a batch uses the same ones; grids follow the instance.
 template <typename T>
-void launch_sweeps(const Geo& g, const Fields<T>& f, const TagBuffers& b, const SweepTables<T>& tb,
-                   cudaStream_t st) {
-  stage_mark(st, ST_SWEEP_X);
-  if (sizeof(T) == 4 && g.nx <= 1024) {
-    const int lines = g.ny * g.nz;   // upper bound over components
-    const dim3 grid((lines + 7) / 8, 3);
-    const int K = (g.nx + 31) / 32;
-    if (K <= 1) k_sweep_x_warp<T, 1><<<grid, 256, 0, st>>>(g, f, b.flags32, tb, b.lines.x);
-    else if (K <= 2) k_sweep_x_warp<T, 2><<<grid, 256, 0, st>>>(g, f, b.flags32, tb, b.lines.x);
-    else if (K <= 3) k_sweep_x_warp<T, 3><<<grid, 256, 0, st>>>(g, f, b.flags32, tb, b.lines.x);
-    else if (K <= 4) k_sweep_x_warp<T, 4><<<grid, 256, 0, st>>>(g, f, b.flags32, tb, b.lines.x);
-    else if (K <= 8) k_sweep_x_warp<T, 8><<<grid, 256, 0, st>>>(g, f, b.flags32, tb, b.lines.x);
-    else if (K <= 16) k_sweep_x_warp<T, 16><<<grid, 256, 0, st>>>(g, f, b.flags32, tb, b.lines.x);
-    else k_sweep_x_warp<T, 32><<<grid, 256, 0, st>>>(g, f, b.flags32, tb, b.lines.x);
+void launch_sweeps(const Geo& g, const Fields<T>& f, const TagBuffers& b, const SweepTables<T>& tb, Exec& ex) {
+  const Geo& sh = ex.shape;
+  ex.mark(ST_SWEEP_X);
+  if (sizeof(T) == 4 && sh.nx <= 1024) {
+    const int K = (sh.nx + 31) / 32;
+    if (K <= 1) sweep_x_warp<T, 1>(g, f, b, tb, ex);
+    else if (K <= 2) sweep_x_warp<T, 2>(g, f, b, tb, ex);
+    else if (K <= 3) sweep_x_warp<T, 3>(g, f, b, tb, ex);
+    else if (K <= 4) sweep_x_warp<T, 4>(g, f, b, tb, ex);
+    else if (K <= 8) sweep_x_warp<T, 8>(g, f, b, tb, ex);
+    else if (K <= 16) sweep_x_warp<T, 16>(g, f, b, tb, ex);
+    else sweep_x_warp<T, 32>(g, f, b, tb, ex);
   } else {
-    const int W = sweep_width<T>(g.nx);
+    const int W = sweep_width<T>(sh.nx);
     const int nlines = g.ny * g.nz;     // upper bound over components (v has ny-1 rows of lines)
-    k_sweep_x<T><<<dim3((nlines + W - 1) / W, 3), W, sweep_smem<T>(W, g.nx, g.nx + 1), st>>>(g, f, b.flags32, tb,
-                                                                                          b.lines.x);
+    ex.launch(dim3((nlines + W - 1) / W, 3), dim3(W), sweep_smem<T>(W, sh.nx, sh.nx + 1),
+              SweepX<T>{g, f, b.flags32, tb, b.lines.x});
   }
-  stage_mark(st, ST_SWEEP_Z);
+  ex.mark(ST_SWEEP_Z);
   {
-    const int W = sweep_width<T>(g.nz);
-    k_sweep_zy<T><<<dim3((g.nx + W - 1) / W, 3, g.ny), W, sweep_smem<T>(W, g.nz, g.nz), st>>>(g, f, b.flags32, tb,
-                                                                                          b.lines.z, 2);
+    int W = sweep_width<T>(sh.nz);
+    if (ex.tune.sweep_w > 0 && ex.tune.sweep_w < W) W = ex.tune.sweep_w;
+    ex.launch(dim3((g.nx + W - 1) / W, 3, g.ny), dim3(W), sweep_smem<T>(W, sh.nz, sh.nz),
+              SweepZY<T>{g, f, b.flags32, tb, b.lines.z, 2});
   }
-  stage_mark(st, ST_SWEEP_Y);
+  ex.mark(ST_SWEEP_Y);
   {
     const int tiles = f.lo[0] ? 3 : 2;
-    const int W = sweep_width<T>(g.ny, tiles);
-    k_sweep_zy<T><<<dim3((g.nx + W - 1) / W, 3, g.nz), W, sweep_smem<T>(W, g.ny, g.ny, tiles), st>>>(
-        g, f, b.flags32, tb, b.lines.y, 1);
+    int W = sweep_width<T>(sh.ny, tiles);
+    if (ex.tune.sweep_w > 0 && ex.tune.sweep_w < W) W = ex.tune.sweep_w;
+    ex.launch(dim3((g.nx + W - 1) / W, 3, g.nz), dim3(W), sweep_smem<T>(W, sh.ny, sh.ny, tiles),
+              SweepZY<T>{g, f, b.flags32, tb, b.lines.y, 1});
   }
 }
 
 template <typename T>
 static void sweep_attrs() {
-  cudaFuncSetAttribute(k_sweep_x<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(k_sweep_zy<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  op_smem_limit<SweepX<T>>(200 * 1024);
+  op_smem_limit<SweepZY<T>>(200 * 1024);
 }
 
 void init_sweep_attributes() {
@@ -807,13 +879,13 @@ void init_sweep_attributes() {
 constexpr int SLIP_BLOCKS = 256, SLIP_THREADS = 256;
 
 template <typename T>
-__global__ void __launch_bounds__(SLIP_THREADS) k_slip_partial(Geo g, Surf s, Fields<T> f,
+__device__ __forceinline__ void slip_partial(const Blk& bk, const Geo& g, const Surf& s, const Fields<T>& f,
                                                                const ForceNode* __restrict__ flist, unsigned cap,
                                                                DevState* ds, double* partial) {
   __shared__ double red[3][SLIP_THREADS];
   const unsigned n = min(ds->nforce_c[0] + ds->nforce_c[1] + ds->nforce_c[2], cap);
   const unsigned per = (n + SLIP_BLOCKS - 1) / SLIP_BLOCKS;
-  const unsigned e0 = blockIdx.x * per, e1 = min(n, e0 + per);
+  const unsigned e0 = bk.x * per, e1 = min(n, e0 + per);
   double acc[3] = {0.0, 0.0, 0.0};
   for (unsigned e = e0 + threadIdx.x; e < e1; e += SLIP_THREADS) {
     const ForceNode fn = flist[e];
@@ -845,10 +917,22 @@ __global__ void __launch_bounds__(SLIP_THREADS) k_slip_partial(Geo g, Surf s, Fi
       for (int c = 0; c < 3; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + w];
     __syncthreads();
   }
-  if (threadIdx.x < 3) partial[blockIdx.x * 3 + threadIdx.x] = red[threadIdx.x][0];
+  if (threadIdx.x < 3) partial[bk.x * 3 + threadIdx.x] = red[threadIdx.x][0];
 }
+template <typename T>
+struct SlipPartial {
+  static constexpr int kThreads = SLIP_THREADS;
+  Geo g;
+  Surf s;
+  Fields<T> f;
+  const ForceNode* flist;
+  unsigned cap;
+  DevState* ds;
+  double* partial;
+  __device__ __forceinline__ void operator()(const Blk& bk) const { slip_partial<T>(bk, g, s, f, flist, cap, ds, partial); }
+};
 
-__global__ void k_slip_final(const double* partial, DevState* ds) {
+__device__ __forceinline__ void slip_final(const Blk& bk, const double* partial, DevState* ds) {
   if (threadIdx.x < 3) {
     double s = 0.0;
     for (int b = 0; b < SLIP_BLOCKS; ++b) s += partial[b * 3 + threadIdx.x];
@@ -856,24 +940,30 @@ __global__ void k_slip_final(const double* partial, DevState* ds) {
     if (!isfinite(s)) atomicOr(&ds->err, ERR_NONFINITE);
   }
 }
+struct SlipFinal {
+  static constexpr int kThreads = 32;
+  const double* partial;
+  DevState* ds;
+  __device__ __forceinline__ void operator()(const Blk& bk) const { slip_final(bk, partial, ds); }
+};
 
 template <typename T>
 void launch_slip(const Geo& g, const Surf& s, const Fields<T>& f, const TagBuffers& b, double* partial,
-                 DevState* ds, cudaStream_t st) {
-  stage_mark(st, ST_SLIP);
-  k_slip_partial<T><<<SLIP_BLOCKS, SLIP_THREADS, 0, st>>>(g, s, f, b.flist, b.cap, ds, partial);
-  k_slip_final<<<1, 32, 0, st>>>(partial, ds);
+                 DevState* ds, Exec& ex) {
+  ex.mark(ST_SLIP);
+  ex.launch(grid_if(s.nt > 0, dim3(SLIP_BLOCKS)), dim3(SLIP_THREADS), 0, SlipPartial<T>{g, s, f, b.flist, b.cap, ds, partial});
+  ex.launch(grid_if(s.nt > 0, dim3(1)), dim3(32), 0, SlipFinal{partial, ds});
 }
 
 #define IBM_INST(T)                                                                                             \
   template void launch_ib_force<T>(const Geo&, const Surf&, const Fields<T>&, const TagBuffers&, DevState*,     \
-                                   cudaStream_t);                                                               \
+                                   Exec&);                                                                      \
   template void launch_rhs<T>(const Geo&, const Fields<T>&, const TagBuffers&, const Stage&, double, double,    \
-                              bool, bool, DevState*, cudaStream_t);                                             \
+                              bool, bool, DevState*, Exec&);                                                    \
   template void launch_sweeps<T>(const Geo&, const Fields<T>&, const TagBuffers&, const SweepTables<T>&,        \
-                                 cudaStream_t);                                                                 \
+                                 Exec&);                                                                        \
   template void launch_slip<T>(const Geo&, const Surf&, const Fields<T>&, const TagBuffers&, double*,           \
-                               DevState*, cudaStream_t);
+                               DevState*, Exec&);
 IBM_INST(double)
 IBM_INST(float)
 #undef IBM_INST

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include "common.cuh"
+#include "exec.cuh"
 
 namespace ibm {
 
@@ -19,7 +20,7 @@ enum StageId {
   ST_TRI_Y, ST_FFT_Z_INV, ST_FFT_X_INV, ST_PROJECT, ST_SLIP, ST_CORRECT, ST_OTHER, ST_COUNT
 };
 // Record the start of stage `id` on stream st when stage timing is active
-// on this thread (no-op otherwise, e.g. during graph capture).
+// on this thread (no-op otherwise).  Launchers call Exec::mark.
 void stage_mark(cudaStream_t st, int id);
 
 // ---- per-line records of forcing nodes (filled by tagging, read by sweeps) -
@@ -48,12 +49,14 @@ struct TagBuffers {
   unsigned long long* d2min;   // per node of the three grids (comp_off layout)
   unsigned* owner;             // per node of the three grids; 0xFFFFFFFF = fluid
   unsigned* flags32;           // per-cell flag bytes packed four to a word
+  unsigned* ub;                // per node of the three grids: FP32 upper bound of the owner's |N|^2 (bits)
+  unsigned* ublist;            // nodes whose ub this step set first (capacity cap)
   unsigned* blk;               // 4 counters per compaction block
   ForceNode* flist;            // forcing nodes, grouped by component, sorted by cell
   unsigned* blist;             // boundary cells, sorted
   LineInfo lines;
 };
-void launch_tagging(const Geo& g, const Surf& s, const TagBuffers& b, DevState* ds, cudaStream_t st);
+void launch_tagging(const Geo& g, const Surf& s, const TagBuffers& b, DevState* ds, Exec& ex);
 int compaction_blocks(const Geo& g);
 
 // ---- tridiagonal coefficient tables (built on the host) -------------------
@@ -110,16 +113,15 @@ struct Fields {
 
 template <typename T>
 void launch_ib_force(const Geo& g, const Surf& s, const Fields<T>& f, const TagBuffers& b, DevState* ds,
-                     cudaStream_t st);
+                     Exec& ex);
 template <typename T>
 void launch_rhs(const Geo& g, const Fields<T>& f, const TagBuffers& b, const Stage& sg, double dt, double re,
-                bool use_hp, bool write_h, DevState* ds, cudaStream_t st);
+                bool use_hp, bool write_h, DevState* ds, Exec& ex);
 template <typename T>
-void launch_sweeps(const Geo& g, const Fields<T>& f, const TagBuffers& b, const SweepTables<T>& tb,
-                   cudaStream_t st);
+void launch_sweeps(const Geo& g, const Fields<T>& f, const TagBuffers& b, const SweepTables<T>& tb, Exec& ex);
 template <typename T>
 void launch_slip(const Geo& g, const Surf& s, const Fields<T>& f, const TagBuffers& b, double* partial,
-                 DevState* ds, cudaStream_t st);
+                 DevState* ds, Exec& ex);
 
 // ---- Poisson and projection (poisson.cu) -----------------------------------
 template <typename T>
@@ -131,8 +133,7 @@ struct SpecTables {
 };
 template <typename T>
 void launch_poisson(const Geo& g, const Fields<T>& f, const TagBuffers& b, const SpecTables<T>& tb,
-                    const Stage& sg, double dt, double re, int use_q, double* partial, DevState* ds,
-                    cudaStream_t st);
+                    const Stage& sg, double dt, double re, int use_q, double* partial, DevState* ds, Exec& ex);
 void launch_build_poisson_tables(const Geo& g, const double* lamx, const double* lamz, double* cp, double* inv,
                                  cudaStream_t st);
 

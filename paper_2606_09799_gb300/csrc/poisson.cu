@@ -188,12 +188,12 @@ __device__ __forceinline__ double div_at(const Geo& g, const T* __restrict__ u, 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(QB_THREADS) k_q_partial(Geo g, Fields<T> f, const unsigned* __restrict__ blist,
+__device__ __forceinline__ void q_partial(const Blk& bk, const Geo& g, const Fields<T>& f, const unsigned* __restrict__ blist,
                                                           unsigned cap, const DevState* ds, double* partial) {
   __shared__ double red[QB_THREADS];
   const unsigned n = min(ds->nbound, cap);
   const unsigned per = (n + QB_BLOCKS - 1) / QB_BLOCKS;
-  const unsigned e0 = blockIdx.x * per, e1 = min(n, e0 + per);
+  const unsigned e0 = bk.x * per, e1 = min(n, e0 + per);
   double acc = 0.0;
   for (unsigned e = e0 + threadIdx.x; e < e1; e += QB_THREADS) {
     const long long cell = blist[e];
@@ -206,10 +206,21 @@ __global__ void __launch_bounds__(QB_THREADS) k_q_partial(Geo g, Fields<T> f, co
     if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
     __syncthreads();
   }
-  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+  if (threadIdx.x == 0) partial[bk.x] = red[0];
 }
+template <typename T>
+struct QPartial {
+  static constexpr int kThreads = QB_THREADS;
+  Geo g;
+  Fields<T> f;
+  const unsigned* blist;
+  unsigned cap;
+  const DevState* ds;
+  double* partial;
+  __device__ __forceinline__ void operator()(const Blk& bk) const { q_partial<T>(bk, g, f, blist, cap, ds, partial); }
+};
 
-__global__ void k_q_final(Geo g, const double* partial, DevState* ds, int s, int use_q) {
+__device__ __forceinline__ void q_final(const Blk& bk, const Geo& g, const double* partial, DevState* ds, int s, int use_q) {
   if (threadIdx.x != 0) return;
   double sum = 0.0;
   for (int b = 0; b < QB_BLOCKS; ++b) sum += partial[b];
@@ -224,6 +235,15 @@ __global__ void k_q_final(Geo g, const double* partial, DevState* ds, int s, int
   ds->qf_lo[s] = (float)(qf - (double)qh);
   if (!isfinite(A)) atomicOr(&ds->err, ERR_NONFINITE);
 }
+struct QFinal {
+  static constexpr int kThreads = 32;
+  Geo g;
+  const double* partial;
+  DevState* ds;
+  int s;
+  int use_q;
+  __device__ __forceinline__ void operator()(const Blk& bk) const { q_final(bk, g, partial, ds, s, use_q); }
+};
 
 // ---------------------------------------------------------------------------
 // forward x transform fused with the right-hand side of Eq. elliptic_mod:
@@ -248,8 +268,8 @@ __device__ __forceinline__ void pair_diff(const T* H, const T* L, long long a, l
 // mode 1: rhs of the correction solve, (D u' - q_F)/(alpha dt) on fluid
 // cells from the projected state held as (hi, lo) pairs, in pair arithmetic
 template <typename T>
-__global__ void k_fft_x_fwd(Geo g, Fields<T> f, const unsigned* __restrict__ flags32, const T* __restrict__ tw,
-                            FftPlan plan, int lines_per_block, const DevState* ds, int s, int use_q,
+__device__ __forceinline__ void fft_x_fwd(const Blk& bk, const Geo& g, const Fields<T>& f, const unsigned* __restrict__ flags32, const T* __restrict__ tw,
+                            const FftPlan& plan, int lines_per_block, const DevState* ds, int s, int use_q,
                             double scale, int mode) {
   using C = typename Cplx<T>::type;
   extern __shared__ unsigned char smem_raw[];
@@ -257,7 +277,7 @@ __global__ void k_fft_x_fwd(Geo g, Fields<T> f, const unsigned* __restrict__ fla
   C* bufb = bufa + lines_per_block * g.nx;
   const int n = g.nx, ny = g.ny;
   const int rows = g.ny * g.nz;
-  const int line0 = blockIdx.x * lines_per_block;
+  const int line0 = bk.x * lines_per_block;
   const T qf = use_q ? (T)ds->qf[s] : (T)0;
   const T sc = (T)scale, idx = (T)g.idx, idy = (T)g.idy, idz = (T)g.idz;
   const long long pu = (long long)ny * n, pv = (long long)(ny + 1) * n;
@@ -332,10 +352,26 @@ __global__ void k_fft_x_fwd(Geo g, Fields<T> f, const unsigned* __restrict__ fla
     if (rb < rows) spec[rb * nkx + kx] = Xb;
   }
 }
+template <typename T>
+struct FftXFwd {
+  static constexpr int kThreads = 256;
+  Geo g;
+  Fields<T> f;
+  const unsigned* flags32;
+  const T* tw;
+  FftPlan plan;
+  int lines_per_block;
+  const DevState* ds;
+  int s;
+  int use_q;
+  double scale;
+  int mode;
+  __device__ __forceinline__ void operator()(const Blk& bk) const { fft_x_fwd<T>(bk, g, f, flags32, tw, plan, lines_per_block, ds, s, use_q, scale, mode); }
+};
 
 // inverse x transform: two half-spectra -> one complex line -> two real rows of phi
 template <typename T>
-__global__ void k_fft_x_inv(Geo g, Fields<T> f, const T* __restrict__ tw, FftPlan plan, int lines_per_block,
+__device__ __forceinline__ void fft_x_inv(const Blk& bk, const Geo& g, const Fields<T>& f, const T* __restrict__ tw, const FftPlan& plan, int lines_per_block,
                             T* __restrict__ out_phi) {
   using C = typename Cplx<T>::type;
   extern __shared__ unsigned char smem_raw[];
@@ -343,7 +379,7 @@ __global__ void k_fft_x_inv(Geo g, Fields<T> f, const T* __restrict__ tw, FftPla
   C* bufb = bufa + lines_per_block * g.nx;
   const int n = g.nx, nkx = g.nkx;
   const long long rows = (long long)g.ny * g.nz;
-  const long long line0 = (long long)blockIdx.x * lines_per_block;
+  const long long line0 = (long long)bk.x * lines_per_block;
   const C* spec = reinterpret_cast<const C*>(f.spec);
   for (int l = threadIdx.y; l < lines_per_block; l += blockDim.y)
   for (int kx = threadIdx.x; kx < n; kx += blockDim.x) {
@@ -372,6 +408,17 @@ __global__ void k_fft_x_inv(Geo g, Fields<T> f, const T* __restrict__ tw, FftPla
     if (rb < rows) out_phi[rb * n + i] = out[t].y;
   }
 }
+template <typename T>
+struct FftXInv {
+  static constexpr int kThreads = 256;
+  Geo g;
+  Fields<T> f;
+  const T* tw;
+  FftPlan plan;
+  int lines_per_block;
+  T* out_phi;
+  __device__ __forceinline__ void operator()(const Blk& bk) const { fft_x_inv<T>(bk, g, f, tw, plan, lines_per_block, out_phi); }
+};
 
 // z transform of the half-spectrum, in place; a block takes `cols` adjacent
 // kx columns of one y-plane (coalesced rows of `cols` complex values), kept
@@ -379,15 +426,15 @@ __global__ void k_fft_x_inv(Geo g, Fields<T> f, const T* __restrict__ tw, FftPla
 // lines (no bank conflicts on load, store or butterflies).  cols is a power
 // of two.
 template <typename T, bool INV>
-__global__ void k_fft_z(Geo g, Fields<T> f, const T* __restrict__ tw, FftPlan plan, int cols) {
+__device__ __forceinline__ void fft_z(const Blk& bk, const Geo& g, const Fields<T>& f, const T* __restrict__ tw, const FftPlan& plan, int cols) {
   using C = typename Cplx<T>::type;
   extern __shared__ unsigned char smem_raw[];
   C* bufa = reinterpret_cast<C*>(smem_raw);
   C* bufb = bufa + cols * g.nz;
   const int n = g.nz, nkx = g.nkx;
   const int ntile = (nkx + cols - 1) / cols;
-  const int j = blockIdx.x / ntile;
-  const int kx0 = (blockIdx.x - j * ntile) * cols;
+  const int j = bk.x / ntile;
+  const int kx0 = (bk.x - j * ntile) * cols;
   const int w = min(cols, nkx - kx0);
   const int lc = __ffs(cols) - 1;
   C* spec = reinterpret_cast<C*>(f.spec);
@@ -406,6 +453,16 @@ __global__ void k_fft_z(Geo g, Fields<T> f, const T* __restrict__ tw, FftPlan pl
     if (c < w) spec[((long long)k * g.ny + j) * nkx + kx0 + c] = out[t];
   }
 }
+template <typename T, bool INV>
+struct FftZ {
+  static constexpr int kThreads = 256;
+  Geo g;
+  Fields<T> f;
+  const T* tw;
+  FftPlan plan;
+  int cols;
+  __device__ __forceinline__ void operator()(const Blk& bk) const { fft_z<T, INV>(bk, g, f, tw, plan, cols); }
+};
 
 // ---------------------------------------------------------------------------
 // Wall-normal Thomas per wavenumber pair (kx, kz), FP64:
@@ -414,12 +471,12 @@ __global__ void k_fft_z(Geo g, Fields<T> f, const T* __restrict__ tw, FftPlan pl
 // mean over j afterwards (zero-mean gauge).  Pivots are tabulated.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(128) k_tri_y(Geo g, Fields<T> f, const double* __restrict__ cp,
+__device__ __forceinline__ void tri_y(const Blk& bk, const Geo& g, const Fields<T>& f, const double* __restrict__ cp,
                                                const double* __restrict__ inv, double* fwd) {
   // one thread per real or imaginary part of a (kx, kz) system: the two
   // share the pivots and are independent
   const int nkx = g.nkx;
-  const long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long l = bk.x * (long long)blockDim.x + threadIdx.x;
   if (l >= 2ll * nkx * g.nz) return;
   const int part = (int)(l & 1);
   const long long mode = l >> 1;
@@ -483,6 +540,16 @@ __global__ void __launch_bounds__(128) k_tri_y(Geo g, Fields<T> f, const double*
     }
   }
 }
+template <typename T>
+struct TriY {
+  static constexpr int kThreads = 128;
+  Geo g;
+  Fields<T> f;
+  const double* cp;
+  const double* inv;
+  double* fwd;
+  __device__ __forceinline__ void operator()(const Blk& bk) const { tri_y<T>(bk, g, f, cp, inv, fwd); }
+};
 
 // Warp-cooperative variant: a warp holds G = 32/L consecutive kx of one kz,
 // L lanes per system, each lane Rr consecutive rows of j in registers (so a
@@ -495,7 +562,7 @@ __global__ void __launch_bounds__(128) k_tri_y(Geo g, Fields<T> f, const double*
 // hand side, 1/pivot, c') before the first use, so the kernel waits for
 // memory once; no forward values leave the registers.
 template <typename T, int L, int Rr>
-__global__ void __launch_bounds__(128) k_tri_y_warp(Geo g, Fields<T> f, const double* __restrict__ cp,
+__device__ __forceinline__ void tri_y_warp(const Blk& bk, const Geo& g, const Fields<T>& f, const double* __restrict__ cp,
                                                     const double* __restrict__ inv) {
   using C = typename Cplx<T>::type;
   constexpr int G = 32 / L;
@@ -503,7 +570,7 @@ __global__ void __launch_bounds__(128) k_tri_y_warp(Geo g, Fields<T> f, const do
   const int sl = lane % L;                      // lane inside its system
   const int nkx = g.nkx, ny = g.ny;
   const int groups_x = (nkx + G - 1) / G;
-  const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long wid = ((long long)bk.x * blockDim.x + threadIdx.x) >> 5;
   if (wid >= (long long)groups_x * g.nz) return;     // whole warps only
   const int kz = (int)(wid / groups_x);
   const int kx = (int)(wid % groups_x) * G + lane / L;
@@ -639,6 +706,15 @@ __global__ void __launch_bounds__(128) k_tri_y_warp(Geo g, Fields<T> f, const do
     spec[base + (long long)j * stride] = o;
   }
 }
+template <typename T, int L, int Rr>
+struct TriYWarp {
+  static constexpr int kThreads = 128;
+  Geo g;
+  Fields<T> f;
+  const double* cp;
+  const double* inv;
+  __device__ __forceinline__ void operator()(const Blk& bk) const { tri_y_warp<T, L, Rr>(bk, g, f, cp, inv); }
+};
 
 // Tabulate the pivots of every (kx, kz) system once per grid.
 __global__ void k_build_tri_tables(Geo g, const double* __restrict__ lamx, const double* __restrict__ lamz,
@@ -689,12 +765,12 @@ struct ProjCoef {
 // mode 2: velocity with the correction phi2 (pairs), pressure with
 //         phi + phi2 (second solve of the mixed path)
 template <typename T>
-__global__ void __launch_bounds__(128) k_project(Geo g, Fields<T> f, ProjCoef<T> cf, int mode) {
+__device__ __forceinline__ void project(const Blk& bk, const Geo& g, const Fields<T>& f, const ProjCoef<T>& cf, int mode) {
   const int nx = g.nx, ny = g.ny, nz = g.nz;
   const long long pu = (long long)ny * nx, pv = (long long)(ny + 1) * nx;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int k = blockIdx.z;
+  const int i = bk.x * blockDim.x + threadIdx.x;
+  const int j = bk.y * blockDim.y + threadIdx.y;
+  const int k = bk.z;
   if (i >= nx || j >= ny) return;
   const int ip = i + 1 == nx ? 0 : i + 1, im = i == 0 ? nx - 1 : i - 1;
   const int kp = k + 1 == nz ? 0 : k + 1, km = k == 0 ? nz - 1 : k - 1;
@@ -737,6 +813,15 @@ __global__ void __launch_bounds__(128) k_project(Geo g, Fields<T> f, ProjCoef<T>
   const T dn = j > 0 ? q0 - PH(r0 - nx + i) : (T)0;
   f.p[r0 + i] += q0 - (cf.bx * (pe - (T)2 * q0 + pw) + cf.by * (up - dn) + cf.bz * (pf - (T)2 * q0 + pb));
 }
+template <typename T>
+struct Project {
+  static constexpr int kThreads = 128;
+  Geo g;
+  Fields<T> f;
+  ProjCoef<T> cf;
+  int mode;
+  __device__ __forceinline__ void operator()(const Blk& bk) const { project<T>(bk, g, f, cf, mode); }
+};
 
 // ---------------------------------------------------------------------------
 // host launcher: the whole elliptic step of one sub-stage
@@ -748,87 +833,89 @@ static int lines_for(int n) {
 
 template <typename T>
 void launch_poisson(const Geo& g, const Fields<T>& f, const TagBuffers& b, const SpecTables<T>& tb,
-                    const Stage& sg, double dt, double re, int use_q, double* partial, DevState* ds,
-                    cudaStream_t st) {
+                    const Stage& sg, double dt, double re, int use_q, double* partial, DevState* ds, Exec& ex) {
   using C = typename Cplx<T>::type;
+  const Geo& sh = ex.shape;
+  const Tune& tu = ex.tune;
   if (use_q) {
-    stage_mark(st, ST_QRED);
-    k_q_partial<T><<<QB_BLOCKS, QB_THREADS, 0, st>>>(g, f, b.blist, b.cap, ds, partial);
-    k_q_final<<<1, 32, 0, st>>>(g, partial, ds, sg.s, use_q);
+    ex.mark(ST_QRED);
+    ex.launch(dim3(QB_BLOCKS), dim3(QB_THREADS), 0, QPartial<T>{g, f, b.blist, b.cap, ds, partial});
+    ex.launch(dim3(1), dim3(32), 0, QFinal{g, partial, ds, sg.s, use_q});
   }
   const double scale = 1.0 / (sg.alp * dt * (double)g.nx * (double)g.nz);
   const FftPlan px = make_plan(g.nx), pz = make_plan(g.nz);
+  // launch shapes from the batch shape (tiles sized for its largest extents)
   int cols = 16;
-  while (cols > 1 && cols * g.nz > 2048) cols >>= 1;
+  while (cols > 1 && cols * sh.nz > 2048) cols >>= 1;
+  if (tu.fft_cols > 0)
+    while (cols > tu.fft_cols) cols >>= 1;
   const int ntile = (g.nkx + cols - 1) / cols;
-  const size_t smz = 2ull * cols * g.nz * sizeof(C);
-  const int lpb = lines_for(g.nx);
+  const size_t smz = 2ull * cols * sh.nz * sizeof(C);
+  int lpb = lines_for(sh.nx);
+  if (tu.fft_lpb > 0 && tu.fft_lpb < lpb) lpb = tu.fft_lpb;
   const long long xlines = ((long long)g.ny * g.nz + 1) / 2;
-  const size_t smx = 2ull * lpb * g.nx * sizeof(C);
-  const int tx = g.nx < 128 ? g.nx : 128;
+  const size_t smx = 2ull * lpb * sh.nx * sizeof(C);
+  const int tx = sh.nx < 128 ? sh.nx : 128;
+  const dim3 xblk(tx, 256 / tx);
+  const dim3 xgrid((unsigned)((xlines + lpb - 1) / lpb));
   const long long tlines = (long long)g.nkx * g.nz;
   double* fwd = sizeof(T) == sizeof(double) ? nullptr : reinterpret_cast<double*>(f.scr);
   // wall-normal Thomas for every (kx, kz): warp-cooperative when the rows fit
   // the registers (16 per lane), else one thread per real/imaginary part
-  auto tri_solve = [&](double* fwdbuf) {
-    if (g.ny <= 8 * 16) {
+  const int tri = tu.tri_y == 2 || sh.ny > 32 * 16 ? 2 : 1;
+  auto tri_solve = [&]() {
+    if (tri == 1 && sh.ny <= 8 * 16) {
       const long long warps = (long long)((g.nkx + 3) / 4) * g.nz;
-      k_tri_y_warp<T, 8, 16><<<(unsigned)((warps * 32 + 127) / 128), 128, 0, st>>>(g, f, tb.cp, tb.inv);
-    } else if (g.ny <= 32 * 16) {
+      ex.launch(dim3((unsigned)((warps * 32 + 127) / 128)), dim3(128), 0, TriYWarp<T, 8, 16>{g, f, tb.cp, tb.inv});
+    } else if (tri == 1) {
       const long long warps = (long long)g.nkx * g.nz;
-      k_tri_y_warp<T, 32, 16><<<(unsigned)((warps * 32 + 127) / 128), 128, 0, st>>>(g, f, tb.cp, tb.inv);
+      ex.launch(dim3((unsigned)((warps * 32 + 127) / 128)), dim3(128), 0, TriYWarp<T, 32, 16>{g, f, tb.cp, tb.inv});
     } else {
-      k_tri_y<T><<<(unsigned)((2 * tlines + 127) / 128), 128, 0, st>>>(g, f, tb.cp, tb.inv, fwdbuf);
+      ex.launch(dim3((unsigned)((2 * tlines + 127) / 128)), dim3(128), 0, TriY<T>{g, f, tb.cp, tb.inv, fwd});
     }
   };
   // the rest of one solve: z transform, wall-normal Thomas, inverse z and x
-  auto solve_rest = [&](T* out) {
-    stage_mark(st, ST_FFT_Z_FWD);
-    k_fft_z<T, false><<<g.ny * ntile, 256, smz, st>>>(g, f, tb.twz, pz, cols);
-    stage_mark(st, ST_TRI_Y);
-    tri_solve(fwd);
-    stage_mark(st, ST_FFT_Z_INV);
-    k_fft_z<T, true><<<g.ny * ntile, 256, smz, st>>>(g, f, tb.twz, pz, cols);
-    stage_mark(st, ST_FFT_X_INV);
-    k_fft_x_inv<T><<<(unsigned)((xlines + lpb - 1) / lpb), dim3(tx, 256 / tx), smx, st>>>(g, f, tb.twx, px, lpb, out);
+  auto solve_rest = [&](T* out, bool marks) {
+    if (marks) ex.mark(ST_FFT_Z_FWD);
+    ex.launch(dim3(g.ny * ntile), dim3(256), smz, FftZ<T, false>{g, f, tb.twz, pz, cols});
+    if (marks) ex.mark(ST_TRI_Y);
+    tri_solve();
+    if (marks) ex.mark(ST_FFT_Z_INV);
+    ex.launch(dim3(g.ny * ntile), dim3(256), smz, FftZ<T, true>{g, f, tb.twz, pz, cols});
+    if (marks) ex.mark(ST_FFT_X_INV);
+    ex.launch(xgrid, xblk, smx, FftXInv<T>{g, f, tb.twx, px, lpb, out});
   };
   const double adt = sg.alp * dt, bb = adt / (2.0 * re);
   ProjCoef<T> cf;
   cf.cx = (T)(adt * g.idx); cf.cy = (T)(adt * g.idy); cf.cz = (T)(adt * g.idz);
   cf.bx = (T)(bb * g.idx * g.idx); cf.by = (T)(bb * g.idy * g.idy); cf.bz = (T)(bb * g.idz * g.idz);
   const dim3 pgrid((g.nx + 31) / 32, (g.ny + 3) / 4, g.nz), pblk(32, 4);
-  stage_mark(st, ST_FFT_X_FWD);
-  k_fft_x_fwd<T><<<(unsigned)((xlines + lpb - 1) / lpb), dim3(tx, 256 / tx), smx, st>>>(g, f, b.flags32, tb.twx, px,
-                                                                                        lpb, ds, sg.s, use_q, scale, 0);
-  solve_rest(f.phi);
+  ex.mark(ST_FFT_X_FWD);
+  ex.launch(xgrid, xblk, smx, FftXFwd<T>{g, f, b.flags32, tb.twx, px, lpb, ds, sg.s, use_q, scale, 0});
+  solve_rest(f.phi, true);
   if (!f.lo[0]) {
-    stage_mark(st, ST_PROJECT);
-    k_project<T><<<pgrid, pblk, 0, st>>>(g, f, cf, 0);
+    ex.mark(ST_PROJECT);
+    ex.launch(pgrid, pblk, 0, Project<T>{g, f, cf, 0});
     return;
   }
   // mixed path: project with the FP32 solve, then solve again for the
   // residual divergence of the projected (hi, lo) state and correct
-  stage_mark(st, ST_PROJECT);
-  k_project<T><<<pgrid, pblk, 0, st>>>(g, f, cf, 1);
-  stage_mark(st, ST_CORRECT);
-  k_fft_x_fwd<T><<<(unsigned)((xlines + lpb - 1) / lpb), dim3(tx, 256 / tx), smx, st>>>(g, f, b.flags32, tb.twx, px,
-                                                                                        lpb, ds, sg.s, use_q, scale, 1);
-  k_fft_z<T, false><<<g.ny * ntile, 256, smz, st>>>(g, f, tb.twz, pz, cols);
-  tri_solve(fwd);
-  k_fft_z<T, true><<<g.ny * ntile, 256, smz, st>>>(g, f, tb.twz, pz, cols);
-  k_fft_x_inv<T><<<(unsigned)((xlines + lpb - 1) / lpb), dim3(tx, 256 / tx), smx, st>>>(g, f, tb.twx, px, lpb,
-                                                                                       f.phi2);
-  k_project<T><<<pgrid, pblk, 0, st>>>(g, f, cf, 2);
+  ex.mark(ST_PROJECT);
+  ex.launch(pgrid, pblk, 0, Project<T>{g, f, cf, 1});
+  ex.mark(ST_CORRECT);
+  ex.launch(xgrid, xblk, smx, FftXFwd<T>{g, f, b.flags32, tb.twx, px, lpb, ds, sg.s, use_q, scale, 1});
+  solve_rest(f.phi2, false);
+  ex.launch(pgrid, pblk, 0, Project<T>{g, f, cf, 2});
 }
 
 template <typename T>
 void set_fft_smem_limits() {
   using C = typename Cplx<T>::type;
   const int maxsm = 2 * 2048 * (int)sizeof(C) + 1024;
-  cudaFuncSetAttribute(k_fft_x_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm);
-  cudaFuncSetAttribute(k_fft_x_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm);
-  cudaFuncSetAttribute(k_fft_z<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm);
-  cudaFuncSetAttribute(k_fft_z<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm);
+  op_smem_limit<FftXFwd<T>>(maxsm);
+  op_smem_limit<FftXInv<T>>(maxsm);
+  op_smem_limit<FftZ<T, false>>(maxsm);
+  op_smem_limit<FftZ<T, true>>(maxsm);
 }
 
 void init_kernel_attributes() {
@@ -838,8 +925,8 @@ void init_kernel_attributes() {
 
 template void launch_poisson<double>(const Geo&, const Fields<double>&, const TagBuffers&,
                                      const SpecTables<double>&, const Stage&, double, double, int, double*,
-                                     DevState*, cudaStream_t);
+                                     DevState*, Exec&);
 template void launch_poisson<float>(const Geo&, const Fields<float>&, const TagBuffers&, const SpecTables<float>&,
-                                    const Stage&, double, double, int, double*, DevState*, cudaStream_t);
+                                    const Stage&, double, double, int, double*, DevState*, Exec&);
 
 }  // namespace ibm

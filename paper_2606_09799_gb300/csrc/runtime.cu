@@ -7,12 +7,14 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 #include <new>
 #include <vector>
 
 #include "../../include/ibm.h"
 #include "common.cuh"
+#include "exec.cuh"
 #include "geometry.cuh"
 #include "launch.h"
 
@@ -91,7 +93,12 @@ __global__ void k_set_force(DevState* ds, double fx, double fy, double fz) {
   ds->fb[2] = fz;
 }
 
-__global__ void k_step_done(DevState* ds) { ds->steps += 1; }
+__device__ __forceinline__ void step_done(const Blk&, DevState* ds) { ds->steps += 1; }
+struct StepDone {
+  static constexpr int kThreads = 32;
+  DevState* ds;
+  __device__ __forceinline__ void operator()(const Blk& bk) const { step_done(bk, ds); }
+};
 
 __global__ void k_aos_to_soa(const double* __restrict__ aos, double* soa, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -183,7 +190,17 @@ struct ibm_grid {
   bool need_full_reset;
   long long steps;
   long long kernels_per_step;
+  long long epoch;        // bumped whenever a captured step of this handle goes stale
+  Tune tune;              // launch-shape choices (autotuner)
 };
+
+// The captured step no longer matches the handle (buffers reallocated,
+// surface sizes or tuning changed): recapture before the next step, and
+// tell every batch holding the handle.
+static void invalidate(ibm_handle h) {
+  h->graph_ok = false;
+  h->epoch += 1;
+}
 
 static void set_err(ibm_handle h, const char* fmt, const char* extra = "") {
   if (h) snprintf(h->err, sizeof(h->err), fmt, extra);
@@ -415,7 +432,7 @@ static int stages(const ibm_grid_desc& d, Stage out[2]) {
 
 // enqueue one full time step on stream st
 template <typename T>
-static void enqueue_step(ibm_handle h, cudaStream_t st) {
+static void enqueue_step(ibm_handle h, Exec& ex) {
   const Geo& g = h->g;
   const Surf s = surface(h);
   const Fields<T> f = fields<T>(h);
@@ -423,17 +440,26 @@ static void enqueue_step(ibm_handle h, cudaStream_t st) {
   const SpecTables<T> sp = spec_tables<T>(h);
   Stage sg[2];
   const int ns = stages(h->desc, sg);
-  launch_tagging(g, s, h->tb, h->ds, st);
+  launch_tagging(g, s, h->tb, h->ds, ex);
   for (int k = 0; k < ns; ++k) {
-    if (s.nt > 0) launch_ib_force<T>(g, s, f, h->tb, h->ds, st);
+    launch_ib_force<T>(g, s, f, h->tb, h->ds, ex);
     const bool use_hp = sg[k].rho != 0.0;
     const bool write_h = (h->desc.scheme == IBM_AB_CN) || (k + 1 < ns);
-    launch_rhs<T>(g, f, h->tb, sg[k], h->desc.dt, h->desc.re, use_hp, write_h, h->ds, st);
-    launch_sweeps<T>(g, f, h->tb, sw, st);
-    launch_poisson<T>(g, f, h->tb, sp, sg[k], h->desc.dt, h->desc.re, h->desc.use_q, h->partial, h->ds, st);
+    launch_rhs<T>(g, f, h->tb, sg[k], h->desc.dt, h->desc.re, use_hp, write_h, h->ds, ex);
+    launch_sweeps<T>(g, f, h->tb, sw, ex);
+    launch_poisson<T>(g, f, h->tb, sp, sg[k], h->desc.dt, h->desc.re, h->desc.use_q, h->partial, h->ds, ex);
   }
-  if (s.nt > 0) launch_slip<T>(g, s, f, h->tb, h->partial, h->ds, st);
-  k_step_done<<<1, 1, 0, st>>>(h->ds);
+  launch_slip<T>(g, s, f, h->tb, h->partial, h->ds, ex);
+  ex.launch(dim3(1), dim3(1), 0, StepDone{h->ds});
+}
+
+// The launch context of one handle stepping alone on stream st.
+static Exec solo_exec(ibm_handle h, cudaStream_t st) {
+  Exec ex;
+  ex.st = st;
+  ex.shape = h->g;
+  ex.tune = h->tune;
+  return ex;
 }
 
 static void release_all(ibm_handle h) {
@@ -453,17 +479,19 @@ static ibm_status alloc_lists(ibm_handle h, unsigned cap) {
   dfree(h, h->tb.cand);
   dfree(h, h->tb.flist);
   dfree(h, h->tb.blist);
+  dfree(h, h->tb.ublist);
   dfree(h, h->uf);
   h->tb.cand = (Cand*)dalloc(h, (size_t)cap * sizeof(Cand));
   h->tb.flist = (ForceNode*)dalloc(h, (size_t)cap * sizeof(ForceNode));
   h->tb.blist = (unsigned*)dalloc(h, (size_t)cap * sizeof(unsigned));
+  h->tb.ublist = (unsigned*)dalloc(h, (size_t)cap * sizeof(unsigned));
   h->uf = dalloc(h, (size_t)cap * h->esize);
-  if (!h->tb.cand || !h->tb.flist || !h->tb.blist || !h->uf) {
+  if (!h->tb.cand || !h->tb.flist || !h->tb.blist || !h->tb.ublist || !h->uf) {
     set_err(h, "device allocation of the work lists failed");
     return IBM_ERR_OOM;
   }
   h->tb.cap = cap;
-  h->graph_ok = false;
+  invalidate(h);
   h->need_full_reset = true;
   return IBM_OK;
 }
@@ -473,6 +501,8 @@ static ibm_status full_reset(ibm_handle h, cudaStream_t st) {
   const long long nall = 2 * g.ncell + g.nvf;
   CK(cudaMemsetAsync(h->tb.d2min, 0xFF, (size_t)nall * 8, st));
   CK(cudaMemsetAsync(h->tb.owner, 0xFF, (size_t)nall * 4, st));
+  CK(cudaMemsetAsync(h->tb.ub, 0xFF, (size_t)nall * 4, st));
+  CK(cudaMemsetAsync(&h->ds->nub, 0, sizeof(unsigned), st));
   CK(cudaMemsetAsync(h->tb.flags32, 0, round16((size_t)(g.ncell + 3) / 4 * 4), st));
   CK(cudaMemsetAsync(h->tb.lines.x, 0x7F, h->tb.lines.bytes, st));
   CK(cudaMemsetAsync(&h->ds->ncand, 0, sizeof(unsigned), st));
@@ -502,12 +532,18 @@ static ibm_status capture(ibm_handle h) {
     if (ls != IBM_OK) return ls;
   }
   CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
-  enqueue_step<T>(h, h->cap);
+  Exec ex = solo_exec(h, h->cap);
+  enqueue_step<T>(h, ex);
   const cudaError_t le = cudaGetLastError();
   cudaGraph_t gr = nullptr;
   cudaError_t e = cudaStreamEndCapture(h->cap, &gr);
-  if (le != cudaSuccess) {
+  if (le != cudaSuccess || ex.first_err != cudaSuccess) {
     if (gr) cudaGraphDestroy(gr);
+    if (ex.first_err != cudaSuccess) {
+      snprintf(h->err, sizeof(h->err), "kernel launch during capture: %s in %.300s",
+               cudaGetErrorString(ex.first_err), ex.first_op);
+      return IBM_ERR_CUDA;
+    }
     return cuda_fail(h, le, "kernel launch during capture");
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "graph capture");
@@ -516,6 +552,395 @@ static ibm_status capture(ibm_handle h) {
   h->graph_ok = true;
   h->kernels_per_step = count_kernel_nodes(gr);
   return IBM_OK;
+}
+
+// Stage timing: one step captured with an (external) event record before
+// every kernel group, replayed nsteps times; ms[stage] accumulates the time
+// between consecutive records, kernels[stage] the number of groups.
+template <class Enqueue>
+static ibm_status profile_graph(Enqueue enqueue, cudaStream_t cap, cudaStream_t run, int nsteps, double* ms,
+                                int64_t* kernels, char* err, size_t errlen) {
+  auto fail = [&](cudaError_t e, const char* what) {
+    snprintf(err, errlen, "%s: %s", what, cudaGetErrorString(e));
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? IBM_ERR_OOM : IBM_ERR_CUDA;
+  };
+  StageTimer* tm = new (std::nothrow) StageTimer();
+  if (!tm) return IBM_ERR_OOM;
+  for (int m = 0; m < StageTimer::MAXM; ++m) {
+    cudaError_t e = cudaEventCreate(&tm->ev[m]);
+    if (e != cudaSuccess) {
+      for (int q = 0; q < m; ++q) cudaEventDestroy(tm->ev[q]);
+      delete tm;
+      return fail(e, "cudaEventCreate");
+    }
+  }
+  double acc[ST_COUNT] = {0};
+  int64_t cnt[ST_COUNT] = {0};
+  ibm_status rc = IBM_OK;
+  cudaGraph_t gr = nullptr;
+  cudaGraphExec_t ex = nullptr;
+  tm->n = 0;
+  t_timer = tm;
+  cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    enqueue(cap);
+    stage_mark(cap, ST_OTHER);
+    e = cudaStreamEndCapture(cap, &gr);
+  }
+  t_timer = nullptr;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, gr, 0);
+  if (e != cudaSuccess) rc = fail(e, "profiling graph");
+  for (int step = 0; step < nsteps && rc == IBM_OK; ++step) {
+    e = cudaGraphLaunch(ex, run);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(run);
+    if (e != cudaSuccess) { rc = fail(e, "profiling step"); break; }
+    for (int m = 0; m + 1 < tm->n && rc == IBM_OK; ++m) {
+      float t = 0.f;
+      e = cudaEventElapsedTime(&t, tm->ev[m], tm->ev[m + 1]);
+      if (e != cudaSuccess) rc = fail(e, "cudaEventElapsedTime");
+      acc[tm->id[m]] += t;
+    }
+  }
+  if (rc == IBM_OK)
+    for (int m = 0; m + 1 < tm->n; ++m) cnt[tm->id[m]] += 1;
+  if (ex) cudaGraphExecDestroy(ex);
+  if (gr) cudaGraphDestroy(gr);
+  for (int m = 0; m < StageTimer::MAXM; ++m) cudaEventDestroy(tm->ev[m]);
+  delete tm;
+  if (rc != IBM_OK) return rc;
+  for (int q = 0; q < ST_COUNT; ++q) {
+    if (ms) ms[q] = acc[q];
+    if (kernels) kernels[q] = cnt[q];
+  }
+  return IBM_OK;
+}
+
+// ---- batches of independent simulations -----------------------------------
+// The step of every instance is recorded launch by launch (Exec::rec) with
+// one launch shape for all (the largest extent of each axis); position p of
+// all instances becomes one grouped launch (k_run_group) whose blocks are
+// the concatenation of the instances' grids.  The ops and block offsets of
+// every position live in one device buffer written once per build; one
+// graph per step replays all positions in order.
+struct ibm_batch {
+  std::vector<ibm_handle> hs;
+  std::vector<long long> epochs;   // handle epochs the graph was built for
+  int device;
+  cudaStream_t user;               // stream the step graph runs on
+  cudaStream_t cap;                // private capture stream
+  cudaEvent_t ev;
+  Allocator al;
+  void* dev;                       // ops + group entries of every position
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+  bool built;
+  Tune tune;
+  Geo shape;
+  long long positions;             // grouped launches per step
+  long long kernels_solo;          // kernel launches per step if stepped one by one
+  char err[512];
+};
+
+static ibm_status bfail(ibm_batch* b, cudaError_t e, const char* what) {
+  snprintf(b->err, sizeof(b->err), "%s: %s", what, cudaGetErrorString(e));
+  cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? IBM_ERR_OOM : IBM_ERR_CUDA;
+}
+
+#define BCK(call)                                             \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return bfail(b, e_, #call);        \
+  } while (0)
+
+static void batch_release(ibm_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  if (b->dev) b->al.put(b->dev);
+  b->dev = nullptr;
+  b->built = false;
+}
+
+// Launch every recorded position of the batch on stream st (used inside a
+// capture).  recs[i] is instance i's launch sequence; layout gives each
+// position's device offsets of its ops and group entries.
+struct BatchLayout {
+  std::vector<size_t> op_off, ge_off;
+  std::vector<unsigned> blocks;
+  std::vector<size_t> smem;
+};
+
+static void batch_enqueue(ibm_batch* b, const std::vector<std::vector<LaunchRec>>& recs, const BatchLayout& L,
+                          cudaStream_t st) {
+  const int n = (int)recs.size();
+  unsigned char* base = static_cast<unsigned char*>(b->dev);
+  for (size_t p = 0; p < recs[0].size(); ++p) {
+    const LaunchRec& r = recs[0][p];
+    if (r.mark >= 0) stage_mark(st, r.mark);
+    if (L.blocks[p] == 0) continue;
+    r.group(base + L.op_off[p], reinterpret_cast<const GroupEntry*>(base + L.ge_off[p]), n, L.blocks[p], r.block,
+            L.smem[p], st);
+  }
+}
+
+template <typename T>
+static ibm_status batch_record(ibm_batch* b, std::vector<std::vector<LaunchRec>>& recs, BatchLayout& L) {
+  const int n = (int)b->hs.size();
+  recs.assign(n, {});
+  for (int i = 0; i < n; ++i) {
+    Exec ex;
+    ex.st = b->cap;
+    ex.rec = &recs[i];
+    ex.shape = b->shape;
+    ex.tune = b->tune;
+    enqueue_step<T>(b->hs[i], ex);
+  }
+  const size_t P = recs[0].size();
+  for (int i = 1; i < n; ++i) {
+    if (recs[i].size() != P) {
+      snprintf(b->err, sizeof(b->err), "instance %d records %zu launches per step, instance 0 %zu", i,
+               recs[i].size(), P);
+      return IBM_ERR_STATE;
+    }
+    for (size_t p = 0; p < P; ++p) {
+      const LaunchRec &a = recs[0][p], &c = recs[i][p];
+      if (a.kind != c.kind || a.block.x != c.block.x || a.block.y != c.block.y || a.block.z != c.block.z ||
+          a.mark != c.mark) {
+        snprintf(b->err, sizeof(b->err), "instance %d differs from instance 0 at launch %zu of the step", i, p);
+        return IBM_ERR_STATE;
+      }
+    }
+  }
+  // device layout: per position the n ops (256-byte aligned) then n entries
+  L.op_off.assign(P, 0);
+  L.ge_off.assign(P, 0);
+  L.blocks.assign(P, 0);
+  L.smem.assign(P, 0);
+  size_t off = 0;
+  for (size_t p = 0; p < P; ++p) {
+    off = (off + 255) & ~(size_t)255;
+    L.op_off[p] = off;
+    off += (size_t)n * recs[0][p].op.size();
+    off = (off + 15) & ~(size_t)15;
+    L.ge_off[p] = off;
+    off += (size_t)n * sizeof(GroupEntry);
+  }
+  std::vector<unsigned char> img(off > 0 ? off : 16, 0);
+  for (size_t p = 0; p < P; ++p) {
+    const size_t osz = recs[0][p].op.size();
+    unsigned long long start = 0;
+    for (int i = 0; i < n; ++i) {
+      const LaunchRec& r = recs[i][p];
+      memcpy(img.data() + L.op_off[p] + (size_t)i * osz, r.op.data(), osz);
+      GroupEntry ge;
+      ge.start = (unsigned)start;
+      ge.gx = r.grid.x;
+      ge.gy = r.grid.y;
+      ge.gz = r.grid.z;
+      memcpy(img.data() + L.ge_off[p] + (size_t)i * sizeof(GroupEntry), &ge, sizeof(ge));
+      start += (unsigned long long)r.grid.x * r.grid.y * r.grid.z;
+      if (r.smem > L.smem[p]) L.smem[p] = r.smem;
+    }
+    if (start > 0x7FFFFFFFull) {
+      snprintf(b->err, sizeof(b->err), "launch %zu of the batch needs %llu blocks (limit 2^31-1)", p, start);
+      return IBM_ERR_ARG;
+    }
+    L.blocks[p] = (unsigned)start;
+    if (L.smem[p] > 48 * 1024) BCK(recs[0][p].set_smem((int)L.smem[p]));
+  }
+  if (b->dev) b->al.put(b->dev);
+  b->dev = b->al.get(img.size());
+  if (!b->dev) {
+    snprintf(b->err, sizeof(b->err), "device allocation of the batch launch table failed");
+    return IBM_ERR_OOM;
+  }
+  BCK(cudaMemcpy(b->dev, img.data(), img.size(), cudaMemcpyHostToDevice));
+  return IBM_OK;
+}
+
+template <typename T>
+static ibm_status batch_build(ibm_batch* b) {
+  if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+  if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+  b->built = false;
+  std::vector<std::vector<LaunchRec>> recs;
+  BatchLayout L;
+  ibm_status s = batch_record<T>(b, recs, L);
+  if (s != IBM_OK) return s;
+  BCK(cudaGetLastError());
+  BCK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+  batch_enqueue(b, recs, L, b->cap);
+  const cudaError_t le = cudaGetLastError();
+  cudaGraph_t gr = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(b->cap, &gr);
+  if (le != cudaSuccess) {
+    if (gr) cudaGraphDestroy(gr);
+    return bfail(b, le, "kernel launch during batch capture");
+  }
+  if (e != cudaSuccess) return bfail(b, e, "batch graph capture");
+  b->graph = gr;
+  BCK(cudaGraphInstantiate(&b->exec, gr, 0));
+  b->positions = count_kernel_nodes(gr);
+  long long solo = 0;
+  for (const auto& r : recs)
+    for (const auto& x : r)
+      if ((unsigned long long)x.grid.x * x.grid.y * x.grid.z > 0) ++solo;
+  b->kernels_solo = solo;
+  for (size_t i = 0; i < b->hs.size(); ++i) b->epochs[i] = b->hs[i]->epoch;
+  b->built = true;
+  return IBM_OK;
+}
+
+static ibm_status batch_prepare(ibm_batch* b) {
+  for (ibm_handle h : b->hs)
+    if (h->need_full_reset) {
+      const ibm_status s = full_reset(h, h->user);
+      if (s != IBM_OK) {
+        snprintf(b->err, sizeof(b->err), "reset of an instance: %s", h->err);
+        return s;
+      }
+    }
+  bool stale = !b->built;
+  for (size_t i = 0; i < b->hs.size() && !stale; ++i) stale = b->epochs[i] != b->hs[i]->epoch;
+  if (!stale) return IBM_OK;
+  return b->hs[0]->esize == 8 ? batch_build<double>(b) : batch_build<float>(b);
+}
+
+// the batch stream waits for every instance's stream (and vice versa after)
+static ibm_status batch_join_in(ibm_batch* b) {
+  for (ibm_handle h : b->hs) {
+    BCK(cudaEventRecord(b->ev, h->user));
+    BCK(cudaStreamWaitEvent(b->user, b->ev, 0));
+  }
+  return IBM_OK;
+}
+static ibm_status batch_join_out(ibm_batch* b) {
+  BCK(cudaEventRecord(b->ev, b->user));
+  for (ibm_handle h : b->hs) BCK(cudaStreamWaitEvent(h->user, b->ev, 0));
+  return IBM_OK;
+}
+
+// handle lists stepped with ibm_step_batch, with their batch
+static std::mutex g_batch_mu;
+static std::vector<ibm_batch*> g_batch_cache;
+
+// ---- autotuning ---------------------------------------------------------------
+// Coordinate search over the launch-shape choices: every candidate value of
+// one knob is timed (whole steps, CUDA events) with the others at their best
+// so far.  The simulation state is saved before and restored after, and the
+// tagging state is rebuilt at the next step.
+struct Knob {
+  int Tune::*field;
+  std::vector<int> values;
+};
+
+static std::vector<Knob> tune_knobs() {
+  return {{&Tune::tri_y, {1, 2}}, {&Tune::sweep_w, {64, 32, 16}}, {&Tune::fft_lpb, {0, 8, 4, 2}},
+          {&Tune::fft_cols, {16, 8, 4}}};
+}
+
+// state a trial step changes that the caller can observe
+struct Snapshot {
+  std::vector<std::pair<void*, size_t>> bufs;
+  void* mem = nullptr;
+};
+
+static ibm_status snapshot_take(ibm_handle h, Snapshot& sn, cudaStream_t st) {
+  const Geo& g = h->g;
+  const size_t es = h->esize;
+  sn.bufs.clear();
+  sn.bufs.push_back({h->u, g.ncell * es});
+  sn.bufs.push_back({h->v, g.nvf * es});
+  sn.bufs.push_back({h->w, g.ncell * es});
+  sn.bufs.push_back({h->p, g.ncell * es});
+  for (int c = 0; c < 3; ++c) {
+    const size_t n = (c == 1 ? g.nvf : g.ncell) * es;
+    sn.bufs.push_back({h->H[c], n});
+    if (h->lo[c]) sn.bufs.push_back({h->lo[c], n});
+  }
+  sn.bufs.push_back({h->ds, sizeof(DevState)});
+  size_t tot = 0;
+  for (auto& b : sn.bufs) tot += round16(b.second);
+  sn.mem = h->al.get(tot);
+  if (!sn.mem) {
+    set_err(h, "%s", "device allocation of the autotuning snapshot failed");
+    return IBM_ERR_OOM;
+  }
+  size_t off = 0;
+  for (auto& b : sn.bufs) {
+    CK(cudaMemcpyAsync((char*)sn.mem + off, b.first, b.second, cudaMemcpyDeviceToDevice, st));
+    off += round16(b.second);
+  }
+  return IBM_OK;
+}
+
+static ibm_status snapshot_restore(ibm_handle h, Snapshot& sn, cudaStream_t st) {
+  size_t off = 0;
+  for (auto& b : sn.bufs) {
+    CK(cudaMemcpyAsync(b.first, (char*)sn.mem + off, b.second, cudaMemcpyDeviceToDevice, st));
+    off += round16(b.second);
+  }
+  CK(cudaStreamSynchronize(st));
+  h->al.put(sn.mem);
+  sn.mem = nullptr;
+  h->need_full_reset = true;   // the sparse tagging reset follows the last trial's candidates
+  return IBM_OK;
+}
+
+static void tune_out(const Tune& t, double ms, ibm_tune* out) {
+  if (!out) return;
+  out->tri_y = t.tri_y;
+  out->sweep_w = t.sweep_w;
+  out->fft_lpb = t.fft_lpb;
+  out->fft_cols = t.fft_cols;
+  out->ms_per_step = ms;
+}
+
+// Time `steps` replays of graph-making function `run_trial` for every
+// candidate; returns the best configuration in `best`.
+template <class Trial>
+static ibm_status autotune_loop(Tune& best, int steps, Trial trial, double* best_ms) {
+  double bms = 0.0;
+  ibm_status s = trial(best, steps, &bms);
+  if (s != IBM_OK) return s;
+  for (const Knob& k : tune_knobs()) {
+    for (int v : k.values) {
+      if (best.*(k.field) == v) continue;
+      Tune cand = best;
+      cand.*(k.field) = v;
+      double ms = 0.0;
+      s = trial(cand, steps, &ms);
+      if (s != IBM_OK) return s;
+      if (ms < bms * 0.995) {
+        bms = ms;
+        best = cand;
+      }
+    }
+  }
+  if (best_ms) *best_ms = bms;
+  return IBM_OK;
+}
+
+// ms per step of `steps` launches of graph exec `ge` on stream st (one
+// untimed launch first)
+static cudaError_t time_graph(cudaGraphExec_t ge, cudaStream_t st, int steps, double* ms) {
+  cudaEvent_t a = nullptr, z = nullptr;
+  cudaError_t e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&z);
+  if (e == cudaSuccess) e = cudaGraphLaunch(ge, st);
+  if (e == cudaSuccess) e = cudaEventRecord(a, st);
+  for (int i = 0; i < steps && e == cudaSuccess; ++i) e = cudaGraphLaunch(ge, st);
+  if (e == cudaSuccess) e = cudaEventRecord(z, st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(z);
+  float t = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, z);
+  *ms = steps > 0 ? t / steps : 0.0;
+  if (a) cudaEventDestroy(a);
+  if (z) cudaEventDestroy(z);
+  return e;
 }
 
 extern "C" {
@@ -605,6 +1030,7 @@ ibm_status ibm_create_grid(const ibm_grid_desc* desc, void* stream, ibm_handle* 
   h->partial = (double*)dalloc(h, 4096 * sizeof(double));
   h->tb.d2min = (unsigned long long*)dalloc(h, nall * 8);
   h->tb.owner = (unsigned*)dalloc(h, nall * 4);
+  h->tb.ub = (unsigned*)dalloc(h, nall * 4);
   h->tb.flags32 = (unsigned*)dalloc(h, round16((size_t)(ncell + 3) / 4 * 4));
   h->tb.blk = (unsigned*)dalloc(h, (size_t)compaction_blocks(g) * 4 * sizeof(unsigned));
   h->bad = (unsigned*)dalloc(h, 16);
@@ -616,8 +1042,8 @@ ibm_status ibm_create_grid(const ibm_grid_desc* desc, void* stream, ibm_handle* 
     h->tb.lines.y = h->tb.lines.x ? h->tb.lines.z + nzl : nullptr;
   }
   void* need[] = {h->u, h->v, h->w, h->p, h->H[0], h->H[1], h->H[2], h->R[0], h->R[1], h->R[2], h->scr,
-                  h->phi, h->spec, h->ds, h->partial, h->tb.d2min, h->tb.owner, h->tb.flags32, h->tb.blk, h->bad,
-                  h->tb.lines.x};
+                  h->phi, h->spec, h->ds, h->partial, h->tb.d2min, h->tb.owner, h->tb.ub, h->tb.flags32, h->tb.blk,
+                  h->bad, h->tb.lines.x};
   for (void* q : need)
     if (!q) {
       release_all(h);
@@ -696,6 +1122,16 @@ ibm_status ibm_create_grid(const ibm_grid_desc* desc, void* stream, ibm_handle* 
 ibm_status ibm_destroy(ibm_handle h) {
   if (!h) return IBM_ERR_ARG;
   cudaStreamSynchronize(h->user);
+  {
+    // batches made by ibm_step_batch that hold this handle go with it
+    std::vector<ibm_batch*> drop;
+    {
+      std::lock_guard<std::mutex> lk(g_batch_mu);
+      for (ibm_batch* b : g_batch_cache)
+        if (std::find(b->hs.begin(), b->hs.end(), h) != b->hs.end()) drop.push_back(b);
+    }
+    for (ibm_batch* b : drop) ibm_batch_destroy(b);
+  }
   release_all(h);
   delete h;
   return IBM_OK;
@@ -734,7 +1170,7 @@ ibm_status ibm_set_surface(ibm_handle h, int nverts, const double* xyz, const do
                            const int32_t* tri, int on_device) {
   if (!h || nverts < 0 || ntris < 0) return IBM_ERR_ARG;
   if (ntris == 0) {
-    if (h->nt != 0) h->graph_ok = false;
+    if (h->nt != 0) invalidate(h);
     h->nt = 0;
     h->nv = 0;
     return IBM_OK;
@@ -767,7 +1203,7 @@ ibm_status ibm_set_surface(ibm_handle h, int nverts, const double* xyz, const do
     h->sx = nsx; h->su = nsu; h->st = nst; h->stage_x = ngx; h->stage_t = ngt; h->trirec = nrec;
     h->nv_cap = nvc;
     h->nt_cap = ntc;
-    h->graph_ok = false;
+    invalidate(h);
   }
   // host-side checks and the candidate-capacity bound
   if (!on_device) {
@@ -830,7 +1266,7 @@ ibm_status ibm_set_surface(ibm_handle h, int nverts, const double* xyz, const do
     k_tri_to_soa<<<(ntris + tb - 1) / tb, tb, 0, st>>>(h->stage_t, h->st, ntris, nverts, h->bad);
   }
   CK(cudaGetLastError());
-  if (nverts != h->nv || ntris != h->nt) h->graph_ok = false;
+  if (nverts != h->nv || ntris != h->nt) invalidate(h);
   h->nv = nverts;
   h->nt = ntris;
   h->has_topology = true;
@@ -999,69 +1435,253 @@ ibm_status ibm_profile_stages(ibm_handle h, int nsteps, double* ms, int64_t* ker
     ibm_status s = full_reset(h, h->user);
     if (s != IBM_OK) return s;
   }
-  StageTimer* tm = new (std::nothrow) StageTimer();
-  if (!tm) return IBM_ERR_OOM;
-  for (int m = 0; m < StageTimer::MAXM; ++m) {
-    cudaError_t e = cudaEventCreate(&tm->ev[m]);
-    if (e != cudaSuccess) {
-      for (int q = 0; q < m; ++q) cudaEventDestroy(tm->ev[q]);
-      delete tm;
-      return cuda_fail(h, e, "cudaEventCreate");
-    }
-  }
-  double acc[ST_COUNT] = {0};
-  int64_t cnt[ST_COUNT] = {0};
-  ibm_status rc = IBM_OK;
-  cudaGraph_t gr = nullptr;
-  cudaGraphExec_t ex = nullptr;
-  // one step captured with an event record before every kernel group
-  tm->n = 0;
-  t_timer = tm;
-  cudaError_t e = cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal);
-  if (e == cudaSuccess) {
-    if (h->esize == 8) enqueue_step<double>(h, h->cap);
-    else enqueue_step<float>(h, h->cap);
-    stage_mark(h->cap, ST_OTHER);
-    e = cudaStreamEndCapture(h->cap, &gr);
-  }
-  t_timer = nullptr;
-  if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, gr, 0);
-  if (e != cudaSuccess) rc = cuda_fail(h, e, "profiling graph");
-  for (int step = 0; step < nsteps && rc == IBM_OK; ++step) {
-    e = cudaGraphLaunch(ex, h->user);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->user);
-    if (e != cudaSuccess) { rc = cuda_fail(h, e, "profiling step"); break; }
-    for (int m = 0; m + 1 < tm->n && rc == IBM_OK; ++m) {
-      float t = 0.f;
-      e = cudaEventElapsedTime(&t, tm->ev[m], tm->ev[m + 1]);
-      if (e != cudaSuccess) rc = cuda_fail(h, e, "cudaEventElapsedTime");
-      acc[tm->id[m]] += t;
-    }
-    h->steps += 1;
-  }
-  if (rc == IBM_OK) {
-    // kernels per group: kernel nodes between consecutive event nodes of one step
-    const long long total = count_kernel_nodes(gr);
-    (void)total;
-    for (int m = 0; m + 1 < tm->n; ++m) cnt[tm->id[m]] += 1;
-  }
-  if (ex) cudaGraphExecDestroy(ex);
-  if (gr) cudaGraphDestroy(gr);
-  for (int m = 0; m < StageTimer::MAXM; ++m) cudaEventDestroy(tm->ev[m]);
-  delete tm;
-  if (rc != IBM_OK) {
-    cudaGetLastError();
-    return rc;
-  }
+  const ibm_status rc = profile_graph(
+      [&](cudaStream_t st) {
+        Exec ex = solo_exec(h, st);
+        if (h->esize == 8) enqueue_step<double>(h, ex);
+        else enqueue_step<float>(h, ex);
+      },
+      h->cap, h->user, nsteps, ms, kernels, h->err, sizeof(h->err));
+  if (rc != IBM_OK) return rc;
+  h->steps += nsteps;
   {
     const ibm_status ls = launch_status(h, "ibm_profile_stages");
     if (ls != IBM_OK) return ls;
   }
-  for (int q = 0; q < ST_COUNT; ++q) {
-    if (ms) ms[q] = acc[q];
-    if (kernels) kernels[q] = cnt[q];
-  }
   return check_device(h);
+}
+
+
+// ---- tuning -------------------------------------------------------------------
+static bool tune_valid(const ibm_tune* t) {
+  if (!t) return false;
+  if (t->tri_y < 0 || t->tri_y > 2) return false;
+  if (t->sweep_w != 0 && t->sweep_w != 16 && t->sweep_w != 32 && t->sweep_w != 64) return false;
+  if (t->fft_lpb < 0 || t->fft_lpb > 2048) return false;
+  if (t->fft_cols < 0 || t->fft_cols > 16 || (t->fft_cols & (t->fft_cols - 1))) return false;
+  return true;
+}
+
+ibm_status ibm_set_tune(ibm_handle h, const ibm_tune* t) {
+  if (!h || !tune_valid(t)) return IBM_ERR_ARG;
+  h->tune = Tune{t->tri_y, t->sweep_w, t->fft_lpb, t->fft_cols};
+  invalidate(h);
+  return IBM_OK;
+}
+
+ibm_status ibm_get_tune(ibm_handle h, ibm_tune* t) {
+  if (!h || !t) return IBM_ERR_ARG;
+  tune_out(h->tune, 0.0, t);
+  return IBM_OK;
+}
+
+ibm_status ibm_autotune(ibm_handle h, int steps, ibm_tune* chosen) {
+  if (!h || steps < 1) return IBM_ERR_ARG;
+  if (h->need_full_reset) {
+    const ibm_status s = full_reset(h, h->user);
+    if (s != IBM_OK) return s;
+  }
+  Snapshot sn;
+  ibm_status s = snapshot_take(h, sn, h->user);
+  if (s != IBM_OK) return s;
+  Tune best = h->tune;
+  double bms = 0.0;
+  s = autotune_loop(best, steps, [&](const Tune& t, int n, double* ms) -> ibm_status {
+    h->tune = t;
+    const ibm_status c = h->esize == 8 ? capture<double>(h) : capture<float>(h);
+    if (c != IBM_OK) return c;
+    const cudaError_t e = time_graph(h->exec, h->user, n, ms);
+    return e == cudaSuccess ? IBM_OK : cuda_fail(h, e, "autotune trial");
+  }, &bms);
+  const ibm_status r = snapshot_restore(h, sn, h->user);
+  if (s != IBM_OK) return s;
+  if (r != IBM_OK) return r;
+  h->tune = best;
+  invalidate(h);
+  tune_out(best, bms, chosen);
+  return launch_status(h, "ibm_autotune");
+}
+
+// ---- batches --------------------------------------------------------------------
+ibm_status ibm_batch_create(const ibm_handle* hs, int n, void* stream, ibm_batch_handle* out) {
+  if (!hs || n < 1 || !out) return IBM_ERR_ARG;
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    if (!hs[i]) return IBM_ERR_ARG;
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return IBM_ERR_ARG;
+    const ibm_grid_desc &a = hs[0]->desc, &c = hs[i]->desc;
+    if (a.precision != c.precision || a.scheme != c.scheme || a.use_q != c.use_q ||
+        hs[0]->device != hs[i]->device)
+      return IBM_ERR_ARG;
+  }
+  ibm_batch* b = new (std::nothrow) ibm_batch();
+  if (!b) return IBM_ERR_OOM;
+  b->hs.assign(hs, hs + n);
+  b->epochs.assign(n, -1);
+  b->device = hs[0]->device;
+  b->user = (cudaStream_t)stream;
+  b->al = hs[0]->al;
+  b->tune = hs[0]->tune;
+  Geo sh = hs[0]->g;
+  for (int i = 1; i < n; ++i) {
+    const Geo& g = hs[i]->g;
+    sh.nx = std::max(sh.nx, g.nx);
+    sh.ny = std::max(sh.ny, g.ny);
+    sh.nz = std::max(sh.nz, g.nz);
+    sh.nkx = std::max(sh.nkx, g.nkx);
+  }
+  b->shape = sh;
+  if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming) != cudaSuccess) {
+    if (b->cap) cudaStreamDestroy(b->cap);
+    cudaGetLastError();
+    delete b;
+    return IBM_ERR_CUDA;
+  }
+  *out = b;
+  return IBM_OK;
+}
+
+ibm_status ibm_batch_destroy(ibm_batch_handle b) {
+  if (!b) return IBM_ERR_ARG;
+  cudaStreamSynchronize(b->user);
+  batch_release(b);
+  if (b->ev) cudaEventDestroy(b->ev);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  {
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    for (size_t i = 0; i < g_batch_cache.size(); ++i)
+      if (g_batch_cache[i] == b) {
+        g_batch_cache.erase(g_batch_cache.begin() + (long)i);
+        break;
+      }
+  }
+  delete b;
+  return IBM_OK;
+}
+
+const char* ibm_batch_last_error(ibm_batch_handle b) { return b ? b->err : "null batch"; }
+
+ibm_status ibm_batch_step(ibm_batch_handle b, int nsteps) {
+  if (!b || nsteps < 0) return IBM_ERR_ARG;
+  ibm_status s = batch_prepare(b);
+  if (s != IBM_OK) return s;
+  s = batch_join_in(b);
+  if (s != IBM_OK) return s;
+  for (int k = 0; k < nsteps; ++k) BCK(cudaGraphLaunch(b->exec, b->user));
+  s = batch_join_out(b);
+  if (s != IBM_OK) return s;
+  for (ibm_handle h : b->hs) h->steps += nsteps;
+  BCK(cudaGetLastError());
+  return IBM_OK;
+}
+
+ibm_status ibm_batch_sync(ibm_batch_handle b) {
+  if (!b) return IBM_ERR_ARG;
+  BCK(cudaStreamSynchronize(b->user));
+  ibm_status first = IBM_OK;
+  for (size_t i = 0; i < b->hs.size(); ++i) {
+    const ibm_status s = ibm_sync(b->hs[i]);
+    if (s != IBM_OK && first == IBM_OK) {
+      first = s;
+      snprintf(b->err, sizeof(b->err), "instance %zu: %s", i, b->hs[i]->err);
+    }
+  }
+  return first;
+}
+
+ibm_status ibm_batch_get_info(ibm_batch_handle b, ibm_batch_info* out) {
+  if (!b || !out) return IBM_ERR_ARG;
+  const ibm_status s = batch_prepare(b);
+  if (s != IBM_OK) return s;
+  memset(out, 0, sizeof(*out));
+  out->instances = (int64_t)b->hs.size();
+  out->launches_per_step = b->positions;
+  out->launches_per_step_solo = b->kernels_solo;
+  for (ibm_handle h : b->hs) out->cells += h->g.ncell;
+  out->shape[0] = b->shape.nx;
+  out->shape[1] = b->shape.ny;
+  out->shape[2] = b->shape.nz;
+  return IBM_OK;
+}
+
+ibm_status ibm_batch_profile_stages(ibm_batch_handle b, int nsteps, double* ms, int64_t* kernels) {
+  if (!b || nsteps < 0) return IBM_ERR_ARG;
+  ibm_status s = batch_prepare(b);
+  if (s != IBM_OK) return s;
+  std::vector<std::vector<LaunchRec>> recs;
+  BatchLayout L;
+  s = b->hs[0]->esize == 8 ? batch_record<double>(b, recs, L) : batch_record<float>(b, recs, L);
+  if (s != IBM_OK) return s;
+  s = batch_join_in(b);
+  if (s != IBM_OK) return s;
+  s = profile_graph([&](cudaStream_t st) { batch_enqueue(b, recs, L, st); }, b->cap, b->user, nsteps, ms, kernels,
+                    b->err, sizeof(b->err));
+  if (s != IBM_OK) return s;
+  for (ibm_handle h : b->hs) h->steps += nsteps;
+  return batch_join_out(b);
+}
+
+ibm_status ibm_batch_set_tune(ibm_batch_handle b, const ibm_tune* t) {
+  if (!b || !tune_valid(t)) return IBM_ERR_ARG;
+  b->tune = Tune{t->tri_y, t->sweep_w, t->fft_lpb, t->fft_cols};
+  b->built = false;
+  return IBM_OK;
+}
+
+ibm_status ibm_batch_autotune(ibm_batch_handle b, int steps, ibm_tune* chosen) {
+  if (!b || steps < 1) return IBM_ERR_ARG;
+  ibm_status s = batch_prepare(b);
+  if (s != IBM_OK) return s;
+  s = batch_join_in(b);
+  if (s != IBM_OK) return s;
+  std::vector<Snapshot> sn(b->hs.size());
+  for (size_t i = 0; i < b->hs.size() && s == IBM_OK; ++i) s = snapshot_take(b->hs[i], sn[i], b->user);
+  Tune best = b->tune;
+  double bms = 0.0;
+  if (s == IBM_OK)
+    s = autotune_loop(best, steps, [&](const Tune& t, int n, double* ms) -> ibm_status {
+      b->tune = t;
+      const ibm_status c = b->hs[0]->esize == 8 ? batch_build<double>(b) : batch_build<float>(b);
+      if (c != IBM_OK) return c;
+      const cudaError_t e = time_graph(b->exec, b->user, n, ms);
+      return e == cudaSuccess ? IBM_OK : bfail(b, e, "autotune trial");
+    }, &bms);
+  ibm_status r = IBM_OK;
+  for (size_t i = 0; i < b->hs.size(); ++i)
+    if (sn[i].mem) {
+      const ibm_status q = snapshot_restore(b->hs[i], sn[i], b->user);
+      if (q != IBM_OK && r == IBM_OK) r = q;
+    }
+  if (s != IBM_OK) return s;
+  if (r != IBM_OK) return r;
+  b->tune = best;
+  b->built = false;
+  tune_out(best, bms, chosen);
+  return batch_join_out(b);
+}
+
+ibm_status ibm_step_batch(const ibm_handle* hs, int n, int nsteps) {
+  if (!hs || n < 1 || nsteps < 0) return IBM_ERR_ARG;
+  ibm_batch* b = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    for (ibm_batch* c : g_batch_cache)
+      if ((int)c->hs.size() == n && std::equal(c->hs.begin(), c->hs.end(), hs)) {
+        b = c;
+        break;
+      }
+  }
+  if (!b) {
+    const ibm_status s = ibm_batch_create(hs, n, hs[0]->user, &b);
+    if (s != IBM_OK) return s;
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    g_batch_cache.push_back(b);
+  }
+  const ibm_status s = ibm_batch_step(b, nsteps);
+  if (s != IBM_OK) snprintf(hs[0]->err, sizeof(hs[0]->err), "ibm_step_batch: %s", b->err);
+  return s;
 }
 
 }  // extern "C"

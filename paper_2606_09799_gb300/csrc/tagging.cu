@@ -15,7 +15,10 @@
 // round-to-nearest operations (no contraction into FMA), in the same order
 // as the textual definition of each quantity, so tags are reproducible
 // bit for bit by any IEEE-754 implementation of the same formulas.
+#include <algorithm>
+
 #include "common.cuh"
+#include "exec.cuh"
 #include "geometry.cuh"
 #include "launch.h"
 
@@ -24,10 +27,11 @@ namespace ibm {
 // ---------------------------------------------------------------------------
 // sparse reset of the per-node state touched by the previous step
 // ---------------------------------------------------------------------------
-__global__ void k_tag_reset(Geo g, const Cand* __restrict__ cand, unsigned cap, DevState* ds,
-                            unsigned long long* d2min, unsigned* owner, unsigned* flags32) {
+__device__ __forceinline__ void tag_reset(const Blk& bk, const Geo& g, const Cand* __restrict__ cand, unsigned cap, DevState* ds,
+                            unsigned long long* d2min, unsigned* owner, unsigned* flags32, unsigned* ub,
+                            const unsigned* __restrict__ ublist) {
   const unsigned n = min(ds->ncand, cap);
-  for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+  for (unsigned e = bk.x * blockDim.x + threadIdx.x; e < n; e += bk.gx * blockDim.x) {
     const Cand cd = cand[e];
     const int c = (int)(cd.key >> 30);
     const long long node = cd.key & KEY_MASK;
@@ -38,7 +42,24 @@ __global__ void k_tag_reset(Geo g, const Cand* __restrict__ cand, unsigned cap, 
     const long long cell = cidx(g, i, j, k);
     atomicAnd(flags32 + (cell >> 2), ~(0xFFu << (8 * (cell & 3))));
   }
+  const unsigned nu = min(ds->nub, cap);
+  for (unsigned e = bk.x * blockDim.x + threadIdx.x; e < nu; e += bk.gx * blockDim.x) ub[ublist[e]] = 0xFFFFFFFFu;
 }
+struct TagReset {
+  static constexpr int kThreads = 256;
+  Geo g;
+  const Cand* cand;
+  unsigned cap;
+  DevState* ds;
+  unsigned long long* d2min;
+  unsigned* owner;
+  unsigned* flags32;
+  unsigned* ub;
+  const unsigned* ublist;
+  __device__ __forceinline__ void operator()(const Blk& bk) const {
+    tag_reset(bk, g, cand, cap, ds, d2min, owner, flags32, ub, ublist);
+  }
+};
 
 // ---------------------------------------------------------------------------
 // Per-triangle set-up, one thread per triangle: closest-point constants,
@@ -47,8 +68,8 @@ __global__ void k_tag_reset(Geo g, const Cand* __restrict__ cand, unsigned cap, 
 // constants reads them here, so they are formed once (FP64 is scarce on
 // this GPU: a warp-wide FP64 instruction costs about 20 SM cycles).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_tri_setup(Geo g, Surf s) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void tri_setup(const Blk& bk, const Geo& g, const Surf& s) {
+  const int t = bk.x * blockDim.x + threadIdx.x;
   if (t >= s.nt) return;
   double A[3], B[3], C[3];
   load_triangle(s, t, A, B, C);
@@ -124,6 +145,12 @@ __global__ void __launch_bounds__(128) k_tri_setup(Geo g, Surf s) {
   F.diag2 = (float)g.diag2;
   s.rec[t] = R;
 }
+struct TriSetup {
+  static constexpr int kThreads = 128;
+  Geo g;
+  Surf s;
+  __device__ __forceinline__ void operator()(const Blk& bk) const { tri_setup(bk, g, s); }
+};
 
 // ---------------------------------------------------------------------------
 // Algorithm 1: one warp per triangle, its lanes spread over the Eulerian
@@ -141,7 +168,8 @@ __global__ void __launch_bounds__(128) k_tri_setup(Geo g, Surf s) {
 // below 1e-4 of the margin's scale (sin^2 > 0.05, edges within 8 cells, cell
 // aspect ratio within 4), else every pair goes to the exact test.  Tags are
 // decided by the FP64 test alone.
-__device__ __forceinline__ bool screen_pair(const TriF32& F, int c, const int idx3[3]) {
+__device__ __forceinline__ void screen_eval(const TriF32& F, int c, const int idx3[3], float& n2, float& lowest,
+                                            float& scale) {
   float p[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
@@ -183,33 +211,56 @@ __device__ __forceinline__ bool screen_pair(const TriF32& F, int c, const int id
   float N[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) N[d] = p[d] - X[d];
-  const float n2 = N[0] * N[0] + N[1] * N[1] + N[2] * N[2];
-  if (n2 > F.diag2 * 1.004f) return false;
+  n2 = N[0] * N[0] + N[1] * N[1] + N[2] * N[2];
   // N . (neighbour - X) = |N|^2 -+ del_d N_d: the smallest over the six
-  float lowest = 3.4e38f, scale = 0.f;
+  lowest = 3.4e38f;
+  scale = 0.f;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     const float t = F.del[d] * fabsf(N[d]);
     lowest = fminf(lowest, n2 - t);
     scale = fmaxf(scale, t);
   }
-  return lowest < 4e-3f * (n2 + scale) + 1e-9f * F.diag2;
 }
+
+// The pair may pass the exact test (false: it certainly fails).
+__device__ __forceinline__ bool screen_maybe(const TriF32& F, float n2, float lowest, float scale) {
+  return !(n2 > F.diag2 * 1.004f) && lowest < 4e-3f * (n2 + scale) + 1e-9f * F.diag2;
+}
+// The pair certainly passes the exact test (the same margins, other side).
+__device__ __forceinline__ bool screen_certain(const TriF32& F, float n2, float lowest, float scale) {
+  return n2 <= F.diag2 * 0.996f && lowest < -(4e-3f * (n2 + scale) + 1e-9f * F.diag2);
+}
+// Bounds of the exact |N|^2 from the FP32 one: the FP32 error of |N|^2 is
+// below 1e-4 diag^2 wherever the screen runs (see above); the bounds leave
+// 4e-3 relative plus 1e-3 diag^2.
+__device__ __forceinline__ float n2_upper(const TriF32& F, float n2) { return n2 * 1.004f + 1e-3f * F.diag2; }
+__device__ __forceinline__ float n2_lower(const TriF32& F, float n2) { return n2 * 0.996f - 1e-3f * F.diag2; }
 
 constexpr int TAG_WARPS = 4;
 
-__global__ void __launch_bounds__(32 * TAG_WARPS) k_tag_candidates(Geo g, Surf s, Cand* __restrict__ cand,
-                                                                   unsigned cap, unsigned long long* d2min,
-                                                                   DevState* ds) {
+// The owner of a node is the qualifying pair of smallest |N|^2, so a pair
+// whose |N|^2 certainly exceeds that of a pair that certainly qualifies
+// can neither own the node nor change whether it is tagged.  Phase 0 folds
+// an upper bound of |N|^2 of every certainly-qualifying pair (FP32 screen)
+// into a per-node word `ub` (first touches listed in `ublist` for the sparse
+// reset); phase 1 sends to the exact FP64 test only the pairs that may
+// qualify and whose lower bound does not exceed the node's `ub` -- the
+// owner and every pair tied with it always among them.
+template <int PHASE>
+__device__ __forceinline__ void tag_pairs(const Blk& bk, const Geo& g, const Surf& s, Cand* __restrict__ cand,
+                                          unsigned cap, unsigned long long* d2min, unsigned* __restrict__ ub,
+                                          unsigned* __restrict__ ublist, DevState* ds) {
   __shared__ long long queue[TAG_WARPS][64];
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-  const long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long t = ((long long)bk.x * blockDim.x + threadIdx.x) >> 5;
   if (t >= s.nt) return;
   const TriRec* __restrict__ rec = s.rec + t;
   const long long cnt0 = rec->cnt[0], cnt1 = rec->cnt[1], cnt2 = rec->cnt[2];
   const long long total = cnt0 + cnt1 + cnt2;
   if (total == 0) return;
   const bool screen = rec->screen != 0;
+  if (PHASE == 0 && !screen) return;   // no FP32 bound without the screen
   const double del[3] = {g.dx, g.dy, g.dz};
   int n0[3][3], ext[3][3];
 #pragma unroll
@@ -316,6 +367,42 @@ __global__ void __launch_bounds__(32 * TAG_WARPS) k_tag_candidates(Geo g, Surf s
   };
   TriF32 F;
   if (screen) F = rec->f;
+  // index of a lattice point in the comp_off layout of the three grids
+  auto node_of = [&](int c, const long long i3[3]) -> unsigned {
+    return (unsigned)(comp_off(g, c) + fidx(g, c, wrapi(i3[0], g.nx), i3[1], wrapi(i3[2], g.nz)));
+  };
+  if (PHASE == 0) {
+    for (long long base = 0; base < total; base += 32) {
+      const long long n = base + lane;
+      bool first = false;
+      unsigned ni = 0;
+      if (n < total) {
+        int c;
+        long long i3[3];
+        decode(n, c, i3);
+        const int idx3[3] = {(int)i3[0], (int)i3[1], (int)i3[2]};
+        float n2, lowest, scale;
+        screen_eval(F, c, idx3, n2, lowest, scale);
+        if (screen_certain(F, n2, lowest, scale)) {
+          ni = node_of(c, i3);
+          first = atomicMin(ub + ni, __float_as_uint(n2_upper(F, n2))) == 0xFFFFFFFFu;
+        }
+      }
+      const unsigned fm = __ballot_sync(0xFFFFFFFFu, first);
+      if (fm) {
+        unsigned pos = 0;
+        const int leader = __ffs(fm) - 1;
+        if (lane == leader) pos = atomicAdd(&ds->nub, (unsigned)__popc(fm));
+        pos = __shfl_sync(0xFFFFFFFFu, pos, leader);
+        if (first) {
+          const unsigned slot = pos + __popc(fm & ((1u << lane) - 1u));
+          if (slot < cap) ublist[slot] = ni;
+          else atomicOr(&ds->err, ERR_CAND_OVERFLOW);
+        }
+      }
+    }
+    return;
+  }
   int qn = 0;   // pairs waiting in this warp's queue (warp-uniform)
   for (long long base = 0; base < total; base += 32) {
     const long long n = base + lane;
@@ -326,7 +413,13 @@ __global__ void __launch_bounds__(32 * TAG_WARPS) k_tag_candidates(Geo g, Surf s
         long long i3[3];
         decode(n, c, i3);
         const int idx3[3] = {(int)i3[0], (int)i3[1], (int)i3[2]};
-        keep = screen_pair(F, c, idx3);
+        float n2, lowest, scale;
+        screen_eval(F, c, idx3, n2, lowest, scale);
+        keep = screen_maybe(F, n2, lowest, scale);
+        if (keep) {
+          const unsigned u = __ldcg(ub + node_of(c, i3));
+          keep = u == 0xFFFFFFFFu || n2_lower(F, n2) <= __uint_as_float(u);
+        }
       } else {
         keep = true;
       }
@@ -345,26 +438,51 @@ __global__ void __launch_bounds__(32 * TAG_WARPS) k_tag_candidates(Geo g, Surf s
   }
   if (qn > 0) exact_batch(qn);
 }
+template <int PHASE>
+struct TagPairs {
+  static constexpr int kThreads = 32 * TAG_WARPS;
+  Geo g;
+  Surf s;
+  Cand* cand;
+  unsigned cap;
+  unsigned long long* d2min;
+  unsigned* ub;
+  unsigned* ublist;
+  DevState* ds;
+  __device__ __forceinline__ void operator()(const Blk& bk) const {
+    tag_pairs<PHASE>(bk, g, s, cand, cap, d2min, ub, ublist, ds);
+  }
+};
 
 // Per node keep the smallest triangle index among the candidates of minimum |N|^2.
-__global__ void k_tag_resolve(Geo g, const Cand* __restrict__ cand, unsigned cap, const DevState* ds,
+__device__ __forceinline__ void tag_resolve(const Blk& bk, const Geo& g, const Cand* __restrict__ cand, unsigned cap, const DevState* ds,
                               const unsigned long long* __restrict__ d2min, unsigned* owner) {
   const unsigned n = min(ds->ncand, cap);
-  for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+  for (unsigned e = bk.x * blockDim.x + threadIdx.x; e < n; e += bk.gx * blockDim.x) {
     const Cand cd = cand[e];
     const long long o = comp_off(g, (int)(cd.key >> 30)) + (cd.key & KEY_MASK);
     if (cd.d2 == d2min[o]) atomicMin(owner + o, cd.tri);
   }
 }
+struct TagResolve {
+  static constexpr int kThreads = 256;
+  Geo g;
+  const Cand* cand;
+  unsigned cap;
+  const DevState* ds;
+  const unsigned long long* d2min;
+  unsigned* owner;
+  __device__ __forceinline__ void operator()(const Blk& bk) const { tag_resolve(bk, g, cand, cap, ds, d2min, owner); }
+};
 
 // Mark the winning (node, owner) pairs in the per-cell flag bytes, and in
 // the per-line records the sweeps use: the first forcing index of every x-
 // and z-line and of every y-line, per component.
-__global__ void k_tag_mark(Geo g, const Cand* __restrict__ cand, unsigned cap, const DevState* ds,
+__device__ __forceinline__ void tag_mark(const Blk& bk, const Geo& g, const Cand* __restrict__ cand, unsigned cap, const DevState* ds,
                            const unsigned long long* __restrict__ d2min, const unsigned* __restrict__ owner,
-                           unsigned* flags32, LineInfo li) {
+                           unsigned* flags32, const LineInfo& li) {
   const unsigned n = min(ds->ncand, cap);
-  for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+  for (unsigned e = bk.x * blockDim.x + threadIdx.x; e < n; e += bk.gx * blockDim.x) {
     const Cand cd = cand[e];
     const int c = (int)(cd.key >> 30);
     const long long node = cd.key & KEY_MASK;
@@ -380,6 +498,18 @@ __global__ void k_tag_mark(Geo g, const Cand* __restrict__ cand, unsigned cap, c
     }
   }
 }
+struct TagMark {
+  static constexpr int kThreads = 256;
+  Geo g;
+  const Cand* cand;
+  unsigned cap;
+  const DevState* ds;
+  const unsigned long long* d2min;
+  const unsigned* owner;
+  unsigned* flags32;
+  LineInfo li;
+  __device__ __forceinline__ void operator()(const Blk& bk) const { tag_mark(bk, g, cand, cap, ds, d2min, owner, flags32, li); }
+};
 
 __device__ __forceinline__ unsigned flag_of(const unsigned* flags32, long long cell) {
   return (flags32[cell >> 2] >> (8 * (cell & 3))) & 0xFFu;
@@ -387,11 +517,11 @@ __device__ __forceinline__ unsigned flag_of(const unsigned* flags32, long long c
 
 // Boundary cells (Section 3.2): all six faces hold forcing nodes.  Checked
 // once per cell, from the candidate that won the cell's lower x-face.
-__global__ void k_tag_boundary(Geo g, const Cand* __restrict__ cand, unsigned cap, const DevState* ds,
+__device__ __forceinline__ void tag_boundary(const Blk& bk, const Geo& g, const Cand* __restrict__ cand, unsigned cap, const DevState* ds,
                                const unsigned long long* __restrict__ d2min, const unsigned* __restrict__ owner,
                                unsigned* flags32) {
   const unsigned n = min(ds->ncand, cap);
-  for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+  for (unsigned e = bk.x * blockDim.x + threadIdx.x; e < n; e += bk.gx * blockDim.x) {
     const Cand cd = cand[e];
     if ((cd.key >> 30) != 0) continue;
     const long long node = cd.key & KEY_MASK;
@@ -407,6 +537,17 @@ __global__ void k_tag_boundary(Geo g, const Cand* __restrict__ cand, unsigned ca
     if (all) atomicOr(flags32 + (cell >> 2), (unsigned)FLAG_B << (8 * (cell & 3)));
   }
 }
+struct TagBoundary {
+  static constexpr int kThreads = 256;
+  Geo g;
+  const Cand* cand;
+  unsigned cap;
+  const DevState* ds;
+  const unsigned long long* d2min;
+  const unsigned* owner;
+  unsigned* flags32;
+  __device__ __forceinline__ void operator()(const Blk& bk) const { tag_boundary(bk, g, cand, cap, ds, d2min, owner, flags32); }
+};
 
 // ---------------------------------------------------------------------------
 // deterministic compaction of the flag bytes: count, scan, write
@@ -430,10 +571,10 @@ __device__ __forceinline__ void load16(const unsigned* flags32, long long ncell,
   }
 }
 
-__global__ void __launch_bounds__(CMP_THREADS) k_cmp_count(Geo g, const unsigned* __restrict__ flags32,
+__device__ __forceinline__ void cmp_count(const Blk& bk, const Geo& g, const unsigned* __restrict__ flags32,
                                                            unsigned* __restrict__ blk) {
   __shared__ unsigned red[4][CMP_THREADS / 32];
-  const long long cell0 = (long long)blockIdx.x * CMP_CHUNK + (long long)threadIdx.x * CMP_PER_THREAD;
+  const long long cell0 = (long long)bk.x * CMP_CHUNK + (long long)threadIdx.x * CMP_PER_THREAD;
   uint8_t f[16];
   load16(flags32, g.ncell, cell0, f);
   unsigned cnt[4] = {0, 0, 0, 0};
@@ -454,12 +595,19 @@ __global__ void __launch_bounds__(CMP_THREADS) k_cmp_count(Geo g, const unsigned
   if (threadIdx.x < 4) {
     unsigned v = 0;
     for (int w = 0; w < CMP_THREADS / 32; ++w) v += red[threadIdx.x][w];
-    blk[(long long)blockIdx.x * 4 + threadIdx.x] = v;
+    blk[(long long)bk.x * 4 + threadIdx.x] = v;
   }
 }
+struct CmpCount {
+  static constexpr int kThreads = CMP_THREADS;
+  Geo g;
+  const unsigned* flags32;
+  unsigned* blk;
+  __device__ __forceinline__ void operator()(const Blk& bk) const { cmp_count(bk, g, flags32, blk); }
+};
 
 // single block: exclusive scan of the per-block counts (in place), totals to ds
-__global__ void __launch_bounds__(1024) k_cmp_scan(unsigned* blk, int nblk, DevState* ds, unsigned fcap) {
+__device__ __forceinline__ void cmp_scan(const Blk& bk, unsigned* blk, int nblk, DevState* ds, unsigned fcap) {
   __shared__ unsigned part[4][1024];
   const int per = (nblk + 1023) / 1024;
   const int b0 = threadIdx.x * per, b1 = min(nblk, b0 + per);
@@ -495,13 +643,21 @@ __global__ void __launch_bounds__(1024) k_cmp_scan(unsigned* blk, int nblk, DevS
     if ((unsigned long long)n0 + n1 + n2 > fcap || ds->nbound > fcap) atomicOr(&ds->err, ERR_LIST_OVERFLOW);
   }
 }
+struct CmpScan {
+  static constexpr int kThreads = 1024;
+  unsigned* blk;
+  int nblk;
+  DevState* ds;
+  unsigned fcap;
+  __device__ __forceinline__ void operator()(const Blk& bk) const { cmp_scan(bk, blk, nblk, ds, fcap); }
+};
 
-__global__ void __launch_bounds__(CMP_THREADS) k_cmp_write(Geo g, const unsigned* __restrict__ flags32,
+__device__ __forceinline__ void cmp_write(const Blk& bk, const Geo& g, const unsigned* __restrict__ flags32,
                                                            const unsigned* __restrict__ blk,
                                                            const unsigned* __restrict__ owner, const DevState* ds,
                                                            ForceNode* flist, unsigned* blist, unsigned fcap) {
   __shared__ unsigned wsum[4][CMP_THREADS / 32];
-  const long long cell0 = (long long)blockIdx.x * CMP_CHUNK + (long long)threadIdx.x * CMP_PER_THREAD;
+  const long long cell0 = (long long)bk.x * CMP_CHUNK + (long long)threadIdx.x * CMP_PER_THREAD;
   uint8_t f[16];
   load16(flags32, g.ncell, cell0, f);
   unsigned cnt[4] = {0, 0, 0, 0};
@@ -527,7 +683,7 @@ __global__ void __launch_bounds__(CMP_THREADS) k_cmp_write(Geo g, const unsigned
   for (int q = 0; q < 4; ++q) {
     unsigned before = 0;
     for (int w = 0; w < wrp; ++w) before += wsum[q][w];
-    pos[q] = blk[(long long)blockIdx.x * 4 + q] + before + excl[q];
+    pos[q] = blk[(long long)bk.x * 4 + q] + before + excl[q];
   }
   const unsigned base[3] = {ds->force_base[0], ds->force_base[1], ds->force_base[2]};
 #pragma unroll
@@ -554,35 +710,73 @@ __global__ void __launch_bounds__(CMP_THREADS) k_cmp_write(Geo g, const unsigned
     }
   }
 }
+struct CmpWrite {
+  static constexpr int kThreads = CMP_THREADS;
+  Geo g;
+  const unsigned* flags32;
+  const unsigned* blk;
+  const unsigned* owner;
+  const DevState* ds;
+  ForceNode* flist;
+  unsigned* blist;
+  unsigned fcap;
+  __device__ __forceinline__ void operator()(const Blk& bk) const { cmp_write(bk, g, flags32, blk, owner, ds, flist, blist, fcap); }
+};
 
 // move this step's candidate count to "previous", zero the current one
-__global__ void k_copy_count(DevState* ds) {
+__device__ __forceinline__ void copy_count(const Blk& bk, DevState* ds) {
   ds->ncand_prev = ds->ncand;
   ds->ncand = 0;
+  ds->nub = 0;
 }
+struct CopyCount {
+  static constexpr int kThreads = 32;
+  DevState* ds;
+  __device__ __forceinline__ void operator()(const Blk& bk) const { copy_count(bk, ds); }
+};
 
 // ---------------------------------------------------------------------------
 // host launcher: the whole tagging stage of one step
 // ---------------------------------------------------------------------------
-void launch_tagging(const Geo& g, const Surf& s, const TagBuffers& b, DevState* ds, cudaStream_t st) {
-  stage_mark(st, ST_TAG);
-  cudaMemsetAsync(b.lines.x, 0x7F, b.lines.bytes, st);   // every line: "no forcing node"
+// Fill `n` words with `value` (the per-line records are reset every step;
+// a kernel rather than a memset so that batches merge it like the rest).
+__device__ __forceinline__ void fill32(const Blk& bk, unsigned* p, long long n, unsigned value) {
+  const long long stride = (long long)bk.gx * blockDim.x;
+  for (long long e = (long long)bk.x * blockDim.x + threadIdx.x; e < n; e += stride) p[e] = value;
+}
+struct Fill32 {
+  static constexpr int kThreads = 256;
+  unsigned* p;
+  long long n;
+  unsigned value;
+  __device__ __forceinline__ void operator()(const Blk& bk) const { fill32(bk, p, n, value); }
+};
+
+void launch_tagging(const Geo& g, const Surf& s, const TagBuffers& b, DevState* ds, Exec& ex) {
+  ex.mark(ST_TAG);
+  const long long words = (long long)(b.lines.bytes / 4);
+  // every line: "no forcing node" (0x7F7F7F7F exceeds any index)
+  ex.launch(dim3((unsigned)std::min<long long>((words + 255) / 256, num_sms() * 4ll)), dim3(256), 0,
+            Fill32{reinterpret_cast<unsigned*>(b.lines.x), words, 0x7F7F7F7Fu});
   // previous step's candidates reset their nodes, then the counters restart
-  k_tag_reset<<<num_sms() * 4, 256, 0, st>>>(g, b.cand, b.cap, ds, b.d2min, b.owner, b.flags32);
-  k_copy_count<<<1, 1, 0, st>>>(ds);
-  if (s.nt > 0) {
-    k_tri_setup<<<(unsigned)((s.nt + 127) / 128), 128, 0, st>>>(g, s);
-    const long long blocks = ((long long)s.nt * 32 + 32 * TAG_WARPS - 1) / (32 * TAG_WARPS);
-    k_tag_candidates<<<(unsigned)blocks, 32 * TAG_WARPS, 0, st>>>(g, s, b.cand, b.cap, b.d2min, ds);
-    const int gb = num_sms() * 8;
-    k_tag_resolve<<<gb, 256, 0, st>>>(g, b.cand, b.cap, ds, b.d2min, b.owner);
-    k_tag_mark<<<gb, 256, 0, st>>>(g, b.cand, b.cap, ds, b.d2min, b.owner, b.flags32, b.lines);
-    k_tag_boundary<<<gb, 256, 0, st>>>(g, b.cand, b.cap, ds, b.d2min, b.owner, b.flags32);
-  }
+  ex.launch(dim3(num_sms() * 4), dim3(256), 0,
+            TagReset{g, b.cand, b.cap, ds, b.d2min, b.owner, b.flags32, b.ub, b.ublist});
+  ex.launch(dim3(1), dim3(1), 0, CopyCount{ds});
+  const bool live = s.nt > 0;
+  ex.launch(grid_if(live, dim3((unsigned)((s.nt + 31) / 32))), dim3(32), 0, TriSetup{g, s});
+  const long long blocks = ((long long)s.nt * 32 + 32 * TAG_WARPS - 1) / (32 * TAG_WARPS);
+  ex.launch(grid_if(live, dim3((unsigned)blocks)), dim3(32 * TAG_WARPS), 0,
+            TagPairs<0>{g, s, b.cand, b.cap, b.d2min, b.ub, b.ublist, ds});
+  ex.launch(grid_if(live, dim3((unsigned)blocks)), dim3(32 * TAG_WARPS), 0,
+            TagPairs<1>{g, s, b.cand, b.cap, b.d2min, b.ub, b.ublist, ds});
+  const dim3 gb = grid_if(live, dim3(num_sms() * 8));
+  ex.launch(gb, dim3(256), 0, TagResolve{g, b.cand, b.cap, ds, b.d2min, b.owner});
+  ex.launch(gb, dim3(256), 0, TagMark{g, b.cand, b.cap, ds, b.d2min, b.owner, b.flags32, b.lines});
+  ex.launch(gb, dim3(256), 0, TagBoundary{g, b.cand, b.cap, ds, b.d2min, b.owner, b.flags32});
   const int nblk = (int)((g.ncell + CMP_CHUNK - 1) / CMP_CHUNK);
-  k_cmp_count<<<nblk, CMP_THREADS, 0, st>>>(g, b.flags32, b.blk);
-  k_cmp_scan<<<1, 1024, 0, st>>>(b.blk, nblk, ds, b.cap);
-  k_cmp_write<<<nblk, CMP_THREADS, 0, st>>>(g, b.flags32, b.blk, b.owner, ds, b.flist, b.blist, b.cap);
+  ex.launch(dim3(nblk), dim3(CMP_THREADS), 0, CmpCount{g, b.flags32, b.blk});
+  ex.launch(dim3(1), dim3(1024), 0, CmpScan{b.blk, nblk, ds, b.cap});
+  ex.launch(dim3(nblk), dim3(CMP_THREADS), 0, CmpWrite{g, b.flags32, b.blk, b.owner, ds, b.flist, b.blist, b.cap});
 }
 
 int compaction_blocks(const Geo& g) { return (int)((g.ncell + CMP_CHUNK - 1) / CMP_CHUNK); }

@@ -56,12 +56,25 @@ class ibm_diag(ctypes.Structure):
 IBM_NSTAGES = 16
 
 
+class ibm_tune(ctypes.Structure):
+    _fields_ = [("tri_y", ctypes.c_int), ("sweep_w", ctypes.c_int), ("fft_lpb", ctypes.c_int),
+                ("fft_cols", ctypes.c_int), ("ms_per_step", ctypes.c_double)]
+
+
+class ibm_batch_info(ctypes.Structure):
+    _fields_ = [("instances", ctypes.c_int64), ("cells", ctypes.c_int64), ("launches_per_step", ctypes.c_int64),
+                ("launches_per_step_solo", ctypes.c_int64), ("shape", ctypes.c_int32 * 3)]
+
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
 EXPORTS = ("ibm_create_grid", "ibm_destroy", "ibm_set_surface", "ibm_set_body_force", "ibm_set_fields",
            "ibm_step", "ibm_get_fields", "ibm_get_tags", "ibm_get_diag", "ibm_sync", "ibm_last_error",
-           "ibm_set_allocator", "ibm_version", "ibm_profile_stages", "ibm_stage_name", "ibm_tag_noalloc")
+           "ibm_set_allocator", "ibm_version", "ibm_profile_stages", "ibm_stage_name", "ibm_tag_noalloc",
+           "ibm_set_tune", "ibm_get_tune", "ibm_autotune", "ibm_batch_create", "ibm_batch_destroy",
+           "ibm_batch_step", "ibm_batch_sync", "ibm_batch_get_info", "ibm_batch_profile_stages",
+           "ibm_batch_set_tune", "ibm_batch_autotune", "ibm_batch_last_error", "ibm_step_batch")
 
 
 def library_path() -> str:
@@ -99,8 +112,22 @@ def load(build_if_needed: bool = True):
         L.ibm_stage_name.argtypes = [I]
         L.ibm_tag_noalloc.argtypes = [ctypes.POINTER(ibm_grid_desc), I, P, I, P, P, P, P, P]
         L.ibm_stage_name.restype = ctypes.c_char_p
+        L.ibm_set_tune.argtypes = [P, ctypes.POINTER(ibm_tune)]
+        L.ibm_get_tune.argtypes = [P, ctypes.POINTER(ibm_tune)]
+        L.ibm_autotune.argtypes = [P, I, ctypes.POINTER(ibm_tune)]
+        L.ibm_batch_create.argtypes = [P, I, P, ctypes.POINTER(P)]
+        L.ibm_batch_destroy.argtypes = [P]
+        L.ibm_batch_step.argtypes = [P, I]
+        L.ibm_batch_sync.argtypes = [P]
+        L.ibm_batch_get_info.argtypes = [P, ctypes.POINTER(ibm_batch_info)]
+        L.ibm_batch_profile_stages.argtypes = [P, I, P, P]
+        L.ibm_batch_set_tune.argtypes = [P, ctypes.POINTER(ibm_tune)]
+        L.ibm_batch_autotune.argtypes = [P, I, ctypes.POINTER(ibm_tune)]
+        L.ibm_batch_last_error.argtypes = [P]
+        L.ibm_batch_last_error.restype = ctypes.c_char_p
+        L.ibm_step_batch.argtypes = [P, I, I]
         for name in EXPORTS:
-            if name not in ("ibm_last_error", "ibm_version", "ibm_stage_name"):
+            if name not in ("ibm_last_error", "ibm_version", "ibm_stage_name", "ibm_batch_last_error"):
                 getattr(L, name).restype = ctypes.c_int
         _LIB = L
     return _LIB
@@ -235,6 +262,89 @@ def ibm_tag_noalloc(nx, ny, nz, xyz, tri, owners, lx=1.0, ly=1.0, lz=1.0, ybc=IB
                                   ptrs[2][0], ptrs[3][0], ptrs[4][0], _stream_handle(stream))
 
 
+def _tune_dict(t: ibm_tune) -> dict:
+    return {"tri_y": t.tri_y, "sweep_w": t.sweep_w, "fft_lpb": t.fft_lpb, "fft_cols": t.fft_cols,
+            "ms_per_step": t.ms_per_step}
+
+
+def ibm_set_tune(h, tri_y=0, sweep_w=0, fft_lpb=0, fft_cols=0):
+    _check(h, load().ibm_set_tune(h, ctypes.byref(ibm_tune(tri_y, sweep_w, fft_lpb, fft_cols, 0.0))))
+
+
+def ibm_get_tune(h) -> dict:
+    t = ibm_tune()
+    _check(h, load().ibm_get_tune(h, ctypes.byref(t)))
+    return _tune_dict(t)
+
+
+def ibm_autotune(h, steps=3) -> dict:
+    t = ibm_tune()
+    _check(h, load().ibm_autotune(h, int(steps), ctypes.byref(t)))
+    return _tune_dict(t)
+
+
+def _bcheck(b, status: int):
+    if status != 0:
+        msg = load().ibm_batch_last_error(b).decode() if b else ""
+        raise IbmError(status, msg)
+
+
+def _handles(hs):
+    arr = (ctypes.c_void_p * len(hs))(*hs)
+    return arr
+
+
+def ibm_batch_create(hs, stream=None):
+    b = ctypes.c_void_p()
+    _check(hs[0] if hs else None, load().ibm_batch_create(_handles(hs), len(hs), _stream_handle(stream),
+                                                          ctypes.byref(b)))
+    return b.value
+
+
+def ibm_batch_destroy(b):
+    _bcheck(b, load().ibm_batch_destroy(b))
+
+
+def ibm_batch_step(b, nsteps=1):
+    _bcheck(b, load().ibm_batch_step(b, int(nsteps)))
+
+
+def ibm_batch_sync(b):
+    _bcheck(b, load().ibm_batch_sync(b))
+
+
+def ibm_batch_get_info(b) -> dict:
+    i = ibm_batch_info()
+    _bcheck(b, load().ibm_batch_get_info(b, ctypes.byref(i)))
+    return {"instances": i.instances, "cells": i.cells, "launches_per_step": i.launches_per_step,
+            "launches_per_step_solo": i.launches_per_step_solo, "shape": list(i.shape)}
+
+
+def ibm_batch_profile_stages(b, nsteps=1) -> dict:
+    ms = (ctypes.c_double * IBM_NSTAGES)()
+    kn = (ctypes.c_int64 * IBM_NSTAGES)()
+    _bcheck(b, load().ibm_batch_profile_stages(b, int(nsteps), ms, kn))
+    return {ibm_stage_name(i): (ms[i], kn[i]) for i in range(IBM_NSTAGES)}
+
+
+def ibm_batch_set_tune(b, tri_y=0, sweep_w=0, fft_lpb=0, fft_cols=0):
+    _bcheck(b, load().ibm_batch_set_tune(b, ctypes.byref(ibm_tune(tri_y, sweep_w, fft_lpb, fft_cols, 0.0))))
+
+
+def ibm_batch_autotune(b, steps=3) -> dict:
+    t = ibm_tune()
+    _bcheck(b, load().ibm_batch_autotune(b, int(steps), ctypes.byref(t)))
+    return _tune_dict(t)
+
+
+def ibm_batch_last_error(b) -> str:
+    return load().ibm_batch_last_error(b).decode()
+
+
+def ibm_step_batch(hs, nsteps=1):
+    _check(hs[0], load().ibm_step_batch(_handles(hs), len(hs), int(nsteps)))
+
+
 def ibm_stage_name(i) -> str:
     return load().ibm_stage_name(int(i)).decode()
 
@@ -333,3 +443,47 @@ class Simulation:
 
     def sync(self):
         ibm_sync(self.h)
+
+    def autotune(self, steps=3):
+        return ibm_autotune(self.h, steps)
+
+    def set_tune(self, **kw):
+        ibm_set_tune(self.h, **kw)
+
+
+class Batch:
+    """Independent simulations advanced together: one launch per kernel of
+    the step for all of them (ibm_batch_*)."""
+
+    def __init__(self, sims, stream=None):
+        self.sims = list(sims)
+        self.b = ibm_batch_create([s.h for s in self.sims], stream)
+
+    def close(self):
+        if self.b:
+            ibm_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n=1):
+        ibm_batch_step(self.b, n)
+
+    def sync(self):
+        ibm_batch_sync(self.b)
+
+    def info(self):
+        return ibm_batch_get_info(self.b)
+
+    def profile_stages(self, nsteps=1):
+        return ibm_batch_profile_stages(self.b, nsteps)
+
+    def autotune(self, steps=3):
+        return ibm_batch_autotune(self.b, steps)
+
+    def set_tune(self, **kw):
+        ibm_batch_set_tune(self.b, **kw)

@@ -17,6 +17,14 @@ Workloads (x and z periodic, walls at y = 0 and y = ly, U_ref = L_ref = 1):
             8,192 triangles, heaving 0.05 sin(2 pi t) plus the bending mode
             0.02 sin(pi s) sin(2 pi t), s = (x - 0.3)/0.4; Re = 200,
             dt = 5e-4, 100 steps, fluid at rest.
+  batch32   32 independent instances advanced together: each of nx, ny, nz
+            drawn from {32, 48, 64, 96} (PCG64 seed 4), unit cube; one body
+            per instance -- icosphere (1,280 triangles), cube (12 n^2
+            triangles, n in 7..20) or zero-thickness disc (500-5,000
+            triangles) of size 0.24-0.4 centred mid-box -- translating with
+            a seeded sinusoid per axis (amplitude <= 0.05, frequency
+            0.5-2); Re uniform in [50, 500], dt = 0.2 dx_min / (1 + U_max),
+            200 steps, fluid at rest.
 """
 from __future__ import annotations
 
@@ -79,6 +87,51 @@ def plate(nq: int, side: float, x0: float, z0: float, y0: float) -> Tuple[np.nda
             tris.append((a, b, d))
             tris.append((a, d, c))
     return np.ascontiguousarray(xyz), np.ascontiguousarray(np.array(tris, dtype=np.int32))
+
+
+def cube(n: int, side: float, center) -> Tuple[np.ndarray, np.ndarray]:
+    """Closed cube surface, each face n x n quads split into two triangles
+    (12 n^2 triangles; vertices on shared edges are duplicated per face,
+    which Algorithm 1 does not mind)."""
+    s = np.linspace(-0.5, 0.5, n + 1) * side
+    A, B = np.meshgrid(s, s, indexing="ij")
+    a, b = A.ravel(), B.ravel()
+    h = np.full(a.size, 0.5 * side)
+    faces = [np.stack([h, a, b], 1), np.stack([-h, a, b], 1), np.stack([a, h, b], 1),
+             np.stack([a, -h, b], 1), np.stack([a, b, h], 1), np.stack([a, b, -h], 1)]
+    xyz, tris = [], []
+    for f, pts in enumerate(faces):
+        base = f * (n + 1) ** 2
+        xyz.append(pts)
+        for i in range(n):
+            for j in range(n):
+                q = base + i * (n + 1) + j
+                tris.append((q, q + n + 1, q + n + 2))
+                tris.append((q, q + n + 2, q + 1))
+    xyz = np.concatenate(xyz) + np.asarray(center, dtype=np.float64)
+    return np.ascontiguousarray(xyz), np.ascontiguousarray(np.array(tris, dtype=np.int32))
+
+
+def disc(nr: int, nth: int, radius: float, center) -> Tuple[np.ndarray, np.ndarray]:
+    """Zero-thickness disc in the x-z plane through `center`: nr rings of nth
+    vertices around the centre vertex (nth + 2 nth (nr - 1) triangles)."""
+    cx, cy, cz = center
+    pts = [(cx, cy, cz)]
+    for r in range(1, nr + 1):
+        rad = radius * r / nr
+        for k in range(nth):
+            th = TWO_PI * k / nth
+            pts.append((cx + rad * math.cos(th), cy, cz + rad * math.sin(th)))
+    tris = []
+    for k in range(nth):
+        tris.append((0, 1 + k, 1 + (k + 1) % nth))
+    for r in range(1, nr):
+        i0, i1 = 1 + (r - 1) * nth, 1 + r * nth
+        for k in range(nth):
+            k1 = (k + 1) % nth
+            tris.append((i0 + k, i1 + k, i1 + k1))
+            tris.append((i0 + k, i1 + k1, i0 + k1))
+    return np.ascontiguousarray(np.array(pts, dtype=np.float64)), np.ascontiguousarray(np.array(tris, dtype=np.int32))
 
 
 # ---------------------------------------------------------------------------
@@ -149,6 +202,50 @@ def heaving_plate(n: int = 128, steps: int = 100, nq: int = 64) -> Workload:
         return xyz, vel
 
     return Workload(f"plate{n}", n, n, n, 1.0, 1.0, 1.0, 200.0, 5e-4, steps, tri, surface_at)
+
+
+def translating(name, nx, ny, nz, re, dt, steps, xyz0, tri, amp, freq, phase) -> Workload:
+    """Rigid body translating with x_c(t) = x_c0 + amp sin(2 pi freq t + phase)
+    per axis (vertex velocity = the translation velocity)."""
+    amp, freq, phase = (np.asarray(v, dtype=np.float64) for v in (amp, freq, phase))
+
+    def surface_at(t):
+        arg = TWO_PI * freq * t + phase
+        xyz = xyz0 + (amp * (np.sin(arg) - np.sin(phase)))[None, :]
+        vel = np.broadcast_to(amp * TWO_PI * freq * np.cos(arg), xyz0.shape).copy()
+        return np.ascontiguousarray(xyz), np.ascontiguousarray(vel)
+
+    return Workload(name, nx, ny, nz, 1.0, 1.0, 1.0, re, dt, steps, tri, surface_at)
+
+
+def batched_instances(count: int = 32, seed: int = 4, steps: int = 200,
+                      sizes=(32, 48, 64, 96)) -> List[Workload]:
+    """The uneven batch: per instance nx, ny, nz from `sizes`, one body
+    (sphere, cube or thin disc, 500-5,000 triangles) on seeded sinusoidal
+    translation, Re in [50, 500], dt = 0.2 dx_min / (1 + U_max)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        nx, ny, nz = (int(v) for v in rng.choice(sizes, size=3))
+        kind = int(rng.integers(0, 3))
+        size = float(rng.uniform(0.24, 0.4))
+        c = (0.5, 0.5, 0.5)
+        if kind == 0:
+            xyz, tri = icosphere(3, size / 2, c)
+        elif kind == 1:
+            xyz, tri = cube(int(rng.integers(7, 21)), size, c)
+        else:
+            nth = int(rng.integers(24, 65))
+            nr = int(rng.integers(max(2, 260 // nth + 1), 2500 // nth + 1))
+            xyz, tri = disc(nr, nth, size / 2, c)
+        amp = rng.uniform(0.0, 0.05, 3)
+        freq = rng.uniform(0.5, 2.0, 3)
+        phase = rng.uniform(0.0, TWO_PI, 3)
+        re = float(rng.uniform(50.0, 500.0))
+        umax = float(np.linalg.norm(amp * TWO_PI * freq))
+        dt = 0.2 * (1.0 / max(nx, ny, nz)) / (1.0 + umax)
+        out.append(translating(f"batch{i}", nx, ny, nz, re, dt, steps, xyz, tri, amp, freq, phase))
+    return out
 
 
 def random_fields(nx: int, ny: int, nz: int, seed: int, amp: float = 1.0):
