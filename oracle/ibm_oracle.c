@@ -230,11 +230,13 @@ static void claim(int32_t* owner, double* d2, long idx, int32_t t, double n2) {
 
 /* Algorithm 1 as printed: loop over triangles, build the Cartesian box
  * min - dx < x < max + dx (strict), visit the Eulerian points of component c
- * inside it, and classify each.  owner[] (size of component c's array) must
- * be -1 on entry; d2[] is scratch of the same size.  Indices that leave the
- * box in x or z wrap periodically (the point keeps its unwrapped coordinate). */
-void orc_tag_alg1(const orc_grid* g, int c, const double* xyz, int ntri, const int* tri,
-                  int32_t* owner, double* d2) {
+ * inside it, and classify each.  Indices that leave the box in x or z wrap
+ * periodically (the point keeps its unwrapped coordinate).  Only nodes whose
+ * wrapped x index lies in [i0, i0 + ni) are recorded, in arrays laid out
+ * [k][j][i - i0] (ni = nx: the whole component).  owner[] must be -1 on
+ * entry; d2[] is scratch of the same size. */
+static void tag_alg1_window(const orc_grid* g, int c, const double* xyz, int ntri, const int* tri, long i0,
+                            long ni, int32_t* owner, double* d2) {
   double off[3], del[3] = {g->dx, g->dy, g->dz};
   node_offset(c, off);
   double diag2 = diag2_of(g);
@@ -264,13 +266,28 @@ void orc_tag_alg1(const orc_grid* g, int c, const double* xyz, int ntri, const i
           for (int d = 0; d < 3; ++d)
             if (!(lo[d] < x[d] && x[d] < hi[d])) inside = 0;
           if (!inside) continue;
+          const long iw = wrap(i, g->nx) - i0;
+          if (iw < 0 || iw >= ni) continue;
           double n2;
           if (tag_test(g, c, i, j, k, x, a, b, c3, diag2, &n2)) {
-            long idx = fidx(g, c, wrap(i, g->nx), j, wrap(k, g->nz));
+            long planes = (c == 1) ? g->ny + 1 : g->ny;
+            long idx = (wrap(k, g->nz) * planes + j) * ni + iw;
             claim(owner, d2, idx, (int32_t)t, n2);
           }
         }
   }
+}
+
+void orc_tag_alg1(const orc_grid* g, int c, const double* xyz, int ntri, const int* tri,
+                  int32_t* owner, double* d2) {
+  tag_alg1_window(g, c, xyz, ntri, tri, 0, g->nx, owner, d2);
+}
+
+/* Algorithm 1 restricted to the nodes with x index in [i0, i0 + ni): the
+ * exact owners of a slab of a grid too large to tag whole. */
+void orc_tag_alg1_window(const orc_grid* g, int c, const double* xyz, int ntri, const int* tri, long i0, long ni,
+                         int32_t* owner, double* d2) {
+  tag_alg1_window(g, c, xyz, ntri, tri, i0, ni, owner, d2);
 }
 
 /* Brute force counterpart of Algorithm 1: every node of component c (and

@@ -79,6 +79,7 @@ def lib():
             L.orc_closest_point.argtypes = [_P] * 6
             L.orc_tag_alg1.argtypes = [_GP, _I, _P, _I, _P, _P, _P]
             L.orc_tag_brute.argtypes = [_GP, _I, _P, _I, _P, _P, _P]
+            L.orc_tag_alg1_window.argtypes = [_GP, _I, _P, _I, _P, ctypes.c_long, ctypes.c_long, _P, _P]
             L.orc_force.argtypes = [_GP, _I, _P, _P, _P, _P, _P, _P, _D]
             L.orc_force.restype = _I
             L.orc_slip.argtypes = [_GP, _I, _P, _P, _P, _P, _P, _D, _P, _P]
@@ -138,6 +139,22 @@ def tag(g: Grid, xyz: np.ndarray, tri: np.ndarray, brute: bool = False):
         owners.append(own)
         d2s.append(d2)
     return owners, d2s
+
+
+def tag_window(g: Grid, xyz: np.ndarray, tri: np.ndarray, i0: int, ni: int):
+    """Algorithm 1 owners of the nodes with x index in [i0, i0 + ni), per
+    component, as arrays [k][j][i - i0] (for grids too large to tag whole)."""
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    tri = np.ascontiguousarray(tri, dtype=np.int32)
+    owners = []
+    for c in range(3):
+        shape = (g.nz, g.ny + 1 if c == 1 else g.ny, ni)
+        own = np.full(shape, -1, dtype=np.int32)
+        d2 = np.full(shape, np.inf)
+        lib().orc_tag_alg1_window(ctypes.byref(g), c, _p(xyz), int(tri.shape[0]), _p(tri), int(i0), int(ni),
+                                  _p(own), _p(d2))
+        owners.append(own)
+    return owners
 
 
 def boundary_cells(g: Grid, owners):

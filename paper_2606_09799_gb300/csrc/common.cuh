@@ -60,6 +60,7 @@ struct DevState {
   unsigned int ncand;            // candidates of the current step
   unsigned int ncand_prev;       // candidates of the previous step (sparse reset)
   unsigned int nub;              // nodes with an |N|^2 bound this step (sparse reset)
+  unsigned int nsurv;            // pairs listed for the exact tagging test this step
   unsigned int nbound;           // boundary cells
   unsigned int nforce_c[3];      // forcing nodes per component
   unsigned int force_base[3];    // start of each component's forcing sub-list

@@ -51,6 +51,7 @@ struct TagBuffers {
   unsigned* flags32;           // per-cell flag bytes packed four to a word
   unsigned* ub;                // per node of the three grids: FP32 upper bound of the owner's |N|^2 (bits)
   unsigned* ublist;            // nodes whose ub this step set first (capacity cap)
+  unsigned long long* surv;    // (triangle << 32 | pair) sent to the exact test (capacity cap)
   unsigned* blk;               // 4 counters per compaction block
   ForceNode* flist;            // forcing nodes, grouped by component, sorted by cell
   unsigned* blist;             // boundary cells, sorted

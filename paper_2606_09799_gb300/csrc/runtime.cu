@@ -480,13 +480,15 @@ static ibm_status alloc_lists(ibm_handle h, unsigned cap) {
   dfree(h, h->tb.flist);
   dfree(h, h->tb.blist);
   dfree(h, h->tb.ublist);
+  dfree(h, h->tb.surv);
   dfree(h, h->uf);
   h->tb.cand = (Cand*)dalloc(h, (size_t)cap * sizeof(Cand));
   h->tb.flist = (ForceNode*)dalloc(h, (size_t)cap * sizeof(ForceNode));
   h->tb.blist = (unsigned*)dalloc(h, (size_t)cap * sizeof(unsigned));
   h->tb.ublist = (unsigned*)dalloc(h, (size_t)cap * sizeof(unsigned));
+  h->tb.surv = (unsigned long long*)dalloc(h, (size_t)cap * sizeof(unsigned long long));
   h->uf = dalloc(h, (size_t)cap * h->esize);
-  if (!h->tb.cand || !h->tb.flist || !h->tb.blist || !h->tb.ublist || !h->uf) {
+  if (!h->tb.cand || !h->tb.flist || !h->tb.blist || !h->tb.ublist || !h->tb.surv || !h->uf) {
     set_err(h, "device allocation of the work lists failed");
     return IBM_ERR_OOM;
   }

@@ -237,76 +237,144 @@ __device__ __forceinline__ bool screen_certain(const TriF32& F, float n2, float 
 __device__ __forceinline__ float n2_upper(const TriF32& F, float n2) { return n2 * 1.004f + 1e-3f * F.diag2; }
 __device__ __forceinline__ float n2_lower(const TriF32& F, float n2) { return n2 * 0.996f - 1e-3f * F.diag2; }
 
-constexpr int TAG_WARPS = 4;
+
+// pair n of a triangle's box -> (component, unwrapped lattice indices)
+__device__ __forceinline__ void decode_pair(const TriRec* __restrict__ rec, long long n, int& c, long long idx3[3]) {
+  const long long cnt0 = rec->cnt[0], cnt1 = rec->cnt[1], total = cnt0 + cnt1 + rec->cnt[2];
+  c = n < cnt0 ? 0 : (n < cnt0 + cnt1 ? 1 : 2);
+  const long long q = n - (c == 0 ? 0 : (c == 1 ? cnt0 : cnt0 + cnt1));
+  // selects instead of runtime indices (keeps the record's fields in registers)
+  const int ni = max(c == 0 ? rec->ext[0][0] : (c == 1 ? rec->ext[1][0] : rec->ext[2][0]), 1);
+  const int nj = max(c == 0 ? rec->ext[0][1] : (c == 1 ? rec->ext[1][1] : rec->ext[2][1]), 1);
+  long long qj, ri, rj;
+  if (total < (1ll << 30)) {
+    const unsigned q32 = (unsigned)q, qi32 = q32 / (unsigned)ni, qj32 = qi32 / (unsigned)nj;
+    qj = qj32;
+    ri = q32 - qi32 * (unsigned)ni;
+    rj = qi32 - qj32 * (unsigned)nj;
+  } else {
+    const long long qi = q / ni;
+    qj = qi / nj;
+    ri = q - qi * ni;
+    rj = qi - qj * nj;
+  }
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int b0 = c == 0 ? rec->n0[0][d] : (c == 1 ? rec->n0[1][d] : rec->n0[2][d]);
+    idx3[d] = b0 + (d == 0 ? ri : (d == 1 ? rj : qj));
+  }
+}
 
 // The owner of a node is the qualifying pair of smallest |N|^2, so a pair
 // whose |N|^2 certainly exceeds that of a pair that certainly qualifies
 // can neither own the node nor change whether it is tagged.  Phase 0 folds
 // an upper bound of |N|^2 of every certainly-qualifying pair (FP32 screen)
 // into a per-node word `ub` (first touches listed in `ublist` for the sparse
-// reset); phase 1 sends to the exact FP64 test only the pairs that may
-// qualify and whose lower bound does not exceed the node's `ub` -- the
-// owner and every pair tied with it always among them.
+// reset); phase 1 lists the pairs that may qualify and whose lower bound
+// does not exceed the node's `ub` -- the owner and every pair tied with it
+// always among them -- for the exact FP64 test (TagExact), which takes
+// them one per lane, so its warps are full whatever the survivors per
+// triangle.  One warp per triangle, lanes over the pairs of its box.
 template <int PHASE>
-__device__ __forceinline__ void tag_pairs(const Blk& bk, const Geo& g, const Surf& s, Cand* __restrict__ cand,
-                                          unsigned cap, unsigned long long* d2min, unsigned* __restrict__ ub,
-                                          unsigned* __restrict__ ublist, DevState* ds) {
-  __shared__ long long queue[TAG_WARPS][64];
-  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+__device__ __forceinline__ void tag_pairs(const Blk& bk, const Geo& g, const Surf& s, unsigned cap,
+                                          unsigned* __restrict__ ub, unsigned* __restrict__ ublist,
+                                          unsigned long long* __restrict__ surv, DevState* ds) {
+  const int lane = threadIdx.x & 31;
   const long long t = ((long long)bk.x * blockDim.x + threadIdx.x) >> 5;
   if (t >= s.nt) return;
   const TriRec* __restrict__ rec = s.rec + t;
-  const long long cnt0 = rec->cnt[0], cnt1 = rec->cnt[1], cnt2 = rec->cnt[2];
-  const long long total = cnt0 + cnt1 + cnt2;
+  const long long total = rec->cnt[0] + rec->cnt[1] + rec->cnt[2];
   if (total == 0) return;
   const bool screen = rec->screen != 0;
   if (PHASE == 0 && !screen) return;   // no FP32 bound without the screen
-  const double del[3] = {g.dx, g.dy, g.dz};
-  int n0[3][3], ext[3][3];
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      n0[c][d] = rec->n0[c][d];
-      ext[c][d] = max(rec->ext[c][d], 1);
-    }
-  // pair n -> (component, lattice indices), with selects instead of
-  // runtime indices (keeps the tables in registers); 32-bit arithmetic when
-  // the box holds fewer than 2^30 pairs (always so where the screen runs)
-  auto decode = [&](long long n, int& c, long long idx3[3]) {
-    c = n < cnt0 ? 0 : (n < cnt0 + cnt1 ? 1 : 2);
-    const long long q = n - (c == 0 ? 0 : (c == 1 ? cnt0 : cnt0 + cnt1));
-    const int ni = c == 0 ? ext[0][0] : (c == 1 ? ext[1][0] : ext[2][0]);
-    const int nj = c == 0 ? ext[0][1] : (c == 1 ? ext[1][1] : ext[2][1]);
-    long long qi, qj, ri, rj;
-    if (total < (1ll << 30)) {
-      const unsigned q32 = (unsigned)q, qi32 = q32 / (unsigned)ni, qj32 = qi32 / (unsigned)nj;
-      qi = qi32;
-      qj = qj32;
-      ri = q32 - qi32 * (unsigned)ni;
-      rj = qi32 - qj32 * (unsigned)nj;
-    } else {
-      qi = q / ni;
-      qj = qi / nj;
-      ri = q - qi * ni;
-      rj = qi - qj * nj;
-    }
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const int b = c == 0 ? n0[0][d] : (c == 1 ? n0[1][d] : n0[2][d]);
-      idx3[d] = b + (d == 0 ? ri : (d == 1 ? rj : qj));
+  TriF32 F;
+  if (screen) F = rec->f;
+  // index of a lattice point in the comp_off layout of the three grids
+  auto node_of = [&](int c, const long long i3[3]) -> unsigned {
+    return (unsigned)(comp_off(g, c) + fidx(g, c, wrapi(i3[0], g.nx), i3[1], wrapi(i3[2], g.nz)));
+  };
+  // warp-aggregated append of this lane's item (if `has`) to a list
+  auto append = [&](bool has, unsigned* counter, auto store) {
+    const unsigned m = __ballot_sync(0xFFFFFFFFu, has);
+    if (!m) return;
+    unsigned pos = 0;
+    const int leader = __ffs(m) - 1;
+    if (lane == leader) pos = atomicAdd(counter, (unsigned)__popc(m));
+    pos = __shfl_sync(0xFFFFFFFFu, pos, leader);
+    if (has) {
+      const unsigned slot = pos + __popc(m & ((1u << lane) - 1u));
+      if (slot < cap) store(slot);
+      else atomicOr(&ds->err, ERR_CAND_OVERFLOW);
     }
   };
-  // the exact FP64 test of Algorithm 1 on `count` queued pairs, one per lane
-  auto exact_batch = [&](int count) {
+  for (long long base = 0; base < total; base += 32) {
+    const long long n = base + lane;
+    bool hit = false;
+    unsigned ni = 0;
+    if (n < total) {
+      if (screen) {
+        int c;
+        long long i3[3];
+        decode_pair(rec, n, c, i3);
+        const int idx3[3] = {(int)i3[0], (int)i3[1], (int)i3[2]};
+        float n2, lowest, scale;
+        screen_eval(F, c, idx3, n2, lowest, scale);
+        if (PHASE == 0) {
+          if (screen_certain(F, n2, lowest, scale)) {
+            ni = node_of(c, i3);
+            hit = atomicMin(ub + ni, __float_as_uint(n2_upper(F, n2))) == 0xFFFFFFFFu;   // first touch
+          }
+        } else if (screen_maybe(F, n2, lowest, scale)) {
+          const unsigned u = __ldcg(ub + node_of(c, i3));
+          hit = u == 0xFFFFFFFFu || n2_lower(F, n2) <= __uint_as_float(u);
+        }
+      } else {
+        hit = true;   // phase 1 only: every pair of an unscreened triangle is tested exactly
+      }
+    }
+    if (PHASE == 0) append(hit, &ds->nub, [&](unsigned slot) { ublist[slot] = ni; });
+    else append(hit, &ds->nsurv, [&](unsigned slot) { surv[slot] = ((unsigned long long)t << 32) | (unsigned)n; });
+  }
+}
+template <int PHASE>
+struct TagPairs {
+  static constexpr int kThreads = 128;
+  Geo g;
+  Surf s;
+  unsigned cap;
+  unsigned* ub;
+  unsigned* ublist;
+  unsigned long long* surv;
+  DevState* ds;
+  __device__ __forceinline__ void operator()(const Blk& bk) const { tag_pairs<PHASE>(bk, g, s, cap, ub, ublist, surv, ds); }
+};
+
+// The exact test of Algorithm 1, FP64 with explicit rounding, one listed
+// (triangle, pair) per thread: |N|^2 <= diag^2 and a scalar product
+// N . (x^{k,n} - X) < 0 for one of the six lattice neighbours (or N = 0).
+// A pair that passes folds |N|^2 into the node's minimum and joins the
+// candidate list.
+__device__ __forceinline__ void tag_exact(const Blk& bk, const Geo& g, const Surf& s, Cand* __restrict__ cand,
+                                          unsigned cap, unsigned long long* d2min,
+                                          const unsigned long long* __restrict__ surv, DevState* ds) {
+  const unsigned ns = min(ds->nsurv, cap);
+  const int lane = threadIdx.x & 31;
+  const double del[3] = {g.dx, g.dy, g.dz};
+  const unsigned stride = bk.gx * blockDim.x;
+  // whole warps iterate together (the candidate append is warp-aggregated)
+  for (unsigned e0 = bk.x * blockDim.x + (threadIdx.x & ~31u); e0 < ns; e0 += stride) {
+    const unsigned e = e0 + lane;
     bool tagged = false;
-    unsigned key = 0;
+    unsigned key = 0, tri = 0;
     unsigned long long d2bits = 0;
-    if (lane < count) {
-      const TriConst TC = rec->tc;
+    if (e < ns) {
+      const unsigned long long sv = surv[e];
+      tri = (unsigned)(sv >> 32);
+      const TriRec* __restrict__ rec = s.rec + tri;
       int c;
       long long idx3[3];
-      decode(queue[wl][lane], c, idx3);
+      decode_pair(rec, (long long)(unsigned)sv, c, idx3);
+      const TriConst TC = rec->tc;
       double x[3];
 #pragma unroll
       for (int d = 0; d < 3; ++d) x[d] = lat(idx3[d], del[d], d == c ? 0 : 1);
@@ -322,9 +390,8 @@ __device__ __forceinline__ void tag_pairs(const Blk& bk, const Geo& g, const Sur
         if (n2 == 0.0) {
           tagged = true;   // a node on the surface: alpha = 0 in Eq. new_IB
         } else {
-          // N . (x^{k,n} - X) for the six lattice neighbours: only the
-          // neighbour's own axis differs from N, the other two products are
-          // the P[] already formed (same operands, same rounding)
+          // only the neighbour's own axis differs from N; the other two
+          // products are the P[] already formed (same operands and rounding)
 #pragma unroll
           for (int d = 0; d < 3 && !tagged; ++d) {
 #pragma unroll
@@ -356,7 +423,7 @@ __device__ __forceinline__ void tag_pairs(const Blk& bk, const Geo& g, const Sur
         if (slot < cap) {
           Cand cd;
           cd.key = key;
-          cd.tri = (unsigned)t;
+          cd.tri = tri;
           cd.d2 = d2bits;
           cand[slot] = cd;
         } else {
@@ -364,94 +431,18 @@ __device__ __forceinline__ void tag_pairs(const Blk& bk, const Geo& g, const Sur
         }
       }
     }
-  };
-  TriF32 F;
-  if (screen) F = rec->f;
-  // index of a lattice point in the comp_off layout of the three grids
-  auto node_of = [&](int c, const long long i3[3]) -> unsigned {
-    return (unsigned)(comp_off(g, c) + fidx(g, c, wrapi(i3[0], g.nx), i3[1], wrapi(i3[2], g.nz)));
-  };
-  if (PHASE == 0) {
-    for (long long base = 0; base < total; base += 32) {
-      const long long n = base + lane;
-      bool first = false;
-      unsigned ni = 0;
-      if (n < total) {
-        int c;
-        long long i3[3];
-        decode(n, c, i3);
-        const int idx3[3] = {(int)i3[0], (int)i3[1], (int)i3[2]};
-        float n2, lowest, scale;
-        screen_eval(F, c, idx3, n2, lowest, scale);
-        if (screen_certain(F, n2, lowest, scale)) {
-          ni = node_of(c, i3);
-          first = atomicMin(ub + ni, __float_as_uint(n2_upper(F, n2))) == 0xFFFFFFFFu;
-        }
-      }
-      const unsigned fm = __ballot_sync(0xFFFFFFFFu, first);
-      if (fm) {
-        unsigned pos = 0;
-        const int leader = __ffs(fm) - 1;
-        if (lane == leader) pos = atomicAdd(&ds->nub, (unsigned)__popc(fm));
-        pos = __shfl_sync(0xFFFFFFFFu, pos, leader);
-        if (first) {
-          const unsigned slot = pos + __popc(fm & ((1u << lane) - 1u));
-          if (slot < cap) ublist[slot] = ni;
-          else atomicOr(&ds->err, ERR_CAND_OVERFLOW);
-        }
-      }
-    }
-    return;
   }
-  int qn = 0;   // pairs waiting in this warp's queue (warp-uniform)
-  for (long long base = 0; base < total; base += 32) {
-    const long long n = base + lane;
-    bool keep = false;
-    if (n < total) {
-      if (screen) {
-        int c;
-        long long i3[3];
-        decode(n, c, i3);
-        const int idx3[3] = {(int)i3[0], (int)i3[1], (int)i3[2]};
-        float n2, lowest, scale;
-        screen_eval(F, c, idx3, n2, lowest, scale);
-        keep = screen_maybe(F, n2, lowest, scale);
-        if (keep) {
-          const unsigned u = __ldcg(ub + node_of(c, i3));
-          keep = u == 0xFFFFFFFFu || n2_lower(F, n2) <= __uint_as_float(u);
-        }
-      } else {
-        keep = true;
-      }
-    }
-    const unsigned km = __ballot_sync(0xFFFFFFFFu, keep);
-    if (keep) queue[wl][qn + __popc(km & ((1u << lane) - 1u))] = n;
-    qn += __popc(km);
-    __syncwarp();
-    if (qn >= 32) {
-      exact_batch(32);
-      __syncwarp();
-      if (lane < qn - 32) queue[wl][lane] = queue[wl][32 + lane];
-      qn -= 32;
-      __syncwarp();
-    }
-  }
-  if (qn > 0) exact_batch(qn);
 }
-template <int PHASE>
-struct TagPairs {
-  static constexpr int kThreads = 32 * TAG_WARPS;
+struct TagExact {
+  static constexpr int kThreads = 128;
   Geo g;
   Surf s;
   Cand* cand;
   unsigned cap;
   unsigned long long* d2min;
-  unsigned* ub;
-  unsigned* ublist;
+  const unsigned long long* surv;
   DevState* ds;
-  __device__ __forceinline__ void operator()(const Blk& bk) const {
-    tag_pairs<PHASE>(bk, g, s, cand, cap, d2min, ub, ublist, ds);
-  }
+  __device__ __forceinline__ void operator()(const Blk& bk) const { tag_exact(bk, g, s, cand, cap, d2min, surv, ds); }
 };
 
 // Per node keep the smallest triangle index among the candidates of minimum |N|^2.
@@ -728,6 +719,7 @@ __device__ __forceinline__ void copy_count(const Blk& bk, DevState* ds) {
   ds->ncand_prev = ds->ncand;
   ds->ncand = 0;
   ds->nub = 0;
+  ds->nsurv = 0;
 }
 struct CopyCount {
   static constexpr int kThreads = 32;
@@ -764,11 +756,10 @@ void launch_tagging(const Geo& g, const Surf& s, const TagBuffers& b, DevState* 
   ex.launch(dim3(1), dim3(1), 0, CopyCount{ds});
   const bool live = s.nt > 0;
   ex.launch(grid_if(live, dim3((unsigned)((s.nt + 31) / 32))), dim3(32), 0, TriSetup{g, s});
-  const long long blocks = ((long long)s.nt * 32 + 32 * TAG_WARPS - 1) / (32 * TAG_WARPS);
-  ex.launch(grid_if(live, dim3((unsigned)blocks)), dim3(32 * TAG_WARPS), 0,
-            TagPairs<0>{g, s, b.cand, b.cap, b.d2min, b.ub, b.ublist, ds});
-  ex.launch(grid_if(live, dim3((unsigned)blocks)), dim3(32 * TAG_WARPS), 0,
-            TagPairs<1>{g, s, b.cand, b.cap, b.d2min, b.ub, b.ublist, ds});
+  const long long blocks = ((long long)s.nt * 32 + 127) / 128;   // one warp per triangle
+  ex.launch(grid_if(live, dim3((unsigned)blocks)), dim3(128), 0, TagPairs<0>{g, s, b.cap, b.ub, b.ublist, b.surv, ds});
+  ex.launch(grid_if(live, dim3((unsigned)blocks)), dim3(128), 0, TagPairs<1>{g, s, b.cap, b.ub, b.ublist, b.surv, ds});
+  ex.launch(grid_if(live, dim3(num_sms() * 8)), dim3(128), 0, TagExact{g, s, b.cand, b.cap, b.d2min, b.surv, ds});
   const dim3 gb = grid_if(live, dim3(num_sms() * 8));
   ex.launch(gb, dim3(256), 0, TagResolve{g, b.cand, b.cap, ds, b.d2min, b.owner});
   ex.launch(gb, dim3(256), 0, TagMark{g, b.cand, b.cap, ds, b.d2min, b.owner, b.flags32, b.lines});

@@ -25,6 +25,14 @@ Workloads (x and z periodic, walls at y = 0 and y = ly, U_ref = L_ref = 1):
             a seeded sinusoid per axis (amplitude <= 0.05, frequency
             0.5-2); Re uniform in [50, 500], dt = 0.2 dx_min / (1 + U_max),
             200 steps, fluid at rest.
+  channel256  256 x 192 x 256 cells on 4/3 x 1 x 4/3, 16 moving bodies of
+            mixed thickness (spheres, capped cylinders, zero-thickness
+            plates; ~125,000 triangles) in a perturbed Poiseuille flow,
+            Re_b = 5600 (see multibody_channel).
+  leaflet512  512 x 384 x 512 cells (~100M), a finite-thickness tube with
+            three zero-thickness leaflets opening and closing periodically,
+            182,800 triangles, pulsatile forcing, Re = 1000 (see
+            leaflet_tube).
 """
 from __future__ import annotations
 
@@ -132,6 +140,132 @@ def disc(nr: int, nth: int, radius: float, center) -> Tuple[np.ndarray, np.ndarr
             tris.append((i0 + k, i1 + k, i1 + k1))
             tris.append((i0 + k, i1 + k1, i0 + k1))
     return np.ascontiguousarray(np.array(pts, dtype=np.float64)), np.ascontiguousarray(np.array(tris, dtype=np.int32))
+
+
+def capped_cylinder(n_around, n_along, radius, length, center, axis):
+    """Closed cylinder (hemispherical caps) of the given axis direction."""
+    axis = np.asarray(axis, float)
+    axis /= np.linalg.norm(axis)
+    # orthonormal frame
+    t = np.array([1.0, 0, 0]) if abs(axis[0]) < 0.9 else np.array([0, 1.0, 0])
+    e1 = np.cross(axis, t)
+    e1 /= np.linalg.norm(e1)
+    e2 = np.cross(axis, e1)
+    pts, tris = [], []
+    th = TWO_PI * np.arange(n_around) / n_around
+    ring = np.stack([np.cos(th), np.sin(th)], 1)
+    ncap = max(2, n_around // 8)
+    # rings: cap A (from pole), body, cap B
+    rings = []
+    for k in range(1, ncap + 1):
+        phi = (math.pi / 2) * k / ncap
+        rings.append((-length / 2 - radius * math.cos(phi), radius * math.sin(phi)))
+    for k in range(1, n_along):
+        rings.append((-length / 2 + length * k / n_along, radius))
+    for k in range(ncap, 0, -1):
+        phi = (math.pi / 2) * k / ncap
+        rings.append((length / 2 + radius * math.cos(phi), radius * math.sin(phi)))
+    c = np.asarray(center, float)
+    pts.append(c + axis * (-length / 2 - radius))
+    for (s, r) in rings:
+        for q in range(n_around):
+            pts.append(c + axis * s + r * (ring[q, 0] * e1 + ring[q, 1] * e2))
+    pts.append(c + axis * (length / 2 + radius))
+    nr = len(rings)
+    for q in range(n_around):
+        tris.append((0, 1 + (q + 1) % n_around, 1 + q))
+    for k in range(nr - 1):
+        a0, b0 = 1 + k * n_around, 1 + (k + 1) * n_around
+        for q in range(n_around):
+            q1 = (q + 1) % n_around
+            tris.append((a0 + q, a0 + q1, b0 + q1))
+            tris.append((a0 + q, b0 + q1, b0 + q))
+    last = len(pts) - 1
+    a0 = 1 + (nr - 1) * n_around
+    for q in range(n_around):
+        tris.append((a0 + q, a0 + (q + 1) % n_around, last))
+    return np.ascontiguousarray(np.array(pts, dtype=np.float64)), np.ascontiguousarray(np.array(tris, dtype=np.int32))
+
+
+def rot_matrix(axis, ang):
+    axis = np.asarray(axis, float) / np.linalg.norm(axis)
+    K = np.array([[0, -axis[2], axis[1]], [axis[2], 0, -axis[0]], [-axis[1], axis[0], 0]])
+    return np.eye(3) + math.sin(ang) * K + (1 - math.cos(ang)) * (K @ K)
+
+
+def rigid(xyz0, center, tamp, tfreq, tphase, raxis, ramp, rfreq, rphase):
+    """Rigid motion: translation c(t) = c0 + tamp sin(2 pi tfreq t + tphase) - tamp sin(tphase)
+    per axis, rotation about raxis through the centre by ramp sin(2 pi rfreq t + rphase)."""
+    rel = xyz0 - center
+    k = np.asarray(raxis, float) / np.linalg.norm(raxis)
+
+    def at(t):
+        arg = TWO_PI * tfreq * t + tphase
+        dc = tamp * (np.sin(arg) - np.sin(tphase))
+        vc = tamp * TWO_PI * tfreq * np.cos(arg)
+        th = ramp * (math.sin(TWO_PI * rfreq * t + rphase) - math.sin(rphase))
+        om = ramp * TWO_PI * rfreq * math.cos(TWO_PI * rfreq * t + rphase)
+        Rm = rot_matrix(k, th)
+        r = rel @ Rm.T
+        xyz = center + dc + r
+        vel = vc + om * np.cross(k, r)
+        return np.ascontiguousarray(xyz), np.ascontiguousarray(vel)
+    return at
+
+
+def tube_surface(radius, nx_rings, n_around, lx, yc, zc, outward=True):
+    """Open cylinder along x spanning the periodic length lx: rings at
+    x = k lx / nx_rings, k = 0..nx_rings (the last ring is the first one
+    shifted by the period, so the surface is continuous across x = 0)."""
+    th = TWO_PI * np.arange(n_around) / n_around
+    pts = []
+    for k in range(nx_rings + 1):
+        x = lx * k / nx_rings
+        for q in range(n_around):
+            pts.append((x, yc + radius * math.cos(th[q]), zc + radius * math.sin(th[q])))
+    tris = []
+    for k in range(nx_rings):
+        a0, b0 = k * n_around, (k + 1) * n_around
+        for q in range(n_around):
+            q1 = (q + 1) % n_around
+            if outward:
+                tris.append((a0 + q, a0 + q1, b0 + q1)); tris.append((a0 + q, b0 + q1, b0 + q))
+            else:
+                tris.append((a0 + q, b0 + q1, a0 + q1)); tris.append((a0 + q, b0 + q, b0 + q1))
+    return np.ascontiguousarray(np.array(pts, dtype=np.float64)), np.ascontiguousarray(np.array(tris, dtype=np.int32))
+
+
+def leaflets(r_in, x0, yc, zc, nr, nphi, theta_max):
+    """Three zero-thickness leaflets, each a 120-degree sector of the cross
+    section at x0 hinged on the circle r = r_in.  A material point at
+    distance s = r_in - rho from its hinge moves to x = x0 + s sin(theta),
+    r = r_in - s cos(theta); theta(t) = theta_max (1 - cos 2 pi t) / 2."""
+    rho_s, phi_s, tris = [], [], []
+    for k in range(3):
+        base = len(rho_s)
+        rho_s.append(0.0); phi_s.append(0.0)     # apex of this leaflet
+        for r in range(1, nr + 1):
+            for q in range(nphi + 1):
+                rho_s.append(r_in * r / nr)
+                phi_s.append(TWO_PI * (k + q / nphi) / 3)
+        for q in range(nphi):
+            tris.append((base, base + 1 + q, base + 1 + q + 1))
+        for r in range(1, nr):
+            i0, i1 = base + 1 + (r - 1) * (nphi + 1), base + 1 + r * (nphi + 1)
+            for q in range(nphi):
+                tris.append((i0 + q, i1 + q, i1 + q + 1)); tris.append((i0 + q, i1 + q + 1, i0 + q + 1))
+    rho = np.array(rho_s); phi = np.array(phi_s)
+    s = r_in - rho
+
+    def at(t):
+        th = theta_max * (1 - math.cos(TWO_PI * t)) / 2
+        dth = theta_max * math.pi * math.sin(TWO_PI * t)
+        r = r_in - s * math.cos(th)
+        xyz = np.stack([x0 + s * math.sin(th), yc + r * np.cos(phi), zc + r * np.sin(phi)], 1)
+        dr = s * math.sin(th) * dth
+        vel = np.stack([s * math.cos(th) * dth, dr * np.cos(phi), dr * np.sin(phi)], 1)
+        return xyz, vel
+    return at, np.array(tris, dtype=np.int32)
 
 
 # ---------------------------------------------------------------------------
@@ -248,6 +382,131 @@ def batched_instances(count: int = 32, seed: int = 4, steps: int = 200,
     return out
 
 
+def _concat(parts):
+    """Concatenate bodies (surface functions of t and connectivities) into
+    one surface; triangle indices are global in body order."""
+    tris, offs, off = [], [], 0
+    for at, tri in parts:
+        n = at(0.0)[0].shape[0]
+        tris.append(tri + off)
+        offs.append(off)
+        off += n
+    tri = np.ascontiguousarray(np.concatenate(tris).astype(np.int32))
+
+    def surface_at(t):
+        xs, vs = zip(*(at(t) for at, _ in parts))
+        return np.ascontiguousarray(np.concatenate(xs)), np.ascontiguousarray(np.concatenate(vs))
+    return tri, surface_at
+
+
+def multibody_channel(steps: int = 100, seed: int = 3) -> Workload:
+    """256 x 192 x 256 cells on 4/3 x 1 x 4/3 (cubic cells, dx = 1/192):
+    8 icospheres d = 0.1 (4 subdivisions), 4 capped cylinders d = 0.05 of
+    length 0.5 (horizontal axes), 4 plates 0.2 x 0.2 (56 x 56 quads) in
+    random planes -- about 125,000 triangles -- placed by PCG64 seed 3 with
+    their boxes, grown by their motion and by h + 2 dx, disjoint from each
+    other (periodic images included) and from the walls; each translating
+    (amplitude U[0, 0.02] per axis) and rotating about a random axis
+    (amplitude U[0, pi/12]) at one frequency U[0.5, 2].  Flow: Poiseuille
+    6y(1-y) plus 5% seeded smooth noise, body force f_x = 12/Re_b,
+    Re_b = 5600, dt = 2e-4."""
+    nx, ny, nz = 256, 192, 256
+    lx = lz = 4.0 / 3.0
+    L = np.array([lx, 1.0, lz])
+    dl = L / np.array([nx, ny, nz])
+    clear = 2 * math.sqrt((dl ** 2).sum()) + 2 * dl.max()
+    rng = np.random.default_rng(seed)
+    boxes, parts = [], []
+    for kind in ["cylinder"] * 4 + ["plate"] * 4 + ["sphere"] * 8:
+        if kind == "sphere":
+            xyz, tri = icosphere(4, 0.05, (0.0, 0.0, 0.0))
+        elif kind == "cylinder":
+            ang = rng.uniform(0, math.pi)
+            xyz, tri = capped_cylinder(64, 100, 0.025, 0.5, (0.0, 0.0, 0.0), (math.cos(ang), 0.0, math.sin(ang)))
+        else:
+            xyz, tri = plate(56, 0.2, -0.1, -0.1, 0.0)
+            xyz = xyz @ rot_matrix(rng.normal(size=3), rng.uniform(0, math.pi)).T
+        tamp = rng.uniform(0, 0.02, 3)
+        ramp = rng.uniform(0, math.pi / 12)
+        f = rng.uniform(0.5, 2.0)
+        raxis = rng.normal(size=3)
+        rad = np.linalg.norm(xyz, axis=1).max()
+        grow = 2 * tamp + 2 * rad * math.sin(ramp) + clear
+        lo0, hi0 = xyz.min(0) - grow, xyz.max(0) + grow
+        for _ in range(20000):
+            c = rng.uniform(0, 1, 3) * L
+            lo, hi = c + lo0, c + hi0
+            if lo[1] < 0 or hi[1] > 1:
+                continue
+            ok = True
+            for (l2, h2) in boxes:
+                sep = hi[1] <= l2[1] or h2[1] <= lo[1]
+                for d in (0, 2):
+                    sep = sep or all(hi[d] <= l2[d] + sh or h2[d] + sh <= lo[d] for sh in (-L[d], 0.0, L[d]))
+                if not sep:
+                    ok = False
+                    break
+            if ok:
+                break
+        else:
+            raise RuntimeError("body placement failed")
+        boxes.append((lo, hi))
+        parts.append((rigid(xyz + c, c, tamp, f, rng.uniform(0, TWO_PI, 3), raxis, ramp, f, rng.uniform(0, TWO_PI)),
+                      tri))
+    tri, surface_at = _concat(parts)
+    re_b = 5600.0
+
+    def initial():
+        r2 = np.random.default_rng(seed + 100)
+        y = (np.arange(ny) + 0.5) / ny
+        yv = np.arange(ny + 1) / ny
+        xs, zs = (np.arange(nx) + 0.5) / nx * lx, (np.arange(nz) + 0.5) / nz * lz
+        Z, Y, X = np.meshgrid(zs, y, xs, indexing="ij")
+        noise = np.zeros((3, nz, ny, nx))
+        for q in range(3):
+            for _ in range(4):
+                kx, kz = r2.integers(1, 4, 2)
+                ph = r2.uniform(0, TWO_PI, 2)
+                noise[q] += (0.05 / 4) * np.sin(math.pi * Y) * np.sin(TWO_PI * kx * X / lx + ph[0]) * \
+                    np.cos(TWO_PI * kz * Z / lz + ph[1])
+        u = 6.0 * Y * (1.0 - Y) + noise[0]
+        w = noise[2]
+        v = np.zeros((nz, ny + 1, nx))
+        v[:, 1:ny, :] = 0.5 * (noise[1][:, 1:, :] + noise[1][:, :-1, :])
+        return u, v, w, np.zeros((nz, ny, nx))
+
+    return Workload("channel256", nx, ny, nz, lx, 1.0, lz, re_b, 2e-4, steps, tri, surface_at,
+                    body_force_at=lambda t: (12.0 / re_b, 0.0, 0.0), initial=initial)
+
+
+def leaflet_tube(steps: int = 50) -> Workload:
+    """512 x 384 x 512 cells on 4/3 x 1 x 4/3 (~100M cells): a tube along x
+    (inner radius 0.3, wall 0.02: inner and outer surfaces, 160 x 256 quads
+    each, continuous across the periodic x boundary) through (y, z) =
+    (0.5, 2/3), and three zero-thickness leaflets (120-degree sectors,
+    40 x 80 each) at x = 2/3 hinged on the inner radius, opening to
+    theta_max (1 - cos 2 pi t)/2 with theta_max = pi/3, period 1: 182,800
+    triangles.  Fluid at rest driven by f_x(t) = U'(t) + 8 U(t)/(Re r^2),
+    U(t) = 1 + 0.5 sin 2 pi t (the periodic-x reading of a pulsatile
+    inflow); Re = 1000, dt = 1e-4."""
+    nx, ny, nz = 512, 384, 512
+    lx = lz = 4.0 / 3.0
+    yc, zc, r_in = 0.5, 2.0 / 3.0, 0.3
+    ti, tti = tube_surface(r_in, 160, 256, lx, yc, zc, outward=False)
+    to, tto = tube_surface(r_in + 0.02, 160, 256, lx, yc, zc, outward=True)
+    lat, ltri = leaflets(r_in, 2.0 / 3.0, yc, zc, 40, 80, math.pi / 3)
+    still = lambda xyz: (lambda t: (xyz, np.zeros_like(xyz)))
+    tri, surface_at = _concat([(still(ti), tti), (still(to), tto), (lat, ltri)])
+    re = 1000.0
+
+    def force(t):
+        U = 1.0 + 0.5 * math.sin(TWO_PI * t)
+        dU = 0.5 * TWO_PI * math.cos(TWO_PI * t)
+        return (dU + 8.0 * U / (re * r_in * r_in), 0.0, 0.0)
+
+    return Workload("leaflet512", nx, ny, nz, lx, 1.0, lz, re, 1e-4, steps, tri, surface_at, body_force_at=force)
+
+
 def random_fields(nx: int, ny: int, nz: int, seed: int, amp: float = 1.0):
     """Seeded smooth-ish random velocity and pressure fields (v = 0 on the
     walls) for stage-level parity tests."""
@@ -273,6 +532,8 @@ def random_triangles(n: int, seed: int, lo=0.3, hi=0.7, size: float = 0.15):
 WORKLOADS = {
     "sphere64": oscillating_sphere,
     "plate128": heaving_plate,
+    "channel256": multibody_channel,
+    "leaflet512": leaflet_tube,
 }
 
 

@@ -150,3 +150,40 @@ def test_tagged_nodes_lie_near_the_surface_on_both_sides():
         assert (np.sqrt(d2[c][m]) <= diag + 1e-15).all()
         assert (np.abs(rad[m] - r) < diag + 0.01).all()   # faceted sphere
         assert (rad[m] < r).sum() > 50 and (rad[m] > r).sum() > 50
+
+
+@pytest.mark.parametrize("i0,ni", [(0, 12), (3, 5), (10, 2)])
+def test_windowed_tagging_equals_slice_of_whole_grid(i0, ni):
+    """The x-window variant of Algorithm 1 (for grids too large to tag whole)
+    gives exactly the whole-grid owners of its slab, across the periodic
+    boundary too (the body straddles x = 0)."""
+    g = orc.make_grid(12, 10, 14, 1.0, 1.0, 1.2)
+    xyz, tri = inputs.icosphere(1, 0.2, (0.05, 0.5, 0.6))
+    xyz2, tri2 = inputs.random_triangles(15, 4, lo=0.3, hi=0.7, size=0.25)
+    xyz = np.concatenate([xyz, xyz2])
+    tri = np.concatenate([tri, tri2 + len(inputs.icosphere(1, 0.2)[0])]).astype(np.int32)
+    whole, _ = orc.tag(g, xyz, tri)
+    win = orc.tag_window(g, xyz, tri, i0, ni)
+    for c in range(3):
+        np.testing.assert_array_equal(win[c], whole[c][:, :, i0:i0 + ni])
+    assert sum(int((w >= 0).sum()) for w in win) > 0
+
+
+def test_large_workload_meshes_are_closed_and_clear_of_the_walls():
+    """Generators of the multi-body channel and the leaflet tube: triangle
+    counts, vertex indices in range, every body at least h + 2 dy from the
+    walls over the first steps."""
+    for wl, ntri in ((inputs.multibody_channel(steps=3), 124928), (inputs.leaflet_tube(steps=3), 182800)):
+        assert wl.tri.shape == (ntri, 3)
+        xyz, vel = wl.surface(0)
+        assert wl.tri.min() >= 0 and wl.tri.max() < len(xyz)
+        dl = np.array([wl.lx / wl.nx, wl.ly / wl.ny, wl.lz / wl.nz])
+        h = 2 * np.sqrt((dl ** 2).sum())
+        for s in range(3):
+            xyz, _ = wl.surface(s)
+            assert xyz[:, 1].min() > h + 2 * dl[1] and xyz[:, 1].max() < wl.ly - h - 2 * dl[1]
+    # the closed bodies: every edge of a capped cylinder and a cube shared by two triangles
+    for xyz, tri in (inputs.capped_cylinder(16, 6, 0.1, 0.4, (0.5, 0.5, 0.5), (1.0, 0.0, 0.2)),):
+        e = np.sort(np.concatenate([tri[:, [0, 1]], tri[:, [1, 2]], tri[:, [2, 0]]]), axis=1)
+        _, counts = np.unique(e, axis=0, return_counts=True)
+        assert (counts == 2).all()
