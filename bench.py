@@ -220,7 +220,11 @@ def gpu_arm(args):
             sim.set_surface(dxyz[s], dvel[s])
             sim.step(1)
         sim.sync()
-        tune = sim.autotune(steps=3) if args.autotune else None   # launch shapes (state restored)
+        if args.tune:
+            sim.set_tune(**args.tune)                                  # fixed launch shapes
+            tune = ibm.ibm_get_tune(sim.h)
+        else:
+            tune = sim.autotune(steps=3) if args.autotune else None   # launch shapes (state restored)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
         if world > 1:
             torch.distributed.barrier()
@@ -476,10 +480,12 @@ def main():
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the built-in launch shapes (no autotuning before timing)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-instances leg")
+    ap.add_argument("--tune", default="", help="fixed launch shapes instead of autotuning, e.g. tri_y=3,sweep_zy=2")
     ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--fp64-peak-tflops", type=float, default=1.0,
                     help="measured FP64 FMA throughput of this GB300")
     args = ap.parse_args()
+    args.tune = {k: int(v) for k, v in (kv.split("=") for kv in args.tune.split(",") if kv)}
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     line = reference_arm(args) if args.impl == "reference" else gpu_arm(args)

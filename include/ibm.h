@@ -213,10 +213,12 @@ ibm_status ibm_tag_noalloc(const ibm_grid_desc* desc, int nverts, const double* 
  * rounding order only).  0 in any field means the built-in heuristic. */
 typedef struct {
   int tri_y;          /* per-wavenumber Thomas in y: 1 warp-cooperative scan, 2 one thread per real or
-                         imaginary part */
+                         imaginary part, 3 the same with its forward values in shared memory */
   int sweep_w;        /* grid lines per block of the z and y sweeps: 16, 32 or 64 */
   int fft_lpb;        /* complex lines per block of the x transforms (capped by shared memory) */
   int fft_cols;       /* kx columns per block of the z transforms: a power of two up to 16 */
+  int sweep_zy;       /* z and y sweeps of the FP32 path: 1 shared-memory tile with one thread per line,
+                         2 several lanes per line (affine-map scans) */
   double ms_per_step; /* set by the autotuners: measured time per step of the chosen shapes */
 } ibm_tune;
 

@@ -119,9 +119,11 @@ const char* op_name() {
 // value is clamped by the launchers to what the shape allows.
 struct Tune {
   int tri_y;      // wall-normal Thomas: 1 warp-cooperative scan, 2 one thread per real/imaginary part
+                  // (forward values in global scratch), 3 the same with them in shared memory
   int sweep_w;    // lines per block of the z and y sweeps (16, 32 or 64)
   int fft_lpb;    // complex lines per block of the x transforms
   int fft_cols;   // kx columns per block of the z transforms (power of two)
+  int sweep_zy;   // z and y sweeps (FP32): 1 shared-memory tile, one thread per line; 2 several lanes per line
 };
 
 struct Exec {

@@ -703,6 +703,308 @@ struct SweepXWarp {
   __device__ __forceinline__ void operator()(const Blk& bk) const { sweep_x_warp<T, K>(bk, g, f, flags32, tb, lfirst); }
 };
 
+// ---------------------------------------------------------------------------
+// Warp-cooperative z and y sweeps (FP32 path).  A warp holds G = 32/L lines
+// (consecutive i), L lanes per line, lane s holding rows [s K, s K + K) of
+// its line in registers, so a warp load of one row offset touches L rows of
+// G consecutive floats (whole 32-byte sectors for G = 8), and 32/L times as
+// many lanes work on the recurrences as with one thread per line.  The
+// Thomas recurrences are composed as affine maps per lane and across the L
+// lanes of a line by shuffle scans restricted to the line's lanes (the
+// lines of one warp take different branches).
+// ---------------------------------------------------------------------------
+template <typename T, int L>
+__device__ __forceinline__ AffMap<T> gscan_up_excl(AffMap<T> m, int s, unsigned mask) {
+  for (int o = 1; o < L; o <<= 1) {
+    const T a = __shfl_up_sync(mask, m.A, o, L), b = __shfl_up_sync(mask, m.B, o, L);
+    if (s >= o) m = aff_then(AffMap<T>{a, b}, m);
+  }
+  const T a = __shfl_up_sync(mask, m.A, 1, L), b = __shfl_up_sync(mask, m.B, 1, L);
+  return s == 0 ? AffMap<T>{(T)1, (T)0} : AffMap<T>{a, b};
+}
+template <typename T, int L>
+__device__ __forceinline__ AffMap<T> gscan_down_excl(AffMap<T> m, int s, unsigned mask) {
+  for (int o = 1; o < L; o <<= 1) {
+    const T a = __shfl_down_sync(mask, m.A, o, L), b = __shfl_down_sync(mask, m.B, o, L);
+    if (s + o < L) m = aff_then(AffMap<T>{a, b}, m);
+  }
+  const T a = __shfl_down_sync(mask, m.A, 1, L), b = __shfl_down_sync(mask, m.B, 1, L);
+  return s == L - 1 ? AffMap<T>{(T)1, (T)0} : AffMap<T>{a, b};
+}
+// index of the last identity row before this lane's rows (-1: none), from
+// the lane's own last identity row `mine`
+template <int L>
+__device__ __forceinline__ int last_identity_before(int mine, int s, unsigned mask) {
+  int before = mine;
+  for (int o = 1; o < L; o <<= 1) {
+    const int t2 = __shfl_up_sync(mask, before, o, L);
+    if (s >= o && t2 > before) before = t2;
+  }
+  before = __shfl_up_sync(mask, before, 1, L);
+  return s == 0 ? -1 : before;
+}
+
+// One periodic line (z direction, table slot d = 1) of n rows at elements
+// R[base + r * stride]; f0 = first forcing row or >= n.  Same recurrences
+// as solve_periodic: Sherman-Morrison without forcing rows, else the line
+// rotated to start at f0 (an identity row) with segment tables.
+template <typename T, int K, int L>
+__device__ __forceinline__ void periodic_line_lanes(int n, int f0, int c, int d, T a, const SweepTables<T>& tb, int s,
+                                                    unsigned mask, T* __restrict__ R, long long base,
+                                                    long long stride, const unsigned char* __restrict__ fbytes,
+                                                    long long fbase, long long fstride) {
+  const int q0 = s * K;
+  T v[K];
+  if (f0 >= n) {
+    const T* __restrict__ inv = tb.inv[d];
+    const T* __restrict__ cp = tb.cp[d];
+    const T* __restrict__ zv = tb.zv[d];
+    const T* __restrict__ g0 = tb.g0[d];
+#pragma unroll
+    for (int u = 0; u < K; ++u) v[u] = q0 + u < n ? R[base + (q0 + u) * stride] : (T)0;
+    T acc = (T)0;
+    AffMap<T> mp{(T)1, (T)0};
+#pragma unroll
+    for (int u = 0; u < K; ++u)
+      if (q0 + u < n) {
+        const T iv = __ldg(inv + q0 + u);
+        acc += __ldg(g0 + q0 + u) * v[u];
+        mp = aff_then(mp, AffMap<T>{-a * iv, v[u] * iv});
+      }
+    for (int o = 1; o < L; o <<= 1) acc += __shfl_xor_sync(mask, acc, o, L);
+    const AffMap<T> pre = gscan_up_excl<T, L>(mp, s, mask);
+    T y = pre.B;
+#pragma unroll
+    for (int u = 0; u < K; ++u)
+      if (q0 + u < n) {
+        y = (v[u] - a * y) * __ldg(inv + q0 + u);
+        v[u] = y;
+      }
+    const T ylast = __shfl_sync(mask, y, (n - 1) / K, L);
+    const T fact = (acc + (a / tb.gam[d]) * ylast) / tb.smden[d];
+    mp = AffMap<T>{(T)1, (T)0};
+#pragma unroll
+    for (int u = K - 1; u >= 0; --u)
+      if (q0 + u < n) {
+        const AffMap<T> rm = (q0 + u == n - 1) ? AffMap<T>{(T)0, v[u]} : AffMap<T>{-__ldg(cp + q0 + u), v[u]};
+        mp = aff_then(mp, rm);
+      }
+    const AffMap<T> suf = gscan_down_excl<T, L>(mp, s, mask);
+    T yn = suf.B;
+#pragma unroll
+    for (int u = K - 1; u >= 0; --u)
+      if (q0 + u < n) {
+        yn = (q0 + u == n - 1) ? v[u] : v[u] - __ldg(cp + q0 + u) * yn;
+        R[base + (q0 + u) * stride] = yn - fact * __ldg(zv + q0 + u);
+      }
+    return;
+  }
+  // forcing rows: the line rotated to start at f0 (an identity row)
+  const T* __restrict__ invR = tb.invR[d];
+  const T* __restrict__ cpR = tb.cpR[d];
+  auto rot = [&](int q) { const int r = f0 + q; return r >= n ? r - n : r; };
+  unsigned idm = 0;   // bit u: row q0 + u is an identity row (or past the end)
+#pragma unroll
+  for (int u = 0; u < K; ++u) {
+    const int q = q0 + u;
+    if (q < n) {
+      const int r = rot(q);
+      v[u] = R[base + r * stride];
+      if ((fbytes[fbase + r * fstride] >> c) & 1) idm |= 1u << u;
+    } else {
+      v[u] = (T)0;
+      idm |= 1u << u;
+    }
+  }
+  const T x0 = __shfl_sync(mask, v[0], 0, L);   // row q = 0 is an identity row
+  const int before = last_identity_before<L>(idm == 0 ? -1 : q0 + 31 - __clz(idm & (q0 + K <= n ? ~0u : ((1u << (n - q0 > 0 ? n - q0 : 0)) - 1u))), s, mask);
+  // position of row q0 + u in its segment (rows since the last identity row)
+  auto mseg = [&](int u) {
+    const unsigned below = idm & ((1u << u) - 1u);
+    const int last = below ? q0 + 31 - __clz(below) : before;
+    return q0 + u - last - 1;
+  };
+  AffMap<T> mp{(T)1, (T)0};
+#pragma unroll
+  for (int u = 0; u < K; ++u) {
+    const int q = q0 + u;
+    if (q >= n) break;
+    if ((idm >> u) & 1) { mp = AffMap<T>{(T)0, v[u]}; continue; }
+    const T iv = __ldg(invR + mseg(u));
+    const T dq = (q == n - 1) ? v[u] - a * x0 : v[u];
+    mp = aff_then(mp, AffMap<T>{-a * iv, dq * iv});
+  }
+  const AffMap<T> pre = gscan_up_excl<T, L>(mp, s, mask);
+  T y = pre.B;
+#pragma unroll
+  for (int u = 0; u < K; ++u) {
+    const int q = q0 + u;
+    if (q >= n) break;
+    if ((idm >> u) & 1) { y = v[u]; continue; }
+    const T dq = (q == n - 1) ? v[u] - a * x0 : v[u];
+    y = (dq - a * y) * __ldg(invR + mseg(u));
+    v[u] = y;
+  }
+  mp = AffMap<T>{(T)1, (T)0};
+#pragma unroll
+  for (int u = K - 1; u >= 0; --u) {
+    const int q = q0 + u;
+    if (q >= n) continue;
+    const bool keep = ((idm >> u) & 1) || q == n - 1;
+    mp = aff_then(mp, keep ? AffMap<T>{(T)0, v[u]} : AffMap<T>{-__ldg(cpR + mseg(u)), v[u]});
+  }
+  const AffMap<T> suf = gscan_down_excl<T, L>(mp, s, mask);
+  T yn = suf.B;
+#pragma unroll
+  for (int u = K - 1; u >= 0; --u) {
+    const int q = q0 + u;
+    if (q >= n) continue;
+    const bool keep = ((idm >> u) & 1) || q == n - 1;
+    yn = keep ? v[u] : v[u] - __ldg(cpR + mseg(u)) * yn;
+    if (!((idm >> u) & 1)) R[base + rot(q) * stride] = yn;
+  }
+}
+
+// One wall-normal line of component c (n rows at R[base + q * stride]):
+// the recurrences of solve_wall (segments from the wall (W) or after an
+// identity row (R), the wall diagonal in a tangential last row, Dirichlet
+// walls for v); the solution du is added to the state u^s on output
+// (uhat = u^s + du), as an error-free pair update when Lc holds low parts.
+template <typename T, int K, int L>
+__device__ __forceinline__ void wall_line_lanes(int n, int c, bool any, T a, const SweepTables<T>& tb, int s,
+                                                unsigned mask, const T* __restrict__ R, T* __restrict__ Uc,
+                                                T* __restrict__ Lc, long long base, long long stride,
+                                                const unsigned char* __restrict__ fbytes, long long fbase,
+                                                long long fstride) {
+  const bool tang = c != 1;
+  const int q0 = s * K;
+  T v[K], us[K], ul[K];
+  unsigned idm = 0;
+  // every load up front: the state (and its low parts) is read here, not in
+  // the output loop, where stores to the same arrays would serialise them
+#pragma unroll
+  for (int u = 0; u < K; ++u) {
+    const int q = q0 + u;
+    v[u] = us[u] = ul[u] = (T)0;
+    if (q < n) {
+      const long long id = base + q * stride;
+      v[u] = R[id];
+      us[u] = Uc[id];
+      if (Lc) ul[u] = Lc[id];
+      if (any && ((fbytes[fbase + q * fstride] >> c) & 1)) idm |= 1u << u;
+    }
+  }
+  const int before = last_identity_before<L>(idm ? q0 + 31 - __clz(idm) : -1, s, mask);
+  // position of row q0 + u in its segment, and whether the segment starts at
+  // the wall (tangential components, no identity row before it)
+  auto last_of = [&](int u) {
+    const unsigned below = idm & ((1u << u) - 1u);
+    return below ? q0 + 31 - __clz(below) : before;
+  };
+  auto inv_of = [&](int u, int q) -> T {
+    const int last = last_of(u), m = q - last - 1;
+    if (!tang) return __ldg(tb.vinvR + m);
+    const bool w = last < 0;
+    if (q == n - 1) return w ? __ldg(tb.yinvLW + m) : __ldg(tb.yinvLR + m);
+    return w ? __ldg(tb.yinvW + m) : __ldg(tb.yinvR + m);
+  };
+  auto cp_of = [&](int u) -> T {
+    const int last = last_of(u), m = q0 + u - last - 1;
+    if (!tang) return __ldg(tb.vcpR + m);
+    return last < 0 ? __ldg(tb.ycpW + m) : __ldg(tb.ycpR + m);
+  };
+  AffMap<T> mp{(T)1, (T)0};
+#pragma unroll
+  for (int u = 0; u < K; ++u) {
+    const int q = q0 + u;
+    if (q >= n) break;
+    if ((idm >> u) & 1) { mp = AffMap<T>{(T)0, v[u]}; continue; }
+    const T iv = inv_of(u, q);
+    mp = aff_then(mp, AffMap<T>{-a * iv, v[u] * iv});
+  }
+  const AffMap<T> pre = gscan_up_excl<T, L>(mp, s, mask);
+  T y = pre.B;
+#pragma unroll
+  for (int u = 0; u < K; ++u) {
+    const int q = q0 + u;
+    if (q >= n) break;
+    if ((idm >> u) & 1) { y = v[u]; continue; }
+    y = (v[u] - a * y) * inv_of(u, q);
+    v[u] = y;
+  }
+  mp = AffMap<T>{(T)1, (T)0};
+#pragma unroll
+  for (int u = K - 1; u >= 0; --u) {
+    const int q = q0 + u;
+    if (q >= n) continue;
+    const bool keep = ((idm >> u) & 1) || q == n - 1;
+    mp = aff_then(mp, keep ? AffMap<T>{(T)0, v[u]} : AffMap<T>{-cp_of(u), v[u]});
+  }
+  const AffMap<T> suf = gscan_down_excl<T, L>(mp, s, mask);
+  T yn = suf.B;
+#pragma unroll
+  for (int u = K - 1; u >= 0; --u) {
+    const int q = q0 + u;
+    if (q >= n) continue;
+    const bool keep = ((idm >> u) & 1) || q == n - 1;
+    yn = keep ? v[u] : v[u] - cp_of(u) * yn;
+    const long long id = base + q * stride;
+    if (Lc) {
+      float hi = (float)us[u], lo = (float)ul[u];
+      ff_add(hi, lo, (float)yn);
+      Uc[id] = (T)hi;
+      Lc[id] = (T)lo;
+    } else {
+      Uc[id] = us[u] + yn;
+    }
+  }
+}
+
+// dir 2: z-lines at fixed j (bk.z); dir 1: y-lines at fixed k (bk.z).
+// Block: 256 threads, 8 warps x G lines = 64 consecutive i of component bk.y.
+template <typename T, int K, int L>
+__device__ __forceinline__ void sweep_lanes(const Blk& bk, const Geo& g, const Fields<T>& f,
+                                            const unsigned* __restrict__ flags32, const SweepTables<T>& tb,
+                                            const int* __restrict__ lfirst, int dir) {
+  constexpr int G = 32 / L;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int grp = lane / L, s = lane % L;
+  const unsigned mask = (L == 32) ? 0xFFFFFFFFu : (((1u << L) - 1u) << (grp * L));
+  const int c = bk.y;
+  const int i = bk.x * (8 * G) + wid * G + grp;
+  if (i >= g.nx) return;   // whole line groups only (their lanes share i)
+  const int pl = planes(g, c);
+  const unsigned char* fbytes = reinterpret_cast<const unsigned char*>(flags32);
+  T* __restrict__ R = f.R[c];
+  if (dir == 2) {
+    if (c == 1 && (int)bk.z >= g.ny - 1) return;   // v has ny-1 interior planes
+    const int j = (c == 1 ? 1 : 0) + bk.z;
+    const long long base = fidx(g, c, i, j, 0), stride = (long long)pl * g.nx;
+    const long long fbase = cidx(g, i, j, 0), fstride = (long long)g.ny * g.nx;
+    periodic_line_lanes<T, K, L>(g.nz, lfirst[line_z(g, c, i, j)], c, 1, -tb.off[2], tb, s, mask, R, base, stride,
+                                 fbytes, fbase, fstride);
+  } else {
+    const int k = bk.z;
+    const int jj0 = c == 1 ? 1 : 0;
+    const int n = c == 1 ? g.ny - 1 : g.ny;
+    const long long base = fidx(g, c, i, jj0, k), fbase = cidx(g, i, jj0, k);
+    T* __restrict__ Uc = c == 0 ? f.u : (c == 1 ? f.v : f.w);
+    wall_line_lanes<T, K, L>(n, c, lfirst[line_y(g, c, i, k)] < g.ny, -tb.off[1], tb, s, mask, R, Uc, f.lo[c], base,
+                             g.nx, fbytes, fbase, g.nx);
+  }
+}
+template <typename T, int K, int L>
+struct SweepLanes {
+  static constexpr int kThreads = 256;
+  Geo g;
+  Fields<T> f;
+  const unsigned* flags32;
+  SweepTables<T> tb;
+  const int* lfirst;
+  int dir;
+  __device__ __forceinline__ void operator()(const Blk& bk) const { sweep_lanes<T, K, L>(bk, g, f, flags32, tb, lfirst, dir); }
+};
+
 // z- and y-sweeps: a block holds the lines of W consecutive i (one plane
 // position each) for all n rows, tile [n][W] (row m of line t at m*W + t);
 // rows are loaded and stored coalesced.  dir 2: z-lines at fixed j
@@ -821,6 +1123,28 @@ static void sweep_x_warp(const Geo& g, const Fields<T>& f, const TagBuffers& b, 
   ex.launch(dim3((lines + 7) / 8, 3), dim3(256), 0, SweepXWarp<T, K>{g, f, b.flags32, tb, b.lines.x});
 }
 
+// Lanes-per-line sweep for lines of up to n_max rows (the shape's extent):
+// 4 lanes x K rows (K = 4..16), 8 lanes x 16 or 32 rows (16 rows per lane
+// keep the kernel near 80 registers); false if too long.
+template <typename T, int K, int L>
+static void lanes_launch(const Geo& g, const Fields<T>& f, const TagBuffers& b, const SweepTables<T>& tb, Exec& ex,
+                         int dir, int planes_z) {
+  constexpr int per_block = 8 * (32 / L);
+  ex.launch(dim3((g.nx + per_block - 1) / per_block, 3, planes_z), dim3(256), 0,
+            SweepLanes<T, K, L>{g, f, b.flags32, tb, dir == 2 ? b.lines.z : b.lines.y, dir});
+}
+template <typename T>
+static bool sweep_lanes_launch(const Geo& g, const Fields<T>& f, const TagBuffers& b, const SweepTables<T>& tb,
+                               Exec& ex, int n_max, int dir, int planes_z) {
+  if (n_max <= 16) lanes_launch<T, 4, 4>(g, f, b, tb, ex, dir, planes_z);
+  else if (n_max <= 32) lanes_launch<T, 8, 4>(g, f, b, tb, ex, dir, planes_z);
+  else if (n_max <= 64) lanes_launch<T, 16, 4>(g, f, b, tb, ex, dir, planes_z);
+  else if (n_max <= 128) lanes_launch<T, 16, 8>(g, f, b, tb, ex, dir, planes_z);
+  else if (n_max <= 256) lanes_launch<T, 32, 8>(g, f, b, tb, ex, dir, planes_z);
+  else return false;
+  return true;
+}
+
 // Launch shapes (lines per block, registers per lane) follow ex.shape, so
 // every instance of a batch uses the same ones; grids follow the instance.
 template <typename T>
@@ -842,15 +1166,18 @@ void launch_sweeps(const Geo& g, const Fields<T>& f, const TagBuffers& b, const 
     ex.launch(dim3((nlines + W - 1) / W, 3), dim3(W), sweep_smem<T>(W, sh.nx, sh.nx + 1),
               SweepX<T>{g, f, b.flags32, tb, b.lines.x});
   }
+  // z and y: several lanes per line (FP32, lines up to 256 rows) unless the
+  // tuning asks for the shared-memory tile with one thread per line
+  const bool lanes = sizeof(T) == 4 && ex.tune.sweep_zy != 1;
   ex.mark(ST_SWEEP_Z);
-  {
+  if (!(lanes && sweep_lanes_launch(g, f, b, tb, ex, sh.nz, 2, g.ny))) {
     int W = sweep_width<T>(sh.nz);
     if (ex.tune.sweep_w > 0 && ex.tune.sweep_w < W) W = ex.tune.sweep_w;
     ex.launch(dim3((g.nx + W - 1) / W, 3, g.ny), dim3(W), sweep_smem<T>(W, sh.nz, sh.nz),
               SweepZY<T>{g, f, b.flags32, tb, b.lines.z, 2});
   }
   ex.mark(ST_SWEEP_Y);
-  {
+  if (!(lanes && sweep_lanes_launch(g, f, b, tb, ex, sh.ny, 1, g.nz))) {
     const int tiles = f.lo[0] ? 3 : 2;
     int W = sweep_width<T>(sh.ny, tiles);
     if (ex.tune.sweep_w > 0 && ex.tune.sweep_w < W) W = ex.tune.sweep_w;

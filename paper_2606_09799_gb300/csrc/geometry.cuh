@@ -59,7 +59,7 @@ __device__ inline void tri_const(const double a[3], const double b[3], const dou
 struct TriF32 {
   float ab[3], ac[3], bc[3];
   float aa, abac, cc, iaa, icc, ibc, iden;
-  long long ia[3][2];
+  int ia[3][2];     // lattice index of the first vertex (32-bit: no 64-bit conversions in the screen)
   float fr[3][2];
   float del[3], diag2;
 };

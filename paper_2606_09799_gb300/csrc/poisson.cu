@@ -716,6 +716,83 @@ struct TriYWarp {
   __device__ __forceinline__ void operator()(const Blk& bk) const { tri_y_warp<T, L, Rr>(bk, g, f, cp, inv); }
 };
 
+// Sequential Thomas per (kx, kz, part) with the forward values in shared
+// memory: the fewest FP64 operations per row (forward: one FMA and one
+// multiply; backward: one FMA), no scratch traffic, loads issued 16 rows at
+// a time.  Block: `blockDim.x` systems (consecutive kx, real and imaginary
+// parts interleaved, so loads of the spectrum are coalesced); shared memory
+// [row][thread] FP64.
+template <typename T>
+__device__ __forceinline__ void tri_y_smem(const Blk& bk, const Geo& g, const Fields<T>& f, const double* __restrict__ cp,
+                                           const double* __restrict__ inv) {
+  extern __shared__ unsigned char smem_raw[];
+  double* fw = reinterpret_cast<double*>(smem_raw);
+  const int nkx = g.nkx, ny = g.ny, nt = blockDim.x, tid = threadIdx.x;
+  const long long l = (long long)bk.x * blockDim.x + threadIdx.x;
+  if (l >= 2ll * nkx * g.nz) return;   // no barrier below: early exit is safe
+  const int part = (int)(l & 1);
+  const long long mode = l >> 1;
+  const long long kx = mode % nkx, kz = mode / nkx;
+  const long long base = kz * (long long)ny * nkx + kx, stride = nkx;
+  T* __restrict__ sp = reinterpret_cast<T*>(f.spec);
+  const double a = g.idy * g.idy;
+  const bool singular = (kx == 0 && kz == 0);
+  constexpr int B = 16;
+  double pr = 0.0;
+  for (int j0 = 0; j0 < ny; j0 += B) {
+    double zb[B], ib[B];
+#pragma unroll
+    for (int u = 0; u < B; ++u)
+      if (j0 + u < ny) {
+        const long long id = base + (long long)(j0 + u) * stride;
+        zb[u] = (double)sp[2 * id + part];
+        ib[u] = __ldg(inv + id);
+      }
+#pragma unroll
+    for (int u = 0; u < B; ++u)
+      if (j0 + u < ny) {
+        const int j = j0 + u;
+        pr = (j == 0) ? (singular ? 0.0 : zb[u] * ib[u]) : (zb[u] - a * pr) * ib[u];
+        fw[j * nt + tid] = pr;
+      }
+  }
+  double x = pr, sr = pr;
+  if (!singular) sp[2 * (base + (long long)(ny - 1) * stride) + part] = (T)x;
+  for (int j1 = ny - 2; j1 >= 0; j1 -= B) {
+    double cb[B];
+#pragma unroll
+    for (int u = 0; u < B; ++u)
+      if (j1 - u >= 0) cb[u] = __ldg(cp + base + (long long)(j1 - u) * stride);
+#pragma unroll
+    for (int u = 0; u < B; ++u)
+      if (j1 - u >= 0) {
+        const int j = j1 - u;
+        x = fw[j * nt + tid] - cb[u] * x;
+        if (singular) {
+          fw[j * nt + tid] = x;
+          sr += x;
+        } else {
+          sp[2 * (base + (long long)j * stride) + part] = (T)x;
+        }
+      }
+  }
+  if (singular) {
+    // zero-mean gauge of the (0, 0) system, from the FP64 values
+    fw[(ny - 1) * nt + tid] = pr;
+    const double mr = sr / ny;
+    for (int j = 0; j < ny; ++j) sp[2 * (base + (long long)j * stride) + part] = (T)(fw[j * nt + tid] - mr);
+  }
+}
+template <typename T>
+struct TriYSmem {
+  static constexpr int kThreads = 64;
+  Geo g;
+  Fields<T> f;
+  const double* cp;
+  const double* inv;
+  __device__ __forceinline__ void operator()(const Blk& bk) const { tri_y_smem<T>(bk, g, f, cp, inv); }
+};
+
 // Tabulate the pivots of every (kx, kz) system once per grid.
 __global__ void k_build_tri_tables(Geo g, const double* __restrict__ lamx, const double* __restrict__ lamz,
                                    double* cp, double* inv) {
@@ -862,9 +939,16 @@ void launch_poisson(const Geo& g, const Fields<T>& f, const TagBuffers& b, const
   double* fwd = sizeof(T) == sizeof(double) ? nullptr : reinterpret_cast<double*>(f.scr);
   // wall-normal Thomas for every (kx, kz): warp-cooperative when the rows fit
   // the registers (16 per lane), else one thread per real/imaginary part
-  const int tri = tu.tri_y == 2 || sh.ny > 32 * 16 ? 2 : 1;
+  // threads per block of the shared-memory variant: its FP64 forward values
+  // (8 B per row and system) must fit 160 KB
+  const int tsm = 64ll * 8 * sh.ny <= 160 * 1024 ? 64 : (32ll * 8 * sh.ny <= 160 * 1024 ? 32 : 0);
+  int tri = tu.tri_y == 2 || sh.ny > 32 * 16 ? 2 : 1;
+  if (tu.tri_y == 3 && tsm > 0) tri = 3;
   auto tri_solve = [&]() {
-    if (tri == 1 && sh.ny <= 8 * 16) {
+    if (tri == 3) {
+      ex.launch(dim3((unsigned)((2 * tlines + tsm - 1) / tsm)), dim3(tsm), (size_t)tsm * 8 * sh.ny,
+                TriYSmem<T>{g, f, tb.cp, tb.inv});
+    } else if (tri == 1 && sh.ny <= 8 * 16) {
       const long long warps = (long long)((g.nkx + 3) / 4) * g.nz;
       ex.launch(dim3((unsigned)((warps * 32 + 127) / 128)), dim3(128), 0, TriYWarp<T, 8, 16>{g, f, tb.cp, tb.inv});
     } else if (tri == 1) {
@@ -916,6 +1000,7 @@ void set_fft_smem_limits() {
   op_smem_limit<FftXInv<T>>(maxsm);
   op_smem_limit<FftZ<T, false>>(maxsm);
   op_smem_limit<FftZ<T, true>>(maxsm);
+  op_smem_limit<TriYSmem<T>>(160 * 1024);
 }
 
 void init_kernel_attributes() {

@@ -5,6 +5,7 @@
 // graph that ibm_step replays on the caller's stream.
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -840,7 +841,8 @@ struct Knob {
 };
 
 static std::vector<Knob> tune_knobs() {
-  return {{&Tune::tri_y, {1, 2}}, {&Tune::sweep_w, {64, 32, 16}}, {&Tune::fft_lpb, {0, 8, 4, 2}},
+  return {{&Tune::sweep_zy, {2, 1}}, {&Tune::tri_y, {1, 2, 3}}, {&Tune::sweep_w, {64, 32, 16}},
+          {&Tune::fft_lpb, {0, 8, 4, 2}},
           {&Tune::fft_cols, {16, 8, 4}}};
 }
 
@@ -898,16 +900,25 @@ static void tune_out(const Tune& t, double ms, ibm_tune* out) {
   out->sweep_w = t.sweep_w;
   out->fft_lpb = t.fft_lpb;
   out->fft_cols = t.fft_cols;
+  out->sweep_zy = t.sweep_zy;
   out->ms_per_step = ms;
 }
 
 // Time `steps` replays of graph-making function `run_trial` for every
 // candidate; returns the best configuration in `best`.
+static void tune_log(const Tune& t, double ms) {
+  static const bool on = getenv("IBM_AUTOTUNE_LOG") != nullptr;
+  if (on)
+    fprintf(stderr, "ibm autotune: tri_y %d sweep_w %d fft_lpb %d fft_cols %d sweep_zy %d -> %.4f ms/step\n", t.tri_y,
+            t.sweep_w, t.fft_lpb, t.fft_cols, t.sweep_zy, ms);
+}
+
 template <class Trial>
 static ibm_status autotune_loop(Tune& best, int steps, Trial trial, double* best_ms) {
   double bms = 0.0;
   ibm_status s = trial(best, steps, &bms);
   if (s != IBM_OK) return s;
+  tune_log(best, bms);
   for (const Knob& k : tune_knobs()) {
     for (int v : k.values) {
       if (best.*(k.field) == v) continue;
@@ -916,6 +927,7 @@ static ibm_status autotune_loop(Tune& best, int steps, Trial trial, double* best
       double ms = 0.0;
       s = trial(cand, steps, &ms);
       if (s != IBM_OK) return s;
+      tune_log(cand, ms);
       if (ms < bms * 0.995) {
         bms = ms;
         best = cand;
@@ -1457,16 +1469,17 @@ ibm_status ibm_profile_stages(ibm_handle h, int nsteps, double* ms, int64_t* ker
 // ---- tuning -------------------------------------------------------------------
 static bool tune_valid(const ibm_tune* t) {
   if (!t) return false;
-  if (t->tri_y < 0 || t->tri_y > 2) return false;
+  if (t->tri_y < 0 || t->tri_y > 3) return false;
   if (t->sweep_w != 0 && t->sweep_w != 16 && t->sweep_w != 32 && t->sweep_w != 64) return false;
   if (t->fft_lpb < 0 || t->fft_lpb > 2048) return false;
   if (t->fft_cols < 0 || t->fft_cols > 16 || (t->fft_cols & (t->fft_cols - 1))) return false;
+  if (t->sweep_zy < 0 || t->sweep_zy > 2) return false;
   return true;
 }
 
 ibm_status ibm_set_tune(ibm_handle h, const ibm_tune* t) {
   if (!h || !tune_valid(t)) return IBM_ERR_ARG;
-  h->tune = Tune{t->tri_y, t->sweep_w, t->fft_lpb, t->fft_cols};
+  h->tune = Tune{t->tri_y, t->sweep_w, t->fft_lpb, t->fft_cols, t->sweep_zy};
   invalidate(h);
   return IBM_OK;
 }
@@ -1627,7 +1640,7 @@ ibm_status ibm_batch_profile_stages(ibm_batch_handle b, int nsteps, double* ms, 
 
 ibm_status ibm_batch_set_tune(ibm_batch_handle b, const ibm_tune* t) {
   if (!b || !tune_valid(t)) return IBM_ERR_ARG;
-  b->tune = Tune{t->tri_y, t->sweep_w, t->fft_lpb, t->fft_cols};
+  b->tune = Tune{t->tri_y, t->sweep_w, t->fft_lpb, t->fft_cols, t->sweep_zy};
   b->built = false;
   return IBM_OK;
 }

@@ -131,7 +131,7 @@ __device__ __forceinline__ void tri_setup(const Blk& bk, const Geo& g, const Sur
     for (int hf = 0; hf < 2; ++hf) {
       const double off = hf ? 0.5 : 0.0;
       const double q = floor(A[d] * idel[d] - off);
-      F.ia[d][hf] = (long long)q;
+      F.ia[d][hf] = (int)q;
       F.fr[d][hf] = (float)(A[d] - (q + off) * del[d]);
     }
   }
@@ -174,8 +174,8 @@ __device__ __forceinline__ void screen_eval(const TriF32& F, int c, const int id
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     // static indices only (a runtime index would put F in local memory)
-    const float pf = (float)((long long)idx3[d] - F.ia[d][0]) * F.del[d] - F.fr[d][0];
-    const float ph = (float)((long long)idx3[d] - F.ia[d][1]) * F.del[d] - F.fr[d][1];
+    const float pf = (float)(idx3[d] - F.ia[d][0]) * F.del[d] - F.fr[d][0];
+    const float ph = (float)(idx3[d] - F.ia[d][1]) * F.del[d] - F.fr[d][1];
     p[d] = d == c ? pf : ph;
   }
   const float d1 = F.ab[0] * p[0] + F.ab[1] * p[1] + F.ab[2] * p[2];
@@ -291,7 +291,12 @@ __device__ __forceinline__ void tag_pairs(const Blk& bk, const Geo& g, const Sur
   if (screen) F = rec->f;
   // index of a lattice point in the comp_off layout of the three grids
   auto node_of = [&](int c, const long long i3[3]) -> unsigned {
-    return (unsigned)(comp_off(g, c) + fidx(g, c, wrapi(i3[0], g.nx), i3[1], wrapi(i3[2], g.nz)));
+    int i = (int)i3[0], k = (int)i3[2];
+    i = i < 0 ? i + g.nx : (i >= g.nx ? i - g.nx : i);   // a box is narrower than the domain
+    k = k < 0 ? k + g.nz : (k >= g.nz ? k - g.nz : k);
+    const unsigned pl = c == 1 ? (unsigned)g.ny + 1u : (unsigned)g.ny;
+    const unsigned off = c == 0 ? 0u : (c == 1 ? (unsigned)g.ncell : (unsigned)(g.ncell + g.nvf));
+    return off + ((unsigned)k * pl + (unsigned)i3[1]) * (unsigned)g.nx + (unsigned)i;
   };
   // warp-aggregated append of this lane's item (if `has`) to a list
   auto append = [&](bool has, unsigned* counter, auto store) {

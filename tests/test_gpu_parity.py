@@ -282,3 +282,27 @@ def test_candidate_capacity_grows_for_large_triangles():
     g.sync()
     d = g.diag()
     assert d["nforce"][0] == 2 * 64 * 64
+
+
+@pytest.mark.parametrize("tune", [dict(tri_y=1), dict(tri_y=2, sweep_w=16), dict(tri_y=3, fft_lpb=2, fft_cols=2),
+                                  dict(tri_y=3, sweep_zy=1, sweep_w=64, fft_lpb=8, fft_cols=16)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-5)])
+def test_every_launch_shape_matches_oracle(tune, precision, tol):
+    """Every choice the autotuner can make (Thomas variant, sweep form and
+    width, FFT tiling) computes the same step: against the oracle on a
+    ragged grid with a moving sphere, 4 steps."""
+    wl = inputs.oscillating_sphere(n=48, steps=4, subdiv=2)
+    o = OracleSim(48, 37, 96, 1.0, 0.9, 1.6, re=150.0, dt=2e-3)
+    g = ibm.Simulation(48, 37, 96, 1.0, 0.9, 1.6, re=150.0, dt=2e-3, precision=precision)
+    ibm.ibm_set_tune(g.h, **tune)
+    for s in range(4):
+        xyz, vel = wl.surface(s)
+        o.set_surface(xyz, vel, wl.tri)
+        g.set_surface(xyz, vel, wl.tri)
+        o.step()
+        g.step()
+    gu, gv, gw, gp = g.fields()
+    err = max(np.abs(o.u - gu).max(), np.abs(o.v - gv).max(), np.abs(o.w - gw).max())
+    assert err <= tol, err
+    for c, own in enumerate(g.tags()):
+        np.testing.assert_array_equal(own, o.owners[c])
