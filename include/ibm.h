@@ -92,7 +92,9 @@ typedef struct {
   int scheme;          /* IBM_RK2_CN (default) or IBM_AB_CN */
   int ybc;             /* IBM_NOSLIP (default) or IBM_FREESLIP */
   int precision;       /* IBM_FP64, IBM_MIXED or IBM_MIXED_FAST (see above) */
-  int use_q;           /* 1: Eq. elliptic_mod with q (the paper's method); 0: Eq. elliptic */
+  int use_q;           /* 1: Eq. elliptic_mod with the uniform q_F (the paper's method, mass
+                          conserving); 2: the same with the energy- and mass-conserving shape of
+                          App. B, q_F^k = a + b (p^k - e^k); 0: Eq. elliptic (no q) */
 } ibm_grid_desc;
 
 typedef struct {

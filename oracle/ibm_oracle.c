@@ -740,6 +740,59 @@ double orc_rhs_poisson(const orc_grid* g, const double* div, const uint8_t* isb,
   return qF;
 }
 
+/* Energy- and mass-conserving shape of q on the fluid cells (App. B,
+ * the minimiser of the augmented Lagrangian with the mass and the inviscid
+ * kinetic-energy constraints):
+ *   q_F^k = (-A S2 + B S1)/C + (A S1 - B S0)/C (p^k - e^k),
+ *   S_i = sum_{C_F} (p - e)^i dV, A = sum_{C_B} Du dV,
+ *   B = sum_{C_B} (p - e) Du dV, C = S0 S2 - S1^2.
+ * Readings: p is the pressure p^s of the sub-stage, e = |u|^2/2 with the
+ * velocity averaged to the cell centre from the provisional field uhat
+ * (whose divergence div[] is); q = Du on C_B (Eq. q_boundary).  When C
+ * vanishes (p - e uniform on C_F) the energy constraint is a multiple of
+ * the mass one and the uniform shape -A/S0 is returned.  q[] gets the
+ * field, coef[] = {alpha, beta, A, B, S0, S1, S2}. */
+void orc_q_energy(const orc_grid* g, const double* div, const uint8_t* isb, const double* p, const double* u,
+                  const double* v, const double* w, double* q, double* coef) {
+  const long nx = g->nx, ny = g->ny, nz = g->nz, n = nx * ny * nz;
+  const double dV = (g->dx * g->dy) * g->dz;
+  double* pe = malloc(sizeof(double) * n);
+  for (long k = 0; k < nz; ++k)
+    for (long j = 0; j < ny; ++j)
+      for (long i = 0; i < nx; ++i) {
+        const long id = (k * ny + j) * nx + i;
+        const long ip = (i + 1) % nx, kp = (k + 1) % nz;
+        const double uc = 0.5 * (u[(k * ny + j) * nx + i] + u[(k * ny + j) * nx + ip]);
+        const double vc = 0.5 * (v[(k * (ny + 1) + j) * nx + i] + v[(k * (ny + 1) + j + 1) * nx + i]);
+        const double wc = 0.5 * (w[(k * ny + j) * nx + i] + w[(kp * ny + j) * nx + i]);
+        const double e = 0.5 * (uc * uc + vc * vc + wc * wc);
+        pe[id] = p[id] - e;
+      }
+  double S0 = 0.0, S1 = 0.0, S2 = 0.0, A = 0.0, B = 0.0;
+  for (long id = 0; id < n; ++id) {
+    if (isb[id]) {
+      A += div[id] * dV;
+      B += pe[id] * div[id] * dV;
+    } else {
+      S0 += dV;
+      S1 += pe[id] * dV;
+      S2 += pe[id] * pe[id] * dV;
+    }
+  }
+  const double C = S0 * S2 - S1 * S1;
+  double alpha, beta;
+  if (S0 > 0.0 && C > 1e-14 * S0 * S2) {
+    alpha = (-A * S2 + B * S1) / C;
+    beta = (A * S1 - B * S0) / C;
+  } else {
+    alpha = S0 > 0.0 ? -A / S0 : 0.0;
+    beta = 0.0;
+  }
+  for (long id = 0; id < n; ++id) q[id] = isb[id] ? div[id] : alpha + beta * pe[id];
+  coef[0] = alpha; coef[1] = beta; coef[2] = A; coef[3] = B; coef[4] = S0; coef[5] = S1; coef[6] = S2;
+  free(pe);
+}
+
 /* ------------------------------------------------------------------ */
 /* Wall-normal solve of the Poisson equation per Fourier mode (Eq.     */
 /* elliptic, solved with FFTs in x and z and the Thomas algorithm in   */

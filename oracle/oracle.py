@@ -80,6 +80,7 @@ def lib():
             L.orc_tag_alg1.argtypes = [_GP, _I, _P, _I, _P, _P, _P]
             L.orc_tag_brute.argtypes = [_GP, _I, _P, _I, _P, _P, _P]
             L.orc_tag_alg1_window.argtypes = [_GP, _I, _P, _I, _P, ctypes.c_long, ctypes.c_long, _P, _P]
+            L.orc_q_energy.argtypes = [_GP, _P, _P, _P, _P, _P, _P, _P, _P]
             L.orc_force.argtypes = [_GP, _I, _P, _P, _P, _P, _P, _P, _D]
             L.orc_force.restype = _I
             L.orc_slip.argtypes = [_GP, _I, _P, _P, _P, _P, _P, _D, _P, _P]
@@ -223,6 +224,15 @@ def rhs_poisson(g: Grid, div, isb, use_q, adt):
     return out, qF, A.value, VF.value
 
 
+def q_energy(g: Grid, div, isb, p, u, v, w):
+    """Energy- and mass-conserving q (App. B): (q field, (alpha, beta, A, B,
+    S0, S1, S2))."""
+    q = np.zeros_like(div)
+    coef = np.zeros(7)
+    lib().orc_q_energy(ctypes.byref(g), _p(div), _p(isb), _p(p), _p(u), _p(v), _p(w), _p(q), _p(coef))
+    return q, coef
+
+
 def project(g: Grid, u, v, w, p, phi, adt, re):
     lp = lap_c(g, phi)
     lib().orc_project(ctypes.byref(g), _p(u), _p(v), _p(w), _p(p), _p(phi), _p(lp), adt, re)
@@ -234,7 +244,8 @@ class OracleSim:
     def __init__(self, nx, ny, nz, lx=1.0, ly=1.0, lz=1.0, re=100.0, dt=1e-3, scheme=RK2_CN, ybc=0,
                  use_q=True):
         self.g = make_grid(nx, ny, nz, lx, ly, lz, ybc)
-        self.re, self.dt, self.scheme, self.use_q = float(re), float(dt), scheme, bool(use_q)
+        # use_q: 0 none, 1 uniform q_F (Eq. for q_F, mass only), 2 energy- and mass-conserving shape (App. B)
+        self.re, self.dt, self.scheme, self.use_q = float(re), float(dt), scheme, int(use_q)
         g = self.g
         self.u = np.zeros(field_shape(g, 0))
         self.v = np.zeros(field_shape(g, 1))
@@ -311,8 +322,13 @@ class OracleSim:
         rhs = np.zeros_like(div)
         A = ctypes.c_double()
         VF = ctypes.c_double()
-        qF = L.orc_rhs_poisson(ctypes.byref(g), _p(div), _p(self.isb), int(self.use_q), adt, _p(rhs),
+        qF = L.orc_rhs_poisson(ctypes.byref(g), _p(div), _p(self.isb), min(self.use_q, 1), adt, _p(rhs),
                                ctypes.byref(A), ctypes.byref(VF))
+        if self.use_q == 2:
+            qk, coef = q_energy(g, div, self.isb, self.p, self.u, self.v, self.w)
+            rhs = (div - qk) / adt
+            qF = coef[0]
+            self.last.update(q_field=qk, q_coef=coef)
         phi = poisson(g, rhs)
         lp = lap_c(g, phi)
         L.orc_project(ctypes.byref(g), _p(self.u), _p(self.v), _p(self.w), _p(self.p), _p(phi), _p(lp), adt, re)

@@ -137,7 +137,7 @@ struct IbScatter {
 template <typename T>
 void launch_ib_force(const Geo& g, const Surf& s, const Fields<T>& f, const TagBuffers& b, DevState* ds,
                      Exec& ex) {
-  const dim3 gb = grid_if(s.nt > 0, dim3(num_sms() * 4));
+  const dim3 gb = grid_if(s.nt > 0, dim3(scaled_blocks(g, 4096, 8, num_sms() * 4)));
   ex.mark(ST_FORCE);
   ex.launch(gb, dim3(128), 0, IbForce<T>{g, s, f, b.flist, b.cap, ds});
   ex.launch(gb, dim3(256), 0, IbScatter<T>{f, b.flist, b.cap, ds});
@@ -1203,7 +1203,7 @@ void init_sweep_attributes() {
 // u_w = (u(x^f) - alpha u(x^e)) / (1 - alpha), eps = u_w - U.
 // Fixed-order two-level reduction of sum |eps| per component.
 // ---------------------------------------------------------------------------
-constexpr int SLIP_BLOCKS = 256, SLIP_THREADS = 256;
+constexpr int SLIP_BLOCKS = 256, SLIP_THREADS = 256;   // SLIP_BLOCKS: the most partial sums
 
 template <typename T>
 __device__ __forceinline__ void slip_partial(const Blk& bk, const Geo& g, const Surf& s, const Fields<T>& f,
@@ -1211,7 +1211,7 @@ __device__ __forceinline__ void slip_partial(const Blk& bk, const Geo& g, const 
                                                                DevState* ds, double* partial) {
   __shared__ double red[3][SLIP_THREADS];
   const unsigned n = min(ds->nforce_c[0] + ds->nforce_c[1] + ds->nforce_c[2], cap);
-  const unsigned per = (n + SLIP_BLOCKS - 1) / SLIP_BLOCKS;
+  const unsigned per = (n + bk.gx - 1) / bk.gx;
   const unsigned e0 = bk.x * per, e1 = min(n, e0 + per);
   double acc[3] = {0.0, 0.0, 0.0};
   for (unsigned e = e0 + threadIdx.x; e < e1; e += SLIP_THREADS) {
@@ -1259,10 +1259,10 @@ struct SlipPartial {
   __device__ __forceinline__ void operator()(const Blk& bk) const { slip_partial<T>(bk, g, s, f, flist, cap, ds, partial); }
 };
 
-__device__ __forceinline__ void slip_final(const Blk& bk, const double* partial, DevState* ds) {
+__device__ __forceinline__ void slip_final(const Blk& bk, const double* partial, DevState* ds, int nblk) {
   if (threadIdx.x < 3) {
     double s = 0.0;
-    for (int b = 0; b < SLIP_BLOCKS; ++b) s += partial[b * 3 + threadIdx.x];
+    for (int b = 0; b < nblk; ++b) s += partial[b * 3 + threadIdx.x];
     ds->slip_sum[threadIdx.x] = s;
     if (!isfinite(s)) atomicOr(&ds->err, ERR_NONFINITE);
   }
@@ -1271,15 +1271,17 @@ struct SlipFinal {
   static constexpr int kThreads = 32;
   const double* partial;
   DevState* ds;
-  __device__ __forceinline__ void operator()(const Blk& bk) const { slip_final(bk, partial, ds); }
+  int nblk;
+  __device__ __forceinline__ void operator()(const Blk& bk) const { slip_final(bk, partial, ds, nblk); }
 };
 
 template <typename T>
 void launch_slip(const Geo& g, const Surf& s, const Fields<T>& f, const TagBuffers& b, double* partial,
                  DevState* ds, Exec& ex) {
   ex.mark(ST_SLIP);
-  ex.launch(grid_if(s.nt > 0, dim3(SLIP_BLOCKS)), dim3(SLIP_THREADS), 0, SlipPartial<T>{g, s, f, b.flist, b.cap, ds, partial});
-  ex.launch(grid_if(s.nt > 0, dim3(1)), dim3(32), 0, SlipFinal{partial, ds});
+  const int nblk = reduce_blocks(g, 8192, SLIP_BLOCKS);
+  ex.launch(grid_if(s.nt > 0, dim3(nblk)), dim3(SLIP_THREADS), 0, SlipPartial<T>{g, s, f, b.flist, b.cap, ds, partial});
+  ex.launch(grid_if(s.nt > 0, dim3(1)), dim3(32), 0, SlipFinal{partial, ds, nblk});
 }
 
 #define IBM_INST(T)                                                                                             \

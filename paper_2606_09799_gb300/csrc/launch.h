@@ -12,6 +12,19 @@ namespace ibm {
 
 int num_sms();
 
+// Blocks of a grid-stride kernel whose work grows with the instance: one per
+// `cells` cells of the grid, within [lo, hi] (hi: enough to fill the GPU).
+// Small instances of a batch then launch few blocks instead of a full GPU's
+// worth each.
+inline int scaled_blocks(const Geo& g, long long cells, int lo, int hi) {
+  const long long b = g.ncell / cells;
+  return (int)(b < lo ? lo : (b > hi ? hi : b));
+}
+// Blocks of the fixed-order two-level reductions (q_F, no-slip error):
+// depends on the instance alone, so an instance reduces in the same order
+// stepped alone or in a batch.
+inline int reduce_blocks(const Geo& g, long long cells, int hi) { return scaled_blocks(g, cells, 8, hi); }
+
 // ---- stage timing -------------------------------------------------------------
 // Kernel groups of one time step; ibm_profile_stages reports the device time
 // of each.  The order matches the stage names in runtime.cu.
@@ -109,6 +122,7 @@ struct Fields {
   void* spec;   // complex half-spectrum nz*ny*nkx
   T* lo[3];     // low parts of the velocity state (mixed path), else null
   T* phi2;      // pseudo-pressure of the correction solve (mixed path)
+  T* qk;        // q_F per fluid cell (energy-conserving shape), else null
   double idh[3][2];  // reciprocal spacings as (hi, lo) pairs, for the pair divergence
 };
 

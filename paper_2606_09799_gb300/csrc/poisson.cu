@@ -175,7 +175,7 @@ __device__ int fft_lines(typename Cplx<T>::type* a, typename Cplx<T>::type* b, i
 // q_F: fixed-order two-level reduction of sum_{C_B} D uhat dV over the
 // sorted boundary-cell list; q_F = -A / |C_F| (uniform on fluid cells).
 // ---------------------------------------------------------------------------
-constexpr int QB_BLOCKS = 128, QB_THREADS = 256;
+constexpr int QB_BLOCKS = 128, QB_THREADS = 256;   // QB_BLOCKS: the most partial sums
 
 template <typename T>
 __device__ __forceinline__ double div_at(const Geo& g, const T* __restrict__ u, const T* __restrict__ v,
@@ -192,7 +192,7 @@ __device__ __forceinline__ void q_partial(const Blk& bk, const Geo& g, const Fie
                                                           unsigned cap, const DevState* ds, double* partial) {
   __shared__ double red[QB_THREADS];
   const unsigned n = min(ds->nbound, cap);
-  const unsigned per = (n + QB_BLOCKS - 1) / QB_BLOCKS;
+  const unsigned per = (n + bk.gx - 1) / bk.gx;
   const unsigned e0 = bk.x * per, e1 = min(n, e0 + per);
   double acc = 0.0;
   for (unsigned e = e0 + threadIdx.x; e < e1; e += QB_THREADS) {
@@ -220,10 +220,11 @@ struct QPartial {
   __device__ __forceinline__ void operator()(const Blk& bk) const { q_partial<T>(bk, g, f, blist, cap, ds, partial); }
 };
 
-__device__ __forceinline__ void q_final(const Blk& bk, const Geo& g, const double* partial, DevState* ds, int s, int use_q) {
+__device__ __forceinline__ void q_final(const Blk& bk, const Geo& g, const double* partial, DevState* ds, int s, int use_q,
+                                        int nblk) {
   if (threadIdx.x != 0) return;
   double sum = 0.0;
-  for (int b = 0; b < QB_BLOCKS; ++b) sum += partial[b];
+  for (int b = 0; b < nblk; ++b) sum += partial[b];
   const double dV = g.dx * g.dy * g.dz;
   const double A = sum * dV;
   const double VF = (double)(g.ncell - (long long)ds->nbound) * dV;
@@ -242,7 +243,105 @@ struct QFinal {
   DevState* ds;
   int s;
   int use_q;
-  __device__ __forceinline__ void operator()(const Blk& bk) const { q_final(bk, g, partial, ds, s, use_q); }
+  int nblk;
+  __device__ __forceinline__ void operator()(const Blk& bk) const { q_final(bk, g, partial, ds, s, use_q, nblk); }
+};
+
+// ---------------------------------------------------------------------------
+// Energy- and mass-conserving shape of q (App. B):
+//   q_F^k = (-A S2 + B S1)/C + (A S1 - B S0)/C (p^k - e^k),  C = S0 S2 - S1^2,
+// S_i = sum_F (p - e)^i dV, A = sum_B Du dV, B = sum_B (p - e) Du dV, with
+// e = |u|^2/2 of the provisional velocity averaged to the cell centre and p
+// the pressure of the sub-stage.  Fixed-order two-level FP64 reduction.
+// ---------------------------------------------------------------------------
+constexpr int QE_THREADS = 256;
+
+// p - e at a cell from the provisional state (bulk type)
+template <typename T>
+__device__ __forceinline__ T p_minus_e(const Geo& g, const Fields<T>& f, long long i, long long j, long long k) {
+  const long long ip = i + 1 == g.nx ? 0 : i + 1, kp = k + 1 == g.nz ? 0 : k + 1;
+  const T uc = (T)0.5 * (f.u[fidx(g, 0, i, j, k)] + f.u[fidx(g, 0, ip, j, k)]);
+  const T vc = (T)0.5 * (f.v[fidx(g, 1, i, j, k)] + f.v[fidx(g, 1, i, j + 1, k)]);
+  const T wc = (T)0.5 * (f.w[fidx(g, 2, i, j, k)] + f.w[fidx(g, 2, i, j, kp)]);
+  return f.p[cidx(g, i, j, k)] - (T)0.5 * (uc * uc + vc * vc + wc * wc);
+}
+
+template <typename T>
+__device__ __forceinline__ void q_energy_partial(const Blk& bk, const Geo& g, const Fields<T>& f,
+                                                 const unsigned* __restrict__ flags32, double* partial) {
+  __shared__ double red[5][QE_THREADS];
+  const unsigned n = (unsigned)g.ncell;
+  const unsigned per = (n + bk.gx - 1) / bk.gx;
+  const unsigned c0 = bk.x * per, c1 = min(n, c0 + per);
+  double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};   // fluid count, S1, S2, A, B (per unit volume)
+  for (unsigned cell = c0 + threadIdx.x; cell < c1; cell += QE_THREADS) {
+    const unsigned i = cell % (unsigned)g.nx, r = cell / (unsigned)g.nx;
+    const unsigned j = r % (unsigned)g.ny, k = r / (unsigned)g.ny;
+    const double pe = (double)p_minus_e<T>(g, f, i, j, k);
+    const unsigned fl = (flags32[cell >> 2] >> (8 * (cell & 3))) & 0xFFu;
+    if (fl & FLAG_B) {
+      const double du = div_at<T>(g, f.u, f.v, f.w, i, j, k);
+      acc[3] += du;
+      acc[4] += pe * du;
+    } else {
+      acc[0] += 1.0;
+      acc[1] += pe;
+      acc[2] += pe * pe;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 5; ++q) red[q][threadIdx.x] = acc[q];
+  __syncthreads();
+  for (int st = QE_THREADS / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st)
+#pragma unroll
+      for (int q = 0; q < 5; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x < 5) partial[5 * bk.x + threadIdx.x] = red[threadIdx.x][0];
+}
+template <typename T>
+struct QEnergyPartial {
+  static constexpr int kThreads = QE_THREADS;
+  Geo g;
+  Fields<T> f;
+  const unsigned* flags32;
+  double* partial;
+  __device__ __forceinline__ void operator()(const Blk& bk) const { q_energy_partial<T>(bk, g, f, flags32, partial); }
+};
+
+__device__ __forceinline__ void q_energy_final(const Blk&, const Geo& g, const double* partial, DevState* ds, int s,
+                                               int nblk) {
+  if (threadIdx.x != 0) return;
+  double t[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int b = 0; b < nblk; ++b)
+    for (int q = 0; q < 5; ++q) t[q] += partial[5 * b + q];
+  const double dV = g.dx * g.dy * g.dz;
+  const double S0 = t[0] * dV, S1 = t[1] * dV, S2 = t[2] * dV, A = t[3] * dV, B = t[4] * dV;
+  const double C = S0 * S2 - S1 * S1;
+  double qa, qb;
+  if (S0 > 0.0 && C > 1e-14 * S0 * S2) {
+    qa = (-A * S2 + B * S1) / C;
+    qb = (A * S1 - B * S0) / C;
+  } else {   // p - e uniform on the fluid cells: the mass constraint alone
+    qa = S0 > 0.0 ? -A / S0 : 0.0;
+    qb = 0.0;
+  }
+  ds->qa[s] = qa;
+  ds->qb[s] = qb;
+  ds->qf[s] = qa;
+  ds->sum_a[s] = A;
+  ds->sum_qdv[s] = A + qa * S0 + qb * S1;
+  if (!isfinite(qa) || !isfinite(qb)) atomicOr(&ds->err, ERR_NONFINITE);
+}
+struct QEnergyFinal {
+  static constexpr int kThreads = 32;
+  Geo g;
+  const double* partial;
+  DevState* ds;
+  int s;
+  int nblk;
+  __device__ __forceinline__ void operator()(const Blk& bk) const { q_energy_final(bk, g, partial, ds, s, nblk); }
 };
 
 // ---------------------------------------------------------------------------
@@ -279,6 +378,7 @@ __device__ __forceinline__ void fft_x_fwd(const Blk& bk, const Geo& g, const Fie
   const int rows = g.ny * g.nz;
   const int line0 = bk.x * lines_per_block;
   const T qf = use_q ? (T)ds->qf[s] : (T)0;
+  const T qa = use_q == 2 ? (T)ds->qa[s] : (T)0, qb = use_q == 2 ? (T)ds->qb[s] : (T)0;
   const T sc = (T)scale, idx = (T)g.idx, idy = (T)g.idy, idz = (T)g.idz;
   const long long pu = (long long)ny * n, pv = (long long)(ny + 1) * n;
   // load: rows 2 l and 2 l + 1 of line l; divergence in the bulk type
@@ -316,7 +416,10 @@ __device__ __forceinline__ void fft_x_fwd(const Blk& bk, const Geo& g, const Fie
             pair_diff(f.w, f.lo[2], wk, cell, (float)f.idh[2][0], (float)f.idh[2][1], bz, sz);
             two_sum(bx, by, a1, e1);
             two_sum(a1, bz, a2, e2);
-            const float qh = use_q ? ds->qf_hi[s] : 0.0f, ql = use_q ? ds->qf_lo[s] : 0.0f;
+            // the target q of the first solve: uniform (an FP32 pair) or the
+            // energy-conserving shape stored per cell by mode 0
+            const float qh = use_q == 2 ? (float)f.qk[cell] : (use_q ? ds->qf_hi[s] : 0.0f);
+            const float ql = use_q == 1 ? ds->qf_lo[s] : 0.0f;
             two_sum(a2, -qh, a3, e3);
             r = (T)((a3 + (((e1 + e2) + e3) + ((sx + sy) + sz) - ql)) * (float)scale);
           }
@@ -325,7 +428,12 @@ __device__ __forceinline__ void fft_x_fwd(const Blk& bk, const Geo& g, const Fie
           const T du = (f.u[r0 + ip] - f.u[cell]) * idx;
           const T dv = (f.v[v0 + n] - f.v[v0]) * idy;
           const T dw = (f.w[(long long)kp * pu + (long long)j * n + i] - f.w[cell]) * idz;
-          r = (du + dv + dw - qf) * sc;
+          T q = qf;
+          if (use_q == 2) {   // App. B shape, kept per cell for the correction solve
+            q = qa + qb * p_minus_e<T>(g, f, i, j, k);
+            f.qk[cell] = q;
+          }
+          r = (du + dv + dw - q) * sc;
         }
         if (hh == 0) z.x = r;
         else z.y = r;
@@ -914,10 +1022,16 @@ void launch_poisson(const Geo& g, const Fields<T>& f, const TagBuffers& b, const
   using C = typename Cplx<T>::type;
   const Geo& sh = ex.shape;
   const Tune& tu = ex.tune;
-  if (use_q) {
+  if (use_q == 1) {
     ex.mark(ST_QRED);
-    ex.launch(dim3(QB_BLOCKS), dim3(QB_THREADS), 0, QPartial<T>{g, f, b.blist, b.cap, ds, partial});
-    ex.launch(dim3(1), dim3(32), 0, QFinal{g, partial, ds, sg.s, use_q});
+    const int nq = reduce_blocks(g, 16384, QB_BLOCKS);
+    ex.launch(dim3(nq), dim3(QB_THREADS), 0, QPartial<T>{g, f, b.blist, b.cap, ds, partial});
+    ex.launch(dim3(1), dim3(32), 0, QFinal{g, partial, ds, sg.s, use_q, nq});
+  } else if (use_q == 2) {
+    ex.mark(ST_QRED);
+    const int nq = reduce_blocks(g, 16384, QB_BLOCKS);
+    ex.launch(dim3(nq), dim3(QE_THREADS), 0, QEnergyPartial<T>{g, f, b.flags32, partial});
+    ex.launch(dim3(1), dim3(32), 0, QEnergyFinal{g, partial, ds, sg.s, nq});
   }
   const double scale = 1.0 / (sg.alp * dt * (double)g.nx * (double)g.nz);
   const FftPlan px = make_plan(g.nx), pz = make_plan(g.nz);

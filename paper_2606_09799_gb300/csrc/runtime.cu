@@ -172,6 +172,7 @@ struct ibm_grid {
   void* u; void* v; void* w; void* p;
   void* H[3]; void* R[3]; void* scr; void* uf; void* phi; void* spec;
   void* lo[3]; void* phi2;   // mixed path: low parts of the velocity pairs, correction pseudo-pressure
+  void* qk;                  // q_F per cell (energy-conserving shape)
   // tables
   void* sweep_mem[24];
   double* pcp; double* pinv; double* lamx; double* lamz;
@@ -390,6 +391,7 @@ static Fields<T> fields(ibm_handle h) {
   f.spec = h->spec;
   for (int c = 0; c < 3; ++c) f.lo[c] = (T*)h->lo[c];
   f.phi2 = (T*)h->phi2;
+  f.qk = (T*)h->qk;
   const double id[3] = {h->g.idx, h->g.idy, h->g.idz};
   for (int d = 0; d < 3; ++d) {
     const float hi = (float)id[d];
@@ -981,6 +983,7 @@ ibm_status ibm_create_grid(const ibm_grid_desc* desc, void* stream, ibm_handle* 
   if (d.scheme != IBM_RK2_CN && d.scheme != IBM_AB_CN) return IBM_ERR_ARG;
   if (d.ybc != IBM_NOSLIP && d.ybc != IBM_FREESLIP) return IBM_ERR_ARG;
   if (d.precision != IBM_FP64 && d.precision != IBM_MIXED && d.precision != IBM_MIXED_FAST) return IBM_ERR_ARG;
+  if (d.use_q < 0 || d.use_q > 2) return IBM_ERR_ARG;
   const long long nvf = (long long)d.nx * (d.ny + 1) * d.nz;
   if (nvf >= (1ll << 30)) return IBM_ERR_ARG;   // node indices are packed into 30 bits
   ibm_handle h = new (std::nothrow) ibm_grid();   // value-initialised: every scalar and pointer is zero
@@ -1039,6 +1042,10 @@ ibm_status ibm_create_grid(const ibm_grid_desc* desc, void* stream, ibm_handle* 
     }
     h->phi2 = dalloc(h, ncell * es);
     if (!h->phi2) { release_all(h); delete h; return IBM_ERR_OOM; }
+  }
+  if (d.use_q == 2) {
+    h->qk = dalloc(h, ncell * es);
+    if (!h->qk) { release_all(h); delete h; return IBM_ERR_OOM; }
   }
   h->ds = (DevState*)dalloc(h, sizeof(DevState));
   h->partial = (double*)dalloc(h, 4096 * sizeof(double));
@@ -1434,7 +1441,8 @@ ibm_status ibm_get_diag(ibm_handle h, ibm_diag* out) {
   const int ns = stages(h->desc, sg);
   out->q_f = ds.qf[ns - 1];
   const double dV = h->g.dx * h->g.dy * h->g.dz;
-  out->sum_q_dv = ds.sum_a[ns - 1] + ds.qf[ns - 1] * (double)(h->g.ncell - (long long)ds.nbound) * dV;
+  out->sum_q_dv = h->desc.use_q == 2 ? ds.sum_qdv[ns - 1]
+                                     : ds.sum_a[ns - 1] + ds.qf[ns - 1] * (double)(h->g.ncell - (long long)ds.nbound) * dV;
   out->steps = (int64_t)ds.steps;
   out->ncandidates = ds.ncand;
   out->kernels_per_step = h->kernels_per_step;

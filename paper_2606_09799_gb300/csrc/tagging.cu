@@ -756,7 +756,7 @@ void launch_tagging(const Geo& g, const Surf& s, const TagBuffers& b, DevState* 
   ex.launch(dim3((unsigned)std::min<long long>((words + 255) / 256, num_sms() * 4ll)), dim3(256), 0,
             Fill32{reinterpret_cast<unsigned*>(b.lines.x), words, 0x7F7F7F7Fu});
   // previous step's candidates reset their nodes, then the counters restart
-  ex.launch(dim3(num_sms() * 4), dim3(256), 0,
+  ex.launch(dim3(scaled_blocks(g, 8192, 4, num_sms() * 4)), dim3(256), 0,
             TagReset{g, b.cand, b.cap, ds, b.d2min, b.owner, b.flags32, b.ub, b.ublist});
   ex.launch(dim3(1), dim3(1), 0, CopyCount{ds});
   const bool live = s.nt > 0;
@@ -764,8 +764,9 @@ void launch_tagging(const Geo& g, const Surf& s, const TagBuffers& b, DevState* 
   const long long blocks = ((long long)s.nt * 32 + 127) / 128;   // one warp per triangle
   ex.launch(grid_if(live, dim3((unsigned)blocks)), dim3(128), 0, TagPairs<0>{g, s, b.cap, b.ub, b.ublist, b.surv, ds});
   ex.launch(grid_if(live, dim3((unsigned)blocks)), dim3(128), 0, TagPairs<1>{g, s, b.cap, b.ub, b.ublist, b.surv, ds});
-  ex.launch(grid_if(live, dim3(num_sms() * 8)), dim3(128), 0, TagExact{g, s, b.cand, b.cap, b.d2min, b.surv, ds});
-  const dim3 gb = grid_if(live, dim3(num_sms() * 8));
+  ex.launch(grid_if(live, dim3(scaled_blocks(g, 8192, 8, num_sms() * 8))), dim3(128), 0,
+            TagExact{g, s, b.cand, b.cap, b.d2min, b.surv, ds});
+  const dim3 gb = grid_if(live, dim3(scaled_blocks(g, 4096, 8, num_sms() * 8)));
   ex.launch(gb, dim3(256), 0, TagResolve{g, b.cand, b.cap, ds, b.d2min, b.owner});
   ex.launch(gb, dim3(256), 0, TagMark{g, b.cand, b.cap, ds, b.d2min, b.owner, b.flags32, b.lines});
   ex.launch(gb, dim3(256), 0, TagBoundary{g, b.cand, b.cap, ds, b.d2min, b.owner, b.flags32});

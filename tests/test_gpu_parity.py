@@ -306,3 +306,29 @@ def test_every_launch_shape_matches_oracle(tune, precision, tol):
     assert err <= tol, err
     for c, own in enumerate(g.tags()):
         np.testing.assert_array_equal(own, o.owners[c])
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-5)])
+def test_energy_conserving_q_matches_oracle(precision, tol):
+    """App. B's energy- and mass-conserving shape of q_F (use_q = 2) on a
+    ragged grid with a moving sphere and a random initial field, 4 steps:
+    fields against the oracle, sum q dV = 0 on the device."""
+    wl = inputs.oscillating_sphere(n=48, steps=4, subdiv=2)
+    u, v, w, p = inputs.random_fields(48, 37, 96, seed=9, amp=0.1)
+    o = OracleSim(48, 37, 96, 1.0, 0.9, 1.6, re=150.0, dt=2e-3, use_q=2)
+    g = ibm.Simulation(48, 37, 96, 1.0, 0.9, 1.6, re=150.0, dt=2e-3, precision=precision, use_q=2)
+    o.set_fields(u, v, w, p)
+    g.set_fields(u, v, w, p)
+    for s in range(4):
+        xyz, vel = wl.surface(s)
+        o.set_surface(xyz, vel, wl.tri)
+        g.set_surface(xyz, vel, wl.tri)
+        o.step()
+        g.step()
+    assert abs(o.last["q_coef"][1]) > 0
+    gu, gv, gw, gp = g.fields()
+    err = max(np.abs(o.u - gu).max(), np.abs(o.v - gv).max(), np.abs(o.w - gw).max())
+    assert err <= tol * max(1.0, np.abs(o.u).max()), err
+    d = g.diag()
+    assert abs(d["q_f"] - o.last["q_coef"][0]) <= 1e-6 * max(1e-12, abs(o.last["q_coef"][0])) + tol
+    assert abs(d["sum_q_dv"]) < 1e-12

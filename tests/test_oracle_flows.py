@@ -249,3 +249,82 @@ def test_gradient_mode_closed_form_pressure(scheme):
     scale = eps / dt
     assert np.abs(sim.u).max() < 1e-6 * eps * np.abs(gu).max()
     np.testing.assert_allclose(sim.p, P * psi, atol=1e-6 * scale)
+
+
+def _energy_case(seed=3, n=12):
+    """A small grid with a body (boundary cells) and random fields."""
+    rng = np.random.default_rng(seed)
+    g = orc.make_grid(n, n, n)
+    xyz, tri = inputs.icosphere(2, 0.3, (0.5, 0.5, 0.5))
+    own, _ = orc.tag(g, xyz, tri)
+    isb = orc.boundary_cells(g, own)
+    u, v, w, p = inputs.random_fields(n, n, n, seed)
+    div = orc.divergence(g, u, v, w)
+    return g, isb, u, v, w, p, div
+
+
+def test_energy_q_satisfies_mass_and_energy_constraints():
+    """App. B: the shape makes sum_F q dV + sum_B Du dV = 0 (mass) and
+    sum_F (p - e) q dV + sum_B (p - e) Du dV = 0 (inviscid kinetic energy);
+    e is |u|^2/2 with the velocity averaged to the cell centre (computed here
+    independently of the oracle)."""
+    g, isb, u, v, w, p, div = _energy_case()
+    assert isb.sum() > 10
+    q, coef = orc.q_energy(g, div, isb, p, u, v, w)
+    dV = g.dx * g.dy * g.dz
+    uc = 0.5 * (u + np.roll(u, -1, axis=2))
+    vc = 0.5 * (v[:, :-1, :] + v[:, 1:, :])
+    wc = 0.5 * (w + np.roll(w, -1, axis=0))
+    pe = p - 0.5 * (uc ** 2 + vc ** 2 + wc ** 2)
+    F, Bm = isb == 0, isb == 1
+    np.testing.assert_array_equal(q[Bm], div[Bm])
+    A = (div[Bm] * dV).sum()
+    B = (pe[Bm] * div[Bm] * dV).sum()
+    mass = (q[F] * dV).sum() + A
+    energy = (pe[F] * q[F] * dV).sum() + B
+    scale = np.abs(div).max() * dV * F.sum() * (1 + np.abs(pe).max())
+    assert abs(mass) < 1e-13 * scale and abs(energy) < 1e-13 * scale
+    assert abs(coef[1]) > 0          # the energy part is active
+
+
+def test_energy_q_is_the_minimum_norm_field_of_the_two_constraints():
+    """The Lagrangian of App. B: among all q on C_F meeting both constraints,
+    the shape has the least sum q^2 dV -- the least-norm solution of the 2 x
+    |C_F| linear system, computed here by numpy's least squares."""
+    g, isb, u, v, w, p, div = _energy_case(seed=5)
+    q, coef = orc.q_energy(g, div, isb, p, u, v, w)
+    dV = g.dx * g.dy * g.dz
+    uc = 0.5 * (u + np.roll(u, -1, axis=2))
+    vc = 0.5 * (v[:, :-1, :] + v[:, 1:, :])
+    wc = 0.5 * (w + np.roll(w, -1, axis=0))
+    pe = p - 0.5 * (uc ** 2 + vc ** 2 + wc ** 2)
+    F, Bm = isb == 0, isb == 1
+    M = np.stack([np.full(F.sum(), dV), pe[F] * dV])
+    rhs = -np.array([(div[Bm] * dV).sum(), (pe[Bm] * div[Bm] * dV).sum()])
+    ref, *_ = np.linalg.lstsq(M, rhs, rcond=None)
+    assert np.abs(q[F] - ref).max() < 1e-10 * np.abs(ref).max()
+
+
+def test_energy_q_reduces_to_uniform_when_p_minus_e_is_uniform():
+    g, isb, u, v, w, p, div = _energy_case(seed=7)
+    z = [np.zeros_like(a) for a in (u, v, w)]
+    q, coef = orc.q_energy(g, div, isb, np.full_like(p, 0.3), *z)
+    _, qF, A, VF = orc.rhs_poisson(g, div, isb, 1, 1.0)
+    assert coef[1] == 0.0
+    np.testing.assert_allclose(q[isb == 0], qF, rtol=1e-15)
+
+
+def test_energy_q_flow_projection_is_exact():
+    """With the energy shape the projected field satisfies D u = q^k cell by
+    cell to machine precision (Eq. mod_div with the App. B shape), and the
+    total mass flux vanishes."""
+    wl = inputs.oscillating_sphere(n=24, steps=3, subdiv=2)
+    sim = OracleSim(wl.nx, wl.ny, wl.nz, re=wl.re, dt=wl.dt, use_q=2)
+    for s in range(wl.steps):
+        xyz, vel = wl.surface(s)
+        sim.set_surface(xyz, vel, wl.tri)
+        sim.step()
+        d = orc.divergence(sim.g, sim.u, sim.v, sim.w)
+        assert np.abs(d - sim.last["q_field"]).max() < 1e-11 / sim.g.dx
+        assert abs((d * sim.g.dx * sim.g.dy * sim.g.dz).sum()) < 1e-14
+        assert abs(sim.last["q_coef"][1]) > 0
