@@ -242,10 +242,7 @@ def gpu_arm(args):
         ms = sum(a.elapsed_time(b) for a, b in ev)
         diag = sim.diag()
         sim.sync()
-        if world > 1:
-            t = torch.tensor([ms], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms, dev, world)
         # stage profile of the same workload (CUDA events recorded on the launching stream)
         prof = ibm.ibm_profile_stages(sim.h, args.profile_steps)
         # end-to-end: host surface in pinned memory -> device, step, diagnostics read back
@@ -274,7 +271,7 @@ def gpu_arm(args):
         return None
     head = results[args.precision]
     cells = wl.cells
-    value = world * cells * K / (head["ms"] / 1e3) / 1e9
+    value = whole_job_gcups(cells, K, world, head["ms"])
     e2e_value = world * cells * head["e2e_steps"] / (head["e2e_ms"] / 1e3) / 1e9
     h2d = 2 * surf[0][0].nbytes
     peaks = measured_peaks()
@@ -333,6 +330,8 @@ def gpu_arm(args):
                       "slip_l1": r["diag"]["slip_l1"], "clocks": r["clocks"], "tune": r["tune"]}
     if batched is not None:
         line["batched"] = batched
+    if args.e5_steps > 0:
+        line["e5_heaving_pitching_plate"] = e5_leg(args, dev, stream)
     if "mixed" in results and "fp64" in results:
         sm, sf = results["mixed"]["diag"]["slip_l1"], results["fp64"]["diag"]["slip_l1"]
         line["slip_rel_diff_mixed_vs_fp64"] = abs(sm - sf) / sf if sf else None
@@ -340,6 +339,24 @@ def gpu_arm(args):
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_steps)
     return line
+
+
+def max_over_ranks(ms: float, device, world: int) -> float:
+    """The slowest rank's time (every rank gets it): the whole job's timed
+    region ends when the last replica finishes."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gcups(cells_per_rank: int, steps: int, world: int, ms_max: float) -> float:
+    """Cell updates of all ranks' replicas over the slowest rank's time (weak
+    scaling: every rank advances its own copy of the workload)."""
+    return world * cells_per_rank * steps / (ms_max / 1e3) / 1e9
 
 
 def batched_leg(args, dev, stream, flush, world):
@@ -413,6 +430,35 @@ def batched_leg(args, dev, stream, flush, world):
             "stages_ms_per_step": {k: v[0] for k, v in prof.items() if v[1] > 0}}
 
 
+def e5_leg(args, dev, stream):
+    """No-slip error time series of the heaving and pitching plate (Section
+    4.4 geometry, 100 x 650 x 100): ||eps||_1 every step on the mixed and
+    the FP64 paths, for context beside the paper's ~1e-4 U_ref over one
+    period.  Opt-in (--e5-steps N)."""
+    from paper_2606_09799_gb300 import ibm, inputs
+
+    wl = inputs.heaving_pitching_plate(steps=args.e5_steps)
+    out = {"workload": "heaving/pitching plate of Section 4.4: 100x650x100 cells on 2x13x2, plate side 1 "
+                       "(50x50 quads), B=6, w=1/6, theta=(pi/6) sin(2wt), Re=100, dt=%g" % wl.dt,
+           "paper": "||eps||_1 of order 1e-4 U over one period (Fig. heaving_plate)"}
+    for prec, nsteps in (("mixed", args.e5_steps), ("fp64", min(args.e5_steps, 500))):
+        g = ibm.Simulation(wl.nx, wl.ny, wl.nz, wl.lx, wl.ly, wl.lz, re=wl.re, dt=wl.dt, precision=prec,
+                           stream=stream.cuda_stream)
+        series = []
+        t0 = time.perf_counter()
+        for s in range(nsteps):
+            xyz, vel = wl.surface(s)
+            g.set_surface(xyz, vel, wl.tri if s == 0 else None)
+            g.step()
+            series.append(g.diag()["slip_l1"])
+        wall = time.perf_counter() - t0
+        g.close()
+        arr = [x for x in series[10:]] or series
+        out[prec] = {"steps": nsteps, "t_end": nsteps * wl.dt, "slip_mean": sum(arr) / len(arr),
+                     "slip_max": max(arr), "series_every_10": series[::10], "wall_s": wall}
+    return out
+
+
 def cpu_baseline(nsteps: int):
     """The FP64 CPU oracle as it stands, on a bounded sample of the same
     workload: its first `nsteps` whole time steps."""
@@ -480,6 +526,8 @@ def main():
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the built-in launch shapes (no autotuning before timing)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-instances leg")
+    ap.add_argument("--e5-steps", type=int, default=0,
+                    help="also record the no-slip error series of the heaving/pitching plate (opt-in)")
     ap.add_argument("--tune", default="", help="fixed launch shapes instead of autotuning, e.g. tri_y=3,sweep_zy=2")
     ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--fp64-peak-tflops", type=float, default=1.0,

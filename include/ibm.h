@@ -85,7 +85,7 @@ enum { IBM_NOSLIP = 0, IBM_FREESLIP = 1 }; /* condition on the y walls */
 enum { IBM_FP64 = 0, IBM_MIXED = 1, IBM_MIXED_FAST = 2 };
 
 typedef struct {
-  int nx, ny, nz;      /* cells; nx and nz must factor into 2s and 3s, 4 <= n <= 1024; ny >= 4 */
+  int nx, ny, nz;      /* cells; nx and nz even, factoring into 2s, 3s and 5s, 4 <= n <= 1024; 4 <= ny <= 4096 */
   double lx, ly, lz;   /* box lengths */
   double re;           /* Reynolds number */
   double dt;           /* time step */

@@ -72,6 +72,7 @@ static FftPlan make_plan(int n) {
   while (m % 4 == 0) { rad[nr++] = 4; m /= 4; }
   while (m % 2 == 0) { rad[nr++] = 2; m /= 2; }
   while (m % 3 == 0) { rad[nr++] = 3; m /= 3; }
+  while (m % 5 == 0) { rad[nr++] = 5; m /= 5; }
   for (int s = 0; s < nr; ++s) {
     FftStage& st = p.st[p.nst++];
     st.R = rad[s];
@@ -111,7 +112,7 @@ __device__ void fft_pass(const typename Cplx<T>::type* src, typename Cplx<T>::ty
     C* dp = dst + line * ls;
     const int jn = (int)fdiv((unsigned)j, S.mNs);
     const int k = j - jn * Ns;
-    C v[4];
+    C v[5];
     for (int r = 0; r < R; ++r) {
       C x = sp[(j + r * nb) * es];
       if (r > 0 && k > 0) {
@@ -135,6 +136,32 @@ __device__ void fft_pass(const typename Cplx<T>::type* src, typename Cplx<T>::ty
       v[2] = csub(s02, s13);
       v[1] = cadd(d02, jd13);
       v[3] = csub(d02, jd13);
+    } else if (R == 5) {
+      // X_k = sum_r v_r w^{rk}, w = exp(-+ 2 pi i / 5): pair the inputs
+      // symmetric about r = 0 (t1 = v1 + v4, t2 = v2 + v3, t3 = v1 - v4,
+      // t4 = v2 - v3); the cosines and sines of 2 pi / 5 and 4 pi / 5 from
+      // sqrt(5): cos = (sqrt5 - 1)/4, -(sqrt5 + 1)/4; sin = sqrt(10 +- 2 sqrt5)/4
+      const T c1 = (T)0.30901699437494742410, c2 = (T)-0.80901699437494742410;
+      const T s1 = (T)0.95105651629515357212, s2 = (T)0.58778525229247312917;
+      const C t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]), t3 = csub(v[1], v[4]), t4 = csub(v[2], v[3]);
+      C a1, a2, b1, b2;
+      a1.x = v[0].x + c1 * t1.x + c2 * t2.x;
+      a1.y = v[0].y + c1 * t1.y + c2 * t2.y;
+      a2.x = v[0].x + c2 * t1.x + c1 * t2.x;
+      a2.y = v[0].y + c2 * t1.y + c1 * t2.y;
+      b1.x = s1 * t3.x + s2 * t4.x;
+      b1.y = s1 * t3.y + s2 * t4.y;
+      b2.x = s2 * t3.x - s1 * t4.x;
+      b2.y = s2 * t3.y - s1 * t4.y;
+      // forward: X1 = a1 - i b1, X4 = a1 + i b1, X2 = a2 - i b2, X3 = a2 + i b2
+      C ib1, ib2;   // -i b (forward) or +i b (inverse)
+      if (INV) { ib1.x = -b1.y; ib1.y = b1.x; ib2.x = -b2.y; ib2.y = b2.x; }
+      else { ib1.x = b1.y; ib1.y = -b1.x; ib2.x = b2.y; ib2.y = -b2.x; }
+      v[0] = cadd(v[0], cadd(t1, t2));
+      v[1] = cadd(a1, ib1);
+      v[4] = csub(a1, ib1);
+      v[2] = cadd(a2, ib2);
+      v[3] = csub(a2, ib2);
     } else {  // R == 3
       const T h = (T)0.86602540378443864676;  // sin(2 pi / 3)
       const C a = v[0], b = v[1], c = v[2];

@@ -246,6 +246,7 @@ static bool good_fft_size(int n) {
   if (n < 4 || n > 1024 || (n % 2) != 0) return false;
   while (n % 2 == 0) n /= 2;
   while (n % 3 == 0) n /= 3;
+  while (n % 5 == 0) n /= 5;
   return n == 1;
 }
 

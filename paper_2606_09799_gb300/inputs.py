@@ -507,6 +507,34 @@ def leaflet_tube(steps: int = 50) -> Workload:
     return Workload("leaflet512", nx, ny, nz, lx, 1.0, lz, re, 1e-4, steps, tri, surface_at, body_force_at=force)
 
 
+def heaving_pitching_plate(steps: int = 2500, dt: float = 2e-3, nq: int = 50) -> Workload:
+    """Section 4.4's moving-plate case at the paper's geometry: a square
+    zero-thickness plate of side L = 1 in quiescent fluid heaving along the
+    wall-normal axis, b(t) = B sin(w t), B = 6, and pitching about the
+    spanwise axis, theta(t) = (pi/6) sin(2 w t); U_ref = B w = 1, Re = 100;
+    box 2 x 13 x 2 (the paper's [-L, L] x [-L, L] x [-6.5L, 6.5L] with the
+    heave axis wall-normal, shifted to start at 0), 100 x 650 x 100 cells,
+    dx = 0.02; the plate (nq x nq quads) centred at (1, 6.5, 1) at t = 0.
+    dt = 2e-3 (CFL ~0.1): the printed step, 1e-5, would need ~4M steps
+    per period."""
+    B, om, th0 = 6.0, 1.0 / 6.0, math.pi / 6.0
+    xyz0, tri = plate(nq, 1.0, 0.5, 0.5, 6.5)
+    X1 = xyz0[:, 0] - 1.0
+
+    def surface_at(t):
+        th, dth = th0 * math.sin(2 * om * t), th0 * 2 * om * math.cos(2 * om * t)
+        b, db = B * math.sin(om * t), B * om * math.cos(om * t)
+        xyz = xyz0.copy()
+        xyz[:, 0] = 1.0 + X1 * math.cos(th)
+        xyz[:, 1] = 6.5 + b - X1 * math.sin(th)
+        vel = np.zeros_like(xyz)
+        vel[:, 0] = -X1 * math.sin(th) * dth
+        vel[:, 1] = db - X1 * math.cos(th) * dth
+        return np.ascontiguousarray(xyz), np.ascontiguousarray(vel)
+
+    return Workload("heaving_plate_e5", 100, 650, 100, 2.0, 13.0, 2.0, 100.0, dt, steps, tri, surface_at)
+
+
 def random_fields(nx: int, ny: int, nz: int, seed: int, amp: float = 1.0):
     """Seeded smooth-ish random velocity and pressure fields (v = 0 on the
     walls) for stage-level parity tests."""

@@ -40,7 +40,7 @@ def test_bad_arguments_are_rejected_without_a_gpu():
     L = ibm.load()
     import ctypes
     h = ctypes.c_void_p()
-    for bad in (ibm.ibm_grid_desc(50, 64, 64, 1, 1, 1, 100, 1e-3, 0, 0, 0, 1),     # 50 = 2 * 5^2
+    for bad in (ibm.ibm_grid_desc(14, 64, 64, 1, 1, 1, 100, 1e-3, 0, 0, 0, 1),     # 14 = 2 * 7
                 ibm.ibm_grid_desc(64, 2, 64, 1, 1, 1, 100, 1e-3, 0, 0, 0, 1),      # ny too small
                 ibm.ibm_grid_desc(64, 64, 64, 1, 1, 1, -1, 1e-3, 0, 0, 0, 1),      # Re <= 0
                 ibm.ibm_grid_desc(64, 64, 64, 1, 1, 1, 100, 1e-3, 7, 0, 0, 1)):    # unknown scheme

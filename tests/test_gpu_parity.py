@@ -332,3 +332,29 @@ def test_energy_conserving_q_matches_oracle(precision, tol):
     d = g.diag()
     assert abs(d["q_f"] - o.last["q_coef"][0]) <= 1e-6 * max(1e-12, abs(o.last["q_coef"][0])) + tol
     assert abs(d["sum_q_dv"]) < 1e-12
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-5)])
+def test_radix5_grid_matches_oracle(precision, tol):
+    """Grid sizes with factors of 5 (x: 100 = 4 * 5 * 5, z: 30 = 2 * 3 * 5;
+    the heaving-pitching plate of Section 4.4 uses 100 x 650 x 100): the
+    FFT's radix-5 butterflies against the oracle's numpy transforms."""
+    nx, ny, nz = 100, 24, 30
+    wl = inputs.oscillating_sphere(n=32, steps=3, subdiv=2)
+    u, v, w, p = inputs.random_fields(nx, ny, nz, seed=13, amp=0.1)
+    o = OracleSim(nx, ny, nz, 1.0, 0.8, 1.0, re=120.0, dt=2e-3)
+    g = ibm.Simulation(nx, ny, nz, 1.0, 0.8, 1.0, re=120.0, dt=2e-3, precision=precision)
+    o.set_fields(u, v, w, p)
+    g.set_fields(u, v, w, p)
+    for s in range(3):
+        xyz, vel = wl.surface(s)
+        xyz = xyz * np.array([1.0, 0.8, 1.0])
+        o.set_surface(xyz, vel, wl.tri)
+        g.set_surface(xyz, vel, wl.tri)
+        o.step()
+        g.step()
+    gu, gv, gw, gp = g.fields()
+    err = max(np.abs(o.u - gu).max(), np.abs(o.v - gv).max(), np.abs(o.w - gw).max())
+    assert err <= tol, err
+    if precision == "fp64":
+        assert np.abs((o.p - o.p.mean()) - (gp - gp.mean())).max() <= 1e-10
