@@ -221,6 +221,8 @@ typedef struct {
   int fft_cols;       /* kx columns per block of the z transforms: a power of two up to 16 */
   int sweep_zy;       /* z and y sweeps of the FP32 path: 1 shared-memory tile with one thread per line,
                          2 several lanes per line (affine-map scans) */
+  int fft_plane;      /* 1 separate x and z transform kernels, 2 both fused per y-plane (when its
+                         half-spectrum fits shared memory) */
   double ms_per_step; /* set by the autotuners: measured time per step of the chosen shapes */
 } ibm_tune;
 
@@ -287,6 +289,29 @@ const char* ibm_batch_last_error(ibm_batch_handle b);
  * with ibm_destroy of any of its handles).  Errors are also described by
  * ibm_last_error(hs[0]). */
 ibm_status ibm_step_batch(const ibm_handle* hs, int n, int nsteps);
+
+/* ---- post-processing of a finished step ----------------------------------
+ * Hydrodynamic loads (Section 3.3): markers at the triangle centroids, a
+ * probe at distance h (twice the cell diagonal) along the oriented normal,
+ * second-order moving-least-squares fits of p and of each velocity
+ * component there (the 4x4x4 nearest nodes of each lattice, Gaussian
+ * weights of width the cell diagonal, nodes behind the marker's plane and
+ * boundary cells left out), the Taylor series back to the wall, traction
+ * t = -p n + (grad u + grad u^T) n / Re.  sides = 1 uses the normal given by
+ * the vertex order (closed bodies: make it outward), sides = 2 adds the
+ * opposite face (zero-thickness surfaces).  Writes the total force and the
+ * torque about `pole` (NULL: the origin), optionally per triangle the force
+ * and torque (6*nt values) and the wall pressure on the normal's side (nt).
+ * Uses the current fields and surface; call after ibm_step and before the
+ * next ibm_set_surface.  Synchronises. */
+ibm_status ibm_get_loads(ibm_handle h, int sides, const double* pole, double* force, double* torque,
+                         double* per_triangle, double* p_wall);
+
+/* Pressure with the boundary cells (Section 3.2), where the solution does
+ * not define it, replaced by its value at each cell's probe point (zero
+ * normal gradient at the wall); p: nz*ny*nx FP64 (host or device, as
+ * on_device says).  Synchronises. */
+ibm_status ibm_get_pressure_recon(ibm_handle h, double* p, int on_device);
 
 /* Library version string. */
 const char* ibm_version(void);

@@ -879,3 +879,249 @@ void orc_project(const orc_grid* g, double* u, double* v, double* w, double* p, 
         p[cidx(g, i, j, k)] += c0 - adt / (2.0 * re) * lapphi[cidx(g, i, j, k)];
       }
 }
+
+/* ------------------------------------------------------------------ */
+/* Hydrodynamic loads on the surface (Section 3.3) and the pressure of  */
+/* the boundary cells (Section 3.2, post-processing).                   */
+/*                                                                      */
+/* Markers are the triangle centroids X^l with the oriented unit normal */
+/* n^l and area A^l.  A probe x^e = X^l + h n^l (h the IB probe length, */
+/* twice the cell diagonal) is cast into the fluid; p and the velocity  */
+/* gradient there come from second-order moving-least-squares fits and  */
+/* are carried back to the wall by the Taylor series of the paper:      */
+/*   p^l = p^e - h dp/dn + h^2/2 d2p/dn2,                               */
+/*   grad u^l = grad u^e - h d(grad u)/dn  (a quadratic fit has no      */
+/*   third derivatives, so the h^2 term of grad u vanishes);            */
+/*   t^l = -p^l n + (grad u^l + grad u^l^T) n / Re,                     */
+/*   F = sum t^l A^l,  M = sum (X^l - X^p) x t^l A^l.                   */
+/* Readings (the MLS kernel is defined in a cited work, not here): the  */
+/* fit of each quantity uses the 4 x 4 x 4 nearest nodes of its own     */
+/* lattice around x^e (indices wrap in x and z, are clamped to the      */
+/* stored planes in y), Gaussian weights exp(-(r/diag)^2), the basis    */
+/* 1, xi, xi^2 and cross terms in xi = (x - x^e)/diag; nodes on the     */
+/* other side of the marker's plane ((x - X^l).n <= 0) and, for p,      */
+/* boundary cells are left out; with fewer than 10 weighted nodes the   */
+/* fit drops to linear.  sides = 2 adds the loads of the opposite face  */
+/* (normal -n) of the same triangle, for zero-thickness surfaces.       */
+/* ------------------------------------------------------------------ */
+static void node_xyz4(const orc_grid* g, int lat, long i, long j, long k, double x[3]) {
+  /* lat 0..2: the u, v, w lattices; 3: cell centres */
+  double off[3] = {0.5, 0.5, 0.5};
+  if (lat < 3) off[lat] = 0.0;
+  x[0] = ((double)i + off[0]) * g->dx;
+  x[1] = ((double)j + off[1]) * g->dy;
+  x[2] = ((double)k + off[2]) * g->dz;
+}
+
+/* Cholesky solve of the m x m SPD system M c = b (in place); 0 if not SPD */
+static int chol_solve(int m, double* M, double* b) {
+  for (int i = 0; i < m; ++i) {
+    for (int j = 0; j <= i; ++j) {
+      double s = M[i * m + j];
+      for (int k = 0; k < j; ++k) s -= M[i * m + k] * M[j * m + k];
+      if (i == j) {
+        if (!(s > 0.0)) return 0;
+        M[i * m + i] = sqrt(s);
+      } else {
+        M[i * m + j] = s / M[j * m + j];
+      }
+    }
+  }
+  for (int i = 0; i < m; ++i) {
+    double s = b[i];
+    for (int k = 0; k < i; ++k) s -= M[i * m + k] * b[k];
+    b[i] = s / M[i * m + i];
+  }
+  for (int i = m - 1; i >= 0; --i) {
+    double s = b[i];
+    for (int k = i + 1; k < m; ++k) s -= M[k * m + i] * b[k];
+    b[i] = s / M[i * m + i];
+  }
+  return 1;
+}
+
+/* Quadratic MLS fit of quantity f on lattice `lat` around xe; returns the
+ * value, gradient and Hessian there.  Side test against (X, n); skip[]
+ * (optional, per cell) excludes boundary cells. */
+static void mls_fit(const orc_grid* g, int lat, const double* f, const uint8_t* skip, const double xe[3],
+                    const double X[3], const double n[3], double* val, double grad[3], double H[9]) {
+  const double del[3] = {g->dx, g->dy, g->dz};
+  const double diag = sqrt(diag2_of(g));
+  double off[3] = {0.5, 0.5, 0.5};
+  if (lat < 3) off[lat] = 0.0;
+  long planes = lat == 1 ? g->ny + 1 : g->ny;
+  long i0[3];
+  for (int d = 0; d < 3; ++d) i0[d] = (long)floor(xe[d] / del[d] - off[d]) - 1;
+  if (i0[1] < 0) i0[1] = 0;
+  if (i0[1] > planes - 4) i0[1] = planes - 4;
+  double M[100] = {0}, b[10] = {0};
+  int used = 0;
+  for (int a = 0; a < 4; ++a)
+    for (int bb = 0; bb < 4; ++bb)
+      for (int c = 0; c < 4; ++c) {
+        long ii = i0[0] + a, jj = i0[1] + bb, kk = i0[2] + c;
+        double x[3];
+        node_xyz4(g, lat, ii, jj, kk, x);
+        double side = (x[0] - X[0]) * n[0] + (x[1] - X[1]) * n[1] + (x[2] - X[2]) * n[2];
+        if (!(side > 0.0)) continue;
+        long iw = wrap(ii, g->nx), kw = wrap(kk, g->nz);
+        long id = (kw * planes + jj) * g->nx + iw;
+        if (skip && skip[id]) continue;
+        double xi[3], r2 = 0.0;
+        for (int d = 0; d < 3; ++d) {
+          xi[d] = (x[d] - xe[d]) / diag;
+          r2 += xi[d] * xi[d];
+        }
+        double w = exp(-r2);
+        double P[10] = {1.0, xi[0], xi[1], xi[2], xi[0] * xi[0], xi[1] * xi[1], xi[2] * xi[2],
+                        xi[0] * xi[1], xi[0] * xi[2], xi[1] * xi[2]};
+        for (int r = 0; r < 10; ++r) {
+          b[r] += w * P[r] * f[id];
+          for (int s = 0; s < 10; ++s) M[r * 10 + s] += w * P[r] * P[s];
+        }
+        ++used;
+      }
+  double cfs[10] = {0};
+  int ok = 0;
+  if (used >= 10) {
+    double Mc[100], bc[10];
+    memcpy(Mc, M, sizeof(Mc));
+    memcpy(bc, b, sizeof(bc));
+    if (chol_solve(10, Mc, bc)) {
+      memcpy(cfs, bc, sizeof(bc));
+      ok = 1;
+    }
+  }
+  if (!ok) { /* linear fit: the leading 4 x 4 block */
+    double Ml[16], bl[4];
+    for (int r = 0; r < 4; ++r) {
+      bl[r] = b[r];
+      for (int s = 0; s < 4; ++s) Ml[r * 4 + s] = M[r * 10 + s];
+    }
+    if (chol_solve(4, Ml, bl))
+      for (int r = 0; r < 4; ++r) cfs[r] = bl[r];
+  }
+  *val = cfs[0];
+  for (int d = 0; d < 3; ++d) grad[d] = cfs[1 + d] / diag;
+  const double id2 = 1.0 / (diag * diag);
+  H[0] = 2.0 * cfs[4] * id2; H[4] = 2.0 * cfs[5] * id2; H[8] = 2.0 * cfs[6] * id2;
+  H[1] = H[3] = cfs[7] * id2; H[2] = H[6] = cfs[8] * id2; H[5] = H[7] = cfs[9] * id2;
+}
+
+/* Traction at one marker and side: probe, fits, Taylor series. */
+static void marker_traction(const orc_grid* g, const double* u, const double* v, const double* w, const double* p,
+                            const uint8_t* isb, double re, const double X[3], const double n[3], double t[3],
+                            double* pwall) {
+  const double h = 2.0 * sqrt(diag2_of(g));
+  double xe[3];
+  for (int d = 0; d < 3; ++d) xe[d] = X[d] + h * n[d];
+  double pe, gp[3], Hp[9];
+  mls_fit(g, 3, p, isb, xe, X, n, &pe, gp, Hp);
+  const double dpn = gp[0] * n[0] + gp[1] * n[1] + gp[2] * n[2];
+  double d2pn = 0.0;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) d2pn += n[a] * Hp[a * 3 + b] * n[b];
+  const double pl = pe - h * dpn + 0.5 * h * h * d2pn;
+  double G[9];   /* G[i*3 + j] = d u_i / d x_j at the wall */
+  const double* comp[3] = {u, v, w};
+  for (int i = 0; i < 3; ++i) {
+    double val, gr[3], H[9];
+    mls_fit(g, i, comp[i], NULL, xe, X, n, &val, gr, H);
+    for (int j = 0; j < 3; ++j) {
+      double Hn = H[j * 3 + 0] * n[0] + H[j * 3 + 1] * n[1] + H[j * 3 + 2] * n[2];
+      G[i * 3 + j] = gr[j] - h * Hn;
+    }
+  }
+  for (int i = 0; i < 3; ++i) {
+    double s = 0.0;
+    for (int j = 0; j < 3; ++j) s += (G[i * 3 + j] + G[j * 3 + i]) * n[j];
+    t[i] = -pl * n[i] + s / re;
+  }
+  *pwall = pl;
+}
+
+/* Loads of all triangles: tr[6 nt] = per triangle the force t A and the
+ * torque (X - pole) x t A (summed over the sides), pwall[nt] the wall
+ * pressure p^l on the normal's side; F, M the sums in triangle order. */
+void orc_loads(const orc_grid* g, const double* xyz, int ntri, const int* tri, const double* u, const double* v,
+               const double* w, const double* p, const uint8_t* isb, double re, int sides, const double* pole,
+               double* tr, double* pwall, double* F, double* M) {
+  for (int d = 0; d < 3; ++d) F[d] = M[d] = 0.0;
+  for (long t = 0; t < ntri; ++t) {
+    const double *a, *b, *c;
+    tri_vertices(xyz, tri, t, &a, &b, &c);
+    double X[3], e1[3], e2[3], nn[3];
+    for (int d = 0; d < 3; ++d) {
+      X[d] = (a[d] + b[d] + c[d]) / 3.0;
+      e1[d] = b[d] - a[d];
+      e2[d] = c[d] - a[d];
+    }
+    nn[0] = e1[1] * e2[2] - e1[2] * e2[1];
+    nn[1] = e1[2] * e2[0] - e1[0] * e2[2];
+    nn[2] = e1[0] * e2[1] - e1[1] * e2[0];
+    const double len = sqrt(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
+    const double area = 0.5 * len;
+    double ft[3] = {0, 0, 0};
+    for (int sd = 0; sd < sides; ++sd) {
+      double n[3], tt[3], pw;
+      for (int d = 0; d < 3; ++d) n[d] = (sd == 0 ? 1.0 : -1.0) * nn[d] / len;
+      marker_traction(g, u, v, w, p, isb, re, X, n, tt, &pw);
+      if (sd == 0) pwall[t] = pw;
+      for (int d = 0; d < 3; ++d) ft[d] += tt[d] * area;
+    }
+    double r[3] = {X[0] - pole[0], X[1] - pole[1], X[2] - pole[2]};
+    double m[3] = {r[1] * ft[2] - r[2] * ft[1], r[2] * ft[0] - r[0] * ft[2], r[0] * ft[1] - r[1] * ft[0]};
+    for (int d = 0; d < 3; ++d) {
+      tr[6 * t + d] = ft[d];
+      tr[6 * t + 3 + d] = m[d];
+      F[d] += ft[d];
+      M[d] += m[d];
+    }
+  }
+}
+
+/* Pressure of the boundary cells (Section 3.2): not defined by the
+ * solution there; the value at the probe point x^e = X + h N/|N| of the
+ * cell centre (X its closest point on the owning triangle of the cell's
+ * lower u face), trilinear from the surrounding cell centres (zero normal
+ * gradient at the wall).  q[] = p with the boundary cells replaced. */
+void orc_pressure_recon(const orc_grid* g, const double* p, const uint8_t* isb, const int32_t* own_u,
+                        const double* xyz, const int* tri, double* q) {
+  const long nx = g->nx, ny = g->ny, nz = g->nz, n = nx * ny * nz;
+  const double h = 2.0 * sqrt(diag2_of(g));
+  for (long id = 0; id < n; ++id) q[id] = p[id];
+  for (long k = 0; k < nz; ++k)
+    for (long j = 0; j < ny; ++j)
+      for (long i = 0; i < nx; ++i) {
+        const long id = (k * ny + j) * nx + i;
+        if (!isb[id]) continue;
+        const int32_t t = own_u[id];   /* u grid and cells share the [k][j][i] layout */
+        if (t < 0) continue;
+        const double *a, *b, *c3;
+        tri_vertices(xyz, tri, t, &a, &b, &c3);
+        double x[3], X[3], wb[3], N[3];
+        node_xyz4(g, 3, i, j, k, x);
+        /* the periodic image of the centre nearest to the triangle */
+        const double cx = (a[0] + b[0] + c3[0]) / 3.0, cz = (a[2] + b[2] + c3[2]) / 3.0;
+        x[0] += g->lx * round((cx - x[0]) / g->lx);
+        x[2] += g->lz * round((cz - x[2]) / g->lz);
+        orc_closest_point(x, a, b, c3, X, wb);
+        double nl = 0.0;
+        for (int d = 0; d < 3; ++d) {
+          N[d] = x[d] - X[d];
+          nl += N[d] * N[d];
+        }
+        nl = sqrt(nl);
+        if (nl == 0.0) {   /* centre on the surface: the triangle's normal */
+          double e1[3], e2[3];
+          for (int d = 0; d < 3; ++d) { e1[d] = b[d] - a[d]; e2[d] = c3[d] - a[d]; }
+          N[0] = e1[1] * e2[2] - e1[2] * e2[1];
+          N[1] = e1[2] * e2[0] - e1[0] * e2[2];
+          N[2] = e1[0] * e2[1] - e1[1] * e2[0];
+          nl = sqrt(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
+        }
+        double xe[3], pe;
+        for (int d = 0; d < 3; ++d) xe[d] = X[d] + h * N[d] / nl;
+        if (trilinear(g, 3, p, xe, &pe) == 0) q[id] = pe;
+      }
+}

@@ -81,6 +81,8 @@ def lib():
             L.orc_tag_brute.argtypes = [_GP, _I, _P, _I, _P, _P, _P]
             L.orc_tag_alg1_window.argtypes = [_GP, _I, _P, _I, _P, ctypes.c_long, ctypes.c_long, _P, _P]
             L.orc_q_energy.argtypes = [_GP, _P, _P, _P, _P, _P, _P, _P, _P]
+            L.orc_loads.argtypes = [_GP, _P, _I, _P, _P, _P, _P, _P, _P, _D, _I, _P, _P, _P, _P, _P]
+            L.orc_pressure_recon.argtypes = [_GP, _P, _P, _P, _P, _P, _P]
             L.orc_force.argtypes = [_GP, _I, _P, _P, _P, _P, _P, _P, _D]
             L.orc_force.restype = _I
             L.orc_slip.argtypes = [_GP, _I, _P, _P, _P, _P, _P, _D, _P, _P]
@@ -231,6 +233,32 @@ def q_energy(g: Grid, div, isb, p, u, v, w):
     coef = np.zeros(7)
     lib().orc_q_energy(ctypes.byref(g), _p(div), _p(isb), _p(p), _p(u), _p(v), _p(w), _p(q), _p(coef))
     return q, coef
+
+
+def loads(g: Grid, xyz, tri, u, v, w, p, isb, re, sides=1, pole=(0.0, 0.0, 0.0)):
+    """Hydrodynamic loads of Section 3.3 (MLS probes at the centroids):
+    (per-triangle force and torque (nt, 6), wall pressure (nt,), F, M)."""
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    tri = np.ascontiguousarray(tri, dtype=np.int32)
+    isb = np.ascontiguousarray(isb, dtype=np.uint8)
+    tr = np.zeros((tri.shape[0], 6))
+    pw = np.zeros(tri.shape[0])
+    F, M = np.zeros(3), np.zeros(3)
+    pole = np.ascontiguousarray(pole, dtype=np.float64)
+    lib().orc_loads(ctypes.byref(g), _p(xyz), int(tri.shape[0]), _p(tri), _p(u), _p(v), _p(w), _p(p), _p(isb),
+                    float(re), int(sides), _p(pole), _p(tr), _p(pw), _p(F), _p(M))
+    return tr, pw, F, M
+
+
+def pressure_recon(g: Grid, p, isb, owners, xyz, tri):
+    """p with the boundary cells given the value at their probe point
+    (Section 3.2, post-processing)."""
+    q = np.zeros_like(p)
+    lib().orc_pressure_recon(ctypes.byref(g), _p(p), _p(np.ascontiguousarray(isb, dtype=np.uint8)),
+                             _p(np.ascontiguousarray(owners[0], dtype=np.int32)),
+                             _p(np.ascontiguousarray(xyz, dtype=np.float64)),
+                             _p(np.ascontiguousarray(tri, dtype=np.int32)), _p(q))
+    return q
 
 
 def project(g: Grid, u, v, w, p, phi, adt, re):

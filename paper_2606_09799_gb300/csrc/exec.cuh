@@ -124,6 +124,7 @@ struct Tune {
   int fft_lpb;    // complex lines per block of the x transforms
   int fft_cols;   // kx columns per block of the z transforms (power of two)
   int sweep_zy;   // z and y sweeps (FP32): 1 shared-memory tile, one thread per line; 2 several lanes per line
+  int fft_plane;  // 1 separate x and z transform kernels; 2 fused per y-plane (when the plane fits)
 };
 
 struct Exec {

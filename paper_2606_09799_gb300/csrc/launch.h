@@ -149,6 +149,14 @@ struct SpecTables {
 template <typename T>
 void launch_poisson(const Geo& g, const Fields<T>& f, const TagBuffers& b, const SpecTables<T>& tb,
                     const Stage& sg, double dt, double re, int use_q, double* partial, DevState* ds, Exec& ex);
+// ---- post-processing (loads.cu) ----------------------------------------------
+template <typename T>
+void launch_loads(const Geo& g, const Surf& s, const Fields<T>& f, const TagBuffers& b, double re, int sides,
+                  const double pole[3], double* tr, double* pw, cudaStream_t st);
+template <typename T>
+void launch_pressure_recon(const Geo& g, const Surf& s, const Fields<T>& f, const TagBuffers& b, DevState* ds,
+                           double* q, cudaStream_t st);
+
 void launch_build_poisson_tables(const Geo& g, const double* lamx, const double* lamz, double* cp, double* inv,
                                  cudaStream_t st);
 

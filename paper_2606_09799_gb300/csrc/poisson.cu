@@ -13,6 +13,8 @@
 // once per grid (they depend only on the wavenumber pair).
 #include <math.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "launch.h"
 
@@ -390,6 +392,62 @@ __device__ __forceinline__ void pair_diff(const T* H, const T* L, long long a, l
   small = pe + e * ih + s * il;
 }
 
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+
+// Right-hand side of Eq. elliptic_mod at cell (i, j, k), scaled by
+// 1/(alpha dt nx nz): mode 0 from the provisional state (bulk type), mode 1
+// the correction solve's rhs from the projected (hi, lo) state in pair
+// arithmetic; 0 on boundary cells when q is on (q_B = D uhat).
+template <typename T>
+__device__ __forceinline__ T poisson_rhs(const Geo& g, const Fields<T>& f, const unsigned* __restrict__ flags32,
+                                         const DevState* ds, int s, int use_q, double scale, int mode, T qf, T qa,
+                                         T qb, int i, int j, int k) {
+  const int n = g.nx, ny = g.ny;
+  const long long pu = (long long)ny * n, pv = (long long)(ny + 1) * n;
+  const T sc = (T)scale, idx = (T)g.idx, idy = (T)g.idy, idz = (T)g.idz;
+  const int ip = i + 1 == n ? 0 : i + 1;
+  const int kp = k + 1 == g.nz ? 0 : k + 1;
+  const long long r0 = (long long)k * pu + (long long)j * n;
+  const long long cell = r0 + i;
+  const unsigned fl = (flags32[cell >> 2] >> (8 * (cell & 3))) & 0xFFu;
+  T r = (T)0;
+  if (mode == 1) {
+    if (!(use_q && (fl & FLAG_B))) {
+      const long long v0 = (long long)k * pv + (long long)j * n + i;
+      const long long wk = (long long)kp * pu + (long long)j * n + i;
+      float bx, sx, by, sy, bz, sz, a1, e1, a2, e2, a3, e3;
+      pair_diff(f.u, f.lo[0], r0 + ip, cell, (float)f.idh[0][0], (float)f.idh[0][1], bx, sx);
+      pair_diff(f.v, f.lo[1], v0 + n, v0, (float)f.idh[1][0], (float)f.idh[1][1], by, sy);
+      pair_diff(f.w, f.lo[2], wk, cell, (float)f.idh[2][0], (float)f.idh[2][1], bz, sz);
+      two_sum(bx, by, a1, e1);
+      two_sum(a1, bz, a2, e2);
+      // the target q of the first solve: uniform (an FP32 pair) or the
+      // energy-conserving shape stored per cell by mode 0
+      const float qh = use_q == 2 ? (float)f.qk[cell] : (use_q ? ds->qf_hi[s] : 0.0f);
+      const float ql = use_q == 1 ? ds->qf_lo[s] : 0.0f;
+      two_sum(a2, -qh, a3, e3);
+      r = (T)((a3 + (((e1 + e2) + e3) + ((sx + sy) + sz) - ql)) * (float)scale);
+    }
+  } else if (!(use_q && (fl & FLAG_B))) {
+    const long long v0 = (long long)k * pv + (long long)j * n + i;
+    // explicit rounding (no contraction): the single-simulation and the
+    // batched kernels compile this body separately and must round alike
+    const T du = mul_rn(f.u[r0 + ip] - f.u[cell], idx);
+    const T dv = mul_rn(f.v[v0 + n] - f.v[v0], idy);
+    const T dw = mul_rn(f.w[(long long)kp * pu + (long long)j * n + i] - f.w[cell], idz);
+    T q = qf;
+    if (use_q == 2) {   // App. B shape, kept per cell for the correction solve
+      q = qa + qb * p_minus_e<T>(g, f, i, j, k);
+      f.qk[cell] = q;
+    }
+    r = mul_rn(add_rn(add_rn(du, dv), dw) - q, sc);
+  }
+  return r;
+}
+
 // mode 0: rhs = (D uhat - q)/(alpha dt) from the (hi part of the) state;
 // mode 1: rhs of the correction solve, (D u' - q_F)/(alpha dt) on fluid
 // cells from the projected state held as (hi, lo) pairs, in pair arithmetic
@@ -406,8 +464,6 @@ __device__ __forceinline__ void fft_x_fwd(const Blk& bk, const Geo& g, const Fie
   const int line0 = bk.x * lines_per_block;
   const T qf = use_q ? (T)ds->qf[s] : (T)0;
   const T qa = use_q == 2 ? (T)ds->qa[s] : (T)0, qb = use_q == 2 ? (T)ds->qb[s] : (T)0;
-  const T sc = (T)scale, idx = (T)g.idx, idy = (T)g.idy, idz = (T)g.idz;
-  const long long pu = (long long)ny * n, pv = (long long)(ny + 1) * n;
   // load: rows 2 l and 2 l + 1 of line l; divergence in the bulk type
   for (int l = threadIdx.y; l < lines_per_block; l += blockDim.y) {
     int jj[2], kk[2];
@@ -423,45 +479,10 @@ __device__ __forceinline__ void fft_x_fwd(const Blk& bk, const Geo& g, const Fie
       C z;
       z.x = (T)0;
       z.y = (T)0;
-      const int ip = i + 1 == n ? 0 : i + 1;
 #pragma unroll
       for (int hh = 0; hh < 2; ++hh) {
         if (!ok[hh]) continue;
-        const int j = jj[hh], k = kk[hh];
-        const int kp = k + 1 == g.nz ? 0 : k + 1;
-        const long long r0 = (long long)k * pu + (long long)j * n;
-        const long long cell = r0 + i;
-        const unsigned fl = (flags32[cell >> 2] >> (8 * (cell & 3))) & 0xFFu;
-        T r = (T)0;
-        if (mode == 1) {
-          if (!(use_q && (fl & FLAG_B))) {
-            const long long v0 = (long long)k * pv + (long long)j * n + i;
-            const long long wk = (long long)kp * pu + (long long)j * n + i;
-            float bx, sx, by, sy, bz, sz, a1, e1, a2, e2, a3, e3;
-            pair_diff(f.u, f.lo[0], r0 + ip, cell, (float)f.idh[0][0], (float)f.idh[0][1], bx, sx);
-            pair_diff(f.v, f.lo[1], v0 + n, v0, (float)f.idh[1][0], (float)f.idh[1][1], by, sy);
-            pair_diff(f.w, f.lo[2], wk, cell, (float)f.idh[2][0], (float)f.idh[2][1], bz, sz);
-            two_sum(bx, by, a1, e1);
-            two_sum(a1, bz, a2, e2);
-            // the target q of the first solve: uniform (an FP32 pair) or the
-            // energy-conserving shape stored per cell by mode 0
-            const float qh = use_q == 2 ? (float)f.qk[cell] : (use_q ? ds->qf_hi[s] : 0.0f);
-            const float ql = use_q == 1 ? ds->qf_lo[s] : 0.0f;
-            two_sum(a2, -qh, a3, e3);
-            r = (T)((a3 + (((e1 + e2) + e3) + ((sx + sy) + sz) - ql)) * (float)scale);
-          }
-        } else if (!(use_q && (fl & FLAG_B))) {
-          const long long v0 = (long long)k * pv + (long long)j * n + i;
-          const T du = (f.u[r0 + ip] - f.u[cell]) * idx;
-          const T dv = (f.v[v0 + n] - f.v[v0]) * idy;
-          const T dw = (f.w[(long long)kp * pu + (long long)j * n + i] - f.w[cell]) * idz;
-          T q = qf;
-          if (use_q == 2) {   // App. B shape, kept per cell for the correction solve
-            q = qa + qb * p_minus_e<T>(g, f, i, j, k);
-            f.qk[cell] = q;
-          }
-          r = (du + dv + dw - q) * sc;
-        }
+        const T r = poisson_rhs<T>(g, f, flags32, ds, s, use_q, scale, mode, qf, qa, qb, i, jj[hh], kk[hh]);
         if (hh == 0) z.x = r;
         else z.y = r;
       }
@@ -553,6 +574,175 @@ struct FftXInv {
   int lines_per_block;
   T* out_phi;
   __device__ __forceinline__ void operator()(const Blk& bk) const { fft_x_inv<T>(bk, g, f, tw, plan, lines_per_block, out_phi); }
+};
+
+// ---------------------------------------------------------------------------
+// Fused per-plane transforms: one block per y-plane j keeps the plane's x
+// half-spectra [k][kx] in shared memory between the x and the z passes, so
+// the forward spectrum leaves the block once and the inverse one arrives
+// once (no global round trip between the two directions).  Used when the
+// plane (nz * nkx complex values) and two work buffers fit.  Rows k and
+// k + 1 of the plane form one complex line of the x transform.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void fft_plane_fwd(const Blk& bk, const Geo& g, const Fields<T>& f,
+                                              const unsigned* __restrict__ flags32, const T* __restrict__ twx,
+                                              const T* __restrict__ twz, const FftPlan& px, const FftPlan& pz, int wbuf,
+                                              int cz, const DevState* ds, int s, int use_q, double scale, int mode) {
+  using C = typename Cplx<T>::type;
+  extern __shared__ unsigned char smem_raw[];
+  const int nx = g.nx, nz = g.nz, nkx = g.nkx, ny = g.ny;
+  C* S = reinterpret_cast<C*>(smem_raw);   // [k][kx]
+  C* bufa = S + (size_t)nz * nkx;
+  C* bufb = bufa + wbuf;
+  const int j = bk.x;
+  const int lc = max(1, wbuf / nx);
+  const T qf = use_q ? (T)ds->qf[s] : (T)0;
+  const T qa = use_q == 2 ? (T)ds->qa[s] : (T)0, qb = use_q == 2 ? (T)ds->qb[s] : (T)0;
+  const int nlines = nz / 2;
+  // x: lc complex lines (row pairs) at a time into S
+  for (int l0 = 0; l0 < nlines; l0 += lc) {
+    const int nl = min(lc, nlines - l0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < nl * nx; t += blockDim.x) {
+      const int l = t / nx, i = t - l * nx;
+      const int k0 = 2 * (l0 + l);
+      C z;
+      z.x = poisson_rhs<T>(g, f, flags32, ds, s, use_q, scale, mode, qf, qa, qb, i, j, k0);
+      z.y = poisson_rhs<T>(g, f, flags32, ds, s, use_q, scale, mode, qf, qa, qb, i, j, k0 + 1);
+      bufa[t] = z;
+    }
+    const int res = fft_lines<T, false>(bufa, bufb, nl, px, reinterpret_cast<const C*>(twx));
+    const C* out = res == 0 ? bufa : bufb;
+    for (int t = threadIdx.x; t < nl * nkx; t += blockDim.x) {
+      const int l = t / nkx, kx = t - l * nkx;
+      const C Z = out[l * nx + kx];
+      const C Zc = cconj(out[l * nx + (kx == 0 ? 0 : nx - kx)]);
+      C Xa, Xb;
+      Xa.x = (T)0.5 * (Z.x + Zc.x);
+      Xa.y = (T)0.5 * (Z.y + Zc.y);
+      Xb.x = (T)0.5 * (Z.y - Zc.y);   // Xb = (Z - Zc) / (2 i)
+      Xb.y = (T)-0.5 * (Z.x - Zc.x);
+      const int k0 = 2 * (l0 + l);
+      S[k0 * nkx + kx] = Xa;
+      S[(k0 + 1) * nkx + kx] = Xb;
+    }
+  }
+  // z: cz columns at a time, strided lines in the work buffers, to global
+  C* spec = reinterpret_cast<C*>(f.spec);
+  const int lcz = __ffs(cz) - 1;
+  const unsigned mcz = magic_div_dev(cz);
+  for (int kx0 = 0; kx0 < nkx; kx0 += cz) {
+    const int w = min(cz, nkx - kx0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < nz * cz; t += blockDim.x) {
+      const int k = t >> lcz, c = t & (cz - 1);
+      C z;
+      z.x = z.y = (T)0;
+      if (c < w) z = S[k * nkx + kx0 + c];
+      bufa[t] = z;
+    }
+    const int res = fft_lines<T, false>(bufa, bufb, cz, pz, reinterpret_cast<const C*>(twz), cz, 1, mcz);
+    const C* out = res == 0 ? bufa : bufb;
+    for (int t = threadIdx.x; t < nz * cz; t += blockDim.x) {
+      const int k = t >> lcz, c = t & (cz - 1);
+      if (c < w) spec[((long long)k * ny + j) * nkx + kx0 + c] = out[t];
+    }
+  }
+}
+template <typename T>
+struct FftPlaneFwd {
+  static constexpr int kThreads = 1024;
+  Geo g;
+  Fields<T> f;
+  const unsigned* flags32;
+  const T* twx;
+  const T* twz;
+  FftPlan px, pz;
+  int wbuf, cz;
+  const DevState* ds;
+  int s, use_q;
+  double scale;
+  int mode;
+  __device__ __forceinline__ void operator()(const Blk& bk) const {
+    fft_plane_fwd<T>(bk, g, f, flags32, twx, twz, px, pz, wbuf, cz, ds, s, use_q, scale, mode);
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ void fft_plane_inv(const Blk& bk, const Geo& g, const Fields<T>& f, const T* __restrict__ twx,
+                                              const T* __restrict__ twz, const FftPlan& px, const FftPlan& pz, int wbuf,
+                                              int cz, T* __restrict__ out_phi) {
+  using C = typename Cplx<T>::type;
+  extern __shared__ unsigned char smem_raw[];
+  const int nx = g.nx, nz = g.nz, nkx = g.nkx, ny = g.ny;
+  C* S = reinterpret_cast<C*>(smem_raw);   // [k][kx]
+  C* bufa = S + (size_t)nz * nkx;
+  C* bufb = bufa + wbuf;
+  const int j = bk.x;
+  const C* spec = reinterpret_cast<const C*>(f.spec);
+  // z inverse: cz columns at a time from global into S
+  const int lcz = __ffs(cz) - 1;
+  const unsigned mcz = magic_div_dev(cz);
+  for (int kx0 = 0; kx0 < nkx; kx0 += cz) {
+    const int w = min(cz, nkx - kx0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < nz * cz; t += blockDim.x) {
+      const int k = t >> lcz, c = t & (cz - 1);
+      C z;
+      z.x = z.y = (T)0;
+      if (c < w) z = spec[((long long)k * ny + j) * nkx + kx0 + c];
+      bufa[t] = z;
+    }
+    const int res = fft_lines<T, true>(bufa, bufb, cz, pz, reinterpret_cast<const C*>(twz), cz, 1, mcz);
+    const C* out = res == 0 ? bufa : bufb;
+    for (int t = threadIdx.x; t < nz * cz; t += blockDim.x) {
+      const int k = t >> lcz, c = t & (cz - 1);
+      if (c < w) S[k * nkx + kx0 + c] = out[t];
+    }
+  }
+  // x inverse: two half-spectra (rows k, k + 1) -> one complex line -> two real rows
+  const int lc = max(1, wbuf / nx);
+  const int nlines = nz / 2;
+  for (int l0 = 0; l0 < nlines; l0 += lc) {
+    const int nl = min(lc, nlines - l0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < nl * nx; t += blockDim.x) {
+      const int l = t / nx, kx = t - l * nx;
+      const int k0 = 2 * (l0 + l);
+      const bool mirror = kx >= nkx;
+      const int q = mirror ? nx - kx : kx;
+      C A = S[k0 * nkx + q], B = S[(k0 + 1) * nkx + q];
+      if (q == 0 || 2 * q == nx) { A.y = (T)0; B.y = (T)0; }   // real DC / Nyquist bins
+      if (mirror) { A = cconj(A); B = cconj(B); }
+      C z;  // A + i B
+      z.x = A.x - B.y;
+      z.y = A.y + B.x;
+      bufa[t] = z;
+    }
+    const int res = fft_lines<T, true>(bufa, bufb, nl, px, reinterpret_cast<const C*>(twx));
+    const C* out = res == 0 ? bufa : bufb;
+    for (int t = threadIdx.x; t < nl * nx; t += blockDim.x) {
+      const int l = t / nx, i = t - l * nx;
+      const int k0 = 2 * (l0 + l);
+      out_phi[((long long)k0 * ny + j) * nx + i] = out[t].x;
+      out_phi[((long long)(k0 + 1) * ny + j) * nx + i] = out[t].y;
+    }
+  }
+}
+template <typename T>
+struct FftPlaneInv {
+  static constexpr int kThreads = 1024;
+  Geo g;
+  Fields<T> f;
+  const T* twx;
+  const T* twz;
+  FftPlan px, pz;
+  int wbuf, cz;
+  T* out_phi;
+  __device__ __forceinline__ void operator()(const Blk& bk) const {
+    fft_plane_inv<T>(bk, g, f, twx, twz, px, pz, wbuf, cz, out_phi);
+  }
 };
 
 // z transform of the half-spectrum, in place; a block takes `cols` adjacent
@@ -1099,16 +1289,44 @@ void launch_poisson(const Geo& g, const Fields<T>& f, const TagBuffers& b, const
       ex.launch(dim3((unsigned)((2 * tlines + 127) / 128)), dim3(128), 0, TriY<T>{g, f, tb.cp, tb.inv, fwd});
     }
   };
+  // fused per-plane transforms when the plane's half-spectrum and two work
+  // buffers fit 200 KB of shared memory; the buffers take what is left, so
+  // a small plane goes through each direction in one or two chunks
+  const long long plane_b = (long long)sh.nz * sh.nkx * (long long)sizeof(C);
+  const long long wmax = (200ll * 1024 - plane_b) / (2 * (long long)sizeof(C));
+  int lcp = (int)std::min<long long>(sh.nz / 2, wmax / sh.nx);
+  int czp = 64;
+  while (czp > 1 && (long long)czp * sh.nz > wmax) czp >>= 1;
+  const int wbuf = std::max(lcp * sh.nx, czp * sh.nz);
+  const size_t smp = (size_t)plane_b + 2ull * wbuf * sizeof(C);
+  // (opt-in: on a 128^3 plate one block per plane is latency-bound and
+  // slower than the separate x and z kernels, which stay the default)
+  const bool plane = tu.fft_plane == 2 && lcp >= 1 && (long long)czp * sh.nz <= wmax && smp <= 200 * 1024;
   // the rest of one solve: z transform, wall-normal Thomas, inverse z and x
   auto solve_rest = [&](T* out, bool marks) {
-    if (marks) ex.mark(ST_FFT_Z_FWD);
-    ex.launch(dim3(g.ny * ntile), dim3(256), smz, FftZ<T, false>{g, f, tb.twz, pz, cols});
+    if (!plane) {
+      if (marks) ex.mark(ST_FFT_Z_FWD);
+      ex.launch(dim3(g.ny * ntile), dim3(256), smz, FftZ<T, false>{g, f, tb.twz, pz, cols});
+    }
     if (marks) ex.mark(ST_TRI_Y);
     tri_solve();
+    if (plane) {
+      if (marks) ex.mark(ST_FFT_X_INV);
+      ex.launch(dim3(g.ny), dim3(1024), smp, FftPlaneInv<T>{g, f, tb.twx, tb.twz, px, pz, wbuf, czp, out});
+      return;
+    }
     if (marks) ex.mark(ST_FFT_Z_INV);
     ex.launch(dim3(g.ny * ntile), dim3(256), smz, FftZ<T, true>{g, f, tb.twz, pz, cols});
     if (marks) ex.mark(ST_FFT_X_INV);
     ex.launch(xgrid, xblk, smx, FftXInv<T>{g, f, tb.twx, px, lpb, out});
+  };
+  // forward x (and z, fused per plane) with the right-hand side of Eq. elliptic_mod
+  auto forward = [&](int mode) {
+    if (plane)
+      ex.launch(dim3(g.ny), dim3(1024), smp,
+                FftPlaneFwd<T>{g, f, b.flags32, tb.twx, tb.twz, px, pz, wbuf, czp, ds, sg.s, use_q, scale, mode});
+    else
+      ex.launch(xgrid, xblk, smx, FftXFwd<T>{g, f, b.flags32, tb.twx, px, lpb, ds, sg.s, use_q, scale, mode});
   };
   const double adt = sg.alp * dt, bb = adt / (2.0 * re);
   ProjCoef<T> cf;
@@ -1116,7 +1334,7 @@ void launch_poisson(const Geo& g, const Fields<T>& f, const TagBuffers& b, const
   cf.bx = (T)(bb * g.idx * g.idx); cf.by = (T)(bb * g.idy * g.idy); cf.bz = (T)(bb * g.idz * g.idz);
   const dim3 pgrid((g.nx + 31) / 32, (g.ny + 3) / 4, g.nz), pblk(32, 4);
   ex.mark(ST_FFT_X_FWD);
-  ex.launch(xgrid, xblk, smx, FftXFwd<T>{g, f, b.flags32, tb.twx, px, lpb, ds, sg.s, use_q, scale, 0});
+  forward(0);
   solve_rest(f.phi, true);
   if (!f.lo[0]) {
     ex.mark(ST_PROJECT);
@@ -1128,7 +1346,7 @@ void launch_poisson(const Geo& g, const Fields<T>& f, const TagBuffers& b, const
   ex.mark(ST_PROJECT);
   ex.launch(pgrid, pblk, 0, Project<T>{g, f, cf, 1});
   ex.mark(ST_CORRECT);
-  ex.launch(xgrid, xblk, smx, FftXFwd<T>{g, f, b.flags32, tb.twx, px, lpb, ds, sg.s, use_q, scale, 1});
+  forward(1);
   solve_rest(f.phi2, false);
   ex.launch(pgrid, pblk, 0, Project<T>{g, f, cf, 2});
 }
@@ -1142,6 +1360,8 @@ void set_fft_smem_limits() {
   op_smem_limit<FftZ<T, false>>(maxsm);
   op_smem_limit<FftZ<T, true>>(maxsm);
   op_smem_limit<TriYSmem<T>>(160 * 1024);
+  op_smem_limit<FftPlaneFwd<T>>(200 * 1024);
+  op_smem_limit<FftPlaneInv<T>>(200 * 1024);
 }
 
 void init_kernel_attributes() {

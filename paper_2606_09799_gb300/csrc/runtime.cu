@@ -805,7 +805,7 @@ static ibm_status batch_prepare(ibm_batch* b) {
     if (h->need_full_reset) {
       const ibm_status s = full_reset(h, h->user);
       if (s != IBM_OK) {
-        snprintf(b->err, sizeof(b->err), "reset of an instance: %s", h->err);
+        snprintf(b->err, sizeof(b->err), "reset of an instance: %.400s", h->err);
         return s;
       }
     }
@@ -844,7 +844,8 @@ struct Knob {
 };
 
 static std::vector<Knob> tune_knobs() {
-  return {{&Tune::sweep_zy, {2, 1}}, {&Tune::tri_y, {1, 2, 3}}, {&Tune::sweep_w, {64, 32, 16}},
+  return {{&Tune::fft_plane, {2, 1}}, {&Tune::sweep_zy, {2, 1}}, {&Tune::tri_y, {1, 2, 3}},
+          {&Tune::sweep_w, {64, 32, 16}},
           {&Tune::fft_lpb, {0, 8, 4, 2}},
           {&Tune::fft_cols, {16, 8, 4}}};
 }
@@ -904,6 +905,7 @@ static void tune_out(const Tune& t, double ms, ibm_tune* out) {
   out->fft_lpb = t.fft_lpb;
   out->fft_cols = t.fft_cols;
   out->sweep_zy = t.sweep_zy;
+  out->fft_plane = t.fft_plane;
   out->ms_per_step = ms;
 }
 
@@ -912,8 +914,8 @@ static void tune_out(const Tune& t, double ms, ibm_tune* out) {
 static void tune_log(const Tune& t, double ms) {
   static const bool on = getenv("IBM_AUTOTUNE_LOG") != nullptr;
   if (on)
-    fprintf(stderr, "ibm autotune: tri_y %d sweep_w %d fft_lpb %d fft_cols %d sweep_zy %d -> %.4f ms/step\n", t.tri_y,
-            t.sweep_w, t.fft_lpb, t.fft_cols, t.sweep_zy, ms);
+    fprintf(stderr, "ibm autotune: tri_y %d sweep_w %d fft_lpb %d fft_cols %d sweep_zy %d fft_plane %d -> %.4f ms/step\n",
+            t.tri_y, t.sweep_w, t.fft_lpb, t.fft_cols, t.sweep_zy, t.fft_plane, ms);
 }
 
 template <class Trial>
@@ -1483,12 +1485,13 @@ static bool tune_valid(const ibm_tune* t) {
   if (t->fft_lpb < 0 || t->fft_lpb > 2048) return false;
   if (t->fft_cols < 0 || t->fft_cols > 16 || (t->fft_cols & (t->fft_cols - 1))) return false;
   if (t->sweep_zy < 0 || t->sweep_zy > 2) return false;
+  if (t->fft_plane < 0 || t->fft_plane > 2) return false;
   return true;
 }
 
 ibm_status ibm_set_tune(ibm_handle h, const ibm_tune* t) {
   if (!h || !tune_valid(t)) return IBM_ERR_ARG;
-  h->tune = Tune{t->tri_y, t->sweep_w, t->fft_lpb, t->fft_cols, t->sweep_zy};
+  h->tune = Tune{t->tri_y, t->sweep_w, t->fft_lpb, t->fft_cols, t->sweep_zy, t->fft_plane};
   invalidate(h);
   return IBM_OK;
 }
@@ -1609,7 +1612,7 @@ ibm_status ibm_batch_sync(ibm_batch_handle b) {
     const ibm_status s = ibm_sync(b->hs[i]);
     if (s != IBM_OK && first == IBM_OK) {
       first = s;
-      snprintf(b->err, sizeof(b->err), "instance %zu: %s", i, b->hs[i]->err);
+      snprintf(b->err, sizeof(b->err), "instance %zu: %.400s", i, b->hs[i]->err);
     }
   }
   return first;
@@ -1649,7 +1652,7 @@ ibm_status ibm_batch_profile_stages(ibm_batch_handle b, int nsteps, double* ms, 
 
 ibm_status ibm_batch_set_tune(ibm_batch_handle b, const ibm_tune* t) {
   if (!b || !tune_valid(t)) return IBM_ERR_ARG;
-  b->tune = Tune{t->tri_y, t->sweep_w, t->fft_lpb, t->fft_cols, t->sweep_zy};
+  b->tune = Tune{t->tri_y, t->sweep_w, t->fft_lpb, t->fft_cols, t->sweep_zy, t->fft_plane};
   b->built = false;
   return IBM_OK;
 }
@@ -1704,8 +1707,63 @@ ibm_status ibm_step_batch(const ibm_handle* hs, int n, int nsteps) {
     g_batch_cache.push_back(b);
   }
   const ibm_status s = ibm_batch_step(b, nsteps);
-  if (s != IBM_OK) snprintf(hs[0]->err, sizeof(hs[0]->err), "ibm_step_batch: %s", b->err);
+  if (s != IBM_OK) snprintf(hs[0]->err, sizeof(hs[0]->err), "ibm_step_batch: %.400s", b->err);
   return s;
+}
+
+
+// ---- post-processing: loads and boundary-cell pressure ---------------------------
+ibm_status ibm_get_loads(ibm_handle h, int sides, const double* pole, double* force, double* torque,
+                         double* per_triangle, double* p_wall) {
+  if (!h || (sides != 1 && sides != 2) || !force || !torque) return IBM_ERR_ARG;
+  const double zero[3] = {0.0, 0.0, 0.0};
+  const double* pl = pole ? pole : zero;
+  for (int d = 0; d < 3; ++d) force[d] = torque[d] = 0.0;
+  if (h->nt == 0) return IBM_OK;
+  const int nt = h->nt;
+  double* dtr = (double*)dalloc(h, (size_t)nt * 7 * sizeof(double));
+  if (!dtr) {
+    set_err(h, "%s", "device allocation for the loads failed");
+    return IBM_ERR_OOM;
+  }
+  double* dpw = dtr + 6ll * nt;
+  if (h->esize == 8)
+    launch_loads<double>(h->g, surface(h), fields<double>(h), h->tb, h->desc.re, sides, pl, dtr, dpw, h->user);
+  else
+    launch_loads<float>(h->g, surface(h), fields<float>(h), h->tb, h->desc.re, sides, pl, dtr, dpw, h->user);
+  std::vector<double> host((size_t)nt * 7);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host.data(), dtr, host.size() * sizeof(double), cudaMemcpyDeviceToHost, h->user);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->user);
+  dfree(h, dtr);
+  if (e != cudaSuccess) return cuda_fail(h, e, "ibm_get_loads");
+  // fixed order: triangle by triangle
+  for (int t = 0; t < nt; ++t)
+    for (int d = 0; d < 3; ++d) {
+      force[d] += host[6ll * t + d];
+      torque[d] += host[6ll * t + 3 + d];
+    }
+  if (per_triangle) memcpy(per_triangle, host.data(), (size_t)nt * 6 * sizeof(double));
+  if (p_wall) memcpy(p_wall, host.data() + 6ll * nt, (size_t)nt * sizeof(double));
+  return check_device(h);
+}
+
+ibm_status ibm_get_pressure_recon(ibm_handle h, double* p, int on_device) {
+  if (!h || !p) return IBM_ERR_ARG;
+  const Geo& g = h->g;
+  cudaStream_t st = h->user;
+  double* stage = (double*)h->scr;   // holds at least ncell doubles in both precisions
+  if (h->esize == 8) {
+    CK(cudaMemcpyAsync(stage, h->p, g.ncell * 8, cudaMemcpyDeviceToDevice, st));
+    launch_pressure_recon<double>(g, surface(h), fields<double>(h), h->tb, h->ds, stage, st);
+  } else {
+    k_convert<float, double><<<num_sms() * 4, 256, 0, st>>>((const float*)h->p, stage, g.ncell);
+    launch_pressure_recon<float>(g, surface(h), fields<float>(h), h->tb, h->ds, stage, st);
+  }
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(p, stage, g.ncell * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return check_device(h);
 }
 
 }  // extern "C"

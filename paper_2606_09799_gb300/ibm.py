@@ -58,7 +58,8 @@ IBM_NSTAGES = 16
 
 class ibm_tune(ctypes.Structure):
     _fields_ = [("tri_y", ctypes.c_int), ("sweep_w", ctypes.c_int), ("fft_lpb", ctypes.c_int),
-                ("fft_cols", ctypes.c_int), ("sweep_zy", ctypes.c_int), ("ms_per_step", ctypes.c_double)]
+                ("fft_cols", ctypes.c_int), ("sweep_zy", ctypes.c_int), ("fft_plane", ctypes.c_int),
+                ("ms_per_step", ctypes.c_double)]
 
 
 class ibm_batch_info(ctypes.Structure):
@@ -74,7 +75,8 @@ EXPORTS = ("ibm_create_grid", "ibm_destroy", "ibm_set_surface", "ibm_set_body_fo
            "ibm_set_allocator", "ibm_version", "ibm_profile_stages", "ibm_stage_name", "ibm_tag_noalloc",
            "ibm_set_tune", "ibm_get_tune", "ibm_autotune", "ibm_batch_create", "ibm_batch_destroy",
            "ibm_batch_step", "ibm_batch_sync", "ibm_batch_get_info", "ibm_batch_profile_stages",
-           "ibm_batch_set_tune", "ibm_batch_autotune", "ibm_batch_last_error", "ibm_step_batch")
+           "ibm_batch_set_tune", "ibm_batch_autotune", "ibm_batch_last_error", "ibm_step_batch",
+           "ibm_get_loads", "ibm_get_pressure_recon")
 
 
 def library_path() -> str:
@@ -126,6 +128,8 @@ def load(build_if_needed: bool = True):
         L.ibm_batch_last_error.argtypes = [P]
         L.ibm_batch_last_error.restype = ctypes.c_char_p
         L.ibm_step_batch.argtypes = [P, I, I]
+        L.ibm_get_loads.argtypes = [P, I, P, P, P, P, P]
+        L.ibm_get_pressure_recon.argtypes = [P, P, I]
         for name in EXPORTS:
             if name not in ("ibm_last_error", "ibm_version", "ibm_stage_name", "ibm_batch_last_error"):
                 getattr(L, name).restype = ctypes.c_int
@@ -264,11 +268,12 @@ def ibm_tag_noalloc(nx, ny, nz, xyz, tri, owners, lx=1.0, ly=1.0, lz=1.0, ybc=IB
 
 def _tune_dict(t: ibm_tune) -> dict:
     return {"tri_y": t.tri_y, "sweep_w": t.sweep_w, "fft_lpb": t.fft_lpb, "fft_cols": t.fft_cols,
-            "sweep_zy": t.sweep_zy, "ms_per_step": t.ms_per_step}
+            "sweep_zy": t.sweep_zy, "fft_plane": t.fft_plane, "ms_per_step": t.ms_per_step}
 
 
-def ibm_set_tune(h, tri_y=0, sweep_w=0, fft_lpb=0, fft_cols=0, sweep_zy=0):
-    _check(h, load().ibm_set_tune(h, ctypes.byref(ibm_tune(tri_y, sweep_w, fft_lpb, fft_cols, sweep_zy, 0.0))))
+def ibm_set_tune(h, tri_y=0, sweep_w=0, fft_lpb=0, fft_cols=0, sweep_zy=0, fft_plane=0):
+    _check(h, load().ibm_set_tune(h, ctypes.byref(ibm_tune(tri_y, sweep_w, fft_lpb, fft_cols, sweep_zy, fft_plane,
+                                                           0.0))))
 
 
 def ibm_get_tune(h) -> dict:
@@ -327,9 +332,9 @@ def ibm_batch_profile_stages(b, nsteps=1) -> dict:
     return {ibm_stage_name(i): (ms[i], kn[i]) for i in range(IBM_NSTAGES)}
 
 
-def ibm_batch_set_tune(b, tri_y=0, sweep_w=0, fft_lpb=0, fft_cols=0, sweep_zy=0):
+def ibm_batch_set_tune(b, tri_y=0, sweep_w=0, fft_lpb=0, fft_cols=0, sweep_zy=0, fft_plane=0):
     _bcheck(b, load().ibm_batch_set_tune(b, ctypes.byref(ibm_tune(tri_y, sweep_w, fft_lpb, fft_cols, sweep_zy,
-                                                                   0.0))))
+                                                                   fft_plane, 0.0))))
 
 
 def ibm_batch_autotune(b, steps=3) -> dict:
@@ -344,6 +349,23 @@ def ibm_batch_last_error(b) -> str:
 
 def ibm_step_batch(hs, nsteps=1):
     _check(hs[0], load().ibm_step_batch(_handles(hs), len(hs), int(nsteps)))
+
+
+def ibm_get_loads(h, nt, sides=1, pole=(0.0, 0.0, 0.0)):
+    """(force (3,), torque (3,), per-triangle force and torque (nt, 6),
+    wall pressure (nt,)) from the current step (Section 3.3)."""
+    F, M = np.zeros(3), np.zeros(3)
+    tr, pw = np.zeros((nt, 6)), np.zeros(nt)
+    pl = np.ascontiguousarray(pole, dtype=np.float64)
+    _check(h, load().ibm_get_loads(h, int(sides), pl.ctypes.data, F.ctypes.data, M.ctypes.data,
+                                   tr.ctypes.data, pw.ctypes.data))
+    return F, M, tr, pw
+
+
+def ibm_get_pressure_recon(h, nx, ny, nz):
+    p = np.empty((nz, ny, nx))
+    _check(h, load().ibm_get_pressure_recon(h, p.ctypes.data, 0))
+    return p
 
 
 def ibm_stage_name(i) -> str:
@@ -447,6 +469,13 @@ class Simulation:
 
     def autotune(self, steps=3):
         return ibm_autotune(self.h, steps)
+
+    def loads(self, sides=1, pole=(0.0, 0.0, 0.0)):
+        return ibm_get_loads(self.h, self.nt, sides, pole)
+
+    def pressure_recon(self):
+        nx, ny, nz = self.shape
+        return ibm_get_pressure_recon(self.h, nx, ny, nz)
 
     def set_tune(self, **kw):
         ibm_set_tune(self.h, **kw)

@@ -284,8 +284,9 @@ def test_candidate_capacity_grows_for_large_triangles():
     assert d["nforce"][0] == 2 * 64 * 64
 
 
-@pytest.mark.parametrize("tune", [dict(tri_y=1), dict(tri_y=2, sweep_w=16), dict(tri_y=3, fft_lpb=2, fft_cols=2),
-                                  dict(tri_y=3, sweep_zy=1, sweep_w=64, fft_lpb=8, fft_cols=16)])
+@pytest.mark.parametrize("tune", [dict(tri_y=1, fft_plane=2), dict(tri_y=2, sweep_w=16, fft_plane=1),
+                                  dict(tri_y=3, fft_lpb=2, fft_cols=2, fft_plane=1),
+                                  dict(tri_y=3, sweep_zy=1, sweep_w=64, fft_lpb=8, fft_cols=16, fft_plane=2)])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-5)])
 def test_every_launch_shape_matches_oracle(tune, precision, tol):
     """Every choice the autotuner can make (Thomas variant, sweep form and
