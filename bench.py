@@ -267,6 +267,9 @@ def gpu_arm(args):
                              clocks=clk.summary(), tune=tune)
         sim.close()
     batched = None if (args.only_headline or args.no_batch) else batched_leg(args, dev, stream, flush, world)
+    ab = None
+    if not (args.only_headline or args.no_ab):
+        ab = ab_leg(args, wl, dxyz, dvel, surf, dev, stream, flush, world, results[args.precision]["tune"])
     if rank != 0:
         return None
     head = results[args.precision]
@@ -330,6 +333,8 @@ def gpu_arm(args):
                       "slip_l1": r["diag"]["slip_l1"], "clocks": r["clocks"], "tune": r["tune"]}
     if batched is not None:
         line["batched"] = batched
+    if ab is not None:
+        line["ab_cn"] = ab
     if args.e5_steps > 0:
         line["e5_heaving_pitching_plate"] = e5_leg(args, dev, stream)
     if "mixed" in results and "fp64" in results:
@@ -339,6 +344,40 @@ def gpu_arm(args):
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_steps)
     return line
+
+
+def ab_leg(args, wl, dxyz, dvel, surf, dev, stream, flush, world, tune):
+    """The same workload and protocol with the AB+CN scheme (one sub-stage
+    per step, Section 2) in the headline precision, launch shapes as tuned
+    for RK2+CN."""
+    import torch
+    from paper_2606_09799_gb300 import ibm
+
+    K, W = args.steps, args.warmup
+    sim = ibm.Simulation(wl.nx, wl.ny, wl.nz, wl.lx, wl.ly, wl.lz, re=wl.re, dt=wl.dt, precision=args.precision,
+                         scheme="ab", stream=stream.cuda_stream)
+    if tune:
+        sim.set_tune(**{k: v for k, v in tune.items() if k != "ms_per_step"})
+    sim.set_surface(surf[0][0], surf[0][1], wl.tri)
+    for s in range(W):
+        sim.set_surface(dxyz[s], dvel[s])
+        sim.step(1)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    for n in range(K):
+        flush.fill_(n & 0xFF)
+        ev[n][0].record(stream)
+        sim.set_surface(dxyz[W + n], dvel[W + n])
+        sim.step(1)
+        ev[n][1].record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), dev, world)
+    diag = sim.diag()
+    sim.close()
+    return {"scheme": "AB+CN", "precision": args.precision, "value": whole_job_gcups(wl.cells, K, world, ms),
+            "unit": UNIT, "ms_per_step": ms / K, "slip_l1": diag["slip_l1"]}
 
 
 def max_over_ranks(ms: float, device, world: int) -> float:
@@ -526,6 +565,7 @@ def main():
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the built-in launch shapes (no autotuning before timing)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-instances leg")
+    ap.add_argument("--no-ab", action="store_true", help="skip the AB+CN leg")
     ap.add_argument("--e5-steps", type=int, default=0,
                     help="also record the no-slip error series of the heaving/pitching plate (opt-in)")
     ap.add_argument("--tune", default="", help="fixed launch shapes instead of autotuning, e.g. tri_y=3,sweep_zy=2")

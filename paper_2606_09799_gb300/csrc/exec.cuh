@@ -34,8 +34,19 @@ __device__ __forceinline__ Blk blk_builtin() {
   return Blk{blockIdx.x, blockIdx.y, blockIdx.z, gridDim.x, gridDim.y, gridDim.z};
 }
 
+// Programmatic dependent launch: every op kernel is launched with the
+// programmatic-serialization attribute, so it may be scheduled while its
+// predecessor in the stream drains.  It first waits until that predecessor
+// has completed and its writes are visible (griddepcontrol.wait), then lets
+// its own successor be scheduled.  No op touches memory before the wait.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
 template <class Op>
 __global__ void __launch_bounds__(Op::kThreads) k_run(const __grid_constant__ Op op) {
+  pdl_enter();
   op(blk_builtin());
 }
 
@@ -48,6 +59,7 @@ struct GroupEntry {
 template <class Op>
 __global__ void __launch_bounds__(Op::kThreads) k_run_group(const Op* __restrict__ ops,
                                                             const GroupEntry* __restrict__ ge, int n) {
+  pdl_enter();
   const unsigned b = blockIdx.x;
   int lo = 0, hi = n - 1;   // last instance whose start <= b (empty instances are skipped)
   while (lo < hi) {
@@ -80,10 +92,27 @@ struct LaunchRec {
   int mark;            // stage that starts with this launch, or -1
 };
 
+// Launch configuration with the programmatic-serialization attribute.
+struct PdlConfig {
+  cudaLaunchConfig_t cfg{};
+  cudaLaunchAttribute attr[1];
+  PdlConfig(dim3 grid, dim3 block, size_t smem, cudaStream_t st) {
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+  }
+};
+
 template <class Op>
 void group_launch(const void* ops, const GroupEntry* ge, int n, unsigned blocks, dim3 block, size_t smem,
                   cudaStream_t st) {
-  k_run_group<Op><<<blocks, block, smem, st>>>(static_cast<const Op*>(ops), ge, n);
+  PdlConfig pc(dim3(blocks), block, smem, st);
+  cudaLaunchKernelEx(&pc.cfg, k_run_group<Op>, static_cast<const Op*>(ops), ge, n);
 }
 
 // Raise the dynamic shared-memory limit of both launch forms of an op on the
@@ -125,6 +154,7 @@ struct Tune {
   int fft_cols;   // kx columns per block of the z transforms (power of two)
   int sweep_zy;   // z and y sweeps (FP32): 1 shared-memory tile, one thread per line; 2 several lanes per line
   int fft_plane;  // 1 separate x and z transform kernels; 2 fused per y-plane (when the plane fits)
+  int sweep_y;    // y sweep: 0 as sweep_zy; 1 one thread per line streamed through registers
 };
 
 struct Exec {
@@ -145,8 +175,9 @@ struct Exec {
   void launch(dim3 grid, dim3 block, size_t smem, const Op& op) {
     if (!rec) {
       if ((unsigned long long)grid.x * grid.y * grid.z == 0) return;
-      k_run<Op><<<grid, block, smem, st>>>(op);
-      const cudaError_t e = cudaPeekAtLastError();
+      PdlConfig pc(grid, block, smem, st);
+      cudaError_t e = cudaLaunchKernelEx(&pc.cfg, k_run<Op>, op);
+      if (e == cudaSuccess) e = cudaPeekAtLastError();
       if (e != cudaSuccess && first_err == cudaSuccess) {
         first_err = e;
         first_op = op_name<Op>();

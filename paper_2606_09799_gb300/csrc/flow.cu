@@ -1103,6 +1103,147 @@ struct SweepZY {
   __device__ __forceinline__ void operator()(const Blk& bk) const { sweep_zy<T>(bk, g, f, flags32, tb, lfirst, dir); }
 };
 
+// y-sweep streamed through registers, one thread per line (component bk.y,
+// line t = i + nx k, so a warp reads each row of 32 neighbouring lines as
+// one coalesced segment).  Rows are read SYB at a time, ahead of the
+// recurrence; the forward values overwrite R (the line stays in L2 between
+// the passes) and the backward pass adds du to the state on its way out.
+// Same recurrences, tables and operation order as solve_wall; the forcing
+// rows of a line are kept as a bitmask for the segment positions of the
+// backward pass (lines of up to SYMAX rows).
+constexpr int SYB = 16, SYMAX = 256;
+
+template <typename T>
+__device__ __forceinline__ void sweep_y_stream(const Blk& bk, const Geo& g, const Fields<T>& f,
+                                               const unsigned* __restrict__ flags32, const SweepTables<T>& tb,
+                                               const int* __restrict__ lfirst) {
+  const int c = bk.y;
+  const long long t = (long long)bk.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)g.nx * g.nz) return;
+  const int i = (int)(t % g.nx), k = (int)(t / g.nx);
+  const int jj0 = c == 1 ? 1 : 0;
+  const int n = c == 1 ? g.ny - 1 : g.ny;
+  const long long base = fidx(g, c, i, jj0, k), stride = g.nx;
+  const long long fbase = cidx(g, i, jj0, k);   // flag byte of row m at fbase + m nx
+  const unsigned char* __restrict__ fb = reinterpret_cast<const unsigned char*>(flags32);
+  T* __restrict__ R = f.R[c];
+  T* __restrict__ Uc = comp_ptr(f, c);
+  T* __restrict__ Lc = f.lo[c];
+  const T a = -tb.off[1];
+  const bool tang = c != 1;
+  const bool any = lfirst[line_y(g, c, i, k)] < g.ny;
+  unsigned fm[SYMAX / 32];   // forcing rows of an `any` line
+#pragma unroll
+  for (int w = 0; w < SYMAX / 32; ++w) fm[w] = 0u;
+  auto forcing = [&](int r) { return (fm[r >> 5] >> (r & 31)) & 1u; };
+  const T* __restrict__ inv0 = tang ? tb.yinvW : tb.vinvR;
+  const T* __restrict__ cp0 = tang ? tb.ycpW : tb.vcpR;
+  // ---- forward
+  T prev = (T)0;
+  int m = 0;
+  bool segW = tang;
+  for (int j0 = 0; j0 < n; j0 += SYB) {
+    T e[SYB];
+    unsigned char fl[SYB];
+#pragma unroll
+    for (int u = 0; u < SYB; ++u) {
+      const int j = j0 + u;
+      e[u] = (T)0;
+      fl[u] = 0;
+      if (j < n) {
+        e[u] = R[base + (long long)j * stride];
+        if (any) fl[u] = fb[fbase + (long long)j * stride];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < SYB; ++u) {
+      const int j = j0 + u;
+      if (j >= n) break;
+      if (!any) {
+        const T iv = (j == n - 1) ? (tang ? __ldg(tb.yinvLW + n - 1) : __ldg(inv0 + n - 1)) : __ldg(inv0 + j);
+        prev = (e[u] - a * prev) * iv;
+      } else if ((fl[u] >> c) & 1) {
+        prev = e[u];
+        m = 0;
+        segW = false;
+        fm[j >> 5] |= 1u << (j & 31);
+        continue;
+      } else {
+        T iv;
+        if (!tang) iv = __ldg(tb.vinvR + m);
+        else if (j == n - 1) iv = segW ? __ldg(tb.yinvLW + m) : __ldg(tb.yinvLR + m);
+        else iv = segW ? __ldg(tb.yinvW + m) : __ldg(tb.yinvR + m);
+        prev = (e[u] - a * prev) * iv;
+        ++m;
+      }
+      R[base + (long long)j * stride] = prev;
+    }
+  }
+  // ---- backward, with u^s + du written out
+  auto seg_of = [&](int q, int& mpos, bool& w) {
+    int lo = q - 1;
+    while (lo >= 0 && !forcing(lo)) --lo;
+    mpos = q - lo - 1;
+    w = tang && lo < 0;
+  };
+  T x = prev;
+  int mq = -1;
+  bool qW = false;
+  if (any && !forcing(n - 1)) seg_of(n - 1, mq, qW);
+  for (int j1 = n - 1; j1 >= 0; j1 -= SYB) {
+    T pv[SYB], uh[SYB], ul[SYB];
+#pragma unroll
+    for (int u = 0; u < SYB; ++u) {
+      const int j = j1 - u;
+      pv[u] = uh[u] = ul[u] = (T)0;
+      if (j >= 0) {
+        const long long id = base + (long long)j * stride;
+        pv[u] = R[id];
+        uh[u] = Uc[id];
+        if (Lc) ul[u] = Lc[id];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < SYB; ++u) {
+      const int j = j1 - u;
+      if (j < 0) break;
+      if (j == n - 1) {
+        x = pv[u];
+      } else if (!any) {
+        x = pv[u] - __ldg(cp0 + j) * x;
+      } else if (forcing(j)) {
+        x = pv[u];
+        mq = -1;
+      } else {
+        if (mq < 0) seg_of(j, mq, qW);
+        else --mq;
+        const T cpj = !tang ? __ldg(tb.vcpR + mq) : (qW ? __ldg(tb.ycpW + mq) : __ldg(tb.ycpR + mq));
+        x = pv[u] - cpj * x;
+      }
+      const long long id = base + (long long)j * stride;
+      if (Lc) {
+        // velocity state as a (hi, lo) pair: add du without rounding it away
+        float hi = (float)uh[u], lo = (float)ul[u];
+        ff_add(hi, lo, (float)x);
+        Uc[id] = (T)hi;
+        Lc[id] = (T)lo;
+      } else {
+        Uc[id] = uh[u] + x;
+      }
+    }
+  }
+}
+template <typename T>
+struct SweepYStream {
+  static constexpr int kThreads = 128;
+  Geo g;
+  Fields<T> f;
+  const unsigned* flags32;
+  SweepTables<T> tb;
+  const int* lfirst;
+  __device__ __forceinline__ void operator()(const Blk& bk) const { sweep_y_stream<T>(bk, g, f, flags32, tb, lfirst); }
+};
+
 template <typename T>
 static size_t sweep_smem(int W, int n, int ld, int tiles = 1) {
   return (size_t)tiles * W * ld * sizeof(T) + (size_t)W * n;
@@ -1177,7 +1318,10 @@ void launch_sweeps(const Geo& g, const Fields<T>& f, const TagBuffers& b, const 
               SweepZY<T>{g, f, b.flags32, tb, b.lines.z, 2});
   }
   ex.mark(ST_SWEEP_Y);
-  if (!(lanes && sweep_lanes_launch(g, f, b, tb, ex, sh.ny, 1, g.nz))) {
+  if (ex.tune.sweep_y == 1 && sh.ny <= SYMAX) {
+    const long long lines = (long long)g.nx * g.nz;
+    ex.launch(dim3((unsigned)((lines + 127) / 128), 3), dim3(128), 0, SweepYStream<T>{g, f, b.flags32, tb, b.lines.y});
+  } else if (!(lanes && sweep_lanes_launch(g, f, b, tb, ex, sh.ny, 1, g.nz))) {
     const int tiles = f.lo[0] ? 3 : 2;
     int W = sweep_width<T>(sh.ny, tiles);
     if (ex.tune.sweep_w > 0 && ex.tune.sweep_w < W) W = ex.tune.sweep_w;

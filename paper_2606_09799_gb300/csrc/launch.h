@@ -139,12 +139,15 @@ void launch_slip(const Geo& g, const Surf& s, const Fields<T>& f, const TagBuffe
                  DevState* ds, Exec& ex);
 
 // ---- Poisson and projection (poisson.cu) -----------------------------------
+constexpr int TRI_SEG = 16;   // rows of j per lane of the warp-cooperative wall-normal Thomas
 template <typename T>
 struct SpecTables {
   const T* twx;          // exp(-2 pi i m / nx), m < nx, complex interleaved
   const T* twz;          // exp(-2 pi i m / nz)
   const double* cp;      // Thomas c' per (kz, j, kx)
   const double* inv;     // Thomas 1/pivot per (kz, j, kx)
+  const double* segf;    // products of the forward multipliers per (kz, segment of TRI_SEG rows, kx)
+  const double* segb;    // ... and of the backward multipliers
 };
 template <typename T>
 void launch_poisson(const Geo& g, const Fields<T>& f, const TagBuffers& b, const SpecTables<T>& tb,
@@ -158,6 +161,7 @@ void launch_pressure_recon(const Geo& g, const Surf& s, const Fields<T>& f, cons
                            double* q, cudaStream_t st);
 
 void launch_build_poisson_tables(const Geo& g, const double* lamx, const double* lamz, double* cp, double* inv,
+                                 double* segf, double* segb,
                                  cudaStream_t st);
 
 }  // namespace ibm

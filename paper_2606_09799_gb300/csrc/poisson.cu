@@ -88,17 +88,80 @@ static FftPlan make_plan(int n) {
   return p;
 }
 
-// One Stockham pass over `lines` transforms of length n; element e of line
-// l sits at l * ls + e * es (src and dst alike).  tw[m] = exp(-2 pi i m/n).
-// Threads take butterflies (line, j) with the line index fastest when
-// es > 1 (column tiles: neighbouring lines are neighbouring words) and j
-// fastest otherwise.
-template <typename T, bool INV>
-__device__ void fft_pass(const typename Cplx<T>::type* src, typename Cplx<T>::type* dst, int lines, int n,
-                         const FftStage& S, const typename Cplx<T>::type* __restrict__ tw, int es, int ls,
-                         unsigned mlines) {
+// Radix-R butterfly on v (inputs already twiddled), in place.
+template <typename T, bool INV, int R>
+__device__ __forceinline__ void butterfly(typename Cplx<T>::type (&v)[R]) {
   using C = typename Cplx<T>::type;
-  const int R = S.R, Ns = S.Ns, nb = S.nb;
+  if constexpr (R == 2) {
+    const C a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+  } else if constexpr (R == 4) {
+    const C s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+    const C s13 = cadd(v[1], v[3]), d13 = csub(v[1], v[3]);
+    C jd13;  // -i d13 (forward) or +i d13 (inverse)
+    if (INV) { jd13.x = -d13.y; jd13.y = d13.x; }
+    else { jd13.x = d13.y; jd13.y = -d13.x; }
+    v[0] = cadd(s02, s13);
+    v[2] = csub(s02, s13);
+    v[1] = cadd(d02, jd13);
+    v[3] = csub(d02, jd13);
+  } else if constexpr (R == 5) {
+    // X_k = sum_r v_r w^{rk}, w = exp(-+ 2 pi i / 5): pair the inputs
+    // symmetric about r = 0 (t1 = v1 + v4, t2 = v2 + v3, t3 = v1 - v4,
+    // t4 = v2 - v3); the cosines and sines of 2 pi / 5 and 4 pi / 5 from
+    // sqrt(5): cos = (sqrt5 - 1)/4, -(sqrt5 + 1)/4; sin = sqrt(10 +- 2 sqrt5)/4
+    const T c1 = (T)0.30901699437494742410, c2 = (T)-0.80901699437494742410;
+    const T s1 = (T)0.95105651629515357212, s2 = (T)0.58778525229247312917;
+    const C t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]), t3 = csub(v[1], v[4]), t4 = csub(v[2], v[3]);
+    C a1, a2, b1, b2;
+    a1.x = v[0].x + c1 * t1.x + c2 * t2.x;
+    a1.y = v[0].y + c1 * t1.y + c2 * t2.y;
+    a2.x = v[0].x + c2 * t1.x + c1 * t2.x;
+    a2.y = v[0].y + c2 * t1.y + c1 * t2.y;
+    b1.x = s1 * t3.x + s2 * t4.x;
+    b1.y = s1 * t3.y + s2 * t4.y;
+    b2.x = s2 * t3.x - s1 * t4.x;
+    b2.y = s2 * t3.y - s1 * t4.y;
+    // forward: X1 = a1 - i b1, X4 = a1 + i b1, X2 = a2 - i b2, X3 = a2 + i b2
+    C ib1, ib2;   // -i b (forward) or +i b (inverse)
+    if (INV) { ib1.x = -b1.y; ib1.y = b1.x; ib2.x = -b2.y; ib2.y = b2.x; }
+    else { ib1.x = b1.y; ib1.y = -b1.x; ib2.x = b2.y; ib2.y = -b2.x; }
+    v[0] = cadd(v[0], cadd(t1, t2));
+    v[1] = cadd(a1, ib1);
+    v[4] = csub(a1, ib1);
+    v[2] = cadd(a2, ib2);
+    v[3] = csub(a2, ib2);
+  } else {  // R == 3
+    const T h = (T)0.86602540378443864676;  // sin(2 pi / 3)
+    const C a = v[0], b = v[1], c = v[2];
+    const C sbc = cadd(b, c), dbc = csub(b, c);
+    C m;
+    m.x = a.x - (T)0.5 * sbc.x;
+    m.y = a.y - (T)0.5 * sbc.y;
+    C rot;  // -i h (b - c) forward, +i h (b - c) inverse
+    if (INV) { rot.x = -h * dbc.y; rot.y = h * dbc.x; }
+    else { rot.x = h * dbc.y; rot.y = -h * dbc.x; }
+    v[0] = cadd(a, sbc);
+    v[1] = cadd(m, rot);
+    v[2] = csub(m, rot);
+  }
+}
+
+// One Stockham pass of radix R over `lines` transforms of length n; element
+// e of line l sits at l * ls + e * es (src and dst alike).
+// tw[m] = exp(-2 pi i m/n).  Threads take butterflies (line, j) with the
+// line index fastest when es > 1 (column tiles: neighbouring lines are
+// neighbouring words) and j fastest otherwise.  R is a template parameter
+// so the butterfly's values stay in registers.
+template <typename T, bool INV, int R>
+__device__ __forceinline__ void fft_pass_r(const typename Cplx<T>::type* src, typename Cplx<T>::type* dst,
+                                           int lines, const FftStage& S,
+                                           const typename Cplx<T>::type* __restrict__ tw, int es, int ls,
+                                           unsigned mlines) {
+  using C = typename Cplx<T>::type;
+  const int Ns = S.Ns, nb = S.nb, scale = S.scale;
+  const unsigned mNs = S.mNs, mnb = S.mnb;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x, nth = blockDim.x * blockDim.y;
   const int total = lines * nb;
   for (int t = tid; t < total; t += nth) {
@@ -107,79 +170,41 @@ __device__ void fft_pass(const typename Cplx<T>::type* src, typename Cplx<T>::ty
       j = (int)fdiv((unsigned)t, mlines);
       line = t - j * lines;
     } else {
-      line = (int)fdiv((unsigned)t, S.mnb);
+      line = (int)fdiv((unsigned)t, mnb);
       j = t - line * nb;
     }
     const C* sp = src + line * ls;
     C* dp = dst + line * ls;
-    const int jn = (int)fdiv((unsigned)j, S.mNs);
+    const int jn = (int)fdiv((unsigned)j, mNs);
     const int k = j - jn * Ns;
-    C v[5];
-    for (int r = 0; r < R; ++r) {
-      C x = sp[(j + r * nb) * es];
-      if (r > 0 && k > 0) {
-        C w = __ldg(tw + (r * k * S.scale));
+    C v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = sp[(j + r * nb) * es];
+    if (k > 0) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        C w = __ldg(tw + (r * k * scale));
         if (INV) w = cconj(w);
-        x = cmul(x, w);
+        v[r] = cmul(v[r], w);
       }
-      v[r] = x;
     }
-    if (R == 2) {
-      const C a = v[0], b = v[1];
-      v[0] = cadd(a, b);
-      v[1] = csub(a, b);
-    } else if (R == 4) {
-      const C s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
-      const C s13 = cadd(v[1], v[3]), d13 = csub(v[1], v[3]);
-      C jd13;  // -i d13 (forward) or +i d13 (inverse)
-      if (INV) { jd13.x = -d13.y; jd13.y = d13.x; }
-      else { jd13.x = d13.y; jd13.y = -d13.x; }
-      v[0] = cadd(s02, s13);
-      v[2] = csub(s02, s13);
-      v[1] = cadd(d02, jd13);
-      v[3] = csub(d02, jd13);
-    } else if (R == 5) {
-      // X_k = sum_r v_r w^{rk}, w = exp(-+ 2 pi i / 5): pair the inputs
-      // symmetric about r = 0 (t1 = v1 + v4, t2 = v2 + v3, t3 = v1 - v4,
-      // t4 = v2 - v3); the cosines and sines of 2 pi / 5 and 4 pi / 5 from
-      // sqrt(5): cos = (sqrt5 - 1)/4, -(sqrt5 + 1)/4; sin = sqrt(10 +- 2 sqrt5)/4
-      const T c1 = (T)0.30901699437494742410, c2 = (T)-0.80901699437494742410;
-      const T s1 = (T)0.95105651629515357212, s2 = (T)0.58778525229247312917;
-      const C t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]), t3 = csub(v[1], v[4]), t4 = csub(v[2], v[3]);
-      C a1, a2, b1, b2;
-      a1.x = v[0].x + c1 * t1.x + c2 * t2.x;
-      a1.y = v[0].y + c1 * t1.y + c2 * t2.y;
-      a2.x = v[0].x + c2 * t1.x + c1 * t2.x;
-      a2.y = v[0].y + c2 * t1.y + c1 * t2.y;
-      b1.x = s1 * t3.x + s2 * t4.x;
-      b1.y = s1 * t3.y + s2 * t4.y;
-      b2.x = s2 * t3.x - s1 * t4.x;
-      b2.y = s2 * t3.y - s1 * t4.y;
-      // forward: X1 = a1 - i b1, X4 = a1 + i b1, X2 = a2 - i b2, X3 = a2 + i b2
-      C ib1, ib2;   // -i b (forward) or +i b (inverse)
-      if (INV) { ib1.x = -b1.y; ib1.y = b1.x; ib2.x = -b2.y; ib2.y = b2.x; }
-      else { ib1.x = b1.y; ib1.y = -b1.x; ib2.x = b2.y; ib2.y = -b2.x; }
-      v[0] = cadd(v[0], cadd(t1, t2));
-      v[1] = cadd(a1, ib1);
-      v[4] = csub(a1, ib1);
-      v[2] = cadd(a2, ib2);
-      v[3] = csub(a2, ib2);
-    } else {  // R == 3
-      const T h = (T)0.86602540378443864676;  // sin(2 pi / 3)
-      const C a = v[0], b = v[1], c = v[2];
-      const C sbc = cadd(b, c), dbc = csub(b, c);
-      C m;
-      m.x = a.x - (T)0.5 * sbc.x;
-      m.y = a.y - (T)0.5 * sbc.y;
-      C rot;  // -i h (b - c) forward, +i h (b - c) inverse
-      if (INV) { rot.x = -h * dbc.y; rot.y = h * dbc.x; }
-      else { rot.x = h * dbc.y; rot.y = -h * dbc.x; }
-      v[0] = cadd(a, sbc);
-      v[1] = cadd(m, rot);
-      v[2] = csub(m, rot);
-    }
+    butterfly<T, INV, R>(v);
     const int dbase = jn * Ns * R + k;
+#pragma unroll
     for (int r = 0; r < R; ++r) dp[(dbase + r * Ns) * es] = v[r];
+  }
+}
+
+template <typename T, bool INV>
+__device__ __forceinline__ void fft_pass(const typename Cplx<T>::type* src, typename Cplx<T>::type* dst,
+                                         int lines, const FftStage& S,
+                                         const typename Cplx<T>::type* __restrict__ tw, int es, int ls,
+                                         unsigned mlines) {
+  switch (S.R) {
+    case 4: fft_pass_r<T, INV, 4>(src, dst, lines, S, tw, es, ls, mlines); break;
+    case 2: fft_pass_r<T, INV, 2>(src, dst, lines, S, tw, es, ls, mlines); break;
+    case 3: fft_pass_r<T, INV, 3>(src, dst, lines, S, tw, es, ls, mlines); break;
+    default: fft_pass_r<T, INV, 5>(src, dst, lines, S, tw, es, ls, mlines); break;
   }
 }
 
@@ -192,8 +217,8 @@ __device__ int fft_lines(typename Cplx<T>::type* a, typename Cplx<T>::type* b, i
   int cur = 0;
   for (int s = 0; s < p.nst; ++s) {
     __syncthreads();
-    if (cur == 0) fft_pass<T, INV>(a, b, lines, p.n, p.st[s], tw, es, ls, mlines);
-    else fft_pass<T, INV>(b, a, lines, p.n, p.st[s], tw, es, ls, mlines);
+    if (cur == 0) fft_pass<T, INV>(a, b, lines, p.st[s], tw, es, ls, mlines);
+    else fft_pass<T, INV>(b, a, lines, p.st[s], tw, es, ls, mlines);
     cur ^= 1;
   }
   __syncthreads();
@@ -877,23 +902,28 @@ struct TriY {
 };
 
 // Warp-cooperative variant: a warp holds G = 32/L consecutive kx of one kz,
-// L lanes per system, each lane Rr consecutive rows of j in registers (so a
-// warp load touches whole 32-byte sectors of G adjacent wavenumbers).  Both
-// Thomas passes are affine recurrences with real multipliers,
-//   forward  p_j = a_j p_{j-1} + b_j,  a_j = -(1/dy^2) inv_j, b_j = r_j inv_j
-//   backward x_j = -cp_j x_{j+1} + p_j,
+// L lanes per system, each lane TRI_SEG consecutive rows of j in registers
+// (so a warp load touches whole 32-byte sectors of G adjacent wavenumbers).
+// Both Thomas passes are affine recurrences with real multipliers,
+//   forward  p_j = -c'_j p_{j-1} + r_j / piv_j   (c'_j = a / piv_j, a = 1/dy^2)
+//   backward x_j = -c'_j x_{j+1} + p_j,
 // composed per lane, then across the L lanes of a system by a segmented
-// shuffle scan, in FP64.  A lane issues the loads of all its rows (right-
-// hand side, 1/pivot, c') before the first use, so the kernel waits for
-// memory once; no forward values leave the registers.
-template <typename T, int L, int Rr>
+// shuffle scan, in FP64.  The multiplier products of each lane's rows depend
+// on the wavenumber only and are tabulated (segf, segb), so a row costs one
+// FMA per part and pass in the compositions and one in each recurrence.  A
+// lane issues the loads of all its rows before the first use; no forward
+// values leave the registers.
+template <typename T, int L>
 __device__ __forceinline__ void tri_y_warp(const Blk& bk, const Geo& g, const Fields<T>& f, const double* __restrict__ cp,
-                                                    const double* __restrict__ inv) {
+                                           const double* __restrict__ inv, const double* __restrict__ segf,
+                                           const double* __restrict__ segb) {
   using C = typename Cplx<T>::type;
+  constexpr int Rr = TRI_SEG;
   constexpr int G = 32 / L;
   const int lane = threadIdx.x & 31;
   const int sl = lane % L;                      // lane inside its system
   const int nkx = g.nkx, ny = g.ny;
+  const int nseg = (ny + Rr - 1) / Rr;
   const int groups_x = (nkx + G - 1) / G;
   const long long wid = ((long long)bk.x * blockDim.x + threadIdx.x) >> 5;
   if (wid >= (long long)groups_x * g.nz) return;     // whole warps only
@@ -903,39 +933,41 @@ __device__ __forceinline__ void tri_y_warp(const Blk& bk, const Geo& g, const Fi
   const long long base = (long long)kz * ny * nkx + (live ? kx : 0);
   const long long stride = nkx;
   C* spec = reinterpret_cast<C*>(f.spec);
-  const double a = g.idy * g.idy;
   const bool singular = live && kx == 0 && kz == 0;
+  const bool gauge = kz == 0 && (int)(wid % groups_x) == 0;   // warp of the (0,0) system
   const int j0 = sl * Rr;
+  const bool rows = live && j0 < ny;            // the lane holds at least one row
   const unsigned FULL = 0xFFFFFFFFu;
-  // ---- every load of the lane's rows, issued together
-  double zr[Rr], zi[Rr], iv[Rr], cq[Rr];
+  // ---- every load of the lane's rows, issued together; br = r / piv
+  double br[Rr], bi[Rr], cq[Rr];
 #pragma unroll
   for (int u = 0; u < Rr; ++u) {
     const int j = j0 + u;
-    zr[u] = zi[u] = 0.0;
-    iv[u] = 1.0;
-    cq[u] = 0.0;
+    br[u] = bi[u] = cq[u] = 0.0;
     if (live && j < ny) {
       const long long id = base + (long long)j * stride;
       const C z = spec[id];
-      zr[u] = (double)z.x;
-      zi[u] = (double)z.y;
-      iv[u] = __ldg(inv + id);
+      const double iv = __ldg(inv + id);
       cq[u] = __ldg(cp + id);
+      br[u] = (double)z.x * iv;
+      bi[u] = (double)z.y * iv;
     }
   }
+  if (singular && j0 == 0) br[0] = bi[0] = 0.0;   // pinned phi_0 of the (0,0) mode
+  const long long sid = ((long long)kz * nseg + sl) * nkx + (live ? kx : 0);
   // ---- forward: compose the lane's maps
-  double A = 1.0, Br = 0.0, Bi = 0.0;
+  double A = rows ? __ldg(segf + sid) : 1.0, Br = 0.0, Bi = 0.0;
 #pragma unroll
   for (int u = 0; u < Rr; ++u) {
     const int j = j0 + u;
     if (!live || j >= ny) continue;
-    const double al = (j == 0) ? 0.0 : -a * iv[u];
-    const double br = (j == 0 && singular) ? 0.0 : zr[u] * iv[u];
-    const double bi = (j == 0 && singular) ? 0.0 : zi[u] * iv[u];
-    A = al * A;
-    Br = fma(al, Br, br);
-    Bi = fma(al, Bi, bi);
+    if (j == 0) {
+      Br = br[u];
+      Bi = bi[u];
+    } else {
+      Br = fma(-cq[u], Br, br[u]);
+      Bi = fma(-cq[u], Bi, bi[u]);
+    }
   }
   for (int o = 1; o < L; o <<= 1) {
     const double pa = __shfl_up_sync(FULL, A, o, L), pr = __shfl_up_sync(FULL, Br, o, L),
@@ -948,35 +980,36 @@ __device__ __forceinline__ void tri_y_warp(const Blk& bk, const Geo& g, const Fi
   }
   double pr = __shfl_up_sync(FULL, Br, 1, L), pi = __shfl_up_sync(FULL, Bi, 1, L);
   if (sl == 0) { pr = 0.0; pi = 0.0; }
-  double vr[Rr], vi[Rr];
+  // forward values p_j, in place of br
 #pragma unroll
   for (int u = 0; u < Rr; ++u) {
     const int j = j0 + u;
-    vr[u] = 0.0;
-    vi[u] = 0.0;
     if (!live || j >= ny) continue;
     if (j == 0) {
-      pr = singular ? 0.0 : zr[u] * iv[u];
-      pi = singular ? 0.0 : zi[u] * iv[u];
+      pr = br[u];
+      pi = bi[u];
     } else {
-      pr = (zr[u] - a * pr) * iv[u];
-      pi = (zi[u] - a * pi) * iv[u];
+      pr = fma(-cq[u], pr, br[u]);
+      pi = fma(-cq[u], pi, bi[u]);
     }
-    vr[u] = pr;
-    vi[u] = pi;
+    br[u] = pr;
+    bi[u] = pi;
   }
   // ---- backward: compose from the top row of the lane down
-  A = 1.0;
+  A = rows ? __ldg(segb + sid) : 1.0;
   Br = 0.0;
   Bi = 0.0;
 #pragma unroll
   for (int u = Rr - 1; u >= 0; --u) {
     const int j = j0 + u;
     if (!live || j >= ny) continue;
-    const double al = (j == ny - 1) ? 0.0 : -cq[u];
-    A = al * A;
-    Br = fma(al, Br, vr[u]);
-    Bi = fma(al, Bi, vi[u]);
+    if (j == ny - 1) {
+      Br = br[u];
+      Bi = bi[u];
+    } else {
+      Br = fma(-cq[u], Br, br[u]);
+      Bi = fma(-cq[u], Bi, bi[u]);
+    }
   }
   for (int o = 1; o < L; o <<= 1) {
     const double na = __shfl_down_sync(FULL, A, o, L), nr = __shfl_down_sync(FULL, Br, o, L),
@@ -995,18 +1028,20 @@ __device__ __forceinline__ void tri_y_warp(const Blk& bk, const Geo& g, const Fi
     const int j = j0 + u;
     if (!live || j >= ny) continue;
     if (j == ny - 1) {
-      xr = vr[u];
-      xi = vi[u];
+      xr = br[u];
+      xi = bi[u];
     } else {
-      xr = vr[u] - cq[u] * xr;
-      xi = vi[u] - cq[u] * xi;
+      xr = fma(-cq[u], xr, br[u]);
+      xi = fma(-cq[u], xi, bi[u]);
     }
-    vr[u] = xr;
-    vi[u] = xi;
-    sr += xr;
-    si += xi;
+    br[u] = xr;
+    bi[u] = xi;
+    if (gauge) {
+      sr += xr;
+      si += xi;
+    }
   }
-  if (kz == 0 && (int)(wid % groups_x) == 0) {
+  if (gauge) {
     // the (0,0) system lives in the first group of kz = 0: zero-mean gauge
     for (int o = 1; o < L; o <<= 1) {
       sr += __shfl_xor_sync(FULL, sr, o, L);
@@ -1016,8 +1051,8 @@ __device__ __forceinline__ void tri_y_warp(const Blk& bk, const Geo& g, const Fi
       const double mr = sr / ny, mi = si / ny;
 #pragma unroll
       for (int u = 0; u < Rr; ++u) {
-        vr[u] -= mr;
-        vi[u] -= mi;
+        br[u] -= mr;
+        bi[u] -= mi;
       }
     }
   }
@@ -1026,19 +1061,21 @@ __device__ __forceinline__ void tri_y_warp(const Blk& bk, const Geo& g, const Fi
     const int j = j0 + u;
     if (!live || j >= ny) continue;
     C o;
-    o.x = (T)vr[u];
-    o.y = (T)vi[u];
+    o.x = (T)br[u];
+    o.y = (T)bi[u];
     spec[base + (long long)j * stride] = o;
   }
 }
-template <typename T, int L, int Rr>
+template <typename T, int L>
 struct TriYWarp {
   static constexpr int kThreads = 128;
   Geo g;
   Fields<T> f;
   const double* cp;
   const double* inv;
-  __device__ __forceinline__ void operator()(const Blk& bk) const { tri_y_warp<T, L, Rr>(bk, g, f, cp, inv); }
+  const double* segf;
+  const double* segb;
+  __device__ __forceinline__ void operator()(const Blk& bk) const { tri_y_warp<T, L>(bk, g, f, cp, inv, segf, segb); }
 };
 
 // Sequential Thomas per (kx, kz, part) with the forward values in shared
@@ -1120,7 +1157,7 @@ struct TriYSmem {
 
 // Tabulate the pivots of every (kx, kz) system once per grid.
 __global__ void k_build_tri_tables(Geo g, const double* __restrict__ lamx, const double* __restrict__ lamz,
-                                   double* cp, double* inv) {
+                                   double* cp, double* inv, double* segf, double* segb) {
   const int nkx = g.nkx;
   const long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (l >= (long long)nkx * g.nz) return;
@@ -1140,14 +1177,38 @@ __global__ void k_build_tri_tables(Geo g, const double* __restrict__ lamx, const
     const double iv = 1.0 / den;
     cprev = cm * iv;
     inv[base + (long long)j * stride] = iv;
-    cp[base + (long long)j * stride] = cprev;
+    // the last row has no super-diagonal; its entry holds a / pivot, the
+    // multiplier of its forward step (no backward step reads it)
+    cp[base + (long long)j * stride] = j == g.ny - 1 ? a * iv : cprev;
+  }
+  // products of the forward (-c'_j, j > 0) and backward (-c'_j, j < ny - 1)
+  // multipliers over each segment of TRI_SEG rows, in the order in which the
+  // warp-cooperative solve composes them
+  const int nseg = (g.ny + TRI_SEG - 1) / TRI_SEG;
+  for (int sg = 0; sg < nseg; ++sg) {
+    double af = 1.0, ab = 1.0;
+    for (int u = 0; u < TRI_SEG; ++u) {
+      const int j = sg * TRI_SEG + u;
+      if (j >= g.ny) break;
+      const double al = j == 0 ? 0.0 : -cp[base + (long long)j * stride];
+      af = al * af;
+    }
+    for (int u = TRI_SEG - 1; u >= 0; --u) {
+      const int j = sg * TRI_SEG + u;
+      if (j >= g.ny) continue;
+      const double al = j == g.ny - 1 ? 0.0 : -cp[base + (long long)j * stride];
+      ab = al * ab;
+    }
+    const long long sid = ((long long)kz * nseg + sg) * nkx + kx;
+    segf[sid] = af;
+    segb[sid] = ab;
   }
 }
 
 void launch_build_poisson_tables(const Geo& g, const double* lamx, const double* lamz, double* cp, double* inv,
-                                 cudaStream_t st) {
+                                 double* segf, double* segb, cudaStream_t st) {
   const long long lines = (long long)g.nkx * g.nz;
-  k_build_tri_tables<<<(unsigned)((lines + 127) / 128), 128, 0, st>>>(g, lamx, lamz, cp, inv);
+  k_build_tri_tables<<<(unsigned)((lines + 127) / 128), 128, 0, st>>>(g, lamx, lamz, cp, inv, segf, segb);
 }
 
 // ---------------------------------------------------------------------------
@@ -1281,10 +1342,10 @@ void launch_poisson(const Geo& g, const Fields<T>& f, const TagBuffers& b, const
                 TriYSmem<T>{g, f, tb.cp, tb.inv});
     } else if (tri == 1 && sh.ny <= 8 * 16) {
       const long long warps = (long long)((g.nkx + 3) / 4) * g.nz;
-      ex.launch(dim3((unsigned)((warps * 32 + 127) / 128)), dim3(128), 0, TriYWarp<T, 8, 16>{g, f, tb.cp, tb.inv});
+      ex.launch(dim3((unsigned)((warps * 32 + 127) / 128)), dim3(128), 0, TriYWarp<T, 8>{g, f, tb.cp, tb.inv, tb.segf, tb.segb});
     } else if (tri == 1) {
       const long long warps = (long long)g.nkx * g.nz;
-      ex.launch(dim3((unsigned)((warps * 32 + 127) / 128)), dim3(128), 0, TriYWarp<T, 32, 16>{g, f, tb.cp, tb.inv});
+      ex.launch(dim3((unsigned)((warps * 32 + 127) / 128)), dim3(128), 0, TriYWarp<T, 32>{g, f, tb.cp, tb.inv, tb.segf, tb.segb});
     } else {
       ex.launch(dim3((unsigned)((2 * tlines + 127) / 128)), dim3(128), 0, TriY<T>{g, f, tb.cp, tb.inv, fwd});
     }

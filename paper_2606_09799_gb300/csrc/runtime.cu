@@ -175,7 +175,7 @@ struct ibm_grid {
   void* qk;                  // q_F per cell (energy-conserving shape)
   // tables
   void* sweep_mem[24];
-  double* pcp; double* pinv; double* lamx; double* lamz;
+  double* pcp; double* pinv; double* psegf; double* psegb; double* lamx; double* lamz;
   void* twx; void* twz;
   double tbl_off[3];
   double tbl_gam[2];
@@ -409,6 +409,8 @@ static SpecTables<T> spec_tables(ibm_handle h) {
   s.twz = (const T*)h->twz;
   s.cp = h->pcp;
   s.inv = h->pinv;
+  s.segf = h->psegf;
+  s.segb = h->psegb;
   return s;
 }
 
@@ -844,7 +846,7 @@ struct Knob {
 };
 
 static std::vector<Knob> tune_knobs() {
-  return {{&Tune::fft_plane, {2, 1}}, {&Tune::sweep_zy, {2, 1}}, {&Tune::tri_y, {1, 2, 3}},
+  return {{&Tune::fft_plane, {2, 1}}, {&Tune::sweep_zy, {2, 1}}, {&Tune::sweep_y, {1}}, {&Tune::tri_y, {1, 2, 3}},
           {&Tune::sweep_w, {64, 32, 16}},
           {&Tune::fft_lpb, {0, 8, 4, 2}},
           {&Tune::fft_cols, {16, 8, 4}}};
@@ -906,6 +908,7 @@ static void tune_out(const Tune& t, double ms, ibm_tune* out) {
   out->fft_cols = t.fft_cols;
   out->sweep_zy = t.sweep_zy;
   out->fft_plane = t.fft_plane;
+  out->sweep_y = t.sweep_y;
   out->ms_per_step = ms;
 }
 
@@ -914,8 +917,9 @@ static void tune_out(const Tune& t, double ms, ibm_tune* out) {
 static void tune_log(const Tune& t, double ms) {
   static const bool on = getenv("IBM_AUTOTUNE_LOG") != nullptr;
   if (on)
-    fprintf(stderr, "ibm autotune: tri_y %d sweep_w %d fft_lpb %d fft_cols %d sweep_zy %d fft_plane %d -> %.4f ms/step\n",
-            t.tri_y, t.sweep_w, t.fft_lpb, t.fft_cols, t.sweep_zy, t.fft_plane, ms);
+    fprintf(stderr,
+            "ibm autotune: tri_y %d sweep_w %d fft_lpb %d fft_cols %d sweep_zy %d fft_plane %d sweep_y %d -> %.4f ms/step\n",
+            t.tri_y, t.sweep_w, t.fft_lpb, t.fft_cols, t.sweep_zy, t.fft_plane, t.sweep_y, ms);
 }
 
 template <class Trial>
@@ -1112,13 +1116,16 @@ ibm_status ibm_create_grid(const ibm_grid_desc* desc, void* stream, ibm_handle* 
   const size_t nspec = (size_t)g.nz * g.ny * g.nkx;
   h->pcp = (double*)dalloc(h, nspec * 8);
   h->pinv = (double*)dalloc(h, nspec * 8);
-  if (!ok || !h->lamx || !h->lamz || !h->twx || !h->twz || !h->pcp || !h->pinv) {
+  const size_t nsegs = (size_t)g.nz * ((g.ny + TRI_SEG - 1) / TRI_SEG) * g.nkx;
+  h->psegf = (double*)dalloc(h, nsegs * 8);
+  h->psegb = (double*)dalloc(h, nsegs * 8);
+  if (!ok || !h->lamx || !h->lamz || !h->twx || !h->twz || !h->pcp || !h->pinv || !h->psegf || !h->psegb) {
     release_all(h);
     delete h;
     return IBM_ERR_OOM;
   }
   cudaStream_t st = h->user;
-  launch_build_poisson_tables(g, h->lamx, h->lamz, h->pcp, h->pinv, st);
+  launch_build_poisson_tables(g, h->lamx, h->lamz, h->pcp, h->pinv, h->psegf, h->psegb, st);
   // state at rest
   cudaMemsetAsync(h->u, 0, ncell * es, st);
   cudaMemsetAsync(h->v, 0, nvf * es, st);
@@ -1486,12 +1493,13 @@ static bool tune_valid(const ibm_tune* t) {
   if (t->fft_cols < 0 || t->fft_cols > 16 || (t->fft_cols & (t->fft_cols - 1))) return false;
   if (t->sweep_zy < 0 || t->sweep_zy > 2) return false;
   if (t->fft_plane < 0 || t->fft_plane > 2) return false;
+  if (t->sweep_y < 0 || t->sweep_y > 1) return false;
   return true;
 }
 
 ibm_status ibm_set_tune(ibm_handle h, const ibm_tune* t) {
   if (!h || !tune_valid(t)) return IBM_ERR_ARG;
-  h->tune = Tune{t->tri_y, t->sweep_w, t->fft_lpb, t->fft_cols, t->sweep_zy, t->fft_plane};
+  h->tune = Tune{t->tri_y, t->sweep_w, t->fft_lpb, t->fft_cols, t->sweep_zy, t->fft_plane, t->sweep_y};
   invalidate(h);
   return IBM_OK;
 }
@@ -1652,7 +1660,7 @@ ibm_status ibm_batch_profile_stages(ibm_batch_handle b, int nsteps, double* ms, 
 
 ibm_status ibm_batch_set_tune(ibm_batch_handle b, const ibm_tune* t) {
   if (!b || !tune_valid(t)) return IBM_ERR_ARG;
-  b->tune = Tune{t->tri_y, t->sweep_w, t->fft_lpb, t->fft_cols, t->sweep_zy, t->fft_plane};
+  b->tune = Tune{t->tri_y, t->sweep_w, t->fft_lpb, t->fft_cols, t->sweep_zy, t->fft_plane, t->sweep_y};
   b->built = false;
   return IBM_OK;
 }
