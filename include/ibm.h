@@ -223,8 +223,8 @@ typedef struct {
                          2 several lanes per line (affine-map scans) */
   int fft_plane;      /* 1 separate x and z transform kernels, 2 both fused per y-plane (when its
                          half-spectrum fits shared memory) */
-  int sweep_y;        /* y sweep: 0 as sweep_zy, 1 one thread per line with its rows streamed through
-                         registers (lines up to 256 rows) */
+  int sweep_y;        /* z and y sweeps: 0 as sweep_zy, 1 one thread per line with its rows streamed
+                         through registers (any line length) */
   double ms_per_step; /* set by the autotuners: measured time per step of the chosen shapes */
 } ibm_tune;
 

@@ -1105,13 +1105,14 @@ struct SweepZY {
 
 // y-sweep streamed through registers, one thread per line (component bk.y,
 // line t = i + nx k, so a warp reads each row of 32 neighbouring lines as
-// one coalesced segment).  Rows are read SYB at a time, ahead of the
-// recurrence; the forward values overwrite R (the line stays in L2 between
-// the passes) and the backward pass adds du to the state on its way out.
-// Same recurrences, tables and operation order as solve_wall; the forcing
-// rows of a line are kept as a bitmask for the segment positions of the
-// backward pass (lines of up to SYMAX rows).
-constexpr int SYB = 16, SYMAX = 256;
+// one coalesced segment).  Rows are read SYB at a time ahead of the
+// recurrence.  The forward pass writes its values over R and the backward
+// multiplier c' of every row into the scratch array (0 on identity rows),
+// so the backward pass is the same branch-free recurrence for every line,
+// x_j = p_j - c'_j x_{j+1}, adding du to the state on its way out.  Same
+// recurrences, tables and operation order as solve_wall: a forcing row is
+// a forward step with multiplier 0 and pivot 1, which leaves its value.
+constexpr int SYB = 16;
 
 template <typename T>
 __device__ __forceinline__ void sweep_y_stream(const Blk& bk, const Geo& g, const Fields<T>& f,
@@ -1123,22 +1124,17 @@ __device__ __forceinline__ void sweep_y_stream(const Blk& bk, const Geo& g, cons
   const int i = (int)(t % g.nx), k = (int)(t / g.nx);
   const int jj0 = c == 1 ? 1 : 0;
   const int n = c == 1 ? g.ny - 1 : g.ny;
-  const long long base = fidx(g, c, i, jj0, k), stride = g.nx;
-  const long long fbase = cidx(g, i, jj0, k);   // flag byte of row m at fbase + m nx
-  const unsigned char* __restrict__ fb = reinterpret_cast<const unsigned char*>(flags32);
-  T* __restrict__ R = f.R[c];
-  T* __restrict__ Uc = comp_ptr(f, c);
-  T* __restrict__ Lc = f.lo[c];
+  const int sn = g.nx;   // row stride of both the field and the flag bytes
+  const long long base = fidx(g, c, i, jj0, k);
+  T* __restrict__ Rl = f.R[c] + base;
+  T* __restrict__ Sl = f.scr + comp_off(g, c) + base;
+  T* __restrict__ Ul = comp_ptr(f, c) + base;
+  T* __restrict__ Ll = f.lo[c] ? f.lo[c] + base : nullptr;
+  const unsigned char* __restrict__ Fl = reinterpret_cast<const unsigned char*>(flags32) + cidx(g, i, jj0, k);
   const T a = -tb.off[1];
   const bool tang = c != 1;
   const bool any = lfirst[line_y(g, c, i, k)] < g.ny;
-  unsigned fm[SYMAX / 32];   // forcing rows of an `any` line
-#pragma unroll
-  for (int w = 0; w < SYMAX / 32; ++w) fm[w] = 0u;
-  auto forcing = [&](int r) { return (fm[r >> 5] >> (r & 31)) & 1u; };
-  const T* __restrict__ inv0 = tang ? tb.yinvW : tb.vinvR;
-  const T* __restrict__ cp0 = tang ? tb.ycpW : tb.vcpR;
-  // ---- forward
+  // ---- forward: p_j = (r_j - a_j p_{j-1}) iv_j; c'_j to the scratch
   T prev = (T)0;
   int m = 0;
   bool segW = tang;
@@ -1151,88 +1147,194 @@ __device__ __forceinline__ void sweep_y_stream(const Blk& bk, const Geo& g, cons
       e[u] = (T)0;
       fl[u] = 0;
       if (j < n) {
-        e[u] = R[base + (long long)j * stride];
-        if (any) fl[u] = fb[fbase + (long long)j * stride];
+        e[u] = Rl[j * sn];
+        if (any) fl[u] = Fl[j * sn];
       }
+    }
+    // segment positions and table entries of the batch (flags only)
+    T iv[SYB], cq[SYB], am[SYB];
+#pragma unroll
+    for (int u = 0; u < SYB; ++u) {
+      const int j = j0 + u;
+      const bool frc = (fl[u] >> c) & 1;
+      const bool last = j == n - 1;
+      const T* ivt = !tang ? tb.vinvR : (last ? (segW ? tb.yinvLW : tb.yinvLR) : (segW ? tb.yinvW : tb.yinvR));
+      const T* cpt = !tang ? tb.vcpR : (segW ? tb.ycpW : tb.ycpR);
+      iv[u] = (T)1;
+      cq[u] = (T)0;
+      am[u] = (T)0;
+      if (j < n && !frc) {
+        iv[u] = __ldg(ivt + m);
+        if (!last) cq[u] = __ldg(cpt + m);
+        am[u] = a;
+      }
+      m = frc ? 0 : m + 1;
+      segW = segW && !frc;
     }
 #pragma unroll
     for (int u = 0; u < SYB; ++u) {
       const int j = j0 + u;
-      if (j >= n) break;
-      if (!any) {
-        const T iv = (j == n - 1) ? (tang ? __ldg(tb.yinvLW + n - 1) : __ldg(inv0 + n - 1)) : __ldg(inv0 + j);
-        prev = (e[u] - a * prev) * iv;
-      } else if ((fl[u] >> c) & 1) {
-        prev = e[u];
-        m = 0;
-        segW = false;
-        fm[j >> 5] |= 1u << (j & 31);
-        continue;
-      } else {
-        T iv;
-        if (!tang) iv = __ldg(tb.vinvR + m);
-        else if (j == n - 1) iv = segW ? __ldg(tb.yinvLW + m) : __ldg(tb.yinvLR + m);
-        else iv = segW ? __ldg(tb.yinvW + m) : __ldg(tb.yinvR + m);
-        prev = (e[u] - a * prev) * iv;
-        ++m;
+      if (j < n) {
+        prev = (e[u] - am[u] * prev) * iv[u];
+        Rl[j * sn] = prev;
+        Sl[j * sn] = cq[u];
       }
-      R[base + (long long)j * stride] = prev;
     }
   }
-  // ---- backward, with u^s + du written out
-  auto seg_of = [&](int q, int& mpos, bool& w) {
-    int lo = q - 1;
-    while (lo >= 0 && !forcing(lo)) --lo;
-    mpos = q - lo - 1;
-    w = tang && lo < 0;
-  };
-  T x = prev;
-  int mq = -1;
-  bool qW = false;
-  if (any && !forcing(n - 1)) seg_of(n - 1, mq, qW);
+  // ---- backward: x_j = p_j - c'_j x_{j+1}; uhat = u^s + x
+  T x = (T)0;
   for (int j1 = n - 1; j1 >= 0; j1 -= SYB) {
-    T pv[SYB], uh[SYB], ul[SYB];
+    T pv[SYB], cv[SYB], uh[SYB], ul[SYB];
 #pragma unroll
     for (int u = 0; u < SYB; ++u) {
       const int j = j1 - u;
-      pv[u] = uh[u] = ul[u] = (T)0;
+      pv[u] = cv[u] = uh[u] = ul[u] = (T)0;
       if (j >= 0) {
-        const long long id = base + (long long)j * stride;
-        pv[u] = R[id];
-        uh[u] = Uc[id];
-        if (Lc) ul[u] = Lc[id];
+        pv[u] = Rl[j * sn];
+        cv[u] = Sl[j * sn];
+        uh[u] = Ul[j * sn];
+        if (Ll) ul[u] = Ll[j * sn];
       }
     }
 #pragma unroll
     for (int u = 0; u < SYB; ++u) {
       const int j = j1 - u;
       if (j < 0) break;
-      if (j == n - 1) {
-        x = pv[u];
-      } else if (!any) {
-        x = pv[u] - __ldg(cp0 + j) * x;
-      } else if (forcing(j)) {
-        x = pv[u];
-        mq = -1;
-      } else {
-        if (mq < 0) seg_of(j, mq, qW);
-        else --mq;
-        const T cpj = !tang ? __ldg(tb.vcpR + mq) : (qW ? __ldg(tb.ycpW + mq) : __ldg(tb.ycpR + mq));
-        x = pv[u] - cpj * x;
-      }
-      const long long id = base + (long long)j * stride;
-      if (Lc) {
+      x = pv[u] - cv[u] * x;
+      if (Ll) {
         // velocity state as a (hi, lo) pair: add du without rounding it away
         float hi = (float)uh[u], lo = (float)ul[u];
         ff_add(hi, lo, (float)x);
-        Uc[id] = (T)hi;
-        Lc[id] = (T)lo;
+        Ul[j * sn] = (T)hi;
+        Ll[j * sn] = (T)lo;
       } else {
-        Uc[id] = uh[u] + x;
+        Ul[j * sn] = uh[u] + x;
       }
     }
   }
 }
+// z-sweep streamed the same way, one thread per periodic line (component
+// bk.y, line t = i + nx l at plane j = l (+1 for v)).  A line without
+// forcing rows is solved by Sherman-Morrison (tabulated Thomas of the
+// modified matrix, first-row dot product g0, correction along zv); a line
+// with forcing rows runs rotated to start at its first forcing row (an
+// identity row), its last row's periodic coupling moved to the right-hand
+// side.  Both share the forward step p_q = (d_q - a_q p_{q-1}) iv_q with c'_q
+// stored in the scratch array, and the backward step x_q = p_q - c'_q x_{q+1}
+// (minus fact zv_q for Sherman-Morrison); same operation order as
+// solve_periodic.
+template <typename T>
+__device__ __forceinline__ void sweep_z_stream(const Blk& bk, const Geo& g, const Fields<T>& f,
+                                               const unsigned* __restrict__ flags32, const SweepTables<T>& tb,
+                                               const int* __restrict__ lfirst) {
+  const int c = bk.y;
+  const int nplanes = c == 1 ? g.ny - 1 : g.ny;    // v: interior planes j = 1 .. ny-1
+  const long long t = (long long)bk.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)g.nx * nplanes) return;
+  const int i = (int)(t % g.nx), l = (int)(t / g.nx);
+  const int j = (c == 1 ? 1 : 0) + l;
+  const int n = g.nz;
+  const int sn = planes(g, c) * g.nx;              // row stride along z
+  const int fs = g.ny * g.nx;                      // flag-byte stride along z
+  const long long base = fidx(g, c, i, j, 0);
+  T* __restrict__ Rl = f.R[c] + base;
+  T* __restrict__ Sl = f.scr + comp_off(g, c) + base;
+  const unsigned char* __restrict__ Fl = reinterpret_cast<const unsigned char*>(flags32) + cidx(g, i, j, 0);
+  const T a = -tb.off[2];
+  const int f0 = lfirst[line_z(g, c, i, j)];
+  const bool any = f0 < n;
+  const int r0 = any ? f0 : 0;
+  const T x0 = any ? Rl[f0 * sn] : (T)0;
+  auto rot = [&](int q) { const int r = r0 + q; return r >= n ? r - n : r; };
+  // ---- forward
+  T prev = (T)0, acc = (T)0;
+  int m = 0;
+  for (int q0 = 0; q0 < n; q0 += SYB) {
+    T e[SYB];
+    unsigned char fl[SYB];
+#pragma unroll
+    for (int u = 0; u < SYB; ++u) {
+      const int q = q0 + u;
+      e[u] = (T)0;
+      fl[u] = 0;
+      if (q < n) {
+        const int r = rot(q);
+        e[u] = Rl[r * sn];
+        if (any) fl[u] = Fl[r * fs];
+      }
+    }
+    T iv[SYB], cq[SYB], am[SYB], gq[SYB];
+#pragma unroll
+    for (int u = 0; u < SYB; ++u) {
+      const int q = q0 + u;
+      const bool frc = (fl[u] >> c) & 1;
+      iv[u] = (T)1;
+      cq[u] = (T)0;
+      am[u] = (T)0;
+      gq[u] = (T)0;
+      if (q < n && !frc) {
+        if (any) {
+          iv[u] = __ldg(tb.invR[1] + m);
+          if (q < n - 1) cq[u] = __ldg(tb.cpR[1] + m);
+        } else {
+          iv[u] = __ldg(tb.inv[1] + q);
+          if (q < n - 1) cq[u] = __ldg(tb.cp[1] + q);
+          gq[u] = __ldg(tb.g0[1] + q);
+        }
+        am[u] = a;
+      }
+      m = frc ? 0 : m + 1;
+    }
+#pragma unroll
+    for (int u = 0; u < SYB; ++u) {
+      const int q = q0 + u;
+      if (q < n) {
+        T dq = e[u];
+        if (any && q == n - 1 && am[u] != (T)0) dq -= a * x0;
+        if (!any) acc += gq[u] * dq;
+        prev = (dq - am[u] * prev) * iv[u];
+        const int r = rot(q);
+        Rl[r * sn] = prev;
+        Sl[r * sn] = cq[u];
+      }
+    }
+  }
+  const T fact = any ? (T)0 : (acc + (a / tb.gam[1]) * prev) / tb.smden[1];
+  // ---- backward
+  T x = (T)0;
+  for (int q1 = n - 1; q1 >= 0; q1 -= SYB) {
+    T pv[SYB], cv[SYB], zq[SYB];
+#pragma unroll
+    for (int u = 0; u < SYB; ++u) {
+      const int q = q1 - u;
+      pv[u] = cv[u] = zq[u] = (T)0;
+      if (q >= 0) {
+        const int r = rot(q);
+        pv[u] = Rl[r * sn];
+        cv[u] = Sl[r * sn];
+        if (!any) zq[u] = __ldg(tb.zv[1] + q);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < SYB; ++u) {
+      const int q = q1 - u;
+      if (q < 0) break;
+      x = pv[u] - cv[u] * x;
+      Rl[rot(q) * sn] = any ? x : x - fact * zq[u];
+    }
+  }
+}
+template <typename T>
+struct SweepZStream {
+  static constexpr int kThreads = 128;
+  Geo g;
+  Fields<T> f;
+  const unsigned* flags32;
+  SweepTables<T> tb;
+  const int* lfirst;
+  __device__ __forceinline__ void operator()(const Blk& bk) const { sweep_z_stream<T>(bk, g, f, flags32, tb, lfirst); }
+};
+
 template <typename T>
 struct SweepYStream {
   static constexpr int kThreads = 128;
@@ -1311,14 +1413,17 @@ void launch_sweeps(const Geo& g, const Fields<T>& f, const TagBuffers& b, const 
   // tuning asks for the shared-memory tile with one thread per line
   const bool lanes = sizeof(T) == 4 && ex.tune.sweep_zy != 1;
   ex.mark(ST_SWEEP_Z);
-  if (!(lanes && sweep_lanes_launch(g, f, b, tb, ex, sh.nz, 2, g.ny))) {
+  if (ex.tune.sweep_y == 1) {
+    const long long lines = (long long)g.nx * g.ny;
+    ex.launch(dim3((unsigned)((lines + 127) / 128), 3), dim3(128), 0, SweepZStream<T>{g, f, b.flags32, tb, b.lines.z});
+  } else if (!(lanes && sweep_lanes_launch(g, f, b, tb, ex, sh.nz, 2, g.ny))) {
     int W = sweep_width<T>(sh.nz);
     if (ex.tune.sweep_w > 0 && ex.tune.sweep_w < W) W = ex.tune.sweep_w;
     ex.launch(dim3((g.nx + W - 1) / W, 3, g.ny), dim3(W), sweep_smem<T>(W, sh.nz, sh.nz),
               SweepZY<T>{g, f, b.flags32, tb, b.lines.z, 2});
   }
   ex.mark(ST_SWEEP_Y);
-  if (ex.tune.sweep_y == 1 && sh.ny <= SYMAX) {
+  if (ex.tune.sweep_y == 1) {
     const long long lines = (long long)g.nx * g.nz;
     ex.launch(dim3((unsigned)((lines + 127) / 128), 3), dim3(128), 0, SweepYStream<T>{g, f, b.flags32, tb, b.lines.y});
   } else if (!(lanes && sweep_lanes_launch(g, f, b, tb, ex, sh.ny, 1, g.nz))) {
