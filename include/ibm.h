@@ -315,6 +315,18 @@ ibm_status ibm_get_loads(ibm_handle h, int sides, const double* pole, double* fo
  * on_device says).  Synchronises. */
 ibm_status ibm_get_pressure_recon(ibm_handle h, double* p, int on_device);
 
+/* Self-check of an implementation detail of the mixed path (no counterpart
+ * in the paper): its kernels convert between FP32 and FP64 with integer
+ * operations (a hardware conversion costs this GPU's narrow FP64 pipe about
+ * two FP64 FMAs).  Runs n cases on the current device -- hashed binary32
+ * bit patterns widened, binary64 values narrowed (every rounding case,
+ * exact ties included) -- and compares each integer-path result with the
+ * hardware conversion bit for bit.  *checked: results the integer path
+ * produced (the rest are subnormal, infinite or NaN cases that the kernels
+ * leave to the hardware); *mismatches: those that differ (0 expected).
+ * Allocates 16 bytes on the device; synchronises the device. */
+ibm_status ibm_check_conversions(long long n, long long* mismatches, long long* checked);
+
 /* Library version string. */
 const char* ibm_version(void);
 

@@ -101,6 +101,47 @@ struct Stage {
   int s;                          // sub-stage index
 };
 
+// ---- FP32 <-> FP64 conversions on the integer pipes ------------------------
+// On this GPU a hardware FP32 <-> FP64 conversion occupies the narrow FP64
+// pipe for about as long as two FP64 FMAs.  Both directions are written here
+// from the IEEE 754 binary32 / binary64 encodings: widening moves the sign,
+// exponent and mantissa fields (exact); narrowing truncates the mantissa to
+// 23 bits and rounds to nearest, ties to even, from the round and sticky
+// bits.  Zero and every normal result take this path; subnormal, infinite
+// or NaN operands set `special`, and the caller redoes the batch with the
+// hardware conversions (a warp-uniform branch that ordinary data never
+// takes), so the results are those of the hardware conversions bit for bit.
+__device__ __forceinline__ double f2d_int(float f, bool& special) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned e = (b >> 23) & 0xFFu, m = b & 0x7FFFFFu;
+  special |= (e == 0u && m != 0u) || e == 0xFFu;
+  const unsigned hi = (b & 0x80000000u) | (e ? (((e + 896u) << 20) | (m >> 3)) : 0u);
+  return __hiloint2double((int)hi, (int)(m << 29));
+}
+__device__ __forceinline__ float d2f_int(double d, bool& special) {
+  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+  const unsigned ah = hi & 0x7FFFFFFFu, e = ah >> 20;
+  const bool zero = ah == 0u && lo == 0u;
+  special |= !zero && (e < 897u || e > 1150u);   // outside the normal binary32 exponents
+  unsigned fb = ((e - 896u) << 23) | ((ah & 0xFFFFFu) << 3) | (lo >> 29);
+  const unsigned rnd = (lo >> 28) & 1u, sticky = (lo & 0x0FFFFFFFu) != 0u, lsb = (lo >> 29) & 1u;
+  fb += rnd & (sticky | lsb);                      // a carry moves into the exponent, as it should
+  return __uint_as_float((hi & 0x80000000u) | (zero ? 0u : fb));
+}
+
+// Sum of n partial values p[b * stride + off] by one warp in a fixed order:
+// lane l adds b = l, l + 32, ... in turn, then a butterfly of pairwise sums.
+// Every lane returns the same value (each pairwise add is commutative), and
+// the result depends only on n and the data.
+__device__ __forceinline__ double warp_sum_fixed(const double* __restrict__ p, int n, int stride, int off) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+#pragma unroll 4
+  for (int b = lane; b < n; b += 32) s += p[(long long)b * stride + off];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+  return s;
+}
+
 // ---- unevaluated FP32 pairs (hi + lo): error-free transformations ----------
 // s + e == a + b exactly (Knuth's TwoSum)
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {

@@ -1509,11 +1509,12 @@ struct SlipPartial {
 };
 
 __device__ __forceinline__ void slip_final(const Blk& bk, const double* partial, DevState* ds, int nblk) {
-  if (threadIdx.x < 3) {
-    double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += partial[b * 3 + threadIdx.x];
-    ds->slip_sum[threadIdx.x] = s;
-    if (!isfinite(s)) atomicOr(&ds->err, ERR_NONFINITE);
+  for (int c = 0; c < 3; ++c) {
+    const double s = warp_sum_fixed(partial, nblk, 3, c);
+    if (threadIdx.x == 0) {
+      ds->slip_sum[c] = s;
+      if (!isfinite(s)) atomicOr(&ds->err, ERR_NONFINITE);
+    }
   }
 }
 struct SlipFinal {

@@ -276,9 +276,8 @@ struct QPartial {
 
 __device__ __forceinline__ void q_final(const Blk& bk, const Geo& g, const double* partial, DevState* ds, int s, int use_q,
                                         int nblk) {
+  const double sum = warp_sum_fixed(partial, nblk, 1, 0);
   if (threadIdx.x != 0) return;
-  double sum = 0.0;
-  for (int b = 0; b < nblk; ++b) sum += partial[b];
   const double dV = g.dx * g.dy * g.dz;
   const double A = sum * dV;
   const double VF = (double)(g.ncell - (long long)ds->nbound) * dV;
@@ -366,10 +365,9 @@ struct QEnergyPartial {
 
 __device__ __forceinline__ void q_energy_final(const Blk&, const Geo& g, const double* partial, DevState* ds, int s,
                                                int nblk) {
+  double t[5];
+  for (int q = 0; q < 5; ++q) t[q] = warp_sum_fixed(partial, nblk, 5, q);
   if (threadIdx.x != 0) return;
-  double t[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  for (int b = 0; b < nblk; ++b)
-    for (int q = 0; q < 5; ++q) t[q] += partial[5 * b + q];
   const double dV = g.dx * g.dy * g.dz;
   const double S0 = t[0] * dV, S1 = t[1] * dV, S2 = t[2] * dV, A = t[3] * dV, B = t[4] * dV;
   const double C = S0 * S2 - S1 * S1;
@@ -940,6 +938,7 @@ __device__ __forceinline__ void tri_y_warp(const Blk& bk, const Geo& g, const Fi
   const unsigned FULL = 0xFFFFFFFFu;
   // ---- every load of the lane's rows, issued together; br = r / piv
   double br[Rr], bi[Rr], cq[Rr];
+  bool special = false;   // an FP32 input the integer conversion leaves to the hardware
 #pragma unroll
   for (int u = 0; u < Rr; ++u) {
     const int j = j0 + u;
@@ -949,8 +948,26 @@ __device__ __forceinline__ void tri_y_warp(const Blk& bk, const Geo& g, const Fi
       const C z = spec[id];
       const double iv = __ldg(inv + id);
       cq[u] = __ldg(cp + id);
-      br[u] = (double)z.x * iv;
-      bi[u] = (double)z.y * iv;
+      if constexpr (sizeof(T) == 4) {
+        br[u] = f2d_int(z.x, special) * iv;
+        bi[u] = f2d_int(z.y, special) * iv;
+      } else {
+        br[u] = (double)z.x * iv;
+        bi[u] = (double)z.y * iv;
+      }
+    }
+  }
+  if (sizeof(T) == 4 && __any_sync(FULL, special)) {
+#pragma unroll
+    for (int u = 0; u < Rr; ++u) {
+      const int j = j0 + u;
+      if (live && j < ny) {
+        const long long id = base + (long long)j * stride;
+        const C z = spec[id];
+        const double iv = __ldg(inv + id);
+        br[u] = (double)z.x * iv;
+        bi[u] = (double)z.y * iv;
+      }
     }
   }
   if (singular && j0 == 0) br[0] = bi[0] = 0.0;   // pinned phi_0 of the (0,0) mode
@@ -1056,14 +1073,30 @@ __device__ __forceinline__ void tri_y_warp(const Blk& bk, const Geo& g, const Fi
       }
     }
   }
+  C o[Rr];
+  special = false;
+#pragma unroll
+  for (int u = 0; u < Rr; ++u) {
+    if constexpr (sizeof(T) == 4) {
+      o[u].x = d2f_int(br[u], special);
+      o[u].y = d2f_int(bi[u], special);
+    } else {
+      o[u].x = (T)br[u];
+      o[u].y = (T)bi[u];
+    }
+  }
+  if (sizeof(T) == 4 && __any_sync(FULL, special)) {
+#pragma unroll
+    for (int u = 0; u < Rr; ++u) {
+      o[u].x = (T)br[u];
+      o[u].y = (T)bi[u];
+    }
+  }
 #pragma unroll
   for (int u = 0; u < Rr; ++u) {
     const int j = j0 + u;
     if (!live || j >= ny) continue;
-    C o;
-    o.x = (T)br[u];
-    o.y = (T)bi[u];
-    spec[base + (long long)j * stride] = o;
+    spec[base + (long long)j * stride] = o[u];
   }
 }
 template <typename T, int L>

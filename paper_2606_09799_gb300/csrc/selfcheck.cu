@@ -1,0 +1,81 @@
+// selfcheck.cu -- bit-for-bit check of the integer-pipe FP32 <-> FP64
+// conversions (common.cuh) against the hardware conversions.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "ibm.h"
+
+namespace ibm {
+
+// 32-bit integer hash "lowbias32" (C. Wellons, hash-prospector): a
+// counter-based source of bit patterns for the check.
+__device__ __forceinline__ unsigned lowbias32(unsigned x) {
+  x ^= x >> 16;
+  x *= 0x7feb352dU;
+  x ^= x >> 15;
+  x *= 0x846ca68bU;
+  x ^= x >> 16;
+  return x;
+}
+
+// Case t: a float with a hashed bit pattern (every class of binary32 value),
+// and a double made from a hashed normal float with hashed low 29 mantissa
+// bits (every rounding case of the narrowing, exact ties included: one
+// pattern in 2^29 is a tie, so some cases force one) or, one case in eight,
+// a fully hashed bit pattern (exponents outside the binary32 range).
+__global__ void k_check_conversions(long long n, unsigned long long* out) {
+  unsigned long long bad = 0, fast = 0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const unsigned h0 = lowbias32((unsigned)t * 2u + 1u), h1 = lowbias32((unsigned)t * 2u + 2u ^ 0x9e3779b9u);
+    // widening
+    const float f = __uint_as_float(h0);
+    bool sp = false;
+    const double w = f2d_int(f, sp);
+    if (!sp) {
+      ++fast;
+      const double ref = (double)f;
+      if (__double_as_longlong(w) != __double_as_longlong(ref) && !(f != f)) ++bad;
+    }
+    // narrowing
+    double d;
+    if ((h1 & 7u) == 0u) {
+      d = __hiloint2double((int)h0, (int)h1);
+    } else {
+      const unsigned fe = 1u + (h1 >> 8) % 254u;                       // normal binary32 exponent
+      const float g = __uint_as_float((h0 & 0x807FFFFFu) | (fe << 23));
+      bool s2 = false;
+      const double gw = f2d_int(g, s2);
+      unsigned low = lowbias32(h1) & 0x1FFFFFFFu;
+      if ((h1 & 0xF0u) == 0u) low = 0x10000000u;                       // an exact tie
+      d = __hiloint2double(__double2hiint(gw), (int)(((unsigned)__double2loint(gw) & 0xE0000000u) | low));
+    }
+    bool sp2 = false;
+    const float r = d2f_int(d, sp2);
+    if (!sp2) {
+      ++fast;
+      if (__float_as_uint(r) != __float_as_uint((float)d) && !(d != d)) ++bad;
+    }
+  }
+  atomicAdd(out, bad);
+  atomicAdd(out + 1, fast);
+}
+
+}  // namespace ibm
+
+extern "C" ibm_status ibm_check_conversions(long long n, long long* mismatches, long long* checked) {
+  if (n < 0 || !mismatches || !checked) return IBM_ERR_ARG;
+  unsigned long long* d = nullptr;
+  if (cudaMalloc(&d, 2 * sizeof(unsigned long long)) != cudaSuccess) return IBM_ERR_OOM;
+  unsigned long long h[2] = {0, 0};
+  ibm_status st = IBM_OK;
+  if (cudaMemset(d, 0, sizeof(h)) != cudaSuccess) st = IBM_ERR_CUDA;
+  if (st == IBM_OK && n > 0) {
+    ibm::k_check_conversions<<<1024, 256>>>(n, d);
+    if (cudaGetLastError() != cudaSuccess) st = IBM_ERR_CUDA;
+  }
+  if (st == IBM_OK && cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) st = IBM_ERR_CUDA;
+  cudaFree(d);
+  *mismatches = (long long)h[0];
+  *checked = (long long)h[1];
+  return st;
+}

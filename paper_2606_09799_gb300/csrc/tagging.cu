@@ -604,27 +604,38 @@ struct CmpCount {
 
 // single block: exclusive scan of the per-block counts (in place), totals to ds
 __device__ __forceinline__ void cmp_scan(const Blk& bk, unsigned* blk, int nblk, DevState* ds, unsigned fcap) {
-  __shared__ unsigned part[4][1024];
+  // block-wide exclusive scan of the per-block counts (integers: exact in any
+  // order): per-thread runs of `per` blocks, warp shuffles, warp totals
+  __shared__ unsigned wsum[4][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int per = (nblk + 1023) / 1024;
   const int b0 = threadIdx.x * per, b1 = min(nblk, b0 + per);
-  unsigned loc[4] = {0, 0, 0, 0};
+  unsigned loc[4] = {0, 0, 0, 0}, inc[4];
   for (int b = b0; b < b1; ++b)
     for (int q = 0; q < 4; ++q) loc[q] += blk[4 * b + q];
-  for (int q = 0; q < 4; ++q) part[q][threadIdx.x] = loc[q];
-  __syncthreads();
-  if (threadIdx.x < 4) {
-    unsigned run = 0;
-    for (int t = 0; t < 1024; ++t) {
-      const unsigned v = part[threadIdx.x][t];
-      part[threadIdx.x][t] = run;
-      run += v;
+  for (int q = 0; q < 4; ++q) {
+    unsigned v = loc[q];
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned nb = __shfl_up_sync(0xFFFFFFFFu, v, o);
+      if (lane >= o) v += nb;
     }
-    if (threadIdx.x < 3) ds->nforce_c[threadIdx.x] = run;
-    else ds->nbound = run;
+    inc[q] = v;
+    if (lane == 31) wsum[q][wid] = v;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    for (int q = 0; q < 4; ++q) {
+      unsigned v = wsum[q][lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned nb = __shfl_up_sync(0xFFFFFFFFu, v, o);
+        if (lane >= o) v += nb;
+      }
+      wsum[q][lane] = v;   // inclusive over warps
+    }
   }
   __syncthreads();
   unsigned run[4];
-  for (int q = 0; q < 4; ++q) run[q] = part[q][threadIdx.x];
+  for (int q = 0; q < 4; ++q) run[q] = inc[q] - loc[q] + (wid > 0 ? wsum[q][wid - 1] : 0u);
   for (int b = b0; b < b1; ++b)
     for (int q = 0; q < 4; ++q) {
       const unsigned v = blk[4 * b + q];
@@ -632,11 +643,15 @@ __device__ __forceinline__ void cmp_scan(const Blk& bk, unsigned* blk, int nblk,
       run[q] += v;
     }
   if (threadIdx.x == 0) {
-    const unsigned n0 = ds->nforce_c[0], n1 = ds->nforce_c[1], n2 = ds->nforce_c[2];
+    const unsigned n0 = wsum[0][31], n1 = wsum[1][31], n2 = wsum[2][31];
+    ds->nforce_c[0] = n0;
+    ds->nforce_c[1] = n1;
+    ds->nforce_c[2] = n2;
+    ds->nbound = wsum[3][31];
     ds->force_base[0] = 0;
     ds->force_base[1] = n0;
     ds->force_base[2] = n0 + n1;
-    if ((unsigned long long)n0 + n1 + n2 > fcap || ds->nbound > fcap) atomicOr(&ds->err, ERR_LIST_OVERFLOW);
+    if ((unsigned long long)n0 + n1 + n2 > fcap || wsum[3][31] > fcap) atomicOr(&ds->err, ERR_LIST_OVERFLOW);
   }
 }
 struct CmpScan {

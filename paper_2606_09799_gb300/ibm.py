@@ -76,7 +76,7 @@ EXPORTS = ("ibm_create_grid", "ibm_destroy", "ibm_set_surface", "ibm_set_body_fo
            "ibm_set_tune", "ibm_get_tune", "ibm_autotune", "ibm_batch_create", "ibm_batch_destroy",
            "ibm_batch_step", "ibm_batch_sync", "ibm_batch_get_info", "ibm_batch_profile_stages",
            "ibm_batch_set_tune", "ibm_batch_autotune", "ibm_batch_last_error", "ibm_step_batch",
-           "ibm_get_loads", "ibm_get_pressure_recon")
+           "ibm_get_loads", "ibm_get_pressure_recon", "ibm_check_conversions")
 
 
 def library_path() -> str:
@@ -130,6 +130,8 @@ def load(build_if_needed: bool = True):
         L.ibm_step_batch.argtypes = [P, I, I]
         L.ibm_get_loads.argtypes = [P, I, P, P, P, P, P]
         L.ibm_get_pressure_recon.argtypes = [P, P, I]
+        L.ibm_check_conversions.argtypes = [ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong),
+                                            ctypes.POINTER(ctypes.c_longlong)]
         for name in EXPORTS:
             if name not in ("ibm_last_error", "ibm_version", "ibm_stage_name", "ibm_batch_last_error"):
                 getattr(L, name).restype = ctypes.c_int
@@ -360,6 +362,16 @@ def ibm_get_loads(h, nt, sides=1, pole=(0.0, 0.0, 0.0)):
     _check(h, load().ibm_get_loads(h, int(sides), pl.ctypes.data, F.ctypes.data, M.ctypes.data,
                                    tr.ctypes.data, pw.ctypes.data))
     return F, M, tr, pw
+
+
+def ibm_check_conversions(n: int) -> tuple:
+    """(mismatches, checked) of the integer-path FP32 <-> FP64 conversions
+    against the hardware conversions on n hashed cases."""
+    bad, fast = ctypes.c_longlong(0), ctypes.c_longlong(0)
+    st = load().ibm_check_conversions(int(n), ctypes.byref(bad), ctypes.byref(fast))
+    if st != 0:
+        raise IbmError(st, "ibm_check_conversions failed")
+    return bad.value, fast.value
 
 
 def ibm_get_pressure_recon(h, nx, ny, nz):

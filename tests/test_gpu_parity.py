@@ -360,3 +360,12 @@ def test_radix5_grid_matches_oracle(precision, tol):
     assert err <= tol, err
     if precision == "fp64":
         assert np.abs((o.p - o.p.mean()) - (gp - gp.mean())).max() <= 1e-10
+
+
+def test_integer_path_conversions_match_hardware():
+    """The mixed path's FP32 <-> FP64 conversions on the integer pipes give
+    the hardware conversion's result bit for bit on 2^22 hashed cases
+    (every class of binary32 input, every rounding case of the narrowing)."""
+    bad, checked = ibm.ibm_check_conversions(1 << 22)
+    assert checked > (1 << 22)   # most cases take the integer path
+    assert bad == 0, bad
