@@ -145,6 +145,57 @@ def algorithmic_bytes_per_cell(stage: str, word: int) -> float:
     return (r + w) * word
 
 
+TRAFFIC_SUMMARY = os.path.join(ROOT, "profiles", "traffic_plate128.md")
+
+
+def stage_kernel(stage: str, tune: dict | None, precision: str) -> str | None:
+    """Kernel that the given launch shapes run for a stage of the 128^3 step
+    (the name the ncu summaries use), or None when it is not recorded."""
+    t = tune or {}
+    T = "float" if precision == "mixed" else "double"
+    if stage in ("sweep_y", "sweep_z"):
+        if t.get("sweep_y", 0) == 1:
+            return f"SweepYStream<{T}>" if stage == "sweep_y" else f"SweepZStream<{T}>"
+        if precision == "mixed" and t.get("sweep_zy", 0) != 1:
+            return f"SweepLanes<{T}, 16, 8>"
+        return f"SweepZY<{T}>"
+    if stage == "tri_y":
+        v = t.get("tri_y", 0)
+        return {0: f"TriYWarp<{T}, 8>", 1: f"TriYWarp<{T}, 8>", 2: f"TriY<{T}>", 3: f"TriYSmem<{T}>"}[v]
+    if stage == "fft_x_fwd":
+        return f"FftPlaneFwd<{T}>" if t.get("fft_plane", 0) == 2 else f"FftXFwd<{T}>"
+    if stage == "rhs":
+        return f"Rhs<{T}>"
+    if stage == "project":
+        return f"Project<{T}>"
+    return None
+
+
+def ncu_traffic(stage: str, kernel: str | None, summary: str = TRAFFIC_SUMMARY, root: str = ROOT) -> float | None:
+    """DRAM bytes (read + write) per launch of `kernel` in `stage` from the
+    committed ncu summary, or None when it has no row for it or the kernel's
+    source file has changed since the counters were taken (its SHA-256 is
+    recorded beside the figure)."""
+    import hashlib
+    if kernel is None or not os.path.exists(summary):
+        return None
+    for line in open(summary):
+        cells = [c.strip().strip("`") for c in line.strip().strip("|").split("|")]
+        if len(cells) < 6 or cells[0] != stage or cells[1] != kernel:
+            continue
+        path = os.path.join(root, cells[2])
+        if not os.path.exists(path):
+            return None
+        with open(path, "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != cells[3]:
+                return None
+        try:
+            return float(cells[5]) * 1e6
+        except ValueError:
+            return None
+    return None
+
+
 TAG_FLOPS_PER_PAIR = 100.0   # closest point ~73, N and |N|^2 8, neighbour tests up to ~36 (FP64, counted from source)
 
 
@@ -305,8 +356,9 @@ def gpu_arm(args):
         g["share"] = g["share"] / tot_all
     top = max(groups, key=lambda k: groups[k]["share"])
     tg = groups[top]
+    kname = stage_kernel(top, head["tune"], args.precision)
     roof = {"bound": tg["bound"], "achieved": tg["achieved"], "peak": tg["peak"], "unit": tg["unit"],
-            "frac": tg["frac"], "traffic": None, "kernel": top,
+            "frac": tg["frac"], "traffic": ncu_traffic(top, kname), "kernel": top, "kernel_name": kname,
             "peak_source": ("FP64 FMA-chain probe on a GB300 of this pool (of measured)" if tg["bound"] == "alu"
                             else "MEASURED_PEAKS.json hbm_gbs (of measured)")}
     kernels_per_step = head["diag"]["kernels_per_step"]

@@ -55,3 +55,24 @@ def test_single_rank_is_unchanged():
     import bench
     assert bench.max_over_ranks(7.0, torch.device("cpu"), 1) == 7.0
     assert bench.whole_job_gcups(100, 10, 1, 1.0) == pytest.approx(100 * 10 / 1e-3 / 1e9)
+
+
+def test_traffic_lookup_follows_the_kernel_source(tmp_path):
+    """The roofline's DRAM traffic comes from the committed ncu summary only
+    while the kernel's source file is the one the counters were taken on."""
+    import hashlib
+    sys.path.insert(0, ROOT)
+    import bench
+    src = tmp_path / "k.cu"
+    src.write_text("kernel source v1\n")
+    sha = hashlib.sha256(src.read_bytes()).hexdigest()
+    summary = tmp_path / "traffic.md"
+    summary.write_text("| stage | kernel | source | sha256 | launches | MB per launch |\n|---|---|---|---|---|---|\n"
+                       f"| sweep_y | `SweepYStream<float>` | k.cu | {sha} | 2 | 80.5 |\n")
+    assert bench.ncu_traffic("sweep_y", "SweepYStream<float>", str(summary), str(tmp_path)) == 80.5e6
+    assert bench.ncu_traffic("sweep_y", "SweepZY<float>", str(summary), str(tmp_path)) is None
+    assert bench.ncu_traffic("tri_y", "SweepYStream<float>", str(summary), str(tmp_path)) is None
+    src.write_text("kernel source v2\n")
+    assert bench.ncu_traffic("sweep_y", "SweepYStream<float>", str(summary), str(tmp_path)) is None
+    assert bench.stage_kernel("sweep_y", {"sweep_y": 1}, "mixed") == "SweepYStream<float>"
+    assert bench.stage_kernel("tri_y", {"tri_y": 3}, "fp64") == "TriYSmem<double>"
