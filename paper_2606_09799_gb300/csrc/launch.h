@@ -139,7 +139,7 @@ void launch_slip(const Geo& g, const Surf& s, const Fields<T>& f, const TagBuffe
                  DevState* ds, Exec& ex);
 
 // ---- Poisson and projection (poisson.cu) -----------------------------------
-constexpr int TRI_SEG = 16;   // rows of j per lane of the warp-cooperative wall-normal Thomas
+constexpr int TRI_SEG = 8;   // rows of j per lane of the warp-cooperative wall-normal Thomas
 template <typename T>
 struct SpecTables {
   const T* twx;          // exp(-2 pi i m / nx), m < nx, complex interleaved

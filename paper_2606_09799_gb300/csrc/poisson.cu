@@ -1073,30 +1073,30 @@ __device__ __forceinline__ void tri_y_warp(const Blk& bk, const Geo& g, const Fi
       }
     }
   }
-  C o[Rr];
   special = false;
 #pragma unroll
   for (int u = 0; u < Rr; ++u) {
+    const int j = j0 + u;
+    C o;
     if constexpr (sizeof(T) == 4) {
-      o[u].x = d2f_int(br[u], special);
-      o[u].y = d2f_int(bi[u], special);
+      o.x = d2f_int(br[u], special);
+      o.y = d2f_int(bi[u], special);
     } else {
-      o[u].x = (T)br[u];
-      o[u].y = (T)bi[u];
+      o.x = (T)br[u];
+      o.y = (T)bi[u];
     }
+    if (live && j < ny) spec[base + (long long)j * stride] = o;
   }
   if (sizeof(T) == 4 && __any_sync(FULL, special)) {
+    // a value outside the normal binary32 range: store the hardware results
 #pragma unroll
     for (int u = 0; u < Rr; ++u) {
-      o[u].x = (T)br[u];
-      o[u].y = (T)bi[u];
+      const int j = j0 + u;
+      C o;
+      o.x = (T)br[u];
+      o.y = (T)bi[u];
+      if (live && j < ny) spec[base + (long long)j * stride] = o;
     }
-  }
-#pragma unroll
-  for (int u = 0; u < Rr; ++u) {
-    const int j = j0 + u;
-    if (!live || j >= ny) continue;
-    spec[base + (long long)j * stride] = o[u];
   }
 }
 template <typename T, int L>
@@ -1367,15 +1367,18 @@ void launch_poisson(const Geo& g, const Fields<T>& f, const TagBuffers& b, const
   // threads per block of the shared-memory variant: its FP64 forward values
   // (8 B per row and system) must fit 160 KB
   const int tsm = 64ll * 8 * sh.ny <= 160 * 1024 ? 64 : (32ll * 8 * sh.ny <= 160 * 1024 ? 32 : 0);
-  int tri = tu.tri_y == 2 || sh.ny > 32 * 16 ? 2 : 1;
+  int tri = tu.tri_y == 2 || sh.ny > 32 * TRI_SEG ? 2 : 1;
   if (tu.tri_y == 3 && tsm > 0) tri = 3;
   auto tri_solve = [&]() {
     if (tri == 3) {
       ex.launch(dim3((unsigned)((2 * tlines + tsm - 1) / tsm)), dim3(tsm), (size_t)tsm * 8 * sh.ny,
                 TriYSmem<T>{g, f, tb.cp, tb.inv});
-    } else if (tri == 1 && sh.ny <= 8 * 16) {
+    } else if (tri == 1 && sh.ny <= 8 * TRI_SEG) {
       const long long warps = (long long)((g.nkx + 3) / 4) * g.nz;
       ex.launch(dim3((unsigned)((warps * 32 + 127) / 128)), dim3(128), 0, TriYWarp<T, 8>{g, f, tb.cp, tb.inv, tb.segf, tb.segb});
+    } else if (tri == 1 && sh.ny <= 16 * TRI_SEG) {
+      const long long warps = (long long)((g.nkx + 1) / 2) * g.nz;
+      ex.launch(dim3((unsigned)((warps * 32 + 127) / 128)), dim3(128), 0, TriYWarp<T, 16>{g, f, tb.cp, tb.inv, tb.segf, tb.segb});
     } else if (tri == 1) {
       const long long warps = (long long)g.nkx * g.nz;
       ex.launch(dim3((unsigned)((warps * 32 + 127) / 128)), dim3(128), 0, TriYWarp<T, 32>{g, f, tb.cp, tb.inv, tb.segf, tb.segb});
