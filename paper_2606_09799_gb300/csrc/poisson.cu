@@ -651,15 +651,15 @@ __device__ __forceinline__ void fft_plane_fwd(const Blk& bk, const Geo& g, const
       S[(k0 + 1) * nkx + kx] = Xb;
     }
   }
-  // z: cz columns at a time, strided lines in the work buffers, to global
+  // z: cz columns at a time (any cz: the host balances the chunks), strided
+  // lines in the work buffers, to global
   C* spec = reinterpret_cast<C*>(f.spec);
-  const int lcz = __ffs(cz) - 1;
   const unsigned mcz = magic_div_dev(cz);
   for (int kx0 = 0; kx0 < nkx; kx0 += cz) {
     const int w = min(cz, nkx - kx0);
     __syncthreads();
     for (int t = threadIdx.x; t < nz * cz; t += blockDim.x) {
-      const int k = t >> lcz, c = t & (cz - 1);
+      const int k = (int)fdiv((unsigned)t, mcz), c = t - k * cz;
       C z;
       z.x = z.y = (T)0;
       if (c < w) z = S[k * nkx + kx0 + c];
@@ -668,7 +668,7 @@ __device__ __forceinline__ void fft_plane_fwd(const Blk& bk, const Geo& g, const
     const int res = fft_lines<T, false>(bufa, bufb, cz, pz, reinterpret_cast<const C*>(twz), cz, 1, mcz);
     const C* out = res == 0 ? bufa : bufb;
     for (int t = threadIdx.x; t < nz * cz; t += blockDim.x) {
-      const int k = t >> lcz, c = t & (cz - 1);
+      const int k = (int)fdiv((unsigned)t, mcz), c = t - k * cz;
       if (c < w) spec[((long long)k * ny + j) * nkx + kx0 + c] = out[t];
     }
   }
@@ -705,13 +705,12 @@ __device__ __forceinline__ void fft_plane_inv(const Blk& bk, const Geo& g, const
   const int j = bk.x;
   const C* spec = reinterpret_cast<const C*>(f.spec);
   // z inverse: cz columns at a time from global into S
-  const int lcz = __ffs(cz) - 1;
   const unsigned mcz = magic_div_dev(cz);
   for (int kx0 = 0; kx0 < nkx; kx0 += cz) {
     const int w = min(cz, nkx - kx0);
     __syncthreads();
     for (int t = threadIdx.x; t < nz * cz; t += blockDim.x) {
-      const int k = t >> lcz, c = t & (cz - 1);
+      const int k = (int)fdiv((unsigned)t, mcz), c = t - k * cz;
       C z;
       z.x = z.y = (T)0;
       if (c < w) z = spec[((long long)k * ny + j) * nkx + kx0 + c];
@@ -720,7 +719,7 @@ __device__ __forceinline__ void fft_plane_inv(const Blk& bk, const Geo& g, const
     const int res = fft_lines<T, true>(bufa, bufb, cz, pz, reinterpret_cast<const C*>(twz), cz, 1, mcz);
     const C* out = res == 0 ? bufa : bufb;
     for (int t = threadIdx.x; t < nz * cz; t += blockDim.x) {
-      const int k = t >> lcz, c = t & (cz - 1);
+      const int k = (int)fdiv((unsigned)t, mcz), c = t - k * cz;
       if (c < w) S[k * nkx + kx0 + c] = out[t];
     }
   }
@@ -1392,8 +1391,14 @@ void launch_poisson(const Geo& g, const Fields<T>& f, const TagBuffers& b, const
   const long long plane_b = (long long)sh.nz * sh.nkx * (long long)sizeof(C);
   const long long wmax = (200ll * 1024 - plane_b) / (2 * (long long)sizeof(C));
   int lcp = (int)std::min<long long>(sh.nz / 2, wmax / sh.nx);
-  int czp = 64;
-  while (czp > 1 && (long long)czp * sh.nz > wmax) czp >>= 1;
+  // z columns per chunk: the fewest chunks that fit the work buffers, of
+  // equal width (65 columns of a 128^3 grid go in one chunk, not 64 + 1)
+  int czp = 1;
+  {
+    const long long cmax = std::max<long long>(1, std::min<long long>(sh.nkx, wmax / sh.nz));
+    const long long nch = (sh.nkx + cmax - 1) / cmax;
+    czp = (int)((sh.nkx + nch - 1) / nch);
+  }
   const int wbuf = std::max(lcp * sh.nx, czp * sh.nz);
   const size_t smp = (size_t)plane_b + 2ull * wbuf * sizeof(C);
   // (opt-in: on a 128^3 plate one block per plane is latency-bound and
