@@ -74,30 +74,58 @@ __device__ inline void forcing_geometry(const Geo& g, const Surf& s, unsigned ke
   ng.U = wb[0] * __ldg(s.u + c * nv + va) + wb[1] * __ldg(s.u + c * nv + vb) + wb[2] * __ldg(s.u + c * nv + vc);
 }
 
+// Probe of one forcing node (Eq. probe): point x^e = X + h N/|N|,
+// alpha = |N| / h (0 for a node on the surface, which takes U) and the wall
+// velocity U.  The surface is that of step n in every sub-stage, so the
+// step's first forcing launch computes it (geom) and stores it; the second
+// sub-stage and the no-slip error read it back.
+__device__ __forceinline__ void forcing_probe(const Geo& g, const Surf& s, const ForceNode& fn, double* __restrict__ rec,
+                                              bool geom, double xe[3], double& alpha, double& U) {
+  if (geom) {
+    NodeGeom ng;
+    forcing_geometry(g, s, fn.key, fn.tri, ng);
+    U = ng.U;
+    alpha = 0.0;
+    for (int d = 0; d < 3; ++d) xe[d] = ng.X[d];
+    if (ng.n2 != 0.0) {
+      const double nl = sqrt(ng.n2);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) xe[d] = ng.X[d] + g.h * (ng.N[d] / nl);
+      alpha = nl / g.h;
+    }
+    rec[0] = xe[0];
+    rec[1] = xe[1];
+    rec[2] = xe[2];
+    rec[3] = alpha;
+    rec[4] = U;
+  } else {
+    xe[0] = rec[0];
+    xe[1] = rec[1];
+    xe[2] = rec[2];
+    alpha = rec[3];
+    U = rec[4];
+  }
+}
+
 // Eq. new_IB for every forcing node, reading u^e from the unmodified state
 // (a snapshot: the values are written by a second kernel).
 template <typename T>
 __device__ __forceinline__ void ib_force(const Blk& bk, const Geo& g, const Surf& s, const Fields<T>& f, const ForceNode* __restrict__ flist, unsigned cap,
-                           DevState* ds) {
+                           DevState* ds, double* __restrict__ probe, bool geom) {
   const unsigned n = min(ds->nforce_c[0] + ds->nforce_c[1] + ds->nforce_c[2], cap);
   for (unsigned e = bk.x * blockDim.x + threadIdx.x; e < n; e += bk.gx * blockDim.x) {
     const ForceNode fn = flist[e];
     const int c = (int)(fn.key >> 30);
-    NodeGeom ng;
-    forcing_geometry(g, s, fn.key, fn.tri, ng);
-    double uf = ng.U;
-    if (ng.n2 != 0.0) {
-      const double nl = sqrt(ng.n2);
-      double xe[3];
-#pragma unroll
-      for (int d = 0; d < 3; ++d) xe[d] = ng.X[d] + g.h * (ng.N[d] / nl);
+    double xe[3], alpha, U;
+    forcing_probe(g, s, fn, probe + 5ull * e, geom, xe, alpha, U);
+    double uf = U;
+    if (alpha != 0.0) {
       double ue;
       if (!trilinear<T>(g, c, comp_ptr(f, c), xe, &ue)) {
         atomicOr(&ds->err, ERR_PROBE);
         ue = 0.0;
       }
-      const double alpha = nl / g.h;
-      uf = (1.0 - alpha) * ng.U + alpha * ue;
+      uf = (1.0 - alpha) * U + alpha * ue;
     }
     f.uf[e] = (T)uf;
   }
@@ -111,7 +139,9 @@ struct IbForce {
   const ForceNode* flist;
   unsigned cap;
   DevState* ds;
-  __device__ __forceinline__ void operator()(const Blk& bk) const { ib_force<T>(bk, g, s, f, flist, cap, ds); }
+  double* probe;
+  int geom;
+  __device__ __forceinline__ void operator()(const Blk& bk) const { ib_force<T>(bk, g, s, f, flist, cap, ds, probe, geom != 0); }
 };
 
 template <typename T>
@@ -135,11 +165,11 @@ struct IbScatter {
 };
 
 template <typename T>
-void launch_ib_force(const Geo& g, const Surf& s, const Fields<T>& f, const TagBuffers& b, DevState* ds,
+void launch_ib_force(const Geo& g, const Surf& s, const Fields<T>& f, const TagBuffers& b, DevState* ds, bool geom,
                      Exec& ex) {
   const dim3 gb = grid_if(s.nt > 0, dim3(scaled_blocks(g, 4096, 8, num_sms() * 4)));
   ex.mark(ST_FORCE);
-  ex.launch(gb, dim3(128), 0, IbForce<T>{g, s, f, b.flist, b.cap, ds});
+  ex.launch(gb, dim3(128), 0, IbForce<T>{g, s, f, b.flist, b.cap, ds, b.probe, geom ? 1 : 0});
   ex.launch(gb, dim3(256), 0, IbScatter<T>{f, b.flist, b.cap, ds});
 }
 
@@ -1457,7 +1487,7 @@ constexpr int SLIP_BLOCKS = 256, SLIP_THREADS = 256;   // SLIP_BLOCKS: the most 
 template <typename T>
 __device__ __forceinline__ void slip_partial(const Blk& bk, const Geo& g, const Surf& s, const Fields<T>& f,
                                                                const ForceNode* __restrict__ flist, unsigned cap,
-                                                               DevState* ds, double* partial) {
+                                                               DevState* ds, double* partial, double* __restrict__ probe) {
   __shared__ double red[3][SLIP_THREADS];
   const unsigned n = min(ds->nforce_c[0] + ds->nforce_c[1] + ds->nforce_c[2], cap);
   const unsigned per = (n + bk.gx - 1) / bk.gx;
@@ -1466,25 +1496,20 @@ __device__ __forceinline__ void slip_partial(const Blk& bk, const Geo& g, const 
   for (unsigned e = e0 + threadIdx.x; e < e1; e += SLIP_THREADS) {
     const ForceNode fn = flist[e];
     const int c = (int)(fn.key >> 30);
-    NodeGeom ng;
-    forcing_geometry(g, s, fn.key, fn.tri, ng);
+    double xe[3], alpha, U;
+    forcing_probe(g, s, fn, probe + 5ull * e, false, xe, alpha, U);
     const T* fc = comp_ptr(f, c);
     const double ux = (double)fc[fn.key & KEY_MASK] + (f.lo[c] ? (double)f.lo[c][fn.key & KEY_MASK] : 0.0);
     double uw = ux;
-    if (ng.n2 != 0.0) {
-      const double nl = sqrt(ng.n2);
-      double xe[3];
-#pragma unroll
-      for (int d = 0; d < 3; ++d) xe[d] = ng.X[d] + g.h * (ng.N[d] / nl);
+    if (alpha != 0.0) {
       double ue;
       if (!trilinear<T>(g, c, fc, xe, &ue)) {
         atomicOr(&ds->err, ERR_PROBE);
         ue = 0.0;
       }
-      const double alpha = nl / g.h;
       uw = (ux - alpha * ue) / (1.0 - alpha);
     }
-    acc[c] += fabs(uw - ng.U);
+    acc[c] += fabs(uw - U);
   }
   for (int c = 0; c < 3; ++c) red[c][threadIdx.x] = acc[c];
   __syncthreads();
@@ -1505,7 +1530,8 @@ struct SlipPartial {
   unsigned cap;
   DevState* ds;
   double* partial;
-  __device__ __forceinline__ void operator()(const Blk& bk) const { slip_partial<T>(bk, g, s, f, flist, cap, ds, partial); }
+  double* probe;
+  __device__ __forceinline__ void operator()(const Blk& bk) const { slip_partial<T>(bk, g, s, f, flist, cap, ds, partial, probe); }
 };
 
 __device__ __forceinline__ void slip_final(const Blk& bk, const double* partial, DevState* ds, int nblk) {
@@ -1530,13 +1556,13 @@ void launch_slip(const Geo& g, const Surf& s, const Fields<T>& f, const TagBuffe
                  DevState* ds, Exec& ex) {
   ex.mark(ST_SLIP);
   const int nblk = reduce_blocks(g, 8192, SLIP_BLOCKS);
-  ex.launch(grid_if(s.nt > 0, dim3(nblk)), dim3(SLIP_THREADS), 0, SlipPartial<T>{g, s, f, b.flist, b.cap, ds, partial});
+  ex.launch(grid_if(s.nt > 0, dim3(nblk)), dim3(SLIP_THREADS), 0, SlipPartial<T>{g, s, f, b.flist, b.cap, ds, partial, b.probe});
   ex.launch(grid_if(s.nt > 0, dim3(1)), dim3(32), 0, SlipFinal{partial, ds, nblk});
 }
 
 #define IBM_INST(T)                                                                                             \
   template void launch_ib_force<T>(const Geo&, const Surf&, const Fields<T>&, const TagBuffers&, DevState*,     \
-                                   Exec&);                                                                      \
+                                   bool, Exec&);                                                                      \
   template void launch_rhs<T>(const Geo&, const Fields<T>&, const TagBuffers&, const Stage&, double, double,    \
                               bool, bool, DevState*, Exec&);                                                    \
   template void launch_sweeps<T>(const Geo&, const Fields<T>&, const TagBuffers&, const SweepTables<T>&,        \

@@ -67,6 +67,7 @@ struct TagBuffers {
   unsigned long long* surv;    // (triangle << 32 | pair) sent to the exact test (capacity cap)
   unsigned* blk;               // 4 counters per compaction block
   ForceNode* flist;            // forcing nodes, grouped by component, sorted by cell
+  double* probe;               // per forcing node, this step: probe point x^e (3), alpha, wall velocity U
   unsigned* blist;             // boundary cells, sorted
   LineInfo lines;
 };
@@ -127,7 +128,7 @@ struct Fields {
 };
 
 template <typename T>
-void launch_ib_force(const Geo& g, const Surf& s, const Fields<T>& f, const TagBuffers& b, DevState* ds,
+void launch_ib_force(const Geo& g, const Surf& s, const Fields<T>& f, const TagBuffers& b, DevState* ds, bool geom,
                      Exec& ex);
 template <typename T>
 void launch_rhs(const Geo& g, const Fields<T>& f, const TagBuffers& b, const Stage& sg, double dt, double re,

@@ -448,7 +448,7 @@ static void enqueue_step(ibm_handle h, Exec& ex) {
   const int ns = stages(h->desc, sg);
   launch_tagging(g, s, h->tb, h->ds, ex);
   for (int k = 0; k < ns; ++k) {
-    launch_ib_force<T>(g, s, f, h->tb, h->ds, ex);
+    launch_ib_force<T>(g, s, f, h->tb, h->ds, k == 0, ex);
     const bool use_hp = sg[k].rho != 0.0;
     const bool write_h = (h->desc.scheme == IBM_AB_CN) || (k + 1 < ns);
     launch_rhs<T>(g, f, h->tb, sg[k], h->desc.dt, h->desc.re, use_hp, write_h, h->ds, ex);
@@ -484,17 +484,19 @@ static size_t round16(size_t b) { return (b + 15) & ~(size_t)15; }
 static ibm_status alloc_lists(ibm_handle h, unsigned cap) {
   dfree(h, h->tb.cand);
   dfree(h, h->tb.flist);
+  dfree(h, h->tb.probe);
   dfree(h, h->tb.blist);
   dfree(h, h->tb.ublist);
   dfree(h, h->tb.surv);
   dfree(h, h->uf);
   h->tb.cand = (Cand*)dalloc(h, (size_t)cap * sizeof(Cand));
   h->tb.flist = (ForceNode*)dalloc(h, (size_t)cap * sizeof(ForceNode));
+  h->tb.probe = (double*)dalloc(h, (size_t)cap * 5 * sizeof(double));
   h->tb.blist = (unsigned*)dalloc(h, (size_t)cap * sizeof(unsigned));
   h->tb.ublist = (unsigned*)dalloc(h, (size_t)cap * sizeof(unsigned));
   h->tb.surv = (unsigned long long*)dalloc(h, (size_t)cap * sizeof(unsigned long long));
   h->uf = dalloc(h, (size_t)cap * h->esize);
-  if (!h->tb.cand || !h->tb.flist || !h->tb.blist || !h->tb.ublist || !h->tb.surv || !h->uf) {
+  if (!h->tb.cand || !h->tb.flist || !h->tb.probe || !h->tb.blist || !h->tb.ublist || !h->tb.surv || !h->uf) {
     set_err(h, "device allocation of the work lists failed");
     return IBM_ERR_OOM;
   }
