@@ -627,6 +627,7 @@ __device__ __forceinline__ void fft_plane_fwd(const Blk& bk, const Geo& g, const
   for (int l0 = 0; l0 < nlines; l0 += lc) {
     const int nl = min(lc, nlines - l0);
     __syncthreads();
+#pragma unroll 4
     for (int t = threadIdx.x; t < nl * nx; t += blockDim.x) {
       const int l = t / nx, i = t - l * nx;
       const int k0 = 2 * (l0 + l);
@@ -667,6 +668,7 @@ __device__ __forceinline__ void fft_plane_fwd(const Blk& bk, const Geo& g, const
     }
     const int res = fft_lines<T, false>(bufa, bufb, cz, pz, reinterpret_cast<const C*>(twz), cz, 1, mcz);
     const C* out = res == 0 ? bufa : bufb;
+#pragma unroll 4
     for (int t = threadIdx.x; t < nz * cz; t += blockDim.x) {
       const int k = (int)fdiv((unsigned)t, mcz), c = t - k * cz;
       if (c < w) spec[((long long)k * ny + j) * nkx + kx0 + c] = out[t];
@@ -709,6 +711,7 @@ __device__ __forceinline__ void fft_plane_inv(const Blk& bk, const Geo& g, const
   for (int kx0 = 0; kx0 < nkx; kx0 += cz) {
     const int w = min(cz, nkx - kx0);
     __syncthreads();
+#pragma unroll 4
     for (int t = threadIdx.x; t < nz * cz; t += blockDim.x) {
       const int k = (int)fdiv((unsigned)t, mcz), c = t - k * cz;
       C z;
@@ -744,6 +747,7 @@ __device__ __forceinline__ void fft_plane_inv(const Blk& bk, const Geo& g, const
     }
     const int res = fft_lines<T, true>(bufa, bufb, nl, px, reinterpret_cast<const C*>(twx));
     const C* out = res == 0 ? bufa : bufb;
+#pragma unroll 4
     for (int t = threadIdx.x; t < nl * nx; t += blockDim.x) {
       const int l = t / nx, i = t - l * nx;
       const int k0 = 2 * (l0 + l);
