@@ -404,16 +404,27 @@ struct QEnergyFinal {
 // ---------------------------------------------------------------------------
 // (H[a] + L[a]) - (H[b] + L[b]) times (ih + il), as a big part and a small
 // correction whose sum carries the product to ~FP32^2 relative accuracy
-template <typename T>
-__device__ __forceinline__ void pair_diff(const T* H, const T* L, long long a, long long b, float ih, float il,
-                                          float& big, float& small) {
+// (a - b) * (ih + il) for pairs a = (ha, la), b = (hb, lb), as a pair
+__device__ __forceinline__ void pair_diff_v(float ha, float la, float hb, float lb, float ih, float il, float& big,
+                                            float& small) {
   float s, e, p, pe;
-  two_sum((float)H[a], -(float)H[b], s, e);
-  e += (float)L[a] - (float)L[b];
+  two_sum(ha, -hb, s, e);
+  e += la - lb;
   two_prod(s, ih, p, pe);
   big = p;
   small = pe + e * ih + s * il;
 }
+
+// Projection coefficients (Eqs. projection, update_pressure).
+template <typename T>
+struct ProjCoef {
+  T cx, cy, cz;          // alpha dt / d
+  T bx, by, bz;          // alpha dt / (2 Re d^2)
+};
+
+// One face of the projected state held as a (hi, lo) pair: the projection's
+// FP32 gradient g subtracted without rounding it away.
+__device__ __forceinline__ void proj_face(float& hi, float& lo, float g) { ff_add(hi, lo, -g); }
 
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
@@ -421,13 +432,14 @@ __device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(
 __device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
 
 // Right-hand side of Eq. elliptic_mod at cell (i, j, k), scaled by
-// 1/(alpha dt nx nz): mode 0 from the provisional state (bulk type), mode 1
+// 1/(alpha dt nx nz): mode 0 from the provisional state (bulk type), mode 3
 // the correction solve's rhs from the projected (hi, lo) state in pair
-// arithmetic; 0 on boundary cells when q is on (q_B = D uhat).
+// arithmetic (the state u' = uhat - G phi is formed at the cell's faces
+// here); 0 on boundary cells when q is on (q_B = D uhat).
 template <typename T>
 __device__ __forceinline__ T poisson_rhs(const Geo& g, const Fields<T>& f, const unsigned* __restrict__ flags32,
-                                         const DevState* ds, int s, int use_q, double scale, int mode, T qf, T qa,
-                                         T qb, int i, int j, int k) {
+                                         const DevState* ds, int s, int use_q, double scale, int mode,
+                                         const ProjCoef<T>& cf, T qf, T qa, T qb, int i, int j, int k) {
   const int n = g.nx, ny = g.ny;
   const long long pu = (long long)ny * n, pv = (long long)(ny + 1) * n;
   const T sc = (T)scale, idx = (T)g.idx, idy = (T)g.idy, idz = (T)g.idz;
@@ -437,14 +449,36 @@ __device__ __forceinline__ T poisson_rhs(const Geo& g, const Fields<T>& f, const
   const long long cell = r0 + i;
   const unsigned fl = (flags32[cell >> 2] >> (8 * (cell & 3))) & 0xFFu;
   T r = (T)0;
-  if (mode == 1) {
+  if (mode == 3) {
     if (!(use_q && (fl & FLAG_B))) {
       const long long v0 = (long long)k * pv + (long long)j * n + i;
       const long long wk = (long long)kp * pu + (long long)j * n + i;
       float bx, sx, by, sy, bz, sz, a1, e1, a2, e2, a3, e3;
-      pair_diff(f.u, f.lo[0], r0 + ip, cell, (float)f.idh[0][0], (float)f.idh[0][1], bx, sx);
-      pair_diff(f.v, f.lo[1], v0 + n, v0, (float)f.idh[1][0], (float)f.idh[1][1], by, sy);
-      pair_diff(f.w, f.lo[2], wk, cell, (float)f.idh[2][0], (float)f.idh[2][1], bz, sz);
+      {
+        // the faces of the projected state u' = uhat - G phi formed here, with
+        // the projection's own arithmetic (FP32 gradient, pair update), so the
+        // first projection need not write u'
+        const int im = i == 0 ? n - 1 : i - 1;
+        const int km = k == 0 ? g.nz - 1 : k - 1;
+        const long long rkm = (long long)km * pu + (long long)j * n, rkp = (long long)kp * pu + (long long)j * n;
+        const T* __restrict__ ph = f.phi;
+        const float p0 = (float)ph[cell];
+        float uh0 = (float)f.u[cell], ul0 = (float)f.lo[0][cell];
+        float uh1 = (float)f.u[r0 + ip], ul1 = (float)f.lo[0][r0 + ip];
+        proj_face(uh0, ul0, (float)(cf.cx * ((T)p0 - ph[r0 + im])));
+        proj_face(uh1, ul1, (float)(cf.cx * (ph[r0 + ip] - (T)p0)));
+        float vh0 = (float)f.v[v0], vl0 = (float)f.lo[1][v0];
+        float vh1 = (float)f.v[v0 + n], vl1 = (float)f.lo[1][v0 + n];
+        if (j > 0) proj_face(vh0, vl0, (float)(cf.cy * ((T)p0 - ph[cell - n])));
+        if (j + 1 < ny) proj_face(vh1, vl1, (float)(cf.cy * (ph[cell + n] - (T)p0)));
+        float wh0 = (float)f.w[cell], wl0 = (float)f.lo[2][cell];
+        float wh1 = (float)f.w[wk], wl1 = (float)f.lo[2][wk];
+        proj_face(wh0, wl0, (float)(cf.cz * ((T)p0 - ph[rkm + i])));
+        proj_face(wh1, wl1, (float)(cf.cz * (ph[rkp + i] - (T)p0)));
+        pair_diff_v(uh1, ul1, uh0, ul0, (float)f.idh[0][0], (float)f.idh[0][1], bx, sx);
+        pair_diff_v(vh1, vl1, vh0, vl0, (float)f.idh[1][0], (float)f.idh[1][1], by, sy);
+        pair_diff_v(wh1, wl1, wh0, wl0, (float)f.idh[2][0], (float)f.idh[2][1], bz, sz);
+      }
       two_sum(bx, by, a1, e1);
       two_sum(a1, bz, a2, e2);
       // the target q of the first solve: uniform (an FP32 pair) or the
@@ -472,12 +506,13 @@ __device__ __forceinline__ T poisson_rhs(const Geo& g, const Fields<T>& f, const
 }
 
 // mode 0: rhs = (D uhat - q)/(alpha dt) from the (hi part of the) state;
-// mode 1: rhs of the correction solve, (D u' - q_F)/(alpha dt) on fluid
-// cells from the projected state held as (hi, lo) pairs, in pair arithmetic
+// mode 3: rhs of the correction solve, (D u' - q_F)/(alpha dt) on fluid
+// cells from the projected state u' = uhat - G phi as (hi, lo) pairs, in
+// pair arithmetic
 template <typename T>
 __device__ __forceinline__ void fft_x_fwd(const Blk& bk, const Geo& g, const Fields<T>& f, const unsigned* __restrict__ flags32, const T* __restrict__ tw,
                             const FftPlan& plan, int lines_per_block, const DevState* ds, int s, int use_q,
-                            double scale, int mode) {
+                            double scale, int mode, const ProjCoef<T>& cf) {
   using C = typename Cplx<T>::type;
   extern __shared__ unsigned char smem_raw[];
   C* bufa = reinterpret_cast<C*>(smem_raw);
@@ -505,7 +540,7 @@ __device__ __forceinline__ void fft_x_fwd(const Blk& bk, const Geo& g, const Fie
 #pragma unroll
       for (int hh = 0; hh < 2; ++hh) {
         if (!ok[hh]) continue;
-        const T r = poisson_rhs<T>(g, f, flags32, ds, s, use_q, scale, mode, qf, qa, qb, i, jj[hh], kk[hh]);
+        const T r = poisson_rhs<T>(g, f, flags32, ds, s, use_q, scale, mode, cf, qf, qa, qb, i, jj[hh], kk[hh]);
         if (hh == 0) z.x = r;
         else z.y = r;
       }
@@ -545,7 +580,8 @@ struct FftXFwd {
   int use_q;
   double scale;
   int mode;
-  __device__ __forceinline__ void operator()(const Blk& bk) const { fft_x_fwd<T>(bk, g, f, flags32, tw, plan, lines_per_block, ds, s, use_q, scale, mode); }
+  ProjCoef<T> cf;
+  __device__ __forceinline__ void operator()(const Blk& bk) const { fft_x_fwd<T>(bk, g, f, flags32, tw, plan, lines_per_block, ds, s, use_q, scale, mode, cf); }
 };
 
 // inverse x transform: two half-spectra -> one complex line -> two real rows of phi
@@ -611,7 +647,8 @@ template <typename T>
 __device__ __forceinline__ void fft_plane_fwd(const Blk& bk, const Geo& g, const Fields<T>& f,
                                               const unsigned* __restrict__ flags32, const T* __restrict__ twx,
                                               const T* __restrict__ twz, const FftPlan& px, const FftPlan& pz, int wbuf,
-                                              int cz, const DevState* ds, int s, int use_q, double scale, int mode) {
+                                              int cz, const DevState* ds, int s, int use_q, double scale, int mode,
+                                              const ProjCoef<T>& cf) {
   using C = typename Cplx<T>::type;
   extern __shared__ unsigned char smem_raw[];
   const int nx = g.nx, nz = g.nz, nkx = g.nkx, ny = g.ny;
@@ -632,8 +669,8 @@ __device__ __forceinline__ void fft_plane_fwd(const Blk& bk, const Geo& g, const
       const int l = t / nx, i = t - l * nx;
       const int k0 = 2 * (l0 + l);
       C z;
-      z.x = poisson_rhs<T>(g, f, flags32, ds, s, use_q, scale, mode, qf, qa, qb, i, j, k0);
-      z.y = poisson_rhs<T>(g, f, flags32, ds, s, use_q, scale, mode, qf, qa, qb, i, j, k0 + 1);
+      z.x = poisson_rhs<T>(g, f, flags32, ds, s, use_q, scale, mode, cf, qf, qa, qb, i, j, k0);
+      z.y = poisson_rhs<T>(g, f, flags32, ds, s, use_q, scale, mode, cf, qf, qa, qb, i, j, k0 + 1);
       bufa[t] = z;
     }
     const int res = fft_lines<T, false>(bufa, bufb, nl, px, reinterpret_cast<const C*>(twx));
@@ -689,8 +726,9 @@ struct FftPlaneFwd {
   int s, use_q;
   double scale;
   int mode;
+  ProjCoef<T> cf;
   __device__ __forceinline__ void operator()(const Blk& bk) const {
-    fft_plane_fwd<T>(bk, g, f, flags32, twx, twz, px, pz, wbuf, cz, ds, s, use_q, scale, mode);
+    fft_plane_fwd<T>(bk, g, f, flags32, twx, twz, px, pz, wbuf, cz, ds, s, use_q, scale, mode, cf);
   }
 };
 
@@ -1252,17 +1290,11 @@ void launch_build_poisson_tables(const Geo& g, const double* lamx, const double*
 //   u <- uhat - alpha dt G phi   (v on the wall planes untouched)
 //   p <- p + phi - alpha dt / (2 Re) L_c phi,  L_c with Neumann walls
 // ---------------------------------------------------------------------------
-template <typename T>
-struct ProjCoef {
-  T cx, cy, cz;          // alpha dt / d
-  T bx, by, bz;          // alpha dt / (2 Re d^2)
-};
 
 // mode 0: u <- uhat - alpha dt G phi and p <- p + phi - beta L_c phi;
-// mode 1: velocity only, state as (hi, lo) pairs (first solve of the mixed
-//         path);
-// mode 2: velocity with the correction phi2 (pairs), pressure with
-//         phi + phi2 (second solve of the mixed path)
+// mode 3 (mixed path): the (hi, lo) state takes the FP32 gradient of phi,
+//         then that of the correction phi2, each subtracted as a pair update;
+//         the pressure takes phi + phi2
 template <typename T>
 __device__ __forceinline__ void project(const Blk& bk, const Geo& g, const Fields<T>& f, const ProjCoef<T>& cf, int mode) {
   const int nx = g.nx, ny = g.ny, nz = g.nz;
@@ -1275,37 +1307,47 @@ __device__ __forceinline__ void project(const Blk& bk, const Geo& g, const Field
   const int kp = k + 1 == nz ? 0 : k + 1, km = k == 0 ? nz - 1 : k - 1;
   const long long r0 = (long long)k * pu + (long long)j * nx;
   const long long rkm = (long long)km * pu + (long long)j * nx, rkp = (long long)kp * pu + (long long)j * nx;
-  const T* __restrict__ ph = mode == 2 ? f.phi2 : f.phi;
+  const T* __restrict__ ph = f.phi;
   const T c0 = ph[r0 + i];
   const T gx = cf.cx * (c0 - ph[r0 + im]);
   const T gz = cf.cz * (c0 - ph[rkm + i]);
   const T gy = j > 0 ? cf.cy * (c0 - ph[r0 - nx + i]) : (T)0;
   const long long vi = (long long)k * pv + (long long)j * nx + i;
-  if (mode == 0) {
-    f.u[r0 + i] -= gx;
-    f.w[r0 + i] -= gz;
-    if (j > 0) f.v[vi] -= gy;
-  } else {
+  if (mode == 3) {
+    // both projections of the mixed path in turn on the (hi, lo) state held
+    // since the provisional step: G phi of the first solve, then G phi2 of
+    // the correction (the same arithmetic as modes 1 and 2 one after the other)
+    const T* __restrict__ p2 = f.phi2;
+    const T d0 = p2[r0 + i];
+    const T hx = cf.cx * (d0 - p2[r0 + im]);
+    const T hz = cf.cz * (d0 - p2[rkm + i]);
+    const T hy = j > 0 ? cf.cy * (d0 - p2[r0 - nx + i]) : (T)0;
     float hi = (float)f.u[r0 + i], lo = (float)f.lo[0][r0 + i];
     ff_add(hi, lo, -(float)gx);
+    ff_add(hi, lo, -(float)hx);
     f.u[r0 + i] = (T)hi;
     f.lo[0][r0 + i] = (T)lo;
     hi = (float)f.w[r0 + i];
     lo = (float)f.lo[2][r0 + i];
     ff_add(hi, lo, -(float)gz);
+    ff_add(hi, lo, -(float)hz);
     f.w[r0 + i] = (T)hi;
     f.lo[2][r0 + i] = (T)lo;
     if (j > 0) {
       hi = (float)f.v[vi];
       lo = (float)f.lo[1][vi];
       ff_add(hi, lo, -(float)gy);
+      ff_add(hi, lo, -(float)hy);
       f.v[vi] = (T)hi;
       f.lo[1][vi] = (T)lo;
     }
+  } else {
+    f.u[r0 + i] -= gx;
+    f.w[r0 + i] -= gz;
+    if (j > 0) f.v[vi] -= gy;
   }
-  if (mode == 1) return;
   // pressure update with the whole pseudo-pressure
-  auto PH = [&](long long id) { return mode == 2 ? f.phi[id] + f.phi2[id] : f.phi[id]; };
+  auto PH = [&](long long id) { return mode == 3 ? f.phi[id] + f.phi2[id] : f.phi[id]; };
   const T q0 = PH(r0 + i);
   const T pw = PH(r0 + im), pe = PH(r0 + ip), pb = PH(rkm + i), pf = PH(rkp + i);
   const T up = j + 1 < ny ? PH(r0 + nx + i) - q0 : (T)0;
@@ -1427,17 +1469,17 @@ void launch_poisson(const Geo& g, const Fields<T>& f, const TagBuffers& b, const
     ex.launch(xgrid, xblk, smx, FftXInv<T>{g, f, tb.twx, px, lpb, out});
   };
   // forward x (and z, fused per plane) with the right-hand side of Eq. elliptic_mod
-  auto forward = [&](int mode) {
-    if (plane)
-      ex.launch(dim3(g.ny), dim3(1024), smp,
-                FftPlaneFwd<T>{g, f, b.flags32, tb.twx, tb.twz, px, pz, wbuf, czp, ds, sg.s, use_q, scale, mode});
-    else
-      ex.launch(xgrid, xblk, smx, FftXFwd<T>{g, f, b.flags32, tb.twx, px, lpb, ds, sg.s, use_q, scale, mode});
-  };
   const double adt = sg.alp * dt, bb = adt / (2.0 * re);
   ProjCoef<T> cf;
   cf.cx = (T)(adt * g.idx); cf.cy = (T)(adt * g.idy); cf.cz = (T)(adt * g.idz);
   cf.bx = (T)(bb * g.idx * g.idx); cf.by = (T)(bb * g.idy * g.idy); cf.bz = (T)(bb * g.idz * g.idz);
+  auto forward = [&](int mode) {
+    if (plane)
+      ex.launch(dim3(g.ny), dim3(1024), smp,
+                FftPlaneFwd<T>{g, f, b.flags32, tb.twx, tb.twz, px, pz, wbuf, czp, ds, sg.s, use_q, scale, mode, cf});
+    else
+      ex.launch(xgrid, xblk, smx, FftXFwd<T>{g, f, b.flags32, tb.twx, px, lpb, ds, sg.s, use_q, scale, mode, cf});
+  };
   const dim3 pgrid((g.nx + 31) / 32, (g.ny + 3) / 4, g.nz), pblk(32, 4);
   ex.mark(ST_FFT_X_FWD);
   forward(0);
@@ -1447,14 +1489,15 @@ void launch_poisson(const Geo& g, const Fields<T>& f, const TagBuffers& b, const
     ex.launch(pgrid, pblk, 0, Project<T>{g, f, cf, 0});
     return;
   }
-  // mixed path: project with the FP32 solve, then solve again for the
-  // residual divergence of the projected (hi, lo) state and correct
-  ex.mark(ST_PROJECT);
-  ex.launch(pgrid, pblk, 0, Project<T>{g, f, cf, 1});
+  // mixed path: solve again for the residual divergence of the projected
+  // (hi, lo) state u' = uhat - G phi (formed face by face inside the
+  // right-hand side, mode 3), then apply both projections and the pressure
+  // update in one pass
   ex.mark(ST_CORRECT);
-  forward(1);
+  forward(3);
   solve_rest(f.phi2, false);
-  ex.launch(pgrid, pblk, 0, Project<T>{g, f, cf, 2});
+  ex.mark(ST_PROJECT);
+  ex.launch(pgrid, pblk, 0, Project<T>{g, f, cf, 3});
 }
 
 template <typename T>
