@@ -609,7 +609,8 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["mixed", "fp64"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
+                    help="headline path: mixed (FP32 bulk, FP64 tagging, tridiagonal and correction) or fp64")
     ap.add_argument("--only-headline", action="store_true", help="skip the other precision's run")
     ap.add_argument("--profile-steps", type=int, default=5)
     ap.add_argument("--cpu-steps", type=int, default=10)
