@@ -465,16 +465,16 @@ __device__ __forceinline__ T poisson_rhs(const Geo& g, const Fields<T>& f, const
         const float p0 = (float)ph[cell];
         float uh0 = (float)f.u[cell], ul0 = (float)f.lo[0][cell];
         float uh1 = (float)f.u[r0 + ip], ul1 = (float)f.lo[0][r0 + ip];
-        proj_face(uh0, ul0, (float)(cf.cx * ((T)p0 - ph[r0 + im])));
-        proj_face(uh1, ul1, (float)(cf.cx * (ph[r0 + ip] - (T)p0)));
+        proj_face(uh0, ul0, (float)mul_rn(cf.cx, (T)p0 - ph[r0 + im]));
+        proj_face(uh1, ul1, (float)mul_rn(cf.cx, ph[r0 + ip] - (T)p0));
         float vh0 = (float)f.v[v0], vl0 = (float)f.lo[1][v0];
         float vh1 = (float)f.v[v0 + n], vl1 = (float)f.lo[1][v0 + n];
-        if (j > 0) proj_face(vh0, vl0, (float)(cf.cy * ((T)p0 - ph[cell - n])));
-        if (j + 1 < ny) proj_face(vh1, vl1, (float)(cf.cy * (ph[cell + n] - (T)p0)));
+        if (j > 0) proj_face(vh0, vl0, (float)mul_rn(cf.cy, (T)p0 - ph[cell - n]));
+        if (j + 1 < ny) proj_face(vh1, vl1, (float)mul_rn(cf.cy, ph[cell + n] - (T)p0));
         float wh0 = (float)f.w[cell], wl0 = (float)f.lo[2][cell];
         float wh1 = (float)f.w[wk], wl1 = (float)f.lo[2][wk];
-        proj_face(wh0, wl0, (float)(cf.cz * ((T)p0 - ph[rkm + i])));
-        proj_face(wh1, wl1, (float)(cf.cz * (ph[rkp + i] - (T)p0)));
+        proj_face(wh0, wl0, (float)mul_rn(cf.cz, (T)p0 - ph[rkm + i]));
+        proj_face(wh1, wl1, (float)mul_rn(cf.cz, ph[rkp + i] - (T)p0));
         pair_diff_v(uh1, ul1, uh0, ul0, (float)f.idh[0][0], (float)f.idh[0][1], bx, sx);
         pair_diff_v(vh1, vl1, vh0, vl0, (float)f.idh[1][0], (float)f.idh[1][1], by, sy);
         pair_diff_v(wh1, wl1, wh0, wl0, (float)f.idh[2][0], (float)f.idh[2][1], bz, sz);
@@ -1307,21 +1307,36 @@ __device__ __forceinline__ void project(const Blk& bk, const Geo& g, const Field
   const int kp = k + 1 == nz ? 0 : k + 1, km = k == 0 ? nz - 1 : k - 1;
   const long long r0 = (long long)k * pu + (long long)j * nx;
   const long long rkm = (long long)km * pu + (long long)j * nx, rkp = (long long)kp * pu + (long long)j * nx;
+  // every pseudo-pressure value of the stencil first: the field stores below
+  // could alias them for the compiler, which would reload them
   const T* __restrict__ ph = f.phi;
-  const T c0 = ph[r0 + i];
-  const T gx = cf.cx * (c0 - ph[r0 + im]);
-  const T gz = cf.cz * (c0 - ph[rkm + i]);
-  const T gy = j > 0 ? cf.cy * (c0 - ph[r0 - nx + i]) : (T)0;
+  const T a0 = ph[r0 + i], aw = ph[r0 + im], ae = ph[r0 + ip], ab = ph[rkm + i], af = ph[rkp + i];
+  const T as = j > 0 ? ph[r0 - nx + i] : a0, an = j + 1 < ny ? ph[r0 + nx + i] : a0;
+  T b0 = (T)0, bw = (T)0, be = (T)0, bb = (T)0, bf = (T)0, bs = (T)0, bn = (T)0;
+  if (mode == 3) {
+    const T* __restrict__ p2 = f.phi2;
+    b0 = p2[r0 + i];
+    bw = p2[r0 + im];
+    be = p2[r0 + ip];
+    bb = p2[rkm + i];
+    bf = p2[rkp + i];
+    bs = j > 0 ? p2[r0 - nx + i] : b0;
+    bn = j + 1 < ny ? p2[r0 + nx + i] : b0;
+  }
+  // every gradient rounded on its own (no contraction into the update that
+  // follows: the pair updates must stay error-free, and the single and the
+  // batched kernels must round alike)
+  const T gx = mul_rn(cf.cx, a0 - aw);
+  const T gz = mul_rn(cf.cz, a0 - ab);
+  const T gy = j > 0 ? mul_rn(cf.cy, a0 - as) : (T)0;
   const long long vi = (long long)k * pv + (long long)j * nx + i;
   if (mode == 3) {
     // both projections of the mixed path in turn on the (hi, lo) state held
     // since the provisional step: G phi of the first solve, then G phi2 of
-    // the correction (the same arithmetic as modes 1 and 2 one after the other)
-    const T* __restrict__ p2 = f.phi2;
-    const T d0 = p2[r0 + i];
-    const T hx = cf.cx * (d0 - p2[r0 + im]);
-    const T hz = cf.cz * (d0 - p2[rkm + i]);
-    const T hy = j > 0 ? cf.cy * (d0 - p2[r0 - nx + i]) : (T)0;
+    // the correction, each subtracted as a pair update
+    const T hx = mul_rn(cf.cx, b0 - bw);
+    const T hz = mul_rn(cf.cz, b0 - bb);
+    const T hy = j > 0 ? mul_rn(cf.cy, b0 - bs) : (T)0;
     float hi = (float)f.u[r0 + i], lo = (float)f.lo[0][r0 + i];
     ff_add(hi, lo, -(float)gx);
     ff_add(hi, lo, -(float)hx);
@@ -1342,17 +1357,22 @@ __device__ __forceinline__ void project(const Blk& bk, const Geo& g, const Field
       f.lo[1][vi] = (T)lo;
     }
   } else {
-    f.u[r0 + i] -= gx;
-    f.w[r0 + i] -= gz;
-    if (j > 0) f.v[vi] -= gy;
+    f.u[r0 + i] = add_rn(f.u[r0 + i], -gx);
+    f.w[r0 + i] = add_rn(f.w[r0 + i], -gz);
+    if (j > 0) f.v[vi] = add_rn(f.v[vi], -gy);
   }
   // pressure update with the whole pseudo-pressure
-  auto PH = [&](long long id) { return mode == 3 ? f.phi[id] + f.phi2[id] : f.phi[id]; };
-  const T q0 = PH(r0 + i);
-  const T pw = PH(r0 + im), pe = PH(r0 + ip), pb = PH(rkm + i), pf = PH(rkp + i);
-  const T up = j + 1 < ny ? PH(r0 + nx + i) - q0 : (T)0;
-  const T dn = j > 0 ? q0 - PH(r0 - nx + i) : (T)0;
-  f.p[r0 + i] += q0 - (cf.bx * (pe - (T)2 * q0 + pw) + cf.by * (up - dn) + cf.bz * (pf - (T)2 * q0 + pb));
+  const bool two = mode == 3;
+  const T q0 = two ? a0 + b0 : a0;
+  const T pw = two ? aw + bw : aw, pe = two ? ae + be : ae, pb = two ? ab + bb : ab, pf = two ? af + bf : af;
+  const T up = j + 1 < ny ? (two ? an + bn : an) - q0 : (T)0;
+  const T dn = j > 0 ? q0 - (two ? as + bs : as) : (T)0;
+  // explicit fma / rounding: the single-simulation and the batched kernels
+  // compile this body separately and must round alike
+  const T lx = add_rn(fma((T)-2, q0, pe), pw);
+  const T lz = add_rn(fma((T)-2, q0, pf), pb);
+  const T lap = fma(cf.bx, lx, fma(cf.by, add_rn(up, -dn), mul_rn(cf.bz, lz)));
+  f.p[r0 + i] = add_rn(f.p[r0 + i], add_rn(q0, -lap));
 }
 template <typename T>
 struct Project {
