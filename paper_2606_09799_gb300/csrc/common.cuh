@@ -43,6 +43,14 @@ __host__ __device__ inline long long cidx(const Geo& g, long long i, long long j
 __host__ __device__ inline long long fidx(const Geo& g, int c, long long i, long long j, long long k) {
   return (k * planes(g, c) + j) * g.nx + i;
 }
+// Lattice indices of linear index `node` (< 2^30, the width of the node
+// keys) on a grid of nx x pl x nz points, by 32-bit division.
+__host__ __device__ inline void split3(long long node, int nx, int pl, long long& i, long long& j, long long& k) {
+  const unsigned nu = (unsigned)node, row = nu / (unsigned)nx;
+  i = (long long)(nu - row * (unsigned)nx);
+  j = (long long)(row % (unsigned)pl);
+  k = (long long)(row / (unsigned)pl);
+}
 __host__ __device__ inline int wrapi(long long i, int n) {
   long long r = i % n;
   return (int)(r < 0 ? r + n : r);

@@ -56,7 +56,8 @@ __device__ inline void forcing_geometry(const Geo& g, const Surf& s, unsigned ke
   const int c = (int)(key >> 30);
   const long long node = key & KEY_MASK;
   const int pl = planes(g, c);
-  const long long i = node % g.nx, j = (node / g.nx) % pl, k = node / ((long long)g.nx * pl);
+  long long i, j, k;
+  split3(node, g.nx, pl, i, j, k);
   const int va = __ldg(s.t + tri), vb = __ldg(s.t + s.nt + tri), vc = __ldg(s.t + 2 * (long long)s.nt + tri);
   // the triangle's constants of this step (formed by the tagging set-up)
   const TriRec* __restrict__ R = s.rec + tri;

@@ -251,7 +251,8 @@ __device__ __forceinline__ void q_partial(const Blk& bk, const Geo& g, const Fie
   double acc = 0.0;
   for (unsigned e = e0 + threadIdx.x; e < e1; e += QB_THREADS) {
     const long long cell = blist[e];
-    const long long i = cell % g.nx, j = (cell / g.nx) % g.ny, k = cell / ((long long)g.nx * g.ny);
+    long long i, j, k;
+    split3(cell, g.nx, g.ny, i, j, k);
     acc += div_at<T>(g, f.u, f.v, f.w, i, j, k);
   }
   red[threadIdx.x] = acc;

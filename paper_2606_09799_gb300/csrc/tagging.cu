@@ -38,7 +38,8 @@ __device__ __forceinline__ void tag_reset(const Blk& bk, const Geo& g, const Can
     d2min[comp_off(g, c) + node] = ~0ull;
     owner[comp_off(g, c) + node] = 0xFFFFFFFFu;
     const int pl = planes(g, c);
-    const long long i = node % g.nx, j = (node / g.nx) % pl, k = node / ((long long)g.nx * pl);
+    long long i, j, k;
+    split3(node, g.nx, pl, i, j, k);
     const long long cell = cidx(g, i, j, k);
     atomicAnd(flags32 + (cell >> 2), ~(0xFFu << (8 * (cell & 3))));
   }
@@ -485,7 +486,8 @@ __device__ __forceinline__ void tag_mark(const Blk& bk, const Geo& g, const Cand
     const long long o = comp_off(g, c) + node;
     if (cd.d2 == d2min[o] && cd.tri == owner[o]) {
       const int pl = planes(g, c);
-      const long long i = node % g.nx, j = (node / g.nx) % pl, k = node / ((long long)g.nx * pl);
+      long long i, j, k;
+      split3(node, g.nx, pl, i, j, k);
       const long long cell = cidx(g, i, j, k);
       atomicOr(flags32 + (cell >> 2), (unsigned)(1u << c) << (8 * (cell & 3)));
       atomicMin(li.x + line_x(g, c, j, k), (int)i);
@@ -522,7 +524,8 @@ __device__ __forceinline__ void tag_boundary(const Blk& bk, const Geo& g, const 
     if ((cd.key >> 30) != 0) continue;
     const long long node = cd.key & KEY_MASK;
     if (!(cd.d2 == d2min[node] && cd.tri == owner[node])) continue;
-    const long long i = node % g.nx, j = (node / g.nx) % g.ny, k = node / ((long long)g.nx * g.ny);
+    long long i, j, k;
+    split3(node, g.nx, g.ny, i, j, k);
     const long long ip = (i + 1 == g.nx) ? 0 : i + 1, kp = (k + 1 == g.nz) ? 0 : k + 1;
     const long long cell = cidx(g, i, j, k);
     const unsigned f0 = flag_of(flags32, cell);
@@ -697,27 +700,43 @@ __device__ __forceinline__ void cmp_write(const Blk& bk, const Geo& g, const uns
     pos[q] = blk[(long long)bk.x * 4 + q] + before + excl[q];
   }
   const unsigned base[3] = {ds->force_base[0], ds->force_base[1], ds->force_base[2]};
+  // (i, j, k) of the thread's first cell by one 32-bit division (node keys
+  // hold 30 bits), then stepped along its 16 consecutive cells
+  const unsigned nxu = (unsigned)g.nx, nyu = (unsigned)g.ny;
+  unsigned ci = 0, cj = 0, ck = 0;
+  if (cell0 < g.ncell) {
+    const unsigned c0 = (unsigned)cell0, row = c0 / nxu;
+    ci = c0 - row * nxu;
+    cj = row % nyu;
+    ck = row / nyu;
+  }
 #pragma unroll
   for (int m = 0; m < 16; ++m) {
-    const long long cell = cell0 + m;
-    if (!f[m]) continue;
-    const long long i = cell % g.nx, j = (cell / g.nx) % g.ny, k = cell / ((long long)g.nx * g.ny);
+    if (f[m]) {
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      if ((f[m] >> c) & 1) {
-        const unsigned slot = base[c] + pos[c]++;
-        const long long node = fidx(g, c, i, j, k);
-        if (slot < fcap) {
-          ForceNode fn;
-          fn.key = ((unsigned)c << 30) | (unsigned)node;
-          fn.tri = owner[comp_off(g, c) + node];
-          flist[slot] = fn;
+      for (int c = 0; c < 3; ++c) {
+        if ((f[m] >> c) & 1) {
+          const unsigned slot = base[c] + pos[c]++;
+          const long long node = fidx(g, c, ci, cj, ck);
+          if (slot < fcap) {
+            ForceNode fn;
+            fn.key = ((unsigned)c << 30) | (unsigned)node;
+            fn.tri = owner[comp_off(g, c) + node];
+            flist[slot] = fn;
+          }
         }
       }
+      if (f[m] & FLAG_B) {
+        const unsigned slot = pos[3]++;
+        if (slot < fcap) blist[slot] = (unsigned)(cell0 + m);
+      }
     }
-    if (f[m] & FLAG_B) {
-      const unsigned slot = pos[3]++;
-      if (slot < fcap) blist[slot] = (unsigned)cell;
+    if (++ci == nxu) {
+      ci = 0;
+      if (++cj == nyu) {
+        cj = 0;
+        ++ck;
+      }
     }
   }
 }
@@ -779,7 +798,8 @@ void launch_tagging(const Geo& g, const Surf& s, const TagBuffers& b, DevState* 
   const long long blocks = ((long long)s.nt * 32 + 127) / 128;   // one warp per triangle
   ex.launch(grid_if(live, dim3((unsigned)blocks)), dim3(128), 0, TagPairs<0>{g, s, b.cap, b.ub, b.ublist, b.surv, ds});
   ex.launch(grid_if(live, dim3((unsigned)blocks)), dim3(128), 0, TagPairs<1>{g, s, b.cap, b.ub, b.ublist, b.surv, ds});
-  ex.launch(grid_if(live, dim3(scaled_blocks(g, 8192, 8, num_sms() * 8))), dim3(128), 0,
+  // about one survivor per thread: the FP64 test is a latency chain
+  ex.launch(grid_if(live, dim3(scaled_blocks(g, 2048, 8, num_sms() * 8))), dim3(128), 0,
             TagExact{g, s, b.cand, b.cap, b.d2min, b.surv, ds});
   const dim3 gb = grid_if(live, dim3(scaled_blocks(g, 4096, 8, num_sms() * 8)));
   ex.launch(gb, dim3(256), 0, TagResolve{g, b.cand, b.cap, ds, b.d2min, b.owner});
