@@ -575,6 +575,46 @@ __device__ __forceinline__ AffMap<T> scan_down_excl(AffMap<T> m, int lane) {
   return lane == 31 ? AffMap<T>{(T)1, (T)0} : AffMap<T>{a, b};
 }
 
+// K consecutive rows q0 .. q0+K-1 of a line (rows >= n read as 0): four at
+// a time as aligned 16-byte vectors when the line and n allow (FP32, K a
+// multiple of 4), so a warp's load covers a contiguous span instead of 32
+// strided words.
+template <typename T, int K>
+__device__ __forceinline__ void load_rows(const T* __restrict__ p, int q0, int n, T (&v)[K]) {
+  if constexpr (sizeof(T) == 4 && K % 4 == 0) {
+    if ((n & 3) == 0 && (reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+#pragma unroll
+      for (int u4 = 0; u4 < K / 4; ++u4) {
+        const int q = q0 + 4 * u4;
+        const float4 x = q < n ? *reinterpret_cast<const float4*>(p + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+        v[4 * u4] = x.x;
+        v[4 * u4 + 1] = x.y;
+        v[4 * u4 + 2] = x.z;
+        v[4 * u4 + 3] = x.w;
+      }
+      return;
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < K; ++u) v[u] = q0 + u < n ? p[q0 + u] : (T)0;
+}
+template <typename T, int K>
+__device__ __forceinline__ void store_rows(T* __restrict__ p, int q0, int n, const T (&v)[K]) {
+  if constexpr (sizeof(T) == 4 && K % 4 == 0) {
+    if ((n & 3) == 0 && (reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+#pragma unroll
+      for (int u4 = 0; u4 < K / 4; ++u4) {
+        const int q = q0 + 4 * u4;
+        if (q < n) *reinterpret_cast<float4*>(p + q) = make_float4(v[4 * u4], v[4 * u4 + 1], v[4 * u4 + 2], v[4 * u4 + 3]);
+      }
+      return;
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < K; ++u)
+    if (q0 + u < n) p[q0 + u] = v[u];
+}
+
 template <typename T, int K>
 __device__ __forceinline__ void sweep_x_warp(const Blk& bk, const Geo& g, const Fields<T>& f, const unsigned* __restrict__ flags32,
                                                       const SweepTables<T>& tb, const int* __restrict__ lfirst) {
@@ -597,15 +637,19 @@ __device__ __forceinline__ void sweep_x_warp(const Blk& bk, const Geo& g, const 
     const T* __restrict__ cp = tb.cp[0];
     const T* __restrict__ zv = tb.zv[0];
     const T* __restrict__ g0 = tb.g0[0];
-#pragma unroll
-    for (int u = 0; u < K; ++u) v[u] = q0 + u < n ? R[base + q0 + u] : (T)0;
+    T ivr[K], g0r[K], cpr[K], zvr[K];
+    load_rows<T, K>(R + base, q0, n, v);
+    load_rows<T, K>(inv, q0, n, ivr);
+    load_rows<T, K>(g0, q0, n, g0r);
+    load_rows<T, K>(cp, q0, n, cpr);
+    load_rows<T, K>(zv, q0, n, zvr);
     T acc = (T)0;
     AffMap<T> mp{(T)1, (T)0};
 #pragma unroll
     for (int u = 0; u < K; ++u)
       if (q0 + u < n) {
-        const T iv = __ldg(inv + q0 + u);
-        acc += __ldg(g0 + q0 + u) * v[u];
+        const T iv = ivr[u];
+        acc += g0r[u] * v[u];
         mp = aff_then(mp, AffMap<T>{-a * iv, v[u] * iv});
       }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
@@ -614,7 +658,7 @@ __device__ __forceinline__ void sweep_x_warp(const Blk& bk, const Geo& g, const 
 #pragma unroll
     for (int u = 0; u < K; ++u)
       if (q0 + u < n) {
-        y = (v[u] - a * y) * __ldg(inv + q0 + u);
+        y = (v[u] - a * y) * ivr[u];
         v[u] = y;
       }
     const T ylast = __shfl_sync(0xFFFFFFFFu, y, (n - 1) / K);
@@ -624,7 +668,7 @@ __device__ __forceinline__ void sweep_x_warp(const Blk& bk, const Geo& g, const 
 #pragma unroll
     for (int u = K - 1; u >= 0; --u)
       if (q0 + u < n) {
-        const AffMap<T> rm = (q0 + u == n - 1) ? AffMap<T>{(T)0, v[u]} : AffMap<T>{-__ldg(cp + q0 + u), v[u]};
+        const AffMap<T> rm = (q0 + u == n - 1) ? AffMap<T>{(T)0, v[u]} : AffMap<T>{-cpr[u], v[u]};
         mp = aff_then(mp, rm);
       }
     const AffMap<T> suf = scan_down_excl(mp, lane);
@@ -632,9 +676,10 @@ __device__ __forceinline__ void sweep_x_warp(const Blk& bk, const Geo& g, const 
 #pragma unroll
     for (int u = K - 1; u >= 0; --u)
       if (q0 + u < n) {
-        yn = (q0 + u == n - 1) ? v[u] : v[u] - __ldg(cp + q0 + u) * yn;
-        R[base + q0 + u] = yn - fact * __ldg(zv + q0 + u);
+        yn = (q0 + u == n - 1) ? v[u] : v[u] - cpr[u] * yn;
+        v[u] = yn - fact * zvr[u];
       }
+    store_rows<T, K>(R + base, q0, n, v);
     return;
   }
   // ------------- forcing rows: the line rotated to start at f0 (identity)
