@@ -387,6 +387,8 @@ def gpu_arm(args):
         line["batched"] = batched
     if ab is not None:
         line["ab_cn"] = ab
+    if args.large and world == 1:
+        line["large"] = large_leg(args, dev, stream, flush)
     if args.e5_steps > 0:
         line["e5_heaving_pitching_plate"] = e5_leg(args, dev, stream)
     if "mixed" in results and "fp64" in results:
@@ -430,6 +432,54 @@ def ab_leg(args, wl, dxyz, dvel, surf, dev, stream, flush, world, tune):
     sim.close()
     return {"scheme": "AB+CN", "precision": args.precision, "value": whole_job_gcups(wl.cells, K, world, ms),
             "unit": UNIT, "ms_per_step": ms / K, "slip_l1": diag["slip_l1"]}
+
+
+def large_leg(args, dev, stream, flush):
+    """Mixed path on the two large synthetic workloads (256x192x256 channel
+    with 16 moving bodies; 512x384x512 tube with three hinged leaflets):
+    same protocol as the headline (device-resident surfaces, L2 flushed
+    between timed steps, autotuned launch shapes), with the stage times."""
+    import torch
+    from paper_2606_09799_gb300 import ibm, inputs
+
+    out = {}
+    W, K = 3, max(3, min(args.steps, 6))
+    for name in ("channel256", "leaflet512"):
+        wl = inputs.workload(name)
+        surf = [wl.surface(s) for s in range(W + K)]
+        dx = [torch.from_numpy(x).to(dev) for x, _ in surf]
+        dv = [torch.from_numpy(v).to(dev) for _, v in surf]
+        sim = ibm.Simulation(wl.nx, wl.ny, wl.nz, wl.lx, wl.ly, wl.lz, re=wl.re, dt=wl.dt, precision="mixed",
+                             stream=stream.cuda_stream)
+        if wl.initial is not None:
+            sim.set_fields(*wl.initial())
+        ibm.ibm_set_body_force(sim.h, *wl.body_force_at(0.0))
+        sim.set_surface(surf[0][0], surf[0][1], wl.tri)
+        for s in range(W):
+            sim.set_surface(dx[s], dv[s])
+            sim.step(1)
+        sim.sync()
+        tune = sim.autotune(steps=2)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        torch.cuda.synchronize()
+        for n in range(K):
+            flush.fill_(n & 0xFF)
+            ev[n][0].record(stream)
+            sim.set_surface(dx[W + n], dv[W + n])
+            sim.step(1)
+            ev[n][1].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / K
+        prof = ibm.ibm_profile_stages(sim.h, 2)
+        cells = wl.nx * wl.ny * wl.nz
+        out[name] = {"cells": cells, "triangles": int(wl.tri.shape[0]), "steps": K, "ms_per_step": ms,
+                     "value": cells / (ms / 1e3) / 1e9, "unit": UNIT, "tune": tune,
+                     "stages_ms_per_step": {k: v[0] / 2 for k, v in prof.items() if v[1] > 0},
+                     "slip_l1": sim.diag()["slip_l1"]}
+        sim.close()
+        del dx, dv
+        torch.cuda.empty_cache()
+    return out
 
 
 def max_over_ranks(ms: float, device, world: int) -> float:
@@ -619,6 +669,8 @@ def main():
                     help="keep the built-in launch shapes (no autotuning before timing)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-instances leg")
     ap.add_argument("--no-ab", action="store_true", help="skip the AB+CN leg")
+    ap.add_argument("--large", action="store_true",
+                    help="also time the 256x192x256 channel and the 512x384x512 tube (mixed path)")
     ap.add_argument("--e5-steps", type=int, default=0,
                     help="also record the no-slip error series of the heaving/pitching plate (opt-in)")
     ap.add_argument("--tune", default="", help="fixed launch shapes instead of autotuning, e.g. tri_y=3,sweep_zy=2")
