@@ -148,7 +148,7 @@ def algorithmic_bytes_per_cell(stage: str, word: int) -> float:
 TRAFFIC_SUMMARY = os.path.join(ROOT, "profiles", "traffic_plate128.md")
 
 
-def stage_kernel(stage: str, tune: dict | None, precision: str) -> str | None:
+def stage_kernel(stage: str, tune: dict | None, precision: str, ny: int = 128) -> str | None:
     """Kernel that the given launch shapes run for a stage of the 128^3 step
     (the name the ncu summaries use), or None when it is not recorded."""
     t = tune or {}
@@ -161,7 +161,9 @@ def stage_kernel(stage: str, tune: dict | None, precision: str) -> str | None:
         return f"SweepZY<{T}>"
     if stage == "tri_y":
         v = t.get("tri_y", 0)
-        return {0: f"TriYWarp<{T}, 8>", 1: f"TriYWarp<{T}, 8>", 2: f"TriY<{T}>", 3: f"TriYSmem<{T}>"}[v]
+        lanes = 8 if ny <= 64 else (16 if ny <= 128 else 32)     # 8 rows per lane
+        warp = f"TriYWarp<{T}, {lanes}>" if ny <= 256 else f"TriY<{T}>"
+        return {0: warp, 1: warp, 2: f"TriY<{T}>", 3: f"TriYSmem<{T}>"}[v]
     if stage == "fft_x_fwd":
         return f"FftPlaneFwd<{T}>" if t.get("fft_plane", 0) == 2 else f"FftXFwd<{T}>"
     if stage == "rhs":
@@ -356,7 +358,7 @@ def gpu_arm(args):
         g["share"] = g["share"] / tot_all
     top = max(groups, key=lambda k: groups[k]["share"])
     tg = groups[top]
-    kname = stage_kernel(top, head["tune"], args.precision)
+    kname = stage_kernel(top, head["tune"], args.precision, wl.ny)
     roof = {"bound": tg["bound"], "achieved": tg["achieved"], "peak": tg["peak"], "unit": tg["unit"],
             "frac": tg["frac"], "traffic": ncu_traffic(top, kname), "kernel": top, "kernel_name": kname,
             "peak_source": ("FP64 FMA-chain probe on a GB300 of this pool (of measured)" if tg["bound"] == "alu"

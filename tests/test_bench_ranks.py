@@ -76,3 +76,4 @@ def test_traffic_lookup_follows_the_kernel_source(tmp_path):
     assert bench.ncu_traffic("sweep_y", "SweepYStream<float>", str(summary), str(tmp_path)) is None
     assert bench.stage_kernel("sweep_y", {"sweep_y": 1}, "mixed") == "SweepYStream<float>"
     assert bench.stage_kernel("tri_y", {"tri_y": 3}, "fp64") == "TriYSmem<double>"
+    assert bench.stage_kernel("tri_y", {"tri_y": 0}, "mixed", 128) == "TriYWarp<float, 16>"
