@@ -440,7 +440,9 @@ def large_leg(args, dev, stream, flush):
     """Mixed path on the two large synthetic workloads (256x192x256 channel
     with 16 moving bodies; 512x384x512 tube with three hinged leaflets):
     same protocol as the headline (device-resident surfaces, L2 flushed
-    between timed steps, autotuned launch shapes), with the stage times."""
+    between timed steps, autotuned launch shapes), with the stage times.
+    The tube's pulsatile body force is held at its t = 0 value (the rate
+    does not depend on it)."""
     import torch
     from paper_2606_09799_gb300 import ibm, inputs
 
