@@ -75,7 +75,8 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        self.path = os.path.join(os.environ.get("IBM_BENCH_OUT", os.path.join(ROOT, "bench_out")),
+                                 f"clocks_rank{index}.csv")
 
     def __enter__(self):
         try:
