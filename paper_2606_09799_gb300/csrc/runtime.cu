@@ -185,6 +185,7 @@ struct ibm_grid {
   TriRec* trirec;         // per-triangle constants, rewritten every step
   int nv, nt, nv_cap, nt_cap;
   bool has_topology;
+  std::vector<int32_t> host_tri;   // host copy (AoS) of the connectivity when the caller gave one, else empty
   // graph
   cudaGraph_t graph;
   cudaGraphExec_t exec;
@@ -1246,17 +1247,16 @@ ibm_status ibm_set_surface(ibm_handle h, int nverts, const double* xyz, const do
           set_err(h, "%s", "ibm_set_surface: triangle vertex index out of range");
           return IBM_ERR_ARG;
         }
-    }
-    const int32_t* tt = tri;
-    std::vector<int32_t> tmp;
-    if (!tt) {
-      tmp.resize(3ull * ntris);
+      h->host_tri.assign(tri, tri + 3ll * ntris);
+    } else if (h->host_tri.size() != 3ull * ntris) {
+      // connectivity given on the device earlier: one read back, kept
       std::vector<int> soa(3ull * ntris);
       CK(cudaMemcpy(soa.data(), h->st, 3ull * ntris * 4, cudaMemcpyDeviceToHost));
+      h->host_tri.resize(3ull * ntris);
       for (int t = 0; t < ntris; ++t)
-        for (int m = 0; m < 3; ++m) tmp[3ull * t + m] = soa[(size_t)m * ntris + t];
-      tt = tmp.data();
+        for (int m = 0; m < 3; ++m) h->host_tri[3ull * t + m] = soa[(size_t)m * ntris + t];
     }
+    const int32_t* tt = tri ? tri : h->host_tri.data();
     unsigned long long need = candidate_bound(h->g, xyz, tt, ntris);
     if (need > 0xF0000000ull) need = 0xF0000000ull;
     if (need > h->tb.cap) {
@@ -1281,13 +1281,15 @@ ibm_status ibm_set_surface(ibm_handle h, int nverts, const double* xyz, const do
         set_err(h, "%s", "ibm_set_surface: triangle vertex index out of range");
         return IBM_ERR_ARG;
       }
-    unsigned long long need = candidate_bound(h->g, hx.data(), ht.data(), ntris) * 3 / 2;
+    h->host_tri.swap(ht);
+    unsigned long long need = candidate_bound(h->g, hx.data(), h->host_tri.data(), ntris) * 3 / 2;
     if (need > 0xF0000000ull) need = 0xF0000000ull;
     if (need > h->tb.cap) {
       CK(cudaStreamSynchronize(st));
       if (alloc_lists(h, (unsigned)need) != IBM_OK) return IBM_ERR_OOM;
     }
   }
+  if (on_device && tri && h->has_topology && ntris == h->nt) h->host_tri.clear();   // new device connectivity
   const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
   const int tb = 256;
   CK(cudaMemcpyAsync(h->stage_x, xyz, 3ull * nverts * 8, kind, st));
