@@ -39,6 +39,9 @@ typedef struct {
   int ybc;              /* 0: no-slip walls, 1: free-slip walls (tests) */
   double lx, ly, lz;
   double dx, dy, dz;
+  const double* yf;     /* ny + 1 wall-normal face positions (yf[0] = 0, yf[ny] = ly) of a
+                           non-uniform grid (Section 2: variable cell size in the wall-normal
+                           direction), or NULL for the uniform spacing dy */
 } orc_grid;
 
 /* ------------------------------------------------------------------ */
@@ -59,6 +62,22 @@ void orc_grid_init(orc_grid* g, int nx, int ny, int nz, double lx, double ly, do
   g->dx = lx / (double)nx;
   g->dy = ly / (double)ny;
   g->dz = lz / (double)nz;
+  g->yf = NULL;
+}
+
+/* Wall-normal spacings (Section 2, variable cell size in the wall-normal
+ * direction).  Cell j spans [yf[j], yf[j+1]]: height dyc(j), centre at the
+ * midpoint.  Across face j the centres are dyf(j) apart; at the walls the
+ * distance is to the mirror image of the first or last centre, so
+ * dyf(0) = dyc(0) and dyf(ny) = dyc(ny-1), where the wall ghost lives.
+ * With yf == NULL both return the uniform dy. */
+static double dyc(const orc_grid* g, long j) { return g->yf ? g->yf[j + 1] - g->yf[j] : g->dy; }
+static double ycen(const orc_grid* g, long j) { return 0.5 * (g->yf[j] + g->yf[j + 1]); }
+static double dyf(const orc_grid* g, long j) {
+  if (!g->yf) return g->dy;
+  if (j <= 0) return dyc(g, 0);
+  if (j >= g->ny) return dyc(g, g->ny - 1);
+  return ycen(g, j) - ycen(g, j - 1);
 }
 
 /* number of y-planes stored for component c (v carries both wall planes) */
@@ -481,6 +500,9 @@ void orc_rhs(const orc_grid* g, const double* u, const double* v, const double* 
   for (long k = 0; k < nz; ++k)
     for (long j = 0; j < ny; ++j)
       for (long i = 0; i < nx; ++i) {
+        /* wall-normal spacings of this row: cell height, centre distances below and above */
+        const int nun = g->yf != NULL;
+        const double hc = dyc(g, j), hs = dyf(g, j), hn = dyf(g, j + 1);
         /* ---- u at (i dx, (j+.5) dy, (k+.5) dz) ---- */
         {
           double uc_p = 0.5 * (U(i, j, k) + U(i + 1, j, k));
@@ -490,7 +512,7 @@ void orc_rhs(const orc_grid* g, const double* u, const double* v, const double* 
           double ut = (j + 1 < ny) ? 0.5 * (U(i, j, k) + U(i, j + 1, k)) : 0.0;
           double vb = 0.5 * (V(i - 1, j, k) + V(i, j, k));
           double ub = (j > 0) ? 0.5 * (U(i, j - 1, k) + U(i, j, k)) : 0.0;
-          double dvu = (vt * ut - vb * ub) / dy;
+          double dvu = (vt * ut - vb * ub) / hc;
           double wf = 0.5 * (W(i - 1, j, k + 1) + W(i, j, k + 1));
           double uf = 0.5 * (U(i, j, k) + U(i, j, k + 1));
           double wb = 0.5 * (W(i - 1, j, k) + W(i, j, k));
@@ -500,8 +522,8 @@ void orc_rhs(const orc_grid* g, const double* u, const double* v, const double* 
           double c0 = U(i, j, k);
           double ujm = (j > 0) ? U(i, j - 1, k) : gs * c0;
           double ujp = (j + 1 < ny) ? U(i, j + 1, k) : gs * c0;
-          double L = (U(i + 1, j, k) - 2.0 * c0 + U(i - 1, j, k)) / (dx * dx) +
-                     (ujp - 2.0 * c0 + ujm) / (dy * dy) +
+          double Ly = nun ? ((ujp - c0) / hn - (c0 - ujm) / hs) / hc : (ujp - 2.0 * c0 + ujm) / (dy * dy);
+          double L = (U(i + 1, j, k) - 2.0 * c0 + U(i - 1, j, k)) / (dx * dx) + Ly +
                      (U(i, j, k + 1) - 2.0 * c0 + U(i, j, k - 1)) / (dz * dz);
           double G = (P(i, j, k) - P(i - 1, j, k)) / dx;
           long id = fidx(g, 0, i, j, k);
@@ -521,7 +543,7 @@ void orc_rhs(const orc_grid* g, const double* u, const double* v, const double* 
           double wt = (j + 1 < ny) ? 0.5 * (W(i, j, k) + W(i, j + 1, k)) : 0.0;
           double vb = 0.5 * (V(i, j, k - 1) + V(i, j, k));
           double wbj = (j > 0) ? 0.5 * (W(i, j - 1, k) + W(i, j, k)) : 0.0;
-          double dvw = (vt * wt - vb * wbj) / dy;
+          double dvw = (vt * wt - vb * wbj) / hc;
           double wc_p = 0.5 * (W(i, j, k) + W(i, j, k + 1));
           double wc_m = 0.5 * (W(i, j, k - 1) + W(i, j, k));
           double dww = (wc_p * wc_p - wc_m * wc_m) / dz;
@@ -529,8 +551,8 @@ void orc_rhs(const orc_grid* g, const double* u, const double* v, const double* 
           double c0 = W(i, j, k);
           double wjm = (j > 0) ? W(i, j - 1, k) : gs * c0;
           double wjp = (j + 1 < ny) ? W(i, j + 1, k) : gs * c0;
-          double L = (W(i + 1, j, k) - 2.0 * c0 + W(i - 1, j, k)) / (dx * dx) +
-                     (wjp - 2.0 * c0 + wjm) / (dy * dy) +
+          double Ly = nun ? ((wjp - c0) / hn - (c0 - wjm) / hs) / hc : (wjp - 2.0 * c0 + wjm) / (dy * dy);
+          double L = (W(i + 1, j, k) - 2.0 * c0 + W(i - 1, j, k)) / (dx * dx) + Ly +
                      (W(i, j, k + 1) - 2.0 * c0 + W(i, j, k - 1)) / (dz * dz);
           double G = (P(i, j, k) - P(i, j, k - 1)) / dz;
           long id = fidx(g, 2, i, j, k);
@@ -548,7 +570,7 @@ void orc_rhs(const orc_grid* g, const double* u, const double* v, const double* 
           double duv = (ur * vr - ul * vl) / dx;
           double vc_p = 0.5 * (V(i, j, k) + V(i, j + 1, k));
           double vc_m = 0.5 * (V(i, j - 1, k) + V(i, j, k));
-          double dvv = (vc_p * vc_p - vc_m * vc_m) / dy;
+          double dvv = (vc_p * vc_p - vc_m * vc_m) / hs;
           double wf = 0.5 * (W(i, j - 1, k + 1) + W(i, j, k + 1));
           double vf = 0.5 * (V(i, j, k) + V(i, j, k + 1));
           double wb = 0.5 * (W(i, j - 1, k) + W(i, j, k));
@@ -556,10 +578,11 @@ void orc_rhs(const orc_grid* g, const double* u, const double* v, const double* 
           double dwv = (wf * vf - wb * vbk) / dz;
           double H = -(duv + dvv + dwv);
           double c0 = V(i, j, k);
-          double L = (V(i + 1, j, k) - 2.0 * c0 + V(i - 1, j, k)) / (dx * dx) +
-                     (V(i, j + 1, k) - 2.0 * c0 + V(i, j - 1, k)) / (dy * dy) +
+          double Ly = nun ? ((V(i, j + 1, k) - c0) / hc - (c0 - V(i, j - 1, k)) / dyc(g, j - 1)) / hs
+                          : (V(i, j + 1, k) - 2.0 * c0 + V(i, j - 1, k)) / (dy * dy);
+          double L = (V(i + 1, j, k) - 2.0 * c0 + V(i - 1, j, k)) / (dx * dx) + Ly +
                      (V(i, j, k + 1) - 2.0 * c0 + V(i, j, k - 1)) / (dz * dz);
-          double G = (P(i, j, k) - P(i, j - 1, k)) / dy;
+          double G = (P(i, j, k) - P(i, j - 1, k)) / hs;
           long id = fidx(g, 1, i, j, k);
           double r = gam * H - alp * G + (alp / re) * L + alp * fb[1];
           if (rho != 0.0) r += rho * Hv_prev[id];
@@ -649,6 +672,36 @@ void orc_sweep(const orc_grid* g, int c, int dir, double* f, const int32_t* owne
       }
       free(a);
     }
+  } else if (g->yf) {
+    /* non-uniform wall-normal spacing: the coefficients of the y part of
+     * the Laplacian of orc_rhs, row by row */
+    const double gs = (g->ybc == 0) ? -1.0 : 1.0;
+    const int j0 = (c == 1) ? 1 : 0, n = ny - j0;
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < nz; ++k) {
+      double *a = malloc(sizeof(double) * n * 5), *b = a + n, *cc = b + n, *x = cc + n, *cw = x + n;
+      for (int i = 0; i < nx; ++i) {
+        for (int m = 0; m < n; ++m) {
+          const long j = j0 + m;
+          long id = fidx(g, c, i, j, k);
+          if (owner[id] >= 0) { a[m] = 0.0; b[m] = 1.0; cc[m] = 0.0; }
+          else if (c != 1) {
+            const double sb = beta / (dyc(g, j) * dyf(g, j)), sn = beta / (dyc(g, j) * dyf(g, j + 1));
+            a[m] = -sb; b[m] = 1.0 + sb + sn; cc[m] = -sn;
+            /* ghost du_{-1} = gs du_0 at the walls folds into the diagonal */
+            if (m == 0) { b[m] -= gs * sb; a[m] = 0.0; }
+            if (m == n - 1) { b[m] -= gs * sn; cc[m] = 0.0; }
+          } else {
+            const double sb = beta / (dyf(g, j) * dyc(g, j - 1)), sn = beta / (dyf(g, j) * dyc(g, j));
+            a[m] = m == 0 ? 0.0 : -sb; b[m] = 1.0 + sb + sn; cc[m] = m == n - 1 ? 0.0 : -sn;
+          }
+          x[m] = f[id];
+        }
+        thomas(n, a, b, cc, x, cw);
+        for (int m = 0; m < n; ++m) f[fidx(g, c, i, j0 + m, k)] = x[m];
+      }
+      free(a);
+    }
   } else {
     const double off = beta / (g->dy * g->dy);
     const double gs = (g->ybc == 0) ? -1.0 : 1.0;
@@ -692,7 +745,7 @@ void orc_divergence(const orc_grid* g, const double* u, const double* v, const d
     for (long j = 0; j < ny; ++j)
       for (long i = 0; i < nx; ++i) {
         double du = (u[fidx(g, 0, wrap(i + 1, nx), j, k)] - u[fidx(g, 0, i, j, k)]) / g->dx;
-        double dv = (v[fidx(g, 1, i, j + 1, k)] - v[fidx(g, 1, i, j, k)]) / g->dy;
+        double dv = (v[fidx(g, 1, i, j + 1, k)] - v[fidx(g, 1, i, j, k)]) / dyc(g, j);
         double dw = (w[fidx(g, 2, i, j, wrap(k + 1, nz))] - w[fidx(g, 2, i, j, k)]) / g->dz;
         div[cidx(g, i, j, k)] = du + dv + dw;
       }
@@ -724,9 +777,9 @@ void orc_boundary_cells(const orc_grid* g, const int32_t* own_u, const int32_t* 
 double orc_rhs_poisson(const orc_grid* g, const double* div, const uint8_t* isb, int use_q, double adt,
                        double* rhs, double* A_out, double* VF_out) {
   const long n = (long)g->nx * g->ny * g->nz;
-  const double dV = (g->dx * g->dy) * g->dz;
   double A = 0.0, VF = 0.0;
   for (long id = 0; id < n; ++id) {
+    const double dV = (g->dx * dyc(g, (id / g->nx) % g->ny)) * g->dz;   /* cell volume */
     if (isb[id]) A += div[id] * dV;
     else VF += dV;
   }
@@ -755,7 +808,6 @@ double orc_rhs_poisson(const orc_grid* g, const double* div, const uint8_t* isb,
 void orc_q_energy(const orc_grid* g, const double* div, const uint8_t* isb, const double* p, const double* u,
                   const double* v, const double* w, double* q, double* coef) {
   const long nx = g->nx, ny = g->ny, nz = g->nz, n = nx * ny * nz;
-  const double dV = (g->dx * g->dy) * g->dz;
   double* pe = malloc(sizeof(double) * n);
   for (long k = 0; k < nz; ++k)
     for (long j = 0; j < ny; ++j)
@@ -770,6 +822,7 @@ void orc_q_energy(const orc_grid* g, const double* div, const uint8_t* isb, cons
       }
   double S0 = 0.0, S1 = 0.0, S2 = 0.0, A = 0.0, B = 0.0;
   for (long id = 0; id < n; ++id) {
+    const double dV = (g->dx * dyc(g, (id / nx) % ny)) * g->dz;   /* cell volume */
     if (isb[id]) {
       A += div[id] * dV;
       B += pe[id] * div[id] * dV;
@@ -815,8 +868,13 @@ void orc_poisson_y(const orc_grid* g, double* spec) {
       double lam = (2.0 - 2.0 * cos(2.0 * pi * kx / nx)) / (g->dx * g->dx) +
                    (2.0 - 2.0 * cos(2.0 * pi * kz / nz)) / (g->dz * g->dz);
       for (int j = 0; j < ny; ++j) {
-        a[j] = (j > 0) ? idy2 : 0.0;
-        c[j] = (j < ny - 1) ? idy2 : 0.0;
+        if (g->yf) {   /* non-uniform rows of L_c (zero flux through the walls) */
+          a[j] = (j > 0) ? 1.0 / (dyc(g, j) * dyf(g, j)) : 0.0;
+          c[j] = (j < ny - 1) ? 1.0 / (dyc(g, j) * dyf(g, j + 1)) : 0.0;
+        } else {
+          a[j] = (j > 0) ? idy2 : 0.0;
+          c[j] = (j < ny - 1) ? idy2 : 0.0;
+        }
         b[j] = -a[j] - c[j] - lam;
         long id = ((long)kz * ny + j) * nkx + kx;
         xr[j] = spec[2 * id];
@@ -828,8 +886,13 @@ void orc_poisson_y(const orc_grid* g, double* spec) {
       thomas(ny, a, b, c, xi, cw);
       if (singular) {
         double mr = 0.0, mi = 0.0;
-        for (int j = 0; j < ny; ++j) { mr += xr[j]; mi += xi[j]; }
-        mr /= ny; mi /= ny;
+        if (g->yf) {   /* volume-weighted mean */
+          for (int j = 0; j < ny; ++j) { mr += xr[j] * dyc(g, j); mi += xi[j] * dyc(g, j); }
+          mr /= g->yf[ny]; mi /= g->yf[ny];
+        } else {
+          for (int j = 0; j < ny; ++j) { mr += xr[j]; mi += xi[j]; }
+          mr /= ny; mi /= ny;
+        }
         for (int j = 0; j < ny; ++j) { xr[j] -= mr; xi[j] -= mi; }
       }
       for (int j = 0; j < ny; ++j) {
@@ -856,7 +919,7 @@ void orc_lap_c(const orc_grid* g, const double* phi, double* out) {
                     (g->dz * g->dz);
         double up = (j + 1 < ny) ? (phi[cidx(g, i, j + 1, k)] - c0) : 0.0;
         double dn = (j > 0) ? (c0 - phi[cidx(g, i, j - 1, k)]) : 0.0;
-        double ly = (up - dn) / (g->dy * g->dy);
+        double ly = g->yf ? (up / dyf(g, j + 1) - dn / dyf(g, j)) / dyc(g, j) : (up - dn) / (g->dy * g->dy);
         out[cidx(g, i, j, k)] = lx + ly + lz;
       }
 }
@@ -875,7 +938,7 @@ void orc_project(const orc_grid* g, double* u, double* v, double* w, double* p, 
         double c0 = phi[cidx(g, i, j, k)];
         u[fidx(g, 0, i, j, k)] -= adt * (c0 - phi[cidx(g, wrap(i - 1, nx), j, k)]) / g->dx;
         w[fidx(g, 2, i, j, k)] -= adt * (c0 - phi[cidx(g, i, j, wrap(k - 1, nz))]) / g->dz;
-        if (j >= 1) v[fidx(g, 1, i, j, k)] -= adt * (c0 - phi[cidx(g, i, j - 1, k)]) / g->dy;
+        if (j >= 1) v[fidx(g, 1, i, j, k)] -= adt * (c0 - phi[cidx(g, i, j - 1, k)]) / dyf(g, j);
         p[cidx(g, i, j, k)] += c0 - adt / (2.0 * re) * lapphi[cidx(g, i, j, k)];
       }
 }

@@ -59,7 +59,8 @@ def build(force: bool = False) -> str:
 class Grid(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("ybc", ctypes.c_int),
                 ("lx", ctypes.c_double), ("ly", ctypes.c_double), ("lz", ctypes.c_double),
-                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double)]
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
+                ("yf", ctypes.c_void_p)]
 
 
 _P = ctypes.c_void_p
@@ -109,9 +110,18 @@ def threads() -> int:
     return int(lib().orc_threads())
 
 
-def make_grid(nx, ny, nz, lx=1.0, ly=1.0, lz=1.0, ybc=0) -> Grid:
+def make_grid(nx, ny, nz, lx=1.0, ly=1.0, lz=1.0, ybc=0, yfaces=None) -> Grid:
+    """yfaces: ny + 1 increasing wall-normal face positions from 0 to ly
+    (Section 2: variable cell size in the wall-normal direction), or None
+    for uniform spacing."""
     g = Grid()
     lib().orc_grid_init(ctypes.byref(g), nx, ny, nz, lx, ly, lz, ybc)
+    if yfaces is not None:
+        yf = np.ascontiguousarray(yfaces, dtype=np.float64)
+        if yf.shape != (ny + 1,) or yf[0] != 0.0 or not np.all(np.diff(yf) > 0) or abs(yf[-1] - ly) > 1e-12 * ly:
+            raise ValueError("yfaces: ny + 1 increasing positions from 0 to ly")
+        g._yf_array = yf          # the grid holds the array its pointer refers to
+        g.yf = yf.ctypes.data
     return g
 
 
@@ -270,8 +280,9 @@ class OracleSim:
     """One simulation instance advanced by the plain FP64 oracle."""
 
     def __init__(self, nx, ny, nz, lx=1.0, ly=1.0, lz=1.0, re=100.0, dt=1e-3, scheme=RK2_CN, ybc=0,
-                 use_q=True):
-        self.g = make_grid(nx, ny, nz, lx, ly, lz, ybc)
+                 use_q=True, yfaces=None):
+        self.g = make_grid(nx, ny, nz, lx, ly, lz, ybc, yfaces)
+        self.nonuniform = yfaces is not None
         # use_q: 0 none, 1 uniform q_F (Eq. for q_F, mass only), 2 energy- and mass-conserving shape (App. B)
         self.re, self.dt, self.scheme, self.use_q = float(re), float(dt), scheme, int(use_q)
         g = self.g
@@ -298,6 +309,8 @@ class OracleSim:
         self.p[...] = p
 
     def set_surface(self, xyz, vel, tri):
+        if self.nonuniform and len(tri):
+            raise ValueError("immersed surfaces on a non-uniform wall-normal grid are not supported")
         self.xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
         self.vel = np.ascontiguousarray(vel, dtype=np.float64).reshape(-1, 3)
         self.tri = np.ascontiguousarray(tri, dtype=np.int32).reshape(-1, 3)

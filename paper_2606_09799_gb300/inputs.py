@@ -535,6 +535,17 @@ def heaving_pitching_plate(steps: int = 2500, dt: float = 2e-3, nq: int = 50) ->
     return Workload("heaving_plate_e5", 100, 650, 100, 2.0, 13.0, 2.0, 100.0, dt, steps, tri, surface_at)
 
 
+def stretched_faces(ny: int, ly: float = 1.0, beta: float = 1.8) -> np.ndarray:
+    """ny + 1 wall-normal face positions clustered at both walls,
+    y = ly/2 (1 + tanh(beta (2 s - 1)) / tanh(beta)), s = j / ny: a smooth
+    stretching (cells about 3x taller at mid-channel than at the walls for
+    beta = 1.8), for the non-uniform grid of Section 2."""
+    s = np.arange(ny + 1) / ny
+    y = 0.5 * ly * (1.0 + np.tanh(beta * (2.0 * s - 1.0)) / np.tanh(beta))
+    y[0], y[-1] = 0.0, ly
+    return y
+
+
 def random_fields(nx: int, ny: int, nz: int, seed: int, amp: float = 1.0):
     """Seeded smooth-ish random velocity and pressure fields (v = 0 on the
     walls) for stage-level parity tests."""
