@@ -117,6 +117,22 @@ typedef struct {
  * buffers (about 200 B per cell in FP64) do not fit. */
 ibm_status ibm_create_grid(const ibm_grid_desc* desc, void* stream, ibm_handle* out);
 
+/* Create a simulation on a non-uniform wall-normal grid (Section 2: the
+ * cells keep uniform spacings in the periodic x and z directions and take
+ * variable heights in the wall-normal direction).  y_faces: host array of
+ * ny + 1 strictly increasing face positions, y_faces[0] = 0 and
+ * y_faces[ny] = desc->ly (to 1e-12 relative); it is copied.  Cell j spans
+ * [y_faces[j], y_faces[j+1]]; u, w and p sit at the cell centres, v on the
+ * faces.  Every wall-normal operator (the explicit terms, the factorised
+ * implicit sweep, the divergence, the per-wavenumber tridiagonal of the
+ * Poisson solve with a volume-weighted zero-mean gauge, the projection and
+ * the pressure update) takes its row's spacings.  Supported for the FP64
+ * path without immersed surfaces: ibm_set_surface returns IBM_ERR_STATE, a
+ * batch refuses the handle (IBM_ERR_ARG), and a precision other than
+ * IBM_FP64 or invalid face positions return IBM_ERR_ARG. */
+ibm_status ibm_create_grid_stretched(const ibm_grid_desc* desc, const double* y_faces, void* stream,
+                                     ibm_handle* out);
+
 /* Release every device buffer of h (waits for its stream). */
 ibm_status ibm_destroy(ibm_handle h);
 

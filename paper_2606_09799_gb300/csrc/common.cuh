@@ -18,6 +18,17 @@ constexpr unsigned ERR_DEGENERATE = 16u;     // a triangle of zero area
 // forcing nodes, and whether the cell is a boundary cell (Section 3.2).
 constexpr uint8_t FLAG_U = 1, FLAG_V = 2, FLAG_W = 4, FLAG_B = 8;
 
+// Wall-normal spacings of a non-uniform grid (Section 2: variable cell size
+// in the wall-normal direction), device FP64 tables: ihc[j] = 1 / height of
+// cell j (ny); ihf[j] = 1 / distance of the centres across face j (ny + 1;
+// the wall faces measure to the mirror image of the first / last centre);
+// hc[j] = height of cell j.  All null on a uniform grid.
+struct YTab {
+  const double* ihc;
+  const double* ihf;
+  const double* hc;
+};
+
 // Grid as seen by every kernel (passed by value).
 struct Geo {
   int nx, ny, nz, nkx;
@@ -29,6 +40,7 @@ struct Geo {
   double h;                      // probe length, twice the cell diagonal (Section 3.1)
   long long ncell;               // nx*ny*nz: size of u, w, p
   long long nvf;                 // nx*(ny+1)*nz: size of v
+  YTab yt;                       // non-uniform wall-normal spacing, or null pointers
 };
 
 __host__ __device__ inline int planes(const Geo& g, int c) { return c == 1 ? g.ny + 1 : g.ny; }

@@ -194,7 +194,7 @@ struct RhsCoef {
   T fba;                // alpha, multiplying the body force read from the device state
 };
 
-template <typename T>
+template <typename T, bool NU>
 __device__ __forceinline__ void rhs(const Blk& bk, const Geo& g, const Fields<T>& f, const unsigned* __restrict__ flags32, const RhsCoef<T>& cf,
                                              int use_hp, int write_h, const DevState* ds) {
   const int nx = g.nx, ny = g.ny, nz = g.nz;
@@ -226,6 +226,10 @@ __device__ __forceinline__ void rhs(const Blk& bk, const Geo& g, const Fields<T>
     const unsigned fl = (flags32[cell >> 2] >> (8 * (cell & 3))) & 0xFFu;
     const bool jlo = j == 0, jhi = j + 1 == ny;
     const T pc = P[r0 + i];
+    // non-uniform wall-normal spacing: this row's inverse cell height and
+    // centre distances below / above (the wall ghosts at mirrored distances)
+    constexpr bool nun = NU;
+    const T ihc = nun ? (T)g.yt.ihc[j] : idy, ihs = nun ? (T)g.yt.ihf[j] : idy, ihn = nun ? (T)g.yt.ihf[j + 1] : idy;
     // ---------------- u at (i dx, (j+1/2) dy, (k+1/2) dz) ----------------
     {
       const T uc = U[r0 + i], ue = U[r0 + ip], uw = U[r0 + im];
@@ -235,12 +239,13 @@ __device__ __forceinline__ void rhs(const Blk& bk, const Geo& g, const Fields<T>
       const T adx = ((uc + ue) * (uc + ue) - (uw + uc) * (uw + uc)) * q * idx;
       const T vt = jhi ? (T)0 : (V[v1 + im] + V[v1 + i]) * (uc + un);
       const T vb = jlo ? (T)0 : (V[v0 + im] + V[v0 + i]) * (us + uc);
-      const T ady = (vt - vb) * q * idy;
+      const T ady = (vt - vb) * q * ihc;
       const T wf = (W[rkp + im] + W[rkp + i]) * (uc + uf);
       const T wb = (W[r0 + im] + W[r0 + i]) * (ub + uc);
       const T adz = (wf - wb) * q * idz;
       const T H = -(adx + ady + adz);
-      const T lap = (ue - (T)2 * uc + uw) * idx2 + (un - (T)2 * uc + us) * idy2 + (uf - (T)2 * uc + ub) * idz2;
+      const T lapy = nun ? ((un - uc) * ihn - (uc - us) * ihs) * ihc : (un - (T)2 * uc + us) * idy2;
+      const T lap = (ue - (T)2 * uc + uw) * idx2 + lapy + (uf - (T)2 * uc + ub) * idz2;
       const T G = (pc - P[r0 + im]) * idx;
       T r = cg * H - ca * G + cv * lap + fbx;
       if (use_hp) r += cr * f.Hp[0][r0 + i];
@@ -258,10 +263,11 @@ __device__ __forceinline__ void rhs(const Blk& bk, const Geo& g, const Fields<T>
       const T adx = (ue - uw) * q * idx;
       const T vt = jhi ? (T)0 : (V[vkm0 + nx + i] + V[v1 + i]) * (wc + wn);
       const T vb = jlo ? (T)0 : (V[vkm0 + i] + V[v0 + i]) * (ws + wc);
-      const T ady = (vt - vb) * q * idy;
+      const T ady = (vt - vb) * q * ihc;
       const T adz = ((wc + wf) * (wc + wf) - (wb + wc) * (wb + wc)) * q * idz;
       const T H = -(adx + ady + adz);
-      const T lap = (we - (T)2 * wc + ww) * idx2 + (wn - (T)2 * wc + ws) * idy2 + (wf - (T)2 * wc + wb) * idz2;
+      const T lapy = nun ? ((wn - wc) * ihn - (wc - ws) * ihs) * ihc : (wn - (T)2 * wc + ws) * idy2;
+      const T lap = (we - (T)2 * wc + ww) * idx2 + lapy + (wf - (T)2 * wc + wb) * idz2;
       const T G = (pc - P[rkm + i]) * idz;
       T r = cg * H - ca * G + cv * lap + fbz;
       if (use_hp) r += cr * f.Hp[2][r0 + i];
@@ -276,13 +282,14 @@ __device__ __forceinline__ void rhs(const Blk& bk, const Geo& g, const Fields<T>
       const T ue = (U[r0 - nx + ip] + U[r0 + ip]) * (vc + ve);
       const T uw = (U[r0 - nx + i] + U[r0 + i]) * (vw + vc);
       const T adx = (ue - uw) * q * idx;
-      const T ady = ((vc + vn) * (vc + vn) - (vs + vc) * (vs + vc)) * q * idy;
+      const T ady = ((vc + vn) * (vc + vn) - (vs + vc) * (vs + vc)) * q * ihs;
       const T wf = (W[rkp - nx + i] + W[rkp + i]) * (vc + vf);
       const T wb = (W[r0 - nx + i] + W[r0 + i]) * (vbk + vc);
       const T adz = (wf - wb) * q * idz;
       const T H = -(adx + ady + adz);
-      const T lap = (ve - (T)2 * vc + vw) * idx2 + (vn - (T)2 * vc + vs) * idy2 + (vf - (T)2 * vc + vbk) * idz2;
-      const T G = (pc - P[r0 - nx + i]) * idy;
+      const T lapy = nun ? ((vn - vc) * ihc - (vc - vs) * (T)g.yt.ihc[j - 1]) * ihs : (vn - (T)2 * vc + vs) * idy2;
+      const T lap = (ve - (T)2 * vc + vw) * idx2 + lapy + (vf - (T)2 * vc + vbk) * idz2;
+      const T G = (pc - P[r0 - nx + i]) * ihs;
       T r = cg * H - ca * G + cv * lap + fby;
       if (use_hp) r += cr * f.Hp[1][v0 + i];
       if (write_h) f.H[1][v0 + i] = H;
@@ -298,7 +305,7 @@ __device__ __forceinline__ void rhs(const Blk& bk, const Geo& g, const Fields<T>
     }
   }
 }
-template <typename T>
+template <typename T, bool NU>
 struct Rhs {
   static constexpr int kThreads = 128;
   Geo g;
@@ -308,7 +315,7 @@ struct Rhs {
   int use_hp;
   int write_h;
   const DevState* ds;
-  __device__ __forceinline__ void operator()(const Blk& bk) const { rhs<T>(bk, g, f, flags32, cf, use_hp, write_h, ds); }
+  __device__ __forceinline__ void operator()(const Blk& bk) const { rhs<T, NU>(bk, g, f, flags32, cf, use_hp, write_h, ds); }
 };
 
 template <typename T>
@@ -322,8 +329,11 @@ void launch_rhs(const Geo& g, const Fields<T>& f, const TagBuffers& b, const Sta
   cf.dt = (T)dt;
   cf.fba = (T)sg.alp;
   ex.mark(ST_RHS);
-  ex.launch(dim3((g.nx + 31) / 32, (g.ny + 3) / 4, g.nz), dim3(32, 4), 0,
-            Rhs<T>{g, f, b.flags32, cf, use_hp ? 1 : 0, write_h ? 1 : 0, ds});
+  const dim3 grid((g.nx + 31) / 32, (g.ny + 3) / 4, g.nz), blk(32, 4);
+  if (g.yt.ihc)   // non-uniform wall-normal spacing
+    ex.launch(grid, blk, 0, Rhs<T, true>{g, f, b.flags32, cf, use_hp ? 1 : 0, write_h ? 1 : 0, ds});
+  else
+    ex.launch(grid, blk, 0, Rhs<T, false>{g, f, b.flags32, cf, use_hp ? 1 : 0, write_h ? 1 : 0, ds});
 }
 
 // ---------------------------------------------------------------------------
@@ -1411,6 +1421,66 @@ struct SweepZStream {
   __device__ __forceinline__ void operator()(const Blk& bk) const { sweep_z_stream<T>(bk, g, f, flags32, tb, lfirst); }
 };
 
+// y-sweep on a non-uniform wall-normal grid (no immersed surface, so no
+// identity rows), one thread per line: the rows' coefficients are those of
+// the y part of the Laplacian of the right-hand side, from the spacing
+// table; the line is factorised as it is swept (c' to the scratch array)
+// and du is added to the state on the way back.
+template <typename T>
+__device__ __forceinline__ void sweep_y_stretched(const Blk& bk, const Geo& g, const Fields<T>& f, double beta) {
+  const int c = bk.y;
+  const long long t = (long long)bk.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)g.nx * g.nz) return;
+  const int i = (int)(t % g.nx), k = (int)(t / g.nx);
+  const int jj0 = c == 1 ? 1 : 0;
+  const int n = c == 1 ? g.ny - 1 : g.ny;
+  const int sn = g.nx;
+  const long long base = fidx(g, c, i, jj0, k);
+  T* __restrict__ Rl = f.R[c] + base;
+  T* __restrict__ Sl = f.scr + comp_off(g, c) + base;
+  T* __restrict__ Ul = comp_ptr(f, c) + base;
+  const double gs = g.ybc == 0 ? -1.0 : 1.0;
+  double prev = 0.0, cprev = 0.0;
+  for (int m = 0; m < n; ++m) {
+    const int j = jj0 + m;
+    double sb, sn2;
+    if (c != 1) {
+      sb = beta * g.yt.ihc[j] * g.yt.ihf[j];
+      sn2 = beta * g.yt.ihc[j] * g.yt.ihf[j + 1];
+    } else {
+      sb = beta * g.yt.ihf[j] * g.yt.ihc[j - 1];
+      sn2 = beta * g.yt.ihf[j] * g.yt.ihc[j];
+    }
+    double a = -sb, b = 1.0 + sb + sn2, cc = -sn2;
+    if (m == 0) {
+      if (c != 1) b -= gs * sb;   // wall ghost du_{-1} = gs du_0
+      a = 0.0;
+    }
+    if (m == n - 1) {
+      if (c != 1) b -= gs * sn2;
+      cc = 0.0;
+    }
+    const double den = b - a * cprev;
+    cprev = cc / den;
+    prev = ((double)Rl[m * sn] - a * prev) / den;
+    Rl[m * sn] = (T)prev;
+    Sl[m * sn] = (T)cprev;
+  }
+  double x = 0.0;
+  for (int m = n - 1; m >= 0; --m) {
+    x = (double)Rl[m * sn] - (double)Sl[m * sn] * x;
+    Ul[m * sn] = (T)((double)Ul[m * sn] + x);
+  }
+}
+template <typename T>
+struct SweepYStretched {
+  static constexpr int kThreads = 128;
+  Geo g;
+  Fields<T> f;
+  double beta;
+  __device__ __forceinline__ void operator()(const Blk& bk) const { sweep_y_stretched<T>(bk, g, f, beta); }
+};
+
 template <typename T>
 struct SweepYStream {
   static constexpr int kThreads = 128;
@@ -1499,7 +1569,12 @@ void launch_sweeps(const Geo& g, const Fields<T>& f, const TagBuffers& b, const 
               SweepZY<T>{g, f, b.flags32, tb, b.lines.z, 2});
   }
   ex.mark(ST_SWEEP_Y);
-  if (ex.tune.sweep_y == 1) {
+  if (g.yt.ihc) {
+    // non-uniform wall-normal spacing (beta from the x coefficient, beta / dx^2)
+    const long long lines = (long long)g.nx * g.nz;
+    ex.launch(dim3((unsigned)((lines + 127) / 128), 3), dim3(128), 0,
+              SweepYStretched<T>{g, f, (double)tb.off[0] * g.dx * g.dx});
+  } else if (ex.tune.sweep_y == 1) {
     const long long lines = (long long)g.nx * g.nz;
     ex.launch(dim3((unsigned)((lines + 127) / 128), 3), dim3(128), 0, SweepYStream<T>{g, f, b.flags32, tb, b.lines.y});
   } else if (!(lanes && sweep_lanes_launch(g, f, b, tb, ex, sh.ny, 1, g.nz))) {

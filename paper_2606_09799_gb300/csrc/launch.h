@@ -149,6 +149,8 @@ struct SpecTables {
   const double* inv;     // Thomas 1/pivot per (kz, j, kx)
   const double* segf;    // products of the forward multipliers per (kz, segment of TRI_SEG rows, kx)
   const double* segb;    // ... and of the backward multipliers
+  const double* pal;     // non-uniform wall-normal grid: forward multipliers (inv then holds
+                         // height / pivot and cp the c' of the height-scaled rows); null if uniform
 };
 template <typename T>
 void launch_poisson(const Geo& g, const Fields<T>& f, const TagBuffers& b, const SpecTables<T>& tb,
@@ -161,6 +163,8 @@ template <typename T>
 void launch_pressure_recon(const Geo& g, const Surf& s, const Fields<T>& f, const TagBuffers& b, DevState* ds,
                            double* q, cudaStream_t st);
 
+void launch_build_poisson_tables_nu(const Geo& g, const double* lamx, const double* lamz, double* cp, double* ivh,
+                                    double* al, cudaStream_t st);
 void launch_build_poisson_tables(const Geo& g, const double* lamx, const double* lamz, double* cp, double* inv,
                                  double* segf, double* segb,
                                  cudaStream_t st);

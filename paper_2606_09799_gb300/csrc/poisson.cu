@@ -421,6 +421,7 @@ template <typename T>
 struct ProjCoef {
   T cx, cy, cz;          // alpha dt / d
   T bx, by, bz;          // alpha dt / (2 Re d^2)
+  T adt, bb;             // alpha dt and alpha dt / (2 Re), for a non-uniform wall-normal spacing
 };
 
 // One face of the projected state held as a (hi, lo) pair: the projection's
@@ -494,7 +495,7 @@ __device__ __forceinline__ T poisson_rhs(const Geo& g, const Fields<T>& f, const
     // explicit rounding (no contraction): the single-simulation and the
     // batched kernels compile this body separately and must round alike
     const T du = mul_rn(f.u[r0 + ip] - f.u[cell], idx);
-    const T dv = mul_rn(f.v[v0 + n] - f.v[v0], idy);
+    const T dv = mul_rn(f.v[v0 + n] - f.v[v0], g.yt.ihc ? (T)g.yt.ihc[j] : idy);
     const T dw = mul_rn(f.w[(long long)kp * pu + (long long)j * n + i] - f.w[cell], idz);
     T q = qf;
     if (use_q == 2) {   // App. B shape, kept per cell for the correction solve
@@ -930,6 +931,57 @@ __device__ __forceinline__ void tri_y(const Blk& bk, const Geo& g, const Fields<
     }
   }
 }
+// Per-wavenumber Thomas on a non-uniform wall-normal grid (FP64 path, one
+// thread per real or imaginary part).  Row j of Eq. elliptic is scaled by
+// the cell height, which makes the matrix symmetric: sub = 1/hf_j,
+// super = 1/hf_{j+1}, diagonal -(sub + super) - lambda hc_j.  Tables: ivh_j =
+// hc_j / pivot_j (the scaled right-hand side folded in), al_j = -sub_j /
+// pivot_j, c'_j.  Mode (0,0) pins phi_0 = 0 (its row 0 has zero entries),
+// then removes the volume-weighted mean over j.
+template <typename T>
+__device__ __forceinline__ void tri_y_nu(const Blk& bk, const Geo& g, const Fields<T>& f, const double* __restrict__ cp,
+                                         const double* __restrict__ ivh, const double* __restrict__ al) {
+  const long long l = (long long)bk.x * blockDim.x + threadIdx.x;
+  const int nkx = g.nkx;
+  if (l >= 2ll * nkx * g.nz) return;
+  const int part = (int)(l & 1);
+  const long long mode = l >> 1;
+  const long long kx = mode % nkx, kz = mode / nkx;
+  const long long base = kz * (long long)g.ny * nkx + kx, stride = nkx;
+  T* __restrict__ sp = reinterpret_cast<T*>(f.spec);
+  const bool singular = kx == 0 && kz == 0;
+  double pr = 0.0;
+  for (int j = 0; j < g.ny; ++j) {
+    const long long id = base + (long long)j * stride;
+    pr = fma(__ldg(al + id), pr, (double)sp[2 * id + part] * __ldg(ivh + id));
+    sp[2 * id + part] = (T)pr;
+  }
+  double x = pr, sw = pr * g.yt.hc[g.ny - 1];
+  for (int j = g.ny - 2; j >= 0; --j) {
+    const long long id = base + (long long)j * stride;
+    x = (double)sp[2 * id + part] - __ldg(cp + id) * x;
+    sp[2 * id + part] = (T)x;
+    sw += x * g.yt.hc[j];
+  }
+  if (singular) {
+    const double mean = sw / g.ly;
+    for (int j = 0; j < g.ny; ++j) {
+      const long long id = base + (long long)j * stride;
+      sp[2 * id + part] = (T)((double)sp[2 * id + part] - mean);
+    }
+  }
+}
+template <typename T>
+struct TriYNU {
+  static constexpr int kThreads = 128;
+  Geo g;
+  Fields<T> f;
+  const double* cp;
+  const double* ivh;
+  const double* al;
+  __device__ __forceinline__ void operator()(const Blk& bk) const { tri_y_nu<T>(bk, g, f, cp, ivh, al); }
+};
+
 template <typename T>
 struct TriY {
   static constexpr int kThreads = 128;
@@ -1280,6 +1332,39 @@ __global__ void k_build_tri_tables(Geo g, const double* __restrict__ lamx, const
   }
 }
 
+// Pivots of the height-scaled rows of a non-uniform wall-normal grid (see
+// tri_y_nu), per (kx, kz) system.
+__global__ void k_build_tri_tables_nu(Geo g, const double* __restrict__ lamx, const double* __restrict__ lamz,
+                                      double* cp, double* ivh, double* al) {
+  const int nkx = g.nkx;
+  const long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (l >= (long long)nkx * g.nz) return;
+  const long long kx = l % nkx, kz = l / nkx;
+  const long long base = kz * (long long)g.ny * nkx + kx, stride = nkx;
+  const double lam = lamx[kx] + lamz[kz];
+  const bool singular = (kx == 0 && kz == 0);
+  double cprev = 0.0;
+  for (int j = 0; j < g.ny; ++j) {
+    double sub = j > 0 ? g.yt.ihf[j] : 0.0;
+    double sup = j < g.ny - 1 ? g.yt.ihf[j + 1] : 0.0;
+    double diag = -sub - sup - lam * g.yt.hc[j];
+    double scale = g.yt.hc[j];
+    if (singular && j == 0) { diag = 1.0; sup = 0.0; sub = 0.0; scale = 0.0; }
+    const double iv = 1.0 / (diag - sub * cprev);
+    cprev = sup * iv;
+    const long long id = base + (long long)j * stride;
+    cp[id] = cprev;
+    al[id] = -sub * iv;
+    ivh[id] = scale * iv;
+  }
+}
+
+void launch_build_poisson_tables_nu(const Geo& g, const double* lamx, const double* lamz, double* cp, double* ivh,
+                                    double* al, cudaStream_t st) {
+  const long long lines = (long long)g.nkx * g.nz;
+  k_build_tri_tables_nu<<<(unsigned)((lines + 127) / 128), 128, 0, st>>>(g, lamx, lamz, cp, ivh, al);
+}
+
 void launch_build_poisson_tables(const Geo& g, const double* lamx, const double* lamz, double* cp, double* inv,
                                  double* segf, double* segb, cudaStream_t st) {
   const long long lines = (long long)g.nkx * g.nz;
@@ -1327,9 +1412,11 @@ __device__ __forceinline__ void project(const Blk& bk, const Geo& g, const Field
   // every gradient rounded on its own (no contraction into the update that
   // follows: the pair updates must stay error-free, and the single and the
   // batched kernels must round alike)
+  const bool nun = g.yt.ihc != nullptr;   // non-uniform wall-normal spacing
   const T gx = mul_rn(cf.cx, a0 - aw);
   const T gz = mul_rn(cf.cz, a0 - ab);
-  const T gy = j > 0 ? mul_rn(cf.cy, a0 - as) : (T)0;
+  const T cyj = nun ? mul_rn(cf.adt, (T)g.yt.ihf[j]) : cf.cy;
+  const T gy = j > 0 ? mul_rn(cyj, a0 - as) : (T)0;
   const long long vi = (long long)k * pv + (long long)j * nx + i;
   if (mode == 3) {
     // both projections of the mixed path in turn on the (hi, lo) state held
@@ -1372,7 +1459,14 @@ __device__ __forceinline__ void project(const Blk& bk, const Geo& g, const Field
   // compile this body separately and must round alike
   const T lx = add_rn(fma((T)-2, q0, pe), pw);
   const T lz = add_rn(fma((T)-2, q0, pf), pb);
-  const T lap = fma(cf.bx, lx, fma(cf.by, add_rn(up, -dn), mul_rn(cf.bz, lz)));
+  T lap;
+  if (nun) {
+    const T ly = mul_rn(mul_rn(cf.bb, (T)g.yt.ihc[j]),
+                        add_rn(mul_rn(up, (T)g.yt.ihf[j + 1]), -mul_rn(dn, (T)g.yt.ihf[j])));
+    lap = fma(cf.bx, lx, add_rn(ly, mul_rn(cf.bz, lz)));
+  } else {
+    lap = fma(cf.bx, lx, fma(cf.by, add_rn(up, -dn), mul_rn(cf.bz, lz)));
+  }
   f.p[r0 + i] = add_rn(f.p[r0 + i], add_rn(q0, -lap));
 }
 template <typename T>
@@ -1436,6 +1530,10 @@ void launch_poisson(const Geo& g, const Fields<T>& f, const TagBuffers& b, const
   int tri = tu.tri_y == 2 || sh.ny > 32 * TRI_SEG ? 2 : 1;
   if (tu.tri_y == 3 && tsm > 0) tri = 3;
   auto tri_solve = [&]() {
+    if (tb.pal) {   // non-uniform wall-normal spacing
+      ex.launch(dim3((unsigned)((2 * tlines + 127) / 128)), dim3(128), 0, TriYNU<T>{g, f, tb.cp, tb.inv, tb.pal});
+      return;
+    }
     if (tri == 3) {
       ex.launch(dim3((unsigned)((2 * tlines + tsm - 1) / tsm)), dim3(tsm), (size_t)tsm * 8 * sh.ny,
                 TriYSmem<T>{g, f, tb.cp, tb.inv});
@@ -1494,6 +1592,7 @@ void launch_poisson(const Geo& g, const Fields<T>& f, const TagBuffers& b, const
   ProjCoef<T> cf;
   cf.cx = (T)(adt * g.idx); cf.cy = (T)(adt * g.idy); cf.cz = (T)(adt * g.idz);
   cf.bx = (T)(bb * g.idx * g.idx); cf.by = (T)(bb * g.idy * g.idy); cf.bz = (T)(bb * g.idz * g.idz);
+  cf.adt = (T)adt; cf.bb = (T)bb;
   auto forward = [&](int mode) {
     if (plane)
       ex.launch(dim3(g.ny), dim3(1024), smp,

@@ -176,6 +176,8 @@ struct ibm_grid {
   // tables
   void* sweep_mem[24];
   double* pcp; double* pinv; double* psegf; double* psegb; double* lamx; double* lamz;
+  double* pal;     // non-uniform wall-normal grid: forward multipliers of the Poisson rows, else null
+  double* ytab;    // non-uniform wall-normal grid: 1/heights (ny), 1/centre distances (ny+1), heights (ny)
   void* twx; void* twz;
   double tbl_off[3];
   double tbl_gam[2];
@@ -412,6 +414,7 @@ static SpecTables<T> spec_tables(ibm_handle h) {
   s.inv = h->pinv;
   s.segf = h->psegf;
   s.segb = h->psegb;
+  s.pal = h->pal;
   return s;
 }
 
@@ -1153,6 +1156,50 @@ ibm_status ibm_create_grid(const ibm_grid_desc* desc, void* stream, ibm_handle* 
   return IBM_OK;
 }
 
+ibm_status ibm_create_grid_stretched(const ibm_grid_desc* desc, const double* y_faces, void* stream,
+                                      ibm_handle* out) {
+  if (!desc || !y_faces || !out) return IBM_ERR_ARG;
+  *out = nullptr;
+  const int ny = desc->ny;
+  if (desc->precision != IBM_FP64 || ny < 4 || ny > 4096) return IBM_ERR_ARG;
+  if (y_faces[0] != 0.0 || !(fabs(y_faces[ny] - desc->ly) <= 1e-12 * desc->ly)) return IBM_ERR_ARG;
+  for (int j = 0; j < ny; ++j)
+    if (!(y_faces[j + 1] > y_faces[j])) return IBM_ERR_ARG;
+  ibm_handle h = nullptr;
+  ibm_status st = ibm_create_grid(desc, stream, &h);
+  if (st != IBM_OK) return st;
+  // spacing tables: cell heights, centre distances across faces (mirrored
+  // centres at the walls), as the oracle defines them
+  std::vector<double> t(3ull * ny + 1);
+  double* ihc = t.data();
+  double* ihf = ihc + ny;
+  double* hc = ihf + ny + 1;
+  for (int j = 0; j < ny; ++j) hc[j] = y_faces[j + 1] - y_faces[j];
+  for (int j = 0; j < ny; ++j) ihc[j] = 1.0 / hc[j];
+  ihf[0] = 1.0 / hc[0];
+  ihf[ny] = 1.0 / hc[ny - 1];
+  for (int j = 1; j < ny; ++j)
+    ihf[j] = 1.0 / (0.5 * (y_faces[j] + y_faces[j + 1]) - 0.5 * (y_faces[j - 1] + y_faces[j]));
+  h->ytab = (double*)upload_vec<double>(h, t);
+  const size_t nspec = (size_t)h->g.nz * h->g.ny * h->g.nkx;
+  h->pal = (double*)dalloc(h, nspec * 8);
+  if (!h->ytab || !h->pal) {
+    ibm_destroy(h);
+    return IBM_ERR_OOM;
+  }
+  h->g.yt.ihc = h->ytab;
+  h->g.yt.ihf = h->ytab + ny;
+  h->g.yt.hc = h->ytab + 2 * ny + 1;
+  launch_build_poisson_tables_nu(h->g, h->lamx, h->lamz, h->pcp, h->pinv, h->pal, h->user);
+  if (cudaStreamSynchronize(h->user) != cudaSuccess) {
+    ibm_destroy(h);
+    return IBM_ERR_CUDA;
+  }
+  invalidate(h);
+  *out = h;
+  return IBM_OK;
+}
+
 ibm_status ibm_destroy(ibm_handle h) {
   if (!h) return IBM_ERR_ARG;
   cudaStreamSynchronize(h->user);
@@ -1210,6 +1257,10 @@ ibm_status ibm_set_surface(ibm_handle h, int nverts, const double* xyz, const do
     return IBM_OK;
   }
   if (nverts < 3 || !xyz || !vel) return IBM_ERR_ARG;
+  if (h->g.yt.ihc) {
+    set_err(h, "%s", "ibm_set_surface: immersed surfaces on a non-uniform wall-normal grid are not supported");
+    return IBM_ERR_STATE;
+  }
   if (!tri && (!h->has_topology || ntris != h->nt)) {
     set_err(h, "%s", "ibm_set_surface: tri == NULL needs the previous connectivity with the same ntris");
     return IBM_ERR_STATE;
@@ -1547,6 +1598,7 @@ ibm_status ibm_batch_create(const ibm_handle* hs, int n, void* stream, ibm_batch
   *out = nullptr;
   for (int i = 0; i < n; ++i) {
     if (!hs[i]) return IBM_ERR_ARG;
+    if (hs[i]->g.yt.ihc) return IBM_ERR_ARG;   // a non-uniform wall-normal grid steps alone
     for (int j = 0; j < i; ++j)
       if (hs[j] == hs[i]) return IBM_ERR_ARG;
     const ibm_grid_desc &a = hs[0]->desc, &c = hs[i]->desc;

@@ -76,7 +76,7 @@ EXPORTS = ("ibm_create_grid", "ibm_destroy", "ibm_set_surface", "ibm_set_body_fo
            "ibm_set_tune", "ibm_get_tune", "ibm_autotune", "ibm_batch_create", "ibm_batch_destroy",
            "ibm_batch_step", "ibm_batch_sync", "ibm_batch_get_info", "ibm_batch_profile_stages",
            "ibm_batch_set_tune", "ibm_batch_autotune", "ibm_batch_last_error", "ibm_step_batch",
-           "ibm_get_loads", "ibm_get_pressure_recon", "ibm_check_conversions")
+           "ibm_get_loads", "ibm_get_pressure_recon", "ibm_check_conversions", "ibm_create_grid_stretched")
 
 
 def library_path() -> str:
@@ -130,6 +130,7 @@ def load(build_if_needed: bool = True):
         L.ibm_step_batch.argtypes = [P, I, I]
         L.ibm_get_loads.argtypes = [P, I, P, P, P, P, P]
         L.ibm_get_pressure_recon.argtypes = [P, P, I]
+        L.ibm_create_grid_stretched.argtypes = [ctypes.POINTER(ibm_grid_desc), P, P, ctypes.POINTER(P)]
         L.ibm_check_conversions.argtypes = [ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong),
                                             ctypes.POINTER(ctypes.c_longlong)]
         for name in EXPORTS:
@@ -176,11 +177,20 @@ def _stream_handle(stream) -> Optional[int]:
 # C entry points
 # ---------------------------------------------------------------------------
 def ibm_create_grid(nx, ny, nz, lx=1.0, ly=1.0, lz=1.0, re=100.0, dt=1e-3, scheme=IBM_RK2_CN, ybc=IBM_NOSLIP,
-                    precision=IBM_FP64, use_q=1, stream=None):
+                    precision=IBM_FP64, use_q=1, stream=None, y_faces=None):
+    """y_faces: None (uniform wall-normal spacing) or ny + 1 face positions
+    (ibm_create_grid_stretched)."""
     L = load()
     d = ibm_grid_desc(nx, ny, nz, lx, ly, lz, re, dt, scheme, ybc, precision, int(use_q))
     h = ctypes.c_void_p()
-    _check(None, L.ibm_create_grid(ctypes.byref(d), _stream_handle(stream), ctypes.byref(h)))
+    if y_faces is None:
+        _check(None, L.ibm_create_grid(ctypes.byref(d), _stream_handle(stream), ctypes.byref(h)))
+    else:
+        yf = np.ascontiguousarray(y_faces, dtype=np.float64)
+        if yf.shape != (ny + 1,):
+            raise ValueError("y_faces: ny + 1 face positions")
+        _check(None, L.ibm_create_grid_stretched(ctypes.byref(d), yf.ctypes.data_as(ctypes.c_void_p),
+                                                 _stream_handle(stream), ctypes.byref(h)))
     return h.value
 
 
@@ -431,11 +441,11 @@ class Simulation:
     """One simulation instance (a handle) with numpy-friendly accessors."""
 
     def __init__(self, nx, ny, nz, lx=1.0, ly=1.0, lz=1.0, re=100.0, dt=1e-3, scheme="rk2", ybc=0,
-                 precision="fp64", use_q=True, stream=None):
+                 precision="fp64", use_q=True, stream=None, y_faces=None):
         self.shape = (nx, ny, nz)
         sch = IBM_AB_CN if scheme == "ab" else IBM_RK2_CN
         prec = {"fp64": IBM_FP64, "mixed": IBM_MIXED, "mixed_fast": IBM_MIXED_FAST}[precision]
-        self.h = ibm_create_grid(nx, ny, nz, lx, ly, lz, re, dt, sch, ybc, prec, int(use_q), stream)
+        self.h = ibm_create_grid(nx, ny, nz, lx, ly, lz, re, dt, sch, ybc, prec, int(use_q), stream, y_faces)
         self.nt = 0
 
     def close(self):
