@@ -324,6 +324,9 @@ def gpu_arm(args):
     ab = None
     if not (args.only_headline or args.no_ab):
         ab = ab_leg(args, wl, dxyz, dvel, surf, dev, stream, flush, world, results[args.precision]["tune"])
+    stretched = None
+    if not (args.only_headline or args.no_stretched):
+        stretched = stretched_leg(args, dev, stream, flush, world)
     if rank != 0:
         return None
     head = results[args.precision]
@@ -390,6 +393,8 @@ def gpu_arm(args):
         line["batched"] = batched
     if ab is not None:
         line["ab_cn"] = ab
+    if stretched is not None:
+        line["stretched"] = stretched
     if args.large and world == 1:
         line["large"] = large_leg(args, dev, stream, flush)
     if args.e5_steps > 0:
@@ -435,6 +440,41 @@ def ab_leg(args, wl, dxyz, dvel, surf, dev, stream, flush, world, tune):
     sim.close()
     return {"scheme": "AB+CN", "precision": args.precision, "value": whole_job_gcups(wl.cells, K, world, ms),
             "unit": UNIT, "ms_per_step": ms / K, "slip_l1": diag["slip_l1"]}
+
+
+def stretched_leg(args, dev, stream, flush, world):
+    """FP64 path on a non-uniform wall-normal grid: the 128^3 channel with
+    cells clustered at both walls (tanh stretching, 3x taller at mid-channel),
+    no immersed surface, driven by a uniform body force from a seeded random
+    field; same timing protocol as the headline."""
+    import torch
+    from paper_2606_09799_gb300 import ibm, inputs
+
+    n = 128
+    K, W = max(3, min(args.steps, 20)), max(3, args.warmup)
+    yf = inputs.stretched_faces(n)
+    sim = ibm.Simulation(n, n, n, re=200.0, dt=5e-4, precision="fp64", stream=stream.cuda_stream, y_faces=yf)
+    sim.set_fields(*inputs.random_fields(n, n, n, seed=31, amp=0.1))
+    sim.set_body_force(8.0 / 200.0, 0.0, 0.0)
+    for _ in range(W):
+        sim.step(1)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    for m in range(K):
+        flush.fill_(m & 0xFF)
+        ev[m][0].record(stream)
+        sim.step(1)
+        ev[m][1].record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), dev, world)
+    prof = ibm.ibm_profile_stages(sim.h, 2)
+    sim.close()
+    return {"workload": "stretched128: 128^3 channel, tanh-stretched wall-normal cells (beta 1.8), no surface, "
+                        "body-force driven from a seeded random field; Re=200, dt=5e-4, RK2+CN, FP64",
+            "cells": n ** 3, "steps": K, "value": whole_job_gcups(n ** 3, K, world, ms), "unit": UNIT,
+            "ms_per_step": ms / K, "stages_ms_per_step": {k: v[0] / 2 for k, v in prof.items() if v[1] > 0}}
 
 
 def large_leg(args, dev, stream, flush):
@@ -674,6 +714,7 @@ def main():
                     help="keep the built-in launch shapes (no autotuning before timing)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-instances leg")
     ap.add_argument("--no-ab", action="store_true", help="skip the AB+CN leg")
+    ap.add_argument("--no-stretched", action="store_true", help="skip the non-uniform wall-normal grid leg")
     ap.add_argument("--large", action="store_true",
                     help="also time the 256x192x256 channel and the 512x384x512 tube (mixed path)")
     ap.add_argument("--e5-steps", type=int, default=0,
