@@ -98,10 +98,40 @@ static long wrap(long i, long n) {
 
 /* Staggered node position of component c with (possibly unwrapped) lattice
  * indices (i,j,k): Fig. problem_and_grid(b), Section 2. */
+/* Wall-normal coordinate of lattice row j: cell centres (half = 1) or faces
+ * (half = 0).  On the non-uniform grid a row beyond a wall is the mirror
+ * image of the row inside it (where the wall ghosts of Section 2 live). */
+static double ylat(const orc_grid* g, long j, int half) {
+  if (!g->yf) return half ? ((double)j + 0.5) * g->dy : (double)j * g->dy;
+  const long ny = g->ny;
+  if (half) {
+    if (j < 0) return 2.0 * g->yf[0] - ycen(g, -1 - j);
+    if (j >= ny) return 2.0 * g->yf[ny] - ycen(g, 2 * ny - 1 - j);
+    return ycen(g, j);
+  }
+  if (j < 0) return 2.0 * g->yf[0] - g->yf[-j];
+  if (j > ny) return 2.0 * g->yf[ny] - g->yf[2 * ny - j];
+  return g->yf[j];
+}
+
 static void node_xyz(const orc_grid* g, int c, long i, long j, long k, double x[3]) {
   x[0] = (c == 0) ? (double)i * g->dx : ((double)i + 0.5) * g->dx;
-  x[1] = (c == 1) ? (double)j * g->dy : ((double)j + 0.5) * g->dy;
+  x[1] = ylat(g, j, c != 1);
   x[2] = (c == 2) ? (double)k * g->dz : ((double)k + 0.5) * g->dz;
+}
+
+/* Wall-normal size of the local Eulerian cell of a node of component c in
+ * row j (Algorithm 1, Section 3.1): the cell height for u and w (cell
+ * centres), the distance between the centres on either side for v (faces). */
+static double hy_of(const orc_grid* g, int c, long j) {
+  if (!g->yf) return g->dy;
+  return c == 1 ? dyf(g, j) : dyc(g, j);
+}
+
+/* Squared diagonal of the local Eulerian cell of that node. */
+static double diag2_at(const orc_grid* g, int c, long j) {
+  const double hy = hy_of(g, c, j);
+  return (g->dx * g->dx + hy * hy) + g->dz * g->dz;
 }
 
 /* Offsets of component c's lattice in units of the spacing. */
@@ -234,9 +264,7 @@ static void tri_vertices(const double* xyz, const int* tri, long t, const double
   *c = xyz + 3 * (long)tri[3 * t + 2];
 }
 
-static double diag2_of(const orc_grid* g) {
-  return (g->dx * g->dx + g->dy * g->dy) + g->dz * g->dz;
-}
+static double diag2_of(const orc_grid* g) { return diag2_at(g, 0, 0); }
 
 /* Owner rule when several triangles tag the same node: the one with the
  * smallest |N|^2, ties to the smallest triangle index. */
@@ -258,7 +286,6 @@ static void tag_alg1_window(const orc_grid* g, int c, const double* xyz, int ntr
                             long ni, int32_t* owner, double* d2) {
   double off[3], del[3] = {g->dx, g->dy, g->dz};
   node_offset(c, off);
-  double diag2 = diag2_of(g);
   long jlo, jhi;
   jrange(g, c, &jlo, &jhi);
   for (long t = 0; t < ntri; ++t) {
@@ -274,10 +301,21 @@ static void tag_alg1_window(const orc_grid* g, int c, const double* xyz, int ntr
       ilo[d] = (long)floor(lo[d] / del[d] - off[d]) - 1;
       ihi[d] = (long)ceil(hi[d] / del[d] - off[d]) + 1;
     }
+    if (g->yf) {
+      /* non-uniform rows: the box margin in y is the node's own cell size,
+       * so every row is visited and the predicate below decides */
+      ilo[1] = jlo;
+      ihi[1] = jhi;
+    }
     if (ilo[1] < jlo) ilo[1] = jlo;
     if (ihi[1] > jhi) ihi[1] = jhi;
     for (long k = ilo[2]; k <= ihi[2]; ++k)
-      for (long j = ilo[1]; j <= ihi[1]; ++j)
+      for (long j = ilo[1]; j <= ihi[1]; ++j) {
+        if (g->yf) {
+          const double hy = hy_of(g, c, j);
+          lo[1] = fmin(a[1], fmin(b[1], c3[1])) - hy;
+          hi[1] = fmax(a[1], fmax(b[1], c3[1])) + hy;
+        }
         for (long i = ilo[0]; i <= ihi[0]; ++i) {
           double x[3];
           node_xyz(g, c, i, j, k, x);
@@ -288,12 +326,13 @@ static void tag_alg1_window(const orc_grid* g, int c, const double* xyz, int ntr
           const long iw = wrap(i, g->nx) - i0;
           if (iw < 0 || iw >= ni) continue;
           double n2;
-          if (tag_test(g, c, i, j, k, x, a, b, c3, diag2, &n2)) {
+          if (tag_test(g, c, i, j, k, x, a, b, c3, diag2_at(g, c, j), &n2)) {
             long planes = (c == 1) ? g->ny + 1 : g->ny;
             long idx = (wrap(k, g->nz) * planes + j) * ni + iw;
             claim(owner, d2, idx, (int32_t)t, n2);
           }
         }
+      }
   }
 }
 
@@ -314,13 +353,14 @@ void orc_tag_alg1_window(const orc_grid* g, int c, const double* xyz, int ntri, 
  * the bounding box applied as a predicate.  Tiny grids only. */
 void orc_tag_brute(const orc_grid* g, int c, const double* xyz, int ntri, const int* tri,
                    int32_t* owner, double* d2) {
-  double del[3] = {g->dx, g->dy, g->dz};
-  double diag2 = diag2_of(g);
   long jlo, jhi;
   jrange(g, c, &jlo, &jhi);
   for (long k = 0; k < g->nz; ++k)
     for (long j = jlo; j <= jhi; ++j)
       for (long i = 0; i < g->nx; ++i) {
+        /* the box margin and the diagonal are those of the node's local cell */
+        const double del[3] = {g->dx, hy_of(g, c, j), g->dz};
+        const double diag2 = diag2_at(g, c, j);
         long idx = fidx(g, c, i, j, k);
         for (int mk = -1; mk <= 1; ++mk)
           for (int mi = -1; mi <= 1; ++mi) {
@@ -363,6 +403,19 @@ static int trilinear(const orc_grid* g, int c, const double* f, const double P[3
     t[d] = s - fl;
   }
   long jmax = planes(g, c) - 1;
+  if (g->yf) {
+    /* non-uniform rows: the bracketing pair by bisection, the weight from
+     * the two row coordinates */
+    const int half = c != 1;
+    if (!(ylat(g, 0, half) <= P[1] && P[1] < ylat(g, jmax, half))) return -1;
+    long ja = 0, jb = jmax;   /* ylat(ja) <= P[1] < ylat(jb) */
+    while (jb - ja > 1) {
+      long jm = (ja + jb) / 2;
+      if (ylat(g, jm, half) <= P[1]) ja = jm; else jb = jm;
+    }
+    i0[1] = ja;
+    t[1] = (P[1] - ylat(g, ja, half)) / (ylat(g, ja + 1, half) - ylat(g, ja, half));
+  }
   if (i0[1] < 0 || i0[1] + 1 > jmax) return -1;
   double acc = 0.0;
   for (int dk = 0; dk <= 1; ++dk)
@@ -395,7 +448,9 @@ static void node_near(const orc_grid* g, int c, long i, long j, long k, const do
 /* U = wall velocity at X^f (barycentric from the vertex velocities),  */
 /* alpha = |N|/h, u^f = (1-alpha) U + alpha u^e.  Writes u^f into dst  */
 /* at the forcing nodes only.  Returns the number of probes that left  */
-/* the domain (0 on success).                                           */
+/* the domain (0 on success).  h is the probe length of a uniform      */
+/* grid; on a non-uniform wall-normal grid every node takes twice the   */
+/* diagonal of its own cell (Section 3.1) and the argument is not read. */
 /* ------------------------------------------------------------------ */
 int orc_force(const orc_grid* g, int c, const double* src, double* dst, const int32_t* owner,
               const double* xyz, const double* vel, const int* tri, double h) {
@@ -415,6 +470,7 @@ int orc_force(const orc_grid* g, int c, const double* src, double* dst, const in
                w[2] * vel[3 * (long)tri[3 * t + 2] + c];
     double n2 = dot3(N, N);
     if (n2 == 0.0) { dst[idx] = U; continue; }
+    if (g->yf) h = 2.0 * sqrt(diag2_at(g, c, j));   /* twice the local diagonal */
     double nl = sqrt(n2);
     double xe[3];
     for (int d = 0; d < 3; ++d) xe[d] = X[d] + h * (N[d] / nl);
@@ -431,6 +487,7 @@ int orc_force(const orc_grid* g, int c, const double* src, double* dst, const in
 /* heaving plate): the flow is interpolated on the surface with the     */
 /* interpolator of Eq. new_IB, u_w = (u(x^f) - alpha u(x^e))/(1-alpha), */
 /* eps = u_w - U.  Returns sum |eps| and the count through pointers.   */
+/* h as in orc_force.                                                   */
 /* ------------------------------------------------------------------ */
 int orc_slip(const orc_grid* g, int c, const double* f, const int32_t* owner, const double* xyz,
              const double* vel, const int* tri, double h, double* sum_abs, long* count) {
@@ -455,6 +512,7 @@ int orc_slip(const orc_grid* g, int c, const double* f, const int32_t* owner, co
     if (n2 == 0.0) {
       uw = f[idx];
     } else {
+      if (g->yf) h = 2.0 * sqrt(diag2_at(g, c, j));   /* twice the local diagonal */
       double nl = sqrt(n2);
       double xe[3];
       for (int d = 0; d < 3; ++d) xe[d] = X[d] + h * (N[d] / nl);

@@ -248,6 +248,8 @@ def q_energy(g: Grid, div, isb, p, u, v, w):
 def loads(g: Grid, xyz, tri, u, v, w, p, isb, re, sides=1, pole=(0.0, 0.0, 0.0)):
     """Hydrodynamic loads of Section 3.3 (MLS probes at the centroids):
     (per-triangle force and torque (nt, 6), wall pressure (nt,), F, M)."""
+    if g.yf:
+        raise ValueError("loads: the MLS probes are written for a uniform grid")
     xyz = np.ascontiguousarray(xyz, dtype=np.float64)
     tri = np.ascontiguousarray(tri, dtype=np.int32)
     isb = np.ascontiguousarray(isb, dtype=np.uint8)
@@ -263,6 +265,8 @@ def loads(g: Grid, xyz, tri, u, v, w, p, isb, re, sides=1, pole=(0.0, 0.0, 0.0))
 def pressure_recon(g: Grid, p, isb, owners, xyz, tri):
     """p with the boundary cells given the value at their probe point
     (Section 3.2, post-processing)."""
+    if g.yf:
+        raise ValueError("pressure_recon: the probes are written for a uniform grid")
     q = np.zeros_like(p)
     lib().orc_pressure_recon(ctypes.byref(g), _p(p), _p(np.ascontiguousarray(isb, dtype=np.uint8)),
                              _p(np.ascontiguousarray(owners[0], dtype=np.int32)),
@@ -309,8 +313,6 @@ class OracleSim:
         self.p[...] = p
 
     def set_surface(self, xyz, vel, tri):
-        if self.nonuniform and len(tri):
-            raise ValueError("immersed surfaces on a non-uniform wall-normal grid are not supported")
         self.xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
         self.vel = np.ascontiguousarray(vel, dtype=np.float64).reshape(-1, 3)
         self.tri = np.ascontiguousarray(tri, dtype=np.int32).reshape(-1, 3)

@@ -163,8 +163,190 @@ def test_wall_normal_viscous_term_is_second_order():
     assert np.all(slopes > 1.8), (errs, slopes)
 
 
-def test_surfaces_are_refused_on_a_stretched_grid():
-    sim = OracleSim(8, 8, 8, yfaces=inputs.stretched_faces(8))
-    xyz, tri = inputs.icosphere(1, 0.2, (0.5, 0.5, 0.5))
-    with pytest.raises(ValueError):
-        sim.set_surface(xyz, np.zeros_like(xyz), tri)
+def row_coords(yf, c):
+    """Wall-normal row coordinates of component c's lattice with one mirrored
+    row beyond each wall (index 0 of the result is row -1), and the local cell
+    size of every stored row (cell height for u, w; centre distance for v)."""
+    hc, hf, yc = spacings(yf)
+    if c == 1:
+        rows = np.concatenate([[-yf[1]], yf, [2 * yf[-1] - yf[-2]]])
+        return rows, hf
+    rows = np.concatenate([[-yc[0]], yc, [2 * yf[-1] - yc[-1]]])
+    return rows, hc
+
+
+def brute_tags(g, yf, xyz, tri):
+    """Algorithm 1 restated with the local cell of each node (box margin and
+    diagonal from that node's row), every node and periodic image against
+    every triangle; owner = smallest |N|^2, ties to the smallest index."""
+    nx, ny, nz = g.nx, g.ny, g.nz
+    out = []
+    for c in range(3):
+        rows, hy = row_coords(yf, c)
+        nyc = ny + 1 if c == 1 else ny
+        own = np.full((nz, nyc, nx), -1, dtype=np.int32)
+        best = np.full((nz, nyc, nx), np.inf)
+        jlo, jhi = (1, ny - 1) if c == 1 else (0, ny - 1)
+        ox = 0.0 if c == 0 else 0.5
+        oz = 0.0 if c == 2 else 0.5
+
+        def pos(i, j, k):
+            return np.array([(i + ox) * g.dx, rows[j + 1], (k + oz) * g.dz])
+
+        for t, (a, b, cc) in enumerate(xyz[tri]):
+            mn = np.minimum(np.minimum(a, b), cc)
+            mx = np.maximum(np.maximum(a, b), cc)
+            for k in range(nz):
+                for j in range(jlo, jhi + 1):
+                    for i in range(nx):
+                        for mk in (-1, 0, 1):
+                            for mi in (-1, 0, 1):
+                                ii, kk = i + mi * nx, k + mk * nz
+                                x = pos(ii, j, kk)
+                                dl = (g.dx, hy[j], g.dz)
+                                if not all(mn[d] - dl[d] < x[d] < mx[d] + dl[d] for d in range(3)):
+                                    continue
+                                X, _ = orc.closest_point(x, a, b, cc)
+                                N = x - X
+                                n2 = N[0] * N[0] + N[1] * N[1] + N[2] * N[2]
+                                if not n2 <= (g.dx * g.dx + hy[j] * hy[j]) + g.dz * g.dz:
+                                    continue
+                                hit = n2 == 0.0
+                                for di, dj, dk in ((-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0), (0, 0, -1),
+                                                   (0, 0, 1)):
+                                    vn = pos(ii + di, j + dj, kk + dk) - X
+                                    if N[0] * vn[0] + N[1] * vn[1] + N[2] * vn[2] < 0.0:
+                                        hit = True
+                                if hit and (own[k, j, i] < 0 or n2 < best[k, j, i]):
+                                    own[k, j, i] = t
+                                    best[k, j, i] = n2
+        out.append(own)
+    return out
+
+
+def test_uniform_faces_reproduce_uniform_surface_path():
+    """Face positions j/ny given explicitly (exact binary fractions) tag, force
+    and measure slip exactly as the uniform grid does."""
+    nx, ny, nz = 16, 16, 16
+    yf = np.arange(ny + 1) / ny
+    gu = orc.make_grid(nx, ny, nz)
+    gs = orc.make_grid(nx, ny, nz, yfaces=yf)
+    xyz, tri = inputs.icosphere(1, 0.18, (0.48, 0.47, 0.53))
+    ou, du = orc.tag(gu, xyz, tri)
+    os_, ds = orc.tag(gs, xyz, tri)
+    for c in range(3):
+        np.testing.assert_array_equal(ou[c], os_[c])
+        np.testing.assert_array_equal(du[c], ds[c])
+    rng = np.random.default_rng(3)
+    vel = rng.standard_normal(xyz.shape)
+    h = 2.0 * np.sqrt((gu.dx * gu.dx + gu.dy * gu.dy) + gu.dz * gu.dz)
+    for c in range(3):
+        src = rng.standard_normal(orc.field_shape(gu, c))
+        a, b = src.copy(), src.copy()
+        assert orc.force(gu, c, src, a, ou[c], xyz, vel, tri, h) == 0
+        assert orc.force(gs, c, src, b, ou[c], xyz, vel, tri, -1.0) == 0
+        np.testing.assert_allclose(b, a, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_stretched_tagging_matches_independent_brute_force(seed):
+    nx, ny, nz = 6, 10, 6
+    yf = inputs.stretched_faces(ny, beta=2.2)
+    g = orc.make_grid(nx, ny, nz, yfaces=yf)
+    xyz, tri = inputs.random_triangles(6, seed, lo=0.15, hi=0.85, size=0.3)
+    own, _ = orc.tag(g, xyz, tri)
+    own_b, _ = orc.tag(g, xyz, tri, brute=True)
+    ref = brute_tags(g, yf, xyz, tri)
+    for c in range(3):
+        np.testing.assert_array_equal(own[c], ref[c])
+        np.testing.assert_array_equal(own_b[c], ref[c])
+    assert sum(int((o >= 0).sum()) for o in own) > 20
+
+
+@pytest.mark.parametrize("yw", [0.0371, 0.2013, 0.5 + 1e-3])
+def test_stretched_flat_plane_closed_form(yw):
+    """A plane y = yw across the periodic box: a node is tagged iff it lies
+    within its own cell size of the plane (the box of Algorithm 1) and one of
+    its wall-normal neighbours lies across the plane."""
+    nx, ny, nz = 64, 24, 64
+    yf = inputs.stretched_faces(ny)
+    g = orc.make_grid(nx, ny, nz, yfaces=yf)
+    # a plate wider than the box; near its edges (and its diagonal) Algorithm 1
+    # also tags nodes whose height above the plane is below about dx / 2, so
+    # dx is kept well below the distance of any non-bracketing row
+    big = 0.3
+    xyz = np.array([[-big, yw, -big], [1 + big, yw, -big], [-big, yw, 1 + big], [1 + big, yw, 1 + big]])
+    tri = np.array([[0, 1, 3], [0, 3, 2]], dtype=np.int32)
+    own, _ = orc.tag(g, xyz, tri)
+    for c in range(3):
+        rows, hy = row_coords(yf, c)
+        y = rows[1:-1]
+        s = y - yw
+        across = (s * (rows[:-2] - yw) < 0) | (s * (rows[2:] - yw) < 0)
+        expect = (np.abs(s) > 0) & (np.abs(s) < hy) & across
+        if c == 1:
+            expect[0] = expect[-1] = False
+        got = own[c] >= 0
+        np.testing.assert_array_equal(got, np.broadcast_to(expect[None, :, None], got.shape))
+        assert expect.sum() >= 1
+
+
+def test_stretched_forcing_is_exact_for_affine_fields():
+    """Eq. new_IB with u^e trilinear on the stretched rows reproduces an
+    affine field at every forcing node (the interpolant, the wall value and
+    the blend are all exact for affine data)."""
+    nx, ny, nz = 24, 24, 24
+    yf = inputs.stretched_faces(ny)
+    g = orc.make_grid(nx, ny, nz, yfaces=yf)
+    xyz, tri = inputs.icosphere(2, 0.2, (0.5, 0.47, 0.5))
+    own, _ = orc.tag(g, xyz, tri)
+    grad = np.array([[0.3, -1.1, 0.7], [1.3, 0.4, -0.2], [-0.6, 0.9, 0.25]])
+    base = np.array([0.2, -0.5, 1.0])
+    for c in range(3):
+        rows, _ = row_coords(yf, c)
+        nyc = ny + 1 if c == 1 else ny
+        x = (np.arange(nx) + (0.0 if c == 0 else 0.5)) * g.dx
+        z = (np.arange(nz) + (0.0 if c == 2 else 0.5)) * g.dz
+        y = rows[1:nyc + 1]
+        Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+        f = base[c] + grad[c, 0] * X + grad[c, 1] * Y + grad[c, 2] * Z
+        vel = np.zeros_like(xyz)
+        vel[:, c] = base[c] + xyz @ grad[c]
+        dst = np.zeros_like(f)
+        assert orc.force(g, c, f, dst, own[c], xyz, vel, tri, -1.0) == 0
+        m = own[c] >= 0
+        assert m.sum() > 50
+        np.testing.assert_allclose(dst[m], f[m], rtol=0, atol=1e-12)
+
+
+def test_stretched_probe_length_is_twice_the_local_diagonal():
+    """Plane y = yw, field (y - yw)^2 and U = 0: a forcing node at distance d
+    takes alpha * I(yw +- h) with h = 2 sqrt(dx^2 + hy^2 + dz^2) from its own
+    row and I the piecewise-linear interpolant along the rows (Eq. probe)."""
+    nx, ny, nz = 64, 24, 64
+    yf = inputs.stretched_faces(ny)
+    g = orc.make_grid(nx, ny, nz, yfaces=yf)
+    yw = 0.2013
+    # a plate wider than the box; near its edges (and its diagonal) Algorithm 1
+    # also tags nodes whose height above the plane is below about dx / 2, so
+    # dx is kept well below the distance of any non-bracketing row
+    big = 0.3
+    xyz = np.array([[-big, yw, -big], [1 + big, yw, -big], [-big, yw, 1 + big], [1 + big, yw, 1 + big]])
+    tri = np.array([[0, 1, 3], [0, 3, 2]], dtype=np.int32)
+    own, _ = orc.tag(g, xyz, tri)
+    for c in range(3):
+        rows, hy = row_coords(yf, c)
+        nyc = ny + 1 if c == 1 else ny
+        y = rows[1:nyc + 1]
+        f = np.broadcast_to(((y - yw) ** 2)[None, :, None], (nz, nyc, nx)).copy()
+        dst = np.zeros_like(f)
+        assert orc.force(g, c, f, dst, own[c], xyz, np.zeros_like(xyz), tri, -1.0) == 0
+        ko, io = 40, 10   # a column far from the plate's edges and diagonal
+        tagged = np.nonzero((own[c] >= 0)[ko, :, io])[0]
+        assert len(tagged) >= 1
+        for j in tagged:
+            d = abs(y[j] - yw)
+            h = 2.0 * np.sqrt((g.dx * g.dx + hy[j] * hy[j]) + g.dz * g.dz)
+            ye = yw + np.sign(y[j] - yw) * h
+            expect = (d / h) * np.interp(ye, y, (y - yw) ** 2)
+            np.testing.assert_allclose(dst[ko, j, io], expect, rtol=1e-12, atol=1e-15)
