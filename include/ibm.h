@@ -126,9 +126,14 @@ ibm_status ibm_create_grid(const ibm_grid_desc* desc, void* stream, ibm_handle* 
  * faces.  Every wall-normal operator (the explicit terms, the factorised
  * implicit sweep, the divergence, the per-wavenumber tridiagonal of the
  * Poisson solve with a volume-weighted zero-mean gauge, the projection and
- * the pressure update) takes its row's spacings.  Supported for the FP64
- * path without immersed surfaces: ibm_set_surface returns IBM_ERR_STATE, a
- * batch refuses the handle (IBM_ERR_ARG), and a precision other than
+ * the pressure update) takes its row's spacings.  Immersed surfaces use the
+ * local Eulerian cell (Algorithm 1, Section 3.1): a node's box margin in y and
+ * its diagonal come from its own row (cell height for u and w, distance of
+ * the centres for v), the probe length is twice that diagonal, and the probe
+ * is interpolated between the rows that bracket it; the q term weights every
+ * cell by its volume.  Supported for the FP64 path: a batch refuses the
+ * handle (IBM_ERR_ARG); ibm_get_loads and ibm_get_pressure_recon return
+ * IBM_ERR_STATE (their probes assume a uniform grid); a precision other than
  * IBM_FP64 or invalid face positions return IBM_ERR_ARG. */
 ibm_status ibm_create_grid_stretched(const ibm_grid_desc* desc, const double* y_faces, void* stream,
                                      ibm_handle* out);

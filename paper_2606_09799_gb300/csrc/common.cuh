@@ -22,11 +22,18 @@ constexpr uint8_t FLAG_U = 1, FLAG_V = 2, FLAG_W = 4, FLAG_B = 8;
 // in the wall-normal direction), device FP64 tables: ihc[j] = 1 / height of
 // cell j (ny); ihf[j] = 1 / distance of the centres across face j (ny + 1;
 // the wall faces measure to the mirror image of the first / last centre);
-// hc[j] = height of cell j.  All null on a uniform grid.
+// hc[j] = height of cell j; hf[j] = distance of the centres across face j
+// (ny + 1); yc[j + 1] = centre of row j for j in [-1, ny] and yv[j + 1] =
+// face j for j in [-1, ny + 1], rows beyond a wall being mirror images;
+// hmax = the largest of hc and hf.  All null (0) on a uniform grid.
 struct YTab {
   const double* ihc;
   const double* ihf;
   const double* hc;
+  const double* hf;
+  const double* yc;
+  const double* yv;
+  double hmax;
 };
 
 // Grid as seen by every kernel (passed by value).

@@ -23,15 +23,32 @@ __device__ __forceinline__ T* comp_ptr(const Fields<T>& f, int c) {
 // Trilinear interpolation of component c at P from the 8 surrounding nodes
 // of the same staggered lattice.  x and z wrap; in y the stencil must lie
 // in the stored planes (u, w: 0..ny-1; v: 0..ny with the wall planes).
+// On the non-uniform wall-normal grid the bracketing rows come from a
+// bisection over the row table and the y weight from their coordinates.
 template <typename T>
 __device__ bool trilinear(const Geo& g, int c, const T* __restrict__ f, const double P[3], double* out) {
   const double sx = P[0] * g.idx - (c == 0 ? 0.0 : 0.5);
   const double sy = P[1] * g.idy - (c == 1 ? 0.0 : 0.5);
   const double sz = P[2] * g.idz - (c == 2 ? 0.0 : 0.5);
   const double fx = floor(sx), fy = floor(sy), fz = floor(sz);
-  const long long i0 = (long long)fx, j0 = (long long)fy, k0 = (long long)fz;
+  const long long i0 = (long long)fx, k0 = (long long)fz;
+  long long j0 = (long long)fy;
+  double ty = sy - fy;
+  if (g.yt.yc) {
+    const int half = c != 1;
+    const long long jmax = planes(g, c) - 1;
+    if (!(ylat(g, 0, half) <= P[1] && P[1] < ylat(g, jmax, half))) return false;
+    long long a = 0, b = jmax;   // ylat(a) <= P[1] < ylat(b)
+    while (b - a > 1) {
+      const long long m = (a + b) >> 1;
+      if (ylat(g, m, half) <= P[1]) a = m; else b = m;
+    }
+    j0 = a;
+    const double ya = ylat(g, a, half);
+    ty = (P[1] - ya) / (ylat(g, a + 1, half) - ya);
+  }
   if (j0 < 0 || j0 + 1 > planes(g, c) - 1) return false;
-  const double tx = sx - fx, ty = sy - fy, tz = sz - fz;
+  const double tx = sx - fx, tz = sz - fz;
   const int ia = wrapi(i0, g.nx), ib = wrapi(i0 + 1, g.nx);
   const int ka = wrapi(k0, g.nz), kb = wrapi(k0 + 1, g.nz);
   const int pl = planes(g, c);
@@ -50,6 +67,7 @@ __device__ bool trilinear(const Geo& g, int c, const T* __restrict__ f, const do
 // owning triangle), closest point, normal vector and the wall velocity U.
 struct NodeGeom {
   double x[3], X[3], N[3], n2, U;
+  double h;   // probe length: twice the diagonal of the node's local cell (Section 3.1)
 };
 
 __device__ inline void forcing_geometry(const Geo& g, const Surf& s, unsigned key, unsigned tri, NodeGeom& ng) {
@@ -73,6 +91,7 @@ __device__ inline void forcing_geometry(const Geo& g, const Surf& s, unsigned ke
   ng.n2 = ddot(ng.N, ng.N);
   const long long nv = s.nv;
   ng.U = wb[0] * __ldg(s.u + c * nv + va) + wb[1] * __ldg(s.u + c * nv + vb) + wb[2] * __ldg(s.u + c * nv + vc);
+  ng.h = g.yt.yc ? 2.0 * sqrt(diag2_at(g, c, j)) : g.h;
 }
 
 // Probe of one forcing node (Eq. probe): point x^e = X + h N/|N|,
@@ -91,8 +110,8 @@ __device__ __forceinline__ void forcing_probe(const Geo& g, const Surf& s, const
     if (ng.n2 != 0.0) {
       const double nl = sqrt(ng.n2);
 #pragma unroll
-      for (int d = 0; d < 3; ++d) xe[d] = ng.X[d] + g.h * (ng.N[d] / nl);
-      alpha = nl / g.h;
+      for (int d = 0; d < 3; ++d) xe[d] = ng.X[d] + ng.h * (ng.N[d] / nl);
+      alpha = nl / ng.h;
     }
     rec[0] = xe[0];
     rec[1] = xe[1];

@@ -16,10 +16,30 @@ __device__ __forceinline__ double ddot(const double x[3], const double y[3]) {
   return dadd(dadd(dmul(x[0], y[0]), dmul(x[1], y[1])), dmul(x[2], y[2]));
 }
 
+// Wall-normal coordinate of lattice row j: faces (half = 0) or cell centres
+// (half = 1).  On the non-uniform grid it comes from the row tables, one row
+// beyond either wall included.
+__device__ __forceinline__ double ylat(const Geo& g, long long j, int half) {
+  if (g.yt.yc) return half ? g.yt.yc[j + 1] : g.yt.yv[j + 1];
+  return half ? dmul(dadd((double)j, 0.5), g.dy) : dmul((double)j, g.dy);
+}
+
+// Squared diagonal of the local Eulerian cell of component c's node in row
+// j (Algorithm 1): on the non-uniform grid its wall-normal side is the cell
+// height for u and w (centres) and the distance of the centres for v (faces).
+__device__ __forceinline__ double yspan(const Geo& g, int c, long long j) {
+  return c == 1 ? g.yt.hf[j] : g.yt.hc[j];
+}
+__device__ __forceinline__ double diag2_at(const Geo& g, int c, long long j) {
+  if (!g.yt.yc) return g.diag2;
+  const double hy = yspan(g, c, j);
+  return dadd(dadd(dmul(g.dx, g.dx), dmul(hy, hy)), dmul(g.dz, g.dz));
+}
+
 // Lattice position of component c's node with (possibly unwrapped) indices.
 __device__ __forceinline__ void node_pos(const Geo& g, int c, long long i, long long j, long long k, double x[3]) {
   x[0] = (c == 0) ? dmul((double)i, g.dx) : dmul(dadd((double)i, 0.5), g.dx);
-  x[1] = (c == 1) ? dmul((double)j, g.dy) : dmul(dadd((double)j, 0.5), g.dy);
+  x[1] = ylat(g, j, c != 1);
   x[2] = (c == 2) ? dmul((double)k, g.dz) : dmul(dadd((double)k, 0.5), g.dz);
 }
 
@@ -158,6 +178,39 @@ __device__ __forceinline__ void exact_range(double lo, double hi, double del, do
   i1 = (long long)ceil(hi * idel - off) + 1;
   while (i0 <= i1 && !(lo < lat(i0, del, half))) ++i0;
   while (i1 >= i0 && !(lat(i1, del, half) < hi)) --i1;
+}
+
+// Whether row j of component c's lattice lies inside the box of Algorithm 1
+// in y, the margin being that node's own cell size (non-uniform grid).
+__device__ __forceinline__ bool row_inside(const Geo& g, int c, long long j, double ymn, double ymx) {
+  const double y = ylat(g, j, c != 1), hy = yspan(g, c, j);
+  return dsub(ymn, hy) < y && y < dadd(ymx, hy);
+}
+
+// First and last row of component c's lattice (j in [jlo, jhi]) inside that
+// box on the non-uniform grid: bisection to the rows within the largest cell
+// size of [ymn, ymx] (a superset, since every margin is at most hmax), then
+// the exact predicate inwards.  Rows between the two may still fail it; the
+// pair test checks every row again.
+__device__ inline void nu_row_range(const Geo& g, int c, long long jlo, long long jhi, double ymn, double ymx,
+                                    long long& j0, long long& j1) {
+  const int half = c != 1;
+  const double lo = dsub(ymn, g.yt.hmax), hi = dadd(ymx, g.yt.hmax);
+  long long a = jlo, b = jhi + 1;   // first row above lo
+  while (a < b) {
+    const long long m = (a + b) >> 1;
+    if (ylat(g, m, half) > lo) b = m; else a = m + 1;
+  }
+  j0 = a;
+  a = jlo - 1;
+  b = jhi;   // last row below hi
+  while (a < b) {
+    const long long m = (a + b + 1) >> 1;
+    if (ylat(g, m, half) < hi) a = m; else b = m - 1;
+  }
+  j1 = a;
+  while (j0 <= j1 && !row_inside(g, c, j0, ymn, ymx)) ++j0;
+  while (j1 >= j0 && !row_inside(g, c, j1, ymn, ymx)) --j1;
 }
 
 __device__ __forceinline__ void load_vertex(const Surf& s, int v, double out[3]) {

@@ -228,6 +228,9 @@ __device__ int fft_lines(typename Cplx<T>::type* a, typename Cplx<T>::type* b, i
 // ---------------------------------------------------------------------------
 // q_F: fixed-order two-level reduction of sum_{C_B} D uhat dV over the
 // sorted boundary-cell list; q_F = -A / |C_F| (uniform on fluid cells).
+// Each block leaves two partial sums: D uhat and the volume of its boundary
+// cells, both per unit dx dz on the non-uniform wall-normal grid (whose cell
+// heights differ), the first per unit dV and the second unused otherwise.
 // ---------------------------------------------------------------------------
 constexpr int QB_BLOCKS = 128, QB_THREADS = 256;   // QB_BLOCKS: the most partial sums
 
@@ -236,7 +239,7 @@ __device__ __forceinline__ double div_at(const Geo& g, const T* __restrict__ u, 
                                          const T* __restrict__ w, long long i, long long j, long long k) {
   const long long ip = i + 1 == g.nx ? 0 : i + 1, kp = k + 1 == g.nz ? 0 : k + 1;
   const double du = ((double)u[fidx(g, 0, ip, j, k)] - (double)u[fidx(g, 0, i, j, k)]) * g.idx;
-  const double dv = ((double)v[fidx(g, 1, i, j + 1, k)] - (double)v[fidx(g, 1, i, j, k)]) * g.idy;
+  const double dv = ((double)v[fidx(g, 1, i, j + 1, k)] - (double)v[fidx(g, 1, i, j, k)]) * (g.yt.ihc ? g.yt.ihc[j] : g.idy);
   const double dw = ((double)w[fidx(g, 2, i, j, kp)] - (double)w[fidx(g, 2, i, j, k)]) * g.idz;
   return du + dv + dw;
 }
@@ -248,20 +251,34 @@ __device__ __forceinline__ void q_partial(const Blk& bk, const Geo& g, const Fie
   const unsigned n = min(ds->nbound, cap);
   const unsigned per = (n + bk.gx - 1) / bk.gx;
   const unsigned e0 = bk.x * per, e1 = min(n, e0 + per);
-  double acc = 0.0;
+  __shared__ double redv[QB_THREADS];
+  double acc = 0.0, vol = 0.0;
   for (unsigned e = e0 + threadIdx.x; e < e1; e += QB_THREADS) {
     const long long cell = blist[e];
     long long i, j, k;
     split3(cell, g.nx, g.ny, i, j, k);
-    acc += div_at<T>(g, f.u, f.v, f.w, i, j, k);
+    const double du = div_at<T>(g, f.u, f.v, f.w, i, j, k);
+    if (g.yt.hc) {
+      acc += du * g.yt.hc[j];
+      vol += g.yt.hc[j];
+    } else {
+      acc += du;
+    }
   }
   red[threadIdx.x] = acc;
+  redv[threadIdx.x] = vol;
   __syncthreads();
   for (int s = QB_THREADS / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    if (threadIdx.x < s) {
+      red[threadIdx.x] += red[threadIdx.x + s];
+      redv[threadIdx.x] += redv[threadIdx.x + s];
+    }
     __syncthreads();
   }
-  if (threadIdx.x == 0) partial[bk.x] = red[0];
+  if (threadIdx.x == 0) {
+    partial[2 * bk.x] = red[0];
+    partial[2 * bk.x + 1] = redv[0];
+  }
 }
 template <typename T>
 struct QPartial {
@@ -277,11 +294,19 @@ struct QPartial {
 
 __device__ __forceinline__ void q_final(const Blk& bk, const Geo& g, const double* partial, DevState* ds, int s, int use_q,
                                         int nblk) {
-  const double sum = warp_sum_fixed(partial, nblk, 1, 0);
+  const double sum = warp_sum_fixed(partial, nblk, 2, 0);
+  const double vb = warp_sum_fixed(partial, nblk, 2, 1);
   if (threadIdx.x != 0) return;
-  const double dV = g.dx * g.dy * g.dz;
-  const double A = sum * dV;
-  const double VF = (double)(g.ncell - (long long)ds->nbound) * dV;
+  double A, VF;
+  if (g.yt.hc) {   // heights summed per unit dx dz: the box volume less the boundary cells
+    const double dxz = g.dx * g.dz;
+    A = sum * dxz;
+    VF = g.lx * g.ly * g.lz - vb * dxz;
+  } else {
+    const double dV = g.dx * g.dy * g.dz;
+    A = sum * dV;
+    VF = (double)(g.ncell - (long long)ds->nbound) * dV;
+  }
   ds->sum_a[s] = A;
   const double qf = (use_q && VF > 0.0) ? -A / VF : 0.0;
   ds->qf[s] = qf;
@@ -327,13 +352,26 @@ __device__ __forceinline__ void q_energy_partial(const Blk& bk, const Geo& g, co
   const unsigned n = (unsigned)g.ncell;
   const unsigned per = (n + bk.gx - 1) / bk.gx;
   const unsigned c0 = bk.x * per, c1 = min(n, c0 + per);
-  double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};   // fluid count, S1, S2, A, B (per unit volume)
+  // fluid volume, S1, S2, A, B per unit dV (uniform grid) or per unit dx dz
+  // (non-uniform wall-normal grid: each cell weighted by its height)
+  double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
   for (unsigned cell = c0 + threadIdx.x; cell < c1; cell += QE_THREADS) {
     const unsigned i = cell % (unsigned)g.nx, r = cell / (unsigned)g.nx;
     const unsigned j = r % (unsigned)g.ny, k = r / (unsigned)g.ny;
     const double pe = (double)p_minus_e<T>(g, f, i, j, k);
     const unsigned fl = (flags32[cell >> 2] >> (8 * (cell & 3))) & 0xFFu;
-    if (fl & FLAG_B) {
+    if (g.yt.hc) {
+      const double wv = g.yt.hc[j];
+      if (fl & FLAG_B) {
+        const double du = div_at<T>(g, f.u, f.v, f.w, i, j, k) * wv;
+        acc[3] += du;
+        acc[4] += pe * du;
+      } else {
+        acc[0] += wv;
+        acc[1] += pe * wv;
+        acc[2] += pe * (pe * wv);
+      }
+    } else if (fl & FLAG_B) {
       const double du = div_at<T>(g, f.u, f.v, f.w, i, j, k);
       acc[3] += du;
       acc[4] += pe * du;
@@ -369,7 +407,7 @@ __device__ __forceinline__ void q_energy_final(const Blk&, const Geo& g, const d
   double t[5];
   for (int q = 0; q < 5; ++q) t[q] = warp_sum_fixed(partial, nblk, 5, q);
   if (threadIdx.x != 0) return;
-  const double dV = g.dx * g.dy * g.dz;
+  const double dV = g.yt.hc ? g.dx * g.dz : g.dx * g.dy * g.dz;
   const double S0 = t[0] * dV, S1 = t[1] * dV, S2 = t[2] * dV, A = t[3] * dV, B = t[4] * dV;
   const double C = S0 * S2 - S1 * S1;
   double qa, qb;

@@ -177,7 +177,9 @@ struct ibm_grid {
   void* sweep_mem[24];
   double* pcp; double* pinv; double* psegf; double* psegb; double* lamx; double* lamz;
   double* pal;     // non-uniform wall-normal grid: forward multipliers of the Poisson rows, else null
-  double* ytab;    // non-uniform wall-normal grid: 1/heights (ny), 1/centre distances (ny+1), heights (ny)
+  double* ytab;    // non-uniform wall-normal grid: 1/heights (ny), 1/centre distances (ny+1), heights (ny),
+                   // centre distances (ny+1), centre rows (ny+2), face rows (ny+3)
+  double ysp_min;  // non-uniform wall-normal grid: smallest cell height or centre distance, else 0
   void* twx; void* twz;
   double tbl_off[3];
   double tbl_gam[2];
@@ -1170,16 +1172,29 @@ ibm_status ibm_create_grid_stretched(const ibm_grid_desc* desc, const double* y_
   if (st != IBM_OK) return st;
   // spacing tables: cell heights, centre distances across faces (mirrored
   // centres at the walls), as the oracle defines them
-  std::vector<double> t(3ull * ny + 1);
+  std::vector<double> t(6ull * ny + 7);
   double* ihc = t.data();
   double* ihf = ihc + ny;
   double* hc = ihf + ny + 1;
+  double* hf = hc + ny;
+  double* yc = hf + ny + 1;
+  double* yv = yc + ny + 2;
   for (int j = 0; j < ny; ++j) hc[j] = y_faces[j + 1] - y_faces[j];
   for (int j = 0; j < ny; ++j) ihc[j] = 1.0 / hc[j];
-  ihf[0] = 1.0 / hc[0];
-  ihf[ny] = 1.0 / hc[ny - 1];
-  for (int j = 1; j < ny; ++j)
-    ihf[j] = 1.0 / (0.5 * (y_faces[j] + y_faces[j + 1]) - 0.5 * (y_faces[j - 1] + y_faces[j]));
+  hf[0] = hc[0];
+  hf[ny] = hc[ny - 1];
+  for (int j = 1; j < ny; ++j) hf[j] = 0.5 * (y_faces[j] + y_faces[j + 1]) - 0.5 * (y_faces[j - 1] + y_faces[j]);
+  for (int j = 0; j <= ny; ++j) ihf[j] = 1.0 / hf[j];
+  // row coordinates, one mirrored row beyond each wall (y_faces[0] = 0)
+  for (int j = 0; j < ny; ++j) yc[j + 1] = 0.5 * (y_faces[j] + y_faces[j + 1]);
+  yc[0] = -yc[1];
+  yc[ny + 1] = 2.0 * y_faces[ny] - yc[ny];
+  for (int j = 0; j <= ny; ++j) yv[j + 1] = y_faces[j];
+  yv[0] = -y_faces[1];
+  yv[ny + 2] = 2.0 * y_faces[ny] - y_faces[ny - 1];
+  double smin = hc[0], smax = hc[0];
+  for (int j = 0; j < ny; ++j) { smin = std::min(smin, hc[j]); smax = std::max(smax, hc[j]); }
+  for (int j = 0; j <= ny; ++j) { smin = std::min(smin, hf[j]); smax = std::max(smax, hf[j]); }
   h->ytab = (double*)upload_vec<double>(h, t);
   const size_t nspec = (size_t)h->g.nz * h->g.ny * h->g.nkx;
   h->pal = (double*)dalloc(h, nspec * 8);
@@ -1190,6 +1205,11 @@ ibm_status ibm_create_grid_stretched(const ibm_grid_desc* desc, const double* y_
   h->g.yt.ihc = h->ytab;
   h->g.yt.ihf = h->ytab + ny;
   h->g.yt.hc = h->ytab + 2 * ny + 1;
+  h->g.yt.hf = h->ytab + 3 * ny + 1;
+  h->g.yt.yc = h->ytab + 4 * ny + 2;
+  h->g.yt.yv = h->ytab + 5 * ny + 4;
+  h->g.yt.hmax = smax;
+  h->ysp_min = smin;
   launch_build_poisson_tables_nu(h->g, h->lamx, h->lamz, h->pcp, h->pinv, h->pal, h->user);
   if (cudaStreamSynchronize(h->user) != cudaSuccess) {
     ibm_destroy(h);
@@ -1226,9 +1246,13 @@ ibm_status ibm_set_body_force(ibm_handle h, double fx, double fy, double fz) {
 
 // upper bound of the candidates a surface can produce: nodes inside every
 // triangle's Cartesian box (with the one-cell margin of Algorithm 1)
-static unsigned long long candidate_bound(const Geo& g, const double* xyz, const int32_t* tri, int nt) {
+// (non-uniform wall-normal grid: rows at least ysp_min apart, margins of at
+// most g.yt.hmax)
+static unsigned long long candidate_bound(const Geo& g, double ysp_min, const double* xyz, const int32_t* tri,
+                                          int nt) {
   unsigned long long tot = 0;
-  const double del[3] = {g.dx, g.dy, g.dz};
+  const double del[3] = {g.dx, ysp_min > 0.0 ? ysp_min : g.dy, g.dz};
+  const double pad = ysp_min > 0.0 ? 2.0 * g.yt.hmax : 0.0;
   for (int t = 0; t < nt; ++t) {
     unsigned long long prod = 1;
     for (int d = 0; d < 3; ++d) {
@@ -1238,7 +1262,7 @@ static unsigned long long candidate_bound(const Geo& g, const double* xyz, const
         mn = x < mn ? x : mn;
         mx = x > mx ? x : mx;
       }
-      long long cnt = (long long)ceil((mx - mn) / del[d]) + 4;
+      long long cnt = (long long)ceil((mx - mn + (d == 1 ? pad : 0.0)) / del[d]) + 4;
       if (d == 1 && cnt > g.ny + 1) cnt = g.ny + 1;
       prod *= (unsigned long long)cnt;
     }
@@ -1257,10 +1281,6 @@ ibm_status ibm_set_surface(ibm_handle h, int nverts, const double* xyz, const do
     return IBM_OK;
   }
   if (nverts < 3 || !xyz || !vel) return IBM_ERR_ARG;
-  if (h->g.yt.ihc) {
-    set_err(h, "%s", "ibm_set_surface: immersed surfaces on a non-uniform wall-normal grid are not supported");
-    return IBM_ERR_STATE;
-  }
   if (!tri && (!h->has_topology || ntris != h->nt)) {
     set_err(h, "%s", "ibm_set_surface: tri == NULL needs the previous connectivity with the same ntris");
     return IBM_ERR_STATE;
@@ -1308,7 +1328,7 @@ ibm_status ibm_set_surface(ibm_handle h, int nverts, const double* xyz, const do
         for (int m = 0; m < 3; ++m) h->host_tri[3ull * t + m] = soa[(size_t)m * ntris + t];
     }
     const int32_t* tt = tri ? tri : h->host_tri.data();
-    unsigned long long need = candidate_bound(h->g, xyz, tt, ntris);
+    unsigned long long need = candidate_bound(h->g, h->ysp_min, xyz, tt, ntris);
     if (need > 0xF0000000ull) need = 0xF0000000ull;
     if (need > h->tb.cap) {
       CK(cudaStreamSynchronize(st));
@@ -1333,7 +1353,7 @@ ibm_status ibm_set_surface(ibm_handle h, int nverts, const double* xyz, const do
         return IBM_ERR_ARG;
       }
     h->host_tri.swap(ht);
-    unsigned long long need = candidate_bound(h->g, hx.data(), h->host_tri.data(), ntris) * 3 / 2;
+    unsigned long long need = candidate_bound(h->g, h->ysp_min, hx.data(), h->host_tri.data(), ntris) * 3 / 2;
     if (need > 0xF0000000ull) need = 0xF0000000ull;
     if (need > h->tb.cap) {
       CK(cudaStreamSynchronize(st));
@@ -1783,6 +1803,10 @@ ibm_status ibm_get_loads(ibm_handle h, int sides, const double* pole, double* fo
   const double zero[3] = {0.0, 0.0, 0.0};
   const double* pl = pole ? pole : zero;
   for (int d = 0; d < 3; ++d) force[d] = torque[d] = 0.0;
+  if (h->g.yt.ihc) {
+    set_err(h, "%s", "ibm_get_loads: the MLS probes are written for a uniform grid");
+    return IBM_ERR_STATE;
+  }
   if (h->nt == 0) return IBM_OK;
   const int nt = h->nt;
   double* dtr = (double*)dalloc(h, (size_t)nt * 7 * sizeof(double));
@@ -1814,6 +1838,10 @@ ibm_status ibm_get_loads(ibm_handle h, int sides, const double* pole, double* fo
 
 ibm_status ibm_get_pressure_recon(ibm_handle h, double* p, int on_device) {
   if (!h || !p) return IBM_ERR_ARG;
+  if (h->g.yt.ihc) {
+    set_err(h, "%s", "ibm_get_pressure_recon: the probes are written for a uniform grid");
+    return IBM_ERR_STATE;
+  }
   const Geo& g = h->g;
   cudaStream_t st = h->user;
   double* stage = (double*)h->scr;   // holds at least ncell doubles in both precisions

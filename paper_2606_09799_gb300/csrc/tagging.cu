@@ -103,6 +103,8 @@ __device__ __forceinline__ void tri_setup(const Blk& bk, const Geo& g, const Sur
       long long a0 = r0[d][hf], a1 = r1[d][hf];
       if (d == 1) {
         const long long jlo = c == 1 ? 1 : 0;
+        if (g.yt.yc)   // non-uniform rows: each node's own cell size is its margin
+          nu_row_range(g, c, jlo, g.ny - 1, fmin(A[1], fmin(B[1], C[1])), fmax(A[1], fmax(B[1], C[1])), a0, a1);
         a0 = a0 < jlo ? jlo : a0;
         a1 = a1 > g.ny - 1 ? g.ny - 1 : a1;
       }
@@ -119,7 +121,8 @@ __device__ __forceinline__ void tri_setup(const Blk& bk, const Geo& g, const Sur
   const double den = dsub(dmul(TC.aa, TC.cc), dmul(TC.abac, TC.abac));
   const double dmin = fmin(del[0], fmin(del[1], del[2])), dmax = fmax(del[0], fmax(del[1], del[2]));
   const double lmax2 = fmax(TC.aa, fmax(TC.cc, dadd(dsub(TC.aa, 2.0 * TC.abac), TC.cc)));
-  R.screen = den > 0.05 * TC.aa * TC.cc && lmax2 <= 64.0 * dmin * dmin && dmax <= 4.0 * dmin &&
+  // (its bounds assume the uniform lattice: off on the non-uniform grid)
+  R.screen = !g.yt.yc && den > 0.05 * TC.aa * TC.cc && lmax2 <= 64.0 * dmin * dmin && dmax <= 4.0 * dmin &&
              total < (1ll << 30);
   TriF32& F = R.f;
 #pragma unroll
@@ -384,6 +387,15 @@ __device__ __forceinline__ void tag_exact(const Blk& bk, const Geo& g, const Sur
       double x[3];
 #pragma unroll
       for (int d = 0; d < 3; ++d) x[d] = lat(idx3[d], del[d], d == c ? 0 : 1);
+      double diag2 = g.diag2;
+      bool inbox = true;
+      if (g.yt.yc) {
+        // non-uniform rows: the node's own cell gives the box margin in y
+        // and the diagonal
+        x[1] = ylat(g, idx3[1], c != 1);
+        inbox = row_inside(g, c, idx3[1], fmin(TC.a[1], fmin(TC.b[1], TC.c[1])), fmax(TC.a[1], fmax(TC.b[1], TC.c[1])));
+        diag2 = diag2_at(g, c, idx3[1]);
+      }
       double X[3], wb[3], N[3], P[3];
       closest_point_exact(x, TC, X, wb);
 #pragma unroll
@@ -392,7 +404,7 @@ __device__ __forceinline__ void tag_exact(const Blk& bk, const Geo& g, const Sur
         P[d] = dmul(N[d], N[d]);
       }
       const double n2 = dadd(dadd(P[0], P[1]), P[2]);
-      if (n2 <= g.diag2) {
+      if (inbox && n2 <= diag2) {
         if (n2 == 0.0) {
           tagged = true;   // a node on the surface: alpha = 0 in Eq. new_IB
         } else {
@@ -402,7 +414,8 @@ __device__ __forceinline__ void tag_exact(const Blk& bk, const Geo& g, const Sur
           for (int d = 0; d < 3 && !tagged; ++d) {
 #pragma unroll
             for (int sg = -1; sg <= 1 && !tagged; sg += 2) {
-              const double vd = dsub(lat(idx3[d] + sg, del[d], d == c ? 0 : 1), X[d]);
+              const double xn = d == 1 ? ylat(g, idx3[1] + sg, c != 1) : lat(idx3[d] + sg, del[d], d == c ? 0 : 1);
+              const double vd = dsub(xn, X[d]);
               const double Q = dmul(N[d], vd);
               const double dot = d == 0 ? dadd(dadd(Q, P[1]), P[2])
                                         : (d == 1 ? dadd(dadd(P[0], Q), P[2]) : dadd(dadd(P[0], P[1]), Q));

@@ -546,6 +546,25 @@ def stretched_faces(ny: int, ly: float = 1.0, beta: float = 1.8) -> np.ndarray:
     return y
 
 
+def immersed_wall_channel(nx: int = 64, ny: int = 96, nz: int = 64, y_wall: float = 0.1013, steps: int = 10,
+                          re: float = 100.0, dt: float = 1e-3, force: float = 2.0) -> Workload:
+    """Channel with an immersed rigid wall across the whole periodic box at
+    y = y_wall (the lower wall of the channel cases of Section 4) and a body
+    force along x.  The wall is a plate wider than the box (two triangles);
+    it is meant for a stretched wall-normal grid (stretched_faces) with no
+    node on the wall."""
+    big = 0.3
+    xyz = np.array([[-big, y_wall, -big], [1.0 + big, y_wall, -big], [-big, y_wall, 1.0 + big],
+                    [1.0 + big, y_wall, 1.0 + big]])
+    tri = np.array([[0, 1, 3], [0, 3, 2]], dtype=np.int32)
+
+    def surface_at(t):
+        return xyz.copy(), np.zeros_like(xyz)
+
+    return Workload(f"wallchannel{nx}x{ny}x{nz}", nx, ny, nz, 1.0, 1.0, 1.0, re, dt, steps, tri, surface_at,
+                    lambda t: (force, 0.0, 0.0))
+
+
 def random_fields(nx: int, ny: int, nz: int, seed: int, amp: float = 1.0):
     """Seeded smooth-ish random velocity and pressure fields (v = 0 on the
     walls) for stage-level parity tests."""
