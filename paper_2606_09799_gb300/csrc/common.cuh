@@ -83,7 +83,7 @@ struct DevState {
   float qf_hi[2], qf_lo[2];      // q_F as an unevaluated FP32 pair (mixed correction)
   double sum_a[2];               // sum over C_B of D uhat dV per sub-stage
   double qa[2], qb[2];           // energy-conserving shape: q_F^k = qa + qb (p^k - e^k) (App. B)
-  double sum_qdv[2];             // sum over all cells of q dV (energy-conserving shape)
+  double sum_qdv[2];             // sum over all cells of q dV
   double slip_sum[3];            // sum |eps_i| of the last step
   unsigned int err;              // ERR_* bits
   unsigned int ncand;            // candidates of the current step

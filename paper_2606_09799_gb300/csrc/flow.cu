@@ -1440,13 +1440,14 @@ struct SweepZStream {
   __device__ __forceinline__ void operator()(const Blk& bk) const { sweep_z_stream<T>(bk, g, f, flags32, tb, lfirst); }
 };
 
-// y-sweep on a non-uniform wall-normal grid (no immersed surface, so no
-// identity rows), one thread per line: the rows' coefficients are those of
-// the y part of the Laplacian of the right-hand side, from the spacing
-// table; the line is factorised as it is swept (c' to the scratch array)
-// and du is added to the state on the way back.
+// y-sweep on a non-uniform wall-normal grid, one thread per line: the rows'
+// coefficients are those of the y part of the Laplacian of the right-hand
+// side, from the spacing table, and a forcing node's row is the identity;
+// the line is factorised as it is swept (c' to the scratch array) and du is
+// added to the state on the way back.
 template <typename T>
-__device__ __forceinline__ void sweep_y_stretched(const Blk& bk, const Geo& g, const Fields<T>& f, double beta) {
+__device__ __forceinline__ void sweep_y_stretched(const Blk& bk, const Geo& g, const Fields<T>& f,
+                                                  const unsigned* __restrict__ flags32, double beta) {
   const int c = bk.y;
   const long long t = (long long)bk.x * blockDim.x + threadIdx.x;
   if (t >= (long long)g.nx * g.nz) return;
@@ -1479,6 +1480,11 @@ __device__ __forceinline__ void sweep_y_stretched(const Blk& bk, const Geo& g, c
       if (c != 1) b -= gs * sn2;
       cc = 0.0;
     }
+    if (is_forcing(flags32, cidx(g, i, j, k), c)) {
+      a = 0.0;
+      b = 1.0;
+      cc = 0.0;
+    }
     const double den = b - a * cprev;
     cprev = cc / den;
     prev = ((double)Rl[m * sn] - a * prev) / den;
@@ -1496,8 +1502,9 @@ struct SweepYStretched {
   static constexpr int kThreads = 128;
   Geo g;
   Fields<T> f;
+  const unsigned* flags32;
   double beta;
-  __device__ __forceinline__ void operator()(const Blk& bk) const { sweep_y_stretched<T>(bk, g, f, beta); }
+  __device__ __forceinline__ void operator()(const Blk& bk) const { sweep_y_stretched<T>(bk, g, f, flags32, beta); }
 };
 
 template <typename T>
@@ -1592,7 +1599,7 @@ void launch_sweeps(const Geo& g, const Fields<T>& f, const TagBuffers& b, const 
     // non-uniform wall-normal spacing (beta from the x coefficient, beta / dx^2)
     const long long lines = (long long)g.nx * g.nz;
     ex.launch(dim3((unsigned)((lines + 127) / 128), 3), dim3(128), 0,
-              SweepYStretched<T>{g, f, (double)tb.off[0] * g.dx * g.dx});
+              SweepYStretched<T>{g, f, b.flags32, (double)tb.off[0] * g.dx * g.dx});
   } else if (ex.tune.sweep_y == 1) {
     const long long lines = (long long)g.nx * g.nz;
     ex.launch(dim3((unsigned)((lines + 127) / 128), 3), dim3(128), 0, SweepYStream<T>{g, f, b.flags32, tb, b.lines.y});

@@ -310,6 +310,7 @@ __device__ __forceinline__ void q_final(const Blk& bk, const Geo& g, const doubl
   ds->sum_a[s] = A;
   const double qf = (use_q && VF > 0.0) ? -A / VF : 0.0;
   ds->qf[s] = qf;
+  ds->sum_qdv[s] = A + qf * VF;
   const float qh = (float)qf;
   ds->qf_hi[s] = qh;
   ds->qf_lo[s] = (float)(qf - (double)qh);

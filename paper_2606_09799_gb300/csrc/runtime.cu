@@ -1525,9 +1525,7 @@ ibm_status ibm_get_diag(ibm_handle h, ibm_diag* out) {
   Stage sg[2];
   const int ns = stages(h->desc, sg);
   out->q_f = ds.qf[ns - 1];
-  const double dV = h->g.dx * h->g.dy * h->g.dz;
-  out->sum_q_dv = h->desc.use_q == 2 ? ds.sum_qdv[ns - 1]
-                                     : ds.sum_a[ns - 1] + ds.qf[ns - 1] * (double)(h->g.ncell - (long long)ds.nbound) * dV;
+  out->sum_q_dv = ds.sum_qdv[ns - 1];   // formed with the fluid volume of the q reduction
   out->steps = (int64_t)ds.steps;
   out->ncandidates = ds.ncand;
   out->kernels_per_step = h->kernels_per_step;

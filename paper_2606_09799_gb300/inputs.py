@@ -546,17 +546,15 @@ def stretched_faces(ny: int, ly: float = 1.0, beta: float = 1.8) -> np.ndarray:
     return y
 
 
-def immersed_wall_channel(nx: int = 64, ny: int = 96, nz: int = 64, y_wall: float = 0.1013, steps: int = 10,
-                          re: float = 100.0, dt: float = 1e-3, force: float = 2.0) -> Workload:
+def immersed_wall_channel(nx: int = 64, ny: int = 96, nz: int = 64, y_wall: float = 0.1213, steps: int = 10,
+                          re: float = 100.0, dt: float = 1e-3, force: float = 2.0, nq: int = 1) -> Workload:
     """Channel with an immersed rigid wall across the whole periodic box at
     y = y_wall (the lower wall of the channel cases of Section 4) and a body
-    force along x.  The wall is a plate wider than the box (two triangles);
-    it is meant for a stretched wall-normal grid (stretched_faces) with no
-    node on the wall."""
+    force along x.  The wall is a plate wider than the box (0.3 beyond it on
+    every side; nq x nq quads, two triangles each); it is meant for a
+    stretched wall-normal grid (stretched_faces) with no node on the wall."""
     big = 0.3
-    xyz = np.array([[-big, y_wall, -big], [1.0 + big, y_wall, -big], [-big, y_wall, 1.0 + big],
-                    [1.0 + big, y_wall, 1.0 + big]])
-    tri = np.array([[0, 1, 3], [0, 3, 2]], dtype=np.int32)
+    xyz, tri = plate(nq, 1.0 + 2.0 * big, -big, -big, y_wall)
 
     def surface_at(t):
         return xyz.copy(), np.zeros_like(xyz)
