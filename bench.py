@@ -443,19 +443,37 @@ def ab_leg(args, wl, dxyz, dvel, surf, dev, stream, flush, world, tune):
 
 
 def stretched_leg(args, dev, stream, flush, world):
-    """FP64 path on a non-uniform wall-normal grid: the 128^3 channel with
+    """The non-uniform wall-normal grid leg: the channel alone and with an
+    immersed wall across it (the channel cases of Section 4)."""
+    from paper_2606_09799_gb300 import inputs
+
+    wl = inputs.immersed_wall_channel(nx=128, ny=128, nz=128, y_wall=0.1213, nq=32)
+    wall = (wl.surface(0)[0], wl.tri)
+    out = stretched_run(args, dev, stream, flush, world, None, "fp64")
+    out["with_immersed_wall"] = stretched_run(args, dev, stream, flush, world, wall, "fp64")
+    out["mixed"] = stretched_run(args, dev, stream, flush, world, None, "mixed")
+    out["mixed"]["with_immersed_wall"] = stretched_run(args, dev, stream, flush, world, wall, "mixed")
+    return out
+
+
+def stretched_run(args, dev, stream, flush, world, wall, precision):
+    """One path on a non-uniform wall-normal grid: the 128^3 channel with
     cells clustered at both walls (tanh stretching, 3x taller at mid-channel),
-    no immersed surface, driven by a uniform body force from a seeded random
-    field; same timing protocol as the headline."""
+    with the immersed wall `wall` = (xyz, tri) or none, driven by a uniform
+    body force from a seeded random field; same timing protocol as the
+    headline."""
+    import numpy as np
     import torch
     from paper_2606_09799_gb300 import ibm, inputs
 
     n = 128
     K, W = max(3, min(args.steps, 20)), max(3, args.warmup)
     yf = inputs.stretched_faces(n)
-    sim = ibm.Simulation(n, n, n, re=200.0, dt=5e-4, precision="fp64", stream=stream.cuda_stream, y_faces=yf)
+    sim = ibm.Simulation(n, n, n, re=200.0, dt=5e-4, precision=precision, stream=stream.cuda_stream, y_faces=yf)
     sim.set_fields(*inputs.random_fields(n, n, n, seed=31, amp=0.1))
     sim.set_body_force(8.0 / 200.0, 0.0, 0.0)
+    if wall is not None:
+        sim.set_surface(wall[0], np.zeros_like(wall[0]), wall[1])
     for _ in range(W):
         sim.step(1)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
@@ -469,12 +487,17 @@ def stretched_leg(args, dev, stream, flush, world):
         ev[m][1].record(stream)
     torch.cuda.synchronize()
     ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), dev, world)
+    slip = sim.diag()["slip_l1"]
     prof = ibm.ibm_profile_stages(sim.h, 2)
     sim.close()
-    return {"workload": "stretched128: 128^3 channel, tanh-stretched wall-normal cells (beta 1.8), no surface, "
-                        "body-force driven from a seeded random field; Re=200, dt=5e-4, RK2+CN, FP64",
+    what = ("no surface" if wall is None else
+            "an immersed rigid wall across the box at y = 0.1213 (plate of 2,048 triangles)")
+    return {"workload": "stretched128: 128^3 channel, tanh-stretched wall-normal cells (beta 1.8), " + what + ", "
+                        "body-force driven from a seeded random field; Re=200, dt=5e-4, RK2+CN, "
+                        + ("FP64" if precision == "fp64" else "mixed (FP32 bulk, (hi, lo) velocity, correction solve)"),
             "cells": n ** 3, "steps": K, "value": whole_job_gcups(n ** 3, K, world, ms), "unit": UNIT,
-            "ms_per_step": ms / K, "stages_ms_per_step": {k: v[0] / 2 for k, v in prof.items() if v[1] > 0}}
+            "ms_per_step": ms / K, "slip_l1": slip if wall is not None else None,
+            "stages_ms_per_step": {k: v[0] / 2 for k, v in prof.items() if v[1] > 0}}
 
 
 def large_leg(args, dev, stream, flush):

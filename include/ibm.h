@@ -131,10 +131,11 @@ ibm_status ibm_create_grid(const ibm_grid_desc* desc, void* stream, ibm_handle* 
  * its diagonal come from its own row (cell height for u and w, distance of
  * the centres for v), the probe length is twice that diagonal, and the probe
  * is interpolated between the rows that bracket it; the q term weights every
- * cell by its volume.  Supported for the FP64 path: a batch refuses the
- * handle (IBM_ERR_ARG); ibm_get_loads and ibm_get_pressure_recon return
- * IBM_ERR_STATE (their probes assume a uniform grid); a precision other than
- * IBM_FP64 or invalid face positions return IBM_ERR_ARG. */
+ * cell by its volume.  Both precisions are supported (the mixed path forms
+ * the correction solve's faces and divergence with each row's spacings, in
+ * pair arithmetic).  A batch refuses the handle (IBM_ERR_ARG);
+ * ibm_get_loads and ibm_get_pressure_recon return IBM_ERR_STATE (their
+ * probes assume a uniform grid); invalid face positions return IBM_ERR_ARG. */
 ibm_status ibm_create_grid_stretched(const ibm_grid_desc* desc, const double* y_faces, void* stream,
                                      ibm_handle* out);
 

@@ -1444,7 +1444,7 @@ struct SweepZStream {
 // coefficients are those of the y part of the Laplacian of the right-hand
 // side, from the spacing table, and a forcing node's row is the identity;
 // the line is factorised as it is swept (c' to the scratch array) and du is
-// added to the state on the way back.
+// added to the state on the way back (as a (hi, lo) pair in the mixed path).
 template <typename T>
 __device__ __forceinline__ void sweep_y_stretched(const Blk& bk, const Geo& g, const Fields<T>& f,
                                                   const unsigned* __restrict__ flags32, double beta) {
@@ -1491,10 +1491,19 @@ __device__ __forceinline__ void sweep_y_stretched(const Blk& bk, const Geo& g, c
     Rl[m * sn] = (T)prev;
     Sl[m * sn] = (T)cprev;
   }
+  T* __restrict__ Ll = f.lo[c] ? f.lo[c] + base : nullptr;
   double x = 0.0;
   for (int m = n - 1; m >= 0; --m) {
     x = (double)Rl[m * sn] - (double)Sl[m * sn] * x;
-    Ul[m * sn] = (T)((double)Ul[m * sn] + x);
+    if (Ll) {
+      // velocity state as a (hi, lo) pair: add du without rounding it away
+      float hi = (float)Ul[m * sn], lo = (float)Ll[m * sn];
+      ff_add(hi, lo, (float)x);
+      Ul[m * sn] = (T)hi;
+      Ll[m * sn] = (T)lo;
+    } else {
+      Ul[m * sn] = (T)((double)Ul[m * sn] + x);
+    }
   }
 }
 template <typename T>

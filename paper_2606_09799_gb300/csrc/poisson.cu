@@ -510,14 +510,25 @@ __device__ __forceinline__ T poisson_rhs(const Geo& g, const Fields<T>& f, const
         proj_face(uh1, ul1, (float)mul_rn(cf.cx, ph[r0 + ip] - (T)p0));
         float vh0 = (float)f.v[v0], vl0 = (float)f.lo[1][v0];
         float vh1 = (float)f.v[v0 + n], vl1 = (float)f.lo[1][v0 + n];
-        if (j > 0) proj_face(vh0, vl0, (float)mul_rn(cf.cy, (T)p0 - ph[cell - n]));
-        if (j + 1 < ny) proj_face(vh1, vl1, (float)mul_rn(cf.cy, ph[cell + n] - (T)p0));
+        // non-uniform wall-normal spacing: each face's own gradient
+        // coefficient (as the projection forms it) and 1/h_c of the cell as
+        // a (hi, lo) pair
+        const T cy0 = g.yt.ihc ? mul_rn(cf.adt, (T)g.yt.ihf[j]) : cf.cy;
+        const T cy1 = g.yt.ihc ? mul_rn(cf.adt, (T)g.yt.ihf[j + 1]) : cf.cy;
+        if (j > 0) proj_face(vh0, vl0, (float)mul_rn(cy0, (T)p0 - ph[cell - n]));
+        if (j + 1 < ny) proj_face(vh1, vl1, (float)mul_rn(cy1, ph[cell + n] - (T)p0));
         float wh0 = (float)f.w[cell], wl0 = (float)f.lo[2][cell];
         float wh1 = (float)f.w[wk], wl1 = (float)f.lo[2][wk];
         proj_face(wh0, wl0, (float)mul_rn(cf.cz, (T)p0 - ph[rkm + i]));
         proj_face(wh1, wl1, (float)mul_rn(cf.cz, ph[rkp + i] - (T)p0));
         pair_diff_v(uh1, ul1, uh0, ul0, (float)f.idh[0][0], (float)f.idh[0][1], bx, sx);
-        pair_diff_v(vh1, vl1, vh0, vl0, (float)f.idh[1][0], (float)f.idh[1][1], by, sy);
+        float ihy = (float)f.idh[1][0], ily = (float)f.idh[1][1];
+        if (g.yt.ihc) {
+          const double ih = g.yt.ihc[j];
+          ihy = (float)ih;
+          ily = (float)(ih - (double)ihy);
+        }
+        pair_diff_v(vh1, vl1, vh0, vl0, ihy, ily, by, sy);
         pair_diff_v(wh1, wl1, wh0, wl0, (float)f.idh[2][0], (float)f.idh[2][1], bz, sz);
       }
       two_sum(bx, by, a1, e1);

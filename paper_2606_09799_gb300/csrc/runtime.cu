@@ -1163,7 +1163,7 @@ ibm_status ibm_create_grid_stretched(const ibm_grid_desc* desc, const double* y_
   if (!desc || !y_faces || !out) return IBM_ERR_ARG;
   *out = nullptr;
   const int ny = desc->ny;
-  if (desc->precision != IBM_FP64 || ny < 4 || ny > 4096) return IBM_ERR_ARG;
+  if (ny < 4 || ny > 4096) return IBM_ERR_ARG;
   if (y_faces[0] != 0.0 || !(fabs(y_faces[ny] - desc->ly) <= 1e-12 * desc->ly)) return IBM_ERR_ARG;
   for (int j = 0; j < ny; ++j)
     if (!(y_faces[j + 1] > y_faces[j])) return IBM_ERR_ARG;

@@ -1,6 +1,7 @@
 """Non-uniform wall-normal grid (Section 2: variable cell height in the
-wall-normal direction) on the GPU, FP64 path, with and without immersed
-surfaces (Algorithm 1 and the probe of Section 3.1 on the local cell).
+wall-normal direction) on the GPU, FP64 and mixed paths, with and without
+immersed surfaces (Algorithm 1 and the probe of Section 3.1 on the local
+cell).
 
 Bars: tags bit-exact against the CPU oracle; fields within 1e-10 of it
 after several steps (RK2+CN and AB+CN, no-slip and free-slip walls, a
@@ -8,10 +9,14 @@ moving sphere, an immersed wall across the channel), from a random initial
 field with a body force; uniform face positions through the stretched entry
 point give the uniform path's tags and fields; the projected field has no
 divergence (computed here from the face positions); unsupported
-combinations are refused."""
+combinations are refused.  The mixed paths meet the bars of the uniform
+grid: velocity within 1e-5 of the oracle, fluid-cell divergence within
+1e-7 U/dx (1e-5 for the single FP32 solve), no-slip error within 5% of the
+oracle's."""
 import numpy as np
 import pytest
 
+from oracle import oracle as orc
 from oracle.oracle import OracleSim, tag as oracle_tag
 from paper_2606_09799_gb300 import ibm, inputs
 
@@ -66,8 +71,6 @@ def test_projected_field_has_no_divergence():
 
 def test_unsupported_combinations_are_refused():
     yf = inputs.stretched_faces(NY)
-    with pytest.raises(ibm.IbmError):
-        ibm.Simulation(NX, NY, NZ, precision="mixed", y_faces=yf)
     with pytest.raises(ibm.IbmError):
         ibm.Simulation(NX, NY, NZ, precision="fp64", y_faces=yf[::-1].copy())
     g = ibm.Simulation(NX, NY, NZ, precision="fp64", y_faces=yf)
@@ -176,3 +179,79 @@ def test_loads_are_refused_on_a_stretched_grid():
         g.loads()
     with pytest.raises(ibm.IbmError):
         g.pressure_recon()
+
+
+# ---------------------------------------------------------------------------
+# mixed paths on the stretched grid
+# ---------------------------------------------------------------------------
+DIV_TOL = {"mixed": 1e-7, "mixed_fast": 1e-5}
+
+
+def divergence_error(g, yf, nx, nz):
+    """max over fluid cells of |D u - q_F| (face positions from yf), in units
+    of U_ref / dx."""
+    ny = len(yf) - 1
+    gr = orc.make_grid(nx, ny, nz, yfaces=yf)
+    u, v, w, _ = g.fields()
+    d = orc.divergence(gr, u, v, w)
+    isb = orc.boundary_cells(gr, g.tags())
+    return np.abs(d - g.diag()["q_f"])[isb == 0].max() * gr.dx
+
+
+@pytest.mark.parametrize("precision", ["mixed", "mixed_fast"])
+@pytest.mark.parametrize("scheme,ybc", [("rk2", 0), ("ab", 1)])
+def test_stretched_mixed_channel_matches_oracle(precision, scheme, ybc):
+    yf = inputs.stretched_faces(NY)
+    u, v, w, p = inputs.random_fields(NX, NY, NZ, seed=21, amp=0.3)
+    o = OracleSim(NX, NY, NZ, re=120.0, dt=2e-3, scheme=scheme, ybc=ybc, yfaces=yf)
+    g = ibm.Simulation(NX, NY, NZ, re=120.0, dt=2e-3, scheme=scheme, ybc=ybc, precision=precision, y_faces=yf)
+    for sim in (o, g):
+        sim.set_fields(u, v, w, p)
+        sim.set_body_force(2.0, 0.0, 0.3)
+        sim.step(5)
+    gu, gv, gw, _ = g.fields()
+    err = max(np.abs(o.u - gu).max(), np.abs(o.v - gv).max(), np.abs(o.w - gw).max())
+    assert err <= 1e-5 * max(1.0, np.abs(o.u).max()), err
+    assert divergence_error(g, yf, NX, NZ) <= DIV_TOL[precision] * max(1.0, np.abs(o.u).max())
+
+
+@pytest.mark.parametrize("precision", ["mixed", "mixed_fast"])
+def test_stretched_mixed_moving_sphere_matches_oracle(precision):
+    wl = inputs.oscillating_sphere(n=32, steps=8, subdiv=2)
+    yf = inputs.stretched_faces(40)
+    o = OracleSim(32, 40, 32, re=wl.re, dt=wl.dt, yfaces=yf)
+    g = ibm.Simulation(32, 40, 32, re=wl.re, dt=wl.dt, precision=precision, y_faces=yf)
+    for s in range(8):
+        xyz, vel = wl.surface(s)
+        for sim in (o, g):
+            sim.set_surface(xyz, vel, wl.tri)
+            sim.step()
+    gu, gv, gw, _ = g.fields()
+    err = max(np.abs(o.u - gu).max(), np.abs(o.v - gv).max(), np.abs(o.w - gw).max())
+    assert err <= 1e-5 * max(1.0, np.abs(o.u).max()), err
+    for c, t in enumerate(g.tags()):
+        np.testing.assert_array_equal(t, o.owners[c], err_msg=f"component {c}")
+    assert divergence_error(g, yf, 32, 32) <= DIV_TOL[precision]
+    slip = g.diag()["slip_l1"]
+    assert abs(slip - o.last["slip"]) <= 0.05 * o.last["slip"]
+
+
+def test_stretched_mixed_immersed_wall_channel_matches_oracle():
+    wl = inputs.immersed_wall_channel(nx=32, ny=48, nz=32, y_wall=0.1213, steps=6)
+    yf = inputs.stretched_faces(48)
+    init = inputs.random_fields(32, 48, 32, seed=5, amp=0.1)
+    o = OracleSim(32, 48, 32, re=wl.re, dt=wl.dt, yfaces=yf)
+    g = ibm.Simulation(32, 48, 32, re=wl.re, dt=wl.dt, precision="mixed", y_faces=yf)
+    for sim in (o, g):
+        sim.set_fields(*init)
+    for s in range(6):
+        xyz, vel = wl.surface(s)
+        for sim in (o, g):
+            sim.set_surface(xyz, vel, wl.tri)
+            sim.set_body_force(*wl.body_force_at(s * wl.dt))
+            sim.step()
+    gu, gv, gw, _ = g.fields()
+    err = max(np.abs(o.u - gu).max(), np.abs(o.v - gv).max(), np.abs(o.w - gw).max())
+    assert err <= 1e-5 * max(1.0, np.abs(o.u).max()), err
+    assert divergence_error(g, yf, 32, 32) <= DIV_TOL["mixed"] * max(1.0, np.abs(o.u).max())
+    assert abs(g.diag()["slip_l1"] - o.last["slip"]) <= 0.05 * o.last["slip"]
