@@ -25,7 +25,12 @@ constexpr uint8_t FLAG_U = 1, FLAG_V = 2, FLAG_W = 4, FLAG_B = 8;
 // hc[j] = height of cell j; hf[j] = distance of the centres across face j
 // (ny + 1); yc[j + 1] = centre of row j for j in [-1, ny] and yv[j + 1] =
 // face j for j in [-1, ny + 1], rows beyond a wall being mirror images;
-// hmax = the largest of hc and hf.  All null (0) on a uniform grid.
+// hmax = the largest of hc and hf.  ysw: the y sweep's rows for lines
+// without forcing nodes (tangential components: a, 1/pivot, c' over ny rows;
+// then v: the same over ny - 1 rows).  ysw2: for lines with forcing nodes,
+// 1/pivot and c' of a segment that starts at row s, at [s][m] (tangential
+// components: two ny x ny arrays; then v: two (ny-1) x (ny-1)); null when ny
+// is above 1024.  All null (0) on a uniform grid.
 struct YTab {
   const double* ihc;
   const double* ihf;
@@ -33,6 +38,8 @@ struct YTab {
   const double* hf;
   const double* yc;
   const double* yv;
+  const double* ysw;
+  const double* ysw2;
   double hmax;
 };
 

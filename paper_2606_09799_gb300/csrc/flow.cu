@@ -1445,9 +1445,12 @@ struct SweepZStream {
 // side, from the spacing table, and a forcing node's row is the identity;
 // the line is factorised as it is swept (c' to the scratch array) and du is
 // added to the state on the way back (as a (hi, lo) pair in the mixed path).
+// A line without forcing rows (most lines) takes its rows' a, 1/pivot and
+// c' from the table built with the grid, with no division and no scratch.
 template <typename T>
 __device__ __forceinline__ void sweep_y_stretched(const Blk& bk, const Geo& g, const Fields<T>& f,
-                                                  const unsigned* __restrict__ flags32, double beta) {
+                                                  const unsigned* __restrict__ flags32,
+                                                  const int* __restrict__ lfirst, double beta) {
   const int c = bk.y;
   const long long t = (long long)bk.x * blockDim.x + threadIdx.x;
   if (t >= (long long)g.nx * g.nz) return;
@@ -1459,39 +1462,85 @@ __device__ __forceinline__ void sweep_y_stretched(const Blk& bk, const Geo& g, c
   T* __restrict__ Rl = f.R[c] + base;
   T* __restrict__ Sl = f.scr + comp_off(g, c) + base;
   T* __restrict__ Ul = comp_ptr(f, c) + base;
-  const double gs = g.ybc == 0 ? -1.0 : 1.0;
-  double prev = 0.0, cprev = 0.0;
-  for (int m = 0; m < n; ++m) {
-    const int j = jj0 + m;
-    double sb, sn2;
-    if (c != 1) {
-      sb = beta * g.yt.ihc[j] * g.yt.ihf[j];
-      sn2 = beta * g.yt.ihc[j] * g.yt.ihf[j + 1];
-    } else {
-      sb = beta * g.yt.ihf[j] * g.yt.ihc[j - 1];
-      sn2 = beta * g.yt.ihf[j] * g.yt.ihc[j];
-    }
-    double a = -sb, b = 1.0 + sb + sn2, cc = -sn2;
-    if (m == 0) {
-      if (c != 1) b -= gs * sb;   // wall ghost du_{-1} = gs du_0
-      a = 0.0;
-    }
-    if (m == n - 1) {
-      if (c != 1) b -= gs * sn2;
-      cc = 0.0;
-    }
-    if (is_forcing(flags32, cidx(g, i, j, k), c)) {
-      a = 0.0;
-      b = 1.0;
-      cc = 0.0;
-    }
-    const double den = b - a * cprev;
-    cprev = cc / den;
-    prev = ((double)Rl[m * sn] - a * prev) / den;
-    Rl[m * sn] = (T)prev;
-    Sl[m * sn] = (T)cprev;
-  }
   T* __restrict__ Ll = f.lo[c] ? f.lo[c] + base : nullptr;
+  if (lfirst[line_y(g, c, i, k)] >= g.ny) {
+    const double* __restrict__ ta = g.yt.ysw + (c == 1 ? 3ll * g.ny : 0);
+    const double* __restrict__ tv = ta + n;
+    const double* __restrict__ tc = tv + n;
+    double p = 0.0;
+    for (int m = 0; m < n; ++m) {
+      p = ((double)Rl[m * sn] - __ldg(ta + m) * p) * __ldg(tv + m);
+      Rl[m * sn] = (T)p;
+    }
+    double x = 0.0;
+    for (int m = n - 1; m >= 0; --m) {
+      x = (double)Rl[m * sn] - __ldg(tc + m) * x;
+      if (Ll) {
+        float hi = (float)Ul[m * sn], lo = (float)Ll[m * sn];
+        ff_add(hi, lo, (float)x);
+        Ul[m * sn] = (T)hi;
+        Ll[m * sn] = (T)lo;
+      } else {
+        Ul[m * sn] = (T)((double)Ul[m * sn] + x);
+      }
+    }
+    return;
+  }
+  if (g.yt.ysw2) {
+    // forcing rows are identity rows; the segment after one restarts the
+    // elimination, its pivots read at [start row][row]
+    const double* __restrict__ ta = g.yt.ysw + (c == 1 ? 3ll * g.ny : 0);
+    const double* __restrict__ iv2 = g.yt.ysw2 + (c == 1 ? 2ll * g.ny * g.ny : 0);
+    const double* __restrict__ cp2 = iv2 + (long long)n * n;
+    long long s0 = 0;
+    double p = 0.0;
+    for (int m = 0; m < n; ++m) {
+      double cq = 0.0;
+      if (is_forcing(flags32, cidx(g, i, jj0 + m, k), c)) {
+        p = (double)Rl[m * sn];
+        s0 = m + 1;
+      } else {
+        const long long id = s0 * n + m;
+        p = ((double)Rl[m * sn] - __ldg(ta + m) * p) * __ldg(iv2 + id);
+        cq = __ldg(cp2 + id);
+      }
+      Rl[m * sn] = (T)p;
+      Sl[m * sn] = (T)cq;
+    }
+  } else {
+    const double gs = g.ybc == 0 ? -1.0 : 1.0;
+    double prev = 0.0, cprev = 0.0;
+    for (int m = 0; m < n; ++m) {
+      const int j = jj0 + m;
+      double sb, sn2;
+      if (c != 1) {
+        sb = beta * g.yt.ihc[j] * g.yt.ihf[j];
+        sn2 = beta * g.yt.ihc[j] * g.yt.ihf[j + 1];
+      } else {
+        sb = beta * g.yt.ihf[j] * g.yt.ihc[j - 1];
+        sn2 = beta * g.yt.ihf[j] * g.yt.ihc[j];
+      }
+      double a = -sb, b = 1.0 + sb + sn2, cc = -sn2;
+      if (m == 0) {
+        if (c != 1) b -= gs * sb;   // wall ghost du_{-1} = gs du_0
+        a = 0.0;
+      }
+      if (m == n - 1) {
+        if (c != 1) b -= gs * sn2;
+        cc = 0.0;
+      }
+      if (is_forcing(flags32, cidx(g, i, j, k), c)) {
+        a = 0.0;
+        b = 1.0;
+        cc = 0.0;
+      }
+      const double den = b - a * cprev;
+      cprev = cc / den;
+      prev = ((double)Rl[m * sn] - a * prev) / den;
+      Rl[m * sn] = (T)prev;
+      Sl[m * sn] = (T)cprev;
+    }
+  }
   double x = 0.0;
   for (int m = n - 1; m >= 0; --m) {
     x = (double)Rl[m * sn] - (double)Sl[m * sn] * x;
@@ -1512,8 +1561,11 @@ struct SweepYStretched {
   Geo g;
   Fields<T> f;
   const unsigned* flags32;
+  const int* lfirst;
   double beta;
-  __device__ __forceinline__ void operator()(const Blk& bk) const { sweep_y_stretched<T>(bk, g, f, flags32, beta); }
+  __device__ __forceinline__ void operator()(const Blk& bk) const {
+    sweep_y_stretched<T>(bk, g, f, flags32, lfirst, beta);
+  }
 };
 
 template <typename T>
@@ -1608,7 +1660,7 @@ void launch_sweeps(const Geo& g, const Fields<T>& f, const TagBuffers& b, const 
     // non-uniform wall-normal spacing (beta from the x coefficient, beta / dx^2)
     const long long lines = (long long)g.nx * g.nz;
     ex.launch(dim3((unsigned)((lines + 127) / 128), 3), dim3(128), 0,
-              SweepYStretched<T>{g, f, b.flags32, (double)tb.off[0] * g.dx * g.dx});
+              SweepYStretched<T>{g, f, b.flags32, b.lines.y, (double)tb.off[0] * g.dx * g.dx});
   } else if (ex.tune.sweep_y == 1) {
     const long long lines = (long long)g.nx * g.nz;
     ex.launch(dim3((unsigned)((lines + 127) / 128), 3), dim3(128), 0, SweepYStream<T>{g, f, b.flags32, tb, b.lines.y});

@@ -1172,7 +1172,7 @@ ibm_status ibm_create_grid_stretched(const ibm_grid_desc* desc, const double* y_
   if (st != IBM_OK) return st;
   // spacing tables: cell heights, centre distances across faces (mirrored
   // centres at the walls), as the oracle defines them
-  std::vector<double> t(6ull * ny + 7);
+  std::vector<double> t(6ull * ny + 7 + 6ull * ny - 3);
   double* ihc = t.data();
   double* ihf = ihc + ny;
   double* hc = ihf + ny + 1;
@@ -1192,13 +1192,98 @@ ibm_status ibm_create_grid_stretched(const ibm_grid_desc* desc, const double* y_
   for (int j = 0; j <= ny; ++j) yv[j + 1] = y_faces[j];
   yv[0] = -y_faces[1];
   yv[ny + 2] = 2.0 * y_faces[ny] - y_faces[ny - 1];
+  // y sweep rows of a line without forcing nodes (tangential components:
+  // ny rows with the wall ghost in the first and last; v: ny - 1 interior
+  // rows), with beta as the sweep kernel receives it (the x table's
+  // coefficient times dx^2, in the path's own type)
+  {
+    const double ox = desc->precision == IBM_FP64 ? h->tbl_off[0] : (double)(float)h->tbl_off[0];
+    const double beta = ox * h->g.dx * h->g.dx;
+    const double gs = h->g.ybc == 0 ? -1.0 : 1.0;
+    double* ysw = yv + ny + 3;
+    for (int kind = 0; kind < 2; ++kind) {
+      const bool tang = kind == 0;
+      const int n = tang ? ny : ny - 1, jj0 = tang ? 0 : 1;
+      double* ta = ysw + (tang ? 0 : 3 * ny);
+      double* tv = ta + n;
+      double* tcp = tv + n;
+      double cprev = 0.0;
+      for (int m = 0; m < n; ++m) {
+        const int j = jj0 + m;
+        volatile double sb, sn;
+        if (tang) {
+          sb = beta * ihc[j] * ihf[j];
+          sn = beta * ihc[j] * ihf[j + 1];
+        } else {
+          sb = beta * ihf[j] * ihc[j - 1];
+          sn = beta * ihf[j] * ihc[j];
+        }
+        volatile double a = -sb, b = 1.0 + sb + sn, cc = -sn;
+        if (m == 0) {
+          if (tang) b = b - gs * sb;
+          a = 0.0;
+        }
+        if (m == n - 1) {
+          if (tang) b = b - gs * sn;
+          cc = 0.0;
+        }
+        volatile double den = b - a * cprev;
+        cprev = cc / den;
+        ta[m] = a;
+        tv[m] = 1.0 / den;
+        tcp[m] = cprev;
+      }
+    }
+  }
+  // segments that start after a forcing row: 1/pivot and c' at [s][m]
+  std::vector<double> t2;
+  if (ny <= 1024) {
+    const double ox = desc->precision == IBM_FP64 ? h->tbl_off[0] : (double)(float)h->tbl_off[0];
+    const double beta = ox * h->g.dx * h->g.dx;
+    const double gs = h->g.ybc == 0 ? -1.0 : 1.0;
+    t2.assign(2ull * ny * ny + 2ull * (ny - 1) * (ny - 1), 0.0);
+    for (int kind = 0; kind < 2; ++kind) {
+      const bool tang = kind == 0;
+      const int n = tang ? ny : ny - 1, jj0 = tang ? 0 : 1;
+      double* iv2 = t2.data() + (tang ? 0 : 2ull * ny * ny);
+      double* cp2 = iv2 + (size_t)n * n;
+      for (int s0 = 0; s0 < n; ++s0) {
+        double cprev = 0.0;
+        for (int m = s0; m < n; ++m) {
+          const int j = jj0 + m;
+          volatile double sb, sn;
+          if (tang) {
+            sb = beta * ihc[j] * ihf[j];
+            sn = beta * ihc[j] * ihf[j + 1];
+          } else {
+            sb = beta * ihf[j] * ihc[j - 1];
+            sn = beta * ihf[j] * ihc[j];
+          }
+          volatile double a = -sb, b = 1.0 + sb + sn, cc = -sn;
+          if (m == 0) {
+            if (tang) b = b - gs * sb;
+            a = 0.0;
+          }
+          if (m == n - 1) {
+            if (tang) b = b - gs * sn;
+            cc = 0.0;
+          }
+          volatile double den = b - a * cprev;
+          cprev = cc / den;
+          iv2[(size_t)s0 * n + m] = 1.0 / den;
+          cp2[(size_t)s0 * n + m] = cprev;
+        }
+      }
+    }
+  }
   double smin = hc[0], smax = hc[0];
   for (int j = 0; j < ny; ++j) { smin = std::min(smin, hc[j]); smax = std::max(smax, hc[j]); }
   for (int j = 0; j <= ny; ++j) { smin = std::min(smin, hf[j]); smax = std::max(smax, hf[j]); }
   h->ytab = (double*)upload_vec<double>(h, t);
+  double* ysw2 = t2.empty() ? nullptr : (double*)upload_vec<double>(h, t2);
   const size_t nspec = (size_t)h->g.nz * h->g.ny * h->g.nkx;
   h->pal = (double*)dalloc(h, nspec * 8);
-  if (!h->ytab || !h->pal) {
+  if (!h->ytab || !h->pal || (!t2.empty() && !ysw2)) {
     ibm_destroy(h);
     return IBM_ERR_OOM;
   }
@@ -1208,6 +1293,8 @@ ibm_status ibm_create_grid_stretched(const ibm_grid_desc* desc, const double* y_
   h->g.yt.hf = h->ytab + 3 * ny + 1;
   h->g.yt.yc = h->ytab + 4 * ny + 2;
   h->g.yt.yv = h->ytab + 5 * ny + 4;
+  h->g.yt.ysw = h->ytab + 6 * ny + 7;
+  h->g.yt.ysw2 = ysw2;
   h->g.yt.hmax = smax;
   h->ysp_min = smin;
   launch_build_poisson_tables_nu(h->g, h->lamx, h->lamz, h->pcp, h->pinv, h->pal, h->user);
