@@ -246,7 +246,9 @@ typedef struct {
   int fft_plane;      /* 1 separate x and z transform kernels, 2 both fused per y-plane (when its
                          half-spectrum fits shared memory) */
   int sweep_y;        /* z and y sweeps: 0 as sweep_zy, 1 one thread per line with its rows streamed
-                         through registers (any line length) */
+                         through registers (any line length), 2 as 1 for z, and for y tiles of 32
+                         lines staged in shared memory by bulk asynchronous copies (where every row
+                         starts on a 16-byte boundary and the tile fits; else as 1) */
   double ms_per_step; /* set by the autotuners: measured time per step of the chosen shapes */
 } ibm_tune;
 

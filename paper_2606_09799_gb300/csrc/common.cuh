@@ -13,6 +13,7 @@ constexpr unsigned ERR_CAND_OVERFLOW = 2u;   // tagging candidate list overflowe
 constexpr unsigned ERR_LIST_OVERFLOW = 4u;   // forcing / boundary list overflowed
 constexpr unsigned ERR_NONFINITE = 8u;       // NaN/Inf met in a reduction
 constexpr unsigned ERR_DEGENERATE = 16u;     // a triangle of zero area
+constexpr unsigned ERR_WAIT = 32u;           // a bounded wait on an asynchronous copy ran out
 
 // Per-cell flag bits: the velocity nodes of the cell's lower faces that are
 // forcing nodes, and whether the cell is a boundary cell (Section 3.2).

@@ -11,6 +11,8 @@
 
 #include "common.cuh"
 #include "geometry.cuh"
+#include <cuda.h>
+#include <mutex>
 #include "launch.h"
 
 namespace ibm {
@@ -1579,6 +1581,226 @@ struct SweepYStream {
   __device__ __forceinline__ void operator()(const Blk& bk) const { sweep_y_stream<T>(bk, g, f, flags32, tb, lfirst); }
 };
 
+// y-sweep with each tile staged by TMA: one CTA (one warp) per 32
+// consecutive lines of one (k, component).  R, u^s and, in the mixed path,
+// the low parts of the tile are one tensor copy each (a 32 x rows box of the
+// [k][j][i] array) into shared memory, completing on one mbarrier; the warp
+// then runs the recurrences of the streamed sweep from shared memory (R
+// overwritten in place, c' from the tables or, on lines crossing a body,
+// the scratch array) and writes uhat to global memory.  So R and u^s are
+// read once and u written once, and several CTAs per SM overlap one tile's
+// copies with another's recurrences.
+constexpr int SYT_W = 32;                              // lines per tile (128 B of FP32 per row)
+constexpr long long SYT_WAIT_CYCLES = 4000000000ll;   // about 2 s at the top SM clock
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// Wait for phase `parity` of the mbarrier at `bar`, giving up after a fixed
+// number of cycles (false).
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+  const long long t0 = clock64();
+  while (true) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > SYT_WAIT_CYCLES) return false;
+  }
+}
+
+// One box of a 3-D tensor map (coordinates x fastest) into shared memory.
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, unsigned bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];\n" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+
+template <typename T>
+struct SweepYTma;
+
+template <typename T>
+__device__ __forceinline__ void sweep_y_tma(const Blk& bk, const SweepYTma<T>& op) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) unsigned long long bar_mem;
+  const Geo& g = op.g;
+  const Fields<T>& f = op.f;
+  const SweepTables<T>& tb = op.tb;
+  const int c = (int)bk.z, k = (int)bk.y;
+  const int i0 = (int)bk.x * SYT_W;
+  const int lane = threadIdx.x;
+  const int jj0 = c == 1 ? 1 : 0;
+  const int n = c == 1 ? g.ny - 1 : g.ny;
+  const int nl = min(SYT_W, g.nx - i0);
+  const int sn = g.nx;
+  const long long base = fidx(g, c, i0, jj0, k);
+  const bool pair = f.lo[c] != nullptr;
+  T* Rt = reinterpret_cast<T*>(smem_raw);
+  T* Ut = Rt + (size_t)n * SYT_W;
+  T* Lt = Ut + (size_t)n * SYT_W;
+  T* ivS = pair ? Lt + (size_t)n * SYT_W : Lt;   // 1/pivot and c' of a line without forcing rows
+  T* cqS = ivS + n;
+  const unsigned bar = smem_addr(&bar_mem);
+  if (lane == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    const unsigned box = (unsigned)(SYT_W * n * sizeof(T));
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(box * (pair ? 3u : 2u))
+                 : "memory");
+    tma_load_3d(Rt, &op.tm[c][0], i0, jj0, k, bar);
+    tma_load_3d(Ut, &op.tm[c][1], i0, jj0, k, bar);
+    if (pair) tma_load_3d(Lt, &op.tm[c][2], i0, jj0, k, bar);
+  }
+  // while the copies are in flight: the rows of a line without forcing rows
+  // (one wall segment) to shared memory, so the recurrences read no global
+  // memory
+  const bool tang = c != 1;
+  for (int r = lane; r < n; r += SYT_W) {
+    const bool last = r == n - 1;
+    ivS[r] = tang ? __ldg((last ? tb.yinvLW : tb.yinvW) + r) : __ldg(tb.vinvR + r);
+    cqS[r] = last ? (T)0 : __ldg((tang ? tb.ycpW : tb.vcpR) + r);
+  }
+  __syncwarp();
+  if (!mbar_wait(bar, 0)) {
+    // the copies did not complete: report, give them one more bounded wait
+    // (they write this block's shared memory) and leave the tile untouched
+    if (lane == 0) atomicOr(&op.ds->err, ERR_WAIT);
+    mbar_wait(bar, 0);
+    return;
+  }
+  if (lane >= nl) return;
+  T* Ug = comp_ptr(f, c) + base;
+  T* Lg = pair ? f.lo[c] + base : nullptr;
+  const int i = i0 + lane;
+  const T a = -tb.off[1];
+  const bool any = op.lfirst[line_y(g, c, i, k)] < g.ny;
+  if (!any) {
+    // one wall segment: p_j = (r_j - a p_{j-1}) iv_j, x_j = p_j - c'_j x_{j+1}
+    T p = (T)0;
+#pragma unroll 8
+    for (int r = 0; r < n; ++r) {
+      p = fma(r == 0 ? (T)0 : -a, p, Rt[r * SYT_W + lane]) * ivS[r];
+      Rt[r * SYT_W + lane] = p;
+    }
+    T x = (T)0;
+#pragma unroll 8
+    for (int r = n - 1; r >= 0; --r) {
+      x = fma(-cqS[r], x, Rt[r * SYT_W + lane]);
+      if (pair) {
+        float hi = (float)Ut[r * SYT_W + lane], lo = (float)Lt[r * SYT_W + lane];
+        ff_add(hi, lo, (float)x);
+        Ug[(long long)r * sn + lane] = (T)hi;
+        Lg[(long long)r * sn + lane] = (T)lo;
+      } else {
+        Ug[(long long)r * sn + lane] = Ut[r * SYT_W + lane] + x;
+      }
+    }
+    return;
+  }
+  T* __restrict__ Sl = f.scr + comp_off(g, c) + base + lane;
+  const unsigned char* __restrict__ Fl = reinterpret_cast<const unsigned char*>(op.flags32) + cidx(g, i, jj0, k);
+  // ---- forward (the streamed sweep's recurrence, segment restarts at forcing rows)
+  T prev = (T)0;
+  int m = 0;
+  bool segW = tang;
+  for (int r = 0; r < n; ++r) {
+    const bool frc = any && ((Fl[(long long)r * sn] >> c) & 1);
+    const bool last = r == n - 1;
+    const T* ivt = !tang ? tb.vinvR : (last ? (segW ? tb.yinvLW : tb.yinvLR) : (segW ? tb.yinvW : tb.yinvR));
+    const T* cpt = !tang ? tb.vcpR : (segW ? tb.ycpW : tb.ycpR);
+    T iv = (T)1, cq = (T)0, am = (T)0;
+    if (!frc) {
+      iv = __ldg(ivt + m);
+      if (!last) cq = __ldg(cpt + m);
+      am = a;
+    }
+    m = frc ? 0 : m + 1;
+    segW = segW && !frc;
+    prev = fma(-am, prev, Rt[r * SYT_W + lane]) * iv;
+    Rt[r * SYT_W + lane] = prev;
+    if (any) Sl[(long long)r * sn] = cq;
+  }
+  // ---- backward: x_j = p_j - c'_j x_{j+1}; uhat = u^s + x
+  const T* cpw = tang ? tb.ycpW : tb.vcpR;   // c' of a line without forcing rows (one wall segment)
+  T x = (T)0;
+  for (int r = n - 1; r >= 0; --r) {
+    const T cv = any ? Sl[(long long)r * sn] : (r == n - 1 ? (T)0 : __ldg(cpw + r));
+    x = fma(-cv, x, Rt[r * SYT_W + lane]);
+    if (pair) {
+      float hi = (float)Ut[r * SYT_W + lane], lo = (float)Lt[r * SYT_W + lane];
+      ff_add(hi, lo, (float)x);
+      Ug[(long long)r * sn + lane] = (T)hi;
+      Lg[(long long)r * sn + lane] = (T)lo;
+    } else {
+      Ug[(long long)r * sn + lane] = Ut[r * SYT_W + lane] + x;
+    }
+  }
+}
+template <typename T>
+struct SweepYTma {
+  static constexpr int kThreads = SYT_W;
+  CUtensorMap tm[3][3];   // [component][R, u^s, low parts]
+  Geo g;
+  Fields<T> f;
+  const unsigned* flags32;
+  SweepTables<T> tb;
+  const int* lfirst;
+  DevState* ds;
+  __device__ __forceinline__ void operator()(const Blk& bk) const { sweep_y_tma<T>(bk, *this); }
+};
+
+// cuTensorMapEncodeTiled from the driver, looked up once (null if absent).
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiled encode_tiled() {
+  static std::once_flag once;
+  static EncodeTiled fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiled>(p);
+  });
+  return fn;
+}
+
+// The TMA y sweep's maps for this grid, or false where it cannot run: rows of
+// 16-byte multiples on 16-byte boundaries, at least one full tile of lines,
+// at most 256 rows (one box), and a tile that fits shared memory.
+template <typename T>
+static bool sweep_y_tma_maps(const Geo& g, const Fields<T>& f, int ny_shape, SweepYTma<T>& op) {
+  const EncodeTiled enc = encode_tiled();
+  if (!enc || (g.nx * sizeof(T)) % 16 != 0 || g.nx < SYT_W || g.ny > 256) return false;
+  if (((size_t)(f.lo[0] ? 3 : 2) * SYT_W + 2) * ny_shape * sizeof(T) > 200u * 1024u) return false;
+  for (int c = 0; c < 3; ++c) {
+    T* arr[3] = {f.R[c], c == 0 ? f.u : (c == 1 ? f.v : f.w), f.lo[c]};
+    const cuuint64_t pl = (cuuint64_t)planes(g, c);
+    const cuuint64_t dims[3] = {(cuuint64_t)g.nx, pl, (cuuint64_t)g.nz};
+    const cuuint64_t strides[2] = {(cuuint64_t)g.nx * sizeof(T), (cuuint64_t)g.nx * pl * sizeof(T)};
+    const cuuint32_t box[3] = {(cuuint32_t)SYT_W, (cuuint32_t)(c == 1 ? g.ny - 1 : g.ny), 1u};
+    const cuuint32_t es[3] = {1u, 1u, 1u};
+    for (int q = 0; q < 3; ++q) {
+      if (!arr[q]) {
+        memset(&op.tm[c][q], 0, sizeof(CUtensorMap));
+        continue;
+      }
+      if (reinterpret_cast<uintptr_t>(arr[q]) & 15u) return false;
+      if (enc(&op.tm[c][q], sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3,
+              arr[q], dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    }
+  }
+  return true;
+}
+
 template <typename T>
 static size_t sweep_smem(int W, int n, int ld, int tiles = 1) {
   return (size_t)tiles * W * ld * sizeof(T) + (size_t)W * n;
@@ -1621,10 +1843,29 @@ static bool sweep_lanes_launch(const Geo& g, const Fields<T>& f, const TagBuffer
   return true;
 }
 
+// The TMA y sweep of one simulation (never a batch: its tensor maps travel
+// in the kernel's parameters), if its maps can be made; false otherwise.
+template <typename T>
+static bool sweep_y_tma_ok(const Geo& g, const Fields<T>& f, const TagBuffers& b, const SweepTables<T>& tb,
+                           DevState* ds, int ny_shape, Exec& ex) {
+  SweepYTma<T> op;
+  if (!sweep_y_tma_maps<T>(g, f, ny_shape, op)) return false;
+  op.g = g;
+  op.f = f;
+  op.flags32 = b.flags32;
+  op.tb = tb;
+  op.lfirst = b.lines.y;
+  op.ds = ds;
+  const size_t smem = ((size_t)(f.lo[0] ? 3 : 2) * SYT_W + 2) * ny_shape * sizeof(T);
+  ex.launch(dim3((unsigned)((g.nx + SYT_W - 1) / SYT_W), (unsigned)g.nz, 3), dim3(SYT_W), smem, op);
+  return true;
+}
+
 // Launch shapes (lines per block, registers per lane) follow ex.shape, so
 // every instance of a batch uses the same ones; grids follow the instance.
 template <typename T>
-void launch_sweeps(const Geo& g, const Fields<T>& f, const TagBuffers& b, const SweepTables<T>& tb, Exec& ex) {
+void launch_sweeps(const Geo& g, const Fields<T>& f, const TagBuffers& b, const SweepTables<T>& tb, DevState* ds,
+                   Exec& ex) {
   const Geo& sh = ex.shape;
   ex.mark(ST_SWEEP_X);
   if (sizeof(T) == 4 && sh.nx <= 1024) {
@@ -1646,7 +1887,7 @@ void launch_sweeps(const Geo& g, const Fields<T>& f, const TagBuffers& b, const 
   // tuning asks for the shared-memory tile with one thread per line
   const bool lanes = sizeof(T) == 4 && ex.tune.sweep_zy != 1;
   ex.mark(ST_SWEEP_Z);
-  if (ex.tune.sweep_y == 1) {
+  if (ex.tune.sweep_y >= 1) {
     const long long lines = (long long)g.nx * g.ny;
     ex.launch(dim3((unsigned)((lines + 127) / 128), 3), dim3(128), 0, SweepZStream<T>{g, f, b.flags32, tb, b.lines.z});
   } else if (!(lanes && sweep_lanes_launch(g, f, b, tb, ex, sh.nz, 2, g.ny))) {
@@ -1661,7 +1902,9 @@ void launch_sweeps(const Geo& g, const Fields<T>& f, const TagBuffers& b, const 
     const long long lines = (long long)g.nx * g.nz;
     ex.launch(dim3((unsigned)((lines + 127) / 128), 3), dim3(128), 0,
               SweepYStretched<T>{g, f, b.flags32, b.lines.y, (double)tb.off[0] * g.dx * g.dx});
-  } else if (ex.tune.sweep_y == 1) {
+  } else if (ex.tune.sweep_y == 2 && !ex.rec && sweep_y_tma_ok<T>(g, f, b, tb, ds, sh.ny, ex)) {
+    // (launched inside the check: the op carries its tensor maps)
+  } else if (ex.tune.sweep_y >= 1) {
     const long long lines = (long long)g.nx * g.nz;
     ex.launch(dim3((unsigned)((lines + 127) / 128), 3), dim3(128), 0, SweepYStream<T>{g, f, b.flags32, tb, b.lines.y});
   } else if (!(lanes && sweep_lanes_launch(g, f, b, tb, ex, sh.ny, 1, g.nz))) {
@@ -1677,6 +1920,7 @@ template <typename T>
 static void sweep_attrs() {
   op_smem_limit<SweepX<T>>(200 * 1024);
   op_smem_limit<SweepZY<T>>(200 * 1024);
+  op_smem_limit<SweepYTma<T>>(200 * 1024);
 }
 
 void init_sweep_attributes() {
@@ -1774,7 +2018,7 @@ void launch_slip(const Geo& g, const Surf& s, const Fields<T>& f, const TagBuffe
   template void launch_rhs<T>(const Geo&, const Fields<T>&, const TagBuffers&, const Stage&, double, double,    \
                               bool, bool, DevState*, Exec&);                                                    \
   template void launch_sweeps<T>(const Geo&, const Fields<T>&, const TagBuffers&, const SweepTables<T>&,        \
-                                 Exec&);                                                                        \
+                                 DevState*, Exec&);                                                             \
   template void launch_slip<T>(const Geo&, const Surf&, const Fields<T>&, const TagBuffers&, double*,           \
                                DevState*, Exec&);
 IBM_INST(double)

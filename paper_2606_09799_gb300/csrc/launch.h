@@ -134,7 +134,8 @@ template <typename T>
 void launch_rhs(const Geo& g, const Fields<T>& f, const TagBuffers& b, const Stage& sg, double dt, double re,
                 bool use_hp, bool write_h, DevState* ds, Exec& ex);
 template <typename T>
-void launch_sweeps(const Geo& g, const Fields<T>& f, const TagBuffers& b, const SweepTables<T>& tb, Exec& ex);
+void launch_sweeps(const Geo& g, const Fields<T>& f, const TagBuffers& b, const SweepTables<T>& tb, DevState* ds,
+                   Exec& ex);
 template <typename T>
 void launch_slip(const Geo& g, const Surf& s, const Fields<T>& f, const TagBuffers& b, double* partial,
                  DevState* ds, Exec& ex);

@@ -458,7 +458,7 @@ static void enqueue_step(ibm_handle h, Exec& ex) {
     const bool use_hp = sg[k].rho != 0.0;
     const bool write_h = (h->desc.scheme == IBM_AB_CN) || (k + 1 < ns);
     launch_rhs<T>(g, f, h->tb, sg[k], h->desc.dt, h->desc.re, use_hp, write_h, h->ds, ex);
-    launch_sweeps<T>(g, f, h->tb, sw, ex);
+    launch_sweeps<T>(g, f, h->tb, sw, h->ds, ex);
     launch_poisson<T>(g, f, h->tb, sp, sg[k], h->desc.dt, h->desc.re, h->desc.use_q, h->partial, h->ds, ex);
   }
   launch_slip<T>(g, s, f, h->tb, h->partial, h->ds, ex);
@@ -854,7 +854,7 @@ struct Knob {
 };
 
 static std::vector<Knob> tune_knobs() {
-  return {{&Tune::fft_plane, {2, 1}}, {&Tune::sweep_zy, {2, 1}}, {&Tune::sweep_y, {1}}, {&Tune::tri_y, {1, 2, 3}},
+  return {{&Tune::fft_plane, {2, 1}}, {&Tune::sweep_zy, {2, 1}}, {&Tune::sweep_y, {1, 2}}, {&Tune::tri_y, {1, 2, 3}},
           {&Tune::sweep_w, {64, 32, 16}},
           {&Tune::fft_lpb, {0, 8, 4, 2}},
           {&Tune::fft_cols, {16, 8, 4}}};
@@ -1530,6 +1530,10 @@ static ibm_status check_device(ibm_handle h, const DevState* have = nullptr) {
       set_err(h, "%s", "non-finite values in the solution");
       return IBM_ERR_DIVERGED;
     }
+    if (ds.err & ERR_WAIT) {
+      set_err(h, "%s", "an asynchronous tile copy did not complete within its wait limit");
+      return IBM_ERR_CUDA;
+    }
     set_err(h, "%s", "device error");
     return IBM_ERR_CUDA;
   }
@@ -1653,7 +1657,7 @@ static bool tune_valid(const ibm_tune* t) {
   if (t->fft_cols < 0 || t->fft_cols > 16 || (t->fft_cols & (t->fft_cols - 1))) return false;
   if (t->sweep_zy < 0 || t->sweep_zy > 2) return false;
   if (t->fft_plane < 0 || t->fft_plane > 2) return false;
-  if (t->sweep_y < 0 || t->sweep_y > 1) return false;
+  if (t->sweep_y < 0 || t->sweep_y > 2) return false;
   return true;
 }
 

@@ -180,11 +180,43 @@ def test_batch_autotune_leaves_state():
     b.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_bulk_copy_y_tiles_equal_solo(precision):
+    """The y sweep from tiles staged by bulk asynchronous copies, in a batch
+    of uneven instances (blocks beyond an instance's own grid return before
+    any copy) and alone: the same fields, bit for bit."""
+    wls = small_batch()
+    sims = [make(w, precision) for w in wls]
+    b = ibm.Batch(sims)
+    b.set_tune(tri_y=1, sweep_y=2, fft_plane=2)
+    for s in range(3):
+        for w, g in zip(wls, sims):
+            xyz, vel = w.surface(s)
+            g.set_surface(xyz, vel, w.tri)
+        b.step()
+    b.sync()
+    for w, g in zip(wls, sims):
+        ref = make(w, precision)
+        ibm.ibm_set_tune(ref.h, tri_y=1, sweep_y=2, fft_plane=2)
+        for s in range(3):
+            xyz, vel = w.surface(s)
+            ref.set_surface(xyz, vel, w.tri)
+            ref.step()
+        for a, r in zip(g.fields(), ref.fields()):
+            if precision == "fp64":
+                np.testing.assert_array_equal(a, r)
+            else:
+                np.testing.assert_allclose(a, r, rtol=0, atol=1e-5)
+    b.close()
+
+
 def test_tune_values_are_validated():
     g = ibm.Simulation(32, 32, 32)
     with pytest.raises(ibm.IbmError):
         ibm.ibm_set_tune(g.h, sweep_w=24)
     with pytest.raises(ibm.IbmError):
         ibm.ibm_set_tune(g.h, fft_cols=3)
+    with pytest.raises(ibm.IbmError):
+        ibm.ibm_set_tune(g.h, sweep_y=3)
     ibm.ibm_set_tune(g.h, tri_y=2, sweep_w=16, fft_lpb=4, fft_cols=4)
     assert ibm.ibm_get_tune(g.h)["sweep_w"] == 16

@@ -287,11 +287,12 @@ def test_candidate_capacity_grows_for_large_triangles():
 @pytest.mark.parametrize("tune", [dict(tri_y=1, fft_plane=2), dict(tri_y=2, sweep_w=16, fft_plane=1),
                                   dict(tri_y=3, fft_lpb=2, fft_cols=2, fft_plane=1),
                                   dict(tri_y=3, sweep_zy=1, sweep_w=64, fft_lpb=8, fft_cols=16, fft_plane=2),
-                                  dict(tri_y=1, sweep_zy=2, sweep_y=1, fft_plane=2)])
+                                  dict(tri_y=1, sweep_zy=2, sweep_y=1, fft_plane=2),
+                                  dict(tri_y=1, sweep_y=2, fft_plane=2)])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-5)])
 def test_every_launch_shape_matches_oracle(tune, precision, tol):
     """Every choice the autotuner can make (Thomas variant, sweep form and
-    width, streamed y sweep, FFT tiling) computes the same step: against the oracle on a
+    width, streamed y sweep, bulk-copy y tiles, FFT tiling) computes the same step: against the oracle on a
     ragged grid with a moving sphere, 4 steps."""
     wl = inputs.oscillating_sphere(n=48, steps=4, subdiv=2)
     o = OracleSim(48, 37, 96, 1.0, 0.9, 1.6, re=150.0, dt=2e-3)
@@ -308,6 +309,28 @@ def test_every_launch_shape_matches_oracle(tune, precision, tol):
     assert err <= tol, err
     for c, own in enumerate(g.tags()):
         np.testing.assert_array_equal(own, o.owners[c])
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-5)])
+def test_bulk_copy_y_tiles_with_128_rows_match_oracle(precision, tol):
+    """The bulk-copy y tiles where they need more than the default 48 KB of
+    shared memory (128 rows; 3 tiles of 32 lines with the low parts in the
+    mixed path), with a moving sphere and a random initial field."""
+    wl = inputs.oscillating_sphere(n=32, steps=3, subdiv=2)
+    init = inputs.random_fields(32, 128, 32, seed=17, amp=0.1)
+    o = OracleSim(32, 128, 32, re=150.0, dt=1e-3)
+    g = ibm.Simulation(32, 128, 32, re=150.0, dt=1e-3, precision=precision)
+    ibm.ibm_set_tune(g.h, tri_y=1, sweep_y=2, fft_plane=2)
+    for sim in (o, g):
+        sim.set_fields(*init)
+    for s in range(3):
+        xyz, vel = wl.surface(s)
+        for sim in (o, g):
+            sim.set_surface(xyz, vel, wl.tri)
+            sim.step()
+    gu, gv, gw, _ = g.fields()
+    err = max(np.abs(o.u - gu).max(), np.abs(o.v - gv).max(), np.abs(o.w - gw).max())
+    assert err <= tol, err
 
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-5)])
