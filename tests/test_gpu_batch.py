@@ -182,9 +182,10 @@ def test_batch_autotune_leaves_state():
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_batch_bulk_copy_y_tiles_equal_solo(precision):
-    """The y sweep from tiles staged by bulk asynchronous copies, in a batch
-    of uneven instances (blocks beyond an instance's own grid return before
-    any copy) and alone: the same fields, bit for bit."""
+    """Launch-shape choice sweep_y = 2 in a batch of uneven instances (which
+    keeps the streamed y sweep: its ops live in global memory, not in kernel
+    parameters where tensor maps must be) and alone (the y sweep from
+    TMA-staged tiles): the same fields, bit for bit in FP64."""
     wls = small_batch()
     sims = [make(w, precision) for w in wls]
     b = ibm.Batch(sims)
