@@ -1032,6 +1032,161 @@ struct TriYNU {
   __device__ __forceinline__ void operator()(const Blk& bk) const { tri_y_nu<T>(bk, g, f, cp, ivh, al); }
 };
 
+// The same systems warp-cooperatively (non-uniform wall-normal spacing): L
+// lanes per (kx, kz) system, TRI_SEG rows per lane.  Forward p_j = al_j
+// p_{j-1} + r_j / pivot_j and backward x_j = p_j - c'_j x_{j+1} are affine
+// maps: each lane composes its rows' maps (the products formed here from the
+// rows' multipliers), a shuffle scan over the lanes composes the prefixes,
+// and each lane then replays its rows from its incoming value.  The (0,0)
+// system takes the volume-weighted zero-mean gauge, as the sequential form.
+template <typename T, int L>
+__device__ __forceinline__ void tri_y_warp_nu(const Blk& bk, const Geo& g, const Fields<T>& f,
+                                              const double* __restrict__ cp, const double* __restrict__ ivh,
+                                              const double* __restrict__ al) {
+  using C = typename Cplx<T>::type;
+  constexpr int Rr = TRI_SEG;
+  constexpr int G = 32 / L;
+  const int lane = threadIdx.x & 31;
+  const int sl = lane % L;
+  const int nkx = g.nkx, ny = g.ny;
+  const int groups_x = (nkx + G - 1) / G;
+  const long long wid = ((long long)bk.x * blockDim.x + threadIdx.x) >> 5;
+  if (wid >= (long long)groups_x * g.nz) return;     // whole warps only
+  const int kz = (int)(wid / groups_x);
+  const int kx = (int)(wid % groups_x) * G + lane / L;
+  const bool live = kx < nkx;
+  const long long base = (long long)kz * ny * nkx + (live ? kx : 0);
+  const long long stride = nkx;
+  C* spec = reinterpret_cast<C*>(f.spec);
+  const bool singular = live && kx == 0 && kz == 0;
+  const bool gauge = kz == 0 && (int)(wid % groups_x) == 0;   // warp of the (0,0) system
+  const int j0 = sl * Rr;
+  const unsigned FULL = 0xFFFFFFFFu;
+  double br[Rr], bi[Rr], am[Rr], cq[Rr];
+#pragma unroll
+  for (int u = 0; u < Rr; ++u) {
+    const int j = j0 + u;
+    br[u] = bi[u] = cq[u] = 0.0;
+    am[u] = 1.0;
+    if (live && j < ny) {
+      const long long id = base + (long long)j * stride;
+      const C z = spec[id];
+      const double iv = __ldg(ivh + id);
+      am[u] = __ldg(al + id);
+      cq[u] = __ldg(cp + id);
+      br[u] = (double)z.x * iv;
+      bi[u] = (double)z.y * iv;
+    }
+  }
+  // ---- forward: the lane's composite map p -> A p + B
+  double A = 1.0, Br = 0.0, Bi = 0.0;
+#pragma unroll
+  for (int u = 0; u < Rr; ++u) {
+    Br = fma(am[u], Br, br[u]);
+    Bi = fma(am[u], Bi, bi[u]);
+    A = A * am[u];
+  }
+  for (int o = 1; o < L; o <<= 1) {
+    const double pa = __shfl_up_sync(FULL, A, o, L), pr = __shfl_up_sync(FULL, Br, o, L),
+                 pi = __shfl_up_sync(FULL, Bi, o, L);
+    if (sl >= o) {
+      Br = fma(A, pr, Br);
+      Bi = fma(A, pi, Bi);
+      A = A * pa;
+    }
+  }
+  double pr = __shfl_up_sync(FULL, Br, 1, L), pi = __shfl_up_sync(FULL, Bi, 1, L);
+  if (sl == 0) { pr = 0.0; pi = 0.0; }
+#pragma unroll
+  for (int u = 0; u < Rr; ++u) {
+    pr = fma(am[u], pr, br[u]);
+    pi = fma(am[u], pi, bi[u]);
+    br[u] = pr;
+    bi[u] = pi;
+  }
+  // ---- backward: the lane's composite map from the row above its top row
+  A = 1.0;
+  Br = 0.0;
+  Bi = 0.0;
+#pragma unroll
+  for (int u = Rr - 1; u >= 0; --u) {
+    const int j = j0 + u;
+    if (!live || j >= ny) continue;
+    if (j == ny - 1) {   // the top row: x = p
+      A = 0.0;
+      Br = br[u];
+      Bi = bi[u];
+    } else {
+      Br = fma(-cq[u], Br, br[u]);
+      Bi = fma(-cq[u], Bi, bi[u]);
+      A = A * -cq[u];
+    }
+  }
+  for (int o = 1; o < L; o <<= 1) {
+    const double na = __shfl_down_sync(FULL, A, o, L), nr = __shfl_down_sync(FULL, Br, o, L),
+                 ni = __shfl_down_sync(FULL, Bi, o, L);
+    if (sl + o < L) {
+      Br = fma(A, nr, Br);
+      Bi = fma(A, ni, Bi);
+      A = A * na;
+    }
+  }
+  double xr = __shfl_down_sync(FULL, Br, 1, L), xi = __shfl_down_sync(FULL, Bi, 1, L);
+  if (sl == L - 1) { xr = 0.0; xi = 0.0; }
+  double sr = 0.0, si = 0.0;
+#pragma unroll
+  for (int u = Rr - 1; u >= 0; --u) {
+    const int j = j0 + u;
+    if (!live || j >= ny) continue;
+    if (j == ny - 1) {
+      xr = br[u];
+      xi = bi[u];
+    } else {
+      xr = fma(-cq[u], xr, br[u]);
+      xi = fma(-cq[u], xi, bi[u]);
+    }
+    br[u] = xr;
+    bi[u] = xi;
+    if (gauge) {
+      sr = fma(xr, g.yt.hc[j], sr);
+      si = fma(xi, g.yt.hc[j], si);
+    }
+  }
+  if (gauge) {
+    // volume-weighted zero mean of the (0,0) system (first group of kz = 0)
+    for (int o = 1; o < L; o <<= 1) {
+      sr += __shfl_xor_sync(FULL, sr, o, L);
+      si += __shfl_xor_sync(FULL, si, o, L);
+    }
+    if (singular) {
+      const double mr = sr / g.ly, mi = si / g.ly;
+#pragma unroll
+      for (int u = 0; u < Rr; ++u) {
+        br[u] -= mr;
+        bi[u] -= mi;
+      }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < Rr; ++u) {
+    const int j = j0 + u;
+    C o;
+    o.x = (T)br[u];
+    o.y = (T)bi[u];
+    if (live && j < ny) spec[base + (long long)j * stride] = o;
+  }
+}
+template <typename T, int L>
+struct TriYWarpNU {
+  static constexpr int kThreads = 128;
+  Geo g;
+  Fields<T> f;
+  const double* cp;
+  const double* ivh;
+  const double* al;
+  __device__ __forceinline__ void operator()(const Blk& bk) const { tri_y_warp_nu<T, L>(bk, g, f, cp, ivh, al); }
+};
+
 template <typename T>
 struct TriY {
   static constexpr int kThreads = 128;
@@ -1581,7 +1736,21 @@ void launch_poisson(const Geo& g, const Fields<T>& f, const TagBuffers& b, const
   if (tu.tri_y == 3 && tsm > 0) tri = 3;
   auto tri_solve = [&]() {
     if (tb.pal) {   // non-uniform wall-normal spacing
-      ex.launch(dim3((unsigned)((2 * tlines + 127) / 128)), dim3(128), 0, TriYNU<T>{g, f, tb.cp, tb.inv, tb.pal});
+      if (tu.tri_y == 2 || sh.ny > 32 * TRI_SEG) {
+        ex.launch(dim3((unsigned)((2 * tlines + 127) / 128)), dim3(128), 0, TriYNU<T>{g, f, tb.cp, tb.inv, tb.pal});
+      } else if (sh.ny <= 8 * TRI_SEG) {
+        const long long warps = (long long)((g.nkx + 3) / 4) * g.nz;
+        ex.launch(dim3((unsigned)((warps * 32 + 127) / 128)), dim3(128), 0,
+                  TriYWarpNU<T, 8>{g, f, tb.cp, tb.inv, tb.pal});
+      } else if (sh.ny <= 16 * TRI_SEG) {
+        const long long warps = (long long)((g.nkx + 1) / 2) * g.nz;
+        ex.launch(dim3((unsigned)((warps * 32 + 127) / 128)), dim3(128), 0,
+                  TriYWarpNU<T, 16>{g, f, tb.cp, tb.inv, tb.pal});
+      } else {
+        const long long warps = (long long)g.nkx * g.nz;
+        ex.launch(dim3((unsigned)((warps * 32 + 127) / 128)), dim3(128), 0,
+                  TriYWarpNU<T, 32>{g, f, tb.cp, tb.inv, tb.pal});
+      }
       return;
     }
     if (tri == 3) {

@@ -47,6 +47,24 @@ def test_stretched_grid_matches_oracle(scheme, ybc):
     assert np.abs(o.p - gp).max() <= 1e-10 * max(1.0, np.abs(o.p).max())
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-5)])
+def test_stretched_sequential_thomas_matches_oracle(precision, tol):
+    """Launch shape tri_y = 2: the wall-normal Thomas one thread per real or
+    imaginary part instead of the warp-cooperative scan."""
+    yf = inputs.stretched_faces(NY)
+    u, v, w, p = inputs.random_fields(NX, NY, NZ, seed=23, amp=0.3)
+    o = OracleSim(NX, NY, NZ, re=120.0, dt=2e-3, yfaces=yf)
+    g = ibm.Simulation(NX, NY, NZ, re=120.0, dt=2e-3, precision=precision, y_faces=yf)
+    ibm.ibm_set_tune(g.h, tri_y=2)
+    for sim in (o, g):
+        sim.set_fields(u, v, w, p)
+        sim.set_body_force(2.0, 0.0, 0.3)
+        sim.step(4)
+    gu, gv, gw, _ = g.fields()
+    err = max(np.abs(o.u - gu).max(), np.abs(o.v - gv).max(), np.abs(o.w - gw).max())
+    assert err <= tol * max(1.0, np.abs(o.u).max()), err
+
+
 def test_uniform_faces_give_the_uniform_path():
     u, v, w, p = inputs.random_fields(NX, NY, NZ, seed=22, amp=0.3)
     a = ibm.Simulation(NX, NY, NZ, re=90.0, dt=2e-3, precision="fp64")
