@@ -477,10 +477,35 @@ __device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, 
 // the correction solve's rhs from the projected (hi, lo) state in pair
 // arithmetic (the state u' = uhat - G phi is formed at the cell's faces
 // here); 0 on boundary cells when q is on (q_B = D uhat).
+// Wall-normal coefficients of one row j of cells, formed once per row by the
+// callers: the projection's gradient coefficients of the faces below and
+// above (cy0, cy1), 1/h of the row as a (hi, lo) pair for the pair
+// divergence, and 1/h in the bulk type.  On a uniform grid they are the
+// grid's own constants.
+template <typename T>
+struct RowY {
+  T cy0, cy1, ih;
+  float ihh, ihl;
+};
+template <typename T>
+__device__ __forceinline__ RowY<T> row_y(const Geo& g, const Fields<T>& f, const ProjCoef<T>& cf, int j) {
+  RowY<T> r{cf.cy, cf.cy, (T)g.idy, (float)f.idh[1][0], (float)f.idh[1][1]};
+  if (g.yt.ihc) {
+    r.cy0 = mul_rn(cf.adt, (T)g.yt.ihf[j]);
+    r.cy1 = mul_rn(cf.adt, (T)g.yt.ihf[j + 1]);
+    const double ih = g.yt.ihc[j];
+    r.ih = (T)ih;
+    r.ihh = (float)ih;
+    r.ihl = (float)(ih - (double)r.ihh);
+  }
+  return r;
+}
+
 template <typename T>
 __device__ __forceinline__ T poisson_rhs(const Geo& g, const Fields<T>& f, const unsigned* __restrict__ flags32,
                                          const DevState* ds, int s, int use_q, double scale, int mode,
-                                         const ProjCoef<T>& cf, T qf, T qa, T qb, int i, int j, int k) {
+                                         const ProjCoef<T>& cf, const RowY<T>& ry, T qf, T qa, T qb, int i, int j,
+                                         int k) {
   const int n = g.nx, ny = g.ny;
   const long long pu = (long long)ny * n, pv = (long long)(ny + 1) * n;
   const T sc = (T)scale, idx = (T)g.idx, idy = (T)g.idy, idz = (T)g.idz;
@@ -510,25 +535,15 @@ __device__ __forceinline__ T poisson_rhs(const Geo& g, const Fields<T>& f, const
         proj_face(uh1, ul1, (float)mul_rn(cf.cx, ph[r0 + ip] - (T)p0));
         float vh0 = (float)f.v[v0], vl0 = (float)f.lo[1][v0];
         float vh1 = (float)f.v[v0 + n], vl1 = (float)f.lo[1][v0 + n];
-        // non-uniform wall-normal spacing: each face's own gradient
-        // coefficient (as the projection forms it) and 1/h_c of the cell as
-        // a (hi, lo) pair
-        const T cy0 = g.yt.ihc ? mul_rn(cf.adt, (T)g.yt.ihf[j]) : cf.cy;
-        const T cy1 = g.yt.ihc ? mul_rn(cf.adt, (T)g.yt.ihf[j + 1]) : cf.cy;
-        if (j > 0) proj_face(vh0, vl0, (float)mul_rn(cy0, (T)p0 - ph[cell - n]));
-        if (j + 1 < ny) proj_face(vh1, vl1, (float)mul_rn(cy1, ph[cell + n] - (T)p0));
+        // each face's own gradient coefficient, as the projection forms it
+        if (j > 0) proj_face(vh0, vl0, (float)mul_rn(ry.cy0, (T)p0 - ph[cell - n]));
+        if (j + 1 < ny) proj_face(vh1, vl1, (float)mul_rn(ry.cy1, ph[cell + n] - (T)p0));
         float wh0 = (float)f.w[cell], wl0 = (float)f.lo[2][cell];
         float wh1 = (float)f.w[wk], wl1 = (float)f.lo[2][wk];
         proj_face(wh0, wl0, (float)mul_rn(cf.cz, (T)p0 - ph[rkm + i]));
         proj_face(wh1, wl1, (float)mul_rn(cf.cz, ph[rkp + i] - (T)p0));
         pair_diff_v(uh1, ul1, uh0, ul0, (float)f.idh[0][0], (float)f.idh[0][1], bx, sx);
-        float ihy = (float)f.idh[1][0], ily = (float)f.idh[1][1];
-        if (g.yt.ihc) {
-          const double ih = g.yt.ihc[j];
-          ihy = (float)ih;
-          ily = (float)(ih - (double)ihy);
-        }
-        pair_diff_v(vh1, vl1, vh0, vl0, ihy, ily, by, sy);
+        pair_diff_v(vh1, vl1, vh0, vl0, ry.ihh, ry.ihl, by, sy);
         pair_diff_v(wh1, wl1, wh0, wl0, (float)f.idh[2][0], (float)f.idh[2][1], bz, sz);
       }
       two_sum(bx, by, a1, e1);
@@ -545,7 +560,7 @@ __device__ __forceinline__ T poisson_rhs(const Geo& g, const Fields<T>& f, const
     // explicit rounding (no contraction): the single-simulation and the
     // batched kernels compile this body separately and must round alike
     const T du = mul_rn(f.u[r0 + ip] - f.u[cell], idx);
-    const T dv = mul_rn(f.v[v0 + n] - f.v[v0], g.yt.ihc ? (T)g.yt.ihc[j] : idy);
+    const T dv = mul_rn(f.v[v0 + n] - f.v[v0], ry.ih);
     const T dw = mul_rn(f.w[(long long)kp * pu + (long long)j * n + i] - f.w[cell], idz);
     T q = qf;
     if (use_q == 2) {   // App. B shape, kept per cell for the correction solve
@@ -585,6 +600,7 @@ __device__ __forceinline__ void fft_x_fwd(const Blk& bk, const Geo& g, const Fie
       jj[hh] = row % ny;
       kk[hh] = row / ny;
     }
+    const RowY<T> ry[2] = {row_y<T>(g, f, cf, ok[0] ? jj[0] : 0), row_y<T>(g, f, cf, ok[1] ? jj[1] : 0)};
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       C z;
       z.x = (T)0;
@@ -592,7 +608,8 @@ __device__ __forceinline__ void fft_x_fwd(const Blk& bk, const Geo& g, const Fie
 #pragma unroll
       for (int hh = 0; hh < 2; ++hh) {
         if (!ok[hh]) continue;
-        const T r = poisson_rhs<T>(g, f, flags32, ds, s, use_q, scale, mode, cf, qf, qa, qb, i, jj[hh], kk[hh]);
+        const T r = poisson_rhs<T>(g, f, flags32, ds, s, use_q, scale, mode, cf, ry[hh], qf, qa, qb, i, jj[hh],
+                                   kk[hh]);
         if (hh == 0) z.x = r;
         else z.y = r;
       }
@@ -712,6 +729,7 @@ __device__ __forceinline__ void fft_plane_fwd(const Blk& bk, const Geo& g, const
   const T qf = use_q ? (T)ds->qf[s] : (T)0;
   const T qa = use_q == 2 ? (T)ds->qa[s] : (T)0, qb = use_q == 2 ? (T)ds->qb[s] : (T)0;
   const int nlines = nz / 2;
+  const RowY<T> ry = row_y<T>(g, f, cf, j);
   // x: lc complex lines (row pairs) at a time into S
   for (int l0 = 0; l0 < nlines; l0 += lc) {
     const int nl = min(lc, nlines - l0);
@@ -721,8 +739,8 @@ __device__ __forceinline__ void fft_plane_fwd(const Blk& bk, const Geo& g, const
       const int l = t / nx, i = t - l * nx;
       const int k0 = 2 * (l0 + l);
       C z;
-      z.x = poisson_rhs<T>(g, f, flags32, ds, s, use_q, scale, mode, cf, qf, qa, qb, i, j, k0);
-      z.y = poisson_rhs<T>(g, f, flags32, ds, s, use_q, scale, mode, cf, qf, qa, qb, i, j, k0 + 1);
+      z.x = poisson_rhs<T>(g, f, flags32, ds, s, use_q, scale, mode, cf, ry, qf, qa, qb, i, j, k0);
+      z.y = poisson_rhs<T>(g, f, flags32, ds, s, use_q, scale, mode, cf, ry, qf, qa, qb, i, j, k0 + 1);
       bufa[t] = z;
     }
     const int res = fft_lines<T, false>(bufa, bufb, nl, px, reinterpret_cast<const C*>(twx));
