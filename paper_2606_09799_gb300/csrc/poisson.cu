@@ -477,11 +477,12 @@ __device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, 
 // the correction solve's rhs from the projected (hi, lo) state in pair
 // arithmetic (the state u' = uhat - G phi is formed at the cell's faces
 // here); 0 on boundary cells when q is on (q_B = D uhat).
-// Wall-normal coefficients of one row j of cells, formed once per row by the
-// callers: the projection's gradient coefficients of the faces below and
-// above (cy0, cy1), 1/h of the row as a (hi, lo) pair for the pair
-// divergence, and 1/h in the bulk type.  On a uniform grid they are the
-// grid's own constants.
+// Wall-normal coefficients of one row j of cells: the projection's gradient
+// coefficients of the faces below and above (cy0, cy1), 1/h of the row as a
+// (hi, lo) pair for the pair divergence, and 1/h in the bulk type.  On a
+// uniform grid they are the grid's own constants.  The per-plane transform
+// forms them once per plane; the per-line transform per cell (measured
+// faster there than holding both rows' values across the line).
 template <typename T>
 struct RowY {
   T cy0, cy1, ih;
@@ -600,7 +601,6 @@ __device__ __forceinline__ void fft_x_fwd(const Blk& bk, const Geo& g, const Fie
       jj[hh] = row % ny;
       kk[hh] = row / ny;
     }
-    const RowY<T> ry[2] = {row_y<T>(g, f, cf, ok[0] ? jj[0] : 0), row_y<T>(g, f, cf, ok[1] ? jj[1] : 0)};
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       C z;
       z.x = (T)0;
@@ -608,8 +608,8 @@ __device__ __forceinline__ void fft_x_fwd(const Blk& bk, const Geo& g, const Fie
 #pragma unroll
       for (int hh = 0; hh < 2; ++hh) {
         if (!ok[hh]) continue;
-        const T r = poisson_rhs<T>(g, f, flags32, ds, s, use_q, scale, mode, cf, ry[hh], qf, qa, qb, i, jj[hh],
-                                   kk[hh]);
+        const T r = poisson_rhs<T>(g, f, flags32, ds, s, use_q, scale, mode, cf, row_y<T>(g, f, cf, jj[hh]), qf, qa,
+                                   qb, i, jj[hh], kk[hh]);
         if (hh == 0) z.x = r;
         else z.y = r;
       }
