@@ -65,6 +65,34 @@ def test_stretched_sequential_thomas_matches_oracle(precision, tol):
     assert err <= tol * max(1.0, np.abs(o.u).max()), err
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-5)])
+def test_tall_stretched_grid_with_a_wall_matches_oracle(precision, tol):
+    """1,100 rows: above the row count for which the y sweep's segment tables
+    are built (its lines that cross the wall then divide on the fly) and above
+    the warp-cooperative Thomas (the sequential form runs), with an immersed
+    wall across the box so every line holds forcing rows."""
+    nx, ny, nz = 8, 1100, 8
+    yf = inputs.stretched_faces(ny)
+    wl = inputs.immersed_wall_channel(nx=nx, ny=ny, nz=nz, y_wall=0.5013, steps=3)
+    init = inputs.random_fields(nx, ny, nz, seed=29, amp=0.1)
+    o = OracleSim(nx, ny, nz, re=wl.re, dt=wl.dt, yfaces=yf)
+    g = ibm.Simulation(nx, ny, nz, re=wl.re, dt=wl.dt, precision=precision, y_faces=yf)
+    for sim in (o, g):
+        sim.set_fields(*init)
+    for s in range(3):
+        xyz, vel = wl.surface(s)
+        for sim in (o, g):
+            sim.set_surface(xyz, vel, wl.tri)
+            sim.set_body_force(*wl.body_force_at(s * wl.dt))
+            sim.step()
+    gu, gv, gw, _ = g.fields()
+    err = max(np.abs(o.u - gu).max(), np.abs(o.v - gv).max(), np.abs(o.w - gw).max())
+    assert err <= tol * max(1.0, np.abs(o.u).max()), err
+    for c, t in enumerate(g.tags()):
+        np.testing.assert_array_equal(t, o.owners[c], err_msg=f"component {c}")
+    assert all(n > 0 for n in g.diag()["nforce"])
+
+
 def test_uniform_faces_give_the_uniform_path():
     u, v, w, p = inputs.random_fields(NX, NY, NZ, seed=22, amp=0.3)
     a = ibm.Simulation(NX, NY, NZ, re=90.0, dt=2e-3, precision="fp64")
