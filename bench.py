@@ -490,6 +490,20 @@ def stretched_run(args, dev, stream, flush, world, wall, precision):
     slip = sim.diag()["slip_l1"]
     prof = ibm.ibm_profile_stages(sim.h, 2)
     sim.close()
+    # mixed path: every HBM-bound kernel group against the measured copy rate,
+    # with the algorithmic bytes per cell of the uniform grid's groups (the
+    # same fields; the wall-normal tables add under 1 MB)
+    roof = {}
+    if precision == "mixed":
+        peak = measured_peaks().get("hbm_gbs", 6800.0)
+        for name, (tot_ms, ngroups) in prof.items():
+            b = algorithmic_bytes_per_cell(name, 4)
+            if ngroups == 0 or tot_ms <= 0 or b <= 0:
+                continue
+            avg_ms = tot_ms / (ngroups * 2)
+            ach = b * n ** 3 / (avg_ms / 1e3) / 1e9
+            roof[name] = {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                          "avg_ms": round(avg_ms, 4), "frac": round(ach / peak, 4)}
     what = ("no surface" if wall is None else
             "an immersed rigid wall across the box at y = 0.1213 (plate of 2,048 triangles)")
     return {"workload": "stretched128: 128^3 channel, tanh-stretched wall-normal cells (beta 1.8), " + what + ", "
@@ -497,7 +511,8 @@ def stretched_run(args, dev, stream, flush, world, wall, precision):
                         + ("FP64" if precision == "fp64" else "mixed (FP32 bulk, (hi, lo) velocity, correction solve)"),
             "cells": n ** 3, "steps": K, "value": whole_job_gcups(n ** 3, K, world, ms), "unit": UNIT,
             "ms_per_step": ms / K, "slip_l1": slip if wall is not None else None,
-            "stages_ms_per_step": {k: v[0] / 2 for k, v in prof.items() if v[1] > 0}}
+            "stages_ms_per_step": {k: v[0] / 2 for k, v in prof.items() if v[1] > 0},
+            **({"stage_roofline": roof} if roof else {})}
 
 
 def large_leg(args, dev, stream, flush):

@@ -31,7 +31,8 @@ constexpr uint8_t FLAG_U = 1, FLAG_V = 2, FLAG_W = 4, FLAG_B = 8;
 // then v: the same over ny - 1 rows).  ysw2: for lines with forcing nodes,
 // 1/pivot and c' of a segment that starts at row s, at [s][m] (tangential
 // components: two ny x ny arrays; then v: two (ny-1) x (ny-1)); null when ny
-// is above 1024.  All null (0) on a uniform grid.
+// is above 1024.  yswf, ysw2f: their FP32 copies for the mixed path.  All
+// null (0) on a uniform grid.
 struct YTab {
   const double* ihc;
   const double* ihf;
@@ -41,6 +42,8 @@ struct YTab {
   const double* yv;
   const double* ysw;
   const double* ysw2;
+  const float* yswf;    // FP32 copies of ysw and ysw2 (mixed path), else null
+  const float* ysw2f;
   double hmax;
 };
 

@@ -1447,6 +1447,68 @@ struct SweepZStream {
 // side, from the spacing table, and a forcing node's row is the identity;
 // the line is factorised as it is swept (c' to the scratch array) and du is
 // added to the state on the way back (as a (hi, lo) pair in the mixed path).
+// The same line in FP32 from the FP32 copies of the row tables (mixed path):
+// a line without forcing rows in one wall segment, a line with forcing rows
+// restarting at [start row][row] after each identity row (c' to the scratch
+// array).
+__device__ __forceinline__ void sweep_y_stretched_f32(const Geo& g, const Fields<float>& f,
+                                                      const unsigned* __restrict__ flags32, bool any, int c, int i,
+                                                      int k, int n, int jj0, int sn, float* __restrict__ Rl,
+                                                      float* __restrict__ Sl, float* __restrict__ Ul,
+                                                      float* __restrict__ Ll) {
+  const float* __restrict__ ta = g.yt.yswf + (c == 1 ? 3ll * g.ny : 0);
+  float p = 0.0f;
+  if (!any) {
+    const float* __restrict__ tv = ta + n;
+    for (int m = 0; m < n; ++m) {
+      p = fmaf(-__ldg(ta + m), p, Rl[m * sn]) * __ldg(tv + m);
+      Rl[m * sn] = p;
+    }
+    const float* __restrict__ tc = tv + n;
+    float x = 0.0f;
+    for (int m = n - 1; m >= 0; --m) {
+      x = fmaf(-__ldg(tc + m), x, Rl[m * sn]);
+      if (Ll) {
+        float hi = Ul[m * sn], lo = Ll[m * sn];
+        ff_add(hi, lo, x);
+        Ul[m * sn] = hi;
+        Ll[m * sn] = lo;
+      } else {
+        Ul[m * sn] += x;
+      }
+    }
+    return;
+  }
+  const float* __restrict__ iv2 = g.yt.ysw2f + (c == 1 ? 2ll * g.ny * g.ny : 0);
+  const float* __restrict__ cp2 = iv2 + (long long)n * n;
+  long long s0 = 0;
+  for (int m = 0; m < n; ++m) {
+    float cq = 0.0f;
+    if (is_forcing(flags32, cidx(g, i, jj0 + m, k), c)) {
+      p = Rl[m * sn];
+      s0 = m + 1;
+    } else {
+      const long long id = s0 * n + m;
+      p = fmaf(-__ldg(ta + m), p, Rl[m * sn]) * __ldg(iv2 + id);
+      cq = __ldg(cp2 + id);
+    }
+    Rl[m * sn] = p;
+    Sl[m * sn] = cq;
+  }
+  float x = 0.0f;
+  for (int m = n - 1; m >= 0; --m) {
+    x = fmaf(-Sl[m * sn], x, Rl[m * sn]);
+    if (Ll) {
+      float hi = Ul[m * sn], lo = Ll[m * sn];
+      ff_add(hi, lo, x);
+      Ul[m * sn] = hi;
+      Ll[m * sn] = lo;
+    } else {
+      Ul[m * sn] += x;
+    }
+  }
+}
+
 // A line without forcing rows (most lines) takes its rows' a, 1/pivot and
 // c' from the table built with the grid, with no division and no scratch.
 template <typename T>
@@ -1465,6 +1527,13 @@ __device__ __forceinline__ void sweep_y_stretched(const Blk& bk, const Geo& g, c
   T* __restrict__ Sl = f.scr + comp_off(g, c) + base;
   T* __restrict__ Ul = comp_ptr(f, c) + base;
   T* __restrict__ Ll = f.lo[c] ? f.lo[c] + base : nullptr;
+  if constexpr (sizeof(T) == 4) {
+    // mixed path: FP32 rows and recurrences, as the uniform grid's sweeps
+    if (g.yt.yswf && (lfirst[line_y(g, c, i, k)] >= g.ny || g.yt.ysw2f)) {
+      sweep_y_stretched_f32(g, f, flags32, lfirst[line_y(g, c, i, k)] < g.ny, c, i, k, n, jj0, sn, Rl, Sl, Ul, Ll);
+      return;
+    }
+  }
   if (lfirst[line_y(g, c, i, k)] >= g.ny) {
     const double* __restrict__ ta = g.yt.ysw + (c == 1 ? 3ll * g.ny : 0);
     const double* __restrict__ tv = ta + n;

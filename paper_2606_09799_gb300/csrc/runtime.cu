@@ -1281,9 +1281,18 @@ ibm_status ibm_create_grid_stretched(const ibm_grid_desc* desc, const double* y_
   for (int j = 0; j <= ny; ++j) { smin = std::min(smin, hf[j]); smax = std::max(smax, hf[j]); }
   h->ytab = (double*)upload_vec<double>(h, t);
   double* ysw2 = t2.empty() ? nullptr : (double*)upload_vec<double>(h, t2);
+  // FP32 copies of the sweep tables for the mixed paths
+  float* yswf = nullptr;
+  float* ysw2f = nullptr;
+  bool f32_ok = true;
+  if (desc->precision != IBM_FP64) {
+    yswf = (float*)upload_vec<float>(h, std::vector<double>(t.begin() + (6ll * ny + 7), t.end()));
+    if (!t2.empty()) ysw2f = (float*)upload_vec<float>(h, t2);
+    f32_ok = yswf && (t2.empty() || ysw2f);
+  }
   const size_t nspec = (size_t)h->g.nz * h->g.ny * h->g.nkx;
   h->pal = (double*)dalloc(h, nspec * 8);
-  if (!h->ytab || !h->pal || (!t2.empty() && !ysw2)) {
+  if (!h->ytab || !h->pal || (!t2.empty() && !ysw2) || !f32_ok) {
     ibm_destroy(h);
     return IBM_ERR_OOM;
   }
@@ -1295,6 +1304,8 @@ ibm_status ibm_create_grid_stretched(const ibm_grid_desc* desc, const double* y_
   h->g.yt.yv = h->ytab + 5 * ny + 4;
   h->g.yt.ysw = h->ytab + 6 * ny + 7;
   h->g.yt.ysw2 = ysw2;
+  h->g.yt.yswf = yswf;
+  h->g.yt.ysw2f = ysw2f;
   h->g.yt.hmax = smax;
   h->ysp_min = smin;
   launch_build_poisson_tables_nu(h->g, h->lamx, h->lamz, h->pcp, h->pinv, h->pal, h->user);
