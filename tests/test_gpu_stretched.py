@@ -188,6 +188,29 @@ def test_stretched_moving_sphere_matches_oracle(use_q, nsteps):
     assert abs(d["sum_q_dv"]) < 1e-12
 
 
+@pytest.mark.parametrize("scheme,ybc", [("ab", 0), ("rk2", 1)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-5)])
+def test_stretched_moving_sphere_schemes_and_walls(scheme, ybc, precision, tol):
+    """AB+CN, and free-slip walls, with a moving body on the stretched grid."""
+    wl = inputs.oscillating_sphere(n=32, steps=6, subdiv=2)
+    yf = inputs.stretched_faces(40)
+    init = inputs.random_fields(32, 40, 32, seed=37, amp=0.05)
+    o = OracleSim(32, 40, 32, re=wl.re, dt=wl.dt, scheme=scheme, ybc=ybc, yfaces=yf)
+    g = ibm.Simulation(32, 40, 32, re=wl.re, dt=wl.dt, scheme=scheme, ybc=ybc, precision=precision, y_faces=yf)
+    for sim in (o, g):
+        sim.set_fields(*init)
+    for s in range(6):
+        xyz, vel = wl.surface(s)
+        for sim in (o, g):
+            sim.set_surface(xyz, vel, wl.tri)
+            sim.step()
+    gu, gv, gw, gp = g.fields()
+    err = max(np.abs(o.u - gu).max(), np.abs(o.v - gv).max(), np.abs(o.w - gw).max())
+    assert err <= tol * max(1.0, np.abs(o.u).max()), err
+    for c, t in enumerate(g.tags()):
+        np.testing.assert_array_equal(t, o.owners[c], err_msg=f"component {c}")
+
+
 def test_stretched_immersed_wall_channel_matches_oracle():
     """An immersed wall across the channel close to the lower wall, where
     the cells are smallest, with a body force along x and a random initial
