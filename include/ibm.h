@@ -351,6 +351,17 @@ ibm_status ibm_get_pressure_recon(ibm_handle h, double* p, int on_device);
  * Allocates 16 bytes on the device; synchronises the device. */
 ibm_status ibm_check_conversions(long long n, long long* mismatches, long long* checked);
 
+/* Self-check of the bounded waits (no counterpart in the paper): kernels
+ * whose tiles arrive by asynchronous copies wait on an mbarrier with a
+ * cycle limit and report a timeout through the device error word instead of
+ * waiting without bound.  Runs one block whose mbarrier can never complete
+ * and waits on it with limit_cycles (0 to 4e9 SM cycles).  *timed_out: 1 if
+ * the wait gave up (expected); *waited_cycles: the cycles it waited.  The
+ * device stays usable afterwards.  Allocates 16 bytes on the device;
+ * synchronises the device.  IBM_ERR_ARG for a limit out of range or null
+ * outputs. */
+ibm_status ibm_check_bounded_wait(long long limit_cycles, int* timed_out, long long* waited_cycles);
+
 /* Library version string. */
 const char* ibm_version(void);
 

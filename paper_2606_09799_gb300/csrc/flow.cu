@@ -14,6 +14,7 @@
 #include <cuda.h>
 #include <mutex>
 #include "launch.h"
+#include "mbar.cuh"
 
 namespace ibm {
 
@@ -1662,24 +1663,6 @@ struct SweepYStream {
 constexpr int SYT_W = 32;                              // lines per tile (128 B of FP32 per row)
 constexpr long long SYT_WAIT_CYCLES = 4000000000ll;   // about 2 s at the top SM clock
 
-__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-// Wait for phase `parity` of the mbarrier at `bar`, giving up after a fixed
-// number of cycles (false).
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
-  const long long t0 = clock64();
-  while (true) {
-    unsigned done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (done) return true;
-    if (clock64() - t0 > SYT_WAIT_CYCLES) return false;
-  }
-}
-
 // One box of a 3-D tensor map (coordinates x fastest) into shared memory.
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, unsigned bar) {
   asm volatile(
@@ -1734,11 +1717,11 @@ __device__ __forceinline__ void sweep_y_tma(const Blk& bk, const SweepYTma<T>& o
     cqS[r] = last ? (T)0 : __ldg((tang ? tb.ycpW : tb.vcpR) + r);
   }
   __syncwarp();
-  if (!mbar_wait(bar, 0)) {
+  if (!mbar_wait(bar, 0, SYT_WAIT_CYCLES)) {
     // the copies did not complete: report, give them one more bounded wait
     // (they write this block's shared memory) and leave the tile untouched
     if (lane == 0) atomicOr(&op.ds->err, ERR_WAIT);
-    mbar_wait(bar, 0);
+    mbar_wait(bar, 0, SYT_WAIT_CYCLES);
     return;
   }
   if (lane >= nl) return;

@@ -1,9 +1,11 @@
 // selfcheck.cu -- bit-for-bit check of the integer-pipe FP32 <-> FP64
-// conversions (common.cuh) against the hardware conversions.
+// conversions (common.cuh) against the hardware conversions, and a check
+// that the bounded mbarrier wait (mbar.cuh) gives up and returns.
 #include <cuda_runtime.h>
 
 #include "common.cuh"
 #include "ibm.h"
+#include "mbar.cuh"
 
 namespace ibm {
 
@@ -60,7 +62,44 @@ __global__ void k_check_conversions(long long n, unsigned long long* out) {
   atomicAdd(out + 1, fast);
 }
 
+// An mbarrier whose phase cannot complete: one expected arrival, made with
+// 16 bytes of transaction count that no copy ever delivers.  Every thread
+// waits on it through the bounded wait; out[0] = 1 if thread 0's wait gave
+// up, out[1] = the cycles it waited.
+__global__ void k_check_bounded_wait(long long limit_cycles, long long* out) {
+  __shared__ __align__(8) unsigned long long bar_mem;
+  const unsigned bar = smem_addr(&bar_mem);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], 16;\n" ::"r"(bar) : "memory");
+  }
+  __syncthreads();
+  const long long t0 = clock64();
+  const bool done = mbar_wait(bar, 0, limit_cycles);
+  const long long t1 = clock64();
+  if (threadIdx.x == 0) {
+    out[0] = done ? 0 : 1;
+    out[1] = t1 - t0;
+  }
+}
+
 }  // namespace ibm
+
+extern "C" ibm_status ibm_check_bounded_wait(long long limit_cycles, int* timed_out, long long* waited_cycles) {
+  if (limit_cycles < 0 || limit_cycles > 4000000000ll || !timed_out || !waited_cycles) return IBM_ERR_ARG;
+  long long* d = nullptr;
+  if (cudaMalloc(&d, 2 * sizeof(long long)) != cudaSuccess) return IBM_ERR_OOM;
+  long long h[2] = {0, 0};
+  ibm_status st = IBM_OK;
+  ibm::k_check_bounded_wait<<<1, 32>>>(limit_cycles, d);
+  if (cudaGetLastError() != cudaSuccess) st = IBM_ERR_CUDA;
+  if (st == IBM_OK && cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) st = IBM_ERR_CUDA;
+  cudaFree(d);
+  *timed_out = (int)h[0];
+  *waited_cycles = h[1];
+  return st;
+}
 
 extern "C" ibm_status ibm_check_conversions(long long n, long long* mismatches, long long* checked) {
   if (n < 0 || !mismatches || !checked) return IBM_ERR_ARG;

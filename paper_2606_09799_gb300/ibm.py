@@ -76,7 +76,7 @@ EXPORTS = ("ibm_create_grid", "ibm_destroy", "ibm_set_surface", "ibm_set_body_fo
            "ibm_set_tune", "ibm_get_tune", "ibm_autotune", "ibm_batch_create", "ibm_batch_destroy",
            "ibm_batch_step", "ibm_batch_sync", "ibm_batch_get_info", "ibm_batch_profile_stages",
            "ibm_batch_set_tune", "ibm_batch_autotune", "ibm_batch_last_error", "ibm_step_batch",
-           "ibm_get_loads", "ibm_get_pressure_recon", "ibm_check_conversions", "ibm_create_grid_stretched")
+           "ibm_get_loads", "ibm_get_pressure_recon", "ibm_check_conversions", "ibm_create_grid_stretched", "ibm_check_bounded_wait")
 
 
 def library_path() -> str:
@@ -131,6 +131,9 @@ def load(build_if_needed: bool = True):
         L.ibm_get_loads.argtypes = [P, I, P, P, P, P, P]
         L.ibm_get_pressure_recon.argtypes = [P, P, I]
         L.ibm_create_grid_stretched.argtypes = [ctypes.POINTER(ibm_grid_desc), P, P, ctypes.POINTER(P)]
+        L.ibm_check_bounded_wait.argtypes = [ctypes.c_longlong, ctypes.POINTER(ctypes.c_int),
+                                             ctypes.POINTER(ctypes.c_longlong)]
+        L.ibm_check_bounded_wait.restype = ctypes.c_int
         L.ibm_check_conversions.argtypes = [ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong),
                                             ctypes.POINTER(ctypes.c_longlong)]
         for name in EXPORTS:
@@ -382,6 +385,16 @@ def ibm_check_conversions(n: int) -> tuple:
     if st != 0:
         raise IbmError(st, "ibm_check_conversions failed")
     return bad.value, fast.value
+
+
+def ibm_check_bounded_wait(limit_cycles: int) -> tuple:
+    """(timed_out, waited_cycles) of a bounded mbarrier wait that cannot
+    complete (ibm_check_bounded_wait)."""
+    t, c = ctypes.c_int(0), ctypes.c_longlong(0)
+    st = load().ibm_check_bounded_wait(int(limit_cycles), ctypes.byref(t), ctypes.byref(c))
+    if st != 0:
+        raise IbmError(st, "ibm_check_bounded_wait failed")
+    return t.value, c.value
 
 
 def ibm_get_pressure_recon(h, nx, ny, nz):

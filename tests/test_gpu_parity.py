@@ -385,6 +385,21 @@ def test_radix5_grid_matches_oracle(precision, tol):
         assert np.abs((o.p - o.p.mean()) - (gp - gp.mean())).max() <= 1e-10
 
 
+
+def test_bounded_wait_gives_up_and_the_device_stays_usable():
+    """The asynchronous-copy kernels never wait without bound: a wait on an
+    mbarrier that cannot complete gives up after its cycle limit and
+    returns, and the device context stays usable."""
+    timed_out, waited = ibm.ibm_check_bounded_wait(2_000_000)
+    assert timed_out == 1
+    assert waited >= 2_000_000
+    g = ibm.Simulation(16, 16, 16, precision="fp64")
+    xyz, tri = inputs.icosphere(1, 0.2, (0.5, 0.5, 0.5))
+    g.set_surface(xyz, np.zeros_like(xyz), tri)
+    g.step(2)
+    g.sync()
+    assert g.diag()["steps"] == 2
+
 def test_integer_path_conversions_match_hardware():
     """The mixed path's FP32 <-> FP64 conversions on the integer pipes give
     the hardware conversion's result bit for bit on 2^22 hashed cases
