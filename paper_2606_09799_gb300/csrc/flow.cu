@@ -1451,61 +1451,97 @@ struct SweepZStream {
 // The same line in FP32 from the FP32 copies of the row tables (mixed path):
 // a line without forcing rows in one wall segment, a line with forcing rows
 // restarting at [start row][row] after each identity row (c' to the scratch
-// array).
+// array).  Rows move in batches of SYS_B through registers, every load of a
+// batch issued before its recurrence runs.
+constexpr int SYS_B = 8;
+
 __device__ __forceinline__ void sweep_y_stretched_f32(const Geo& g, const Fields<float>& f,
                                                       const unsigned* __restrict__ flags32, bool any, int c, int i,
                                                       int k, int n, int jj0, int sn, float* __restrict__ Rl,
                                                       float* __restrict__ Sl, float* __restrict__ Ul,
                                                       float* __restrict__ Ll) {
   const float* __restrict__ ta = g.yt.yswf + (c == 1 ? 3ll * g.ny : 0);
-  float p = 0.0f;
-  if (!any) {
-    const float* __restrict__ tv = ta + n;
-    for (int m = 0; m < n; ++m) {
-      p = fmaf(-__ldg(ta + m), p, Rl[m * sn]) * __ldg(tv + m);
-      Rl[m * sn] = p;
-    }
-    const float* __restrict__ tc = tv + n;
-    float x = 0.0f;
-    for (int m = n - 1; m >= 0; --m) {
-      x = fmaf(-__ldg(tc + m), x, Rl[m * sn]);
-      if (Ll) {
-        float hi = Ul[m * sn], lo = Ll[m * sn];
-        ff_add(hi, lo, x);
-        Ul[m * sn] = hi;
-        Ll[m * sn] = lo;
-      } else {
-        Ul[m * sn] += x;
-      }
-    }
-    return;
-  }
+  const float* __restrict__ tv = ta + n;
+  const float* __restrict__ tc = tv + n;
   const float* __restrict__ iv2 = g.yt.ysw2f + (c == 1 ? 2ll * g.ny * g.ny : 0);
   const float* __restrict__ cp2 = iv2 + (long long)n * n;
+  const unsigned char* __restrict__ Fl = reinterpret_cast<const unsigned char*>(flags32) + cidx(g, i, jj0, k);
+  // ---- forward
+  float p = 0.0f;
   long long s0 = 0;
-  for (int m = 0; m < n; ++m) {
-    float cq = 0.0f;
-    if (is_forcing(flags32, cidx(g, i, jj0 + m, k), c)) {
-      p = Rl[m * sn];
-      s0 = m + 1;
-    } else {
-      const long long id = s0 * n + m;
-      p = fmaf(-__ldg(ta + m), p, Rl[m * sn]) * __ldg(iv2 + id);
-      cq = __ldg(cp2 + id);
+  for (int m0 = 0; m0 < n; m0 += SYS_B) {
+    float r[SYS_B];
+    unsigned char fl[SYS_B];
+#pragma unroll
+    for (int u = 0; u < SYS_B; ++u) {
+      const int m = m0 + u;
+      r[u] = 0.0f;
+      fl[u] = 0;
+      if (m < n) {
+        r[u] = Rl[m * sn];
+        if (any) fl[u] = Fl[(long long)m * sn];
+      }
     }
-    Rl[m * sn] = p;
-    Sl[m * sn] = cq;
+    float cq[SYS_B];
+#pragma unroll
+    for (int u = 0; u < SYS_B; ++u) {
+      const int m = m0 + u;
+      cq[u] = 0.0f;
+      if (m >= n) continue;
+      if (!any) {
+        p = fmaf(-__ldg(ta + m), p, r[u]) * __ldg(tv + m);
+      } else if ((fl[u] >> c) & 1) {
+        p = r[u];
+        s0 = m + 1;
+      } else {
+        const long long id = s0 * n + m;
+        p = fmaf(-__ldg(ta + m), p, r[u]) * __ldg(iv2 + id);
+        cq[u] = __ldg(cp2 + id);
+      }
+      r[u] = p;
+    }
+#pragma unroll
+    for (int u = 0; u < SYS_B; ++u) {
+      const int m = m0 + u;
+      if (m < n) {
+        Rl[m * sn] = r[u];
+        if (any) Sl[m * sn] = cq[u];
+      }
+    }
   }
+  // ---- backward: x_m = p_m - c'_m x_{m+1}; uhat = u^s + x
   float x = 0.0f;
-  for (int m = n - 1; m >= 0; --m) {
-    x = fmaf(-Sl[m * sn], x, Rl[m * sn]);
-    if (Ll) {
-      float hi = Ul[m * sn], lo = Ll[m * sn];
-      ff_add(hi, lo, x);
-      Ul[m * sn] = hi;
-      Ll[m * sn] = lo;
-    } else {
-      Ul[m * sn] += x;
+  for (int m1 = n - 1; m1 >= 0; m1 -= SYS_B) {
+    float pv[SYS_B], cv[SYS_B], uh[SYS_B], ul[SYS_B];
+#pragma unroll
+    for (int u = 0; u < SYS_B; ++u) {
+      const int m = m1 - u;
+      pv[u] = cv[u] = uh[u] = ul[u] = 0.0f;
+      if (m >= 0) {
+        pv[u] = Rl[m * sn];
+        cv[u] = any ? Sl[m * sn] : __ldg(tc + m);
+        uh[u] = Ul[m * sn];
+        if (Ll) ul[u] = Ll[m * sn];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < SYS_B; ++u) {
+      const int m = m1 - u;
+      if (m < 0) break;
+      x = fmaf(-cv[u], x, pv[u]);
+      if (Ll) {
+        ff_add(uh[u], ul[u], x);
+      } else {
+        uh[u] += x;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < SYS_B; ++u) {
+      const int m = m1 - u;
+      if (m >= 0) {
+        Ul[m * sn] = uh[u];
+        if (Ll) Ll[m * sn] = ul[u];
+      }
     }
   }
 }
