@@ -1285,11 +1285,12 @@ __device__ __forceinline__ void sweep_y_stream(const Blk& bk, const Geo& g, cons
       if (j < n) {
         prev = (e[u] - am[u] * prev) * iv[u];
         Rl[j * sn] = prev;
-        Sl[j * sn] = cq[u];
+        if (any) Sl[j * sn] = cq[u];   // a line without forcing rows reads c' from the table
       }
     }
   }
   // ---- backward: x_j = p_j - c'_j x_{j+1}; uhat = u^s + x
+  const T* __restrict__ cpw = tang ? tb.ycpW : tb.vcpR;   // c' of one wall segment
   T x = (T)0;
   for (int j1 = n - 1; j1 >= 0; j1 -= SYB) {
     T pv[SYB], cv[SYB], uh[SYB], ul[SYB];
@@ -1299,7 +1300,7 @@ __device__ __forceinline__ void sweep_y_stream(const Blk& bk, const Geo& g, cons
       pv[u] = cv[u] = uh[u] = ul[u] = (T)0;
       if (j >= 0) {
         pv[u] = Rl[j * sn];
-        cv[u] = Sl[j * sn];
+        cv[u] = any ? Sl[j * sn] : (j < n - 1 ? __ldg(cpw + j) : (T)0);
         uh[u] = Ul[j * sn];
         if (Ll) ul[u] = Ll[j * sn];
       }
@@ -1403,7 +1404,7 @@ __device__ __forceinline__ void sweep_z_stream(const Blk& bk, const Geo& g, cons
         prev = (dq - am[u] * prev) * iv[u];
         const int r = rot(q);
         Rl[r * sn] = prev;
-        Sl[r * sn] = cq[u];
+        if (any) Sl[r * sn] = cq[u];   // a line without forcing rows reads c' from the table
       }
     }
   }
@@ -1419,7 +1420,7 @@ __device__ __forceinline__ void sweep_z_stream(const Blk& bk, const Geo& g, cons
       if (q >= 0) {
         const int r = rot(q);
         pv[u] = Rl[r * sn];
-        cv[u] = Sl[r * sn];
+        cv[u] = any ? Sl[r * sn] : (q < n - 1 ? __ldg(tb.cp[1] + q) : (T)0);
         if (!any) zq[u] = __ldg(tb.zv[1] + q);
       }
     }
