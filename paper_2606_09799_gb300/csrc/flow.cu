@@ -1404,7 +1404,7 @@ __device__ __forceinline__ void sweep_z_stream(const Blk& bk, const Geo& g, cons
         prev = (dq - am[u] * prev) * iv[u];
         const int r = rot(q);
         Rl[r * sn] = prev;
-        if (any) Sl[r * sn] = cq[u];   // a line without forcing rows reads c' from the table
+        Sl[r * sn] = cq[u];
       }
     }
   }
@@ -1420,7 +1420,7 @@ __device__ __forceinline__ void sweep_z_stream(const Blk& bk, const Geo& g, cons
       if (q >= 0) {
         const int r = rot(q);
         pv[u] = Rl[r * sn];
-        cv[u] = any ? Sl[r * sn] : (q < n - 1 ? __ldg(tb.cp[1] + q) : (T)0);
+        cv[u] = Sl[r * sn];
         if (!any) zq[u] = __ldg(tb.zv[1] + q);
       }
     }
