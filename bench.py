@@ -155,8 +155,15 @@ def stage_kernel(stage: str, tune: dict | None, precision: str, ny: int = 128) -
     t = tune or {}
     T = "float" if precision == "mixed" else "double"
     if stage in ("sweep_y", "sweep_z"):
-        if t.get("sweep_y", 0) == 1:
-            return f"SweepYStream<{T}>" if stage == "sweep_y" else f"SweepZStream<{T}>"
+        sy = t.get("sweep_y", 0)
+        if sy in (1, 2, 3):
+            if stage == "sweep_z":
+                return f"SweepZStream<{T}>"
+            if sy == 3 and precision == "mixed":
+                return f"SweepYStretched<{T}>"
+            if sy == 2:
+                return f"SweepYTma<{T}>"
+            return f"SweepYStream<{T}>"
         if precision == "mixed" and t.get("sweep_zy", 0) != 1:
             return f"SweepLanes<{T}, 16, 8>"
         return f"SweepZY<{T}>"

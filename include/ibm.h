@@ -248,7 +248,9 @@ typedef struct {
   int sweep_y;        /* z and y sweeps: 0 as sweep_zy, 1 one thread per line with its rows streamed
                          through registers (any line length), 2 as 1 for z, and for y tiles of 32
                          lines staged in shared memory by bulk asynchronous copies (where every row
-                         starts on a 16-byte boundary and the tile fits; else as 1) */
+                         starts on a 16-byte boundary and the tile fits; else as 1), 3 as 1 for z,
+                         and for y the mixed path's tabulated FP32 rows in register batches (grids of
+                         at most 1024 rows; else as 1) */
   double ms_per_step; /* set by the autotuners: measured time per step of the chosen shapes */
 } ibm_tune;
 

@@ -155,7 +155,8 @@ struct Tune {
   int sweep_zy;   // z and y sweeps (FP32): 1 shared-memory tile, one thread per line; 2 several lanes per line
   int fft_plane;  // 1 separate x and z transform kernels; 2 fused per y-plane (when the plane fits)
   int sweep_y;    // z and y sweeps: 0 as sweep_zy; 1 one thread per line, rows streamed through registers;
-                  // 2 z as 1, y from tiles staged by bulk asynchronous copies (else as 1)
+                  // 2 z as 1, y from tiles staged by bulk asynchronous copies (else as 1);
+                  // 3 z as 1, y from the tabulated FP32 rows in register batches (mixed path, else as 1)
 };
 
 struct Exec {

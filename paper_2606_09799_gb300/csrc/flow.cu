@@ -1993,6 +1993,12 @@ void launch_sweeps(const Geo& g, const Fields<T>& f, const TagBuffers& b, const 
               SweepYStretched<T>{g, f, b.flags32, b.lines.y, (double)tb.off[0] * g.dx * g.dx});
   } else if (ex.tune.sweep_y == 2 && !ex.rec && sweep_y_tma_ok<T>(g, f, b, tb, ds, sh.ny, ex)) {
     // (launched inside the check: the op carries its tensor maps)
+  } else if (ex.tune.sweep_y == 3 && sizeof(T) == 4 && sh.ny <= 1024 && g.yt.yswf && g.yt.ysw2f) {
+    // the tabulated FP32 rows (uniform spacing written as the non-uniform
+    // grid's tables; built for every mixed grid of at most 1024 rows)
+    const long long lines = (long long)g.nx * g.nz;
+    ex.launch(dim3((unsigned)((lines + 127) / 128), 3), dim3(128), 0,
+              SweepYStretched<T>{g, f, b.flags32, b.lines.y, (double)tb.off[0] * g.dx * g.dx});
   } else if (ex.tune.sweep_y >= 1) {
     const long long lines = (long long)g.nx * g.nz;
     ex.launch(dim3((unsigned)((lines + 127) / 128), 3), dim3(128), 0, SweepYStream<T>{g, f, b.flags32, tb, b.lines.y});

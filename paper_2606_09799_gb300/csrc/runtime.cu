@@ -354,6 +354,61 @@ static bool build_wall(ibm_handle h, double off) {
   return true;
 }
 
+// Rows of the wall-normal sweep, for lines without forcing nodes and for
+// segments that restart after a forcing row.  Row j of the tangential
+// components (ny rows, wall ghost in the first and last) and of v (ny - 1
+// interior rows) couples to its neighbours with beta / (h_c h_f) from the
+// inverse spacings ihc (ny) and ihf (ny + 1).  out1 (6 ny - 3): a, 1/pivot,
+// c' of one wall segment, tangential then v; out2 (if not null): 1/pivot and
+// c' at [start row][row], tangential (two ny x ny) then v (two (ny-1)^2).
+static void y_sweep_rows(int ny, double beta, double gs, const double* ihc, const double* ihf, double* out1,
+                         std::vector<double>* out2) {
+  if (out2) out2->assign(2ull * ny * ny + 2ull * (ny - 1) * (ny - 1), 0.0);
+  for (int kind = 0; kind < 2; ++kind) {
+    const bool tang = kind == 0;
+    const int n = tang ? ny : ny - 1, jj0 = tang ? 0 : 1;
+    double* ta = out1 + (tang ? 0 : 3 * ny);
+    double* tv = ta + n;
+    double* tcp = tv + n;
+    double* iv2 = out2 ? out2->data() + (tang ? 0 : 2ull * ny * ny) : nullptr;
+    double* cp2 = iv2 ? iv2 + (size_t)n * n : nullptr;
+    for (int s0 = 0; s0 < (out2 ? n : 1); ++s0) {
+      double cprev = 0.0;
+      for (int m = s0; m < n; ++m) {
+        const int j = jj0 + m;
+        volatile double sb, sn;
+        if (tang) {
+          sb = beta * ihc[j] * ihf[j];
+          sn = beta * ihc[j] * ihf[j + 1];
+        } else {
+          sb = beta * ihf[j] * ihc[j - 1];
+          sn = beta * ihf[j] * ihc[j];
+        }
+        volatile double a = -sb, b = 1.0 + sb + sn, cc = -sn;
+        if (m == 0) {
+          if (tang) b = b - gs * sb;
+          a = 0.0;
+        }
+        if (m == n - 1) {
+          if (tang) b = b - gs * sn;
+          cc = 0.0;
+        }
+        volatile double den = b - a * cprev;
+        cprev = cc / den;
+        if (s0 == 0) {
+          ta[m] = a;
+          tv[m] = 1.0 / den;
+          tcp[m] = cprev;
+        }
+        if (iv2) {
+          iv2[(size_t)s0 * n + m] = 1.0 / den;
+          cp2[(size_t)s0 * n + m] = cprev;
+        }
+      }
+    }
+  }
+}
+
 template <typename T>
 static SweepTables<T> sweep_tables(ibm_handle h) {
   SweepTables<T> t;
@@ -854,7 +909,7 @@ struct Knob {
 };
 
 static std::vector<Knob> tune_knobs() {
-  return {{&Tune::fft_plane, {2, 1}}, {&Tune::sweep_zy, {2, 1}}, {&Tune::sweep_y, {1, 2}}, {&Tune::tri_y, {1, 2, 3}},
+  return {{&Tune::fft_plane, {2, 1}}, {&Tune::sweep_zy, {2, 1}}, {&Tune::sweep_y, {1, 2, 3}}, {&Tune::tri_y, {1, 2, 3}},
           {&Tune::sweep_w, {64, 32, 16}},
           {&Tune::fft_lpb, {0, 8, 4, 2}},
           {&Tune::fft_cols, {16, 8, 4}}};
@@ -1105,6 +1160,15 @@ ibm_status ibm_create_grid(const ibm_grid_desc* desc, void* stream, ibm_handle* 
   else
     ok = build_periodic<float>(h, d.nx, h->tbl_off[0], 0) && build_periodic<float>(h, d.nz, h->tbl_off[2], 1) &&
          build_wall<float>(h, h->tbl_off[1]);
+  if (ok && d.precision != IBM_FP64 && d.ny <= 1024) {
+    // FP32 rows of the tabulated y sweep (launch shape sweep_y = 3), the
+    // uniform spacing written as the non-uniform grid's tables
+    std::vector<double> ih(d.ny + 1, g.idy), t1(6ull * d.ny - 3), t2;
+    y_sweep_rows(d.ny, h->tbl_off[0] * g.dx * g.dx, d.ybc == 0 ? -1.0 : 1.0, ih.data(), ih.data(), t1.data(), &t2);
+    h->g.yt.yswf = (const float*)upload_vec<float>(h, t1);
+    h->g.yt.ysw2f = (const float*)upload_vec<float>(h, t2);
+    ok = h->g.yt.yswf && h->g.yt.ysw2f;
+  }
   // Poisson: modified wavenumbers, twiddles, pivots
   const double pi = 3.14159265358979323846;
   std::vector<double> lx(g.nkx), lz(g.nz), twx(2 * g.nx), twz(2 * g.nz);
@@ -1192,89 +1256,14 @@ ibm_status ibm_create_grid_stretched(const ibm_grid_desc* desc, const double* y_
   for (int j = 0; j <= ny; ++j) yv[j + 1] = y_faces[j];
   yv[0] = -y_faces[1];
   yv[ny + 2] = 2.0 * y_faces[ny] - y_faces[ny - 1];
-  // y sweep rows of a line without forcing nodes (tangential components:
-  // ny rows with the wall ghost in the first and last; v: ny - 1 interior
-  // rows), with beta as the sweep kernel receives it (the x table's
+  // y sweep rows (one wall segment; and [start row][row] segments for ny up
+  // to 1024), with beta as the sweep kernel receives it (the x table's
   // coefficient times dx^2, in the path's own type)
+  std::vector<double> t2;
   {
     const double ox = desc->precision == IBM_FP64 ? h->tbl_off[0] : (double)(float)h->tbl_off[0];
-    const double beta = ox * h->g.dx * h->g.dx;
-    const double gs = h->g.ybc == 0 ? -1.0 : 1.0;
-    double* ysw = yv + ny + 3;
-    for (int kind = 0; kind < 2; ++kind) {
-      const bool tang = kind == 0;
-      const int n = tang ? ny : ny - 1, jj0 = tang ? 0 : 1;
-      double* ta = ysw + (tang ? 0 : 3 * ny);
-      double* tv = ta + n;
-      double* tcp = tv + n;
-      double cprev = 0.0;
-      for (int m = 0; m < n; ++m) {
-        const int j = jj0 + m;
-        volatile double sb, sn;
-        if (tang) {
-          sb = beta * ihc[j] * ihf[j];
-          sn = beta * ihc[j] * ihf[j + 1];
-        } else {
-          sb = beta * ihf[j] * ihc[j - 1];
-          sn = beta * ihf[j] * ihc[j];
-        }
-        volatile double a = -sb, b = 1.0 + sb + sn, cc = -sn;
-        if (m == 0) {
-          if (tang) b = b - gs * sb;
-          a = 0.0;
-        }
-        if (m == n - 1) {
-          if (tang) b = b - gs * sn;
-          cc = 0.0;
-        }
-        volatile double den = b - a * cprev;
-        cprev = cc / den;
-        ta[m] = a;
-        tv[m] = 1.0 / den;
-        tcp[m] = cprev;
-      }
-    }
-  }
-  // segments that start after a forcing row: 1/pivot and c' at [s][m]
-  std::vector<double> t2;
-  if (ny <= 1024) {
-    const double ox = desc->precision == IBM_FP64 ? h->tbl_off[0] : (double)(float)h->tbl_off[0];
-    const double beta = ox * h->g.dx * h->g.dx;
-    const double gs = h->g.ybc == 0 ? -1.0 : 1.0;
-    t2.assign(2ull * ny * ny + 2ull * (ny - 1) * (ny - 1), 0.0);
-    for (int kind = 0; kind < 2; ++kind) {
-      const bool tang = kind == 0;
-      const int n = tang ? ny : ny - 1, jj0 = tang ? 0 : 1;
-      double* iv2 = t2.data() + (tang ? 0 : 2ull * ny * ny);
-      double* cp2 = iv2 + (size_t)n * n;
-      for (int s0 = 0; s0 < n; ++s0) {
-        double cprev = 0.0;
-        for (int m = s0; m < n; ++m) {
-          const int j = jj0 + m;
-          volatile double sb, sn;
-          if (tang) {
-            sb = beta * ihc[j] * ihf[j];
-            sn = beta * ihc[j] * ihf[j + 1];
-          } else {
-            sb = beta * ihf[j] * ihc[j - 1];
-            sn = beta * ihf[j] * ihc[j];
-          }
-          volatile double a = -sb, b = 1.0 + sb + sn, cc = -sn;
-          if (m == 0) {
-            if (tang) b = b - gs * sb;
-            a = 0.0;
-          }
-          if (m == n - 1) {
-            if (tang) b = b - gs * sn;
-            cc = 0.0;
-          }
-          volatile double den = b - a * cprev;
-          cprev = cc / den;
-          iv2[(size_t)s0 * n + m] = 1.0 / den;
-          cp2[(size_t)s0 * n + m] = cprev;
-        }
-      }
-    }
+    y_sweep_rows(ny, ox * h->g.dx * h->g.dx, h->g.ybc == 0 ? -1.0 : 1.0, ihc, ihf, yv + ny + 3,
+                 ny <= 1024 ? &t2 : nullptr);
   }
   double smin = hc[0], smax = hc[0];
   for (int j = 0; j < ny; ++j) { smin = std::min(smin, hc[j]); smax = std::max(smax, hc[j]); }
@@ -1668,7 +1657,7 @@ static bool tune_valid(const ibm_tune* t) {
   if (t->fft_cols < 0 || t->fft_cols > 16 || (t->fft_cols & (t->fft_cols - 1))) return false;
   if (t->sweep_zy < 0 || t->sweep_zy > 2) return false;
   if (t->fft_plane < 0 || t->fft_plane > 2) return false;
-  if (t->sweep_y < 0 || t->sweep_y > 2) return false;
+  if (t->sweep_y < 0 || t->sweep_y > 3) return false;
   return true;
 }
 

@@ -180,16 +180,18 @@ def test_batch_autotune_leaves_state():
     b.close()
 
 
+@pytest.mark.parametrize("sweep_y", [2, 3])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_batch_bulk_copy_y_tiles_equal_solo(precision):
-    """Launch-shape choice sweep_y = 2 in a batch of uneven instances (which
-    keeps the streamed y sweep: its ops live in global memory, not in kernel
-    parameters where tensor maps must be) and alone (the y sweep from
-    TMA-staged tiles): the same fields, bit for bit in FP64."""
+def test_batch_bulk_copy_y_tiles_equal_solo(precision, sweep_y):
+    """Launch-shape choices sweep_y = 2 and 3 in a batch of uneven instances
+    and alone: the same fields, bit for bit in FP64.  (With 2 a batch keeps
+    the streamed y sweep: its ops live in global memory, not in kernel
+    parameters where tensor maps must be; 3 is the mixed path's tabulated
+    rows in both.)"""
     wls = small_batch()
     sims = [make(w, precision) for w in wls]
     b = ibm.Batch(sims)
-    b.set_tune(tri_y=1, sweep_y=2, fft_plane=2)
+    b.set_tune(tri_y=1, sweep_y=sweep_y, fft_plane=2)
     for s in range(3):
         for w, g in zip(wls, sims):
             xyz, vel = w.surface(s)
@@ -198,7 +200,7 @@ def test_batch_bulk_copy_y_tiles_equal_solo(precision):
     b.sync()
     for w, g in zip(wls, sims):
         ref = make(w, precision)
-        ibm.ibm_set_tune(ref.h, tri_y=1, sweep_y=2, fft_plane=2)
+        ibm.ibm_set_tune(ref.h, tri_y=1, sweep_y=sweep_y, fft_plane=2)
         for s in range(3):
             xyz, vel = w.surface(s)
             ref.set_surface(xyz, vel, w.tri)
@@ -218,6 +220,6 @@ def test_tune_values_are_validated():
     with pytest.raises(ibm.IbmError):
         ibm.ibm_set_tune(g.h, fft_cols=3)
     with pytest.raises(ibm.IbmError):
-        ibm.ibm_set_tune(g.h, sweep_y=3)
+        ibm.ibm_set_tune(g.h, sweep_y=4)
     ibm.ibm_set_tune(g.h, tri_y=2, sweep_w=16, fft_lpb=4, fft_cols=4)
     assert ibm.ibm_get_tune(g.h)["sweep_w"] == 16

@@ -288,11 +288,12 @@ def test_candidate_capacity_grows_for_large_triangles():
                                   dict(tri_y=3, fft_lpb=2, fft_cols=2, fft_plane=1),
                                   dict(tri_y=3, sweep_zy=1, sweep_w=64, fft_lpb=8, fft_cols=16, fft_plane=2),
                                   dict(tri_y=1, sweep_zy=2, sweep_y=1, fft_plane=2),
-                                  dict(tri_y=1, sweep_y=2, fft_plane=2)])
+                                  dict(tri_y=1, sweep_y=2, fft_plane=2),
+                                  dict(tri_y=1, sweep_y=3, fft_plane=2)])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-5)])
 def test_every_launch_shape_matches_oracle(tune, precision, tol):
     """Every choice the autotuner can make (Thomas variant, sweep form and
-    width, streamed y sweep, bulk-copy y tiles, FFT tiling) computes the same step: against the oracle on a
+    width, streamed y sweep, bulk-copy y tiles, tabulated y rows, FFT tiling) computes the same step: against the oracle on a
     ragged grid with a moving sphere, 4 steps."""
     wl = inputs.oscillating_sphere(n=48, steps=4, subdiv=2)
     o = OracleSim(48, 37, 96, 1.0, 0.9, 1.6, re=150.0, dt=2e-3)
