@@ -154,27 +154,21 @@ static double dot3(const double a[3], const double b[3]) {
 /* ------------------------------------------------------------------ */
 /* Closest point on a triangle (Algorithm 1, step "closest point",     */
 /* which cites Ericson 2004).  Voronoi-region classification of p      */
-/* against the vertex, edge and face regions of triangle (a,b,c).       */
-/* The six scalar products of the classification are formed from two   */
-/* per-point products and four per-triangle constants (ab.bp = ab.ap - */
-/* |ab|^2, etc.), and the edge/face parameters divide by per-triangle  */
-/* constants (|ab|^2, |ac|^2, |bc|^2, |ab|^2|ac|^2 - (ab.ac)^2), all    */
-/* equal in exact arithmetic to the textbook quotients.                 */
+/* against the vertex, edge and face regions of triangle (a,b,c), with  */
+/* the textbook quantities: the six scalar products of the edge vectors */
+/* with p - a, p - b and p - c, each formed from its own difference     */
+/* vector, and the edge and face parameters as the quotients of those   */
+/* products (t = d1 / (d1 - d3), ..., s = 1 / (va + vb + vc)).          */
 /* Returns X and its barycentric weights w (w[0]+w[1]+w[2]=1).         */
 /* ------------------------------------------------------------------ */
 void orc_closest_point(const double p[3], const double a[3], const double b[3], const double c[3],
                        double X[3], double w[3]) {
-  double ab[3], ac[3], bc[3], ap[3];
+  double ab[3], ac[3], ap[3], bp[3], cp[3];
   for (int d = 0; d < 3; ++d) {
     ab[d] = b[d] - a[d];
     ac[d] = c[d] - a[d];
-    bc[d] = c[d] - b[d];
+    ap[d] = p[d] - a[d];
   }
-  /* per-triangle constants */
-  const double aa = dot3(ab, ab), abac = dot3(ab, ac), cc = dot3(ac, ac), bcbc = dot3(bc, bc);
-  const double den = aa * cc - abac * abac;
-  /* per-point products */
-  for (int d = 0; d < 3; ++d) ap[d] = p[d] - a[d];
   const double d1 = dot3(ab, ap);
   const double d2 = dot3(ac, ap);
   if (d1 <= 0.0 && d2 <= 0.0) {                         /* vertex a region */
@@ -182,8 +176,9 @@ void orc_closest_point(const double p[3], const double a[3], const double b[3], 
     w[0] = 1.0; w[1] = 0.0; w[2] = 0.0;
     return;
   }
-  const double d3 = d1 - aa;                            /* ab . (p - b) */
-  const double d4 = d2 - abac;                          /* ac . (p - b) */
+  for (int d = 0; d < 3; ++d) bp[d] = p[d] - b[d];
+  const double d3 = dot3(ab, bp);
+  const double d4 = dot3(ac, bp);
   if (d3 >= 0.0 && d4 <= d3) {                          /* vertex b region */
     for (int d = 0; d < 3; ++d) X[d] = b[d];
     w[0] = 0.0; w[1] = 1.0; w[2] = 0.0;
@@ -191,13 +186,14 @@ void orc_closest_point(const double p[3], const double a[3], const double b[3], 
   }
   const double vc = d1 * d4 - d3 * d2;
   if (vc <= 0.0 && d1 >= 0.0 && d3 <= 0.0) {           /* edge ab region */
-    const double t = d1 * (1.0 / aa);
+    const double t = d1 / (d1 - d3);
     for (int d = 0; d < 3; ++d) X[d] = a[d] + t * ab[d];
     w[0] = 1.0 - t; w[1] = t; w[2] = 0.0;
     return;
   }
-  const double d5 = d1 - abac;                          /* ab . (p - c) */
-  const double d6 = d2 - cc;                            /* ac . (p - c) */
+  for (int d = 0; d < 3; ++d) cp[d] = p[d] - c[d];
+  const double d5 = dot3(ab, cp);
+  const double d6 = dot3(ac, cp);
   if (d6 >= 0.0 && d5 <= d6) {                          /* vertex c region */
     for (int d = 0; d < 3; ++d) X[d] = c[d];
     w[0] = 0.0; w[1] = 0.0; w[2] = 1.0;
@@ -205,20 +201,19 @@ void orc_closest_point(const double p[3], const double a[3], const double b[3], 
   }
   const double vb = d5 * d2 - d1 * d6;
   if (vb <= 0.0 && d2 >= 0.0 && d6 <= 0.0) {           /* edge ac region */
-    const double t = d2 * (1.0 / cc);
+    const double t = d2 / (d2 - d6);
     for (int d = 0; d < 3; ++d) X[d] = a[d] + t * ac[d];
     w[0] = 1.0 - t; w[1] = 0.0; w[2] = t;
     return;
   }
   const double va = d3 * d6 - d5 * d4;
-  const double e43 = d4 - d3, e56 = d5 - d6;
-  if (va <= 0.0 && e43 >= 0.0 && e56 >= 0.0) {        /* edge bc region */
-    const double t = e43 * (1.0 / bcbc);
-    for (int d = 0; d < 3; ++d) X[d] = b[d] + t * bc[d];
+  if (va <= 0.0 && (d4 - d3) >= 0.0 && (d5 - d6) >= 0.0) { /* edge bc region */
+    const double t = (d4 - d3) / ((d4 - d3) + (d5 - d6));
+    for (int d = 0; d < 3; ++d) X[d] = b[d] + t * (c[d] - b[d]);
     w[0] = 0.0; w[1] = 1.0 - t; w[2] = t;
     return;
   }
-  const double s = 1.0 / den;                           /* face region */
+  const double s = 1.0 / ((va + vb) + vc);              /* face region */
   const double v = vb * s;
   const double u = vc * s;
   for (int d = 0; d < 3; ++d) X[d] = (a[d] + ab[d] * v) + ac[d] * u;
