@@ -43,13 +43,11 @@ __device__ __forceinline__ void node_pos(const Geo& g, int c, long long i, long 
   x[2] = (c == 2) ? dmul((double)k, g.dz) : dmul(dadd((double)k, 0.5), g.dz);
 }
 
-// Per-triangle constants of the closest-point classification: edge
-// vectors, their scalar products and the reciprocal denominators of the
-// edge and face parameters.
+// Per-triangle data of the closest-point classification: the vertices and
+// edge vectors (each edge formed as the same difference of vertices as in
+// the per-point formulas, so reusing them changes no rounding).
 struct TriConst {
   double a[3], b[3], c[3], ab[3], ac[3], bc[3];
-  double aa, abac, cc;
-  double iaa, icc, ibc, iden;
 };
 
 __device__ inline void tri_const(const double a[3], const double b[3], const double c[3], TriConst& T) {
@@ -62,15 +60,6 @@ __device__ inline void tri_const(const double a[3], const double b[3], const dou
     T.ac[d] = dsub(c[d], a[d]);
     T.bc[d] = dsub(c[d], b[d]);
   }
-  T.aa = ddot(T.ab, T.ab);
-  T.abac = ddot(T.ab, T.ac);
-  T.cc = ddot(T.ac, T.ac);
-  const double bcbc = ddot(T.bc, T.bc);
-  const double den = dsub(dmul(T.aa, T.cc), dmul(T.abac, T.abac));
-  T.iaa = ddiv(1.0, T.aa);
-  T.icc = ddiv(1.0, T.cc);
-  T.ibc = ddiv(1.0, bcbc);
-  T.iden = ddiv(1.0, den);
 }
 
 // FP32 copy of a triangle's constants for the tagging pre-screen, in
@@ -101,11 +90,14 @@ struct TriRec {
 };
 
 // Closest point X on the triangle to p with barycentric weights (Ericson
-// 2004, Voronoi regions: three vertex regions, three edge regions, the
-// face), the six classifying scalar products formed from two per-point
-// products and the per-triangle constants.  Exact-rounding FP64.
+// 2004, cited by Algorithm 1; Voronoi regions: three vertex regions, three
+// edge regions, the face).  The textbook quantities in the textbook order:
+// the six scalar products of the edge vectors with p - a, p - b and p - c,
+// each from its own difference vector, and the edge and face parameters as
+// quotients of those products.  Exact-rounding FP64 (no contraction), so the
+// result is the IEEE-754 value of these formulas bit for bit.
 __device__ inline void closest_point_exact(const double p[3], const TriConst& T, double X[3], double w[3]) {
-  double ap[3];
+  double ap[3], bp[3], cp[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) ap[d] = dsub(p[d], T.a[d]);
   const double d1 = ddot(T.ab, ap), d2 = ddot(T.ac, ap);
@@ -115,7 +107,9 @@ __device__ inline void closest_point_exact(const double p[3], const TriConst& T,
     w[0] = 1.0; w[1] = 0.0; w[2] = 0.0;
     return;
   }
-  const double d3 = dsub(d1, T.aa), d4 = dsub(d2, T.abac);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) bp[d] = dsub(p[d], T.b[d]);
+  const double d3 = ddot(T.ab, bp), d4 = ddot(T.ac, bp);
   if (d3 >= 0.0 && d4 <= d3) {
 #pragma unroll
     for (int d = 0; d < 3; ++d) X[d] = T.b[d];
@@ -124,13 +118,15 @@ __device__ inline void closest_point_exact(const double p[3], const TriConst& T,
   }
   const double vc = dsub(dmul(d1, d4), dmul(d3, d2));
   if (vc <= 0.0 && d1 >= 0.0 && d3 <= 0.0) {
-    const double t = dmul(d1, T.iaa);
+    const double t = ddiv(d1, dsub(d1, d3));
 #pragma unroll
     for (int d = 0; d < 3; ++d) X[d] = dadd(T.a[d], dmul(t, T.ab[d]));
     w[0] = dsub(1.0, t); w[1] = t; w[2] = 0.0;
     return;
   }
-  const double d5 = dsub(d1, T.abac), d6 = dsub(d2, T.cc);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) cp[d] = dsub(p[d], T.c[d]);
+  const double d5 = ddot(T.ab, cp), d6 = ddot(T.ac, cp);
   if (d6 >= 0.0 && d5 <= d6) {
 #pragma unroll
     for (int d = 0; d < 3; ++d) X[d] = T.c[d];
@@ -139,7 +135,7 @@ __device__ inline void closest_point_exact(const double p[3], const TriConst& T,
   }
   const double vb = dsub(dmul(d5, d2), dmul(d1, d6));
   if (vb <= 0.0 && d2 >= 0.0 && d6 <= 0.0) {
-    const double t = dmul(d2, T.icc);
+    const double t = ddiv(d2, dsub(d2, d6));
 #pragma unroll
     for (int d = 0; d < 3; ++d) X[d] = dadd(T.a[d], dmul(t, T.ac[d]));
     w[0] = dsub(1.0, t); w[1] = 0.0; w[2] = t;
@@ -148,13 +144,14 @@ __device__ inline void closest_point_exact(const double p[3], const TriConst& T,
   const double va = dsub(dmul(d3, d6), dmul(d5, d4));
   const double e43 = dsub(d4, d3), e56 = dsub(d5, d6);
   if (va <= 0.0 && e43 >= 0.0 && e56 >= 0.0) {
-    const double t = dmul(e43, T.ibc);
+    const double t = ddiv(e43, dadd(e43, e56));
 #pragma unroll
     for (int d = 0; d < 3; ++d) X[d] = dadd(T.b[d], dmul(t, T.bc[d]));
     w[0] = 0.0; w[1] = dsub(1.0, t); w[2] = t;
     return;
   }
-  const double v = dmul(vb, T.iden), u = dmul(vc, T.iden);
+  const double s = ddiv(1.0, dadd(dadd(va, vb), vc));
+  const double v = dmul(vb, s), u = dmul(vc, s);
 #pragma unroll
   for (int d = 0; d < 3; ++d) X[d] = dadd(dadd(T.a[d], dmul(T.ab[d], v)), dmul(T.ac[d], u));
   w[0] = dsub(dsub(1.0, v), u); w[1] = v; w[2] = u;

@@ -118,11 +118,15 @@ __device__ __forceinline__ void tri_setup(const Blk& bk, const Geo& g, const Sur
   }
   // FP32 screen: skinny or large triangles and strongly anisotropic cells
   // (where its error bound does not hold) skip it
-  const double den = dsub(dmul(TC.aa, TC.cc), dmul(TC.abac, TC.abac));
+  // (the screen's constants: scalar products of the edge vectors and the
+  // reciprocal denominators of its edge and face parameters)
+  const double aa = ddot(TC.ab, TC.ab), abac = ddot(TC.ab, TC.ac), cc = ddot(TC.ac, TC.ac);
+  const double bcbc = ddot(TC.bc, TC.bc);
+  const double den = dsub(dmul(aa, cc), dmul(abac, abac));
   const double dmin = fmin(del[0], fmin(del[1], del[2])), dmax = fmax(del[0], fmax(del[1], del[2]));
-  const double lmax2 = fmax(TC.aa, fmax(TC.cc, dadd(dsub(TC.aa, 2.0 * TC.abac), TC.cc)));
+  const double lmax2 = fmax(aa, fmax(cc, bcbc));
   // (its bounds assume the uniform lattice: off on the non-uniform grid)
-  R.screen = !g.yt.yc && den > 0.05 * TC.aa * TC.cc && lmax2 <= 64.0 * dmin * dmin && dmax <= 4.0 * dmin &&
+  R.screen = !g.yt.yc && den > 0.05 * aa * cc && lmax2 <= 64.0 * dmin * dmin && dmax <= 4.0 * dmin &&
              total < (1ll << 30);
   TriF32& F = R.f;
 #pragma unroll
@@ -139,13 +143,13 @@ __device__ __forceinline__ void tri_setup(const Blk& bk, const Geo& g, const Sur
       F.fr[d][hf] = (float)(A[d] - (q + off) * del[d]);
     }
   }
-  F.aa = (float)TC.aa;
-  F.abac = (float)TC.abac;
-  F.cc = (float)TC.cc;
-  F.iaa = (float)TC.iaa;
-  F.icc = (float)TC.icc;
-  F.ibc = (float)TC.ibc;
-  F.iden = (float)TC.iden;
+  F.aa = (float)aa;
+  F.abac = (float)abac;
+  F.cc = (float)cc;
+  F.iaa = (float)(1.0 / aa);
+  F.icc = (float)(1.0 / cc);
+  F.ibc = (float)(1.0 / bcbc);
+  F.iden = (float)(1.0 / den);
   F.diag2 = (float)g.diag2;
   s.rec[t] = R;
 }
