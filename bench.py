@@ -237,6 +237,20 @@ def tag_pairs(wl, step: int) -> int:
     return total
 
 
+# Plain Thomas per wavenumber (Eq. elliptic after the x and z transforms):
+# forward y_j = (r_j - a y_{j-1}) / d_j, one multiply-add and one multiply
+# (3 flops), backward x_j = y_j - c'_j x_{j+1}, one multiply-add (2 flops),
+# for the real and the imaginary part of every (kx, kz, j).
+TRI_FLOPS_PER_ROW = 10.0
+# Algorithmic bytes of the Thomas pass per (kx, kz, j): read and write the
+# complex spectrum (FP32 pairs in the mixed path, FP64 in the FP64 path).
+TRI_BYTES_PER_ROW = {"mixed": 16.0, "fp64": 32.0}
+# Algorithmic bytes per cell of one whole step (two RK2 sub-stages), the
+# planned compulsory traffic of every stage: 224 B per sub-stage in the
+# mixed path (FP32 words, FP64 Thomas), 432 B in the FP64 path.
+STEP_BYTES_PER_CELL = {"mixed": 448.0, "fp64": 864.0}
+
+
 def fp64_flops_per_cell(stage: str) -> float:
     """FP64 floating-point operations per cell of each kernel group in the
     FP64 path (adds, multiplies and FMAs counted as executed instructions x
@@ -260,6 +274,8 @@ def gpu_arm(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
+    if args.fp64_peak_tflops <= 0:
+        args.fp64_peak_tflops, args.fp32_peak_tflops = ibm.ibm_measure_alu_peaks()
     wl = inputs.heaving_plate()
     K, W = args.steps, args.warmup
     nsteps_total = W + K
@@ -343,37 +359,71 @@ def gpu_arm(args):
     h2d = 2 * surf[0][0].nbytes
     peaks = measured_peaks()
     prof = head["prof"]
-    # roofline of every kernel group of the headline path; the dominant one is reported
+    # roofline of every kernel group of the headline path; the kernel with the
+    # most device time per step is reported (stages that run the same kernel,
+    # such as the Thomas passes of the first and the correction solve, summed)
+    fp64_peak = args.fp64_peak_tflops
     pairs = tag_pairs(wl, W)
+    nrows = (wl.nx // 2 + 1) * wl.nz * wl.ny
+    hbm = peaks.get("hbm_gbs", 6800.0)
     groups = {}
+    tune_h = head["tune"] or {}
+    plane = tune_h.get("fft_plane", 0) == 2
+    merged = {"tri_y": ("tri_y", "correction_tri")}
+    if plane:
+        merged["fft_x_fwd"] = ("fft_x_fwd", "correction")
+        merged["fft_x_inv"] = ("fft_x_inv", "correction_inv")
+    skip = {s2 for k, v in merged.items() for s2 in v if s2 != k}
     for name, (tot_ms, ngroups) in prof.items():
-        if name == "other" or ngroups == 0 or tot_ms <= 0:
+        if name in ("other",) or name in skip or ngroups == 0 or tot_ms <= 0:
             continue
-        launches = ngroups * args.profile_steps
-        avg_ms = tot_ms / launches
+        stages = merged.get(name, (name,))
+        tot = sum(prof[s2][0] for s2 in stages if s2 in prof)
+        launches = sum(prof[s2][1] for s2 in stages if s2 in prof) * args.profile_steps
+        avg_ms = tot / launches
+        per_step_ms = tot / args.profile_steps
         if name == "tagging":
             work = pairs * TAG_FLOPS_PER_PAIR
-            groups[name] = dict(bound="alu", achieved=work / (avg_ms / 1e3) / 1e12, peak=args.fp64_peak_tflops,
-                                unit="TFLOP/s", avg_ms=avg_ms, share=tot_ms)
+            g = dict(bound="alu", achieved=work / (avg_ms / 1e3) / 1e12, peak=fp64_peak, unit="TFLOP/s")
+        elif name == "tri_y":
+            fl = TRI_FLOPS_PER_ROW * nrows / (avg_ms / 1e3) / 1e12
+            by = TRI_BYTES_PER_ROW[args.precision] * nrows / (avg_ms / 1e3) / 1e9
+            g = dict(bound="alu", achieved=fl, peak=fp64_peak, unit="TFLOP/s",
+                     hbm={"achieved": by, "peak": hbm, "frac": by / hbm})
+            if by / hbm > fl / fp64_peak:
+                g = dict(bound="hbm", achieved=by, peak=hbm, unit="GB/s", alu={"achieved": fl, "peak": fp64_peak,
+                                                                               "frac": fl / fp64_peak})
         elif args.precision == "fp64" and fp64_flops_per_cell(name) > 0:
             work = fp64_flops_per_cell(name) * cells
-            groups[name] = dict(bound="alu", achieved=work / (avg_ms / 1e3) / 1e12, peak=args.fp64_peak_tflops,
-                                unit="TFLOP/s", avg_ms=avg_ms, share=tot_ms)
+            g = dict(bound="alu", achieved=work / (avg_ms / 1e3) / 1e12, peak=fp64_peak, unit="TFLOP/s")
         elif algorithmic_bytes_per_cell(name, 4) > 0:
             work = algorithmic_bytes_per_cell(name, 4) * cells
-            groups[name] = dict(bound="hbm", achieved=work / (avg_ms / 1e3) / 1e9, peak=peaks.get("hbm_gbs", 6800.0),
-                                unit="GB/s", avg_ms=avg_ms, share=tot_ms)
-    tot_all = sum(g["share"] for g in groups.values())
-    for g in groups.values():
+            g = dict(bound="hbm", achieved=work / (avg_ms / 1e3) / 1e9, peak=hbm, unit="GB/s")
+        else:
+            continue
+        g.update(avg_ms=avg_ms, ms_per_step=per_step_ms, launches_per_step=launches / args.profile_steps,
+                 stages=list(stages))
         g["frac"] = g["achieved"] / g["peak"] if g["peak"] else None
-        g["share"] = g["share"] / tot_all
-    top = max(groups, key=lambda k: groups[k]["share"])
+        groups[name] = g
+    tot_all = sum(g["ms_per_step"] for g in groups.values())
+    for g in groups.values():
+        g["share"] = g["ms_per_step"] / tot_all
+    top = max(groups, key=lambda k: groups[k]["ms_per_step"])
     tg = groups[top]
     kname = stage_kernel(top, head["tune"], args.precision, wl.ny)
     roof = {"bound": tg["bound"], "achieved": tg["achieved"], "peak": tg["peak"], "unit": tg["unit"],
             "frac": tg["frac"], "traffic": ncu_traffic(top, kname), "kernel": top, "kernel_name": kname,
-            "peak_source": ("FP64 FMA-chain probe on a GB300 of this pool (of measured)" if tg["bound"] == "alu"
-                            else "MEASURED_PEAKS.json hbm_gbs (of measured)")}
+            "ms_per_step": tg["ms_per_step"], "launches_per_step": tg["launches_per_step"],
+            "peak_source": ("FP64 FMA-chain probe ibm_measure_alu_peaks, this run (of measured)"
+                            if tg["bound"] == "alu" else "MEASURED_PEAKS.json hbm_gbs (of measured)")}
+    for k in ("hbm", "alu"):
+        if k in tg:
+            roof[k] = tg[k]
+    step_bytes = STEP_BYTES_PER_CELL[args.precision] * cells
+    step_ach = step_bytes / (head["ms"] / K / 1e3) / 1e9
+    step_roof = {"bound": "hbm", "bytes_per_cell": STEP_BYTES_PER_CELL[args.precision], "achieved": step_ach,
+                 "peak": hbm, "unit": "GB/s", "frac": step_ach / hbm,
+                 "roof_gcups": hbm * 1e9 / STEP_BYTES_PER_CELL[args.precision] / 1e9}
     kernels_per_step = head["diag"]["kernels_per_step"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
@@ -384,6 +434,9 @@ def gpu_arm(args):
                    "precision": args.precision, "parallelism": f"replicas x{world}",
                    "l2": "flushed between timed steps (256 MiB write outside the events)"},
         "roofline": roof,
+        "step_roofline": step_roof,
+        "alu_peaks": {"fp64_tflops": args.fp64_peak_tflops, "fp32_tflops": args.fp32_peak_tflops,
+                      "source": "ibm_measure_alu_peaks (FMA chains, CUDA events), this run"},
         "gpu_launches": (kernels_per_step + 2) * K,
         "clocks": head["clocks"],
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": head["d2h"]},
@@ -394,15 +447,17 @@ def gpu_arm(args):
         "tag_pairs_per_step": pairs,
     }
     for prec, r in results.items():
+        dg = r["diag"]
         line[prec] = {"value": world * cells * K / (r["ms"] / 1e3) / 1e9, "ms_per_step": r["ms"] / K,
-                      "slip_l1": r["diag"]["slip_l1"], "clocks": r["clocks"], "tune": r["tune"]}
+                      "slip_l1": dg["slip_l1"], "clocks": r["clocks"], "tune": r["tune"],
+                      "div_max_U_per_dx": dg["div_max"] * wl.lx / wl.nx, "ke": dg["ke"], "cfl": dg["cfl"]}
     if batched is not None:
         line["batched"] = batched
     if ab is not None:
         line["ab_cn"] = ab
     if stretched is not None:
         line["stretched"] = stretched
-    if args.large and world == 1:
+    if not args.no_large and world == 1:
         line["large"] = large_leg(args, dev, stream, flush)
     if args.e5_steps > 0:
         line["e5_heaving_pitching_plate"] = e5_leg(args, dev, stream)
@@ -412,6 +467,8 @@ def gpu_arm(args):
         line["speedup_mixed_vs_fp64"] = line["mixed"]["value"] / line["fp64"]["value"]
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_steps)
+        if not args.no_large:
+            line["cpu_baseline_extra"] = cpu_baseline_extra()
     return line
 
 
@@ -523,12 +580,15 @@ def stretched_run(args, dev, stream, flush, world, wall, precision):
 
 
 def large_leg(args, dev, stream, flush):
-    """Mixed path on the two large synthetic workloads (256x192x256 channel
-    with 16 moving bodies; 512x384x512 tube with three hinged leaflets):
-    same protocol as the headline (device-resident surfaces, L2 flushed
-    between timed steps, autotuned launch shapes), with the stage times.
-    The tube's pulsatile body force is held at its t = 0 value (the rate
-    does not depend on it)."""
+    """The two large synthetic workloads of the metric's family -- the
+    256x192x256 channel with 16 moving bodies and the 512x384x512 tube with
+    three hinged leaflets -- on the mixed path, same protocol as the headline
+    (device-resident surfaces, L2 flushed between timed steps, autotuned
+    launch shapes), with the stage times and the device's own divergence
+    residual.  The tube also runs the FP64 path on the same inputs and steps,
+    and reports the largest difference of the mixed fields from it (velocity
+    over U_ref, pressure over U_ref^2).  The tube's pulsatile body force is
+    held at its t = 0 value (the rate does not depend on it)."""
     import torch
     from paper_2606_09799_gb300 import ibm, inputs
 
@@ -539,36 +599,106 @@ def large_leg(args, dev, stream, flush):
         surf = [wl.surface(s) for s in range(W + K)]
         dx = [torch.from_numpy(x).to(dev) for x, _ in surf]
         dv = [torch.from_numpy(v).to(dev) for _, v in surf]
-        sim = ibm.Simulation(wl.nx, wl.ny, wl.nz, wl.lx, wl.ly, wl.lz, re=wl.re, dt=wl.dt, precision="mixed",
-                             stream=stream.cuda_stream)
-        if wl.initial is not None:
-            sim.set_fields(*wl.initial())
-        ibm.ibm_set_body_force(sim.h, *wl.body_force_at(0.0))
-        sim.set_surface(surf[0][0], surf[0][1], wl.tri)
-        for s in range(W):
-            sim.set_surface(dx[s], dv[s])
-            sim.step(1)
-        sim.sync()
-        tune = sim.autotune(steps=2)
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-        torch.cuda.synchronize()
-        for n in range(K):
-            flush.fill_(n & 0xFF)
-            ev[n][0].record(stream)
-            sim.set_surface(dx[W + n], dv[W + n])
-            sim.step(1)
-            ev[n][1].record(stream)
-        torch.cuda.synchronize()
-        ms = sum(a.elapsed_time(b) for a, b in ev) / K
-        prof = ibm.ibm_profile_stages(sim.h, 2)
         cells = wl.nx * wl.ny * wl.nz
-        out[name] = {"cells": cells, "triangles": int(wl.tri.shape[0]), "steps": K, "ms_per_step": ms,
-                     "value": cells / (ms / 1e3) / 1e9, "unit": UNIT, "tune": tune,
-                     "stages_ms_per_step": {k: v[0] / 2 for k, v in prof.items() if v[1] > 0},
-                     "slip_l1": sim.diag()["slip_l1"]}
-        sim.close()
+        precs = ("mixed", "fp64") if name == "leaflet512" else ("mixed",)
+        res = {}
+        fields = {}
+        for prec in precs:
+            sim = ibm.Simulation(wl.nx, wl.ny, wl.nz, wl.lx, wl.ly, wl.lz, re=wl.re, dt=wl.dt, precision=prec,
+                                 stream=stream.cuda_stream)
+            if wl.initial is not None:
+                sim.set_fields(*wl.initial())
+            ibm.ibm_set_body_force(sim.h, *wl.body_force_at(0.0))
+            sim.set_surface(surf[0][0], surf[0][1], wl.tri)
+            for s in range(W):
+                sim.set_surface(dx[s], dv[s])
+                sim.step(1)
+            sim.sync()
+            tune = sim.autotune(steps=2) if prec == "mixed" else None   # state saved and restored
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+            torch.cuda.synchronize()
+            for n in range(K):
+                flush.fill_(n & 0xFF)
+                ev[n][0].record(stream)
+                sim.set_surface(dx[W + n], dv[W + n])
+                sim.step(1)
+                ev[n][1].record(stream)
+            torch.cuda.synchronize()
+            ms = sum(a.elapsed_time(b) for a, b in ev) / K
+            d = sim.diag()
+            r = {"precision": prec, "cells": cells, "triangles": int(wl.tri.shape[0]), "steps": K, "warmup": W,
+                 "ms_per_step": ms, "value": cells / (ms / 1e3) / 1e9, "unit": UNIT, "slip_l1": d["slip_l1"],
+                 "div_max_U_per_dx": d["div_max"] * wl.lx / wl.nx, "cfl": d["cfl"]}
+            if len(precs) > 1:
+                # the state after the same W + K steps on both paths
+                shp = [(wl.nz, wl.ny, wl.nx), (wl.nz, wl.ny + 1, wl.nx), (wl.nz, wl.ny, wl.nx), (wl.nz, wl.ny, wl.nx)]
+                f = tuple(torch.empty(sh, dtype=torch.float64, device=dev) for sh in shp)
+                ibm.ibm_get_fields(sim.h, wl.nx, wl.ny, wl.nz, out=f)
+                fields[prec] = f
+            if prec == "mixed":
+                prof = ibm.ibm_profile_stages(sim.h, 2)   # two more steps, after the fields were taken
+                r["tune"] = tune
+                r["stages_ms_per_step"] = {k: v[0] / 2 for k, v in prof.items() if v[1] > 0}
+            sim.close()
+            res[prec] = r
+        entry = dict(res["mixed"])
+        if "fp64" in res:
+            fm, ff = fields["mixed"], fields["fp64"]
+            entry["fp64_gpu"] = res["fp64"]
+            entry["vs_fp64_gpu"] = {
+                "max_abs_du": max(float((a - b).abs().max()) for a, b in zip(fm[:3], ff[:3])),
+                "max_abs_dp": float((fm[3] - ff[3]).abs().max()),
+                "max_abs_u": max(float(b.abs().max()) for b in ff[:3]),
+                "after_steps": W + K,
+                "slip_rel_diff": (abs(res["mixed"]["slip_l1"] - res["fp64"]["slip_l1"]) / res["fp64"]["slip_l1"]
+                                  if res["fp64"]["slip_l1"] else None)}
+            del fm, ff
+        fields.clear()
+        out[name] = entry
         del dx, dv
         torch.cuda.empty_cache()
+    return out
+
+
+def cpu_baseline_extra():
+    """The oracle's other timings: one thread on the 64^3 oscillating sphere
+    (all 10 steps), and all host cores on the 256x192x256 channel with 16
+    bodies (2 whole steps, reported per step as cell updates/s)."""
+    from oracle import oracle as orc
+    from oracle.oracle import OracleSim
+    from paper_2606_09799_gb300 import inputs
+    out = {}
+    wl = inputs.oscillating_sphere()
+    ncores = orc.threads()
+    orc.set_threads(1)
+    try:
+        sim = OracleSim(wl.nx, wl.ny, wl.nz, wl.lx, wl.ly, wl.lz, re=wl.re, dt=wl.dt)
+        t0 = time.perf_counter()
+        for s in range(10):
+            xyz, vel = wl.surface(s)
+            sim.set_surface(xyz, vel, wl.tri)
+            sim.step()
+        dt = time.perf_counter() - t0
+    finally:
+        orc.set_threads(ncores)
+    out["sphere64_one_thread"] = {"value": wl.cells * 10 / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                  "sample": "10 whole time steps of the 64^3 oscillating sphere (FP64)",
+                                  "seconds": dt}
+    wl = inputs.workload("channel256")
+    sim = OracleSim(wl.nx, wl.ny, wl.nz, wl.lx, wl.ly, wl.lz, re=wl.re, dt=wl.dt)
+    if wl.initial is not None:
+        sim.set_fields(*wl.initial())
+    sim.set_body_force(*wl.body_force_at(0.0))
+    t0 = time.perf_counter()
+    for s in range(2):
+        xyz, vel = wl.surface(s)
+        sim.set_surface(xyz, vel, wl.tri)
+        sim.step()
+    dt = time.perf_counter() - t0
+    cells = wl.nx * wl.ny * wl.nz
+    out["channel256"] = {"value": cells * 2 / dt / 1e9, "unit": UNIT, "cores": ncores, "kind": "oracle",
+                         "sample": "2 whole time steps of the 256x192x256 channel with 16 moving bodies (FP64)",
+                         "seconds_per_step": dt / 2}
     return out
 
 
@@ -760,16 +890,17 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-instances leg")
     ap.add_argument("--no-ab", action="store_true", help="skip the AB+CN leg")
     ap.add_argument("--no-stretched", action="store_true", help="skip the non-uniform wall-normal grid leg")
-    ap.add_argument("--large", action="store_true",
-                    help="also time the 256x192x256 channel and the 512x384x512 tube (mixed path)")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the 256x192x256 channel and 512x384x512 tube leg (and the oracle's extra timings)")
     ap.add_argument("--e5-steps", type=int, default=0,
                     help="also record the no-slip error series of the heaving/pitching plate (opt-in)")
     ap.add_argument("--tune", default="", help="fixed launch shapes instead of autotuning, e.g. tri_y=3,sweep_zy=2")
     ap.add_argument("--batch-steps", type=int, default=20)
-    ap.add_argument("--fp64-peak-tflops", type=float, default=1.0,
-                    help="measured FP64 FMA throughput of this GB300")
+    ap.add_argument("--fp64-peak-tflops", type=float, default=0.0,
+                    help="FP64 roof in TFLOP/s; 0 (default) measures it on the device (ibm_measure_alu_peaks)")
     args = ap.parse_args()
     args.tune = {k: int(v) for k, v in (kv.split("=") for kv in args.tune.split(",") if kv)}
+    args.fp32_peak_tflops = None
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     line = reference_arm(args) if args.impl == "reference" else gpu_arm(args)

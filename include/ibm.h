@@ -67,7 +67,11 @@ typedef enum {
   IBM_ERR_DIVERGED = 5,  /* non-finite values in the solution */
   IBM_ERR_TIMEOUT = 6,   /* a bounded device wait gave up */
   IBM_ERR_STATE = 7,     /* call not valid in the handle's current state */
-  IBM_ERR_CAPACITY = 8   /* a device work list overflowed; the step must be redone */
+  IBM_ERR_CAPACITY = 8   /* a capacity was exceeded.  From ibm_step's synchronising calls: a
+                            device work list overflowed; its capacity has been grown, and the step
+                            must be redone.  From ibm_tag_noalloc: the grid needs more than the
+                            library's fixed array holds (IBM_NOALLOC_MAX_NODES); retrying cannot
+                            succeed */
 } ibm_status;
 
 enum { IBM_RK2_CN = 0, IBM_AB_CN = 1 };   /* time schemes, Section 2 */
@@ -108,6 +112,13 @@ typedef struct {
   int64_t ncandidates;    /* (node, triangle) pairs that passed Algorithm 1 in the last step */
   int64_t kernels_per_step; /* GPU kernels one ibm_step launches (nodes of its CUDA graph) */
   int64_t d2h_bytes;      /* bytes this ibm_get_diag call copied from the device */
+  double div_max;         /* max over the fluid cells C_F of |D u - q| after the step's last projection
+                             (Eq. mod_div: the projected field satisfies D u = q; every cell when use_q = 0);
+                             the mixed paths form D u in (hi, lo) pair arithmetic */
+  double ke;              /* kinetic energy 1/2 sum u^2 dV over the velocity nodes of the three grids
+                             (dV = dx h dz, h the cell height for u and w, the centre distance for v) */
+  double cfl;             /* dt max over the cells of |u_c|/dx + |v_c|/h + |w_c|/dz, u_c the mean of the
+                             cell's two faces of each component (the step's result) */
 } ibm_diag;
 
 /* Create a simulation on the current CUDA device.  stream is a cudaStream_t
@@ -156,9 +167,24 @@ ibm_status ibm_set_surface(ibm_handle h, int nverts, const double* xyz, const do
 ibm_status ibm_set_body_force(ibm_handle h, double fx, double fy, double fz);
 
 /* Overwrite the state u, v, w, p (layouts above; v's wall planes are taken
- * as given).  The non-linear history H^{n-1} of AB+CN is reset to zero. */
+ * as given).  The non-linear history H^{n-1} of AB+CN is reset to zero (a
+ * restart from rest); ibm_set_history afterwards restores a saved one. */
 ibm_status ibm_set_fields(ibm_handle h, const double* u, const double* v, const double* w, const double* p,
                           int on_device);
+
+/* The non-linear history that AB+CN carries from step n to step n+1: the
+ * explicit terms H^n of Eq. NS_prov (advection of the step's state, one per
+ * velocity component, on that component's grid: hu and hw nz*ny*nx, hv
+ * nz*(ny+1)*nx, FP64, layouts as the fields).  With ibm_get_fields and
+ * ibm_set_fields it makes the whole state of a simulation: a run saved after
+ * step n and restored into a new handle (fields, then history, then the
+ * surface of step n+1) continues as the original would, bit for bit in
+ * FP64.  RK2+CN carries no history across steps (its first sub-stage has
+ * rho = 0); the calls then copy the first sub-stage's terms, which the next
+ * step overwrites.  In the mixed paths H is FP32 and converts exactly.
+ * ibm_get_history synchronises the stream; any pointer may be NULL. */
+ibm_status ibm_get_history(ibm_handle h, double* hu, double* hv, double* hw, int on_device);
+ibm_status ibm_set_history(ibm_handle h, const double* hu, const double* hv, const double* hw, int on_device);
 
 /* Advance nsteps time steps with the current surface (asynchronous). */
 ibm_status ibm_step(ibm_handle h, int nsteps);
@@ -193,7 +219,7 @@ ibm_status ibm_set_allocator(ibm_alloc_fn alloc, ibm_free_fn free_fn, void* ctx)
  * event records between its kernel groups, and returns per group the total
  * device milliseconds in ms[IBM_NSTAGES] and the number of kernels in
  * kernels[IBM_NSTAGES] (either may be NULL).  Synchronises. */
-#define IBM_NSTAGES 16
+#define IBM_NSTAGES 19
 ibm_status ibm_profile_stages(ibm_handle h, int nsteps, double* ms, int64_t* kernels);
 
 /* Name of kernel group `stage` (0 <= stage < IBM_NSTAGES), else "". */
@@ -206,8 +232,11 @@ const char* ibm_stage_name(int stage);
  * allocator's callback, or a time-critical loop that may not block on the
  * allocator's implicit synchronisation.  It computes the forcing-node owners
  * of Algorithm 1 for one surface on the three staggered grids, bit for bit
- * the tags that ibm_step followed by ibm_get_tags gives for the same grid
- * and surface, without a handle.
+ * the tags that ibm_step followed by ibm_get_tags gives for the same surface
+ * on a handle made by ibm_create_grid with the same sizes, box and wall
+ * condition (uniform spacing in every direction: this call knows nothing of
+ * the non-uniform wall-normal rows of ibm_create_grid_stretched), without a
+ * handle.
  *
  * All array arguments are device pointers owned by the caller: xyz (3*nverts
  * FP64 vertex positions), tri (3*ntris int32 vertex indices) and the outputs
@@ -219,9 +248,10 @@ const char* ibm_stage_name(int stage);
  * IBM_NOALLOC_MAX_NODES nodes of the three grids together (8 MiB of device
  * memory, held on every GPU that loads the library until the process
  * exits); larger grids are rejected with IBM_ERR_CAPACITY before any work.
- * The first call on a device resolves the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  Every call shares the one array: calls that overlap on the GPU
+ * Every call resolves the array's device address on the current device (a
+ * host-side lookup, so a device reset never leaves a stale address); the
+ * first call on a device may load the library's device code there, so make
+ * it before any stream capture.  Every call shares the one array: calls that overlap on the GPU
  * (on different streams, or from different threads) race and give wrong
  * tags.  The call clears what it uses, runs on `stream`, and waits for it.
  * Returns IBM_ERR_ARG for bad sizes or pointers, or when a triangle names a
@@ -363,6 +393,15 @@ ibm_status ibm_check_conversions(long long n, long long* mismatches, long long* 
  * synchronises the device.  IBM_ERR_ARG for a limit out of range or null
  * outputs. */
 ibm_status ibm_check_bounded_wait(long long limit_cycles, int* timed_out, long long* waited_cycles);
+
+/* Arithmetic roofs of the current device (no counterpart in the paper):
+ * the FP64 and FP32 fused multiply-add throughput in TFLOP/s (an FMA counts
+ * two flops), measured by a kernel whose every thread runs eight
+ * independent FMA chains on every SM, timed with CUDA events after an
+ * untimed launch (~20 ms per type).  The benchmark reports FP64-bound
+ * kernels against *fp64_tflops.  Allocates 16 bytes on the device;
+ * synchronises the device. */
+ibm_status ibm_measure_alu_peaks(double* fp64_tflops, double* fp32_tflops);
 
 /* Library version string. */
 const char* ibm_version(void);

@@ -56,6 +56,16 @@ int orc_threads(void) {
 #endif
 }
 
+/* Threads of the OpenMP loops from now on (the timing of the oracle on one
+ * core); n < 1 leaves the setting unchanged. */
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n >= 1) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
 void orc_grid_init(orc_grid* g, int nx, int ny, int nz, double lx, double ly, double lz, int ybc) {
   g->nx = nx; g->ny = ny; g->nz = nz; g->ybc = ybc;
   g->lx = lx; g->ly = ly; g->lz = lz;

@@ -76,6 +76,7 @@ def lib():
             build()
             L = ctypes.CDLL(_SO)
             L.orc_threads.restype = _I
+            L.orc_set_threads.argtypes = [_I]
             L.orc_grid_init.argtypes = [_GP, _I, _I, _I, _D, _D, _D, _I]
             L.orc_closest_point.argtypes = [_P] * 6
             L.orc_tag_alg1.argtypes = [_GP, _I, _P, _I, _P, _P, _P]
@@ -108,6 +109,11 @@ def _p(a: np.ndarray):
 
 def threads() -> int:
     return int(lib().orc_threads())
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's OpenMP loops from now on."""
+    lib().orc_set_threads(int(n))
 
 
 def make_grid(nx, ny, nz, lx=1.0, ly=1.0, lz=1.0, ybc=0, yfaces=None) -> Grid:
@@ -275,6 +281,47 @@ def pressure_recon(g: Grid, p, isb, owners, xyz, tri):
     return q
 
 
+def row_heights(g: Grid):
+    """Wall-normal cell heights h_c(j) (ny) and centre distances across the
+    faces h_f(j) (ny; face j = 0 is the wall, measured to the mirror image of
+    the first centre) of the grid, uniform or not."""
+    if g.yf:
+        yf = g._yf_array
+        hc = np.diff(yf)
+        yc = 0.5 * (yf[:-1] + yf[1:])
+        hf = np.empty(g.ny)
+        hf[0] = 2.0 * yc[0]
+        hf[1:] = np.diff(yc)
+        return hc, hf
+    return np.full(g.ny, g.dy), np.full(g.ny, g.dy)
+
+
+def state_diagnostics(g: Grid, u, v, w, q, fluid, dt):
+    """Diagnostics of a velocity state (no counterpart in the method's
+    steps; they measure its result):
+      div_max = max over the cells where `fluid` holds of |D u - q|, the
+                residual of Eq. mod_div (the projected field has D u = q);
+      ke      = 1/2 sum over the velocity nodes of the three grids of
+                u^2 dV, dV the node's control volume (dx h dz, h the cell
+                height for u and w, the distance of the centres for v; the
+                wall planes of v hold no unknown and are left out);
+      cfl     = dt max over the cells of |u_c|/dx + |v_c|/h + |w_c|/dz with
+                u_c the mean of the cell's two faces of each component.
+    q: scalar or per-cell array; fluid: boolean mask of the cells (nz, ny, nx)."""
+    hc, hf = row_heights(g)
+    div = divergence(g, u, v, w)
+    r = np.abs(div - q)
+    div_max = float(r[fluid].max()) if np.any(fluid) else 0.0
+    hcb = hc[None, :, None]
+    ke = 0.5 * g.dx * g.dz * (np.sum(u * u * hcb) + np.sum(v[:, :g.ny, :] ** 2 * hf[None, :, None])
+                               + np.sum(w * w * hcb))
+    uc = 0.5 * np.abs(u + np.roll(u, -1, axis=2))
+    vc = 0.5 * np.abs(v[:, :-1, :] + v[:, 1:, :])
+    wc = 0.5 * np.abs(w + np.roll(w, -1, axis=0))
+    cfl = dt * float(np.max(uc / g.dx + vc / hcb + wc / g.dz))
+    return div_max, float(ke), cfl
+
+
 def project(g: Grid, u, v, w, p, phi, adt, re):
     lp = lap_c(g, phi)
     lib().orc_project(ctypes.byref(g), _p(u), _p(v), _p(w), _p(p), _p(phi), _p(lp), adt, re)
@@ -395,12 +442,26 @@ class OracleSim:
             tot += m
         return tot / 3.0, per
 
+    def diagnostics(self):
+        """(max |D u - q| over C_F, kinetic energy, CFL) of the current state
+        with the last sub-stage's q: q_F (uniform shape) or the per-cell
+        shape of App. B on the fluid cells; without q, D u = 0 on every cell."""
+        if self.use_q == 2:
+            q = self.last["q_field"]
+        elif self.use_q:
+            q = self.last.get("qF", 0.0)
+        else:
+            q = 0.0
+        fluid = (self.isb == 0) if self.use_q else np.ones((self.g.nz, self.g.ny, self.g.nx), dtype=bool)
+        return state_diagnostics(self.g, self.u, self.v, self.w, q, fluid, self.dt)
+
     def step(self, n: int = 1):
         for _ in range(n):
             self._tag()
             for (gam, rho, alp) in SCHEMES[self.scheme]:
                 self._substage(gam, rho, alp)
             self.nsteps += 1
+            self.last["div_max"], self.last["ke"], self.last["cfl"] = self.diagnostics()
             if self.tri.shape[0]:
                 self.last["slip"], self.last["slip_per_comp"] = self.slip()
         return self

@@ -96,6 +96,9 @@ struct DevState {
   double qa[2], qb[2];           // energy-conserving shape: q_F^k = qa + qb (p^k - e^k) (App. B)
   double sum_qdv[2];             // sum over all cells of q dV
   double slip_sum[3];            // sum |eps_i| of the last step
+  double div_max;                // max over C_F of |D u - q| after the last projection of the step
+  double ke;                     // kinetic energy 1/2 sum u^2 dV of the step's result
+  double cfl;                    // CFL number of the step's result
   unsigned int err;              // ERR_* bits
   unsigned int ncand;            // candidates of the current step
   unsigned int ncand_prev;       // candidates of the previous step (sparse reset)

@@ -30,7 +30,8 @@ inline int reduce_blocks(const Geo& g, long long cells, int hi) { return scaled_
 // of each.  The order matches the stage names in runtime.cu.
 enum StageId {
   ST_TAG = 0, ST_FORCE, ST_RHS, ST_SWEEP_X, ST_SWEEP_Z, ST_SWEEP_Y, ST_QRED, ST_FFT_X_FWD, ST_FFT_Z_FWD,
-  ST_TRI_Y, ST_FFT_Z_INV, ST_FFT_X_INV, ST_PROJECT, ST_SLIP, ST_CORRECT, ST_OTHER, ST_COUNT
+  ST_TRI_Y, ST_FFT_Z_INV, ST_FFT_X_INV, ST_PROJECT, ST_SLIP, ST_CORRECT, ST_DIAG, ST_CORR_TRI, ST_CORR_INV,
+  ST_OTHER, ST_COUNT
 };
 // Record the start of stage `id` on stream st when stage timing is active
 // on this thread (no-op otherwise).  Launchers call Exec::mark.
@@ -156,6 +157,11 @@ struct SpecTables {
 template <typename T>
 void launch_poisson(const Geo& g, const Fields<T>& f, const TagBuffers& b, const SpecTables<T>& tb,
                     const Stage& sg, double dt, double re, int use_q, double* partial, DevState* ds, Exec& ex);
+// State diagnostics of the step after its last projection: max |D u - q| over
+// C_F, kinetic energy and CFL number into the device state (poisson.cu).
+template <typename T>
+void launch_state_diag(const Geo& g, const Fields<T>& f, const TagBuffers& b, int s, int use_q, double dt,
+                       double* partial, DevState* ds, Exec& ex);
 // ---- post-processing (loads.cu) ----------------------------------------------
 template <typename T>
 void launch_loads(const Geo& g, const Surf& s, const Fields<T>& f, const TagBuffers& b, double re, int sides,

@@ -1,10 +1,9 @@
 // noalloc.cu -- tagging of the forcing nodes (Algorithm 1) for callers that
 // must not allocate device memory.  The result is identical, bit for bit, to
-// the tags a simulation handle computes (ibm_step followed by ibm_get_tags);
+// the tags a simulation handle on a uniform grid (ibm_create_grid) computes
+// (ibm_step followed by ibm_get_tags);
 // the working memory lives in a fixed, file-scope device array instead of
 // buffers allocated per handle.
-#include <mutex>
-
 #include "../../include/ibm.h"
 #include "common.cuh"
 #include "geometry.cuh"
@@ -20,27 +19,18 @@ static __device__ __align__(256) unsigned g_noalloc_bad[64];
 
 namespace {
 
-std::mutex g_setup_mu;
-unsigned long long* g_d2_ptr[64];
-unsigned* g_bad_ptr[64];
-bool g_ready[64];
-
-// Device addresses of the working memory on the current device (resolved
-// once per device: host code cannot use the symbols' addresses directly).
-cudaError_t noalloc_setup(int dev, unsigned long long** d2, unsigned** bad) {
-  std::lock_guard<std::mutex> lk(g_setup_mu);
-  if (!g_ready[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_d2);
-    if (e != cudaSuccess) return e;
-    g_d2_ptr[dev] = static_cast<unsigned long long*>(p);
-    e = cudaGetSymbolAddress(&p, g_noalloc_bad);
-    if (e != cudaSuccess) return e;
-    g_bad_ptr[dev] = static_cast<unsigned*>(p);
-    g_ready[dev] = true;
-  }
-  *d2 = g_d2_ptr[dev];
-  *bad = g_bad_ptr[dev];
+// Device addresses of the working memory on the current device.  Host code
+// cannot use the symbols' addresses directly; they are looked up on every
+// call (a host-side query once the library's device code is loaded), so a
+// device reset or a new primary context never leaves a stale address.
+cudaError_t noalloc_setup(unsigned long long** d2, unsigned** bad) {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_d2);
+  if (e != cudaSuccess) return e;
+  *d2 = static_cast<unsigned long long*>(p);
+  e = cudaGetSymbolAddress(&p, g_noalloc_bad);
+  if (e != cudaSuccess) return e;
+  *bad = static_cast<unsigned*>(p);
   return cudaSuccess;
 }
 
@@ -179,11 +169,9 @@ extern "C" ibm_status ibm_tag_noalloc(const ibm_grid_desc* desc, int nverts, con
   g.nvf = (long long)d.nx * (d.ny + 1) * d.nz;
   const long long nall = 2 * g.ncell + g.nvf;
   if (nall > IBM_NOALLOC_MAX_NODES) return IBM_ERR_CAPACITY;
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return IBM_ERR_CUDA;
   unsigned long long* d2 = nullptr;
   unsigned* bad = nullptr;
-  if (noalloc_setup(dev, &d2, &bad) != cudaSuccess) return IBM_ERR_CUDA;
+  if (noalloc_setup(&d2, &bad) != cudaSuccess) return IBM_ERR_CUDA;
   cudaStream_t st = (cudaStream_t)stream;
   // the three owner arrays are cleared one after the other (they need not
   // be contiguous)

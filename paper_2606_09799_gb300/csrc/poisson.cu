@@ -929,73 +929,134 @@ struct FftZ {
 // Neumann rows at both walls; mode (0,0) pins phi_0 = 0 and removes the
 // mean over j afterwards (zero-mean gauge).  Pivots are tabulated.
 // ---------------------------------------------------------------------------
+// FP32 spectrum value -> FP64 on the integer pipes (FP64 spectrum: as is);
+// `special` collects the inputs the integer path leaves to the hardware.
+__device__ __forceinline__ double widen(float v, bool& special) { return f2d_int(v, special); }
+__device__ __forceinline__ double widen(double v, bool&) { return v; }
+__device__ __forceinline__ float narrow_to(float*, double v, bool& special) { return d2f_int(v, special); }
+__device__ __forceinline__ double narrow_to(double*, double v, bool&) { return v; }
+
 template <typename T>
 __device__ __forceinline__ void tri_y(const Blk& bk, const Geo& g, const Fields<T>& f, const double* __restrict__ cp,
                                                const double* __restrict__ inv, double* fwd) {
   // one thread per real or imaginary part of a (kx, kz) system: the two
-  // share the pivots and are independent
-  const int nkx = g.nkx;
+  // share the pivots and are independent.  Only the recurrences use the FP64
+  // pipe (one FMA and one multiply forward, one FMA backward per row): the
+  // FP32 spectrum is widened and narrowed on the integer pipes, and every
+  // load of the next batch of rows is issued before the current batch's
+  // recurrence, so a warp that holds its SM sub-partition alone still
+  // overlaps its loads with its arithmetic.
+  const int nkx = g.nkx, ny = g.ny;
+  const unsigned FULL = 0xFFFFFFFFu;
   const long long l = bk.x * (long long)blockDim.x + threadIdx.x;
-  if (l >= 2ll * nkx * g.nz) return;
+  const bool live = l < 2ll * nkx * g.nz;       // whole warps stay in the loops (warp votes)
   const int part = (int)(l & 1);
-  const long long mode = l >> 1;
+  const long long mode = live ? l >> 1 : 0;
   const long long kx = mode % nkx, kz = mode / nkx;
-  const long long base = kz * (long long)g.ny * nkx + kx, stride = nkx;
+  const long long base = kz * (long long)ny * nkx + kx, stride = nkx;
   T* __restrict__ sp = reinterpret_cast<T*>(f.spec);
   // forward values stay FP64: in place for the FP64 path, in an FP64 scratch
   // spectrum for the mixed path
   double* __restrict__ F = fwd ? fwd : reinterpret_cast<double*>(f.spec);
   const double a = g.idy * g.idy;
-  const bool singular = (kx == 0 && kz == 0);
-  constexpr int B = 16;   // rows per batch: independent loads issued together
+  const bool singular = live && kx == 0 && kz == 0;
+  constexpr int B = 8;   // rows per batch
+  auto at = [&](int j) { return 2 * (base + (long long)j * stride) + part; };
+  // ---- forward: p_j = (r_j - a p_{j-1}) / piv_j
+  double zc[B], ic[B];
+  bool special = false;
+#pragma unroll
+  for (int u = 0; u < B; ++u)
+    if (live && u < ny) {
+      zc[u] = widen(sp[at(u)], special);
+      ic[u] = __ldg(inv + base + (long long)u * stride);
+    }
   double pr = 0.0;
-  for (int j0 = 0; j0 < g.ny; j0 += B) {
-    double zb[B], ib[B];
+  for (int j0 = 0; j0 < ny; j0 += B) {
+    double zn[B], in[B];
+    bool sn = false;
 #pragma unroll
     for (int u = 0; u < B; ++u)
-      if (j0 + u < g.ny) {
-        const long long id = base + (long long)(j0 + u) * stride;
-        zb[u] = (double)sp[2 * id + part];
-        ib[u] = inv[id];
+      if (live && j0 + B + u < ny) {
+        zn[u] = widen(sp[at(j0 + B + u)], sn);
+        in[u] = __ldg(inv + base + (long long)(j0 + B + u) * stride);
       }
+    if (sizeof(T) == 4 && __any_sync(FULL, special)) {   // subnormal, infinite or NaN inputs: hardware widening
+#pragma unroll
+      for (int u = 0; u < B; ++u)
+        if (live && j0 + u < ny) zc[u] = (double)sp[at(j0 + u)];
+    }
+    if (j0 == 0 && singular) zc[0] = 0.0;   // pinned phi_0 of the (0,0) mode
+    // (row 0 takes the same formula: p_{-1} = 0 leaves r_0 / piv_0)
 #pragma unroll
     for (int u = 0; u < B; ++u)
-      if (j0 + u < g.ny) {
-        const int j = j0 + u;
-        pr = (j == 0) ? (singular ? 0.0 : zb[u] * ib[u]) : (zb[u] - a * pr) * ib[u];
-        F[2 * (base + (long long)j * stride) + part] = pr;
+      if (live && j0 + u < ny) {
+        pr = (zc[u] - a * pr) * ic[u];
+        F[at(j0 + u)] = pr;
       }
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      zc[u] = zn[u];
+      ic[u] = in[u];
+    }
+    special = sn;
   }
+  // ---- backward: x_j = p_j - c'_j x_{j+1}
   double xr = pr, sr = pr;
-  sp[2 * (base + (long long)(g.ny - 1) * stride) + part] = (T)xr;
-  for (int j1 = g.ny - 2; j1 >= 0; j1 -= B) {
-    double fb[B], cb[B];
+  if (live) {
+    bool s0 = false;
+    const T o = narrow_to((T*)nullptr, xr, s0);
+    sp[at(ny - 1)] = s0 ? (T)xr : o;
+  }
+  double fc[B], cc[B];
+#pragma unroll
+  for (int u = 0; u < B; ++u)
+    if (live && ny - 2 - u >= 0) {
+      fc[u] = F[at(ny - 2 - u)];
+      cc[u] = __ldg(cp + base + (long long)(ny - 2 - u) * stride);
+    }
+  for (int j1 = ny - 2; j1 >= 0; j1 -= B) {
+    double fn[B], cn[B];
 #pragma unroll
     for (int u = 0; u < B; ++u)
-      if (j1 - u >= 0) {
-        const long long id = base + (long long)(j1 - u) * stride;
-        fb[u] = F[2 * id + part];
-        cb[u] = cp[id];
+      if (live && j1 - B - u >= 0) {
+        fn[u] = F[at(j1 - B - u)];
+        cn[u] = __ldg(cp + base + (long long)(j1 - B - u) * stride);
       }
+    double xs[B];
+    bool so = false;
+    T ob[B];
 #pragma unroll
     for (int u = 0; u < B; ++u)
-      if (j1 - u >= 0) {
-        const long long id = base + (long long)(j1 - u) * stride;
-        xr = fb[u] - cb[u] * xr;
-        sp[2 * id + part] = (T)xr;
-        if (singular) {
-          F[2 * id + part] = xr;
-          sr += xr;
-        }
+      if (live && j1 - u >= 0) {
+        xr = fc[u] - cc[u] * xr;
+        xs[u] = xr;
+        ob[u] = narrow_to((T*)nullptr, xr, so);
+        if (singular) sr += xr;
       }
+    if (sizeof(T) == 4 && __any_sync(FULL, so)) {   // results outside the normal FP32 range: hardware narrowing
+#pragma unroll
+      for (int u = 0; u < B; ++u)
+        if (live && j1 - u >= 0) ob[u] = (T)xs[u];
+    }
+#pragma unroll
+    for (int u = 0; u < B; ++u)
+      if (live && j1 - u >= 0) {
+        sp[at(j1 - u)] = ob[u];
+        if (singular) F[at(j1 - u)] = xs[u];
+      }
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      fc[u] = fn[u];
+      cc[u] = cn[u];
+    }
   }
   if (singular) {
     // zero-mean gauge, from the FP64 values
-    const double mr = sr / g.ny;
-    for (int j = 0; j < g.ny; ++j) {
-      const long long id = base + (long long)j * stride;
-      const double v = (j == g.ny - 1) ? pr : F[2 * id + part];
-      sp[2 * id + part] = (T)(v - mr);
+    const double mr = sr / ny;
+    for (int j = 0; j < ny; ++j) {
+      const double v = (j == ny - 1) ? pr : F[at(j)];
+      sp[at(j)] = (T)(v - mr);
     }
   }
 }
@@ -1703,6 +1764,200 @@ struct Project {
 };
 
 // ---------------------------------------------------------------------------
+// State diagnostics of a step, after its last projection:
+//   div_max = max over C_F of |D u - q| (Eq. mod_div: the projected field
+//             has D u = q on the fluid cells; every cell when q is off),
+//   ke      = 1/2 sum over the velocity nodes of u^2 dV (dV = dx h dz: the
+//             cell height for u and w, the distance of the centres for v),
+//   cfl     = dt max over the cells of |u_c|/dx + |v_c|/h + |w_c|/dz, u_c the
+//             mean of the cell's two faces of each component.
+// A cell counts the nodes of its three lower faces for the energy (the top
+// wall plane of v holds no unknown).  The mixed path forms D u in pair
+// arithmetic from the (hi, lo) state, q as the FP32 pair of q_F, and the
+// energy and CFL number from the hi parts.  Fixed-order two-level reduction:
+// each thread walks a fixed set of cells, sums go through a fixed butterfly.
+// ---------------------------------------------------------------------------
+constexpr int DG_BLOCKS = 4096, DG_THREADS = 256;   // DG_BLOCKS: the most partial triples
+
+template <typename T>
+__device__ __forceinline__ void state_diag(const Blk& bk, const Geo& g, const Fields<T>& f,
+                                           const unsigned* __restrict__ flags32, const DevState* ds, int s,
+                                           int use_q, double* partial) {
+  __shared__ double red[DG_THREADS / 32][3];
+  const long long n = g.ncell;
+  const long long per = (n + bk.gx - 1) / bk.gx;
+  const long long e0 = (long long)bk.x * per, e1 = min(n, e0 + per);
+  const int nx = g.nx, ny = g.ny;
+  const long long pu = (long long)ny * nx, pv = (long long)(ny + 1) * nx;
+  const bool nun = g.yt.ihc != nullptr;
+  double dmax = 0.0, ke = 0.0, cmax = 0.0;
+  if (f.lo[0]) {
+    // FP32 throughout (FP64 is this GPU's narrow pipe): the row constants of
+    // a uniform grid once, a non-uniform row's from its FP64 values through
+    // the integer-pipe conversions (one FP64 subtraction for the low part)
+    const float idx = (float)g.idx, idz = (float)g.idz;
+    const float ixh = (float)f.idh[0][0], ixl = (float)f.idh[0][1], izh = (float)f.idh[2][0], izl = (float)f.idh[2][1];
+    const float uyh = (float)f.idh[1][0], uyl = (float)f.idh[1][1], udy = (float)g.dy;
+    const float qh1 = use_q == 1 ? ds->qf_hi[s] : 0.0f, ql1 = use_q == 1 ? ds->qf_lo[s] : 0.0f;
+    float fdmax = 0.0f, fke = 0.0f, fcmax = 0.0f;
+#pragma unroll 2
+    for (long long e = e0 + threadIdx.x; e < e1; e += DG_THREADS) {
+      long long i, j, k;
+      split3(e, nx, ny, i, j, k);
+      const long long ip = i + 1 == nx ? e - i : e + 1;
+      const long long kp = k + 1 == g.nz ? e - k * pu : e + pu;
+      const long long v0 = k * pv + j * nx + i;
+      float ihh = uyh, ihl = uyl, hc = udy, hf = udy;
+      if (nun) {
+        bool sp = false;
+        const double ih = g.yt.ihc[j];
+        ihh = d2f_int(ih, sp);
+        ihl = d2f_int(ih - f2d_int(ihh, sp), sp);
+        hc = d2f_int(g.yt.hc[j], sp);
+        hf = d2f_int(g.yt.hf[j], sp);
+      }
+      const float uh0 = (float)f.u[e], uh1 = (float)f.u[ip], vh0 = (float)f.v[v0], vh1 = (float)f.v[v0 + nx];
+      const float wh0 = (float)f.w[e], wh1 = (float)f.w[kp];
+      fke += (uh0 * uh0 + wh0 * wh0) * hc + vh0 * vh0 * hf;
+      fcmax = fmaxf(fcmax, fabsf(uh0 + uh1) * idx + fabsf(vh0 + vh1) * ihh + fabsf(wh0 + wh1) * idz);
+      const unsigned fl = (flags32[e >> 2] >> (8 * (e & 3))) & 0xFFu;
+      if (!(use_q && (fl & FLAG_B))) {
+        float bx, sx, by, sy, bz, sz, a1, er1, a2, er2, a3, er3;
+        pair_diff_v(uh1, (float)f.lo[0][ip], uh0, (float)f.lo[0][e], ixh, ixl, bx, sx);
+        pair_diff_v(vh1, (float)f.lo[1][v0 + nx], vh0, (float)f.lo[1][v0], ihh, ihl, by, sy);
+        pair_diff_v(wh1, (float)f.lo[2][kp], wh0, (float)f.lo[2][e], izh, izl, bz, sz);
+        two_sum(bx, by, a1, er1);
+        two_sum(a1, bz, a2, er2);
+        const float qh = use_q == 2 ? (float)f.qk[e] : qh1;
+        two_sum(a2, -qh, a3, er3);
+        const float r = a3 + ((((er1 + er2) + er3) + ((sx + sy) + sz)) - ql1);
+        fdmax = fmaxf(fdmax, fabsf(r));
+      }
+    }
+    // warp reduction in FP32 (an FP64 shuffle reduction per thread would
+    // keep this GPU's narrow FP64 pipe busy longer than the loads take)
+    for (int o = 16; o > 0; o >>= 1) {
+      fdmax = fmaxf(fdmax, __shfl_xor_sync(0xFFFFFFFFu, fdmax, o));
+      fke += __shfl_xor_sync(0xFFFFFFFFu, fke, o);
+      fcmax = fmaxf(fcmax, __shfl_xor_sync(0xFFFFFFFFu, fcmax, o));
+    }
+    dmax = (double)fdmax;
+    ke = (double)fke;
+    cmax = (double)fcmax;
+  } else {
+#pragma unroll 2
+    for (long long e = e0 + threadIdx.x; e < e1; e += DG_THREADS) {
+      long long i, j, k;
+      split3(e, nx, ny, i, j, k);
+      const long long ip = i + 1 == nx ? e - i : e + 1;
+      const long long kp = k + 1 == g.nz ? e - k * pu : e + pu;
+      const long long v0 = k * pv + j * nx + i;
+      const double ih = nun ? g.yt.ihc[j] : g.idy;
+      const double hc = nun ? g.yt.hc[j] : g.dy, hf = nun ? g.yt.hf[j] : g.dy;
+      const double u0 = (double)f.u[e], u1 = (double)f.u[ip], vv0 = (double)f.v[v0], vv1 = (double)f.v[v0 + nx];
+      const double w0 = (double)f.w[e], w1 = (double)f.w[kp];
+      ke += (u0 * u0 + w0 * w0) * hc + vv0 * vv0 * hf;
+      cmax = fmax(cmax, fabs(u0 + u1) * g.idx + fabs(vv0 + vv1) * ih + fabs(w0 + w1) * g.idz);
+      const unsigned fl = (flags32[e >> 2] >> (8 * (e & 3))) & 0xFFu;
+      if (!(use_q && (fl & FLAG_B))) {
+        const double d = ((u1 - u0) * g.idx + (vv1 - vv0) * ih) + (w1 - w0) * g.idz;
+        const double q = use_q == 2 ? (double)f.qk[e] : (use_q ? ds->qf[s] : 0.0);
+        dmax = fmax(dmax, fabs(d - q));
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      dmax = fmax(dmax, __shfl_xor_sync(0xFFFFFFFFu, dmax, o));
+      ke += __shfl_xor_sync(0xFFFFFFFFu, ke, o);
+      cmax = fmax(cmax, __shfl_xor_sync(0xFFFFFFFFu, cmax, o));
+    }
+  }
+  const int wid = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    red[wid][0] = dmax;
+    red[wid][1] = ke;
+    red[wid][2] = cmax;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int w = 0; w < DG_THREADS / 32; ++w) {
+      a = fmax(a, red[w][0]);
+      b += red[w][1];
+      c = fmax(c, red[w][2]);
+    }
+    partial[3 * bk.x] = a;
+    partial[3 * bk.x + 1] = b;
+    partial[3 * bk.x + 2] = c;
+  }
+}
+template <typename T>
+struct StateDiag {
+  static constexpr int kThreads = DG_THREADS;
+  Geo g;
+  Fields<T> f;
+  const unsigned* flags32;
+  const DevState* ds;
+  int s;
+  int use_q;
+  double* partial;
+  __device__ __forceinline__ void operator()(const Blk& bk) const { state_diag<T>(bk, g, f, flags32, ds, s, use_q, partial); }
+};
+
+// 256 threads: thread t adds the partials t, t + 256, ... in turn, then a
+// fixed tree over the threads (reproducible: the order depends only on the
+// number of partials)
+constexpr int DGF_THREADS = 256;
+__device__ __forceinline__ void state_diag_final(const Geo& g, const double* partial, DevState* ds, double dt,
+                                                 int nblk) {
+  __shared__ double red[3][DGF_THREADS];
+  const int t = threadIdx.x;
+  double a = 0.0, k = 0.0, c = 0.0;
+  for (int b = t; b < nblk; b += DGF_THREADS) {
+    a = fmax(a, partial[3 * b]);
+    k += partial[3 * b + 1];
+    c = fmax(c, partial[3 * b + 2]);
+  }
+  red[0][t] = a;
+  red[1][t] = k;
+  red[2][t] = c;
+  __syncthreads();
+  for (int w = DGF_THREADS / 2; w > 0; w >>= 1) {
+    if (t < w) {
+      red[0][t] = fmax(red[0][t], red[0][t + w]);
+      red[1][t] += red[1][t + w];
+      red[2][t] = fmax(red[2][t], red[2][t + w]);
+    }
+    __syncthreads();
+  }
+  if (t == 0) {
+    const double dm = red[0][0], ke = red[1][0], cm = red[2][0];
+    ds->div_max = dm;
+    ds->ke = 0.5 * g.dx * g.dz * ke;
+    ds->cfl = 0.5 * dt * cm;
+    if (!isfinite(ke) || !isfinite(cm) || !isfinite(dm)) atomicOr(&ds->err, ERR_NONFINITE);
+  }
+}
+struct StateDiagFinal {
+  static constexpr int kThreads = DGF_THREADS;
+  Geo g;
+  const double* partial;
+  DevState* ds;
+  double dt;
+  int nblk;
+  __device__ __forceinline__ void operator()(const Blk&) const { state_diag_final(g, partial, ds, dt, nblk); }
+};
+
+template <typename T>
+void launch_state_diag(const Geo& g, const Fields<T>& f, const TagBuffers& b, int s, int use_q, double dt,
+                       double* partial, DevState* ds, Exec& ex) {
+  ex.mark(ST_DIAG);
+  // about four cells per thread
+  const int nblk = reduce_blocks(g, 4 * DG_THREADS, DG_BLOCKS);
+  ex.launch(dim3(nblk), dim3(DG_THREADS), 0, StateDiag<T>{g, f, b.flags32, ds, s, use_q, partial});
+  ex.launch(dim3(1), dim3(DGF_THREADS), 0, StateDiagFinal{g, partial, ds, dt, nblk});
+}
+
+// ---------------------------------------------------------------------------
 // host launcher: the whole elliptic step of one sub-stage
 // ---------------------------------------------------------------------------
 static int lines_for(int n) {
@@ -1784,7 +2039,9 @@ void launch_poisson(const Geo& g, const Fields<T>& f, const TagBuffers& b, const
       const long long warps = (long long)g.nkx * g.nz;
       ex.launch(dim3((unsigned)((warps * 32 + 127) / 128)), dim3(128), 0, TriYWarp<T, 32>{g, f, tb.cp, tb.inv, tb.segf, tb.segb});
     } else {
-      ex.launch(dim3((unsigned)((2 * tlines + 127) / 128)), dim3(128), 0, TriY<T>{g, f, tb.cp, tb.inv, fwd});
+      // blocks of two warps: the systems of a 128^3 grid then spread over
+      // every SM, about one warp per SM sub-partition
+      ex.launch(dim3((unsigned)((2 * tlines + 63) / 64)), dim3(64), 0, TriY<T>{g, f, tb.cp, tb.inv, fwd});
     }
   };
   // fused per-plane transforms when the plane's half-spectrum and two work
@@ -1807,21 +2064,24 @@ void launch_poisson(const Geo& g, const Fields<T>& f, const TagBuffers& b, const
   // slower than the separate x and z kernels, which stay the default)
   const bool plane = tu.fft_plane == 2 && lcp >= 1 && (long long)czp * sh.nz <= wmax && smp <= 200 * 1024;
   // the rest of one solve: z transform, wall-normal Thomas, inverse z and x
-  auto solve_rest = [&](T* out, bool marks) {
+  // (the first solve marks each kernel group; the correction solve keeps its
+  // forward transforms in one group and marks its Thomas and inverse
+  // transforms separately)
+  auto solve_rest = [&](T* out, bool first) {
     if (!plane) {
-      if (marks) ex.mark(ST_FFT_Z_FWD);
+      if (first) ex.mark(ST_FFT_Z_FWD);
       ex.launch(dim3(g.ny * ntile), dim3(256), smz, FftZ<T, false>{g, f, tb.twz, pz, cols});
     }
-    if (marks) ex.mark(ST_TRI_Y);
+    ex.mark(first ? ST_TRI_Y : ST_CORR_TRI);
     tri_solve();
     if (plane) {
-      if (marks) ex.mark(ST_FFT_X_INV);
+      ex.mark(first ? ST_FFT_X_INV : ST_CORR_INV);
       ex.launch(dim3(g.ny), dim3(1024), smp, FftPlaneInv<T>{g, f, tb.twx, tb.twz, px, pz, wbuf, czp, out});
       return;
     }
-    if (marks) ex.mark(ST_FFT_Z_INV);
+    ex.mark(first ? ST_FFT_Z_INV : ST_CORR_INV);
     ex.launch(dim3(g.ny * ntile), dim3(256), smz, FftZ<T, true>{g, f, tb.twz, pz, cols});
-    if (marks) ex.mark(ST_FFT_X_INV);
+    if (first) ex.mark(ST_FFT_X_INV);
     ex.launch(xgrid, xblk, smx, FftXInv<T>{g, f, tb.twx, px, lpb, out});
   };
   // forward x (and z, fused per plane) with the right-hand side of Eq. elliptic_mod
@@ -1875,6 +2135,10 @@ void init_kernel_attributes() {
   set_fft_smem_limits<float>();
 }
 
+template void launch_state_diag<double>(const Geo&, const Fields<double>&, const TagBuffers&, int, int, double,
+                                        double*, DevState*, Exec&);
+template void launch_state_diag<float>(const Geo&, const Fields<float>&, const TagBuffers&, int, int, double,
+                                       double*, DevState*, Exec&);
 template void launch_poisson<double>(const Geo&, const Fields<double>&, const TagBuffers&,
                                      const SpecTables<double>&, const Stage&, double, double, int, double*,
                                      DevState*, Exec&);

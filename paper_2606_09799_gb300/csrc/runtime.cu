@@ -46,7 +46,8 @@ void stage_mark(cudaStream_t st, int id) {
 
 static const char* kStageNames[ST_COUNT] = {
     "tagging", "ib_force", "rhs", "sweep_x", "sweep_z", "sweep_y", "q_reduce", "fft_x_fwd", "fft_z_fwd",
-    "tri_y", "fft_z_inv", "fft_x_inv", "project", "slip", "correction", "other"};
+    "tri_y", "fft_z_inv", "fft_x_inv", "project", "slip", "correction", "diagnostics", "correction_tri",
+    "correction_inv", "other"};
 
 int num_sms() {
   int dev = 0;
@@ -516,6 +517,7 @@ static void enqueue_step(ibm_handle h, Exec& ex) {
     launch_sweeps<T>(g, f, h->tb, sw, h->ds, ex);
     launch_poisson<T>(g, f, h->tb, sp, sg[k], h->desc.dt, h->desc.re, h->desc.use_q, h->partial, h->ds, ex);
   }
+  launch_state_diag<T>(g, f, h->tb, sg[ns - 1].s, h->desc.use_q, h->desc.dt, h->partial, h->ds, ex);
   launch_slip<T>(g, s, f, h->tb, h->partial, h->ds, ex);
   ex.launch(dim3(1), dim3(1), 0, StepDone{h->ds});
 }
@@ -1118,7 +1120,7 @@ ibm_status ibm_create_grid(const ibm_grid_desc* desc, void* stream, ibm_handle* 
     if (!h->qk) { release_all(h); delete h; return IBM_ERR_OOM; }
   }
   h->ds = (DevState*)dalloc(h, sizeof(DevState));
-  h->partial = (double*)dalloc(h, 4096 * sizeof(double));
+  h->partial = (double*)dalloc(h, 16384 * sizeof(double));
   h->tb.d2min = (unsigned long long*)dalloc(h, nall * 8);
   h->tb.owner = (unsigned*)dalloc(h, nall * 4);
   h->tb.ub = (unsigned*)dalloc(h, nall * 4);
@@ -1495,9 +1497,56 @@ ibm_status ibm_set_fields(ibm_handle h, const double* u, const double* v, const 
   return IBM_OK;
 }
 
+static ibm_status check_device(ibm_handle h, const DevState* have = nullptr);
+
+// Copy the non-linear history H of the three grids out of / into the handle
+// (FP64 caller arrays; the mixed paths convert, exactly in both directions).
+ibm_status ibm_get_history(ibm_handle h, double* hu, double* hv, double* hw, int on_device) {
+  if (!h) return IBM_ERR_ARG;
+  const Geo& g = h->g;
+  cudaStream_t st = h->user;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  double* dst[3] = {hu, hv, hw};
+  for (int c = 0; c < 3; ++c) {
+    if (!dst[c]) continue;
+    const long long n = comp_size(g, c);
+    if (h->esize == 8) {
+      CK(cudaMemcpyAsync(dst[c], h->H[c], n * 8, kind, st));
+    } else {
+      double* stage = (double*)h->scr;
+      k_convert<float, double><<<num_sms() * 4, 256, 0, st>>>((const float*)h->H[c], stage, n);
+      CK(cudaMemcpyAsync(dst[c], stage, n * 8, kind, st));
+    }
+    CK(cudaStreamSynchronize(st));
+  }
+  return check_device(h);
+}
+
+ibm_status ibm_set_history(ibm_handle h, const double* hu, const double* hv, const double* hw, int on_device) {
+  if (!h) return IBM_ERR_ARG;
+  const Geo& g = h->g;
+  cudaStream_t st = h->user;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const double* src[3] = {hu, hv, hw};
+  for (int c = 0; c < 3; ++c) {
+    if (!src[c]) continue;
+    const long long n = comp_size(g, c);
+    if (h->esize == 8) {
+      CK(cudaMemcpyAsync(h->H[c], src[c], n * 8, kind, st));
+    } else {
+      double* stage = (double*)h->scr;
+      CK(cudaMemcpyAsync(stage, src[c], n * 8, kind, st));
+      k_convert<double, float><<<num_sms() * 4, 256, 0, st>>>(stage, (float*)h->H[c], n);
+    }
+  }
+  CK(cudaGetLastError());
+  if (!on_device) CK(cudaStreamSynchronize(st));
+  return IBM_OK;
+}
+
 // Turn the device error word (and the surface-index flag) into a status.
 // `have` (optional) is a device-state copy taken after the stream finished.
-static ibm_status check_device(ibm_handle h, const DevState* have = nullptr) {
+static ibm_status check_device(ibm_handle h, const DevState* have) {
   DevState ds;
   unsigned bad = 0;
   if (have) {
@@ -1620,6 +1669,9 @@ ibm_status ibm_get_diag(ibm_handle h, ibm_diag* out) {
   out->steps = (int64_t)ds.steps;
   out->ncandidates = ds.ncand;
   out->kernels_per_step = h->kernels_per_step;
+  out->div_max = ds.div_max;
+  out->ke = ds.ke;
+  out->cfl = ds.cfl;
   return s;
 }
 

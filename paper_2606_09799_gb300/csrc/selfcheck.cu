@@ -1,6 +1,8 @@
 // selfcheck.cu -- bit-for-bit check of the integer-pipe FP32 <-> FP64
-// conversions (common.cuh) against the hardware conversions, and a check
-// that the bounded mbarrier wait (mbar.cuh) gives up and returns.
+// conversions (common.cuh) against the hardware conversions, a check that
+// the bounded mbarrier wait (mbar.cuh) gives up and returns, and the FP64 /
+// FP32 fused multiply-add throughput of the device (the arithmetic roofs
+// the benchmark reports against).
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -84,7 +86,73 @@ __global__ void k_check_bounded_wait(long long limit_cycles, long long* out) {
   }
 }
 
+// Arithmetic throughput probe: every thread runs eight independent chains
+// of fused multiply-adds (a <- a m + b), so the pipe of type T, not the
+// latency of one chain, bounds the rate.  The result is stored only under a
+// condition the data never meets, which keeps the chains alive.
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma_chains(int iters, T seed, T* out) {
+  T a[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) a[c] = seed + (T)(threadIdx.x + 7 * c);
+  const T m = (T)0.9999, b = (T)1e-4;
+#pragma unroll 4
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) a[c] = fma(a[c], m, b);
+  }
+  T s = (T)0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) s += a[c];
+  if (s == (T)-1.25) out[0] = s;
+}
+
+template <typename T>
+static cudaError_t fma_rate(T* out, double* tflops) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const dim3 grid((unsigned)(sms * 8)), block(256);
+  cudaEvent_t a = nullptr, z = nullptr;
+  e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&z);
+  // size the run from a short one so that the timed launch takes ~20 ms
+  int iters = 256;
+  float ms = 0.f;
+  for (int round = 0; round < 3 && e == cudaSuccess; ++round) {
+    k_fma_chains<T><<<grid, block>>>(iters, (T)1, out);
+    e = cudaEventRecord(a);
+    if (e == cudaSuccess) {
+      k_fma_chains<T><<<grid, block>>>(iters, (T)1, out);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(z);
+    if (e == cudaSuccess) e = cudaEventSynchronize(z);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, z);
+    if (e != cudaSuccess || round == 2) break;
+    const double scale = ms > 0.f ? 20.0 / ms : 64.0;
+    iters = (int)fmin(fmax(iters * scale, 256.0), 1e8);
+  }
+  if (e == cudaSuccess)
+    *tflops = 2.0 * 8.0 * (double)iters * (double)grid.x * block.x / (ms * 1e-3) / 1e12;
+  if (a) cudaEventDestroy(a);
+  if (z) cudaEventDestroy(z);
+  return e;
+}
+
 }  // namespace ibm
+
+extern "C" ibm_status ibm_measure_alu_peaks(double* fp64_tflops, double* fp32_tflops) {
+  if (!fp64_tflops || !fp32_tflops) return IBM_ERR_ARG;
+  double* d = nullptr;
+  if (cudaMalloc(&d, 16) != cudaSuccess) return IBM_ERR_OOM;
+  ibm_status st = IBM_OK;
+  if (ibm::fma_rate<double>(d, fp64_tflops) != cudaSuccess) st = IBM_ERR_CUDA;
+  if (st == IBM_OK && ibm::fma_rate<float>(reinterpret_cast<float*>(d), fp32_tflops) != cudaSuccess) st = IBM_ERR_CUDA;
+  cudaFree(d);
+  return st;
+}
 
 extern "C" ibm_status ibm_check_bounded_wait(long long limit_cycles, int* timed_out, long long* waited_cycles) {
   if (limit_cycles < 0 || limit_cycles > 4000000000ll || !timed_out || !waited_cycles) return IBM_ERR_ARG;

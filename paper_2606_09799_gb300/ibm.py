@@ -51,9 +51,10 @@ class ibm_diag(ctypes.Structure):
                 ("nforce", ctypes.c_int64 * 3), ("nboundary", ctypes.c_int64),
                 ("q_f", ctypes.c_double), ("sum_q_dv", ctypes.c_double), ("steps", ctypes.c_int64),
                 ("ncandidates", ctypes.c_int64), ("kernels_per_step", ctypes.c_int64),
-                ("d2h_bytes", ctypes.c_int64)]
+                ("d2h_bytes", ctypes.c_int64), ("div_max", ctypes.c_double), ("ke", ctypes.c_double),
+                ("cfl", ctypes.c_double)]
 
-IBM_NSTAGES = 16
+IBM_NSTAGES = 19
 
 
 class ibm_tune(ctypes.Structure):
@@ -76,7 +77,8 @@ EXPORTS = ("ibm_create_grid", "ibm_destroy", "ibm_set_surface", "ibm_set_body_fo
            "ibm_set_tune", "ibm_get_tune", "ibm_autotune", "ibm_batch_create", "ibm_batch_destroy",
            "ibm_batch_step", "ibm_batch_sync", "ibm_batch_get_info", "ibm_batch_profile_stages",
            "ibm_batch_set_tune", "ibm_batch_autotune", "ibm_batch_last_error", "ibm_step_batch",
-           "ibm_get_loads", "ibm_get_pressure_recon", "ibm_check_conversions", "ibm_create_grid_stretched", "ibm_check_bounded_wait")
+           "ibm_get_loads", "ibm_get_pressure_recon", "ibm_check_conversions", "ibm_create_grid_stretched", "ibm_check_bounded_wait",
+           "ibm_get_history", "ibm_set_history", "ibm_measure_alu_peaks")
 
 
 def library_path() -> str:
@@ -103,6 +105,8 @@ def load(build_if_needed: bool = True):
         L.ibm_set_fields.argtypes = [P, P, P, P, P, I]
         L.ibm_step.argtypes = [P, I]
         L.ibm_get_fields.argtypes = [P, P, P, P, P, I]
+        L.ibm_get_history.argtypes = [P, P, P, P, I]
+        L.ibm_set_history.argtypes = [P, P, P, P, I]
         L.ibm_get_tags.argtypes = [P, I, P, I]
         L.ibm_get_diag.argtypes = [P, ctypes.POINTER(ibm_diag)]
         L.ibm_sync.argtypes = [P]
@@ -134,6 +138,7 @@ def load(build_if_needed: bool = True):
         L.ibm_check_bounded_wait.argtypes = [ctypes.c_longlong, ctypes.POINTER(ctypes.c_int),
                                              ctypes.POINTER(ctypes.c_longlong)]
         L.ibm_check_bounded_wait.restype = ctypes.c_int
+        L.ibm_measure_alu_peaks.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
         L.ibm_check_conversions.argtypes = [ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong),
                                             ctypes.POINTER(ctypes.c_longlong)]
         for name in EXPORTS:
@@ -243,6 +248,24 @@ def ibm_get_fields(h, nx, ny, nz, out=None):
     return out
 
 
+def ibm_get_history(h, nx, ny, nz, out=None):
+    """Returns the non-linear history (hu, hv, hw) of AB+CN as FP64 arrays
+    (or fills `out`, three contiguous FP64 arrays or device tensors)."""
+    if out is None:
+        out = (np.empty((nz, ny, nx)), np.empty((nz, ny + 1, nx)), np.empty((nz, ny, nx)))
+    ptrs = [_ptr(a) for a in out]
+    _check(h, load().ibm_get_history(h, *[q for q, _ in ptrs], ptrs[0][1]))
+    return out
+
+
+def ibm_set_history(h, hu=None, hv=None, hw=None):
+    ptrs = [_ptr(a) for a in (hu, hv, hw)]
+    dev = {d for (q, d) in ptrs if q is not None}
+    if len(dev) > 1:
+        raise ValueError("history arrays must all live on the host or all on the device")
+    _check(h, load().ibm_set_history(h, *[q for q, _ in ptrs], dev.pop() if dev else 0))
+
+
 def ibm_get_tags(h, comp, shape):
     owner = np.empty(shape, dtype=np.int32)
     _check(h, load().ibm_get_tags(h, int(comp), owner.ctypes.data, 0))
@@ -254,7 +277,8 @@ def ibm_get_diag(h) -> dict:
     _check(h, load().ibm_get_diag(h, ctypes.byref(d)))
     return {"slip_l1": d.slip_l1, "slip_comp": list(d.slip_comp), "nforce": list(d.nforce),
             "nboundary": d.nboundary, "q_f": d.q_f, "sum_q_dv": d.sum_q_dv, "steps": d.steps,
-            "ncandidates": d.ncandidates, "kernels_per_step": d.kernels_per_step, "d2h_bytes": d.d2h_bytes}
+            "ncandidates": d.ncandidates, "kernels_per_step": d.kernels_per_step, "d2h_bytes": d.d2h_bytes,
+            "div_max": d.div_max, "ke": d.ke, "cfl": d.cfl}
 
 
 def ibm_profile_stages(h, nsteps=1) -> dict:
@@ -377,6 +401,16 @@ def ibm_get_loads(h, nt, sides=1, pole=(0.0, 0.0, 0.0)):
     return F, M, tr, pw
 
 
+def ibm_measure_alu_peaks() -> tuple:
+    """(FP64, FP32) fused multiply-add throughput of the current device in
+    TFLOP/s (FMA = 2 flops)."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    st = load().ibm_measure_alu_peaks(ctypes.byref(a), ctypes.byref(b))
+    if st != 0:
+        raise IbmError(st, "ibm_measure_alu_peaks failed")
+    return a.value, b.value
+
+
 def ibm_check_conversions(n: int) -> tuple:
     """(mismatches, checked) of the integer-path FP32 <-> FP64 conversions
     against the hardware conversions on n hashed cases."""
@@ -491,6 +525,13 @@ class Simulation:
     def fields(self):
         nx, ny, nz = self.shape
         return ibm_get_fields(self.h, nx, ny, nz)
+
+    def history(self):
+        nx, ny, nz = self.shape
+        return ibm_get_history(self.h, nx, ny, nz)
+
+    def set_history(self, hu=None, hv=None, hw=None):
+        ibm_set_history(self.h, hu, hv, hw)
 
     def tags(self):
         nx, ny, nz = self.shape

@@ -180,18 +180,19 @@ def test_batch_autotune_leaves_state():
     b.close()
 
 
-@pytest.mark.parametrize("sweep_y", [2, 3])
+@pytest.mark.parametrize("tune", [dict(tri_y=1, sweep_y=2, fft_plane=2), dict(tri_y=1, sweep_y=3, fft_plane=2),
+                                  dict(tri_y=2, sweep_y=3, fft_plane=2)])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_batch_bulk_copy_y_tiles_equal_solo(precision, sweep_y):
-    """Launch-shape choices sweep_y = 2 and 3 in a batch of uneven instances
-    and alone: the same fields, bit for bit in FP64.  (With 2 a batch keeps
-    the streamed y sweep: its ops live in global memory, not in kernel
-    parameters where tensor maps must be; 3 is the mixed path's tabulated
-    rows in both.)"""
+def test_batch_bulk_copy_y_tiles_equal_solo(precision, tune):
+    """Launch-shape choices sweep_y = 2 and 3 (with either Thomas variant)
+    in a batch of uneven instances and alone: the same fields, bit for bit
+    in FP64.  (With 2 a batch keeps the streamed y sweep: its ops live in
+    global memory, not in kernel parameters where tensor maps must be; 3 is
+    the mixed path's tabulated rows in both.)"""
     wls = small_batch()
     sims = [make(w, precision) for w in wls]
     b = ibm.Batch(sims)
-    b.set_tune(tri_y=1, sweep_y=sweep_y, fft_plane=2)
+    b.set_tune(**tune)
     for s in range(3):
         for w, g in zip(wls, sims):
             xyz, vel = w.surface(s)
@@ -200,7 +201,7 @@ def test_batch_bulk_copy_y_tiles_equal_solo(precision, sweep_y):
     b.sync()
     for w, g in zip(wls, sims):
         ref = make(w, precision)
-        ibm.ibm_set_tune(ref.h, tri_y=1, sweep_y=sweep_y, fft_plane=2)
+        ibm.ibm_set_tune(ref.h, **tune)
         for s in range(3):
             xyz, vel = w.surface(s)
             ref.set_surface(xyz, vel, w.tri)

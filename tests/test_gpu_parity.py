@@ -289,12 +289,14 @@ def test_candidate_capacity_grows_for_large_triangles():
                                   dict(tri_y=3, sweep_zy=1, sweep_w=64, fft_lpb=8, fft_cols=16, fft_plane=2),
                                   dict(tri_y=1, sweep_zy=2, sweep_y=1, fft_plane=2),
                                   dict(tri_y=1, sweep_y=2, fft_plane=2),
-                                  dict(tri_y=1, sweep_y=3, fft_plane=2)])
+                                  dict(tri_y=1, sweep_y=3, fft_plane=2),
+                                  dict(tri_y=2, sweep_y=3, fft_plane=2)])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-5)])
 def test_every_launch_shape_matches_oracle(tune, precision, tol):
     """Every choice the autotuner can make (Thomas variant, sweep form and
-    width, streamed y sweep, bulk-copy y tiles, tabulated y rows, FFT tiling) computes the same step: against the oracle on a
-    ragged grid with a moving sphere, 4 steps."""
+    width, streamed y sweep, bulk-copy y tiles, tabulated y rows, FFT
+    tiling) computes the same step: against the oracle on a ragged grid with
+    a moving sphere, 4 steps."""
     wl = inputs.oscillating_sphere(n=48, steps=4, subdiv=2)
     o = OracleSim(48, 37, 96, 1.0, 0.9, 1.6, re=150.0, dt=2e-3)
     g = ibm.Simulation(48, 37, 96, 1.0, 0.9, 1.6, re=150.0, dt=2e-3, precision=precision)
@@ -408,3 +410,13 @@ def test_integer_path_conversions_match_hardware():
     bad, checked = ibm.ibm_check_conversions(1 << 22)
     assert checked > (1 << 22)   # most cases take the integer path
     assert bad == 0, bad
+
+
+def test_alu_peak_probe_reports_plausible_rates():
+    """The arithmetic roofs the benchmark reports FP64-bound kernels
+    against: FMA-chain throughput of this device, FP64 far below FP32 on
+    this GPU (its FP64 pipe is narrow), both within wide physical bounds."""
+    fp64, fp32 = ibm.ibm_measure_alu_peaks()
+    assert 0.1 < fp64 < 10.0, fp64
+    assert 10.0 < fp32 < 300.0, fp32
+    assert fp32 > 8 * fp64

@@ -48,6 +48,32 @@ def test_tag_noalloc_equals_allocating_path_on_two_calls():
     sim.close()
 
 
+def test_tag_noalloc_free_slip_walls_and_a_non_unit_box():
+    """Other sizes, box lengths and wall condition than the 64^3 cube: the
+    owners still equal those of a handle made by ibm_create_grid with the
+    same description, on two calls in a row."""
+    torch = pytest.importorskip("torch")
+    nx, ny, nz, lx, ly, lz = 48, 40, 60, 1.2, 1.0, 1.5
+    assert 3 * nx * ny * nz + nx * nz <= ibm.IBM_NOALLOC_MAX_NODES
+    dev = torch.device("cuda", 0)
+    owners = _owners_like(torch, nx, ny, nz)
+    sim = ibm.Simulation(nx, ny, nz, lx, ly, lz, re=100.0, dt=1e-3, ybc=ibm.IBM_FREESLIP)
+    stream = torch.cuda.current_stream().cuda_stream
+    for seed, centre in ((3, (0.6, 0.5, 0.75)), (4, (0.05, 0.45, 1.45))):   # the second wraps in x and z
+        xyz, tri = inputs.icosphere(2, 0.22, centre)
+        xyz = xyz + 0.01 * np.random.default_rng(seed).standard_normal(xyz.shape)
+        sim.set_surface(xyz, np.zeros_like(xyz), tri)
+        sim.step()
+        ref = sim.tags()
+        st = ibm.ibm_tag_noalloc(nx, ny, nz, torch.from_numpy(xyz).to(dev), torch.from_numpy(tri).to(dev), owners,
+                                 lx=lx, ly=ly, lz=lz, ybc=ibm.IBM_FREESLIP, stream=stream)
+        assert st == 0, ibm.STATUS.get(st, st)
+        for c in range(3):
+            np.testing.assert_array_equal(owners[c].cpu().numpy(), ref[c])
+        assert sum(int((o >= 0).sum()) for o in owners) > 1000
+    sim.close()
+
+
 def test_tag_noalloc_rejects_oversized_grid_and_bad_indices():
     torch = pytest.importorskip("torch")
     dev = torch.device("cuda", 0)
