@@ -44,6 +44,11 @@ struct YTab {
   const double* ysw2;
   const float* yswf;    // FP32 copies of ysw and ysw2 (mixed path), else null
   const float* ysw2f;
+  // rows of the tagging pre-screen, FP32: for the face rows (v, [0][j]) and
+  // the centre rows (u and w, [1][j]), j = 0..ny, at [half * (ny + 1) + j]:
+  // (y_j, the wall-normal side of the node's local cell, y_j - y_{j-1},
+  // y_{j+1} - y_j)
+  const float4* rowf;
   double hmax;
 };
 

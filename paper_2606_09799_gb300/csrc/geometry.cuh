@@ -71,6 +71,8 @@ struct TriF32 {
   int ia[3][2];     // lattice index of the first vertex (32-bit: no 64-bit conversions in the screen)
   float fr[3][2];
   float del[3], diag2;
+  float ay;         // y of the first vertex (non-uniform rows: positions from the row table)
+  float ymn, ymx;   // the triangle's y extent
 };
 
 // Everything the kernels of one step derive from a triangle alone, formed

@@ -1779,35 +1779,36 @@ struct Project {
 // ---------------------------------------------------------------------------
 constexpr int DG_BLOCKS = 4096, DG_THREADS = 256;   // DG_BLOCKS: the most partial triples
 
+// FP32 constants of the mixed path's diagnostics, formed on the host (a
+// conversion from FP64 occupies this GPU's narrow FP64 pipe): 1/dx, 1/dz,
+// the reciprocal spacings as (hi, lo) pairs, dy.
+struct DiagF32 {
+  float idx, idz, ixh, ixl, izh, izl, uyh, uyl, dy;
+};
+
 template <typename T>
 __device__ __forceinline__ void state_diag(const Blk& bk, const Geo& g, const Fields<T>& f,
                                            const unsigned* __restrict__ flags32, const DevState* ds, int s,
-                                           int use_q, double* partial) {
+                                           int use_q, const DiagF32& fc, double* partial) {
   __shared__ double red[DG_THREADS / 32][3];
-  const long long n = g.ncell;
-  const long long per = (n + bk.gx - 1) / bk.gx;
-  const long long e0 = (long long)bk.x * per, e1 = min(n, e0 + per);
+  // a warp walks whole x-rows (j, k) -- the row's constants once, cells along
+  // the lanes -- rows in a fixed order per warp
   const int nx = g.nx, ny = g.ny;
   const long long pu = (long long)ny * nx, pv = (long long)(ny + 1) * nx;
   const bool nun = g.yt.ihc != nullptr;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const long long nrows = (long long)ny * g.nz;
+  const long long wstride = (long long)bk.gx * (DG_THREADS / 32);
   double dmax = 0.0, ke = 0.0, cmax = 0.0;
   if (f.lo[0]) {
-    // FP32 throughout (FP64 is this GPU's narrow pipe): the row constants of
-    // a uniform grid once, a non-uniform row's from its FP64 values through
-    // the integer-pipe conversions (one FP64 subtraction for the low part)
-    const float idx = (float)g.idx, idz = (float)g.idz;
-    const float ixh = (float)f.idh[0][0], ixl = (float)f.idh[0][1], izh = (float)f.idh[2][0], izl = (float)f.idh[2][1];
-    const float uyh = (float)f.idh[1][0], uyl = (float)f.idh[1][1], udy = (float)g.dy;
+    const float idx = fc.idx, idz = fc.idz;
+    const float ixh = fc.ixh, ixl = fc.ixl, izh = fc.izh, izl = fc.izl;
     const float qh1 = use_q == 1 ? ds->qf_hi[s] : 0.0f, ql1 = use_q == 1 ? ds->qf_lo[s] : 0.0f;
     float fdmax = 0.0f, fke = 0.0f, fcmax = 0.0f;
-#pragma unroll 2
-    for (long long e = e0 + threadIdx.x; e < e1; e += DG_THREADS) {
-      long long i, j, k;
-      split3(e, nx, ny, i, j, k);
-      const long long ip = i + 1 == nx ? e - i : e + 1;
-      const long long kp = k + 1 == g.nz ? e - k * pu : e + pu;
-      const long long v0 = k * pv + j * nx + i;
-      float ihh = uyh, ihl = uyl, hc = udy, hf = udy;
+    for (long long r = (long long)bk.x * (DG_THREADS / 32) + wid; r < nrows; r += wstride) {
+      const int j = (int)(r % ny), k = (int)(r / ny);
+      // row constants: FP32 pair of 1/h and the node volumes' heights
+      float ihh = fc.uyh, ihl = fc.uyl, hc = fc.dy, hf = fc.dy;
       if (nun) {
         bool sp = false;
         const double ih = g.yt.ihc[j];
@@ -1816,22 +1817,28 @@ __device__ __forceinline__ void state_diag(const Blk& bk, const Geo& g, const Fi
         hc = d2f_int(g.yt.hc[j], sp);
         hf = d2f_int(g.yt.hf[j], sp);
       }
-      const float uh0 = (float)f.u[e], uh1 = (float)f.u[ip], vh0 = (float)f.v[v0], vh1 = (float)f.v[v0 + nx];
-      const float wh0 = (float)f.w[e], wh1 = (float)f.w[kp];
-      fke += (uh0 * uh0 + wh0 * wh0) * hc + vh0 * vh0 * hf;
-      fcmax = fmaxf(fcmax, fabsf(uh0 + uh1) * idx + fabsf(vh0 + vh1) * ihh + fabsf(wh0 + wh1) * idz);
-      const unsigned fl = (flags32[e >> 2] >> (8 * (e & 3))) & 0xFFu;
-      if (!(use_q && (fl & FLAG_B))) {
-        float bx, sx, by, sy, bz, sz, a1, er1, a2, er2, a3, er3;
-        pair_diff_v(uh1, (float)f.lo[0][ip], uh0, (float)f.lo[0][e], ixh, ixl, bx, sx);
-        pair_diff_v(vh1, (float)f.lo[1][v0 + nx], vh0, (float)f.lo[1][v0], ihh, ihl, by, sy);
-        pair_diff_v(wh1, (float)f.lo[2][kp], wh0, (float)f.lo[2][e], izh, izl, bz, sz);
-        two_sum(bx, by, a1, er1);
-        two_sum(a1, bz, a2, er2);
-        const float qh = use_q == 2 ? (float)f.qk[e] : qh1;
-        two_sum(a2, -qh, a3, er3);
-        const float r = a3 + ((((er1 + er2) + er3) + ((sx + sy) + sz)) - ql1);
-        fdmax = fmaxf(fdmax, fabsf(r));
+      const long long e0 = (long long)k * pu + (long long)j * nx;
+      const long long kp0 = (k + 1 == g.nz ? 0 : (long long)(k + 1) * pu) + (long long)j * nx;
+      const long long v00 = (long long)k * pv + (long long)j * nx;
+      for (int i = lane; i < nx; i += 32) {
+        const long long e = e0 + i, ip = e0 + (i + 1 == nx ? 0 : i + 1), kp = kp0 + i, v0 = v00 + i;
+        const float uh0 = (float)f.u[e], uh1 = (float)f.u[ip], vh0 = (float)f.v[v0], vh1 = (float)f.v[v0 + nx];
+        const float wh0 = (float)f.w[e], wh1 = (float)f.w[kp];
+        fke += (uh0 * uh0 + wh0 * wh0) * hc + vh0 * vh0 * hf;
+        fcmax = fmaxf(fcmax, fabsf(uh0 + uh1) * idx + fabsf(vh0 + vh1) * ihh + fabsf(wh0 + wh1) * idz);
+        const unsigned fl = (flags32[e >> 2] >> (8 * (e & 3))) & 0xFFu;
+        if (!(use_q && (fl & FLAG_B))) {
+          float bx, sx, by, sy, bz, sz, a1, er1, a2, er2, a3, er3;
+          pair_diff_v(uh1, (float)f.lo[0][ip], uh0, (float)f.lo[0][e], ixh, ixl, bx, sx);
+          pair_diff_v(vh1, (float)f.lo[1][v0 + nx], vh0, (float)f.lo[1][v0], ihh, ihl, by, sy);
+          pair_diff_v(wh1, (float)f.lo[2][kp], wh0, (float)f.lo[2][e], izh, izl, bz, sz);
+          two_sum(bx, by, a1, er1);
+          two_sum(a1, bz, a2, er2);
+          const float qh = use_q == 2 ? (float)f.qk[e] : qh1;
+          two_sum(a2, -qh, a3, er3);
+          const float rr = a3 + ((((er1 + er2) + er3) + ((sx + sy) + sz)) - ql1);
+          fdmax = fmaxf(fdmax, fabsf(rr));
+        }
       }
     }
     // warp reduction in FP32 (an FP64 shuffle reduction per thread would
@@ -1841,28 +1848,31 @@ __device__ __forceinline__ void state_diag(const Blk& bk, const Geo& g, const Fi
       fke += __shfl_xor_sync(0xFFFFFFFFu, fke, o);
       fcmax = fmaxf(fcmax, __shfl_xor_sync(0xFFFFFFFFu, fcmax, o));
     }
-    dmax = (double)fdmax;
-    ke = (double)fke;
-    cmax = (double)fcmax;
+    if (lane == 0) {   // (one conversion per warp)
+      dmax = (double)fdmax;
+      ke = (double)fke;
+      cmax = (double)fcmax;
+    }
   } else {
-#pragma unroll 2
-    for (long long e = e0 + threadIdx.x; e < e1; e += DG_THREADS) {
-      long long i, j, k;
-      split3(e, nx, ny, i, j, k);
-      const long long ip = i + 1 == nx ? e - i : e + 1;
-      const long long kp = k + 1 == g.nz ? e - k * pu : e + pu;
-      const long long v0 = k * pv + j * nx + i;
+    for (long long r = (long long)bk.x * (DG_THREADS / 32) + wid; r < nrows; r += wstride) {
+      const int j = (int)(r % ny), k = (int)(r / ny);
       const double ih = nun ? g.yt.ihc[j] : g.idy;
       const double hc = nun ? g.yt.hc[j] : g.dy, hf = nun ? g.yt.hf[j] : g.dy;
-      const double u0 = (double)f.u[e], u1 = (double)f.u[ip], vv0 = (double)f.v[v0], vv1 = (double)f.v[v0 + nx];
-      const double w0 = (double)f.w[e], w1 = (double)f.w[kp];
-      ke += (u0 * u0 + w0 * w0) * hc + vv0 * vv0 * hf;
-      cmax = fmax(cmax, fabs(u0 + u1) * g.idx + fabs(vv0 + vv1) * ih + fabs(w0 + w1) * g.idz);
-      const unsigned fl = (flags32[e >> 2] >> (8 * (e & 3))) & 0xFFu;
-      if (!(use_q && (fl & FLAG_B))) {
-        const double d = ((u1 - u0) * g.idx + (vv1 - vv0) * ih) + (w1 - w0) * g.idz;
-        const double q = use_q == 2 ? (double)f.qk[e] : (use_q ? ds->qf[s] : 0.0);
-        dmax = fmax(dmax, fabs(d - q));
+      const long long e0 = (long long)k * pu + (long long)j * nx;
+      const long long kp0 = (k + 1 == g.nz ? 0 : (long long)(k + 1) * pu) + (long long)j * nx;
+      const long long v00 = (long long)k * pv + (long long)j * nx;
+      for (int i = lane; i < nx; i += 32) {
+        const long long e = e0 + i, ip = e0 + (i + 1 == nx ? 0 : i + 1), kp = kp0 + i, v0 = v00 + i;
+        const double u0 = (double)f.u[e], u1 = (double)f.u[ip], vv0 = (double)f.v[v0], vv1 = (double)f.v[v0 + nx];
+        const double w0 = (double)f.w[e], w1 = (double)f.w[kp];
+        ke += (u0 * u0 + w0 * w0) * hc + vv0 * vv0 * hf;
+        cmax = fmax(cmax, fabs(u0 + u1) * g.idx + fabs(vv0 + vv1) * ih + fabs(w0 + w1) * g.idz);
+        const unsigned fl = (flags32[e >> 2] >> (8 * (e & 3))) & 0xFFu;
+        if (!(use_q && (fl & FLAG_B))) {
+          const double d = ((u1 - u0) * g.idx + (vv1 - vv0) * ih) + (w1 - w0) * g.idz;
+          const double q = use_q == 2 ? (double)f.qk[e] : (use_q ? ds->qf[s] : 0.0);
+          dmax = fmax(dmax, fabs(d - q));
+        }
       }
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -1871,8 +1881,7 @@ __device__ __forceinline__ void state_diag(const Blk& bk, const Geo& g, const Fi
       cmax = fmax(cmax, __shfl_xor_sync(0xFFFFFFFFu, cmax, o));
     }
   }
-  const int wid = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0) {
+  if (lane == 0) {
     red[wid][0] = dmax;
     red[wid][1] = ke;
     red[wid][2] = cmax;
@@ -1899,8 +1908,11 @@ struct StateDiag {
   const DevState* ds;
   int s;
   int use_q;
+  DiagF32 fc;
   double* partial;
-  __device__ __forceinline__ void operator()(const Blk& bk) const { state_diag<T>(bk, g, f, flags32, ds, s, use_q, partial); }
+  __device__ __forceinline__ void operator()(const Blk& bk) const {
+    state_diag<T>(bk, g, f, flags32, ds, s, use_q, fc, partial);
+  }
 };
 
 // 256 threads: thread t adds the partials t, t + 256, ... in turn, then a
@@ -1951,9 +1963,12 @@ template <typename T>
 void launch_state_diag(const Geo& g, const Fields<T>& f, const TagBuffers& b, int s, int use_q, double dt,
                        double* partial, DevState* ds, Exec& ex) {
   ex.mark(ST_DIAG);
-  // about four cells per thread
-  const int nblk = reduce_blocks(g, 4 * DG_THREADS, DG_BLOCKS);
-  ex.launch(dim3(nblk), dim3(DG_THREADS), 0, StateDiag<T>{g, f, b.flags32, ds, s, use_q, partial});
+  // about two rows of cells per warp
+  const int nblk = (int)std::min<long long>(DG_BLOCKS, std::max<long long>(
+      8, ((long long)g.ny * g.nz + 2 * (DG_THREADS / 32) - 1) / (2 * (DG_THREADS / 32))));
+  const DiagF32 fc{(float)g.idx, (float)g.idz, (float)f.idh[0][0], (float)f.idh[0][1], (float)f.idh[2][0],
+                   (float)f.idh[2][1], (float)f.idh[1][0], (float)f.idh[1][1], (float)g.dy};
+  ex.launch(dim3(nblk), dim3(DG_THREADS), 0, StateDiag<T>{g, f, b.flags32, ds, s, use_q, fc, partial});
   ex.launch(dim3(1), dim3(DGF_THREADS), 0, StateDiagFinal{g, partial, ds, dt, nblk});
 }
 

@@ -1281,9 +1281,30 @@ ibm_status ibm_create_grid_stretched(const ibm_grid_desc* desc, const double* y_
     if (!t2.empty()) ysw2f = (float*)upload_vec<float>(h, t2);
     f32_ok = yswf && (t2.empty() || ysw2f);
   }
+  // rows of the tagging pre-screen: FP32 position, wall-normal side of the
+  // node's local cell, distances to the rows below and above
+  float4* rowf = nullptr;
+  {
+    std::vector<float> rf(8ull * (ny + 1), 0.0f);
+    for (int half = 0; half < 2; ++half)
+      for (int j = 0; j <= ny; ++j) {
+        const double* yr = half ? yc : yv;   // [j + 1] = row j; one mirrored row beyond each wall
+        if (half && j == ny) continue;      // (centre rows end at ny - 1)
+        const double y = yr[j + 1], ylo = yr[j], yhi = yr[j + 2];
+        const double hy = half ? hc[j] : hf[j];
+        float* q = rf.data() + 4ull * (half * (ny + 1) + j);
+        q[0] = (float)y;
+        q[1] = (float)hy;
+        q[2] = (float)(y - ylo);
+        q[3] = (float)(yhi - y);
+      }
+    rowf = (float4*)dalloc(h, rf.size() * sizeof(float));
+    if (rowf && cudaMemcpy(rowf, rf.data(), rf.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+      rowf = nullptr;
+  }
   const size_t nspec = (size_t)h->g.nz * h->g.ny * h->g.nkx;
   h->pal = (double*)dalloc(h, nspec * 8);
-  if (!h->ytab || !h->pal || (!t2.empty() && !ysw2) || !f32_ok) {
+  if (!h->ytab || !h->pal || (!t2.empty() && !ysw2) || !f32_ok || !rowf) {
     ibm_destroy(h);
     return IBM_ERR_OOM;
   }
@@ -1297,6 +1318,7 @@ ibm_status ibm_create_grid_stretched(const ibm_grid_desc* desc, const double* y_
   h->g.yt.ysw2 = ysw2;
   h->g.yt.yswf = yswf;
   h->g.yt.ysw2f = ysw2f;
+  h->g.yt.rowf = rowf;
   h->g.yt.hmax = smax;
   h->ysp_min = smin;
   launch_build_poisson_tables_nu(h->g, h->lamx, h->lamz, h->pcp, h->pinv, h->pal, h->user);

@@ -123,10 +123,27 @@ __device__ __forceinline__ void tri_setup(const Blk& bk, const Geo& g, const Sur
   const double aa = ddot(TC.ab, TC.ab), abac = ddot(TC.ab, TC.ac), cc = ddot(TC.ac, TC.ac);
   const double bcbc = ddot(TC.bc, TC.bc);
   const double den = dsub(dmul(aa, cc), dmul(abac, abac));
-  const double dmin = fmin(del[0], fmin(del[1], del[2])), dmax = fmax(del[0], fmax(del[1], del[2]));
+  double dmin = fmin(del[0], fmin(del[1], del[2])), dmax = fmax(del[0], fmax(del[1], del[2]));
+  bool rows_ok = true;
+  if (g.yt.yc) {
+    // non-uniform rows: the local cells of the rows in the triangle's box
+    // (and one beyond), from the row table, decide the scale
+    dmin = fmin(del[0], del[2]);
+    dmax = fmax(del[0], del[2]);
+    const int ny = g.ny;
+    for (int half = 0; half < 2 && rows_ok; ++half) {
+      const int c = half ? 0 : 1;
+      const int j0 = R.n0[c][1] - 1, j1 = R.n0[c][1] + R.ext[c][1];
+      if (R.ext[c][1] > 64) rows_ok = false;
+      for (int j = max(j0, half ? 0 : 1); j <= min(j1, half ? ny - 1 : ny - 1) && rows_ok; ++j) {
+        const float4 r = g.yt.rowf[half * (ny + 1) + j];
+        dmin = fmin(dmin, (double)fmin(r.y, fmin(r.z, r.w)));
+        dmax = fmax(dmax, (double)fmax(r.y, fmax(r.z, r.w)));
+      }
+    }
+  }
   const double lmax2 = fmax(aa, fmax(cc, bcbc));
-  // (its bounds assume the uniform lattice: off on the non-uniform grid)
-  R.screen = !g.yt.yc && den > 0.05 * aa * cc && lmax2 <= 64.0 * dmin * dmin && dmax <= 4.0 * dmin &&
+  R.screen = rows_ok && den > 0.05 * aa * cc && lmax2 <= 256.0 * dmin * dmin && dmax <= 4.0 * dmin &&
              total < (1ll << 30);
   TriF32& F = R.f;
 #pragma unroll
@@ -151,6 +168,9 @@ __device__ __forceinline__ void tri_setup(const Blk& bk, const Geo& g, const Sur
   F.ibc = (float)(1.0 / bcbc);
   F.iden = (float)(1.0 / den);
   F.diag2 = (float)g.diag2;
+  F.ay = (float)A[1];
+  F.ymn = (float)fmin(A[1], fmin(B[1], C[1]));
+  F.ymx = (float)fmax(A[1], fmax(B[1], C[1]));
   s.rec[t] = R;
 }
 struct TriSetup {
@@ -173,11 +193,15 @@ struct TriSetup {
 // margins (0.4% of |N|^2 + del |N_d|) bound the FP32 error of N relative to
 // the cell.  That error is about eps_32 * L / sin^2(theta) for a triangle of
 // edge L and smallest angle theta; the screen is used only where this stays
-// below 1e-4 of the margin's scale (sin^2 > 0.05, edges within 8 cells, cell
-// aspect ratio within 4), else every pair goes to the exact test.  Tags are
-// decided by the FP64 test alone.
-__device__ __forceinline__ void screen_eval(const TriF32& F, int c, const int idx3[3], float& n2, float& lowest,
-                                            float& scale) {
+// below 1e-3 of the margin's scale (sin^2 > 0.05, edges within 16 cells, cell
+// aspect ratio within 4), else every pair goes to the exact test.  On the
+// non-uniform wall-normal grid the cell is the node's own (its row's
+// spacing, the rows bracketing it for the neighbour test), and the row's
+// position is its FP32 table value less the vertex's (an error of about
+// 1e-7 of the box, well inside the margins).  Tags are decided by the FP64
+// test alone.
+__device__ __forceinline__ void screen_eval(const TriF32& F, const Geo& g, int c, const int idx3[3], float& n2,
+                                            float& lowest, float& scale, float& diag2) {
   float p[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
@@ -185,6 +209,15 @@ __device__ __forceinline__ void screen_eval(const TriF32& F, int c, const int id
     const float pf = (float)(idx3[d] - F.ia[d][0]) * F.del[d] - F.fr[d][0];
     const float ph = (float)(idx3[d] - F.ia[d][1]) * F.del[d] - F.fr[d][1];
     p[d] = d == c ? pf : ph;
+  }
+  float dlo = F.del[1], dhi = F.del[1];
+  diag2 = F.diag2;
+  if (g.yt.rowf) {
+    const float4 r = g.yt.rowf[(c != 1) * (g.ny + 1) + idx3[1]];
+    p[1] = r.x - F.ay;
+    dlo = r.z;
+    dhi = r.w;
+    diag2 = (F.del[0] * F.del[0] + r.y * r.y) + F.del[2] * F.del[2];
   }
   const float d1 = F.ab[0] * p[0] + F.ab[1] * p[1] + F.ab[2] * p[2];
   const float d2 = F.ac[0] * p[0] + F.ac[1] * p[1] + F.ac[2] * p[2];
@@ -220,31 +253,43 @@ __device__ __forceinline__ void screen_eval(const TriF32& F, int c, const int id
 #pragma unroll
   for (int d = 0; d < 3; ++d) N[d] = p[d] - X[d];
   n2 = N[0] * N[0] + N[1] * N[1] + N[2] * N[2];
-  // N . (neighbour - X) = |N|^2 -+ del_d N_d: the smallest over the six
+  // N . (neighbour - X) = |N|^2 -+ del_d N_d: the smallest over the six (in
+  // y the neighbour on N's side: the row below if N_y > 0, else above)
   lowest = 3.4e38f;
   scale = 0.f;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    const float t = F.del[d] * fabsf(N[d]);
+    const float dd = d == 1 ? (N[1] > 0.f ? dlo : dhi) : F.del[d];
+    const float t = dd * fabsf(N[d]);
     lowest = fminf(lowest, n2 - t);
-    scale = fmaxf(scale, t);
+    scale = fmaxf(scale, d == 1 ? fmaxf(dlo, dhi) * fabsf(N[1]) : t);
   }
 }
 
 // The pair may pass the exact test (false: it certainly fails).
-__device__ __forceinline__ bool screen_maybe(const TriF32& F, float n2, float lowest, float scale) {
-  return !(n2 > F.diag2 * 1.004f) && lowest < 4e-3f * (n2 + scale) + 1e-9f * F.diag2;
+__device__ __forceinline__ bool screen_maybe(float diag2, float n2, float lowest, float scale) {
+  return !(n2 > diag2 * 1.004f) && lowest < 4e-3f * (n2 + scale) + 1e-9f * diag2;
 }
 // The pair certainly passes the exact test (the same margins, other side).
-__device__ __forceinline__ bool screen_certain(const TriF32& F, float n2, float lowest, float scale) {
-  return n2 <= F.diag2 * 0.996f && lowest < -(4e-3f * (n2 + scale) + 1e-9f * F.diag2);
+__device__ __forceinline__ bool screen_certain(float diag2, float n2, float lowest, float scale) {
+  return n2 <= diag2 * 0.996f && lowest < -(4e-3f * (n2 + scale) + 1e-9f * diag2);
 }
 // Bounds of the exact |N|^2 from the FP32 one: the FP32 error of |N|^2 is
 // below 1e-4 diag^2 wherever the screen runs (see above); the bounds leave
 // 4e-3 relative plus 1e-3 diag^2.
-__device__ __forceinline__ float n2_upper(const TriF32& F, float n2) { return n2 * 1.004f + 1e-3f * F.diag2; }
-__device__ __forceinline__ float n2_lower(const TriF32& F, float n2) { return n2 * 0.996f - 1e-3f * F.diag2; }
+__device__ __forceinline__ float n2_upper(float diag2, float n2) { return n2 * 1.004f + 1e-3f * diag2; }
+__device__ __forceinline__ float n2_lower(float diag2, float n2) { return n2 * 0.996f - 1e-3f * diag2; }
 
+
+// Non-uniform rows: row j of component c's lattice lies inside the box of
+// Algorithm 1 (margin: the node's own cell), with a margin of 1e-3 of the
+// cell over the FP32 errors (about 1e-7 of the box) -- a pair the screen
+// calls certain must pass the exact test, box included.
+__device__ __forceinline__ bool row_inside_f(const Geo& g, const TriF32& F, int c, int j) {
+  const float4 r = g.yt.rowf[(c != 1) * (g.ny + 1) + j];
+  const float m = 1e-3f * r.y;
+  return r.x > F.ymn - r.y + m && r.x < F.ymx + r.y - m;
+}
 
 // pair n of a triangle's box -> (component, unwrapped lattice indices)
 __device__ __forceinline__ void decode_pair(const TriRec* __restrict__ rec, long long n, int& c, long long idx3[3]) {
@@ -330,16 +375,18 @@ __device__ __forceinline__ void tag_pairs(const Blk& bk, const Geo& g, const Sur
         long long i3[3];
         decode_pair(rec, n, c, i3);
         const int idx3[3] = {(int)i3[0], (int)i3[1], (int)i3[2]};
-        float n2, lowest, scale;
-        screen_eval(F, c, idx3, n2, lowest, scale);
+        float n2, lowest, scale, d2;
+        screen_eval(F, g, c, idx3, n2, lowest, scale, d2);
+        // (non-uniform rows: a row outside the box of Algorithm 1, whose
+        // margin is the node's own cell, is left to the exact test)
         if (PHASE == 0) {
-          if (screen_certain(F, n2, lowest, scale)) {
+          if (screen_certain(d2, n2, lowest, scale) && !(g.yt.rowf && !row_inside_f(g, F, c, idx3[1]))) {
             ni = node_of(c, i3);
-            hit = atomicMin(ub + ni, __float_as_uint(n2_upper(F, n2))) == 0xFFFFFFFFu;   // first touch
+            hit = atomicMin(ub + ni, __float_as_uint(n2_upper(d2, n2))) == 0xFFFFFFFFu;   // first touch
           }
-        } else if (screen_maybe(F, n2, lowest, scale)) {
+        } else if (screen_maybe(d2, n2, lowest, scale)) {
           const unsigned u = __ldcg(ub + node_of(c, i3));
-          hit = u == 0xFFFFFFFFu || n2_lower(F, n2) <= __uint_as_float(u);
+          hit = u == 0xFFFFFFFFu || n2_lower(d2, n2) <= __uint_as_float(u);
         }
       } else {
         hit = true;   // phase 1 only: every pair of an unscreened triangle is tested exactly
