@@ -95,6 +95,7 @@ __host__ __device__ inline int wrapi(long long i, int n) {
 // reduction results, so a captured graph never bakes values in.
 struct DevState {
   double fb[3];                  // uniform body force
+  float fbf[3];                  // the same in FP32 (the FP32 kernels read it without a conversion)
   double qf[2];                  // q_F of each sub-stage
   float qf_hi[2], qf_lo[2];      // q_F as an unevaluated FP32 pair (mixed correction)
   double sum_a[2];               // sum over C_B of D uhat dV per sub-stage

@@ -225,7 +225,18 @@ __device__ __forceinline__ void rhs(const Blk& bk, const Geo& g, const Fields<T>
   const T gs = cf.gs;
   const T q = (T)0.25;
   const T cg = cf.cg, cr = cf.cr, ca = cf.ca, cv = cf.cv, tdt = cf.dt;
-  const T fbx = cf.fba * (T)ds->fb[0], fby = cf.fba * (T)ds->fb[1], fbz = cf.fba * (T)ds->fb[2];
+  // (the FP32 path reads the force's FP32 copy: a conversion would occupy
+  // the narrow FP64 pipe once per thread)
+  T fbx, fby, fbz;
+  if constexpr (sizeof(T) == 4) {
+    fbx = cf.fba * ds->fbf[0];
+    fby = cf.fba * ds->fbf[1];
+    fbz = cf.fba * ds->fbf[2];
+  } else {
+    fbx = cf.fba * (T)ds->fb[0];
+    fby = cf.fba * (T)ds->fb[1];
+    fbz = cf.fba * (T)ds->fb[2];
+  }
   const long long pv = (long long)(ny + 1) * nx;   // v plane stride (k)
   const long long pu = (long long)ny * nx;         // u, w, p plane stride
   const T* __restrict__ U = f.u;

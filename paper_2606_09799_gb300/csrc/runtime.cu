@@ -93,6 +93,9 @@ __global__ void k_set_force(DevState* ds, double fx, double fy, double fz) {
   ds->fb[0] = fx;
   ds->fb[1] = fy;
   ds->fb[2] = fz;
+  ds->fbf[0] = (float)fx;
+  ds->fbf[1] = (float)fy;
+  ds->fbf[2] = (float)fz;
 }
 
 __device__ __forceinline__ void step_done(const Blk&, DevState* ds) { ds->steps += 1; }

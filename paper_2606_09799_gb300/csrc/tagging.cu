@@ -77,8 +77,9 @@ __device__ __forceinline__ void tri_setup(const Blk& bk, const Geo& g, const Sur
   TriRec R;
   tri_const(A, B, C, R.tc);
   const TriConst& TC = R.tc;
+  // (the centroid only picks a node's periodic image: any rounding serves)
 #pragma unroll
-  for (int d = 0; d < 3; ++d) R.cen[d] = (A[d] + B[d] + C[d]) / 3.0;
+  for (int d = 0; d < 3; ++d) R.cen[d] = (A[d] + B[d] + C[d]) * (1.0 / 3.0);
   const double del[3] = {g.dx, g.dy, g.dz};
   const double idel[3] = {g.idx, g.idy, g.idz};
   double lo[3], hi[3];
@@ -160,13 +161,15 @@ __device__ __forceinline__ void tri_setup(const Blk& bk, const Geo& g, const Sur
       F.fr[d][hf] = (float)(A[d] - (q + off) * del[d]);
     }
   }
+  // (FP32 reciprocals: the screen's margins are far wider than their error,
+  // and an FP64 division is costly on this GPU)
   F.aa = (float)aa;
   F.abac = (float)abac;
   F.cc = (float)cc;
-  F.iaa = (float)(1.0 / aa);
-  F.icc = (float)(1.0 / cc);
-  F.ibc = (float)(1.0 / bcbc);
-  F.iden = (float)(1.0 / den);
+  F.iaa = 1.0f / F.aa;
+  F.icc = 1.0f / F.cc;
+  F.ibc = 1.0f / (float)bcbc;
+  F.iden = 1.0f / (float)den;
   F.diag2 = (float)g.diag2;
   F.ay = (float)A[1];
   F.ymn = (float)fmin(A[1], fmin(B[1], C[1]));
