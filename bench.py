@@ -126,10 +126,12 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # roofline bookkeeping: algorithmic bytes (FP32/mixed) and FP64 flops per cell
 # ---------------------------------------------------------------------------
-def algorithmic_bytes_per_cell(stage: str, word: int) -> float:
+def algorithmic_bytes_per_cell(stage: str, word: int, pairs: bool = False) -> float:
     """Compulsory words per cell of each kernel group and sub-stage: one read
     of every input field, one write of every output field (the sparse IB
-    part is counted per forcing node elsewhere)."""
+    part is counted per forcing node elsewhere).  pairs: the mixed path's
+    velocity state is an FP32 (hi, lo) pair, two words per velocity node
+    where a kernel reads or writes the state."""
     reads_writes = {
         "rhs": (5.5, 4.5),          # u, v, w, p (+ H^{s-1} on sub-stage 2, averaged) -> R x3 (+ H x3 on sub-stage 1)
         "sweep_x": (3, 3),
@@ -142,6 +144,11 @@ def algorithmic_bytes_per_cell(stage: str, word: int) -> float:
         "fft_x_inv": (1, 1),
         "project": (5, 4),          # uhat x3, phi, p -> u x3, p
     }
+    if pairs:
+        reads_writes.update({
+            "sweep_y": (9, 6),      # du x3 and u^s x3 as (hi, lo) -> uhat x3 as (hi, lo)
+            "project": (9, 7),      # uhat x3 (hi, lo), p, phi, phi2 -> u x3 (hi, lo), p
+        })
     r, w = reads_writes.get(stage, (0, 0))
     return (r + w) * word
 
@@ -397,7 +404,7 @@ def gpu_arm(args):
             work = fp64_flops_per_cell(name) * cells
             g = dict(bound="alu", achieved=work / (avg_ms / 1e3) / 1e12, peak=fp64_peak, unit="TFLOP/s")
         elif algorithmic_bytes_per_cell(name, 4) > 0:
-            work = algorithmic_bytes_per_cell(name, 4) * cells
+            work = algorithmic_bytes_per_cell(name, 4, pairs=args.precision == "mixed") * cells
             g = dict(bound="hbm", achieved=work / (avg_ms / 1e3) / 1e9, peak=hbm, unit="GB/s")
         else:
             continue
@@ -561,7 +568,7 @@ def stretched_run(args, dev, stream, flush, world, wall, precision):
     if precision == "mixed":
         peak = measured_peaks().get("hbm_gbs", 6800.0)
         for name, (tot_ms, ngroups) in prof.items():
-            b = algorithmic_bytes_per_cell(name, 4)
+            b = algorithmic_bytes_per_cell(name, 4, pairs=True)
             if ngroups == 0 or tot_ms <= 0 or b <= 0:
                 continue
             avg_ms = tot_ms / (ngroups * 2)
