@@ -266,6 +266,20 @@ def fp64_flops_per_cell(stage: str) -> float:
             "fft_z_fwd": 40.0, "tri_y": 8.0, "fft_z_inv": 40.0, "fft_x_inv": 40.0, "project": 30.0}.get(stage, 0.0)
 
 
+def set_budget(sim, args, dx):
+    """Divergence budget of the mixed path's correction solve: the solve runs
+    in a sub-stage only when the first solve leaves max |D u - q| over the
+    fluid cells above it (U_ref = 1, so the budget is a multiple of 1/dx)."""
+    if sim.precision == "mixed" and args.div_budget > 0.0:
+        sim.set_div_budget(args.div_budget / dx)
+
+
+def correction_record(args, diag, substages, dx):
+    """How many of the timed sub-stages took the correction solve."""
+    return {"budget_U_per_dx": args.div_budget, "taken": int(diag.get("corr_timed", diag["corr_solves"])),
+            "substages": int(substages), "last_first_solve_residual_U_per_dx": diag["div_first"] * dx}
+
+
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
@@ -299,6 +313,7 @@ def gpu_arm(args):
     for prec in order:
         sim = ibm.Simulation(wl.nx, wl.ny, wl.nz, wl.lx, wl.ly, wl.lz, re=wl.re, dt=wl.dt, precision=prec,
                              stream=stream.cuda_stream)
+        set_budget(sim, args, wl.lx / wl.nx)
         sim.set_surface(surf[0][0], surf[0][1], tri)
         for s in range(W):
             sim.set_surface(dxyz[s], dvel[s])
@@ -310,6 +325,7 @@ def gpu_arm(args):
         else:
             tune = sim.autotune(steps=3) if args.autotune else None   # launch shapes (state restored)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        corr0 = sim.diag()["corr_solves"]
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
@@ -325,6 +341,7 @@ def gpu_arm(args):
             torch.distributed.barrier()
         ms = sum(a.elapsed_time(b) for a, b in ev)
         diag = sim.diag()
+        diag["corr_timed"] = diag["corr_solves"] - corr0
         sim.sync()
         ms = max_over_ranks(ms, dev, world)
         # stage profile of the same workload (CUDA events recorded on the launching stream)
@@ -458,6 +475,8 @@ def gpu_arm(args):
         line[prec] = {"value": world * cells * K / (r["ms"] / 1e3) / 1e9, "ms_per_step": r["ms"] / K,
                       "slip_l1": dg["slip_l1"], "clocks": r["clocks"], "tune": r["tune"],
                       "div_max_U_per_dx": dg["div_max"] * wl.lx / wl.nx, "ke": dg["ke"], "cfl": dg["cfl"]}
+        if prec == "mixed":
+            line[prec]["correction"] = correction_record(args, dg, 2 * K, wl.lx / wl.nx)
     if batched is not None:
         line["batched"] = batched
     if ab is not None:
@@ -489,6 +508,7 @@ def ab_leg(args, wl, dxyz, dvel, surf, dev, stream, flush, world, tune):
     K, W = args.steps, args.warmup
     sim = ibm.Simulation(wl.nx, wl.ny, wl.nz, wl.lx, wl.ly, wl.lz, re=wl.re, dt=wl.dt, precision=args.precision,
                          scheme="ab", stream=stream.cuda_stream)
+    set_budget(sim, args, wl.lx / wl.nx)
     if tune:
         sim.set_tune(**{k: v for k, v in tune.items() if k != "ms_per_step"})
     sim.set_surface(surf[0][0], surf[0][1], wl.tri)
@@ -543,11 +563,14 @@ def stretched_run(args, dev, stream, flush, world, wall, precision):
     sim = ibm.Simulation(n, n, n, re=200.0, dt=5e-4, precision=precision, stream=stream.cuda_stream, y_faces=yf)
     sim.set_fields(*inputs.random_fields(n, n, n, seed=31, amp=0.1))
     sim.set_body_force(8.0 / 200.0, 0.0, 0.0)
+    hmin = float(np.min(np.diff(yf)))
+    set_budget(sim, args, hmin)
     if wall is not None:
         sim.set_surface(wall[0], np.zeros_like(wall[0]), wall[1])
     for _ in range(W):
         sim.step(1)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    corr0 = sim.diag()["corr_solves"]
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -558,7 +581,9 @@ def stretched_run(args, dev, stream, flush, world, wall, precision):
         ev[m][1].record(stream)
     torch.cuda.synchronize()
     ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), dev, world)
-    slip = sim.diag()["slip_l1"]
+    dg = sim.diag()
+    slip = dg["slip_l1"]
+    dg["corr_timed"] = dg["corr_solves"] - corr0
     prof = ibm.ibm_profile_stages(sim.h, 2)
     sim.close()
     # mixed path: every HBM-bound kernel group against the measured copy rate,
@@ -583,6 +608,8 @@ def stretched_run(args, dev, stream, flush, world, wall, precision):
             "cells": n ** 3, "steps": K, "value": whole_job_gcups(n ** 3, K, world, ms), "unit": UNIT,
             "ms_per_step": ms / K, "slip_l1": slip if wall is not None else None,
             "stages_ms_per_step": {k: v[0] / 2 for k, v in prof.items() if v[1] > 0},
+            "div_max_U_per_hmin": dg["div_max"] * hmin,
+            **({"correction": correction_record(args, dg, 2 * K, hmin)} if precision == "mixed" else {}),
             **({"stage_roofline": roof} if roof else {})}
 
 
@@ -616,6 +643,7 @@ def large_leg(args, dev, stream, flush):
             if wl.initial is not None:
                 sim.set_fields(*wl.initial())
             ibm.ibm_set_body_force(sim.h, *wl.body_force_at(0.0))
+            set_budget(sim, args, wl.lx / wl.nx)
             sim.set_surface(surf[0][0], surf[0][1], wl.tri)
             for s in range(W):
                 sim.set_surface(dx[s], dv[s])
@@ -623,6 +651,7 @@ def large_leg(args, dev, stream, flush):
             sim.sync()
             tune = sim.autotune(steps=2) if prec == "mixed" else None   # state saved and restored
             ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+            corr0 = sim.diag()["corr_solves"]
             torch.cuda.synchronize()
             for n in range(K):
                 flush.fill_(n & 0xFF)
@@ -636,6 +665,9 @@ def large_leg(args, dev, stream, flush):
             r = {"precision": prec, "cells": cells, "triangles": int(wl.tri.shape[0]), "steps": K, "warmup": W,
                  "ms_per_step": ms, "value": cells / (ms / 1e3) / 1e9, "unit": UNIT, "slip_l1": d["slip_l1"],
                  "div_max_U_per_dx": d["div_max"] * wl.lx / wl.nx, "cfl": d["cfl"]}
+            if prec == "mixed":
+                d["corr_timed"] = d["corr_solves"] - corr0
+                r["correction"] = correction_record(args, d, 2 * K, wl.lx / wl.nx)
             if len(precs) > 1:
                 # the state after the same W + K steps on both paths
                 shp = [(wl.nz, wl.ny, wl.nx), (wl.nz, wl.ny + 1, wl.nx), (wl.nz, wl.ny, wl.nx), (wl.nz, wl.ny, wl.nx)]
@@ -747,6 +779,7 @@ def batched_leg(args, dev, stream, flush, world):
         for w, ss in zip(wls, surf):
             g = ibm.Simulation(w.nx, w.ny, w.nz, w.lx, w.ly, w.lz, re=w.re, dt=w.dt, precision="mixed",
                                stream=stream.cuda_stream)
+            set_budget(g, args, w.lx / w.nx)
             g.set_surface(ss[0][0], ss[0][1], w.tri)
             sims.append(g)
         return sims
@@ -903,6 +936,8 @@ def main():
                     help="also record the no-slip error series of the heaving/pitching plate (opt-in)")
     ap.add_argument("--tune", default="", help="fixed launch shapes instead of autotuning, e.g. tri_y=3,sweep_zy=2")
     ap.add_argument("--batch-steps", type=int, default=20)
+    ap.add_argument("--div-budget", type=float, default=5e-8,
+                    help="mixed path: correction-solve budget on max |D u - q| in U_ref/dx (0: always correct)")
     ap.add_argument("--fp64-peak-tflops", type=float, default=0.0,
                     help="FP64 roof in TFLOP/s; 0 (default) measures it on the device (ibm_measure_alu_peaks)")
     args = ap.parse_args()

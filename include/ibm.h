@@ -83,7 +83,9 @@ enum { IBM_NOSLIP = 0, IBM_FREESLIP = 1 }; /* condition on the y walls */
  *                   velocity state kept as an unevaluated FP32 pair (hi + lo)
  *                   and a final correction solve on the residual divergence
  *                   computed in that pair arithmetic, so D u = q holds to
- *                   ~1e-12 of U/dx;
+ *                   ~1e-12 of U/dx (the correction runs in the sub-stages
+ *                   whose first-solve residual exceeds the divergence
+ *                   budget, ibm_set_div_budget);
  *   IBM_MIXED_FAST  as IBM_MIXED with an FP32 velocity state and a single
  *                   solve (divergence at the FP32 solve error, ~1e-6 U/dx). */
 enum { IBM_FP64 = 0, IBM_MIXED = 1, IBM_MIXED_FAST = 2 };
@@ -119,6 +121,10 @@ typedef struct {
                              (dV = dx h dz, h the cell height for u and w, the centre distance for v) */
   double cfl;             /* dt max over the cells of |u_c|/dx + |v_c|/h + |w_c|/dz, u_c the mean of the
                              cell's two faces of each component (the step's result) */
+  double div_first;       /* IBM_MIXED: max over C_F of |D u' - q| after the first Poisson solve of the
+                             step's sub-stages (u' the once-projected pair state, FP32), the residual
+                             that decides the correction solve; 0 in the other modes */
+  int64_t corr_solves;    /* IBM_MIXED: correction solves taken since the handle was created */
 } ibm_diag;
 
 /* Create a simulation on the current CUDA device.  stream is a cudaStream_t
@@ -165,6 +171,17 @@ ibm_status ibm_set_surface(ibm_handle h, int nverts, const double* xyz, const do
 /* Uniform volume force f of Eq. ns1 (e.g. a mean pressure gradient),
  * applied on the fluid nodes with the weight alpha of each sub-stage. */
 ibm_status ibm_set_body_force(ibm_handle h, double fx, double fy, double fz);
+
+/* IBM_MIXED: divergence budget of the correction solve (Eq. mod_div).  After
+ * the first Poisson solve of a sub-stage the device takes the largest
+ * |D u' - q| over the fluid cells C_F of the once-projected (hi, lo) state;
+ * the correction solve runs only when it exceeds `budget` (in the units of
+ * D u, velocity / length), otherwise its kernels return at once and the
+ * step keeps u'.  Default 0: the correction runs unless the residual is
+ * exactly zero.  A mixed run that must meet max |D u - q| <= b passes a
+ * budget below b (the first-solve residual is an FP32 value).  Other modes
+ * accept and ignore it.  IBM_ERR_ARG for a negative or NaN budget. */
+ibm_status ibm_set_div_budget(ibm_handle h, double budget);
 
 /* Overwrite the state u, v, w, p (layouts above; v's wall planes are taken
  * as given).  The non-linear history H^{n-1} of AB+CN is reset to zero (a

@@ -105,6 +105,10 @@ struct DevState {
   double div_max;                // max over C_F of |D u - q| after the last projection of the step
   double ke;                     // kinetic energy 1/2 sum u^2 dV of the step's result
   double cfl;                    // CFL number of the step's result
+  unsigned int res1[2];          // mixed path: bits of max over C_F of |D u' - q| (FP32) after the first solve
+                                 // of each sub-stage, u' the once-projected state
+  float div_budget;              // the correction solve runs when that residual exceeds it (NaN: runs)
+  unsigned long long ncorr;      // correction solves taken
   unsigned int err;              // ERR_* bits
   unsigned int ncand;            // candidates of the current step
   unsigned int ncand_prev;       // candidates of the previous step (sparse reset)

@@ -14,6 +14,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 #include "launch.h"
@@ -472,6 +473,38 @@ __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, 
 __device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
 
+// Largest |D u' - q| over the fluid cells after the first solve of the mixed
+// path (Eq. mod_div), kept as the bits of a non-negative FP32 value (their
+// integer order is the numbers' order; NaN sorts above every number).  The
+// first solve's forward transform clears the word, the correction solve's
+// forward transform folds every cell into it: a block maximum, then one
+// atomicMax per block, and only when the word does not already hold as much
+// (thousands of blocks would otherwise queue on one address).  Every thread
+// of the block calls this (the last warp may be partial).
+__device__ __forceinline__ void fold_residual(unsigned* res1, unsigned rmax) {
+  __shared__ unsigned wmax[32];
+  const unsigned tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const unsigned nt = blockDim.x * blockDim.y * blockDim.z;
+  const unsigned lanes = min(32u, nt - (tid & ~31u));
+  const unsigned mask = lanes == 32u ? 0xFFFFFFFFu : (1u << lanes) - 1u;
+  const unsigned m = __reduce_max_sync(mask, rmax);
+  if ((tid & 31u) == 0u) wmax[tid >> 5] = m;
+  __syncthreads();
+  if (tid < 32u) {
+    const unsigned nw = (nt + 31u) >> 5;
+    const unsigned b = __reduce_max_sync(nt >= 32u ? 0xFFFFFFFFu : (1u << nt) - 1u, tid < nw ? wmax[tid] : 0u);
+    if (tid == 0u && b > *reinterpret_cast<volatile unsigned*>(res1)) atomicMax(res1, b);
+  }
+}
+__device__ __forceinline__ void clear_residual(const Blk& bk, unsigned* res1) {
+  if (bk.x == 0 && bk.y == 0 && bk.z == 0 && threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0) *res1 = 0u;
+}
+// The correction solve is needed unless the first solve's residual is
+// within the budget (a NaN residual or budget always runs it).
+__device__ __forceinline__ bool correction_needed(const DevState* ds, int s) {
+  return !(__uint_as_float(ds->res1[s]) <= ds->div_budget);
+}
+
 // Right-hand side of Eq. elliptic_mod at cell (i, j, k), scaled by
 // 1/(alpha dt nx nz): mode 0 from the provisional state (bulk type), mode 3
 // the correction solve's rhs from the projected (hi, lo) state in pair
@@ -506,7 +539,7 @@ template <typename T>
 __device__ __forceinline__ T poisson_rhs(const Geo& g, const Fields<T>& f, const unsigned* __restrict__ flags32,
                                          const DevState* ds, int s, int use_q, double scale, int mode,
                                          const ProjCoef<T>& cf, const RowY<T>& ry, T qf, T qa, T qb, int i, int j,
-                                         int k) {
+                                         int k, unsigned& rmax) {
   const int n = g.nx, ny = g.ny;
   const long long pu = (long long)ny * n, pv = (long long)(ny + 1) * n;
   const T sc = (T)scale, idx = (T)g.idx, idy = (T)g.idy, idz = (T)g.idz;
@@ -554,7 +587,9 @@ __device__ __forceinline__ T poisson_rhs(const Geo& g, const Fields<T>& f, const
       const float qh = use_q == 2 ? (float)f.qk[cell] : (use_q ? ds->qf_hi[s] : 0.0f);
       const float ql = use_q == 1 ? ds->qf_lo[s] : 0.0f;
       two_sum(a2, -qh, a3, e3);
-      r = (T)((a3 + (((e1 + e2) + e3) + ((sx + sy) + sz) - ql)) * (float)scale);
+      const float d = a3 + (((e1 + e2) + e3) + ((sx + sy) + sz) - ql);   // D u' - q
+      rmax = max(rmax, __float_as_uint(d) & 0x7FFFFFFFu);                 // |d| (NaN above every number)
+      r = (T)(d * (float)scale);
     }
   } else if (!(use_q && (fl & FLAG_B))) {
     const long long v0 = (long long)k * pv + (long long)j * n + i;
@@ -580,7 +615,7 @@ __device__ __forceinline__ T poisson_rhs(const Geo& g, const Fields<T>& f, const
 template <typename T>
 __device__ __forceinline__ void fft_x_fwd(const Blk& bk, const Geo& g, const Fields<T>& f, const unsigned* __restrict__ flags32, const T* __restrict__ tw,
                             const FftPlan& plan, int lines_per_block, const DevState* ds, int s, int use_q,
-                            double scale, int mode, const ProjCoef<T>& cf) {
+                            double scale, int mode, const ProjCoef<T>& cf, unsigned* res1) {
   using C = typename Cplx<T>::type;
   extern __shared__ unsigned char smem_raw[];
   C* bufa = reinterpret_cast<C*>(smem_raw);
@@ -590,6 +625,8 @@ __device__ __forceinline__ void fft_x_fwd(const Blk& bk, const Geo& g, const Fie
   const int line0 = bk.x * lines_per_block;
   const T qf = use_q ? (T)ds->qf[s] : (T)0;
   const T qa = use_q == 2 ? (T)ds->qa[s] : (T)0, qb = use_q == 2 ? (T)ds->qb[s] : (T)0;
+  if (mode == 0) clear_residual(bk, res1);
+  unsigned rmax = 0u;
   // load: rows 2 l and 2 l + 1 of line l; divergence in the bulk type
   for (int l = threadIdx.y; l < lines_per_block; l += blockDim.y) {
     int jj[2], kk[2];
@@ -609,13 +646,14 @@ __device__ __forceinline__ void fft_x_fwd(const Blk& bk, const Geo& g, const Fie
       for (int hh = 0; hh < 2; ++hh) {
         if (!ok[hh]) continue;
         const T r = poisson_rhs<T>(g, f, flags32, ds, s, use_q, scale, mode, cf, row_y<T>(g, f, cf, jj[hh]), qf, qa,
-                                   qb, i, jj[hh], kk[hh]);
+                                   qb, i, jj[hh], kk[hh], rmax);
         if (hh == 0) z.x = r;
         else z.y = r;
       }
       bufa[l * n + i] = z;
     }
   }
+  if (mode == 3) fold_residual(res1, rmax);
   const int res = fft_lines<T, false>(bufa, bufb, lines_per_block, plan, reinterpret_cast<const C*>(tw));
   const C* out = res == 0 ? bufa : bufb;
   C* spec = reinterpret_cast<C*>(f.spec);
@@ -650,7 +688,8 @@ struct FftXFwd {
   double scale;
   int mode;
   ProjCoef<T> cf;
-  __device__ __forceinline__ void operator()(const Blk& bk) const { fft_x_fwd<T>(bk, g, f, flags32, tw, plan, lines_per_block, ds, s, use_q, scale, mode, cf); }
+  unsigned* res1;   // the sub-stage's residual word
+  __device__ __forceinline__ void operator()(const Blk& bk) const { fft_x_fwd<T>(bk, g, f, flags32, tw, plan, lines_per_block, ds, s, use_q, scale, mode, cf, res1); }
 };
 
 // inverse x transform: two half-spectra -> one complex line -> two real rows of phi
@@ -717,7 +756,7 @@ __device__ __forceinline__ void fft_plane_fwd(const Blk& bk, const Geo& g, const
                                               const unsigned* __restrict__ flags32, const T* __restrict__ twx,
                                               const T* __restrict__ twz, const FftPlan& px, const FftPlan& pz, int wbuf,
                                               int cz, const DevState* ds, int s, int use_q, double scale, int mode,
-                                              const ProjCoef<T>& cf) {
+                                              const ProjCoef<T>& cf, unsigned* res1) {
   using C = typename Cplx<T>::type;
   extern __shared__ unsigned char smem_raw[];
   const int nx = g.nx, nz = g.nz, nkx = g.nkx, ny = g.ny;
@@ -730,6 +769,8 @@ __device__ __forceinline__ void fft_plane_fwd(const Blk& bk, const Geo& g, const
   const T qa = use_q == 2 ? (T)ds->qa[s] : (T)0, qb = use_q == 2 ? (T)ds->qb[s] : (T)0;
   const int nlines = nz / 2;
   const RowY<T> ry = row_y<T>(g, f, cf, j);
+  if (mode == 0) clear_residual(bk, res1);
+  unsigned rmax = 0u;
   // x: lc complex lines (row pairs) at a time into S
   for (int l0 = 0; l0 < nlines; l0 += lc) {
     const int nl = min(lc, nlines - l0);
@@ -739,8 +780,8 @@ __device__ __forceinline__ void fft_plane_fwd(const Blk& bk, const Geo& g, const
       const int l = t / nx, i = t - l * nx;
       const int k0 = 2 * (l0 + l);
       C z;
-      z.x = poisson_rhs<T>(g, f, flags32, ds, s, use_q, scale, mode, cf, ry, qf, qa, qb, i, j, k0);
-      z.y = poisson_rhs<T>(g, f, flags32, ds, s, use_q, scale, mode, cf, ry, qf, qa, qb, i, j, k0 + 1);
+      z.x = poisson_rhs<T>(g, f, flags32, ds, s, use_q, scale, mode, cf, ry, qf, qa, qb, i, j, k0, rmax);
+      z.y = poisson_rhs<T>(g, f, flags32, ds, s, use_q, scale, mode, cf, ry, qf, qa, qb, i, j, k0 + 1, rmax);
       bufa[t] = z;
     }
     const int res = fft_lines<T, false>(bufa, bufb, nl, px, reinterpret_cast<const C*>(twx));
@@ -759,6 +800,7 @@ __device__ __forceinline__ void fft_plane_fwd(const Blk& bk, const Geo& g, const
       S[(k0 + 1) * nkx + kx] = Xb;
     }
   }
+  if (mode == 3) fold_residual(res1, rmax);
   // z: cz columns at a time (any cz: the host balances the chunks), strided
   // lines in the work buffers, to global
   C* spec = reinterpret_cast<C*>(f.spec);
@@ -797,8 +839,9 @@ struct FftPlaneFwd {
   double scale;
   int mode;
   ProjCoef<T> cf;
+  unsigned* res1;   // the sub-stage's residual word
   __device__ __forceinline__ void operator()(const Blk& bk) const {
-    fft_plane_fwd<T>(bk, g, f, flags32, twx, twz, px, pz, wbuf, cz, ds, s, use_q, scale, mode, cf);
+    fft_plane_fwd<T>(bk, g, f, flags32, twx, twz, px, pz, wbuf, cz, ds, s, use_q, scale, mode, cf, res1);
   }
 };
 
@@ -1666,7 +1709,8 @@ void launch_build_poisson_tables(const Geo& g, const double* lamx, const double*
 //         then that of the correction phi2, each subtracted as a pair update;
 //         the pressure takes phi + phi2
 template <typename T>
-__device__ __forceinline__ void project(const Blk& bk, const Geo& g, const Fields<T>& f, const ProjCoef<T>& cf, int mode) {
+__device__ __forceinline__ void project(const Blk& bk, const Geo& g, const Fields<T>& f, const ProjCoef<T>& cf, int mode,
+                                       DevState* ds, int s) {
   const int nx = g.nx, ny = g.ny, nz = g.nz;
   const long long pu = (long long)ny * nx, pv = (long long)(ny + 1) * nx;
   const int i = bk.x * blockDim.x + threadIdx.x;
@@ -1683,7 +1727,12 @@ __device__ __forceinline__ void project(const Blk& bk, const Geo& g, const Field
   const T a0 = ph[r0 + i], aw = ph[r0 + im], ae = ph[r0 + ip], ab = ph[rkm + i], af = ph[rkp + i];
   const T as = j > 0 ? ph[r0 - nx + i] : a0, an = j + 1 < ny ? ph[r0 + nx + i] : a0;
   T b0 = (T)0, bw = (T)0, be = (T)0, bb = (T)0, bf = (T)0, bs = (T)0, bn = (T)0;
-  if (mode == 3) {
+  // phi2 = 0 when the correction solve was skipped (the pair updates by -0
+  // below then leave the state as the first projection made it)
+  const bool corr = mode == 3 && correction_needed(ds, s);
+  if (mode == 3 && corr && bk.x == 0 && bk.y == 0 && bk.z == 0 && threadIdx.x == 0 && threadIdx.y == 0)
+    ds->ncorr += 1;
+  if (corr) {
     const T* __restrict__ p2 = f.phi2;
     b0 = p2[r0 + i];
     bw = p2[r0 + im];
@@ -1760,7 +1809,24 @@ struct Project {
   Fields<T> f;
   ProjCoef<T> cf;
   int mode;
-  __device__ __forceinline__ void operator()(const Blk& bk) const { project<T>(bk, g, f, cf, mode); }
+  DevState* ds;   // mode 3: the correction-solve decision of sub-stage s
+  int s;
+  __device__ __forceinline__ void operator()(const Blk& bk) const { project<T>(bk, g, f, cf, mode, ds, s); }
+};
+
+// A kernel of the correction solve: does its work only when the first
+// solve's residual exceeds the budget (every block reads the decision the
+// correction's forward transform completed before this launch).
+template <class Op>
+struct Gated {
+  static constexpr int kThreads = Op::kThreads;
+  Op op;
+  const DevState* ds;
+  int s;
+  __device__ __forceinline__ void operator()(const Blk& bk) const {
+    if (!correction_needed(ds, s)) return;
+    op(bk);
+  }
 };
 
 // ---------------------------------------------------------------------------
@@ -2022,41 +2088,54 @@ void launch_poisson(const Geo& g, const Fields<T>& f, const TagBuffers& b, const
   const int tsm = 64ll * 8 * sh.ny <= 160 * 1024 ? 64 : (32ll * 8 * sh.ny <= 160 * 1024 ? 32 : 0);
   int tri = tu.tri_y == 2 || sh.ny > 32 * TRI_SEG ? 2 : 1;
   if (tu.tri_y == 3 && tsm > 0) tri = 3;
+  // the kernels of the correction solve after its forward transform run
+  // gated: they return at once when the first solve met the budget
+  bool gate = false;
+  auto glaunch = [&](dim3 gr, dim3 bl, size_t sm, const auto& op) {
+    using Op = std::decay_t<decltype(op)>;
+    if constexpr (sizeof(T) == 4) {
+      if (gate) {
+        ex.launch(gr, bl, sm, Gated<Op>{op, ds, sg.s});
+        return;
+      }
+    }
+    ex.launch(gr, bl, sm, op);
+  };
   auto tri_solve = [&]() {
     if (tb.pal) {   // non-uniform wall-normal spacing
       if (tu.tri_y == 2 || sh.ny > 32 * TRI_SEG) {
-        ex.launch(dim3((unsigned)((2 * tlines + 127) / 128)), dim3(128), 0, TriYNU<T>{g, f, tb.cp, tb.inv, tb.pal});
+        glaunch(dim3((unsigned)((2 * tlines + 127) / 128)), dim3(128), 0, TriYNU<T>{g, f, tb.cp, tb.inv, tb.pal});
       } else if (sh.ny <= 8 * TRI_SEG) {
         const long long warps = (long long)((g.nkx + 3) / 4) * g.nz;
-        ex.launch(dim3((unsigned)((warps * 32 + 127) / 128)), dim3(128), 0,
+        glaunch(dim3((unsigned)((warps * 32 + 127) / 128)), dim3(128), 0,
                   TriYWarpNU<T, 8>{g, f, tb.cp, tb.inv, tb.pal});
       } else if (sh.ny <= 16 * TRI_SEG) {
         const long long warps = (long long)((g.nkx + 1) / 2) * g.nz;
-        ex.launch(dim3((unsigned)((warps * 32 + 127) / 128)), dim3(128), 0,
+        glaunch(dim3((unsigned)((warps * 32 + 127) / 128)), dim3(128), 0,
                   TriYWarpNU<T, 16>{g, f, tb.cp, tb.inv, tb.pal});
       } else {
         const long long warps = (long long)g.nkx * g.nz;
-        ex.launch(dim3((unsigned)((warps * 32 + 127) / 128)), dim3(128), 0,
+        glaunch(dim3((unsigned)((warps * 32 + 127) / 128)), dim3(128), 0,
                   TriYWarpNU<T, 32>{g, f, tb.cp, tb.inv, tb.pal});
       }
       return;
     }
     if (tri == 3) {
-      ex.launch(dim3((unsigned)((2 * tlines + tsm - 1) / tsm)), dim3(tsm), (size_t)tsm * 8 * sh.ny,
+      glaunch(dim3((unsigned)((2 * tlines + tsm - 1) / tsm)), dim3(tsm), (size_t)tsm * 8 * sh.ny,
                 TriYSmem<T>{g, f, tb.cp, tb.inv});
     } else if (tri == 1 && sh.ny <= 8 * TRI_SEG) {
       const long long warps = (long long)((g.nkx + 3) / 4) * g.nz;
-      ex.launch(dim3((unsigned)((warps * 32 + 127) / 128)), dim3(128), 0, TriYWarp<T, 8>{g, f, tb.cp, tb.inv, tb.segf, tb.segb});
+      glaunch(dim3((unsigned)((warps * 32 + 127) / 128)), dim3(128), 0, TriYWarp<T, 8>{g, f, tb.cp, tb.inv, tb.segf, tb.segb});
     } else if (tri == 1 && sh.ny <= 16 * TRI_SEG) {
       const long long warps = (long long)((g.nkx + 1) / 2) * g.nz;
-      ex.launch(dim3((unsigned)((warps * 32 + 127) / 128)), dim3(128), 0, TriYWarp<T, 16>{g, f, tb.cp, tb.inv, tb.segf, tb.segb});
+      glaunch(dim3((unsigned)((warps * 32 + 127) / 128)), dim3(128), 0, TriYWarp<T, 16>{g, f, tb.cp, tb.inv, tb.segf, tb.segb});
     } else if (tri == 1) {
       const long long warps = (long long)g.nkx * g.nz;
-      ex.launch(dim3((unsigned)((warps * 32 + 127) / 128)), dim3(128), 0, TriYWarp<T, 32>{g, f, tb.cp, tb.inv, tb.segf, tb.segb});
+      glaunch(dim3((unsigned)((warps * 32 + 127) / 128)), dim3(128), 0, TriYWarp<T, 32>{g, f, tb.cp, tb.inv, tb.segf, tb.segb});
     } else {
       // blocks of two warps: the systems of a 128^3 grid then spread over
       // every SM, about one warp per SM sub-partition
-      ex.launch(dim3((unsigned)((2 * tlines + 63) / 64)), dim3(64), 0, TriY<T>{g, f, tb.cp, tb.inv, fwd});
+      glaunch(dim3((unsigned)((2 * tlines + 63) / 64)), dim3(64), 0, TriY<T>{g, f, tb.cp, tb.inv, fwd});
     }
   };
   // fused per-plane transforms when the plane's half-spectrum and two work
@@ -2085,19 +2164,19 @@ void launch_poisson(const Geo& g, const Fields<T>& f, const TagBuffers& b, const
   auto solve_rest = [&](T* out, bool first) {
     if (!plane) {
       if (first) ex.mark(ST_FFT_Z_FWD);
-      ex.launch(dim3(g.ny * ntile), dim3(256), smz, FftZ<T, false>{g, f, tb.twz, pz, cols});
+      glaunch(dim3(g.ny * ntile), dim3(256), smz, FftZ<T, false>{g, f, tb.twz, pz, cols});
     }
     ex.mark(first ? ST_TRI_Y : ST_CORR_TRI);
     tri_solve();
     if (plane) {
       ex.mark(first ? ST_FFT_X_INV : ST_CORR_INV);
-      ex.launch(dim3(g.ny), dim3(1024), smp, FftPlaneInv<T>{g, f, tb.twx, tb.twz, px, pz, wbuf, czp, out});
+      glaunch(dim3(g.ny), dim3(1024), smp, FftPlaneInv<T>{g, f, tb.twx, tb.twz, px, pz, wbuf, czp, out});
       return;
     }
     ex.mark(first ? ST_FFT_Z_INV : ST_CORR_INV);
-    ex.launch(dim3(g.ny * ntile), dim3(256), smz, FftZ<T, true>{g, f, tb.twz, pz, cols});
+    glaunch(dim3(g.ny * ntile), dim3(256), smz, FftZ<T, true>{g, f, tb.twz, pz, cols});
     if (first) ex.mark(ST_FFT_X_INV);
-    ex.launch(xgrid, xblk, smx, FftXInv<T>{g, f, tb.twx, px, lpb, out});
+    glaunch(xgrid, xblk, smx, FftXInv<T>{g, f, tb.twx, px, lpb, out});
   };
   // forward x (and z, fused per plane) with the right-hand side of Eq. elliptic_mod
   const double adt = sg.alp * dt, bb = adt / (2.0 * re);
@@ -2108,9 +2187,11 @@ void launch_poisson(const Geo& g, const Fields<T>& f, const TagBuffers& b, const
   auto forward = [&](int mode) {
     if (plane)
       ex.launch(dim3(g.ny), dim3(1024), smp,
-                FftPlaneFwd<T>{g, f, b.flags32, tb.twx, tb.twz, px, pz, wbuf, czp, ds, sg.s, use_q, scale, mode, cf});
+                FftPlaneFwd<T>{g, f, b.flags32, tb.twx, tb.twz, px, pz, wbuf, czp, ds, sg.s, use_q, scale, mode, cf,
+                               ds->res1 + sg.s});
     else
-      ex.launch(xgrid, xblk, smx, FftXFwd<T>{g, f, b.flags32, tb.twx, px, lpb, ds, sg.s, use_q, scale, mode, cf});
+      ex.launch(xgrid, xblk, smx,
+                FftXFwd<T>{g, f, b.flags32, tb.twx, px, lpb, ds, sg.s, use_q, scale, mode, cf, ds->res1 + sg.s});
   };
   const dim3 pgrid((g.nx + 31) / 32, (g.ny + 3) / 4, g.nz), pblk(32, 4);
   ex.mark(ST_FFT_X_FWD);
@@ -2118,7 +2199,7 @@ void launch_poisson(const Geo& g, const Fields<T>& f, const TagBuffers& b, const
   solve_rest(f.phi, true);
   if (!f.lo[0]) {
     ex.mark(ST_PROJECT);
-    ex.launch(pgrid, pblk, 0, Project<T>{g, f, cf, 0});
+    ex.launch(pgrid, pblk, 0, Project<T>{g, f, cf, 0, ds, sg.s});
     return;
   }
   // mixed path: solve again for the residual divergence of the projected
@@ -2127,9 +2208,11 @@ void launch_poisson(const Geo& g, const Fields<T>& f, const TagBuffers& b, const
   // update in one pass
   ex.mark(ST_CORRECT);
   forward(3);
+  gate = true;
   solve_rest(f.phi2, false);
+  gate = false;
   ex.mark(ST_PROJECT);
-  ex.launch(pgrid, pblk, 0, Project<T>{g, f, cf, 3});
+  ex.launch(pgrid, pblk, 0, Project<T>{g, f, cf, 3, ds, sg.s});
 }
 
 template <typename T>
@@ -2143,6 +2226,13 @@ void set_fft_smem_limits() {
   op_smem_limit<TriYSmem<T>>(160 * 1024);
   op_smem_limit<FftPlaneFwd<T>>(200 * 1024);
   op_smem_limit<FftPlaneInv<T>>(200 * 1024);
+  if constexpr (sizeof(T) == 4) {   // the correction solve's kernels (mixed path)
+    op_smem_limit<Gated<FftXInv<T>>>(maxsm);
+    op_smem_limit<Gated<FftZ<T, false>>>(maxsm);
+    op_smem_limit<Gated<FftZ<T, true>>>(maxsm);
+    op_smem_limit<Gated<TriYSmem<T>>>(160 * 1024);
+    op_smem_limit<Gated<FftPlaneInv<T>>>(200 * 1024);
+  }
 }
 
 void init_kernel_attributes() {

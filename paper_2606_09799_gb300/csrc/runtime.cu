@@ -98,6 +98,8 @@ __global__ void k_set_force(DevState* ds, double fx, double fy, double fz) {
   ds->fbf[2] = (float)fz;
 }
 
+__global__ void k_set_budget(DevState* ds, float budget) { ds->div_budget = budget; }
+
 __device__ __forceinline__ void step_done(const Blk&, DevState* ds) { ds->steps += 1; }
 struct StepDone {
   static constexpr int kThreads = 32;
@@ -1358,6 +1360,16 @@ ibm_status ibm_set_body_force(ibm_handle h, double fx, double fy, double fz) {
   return launch_status(h, "ibm_set_body_force");
 }
 
+ibm_status ibm_set_div_budget(ibm_handle h, double budget) {
+  if (!h || !(budget >= 0.0)) return IBM_ERR_ARG;
+  // rounded down to FP32, so a residual the FP32 comparison lets through is
+  // within the budget as given
+  float b = (float)budget;
+  if ((double)b > budget) b = nextafterf(b, 0.0f);
+  k_set_budget<<<1, 1, 0, h->user>>>(h->ds, b);
+  return launch_status(h, "ibm_set_div_budget");
+}
+
 // upper bound of the candidates a surface can produce: nodes inside every
 // triangle's Cartesian box (with the one-cell margin of Algorithm 1)
 // (non-uniform wall-normal grid: rows at least ysp_min apart, margins of at
@@ -1697,6 +1709,16 @@ ibm_status ibm_get_diag(ibm_handle h, ibm_diag* out) {
   out->div_max = ds.div_max;
   out->ke = ds.ke;
   out->cfl = ds.cfl;
+  if (h->desc.precision == IBM_MIXED) {
+    float r = 0.0f;
+    for (int i = 0; i < ns; ++i) {
+      float v;
+      memcpy(&v, &ds.res1[i], sizeof v);
+      r = (v > r || v != v) ? v : r;
+    }
+    out->div_first = r;
+    out->corr_solves = (int64_t)ds.ncorr;
+  }
   return s;
 }
 

@@ -52,7 +52,7 @@ class ibm_diag(ctypes.Structure):
                 ("q_f", ctypes.c_double), ("sum_q_dv", ctypes.c_double), ("steps", ctypes.c_int64),
                 ("ncandidates", ctypes.c_int64), ("kernels_per_step", ctypes.c_int64),
                 ("d2h_bytes", ctypes.c_int64), ("div_max", ctypes.c_double), ("ke", ctypes.c_double),
-                ("cfl", ctypes.c_double)]
+                ("cfl", ctypes.c_double), ("div_first", ctypes.c_double), ("corr_solves", ctypes.c_int64)]
 
 IBM_NSTAGES = 19
 
@@ -78,7 +78,7 @@ EXPORTS = ("ibm_create_grid", "ibm_destroy", "ibm_set_surface", "ibm_set_body_fo
            "ibm_batch_step", "ibm_batch_sync", "ibm_batch_get_info", "ibm_batch_profile_stages",
            "ibm_batch_set_tune", "ibm_batch_autotune", "ibm_batch_last_error", "ibm_step_batch",
            "ibm_get_loads", "ibm_get_pressure_recon", "ibm_check_conversions", "ibm_create_grid_stretched", "ibm_check_bounded_wait",
-           "ibm_get_history", "ibm_set_history", "ibm_measure_alu_peaks")
+           "ibm_get_history", "ibm_set_history", "ibm_measure_alu_peaks", "ibm_set_div_budget")
 
 
 def library_path() -> str:
@@ -102,6 +102,7 @@ def load(build_if_needed: bool = True):
         L.ibm_destroy.argtypes = [P]
         L.ibm_set_surface.argtypes = [P, I, P, P, I, P, I]
         L.ibm_set_body_force.argtypes = [P, D, D, D]
+        L.ibm_set_div_budget.argtypes = [P, D]
         L.ibm_set_fields.argtypes = [P, P, P, P, P, I]
         L.ibm_step.argtypes = [P, I]
         L.ibm_get_fields.argtypes = [P, P, P, P, P, I]
@@ -226,6 +227,10 @@ def ibm_set_body_force(h, fx, fy, fz):
     _check(h, load().ibm_set_body_force(h, float(fx), float(fy), float(fz)))
 
 
+def ibm_set_div_budget(h, budget):
+    _check(h, load().ibm_set_div_budget(h, float(budget)))
+
+
 def ibm_set_fields(h, u=None, v=None, w=None, p=None):
     ptrs = [_ptr(a) for a in (u, v, w, p)]
     dev = {d for (q, d) in ptrs if q is not None}
@@ -278,7 +283,8 @@ def ibm_get_diag(h) -> dict:
     return {"slip_l1": d.slip_l1, "slip_comp": list(d.slip_comp), "nforce": list(d.nforce),
             "nboundary": d.nboundary, "q_f": d.q_f, "sum_q_dv": d.sum_q_dv, "steps": d.steps,
             "ncandidates": d.ncandidates, "kernels_per_step": d.kernels_per_step, "d2h_bytes": d.d2h_bytes,
-            "div_max": d.div_max, "ke": d.ke, "cfl": d.cfl}
+            "div_max": d.div_max, "ke": d.ke, "cfl": d.cfl, "div_first": d.div_first,
+            "corr_solves": d.corr_solves}
 
 
 def ibm_profile_stages(h, nsteps=1) -> dict:
@@ -490,6 +496,7 @@ class Simulation:
     def __init__(self, nx, ny, nz, lx=1.0, ly=1.0, lz=1.0, re=100.0, dt=1e-3, scheme="rk2", ybc=0,
                  precision="fp64", use_q=True, stream=None, y_faces=None):
         self.shape = (nx, ny, nz)
+        self.precision = precision
         sch = IBM_AB_CN if scheme == "ab" else IBM_RK2_CN
         prec = {"fp64": IBM_FP64, "mixed": IBM_MIXED, "mixed_fast": IBM_MIXED_FAST}[precision]
         self.h = ibm_create_grid(nx, ny, nz, lx, ly, lz, re, dt, sch, ybc, prec, int(use_q), stream, y_faces)
@@ -515,6 +522,9 @@ class Simulation:
 
     def set_body_force(self, fx, fy, fz):
         ibm_set_body_force(self.h, fx, fy, fz)
+
+    def set_div_budget(self, budget):
+        ibm_set_div_budget(self.h, budget)
 
     def set_fields(self, u=None, v=None, w=None, p=None):
         ibm_set_fields(self.h, u, v, w, p)

@@ -8,7 +8,9 @@ pairs plus a correction solve on the residual divergence):
   - velocity: max |u_mixed - u_oracle| <= 1e-5 U_ref after 10 steps;
   - discrete divergence of the projected field on the fluid cells:
     max |D u - q_F| <= 1e-7 U_ref / dx;
-  - mean no-slip error ||eps||_1 within 5% of the FP64 path's.
+  - mean no-slip error ||eps||_1 within 5% of the FP64 path's;
+  - pressure up to its mean: max |p_mixed - p_oracle| <= 1e-5 max(1, max |p|)
+    U_ref^2 (no bar is set for it; this holds the measured 3-5e-7 with room).
 IBM_MIXED_FAST (FP32 state, one solve) meets the velocity and no-slip bars;
 its divergence is bounded by the FP32 solve, checked at 1e-5 U_ref / dx.
 """
@@ -22,6 +24,10 @@ from paper_2606_09799_gb300 import ibm, inputs
 pytestmark = pytest.mark.gpu
 
 VEL_TOL = 1e-5
+# pressure (up to its mean) over max(1, max |p|) in units of U_ref^2: no bar
+# is set for the mixed pressure; measured 2.9e-7 - 4.7e-7 on both workloads
+# and both mixed forms, held here at 1e-5
+PRES_TOL = 1e-5
 DIV_TOL = 1e-7
 DIV_TOL_FAST = 1e-5
 SLIP_REL = 0.05
@@ -75,7 +81,7 @@ def test_mixed_vs_oracle(name, nsteps, precision):
     err = max(np.abs(o.u - gu).max(), np.abs(o.v - gv).max(), np.abs(o.w - gw).max())
     assert err <= VEL_TOL, f"velocity error {err:.3e}"
     perr = np.abs((o.p - o.p.mean()) - (gp - gp.mean())).max()
-    assert perr <= 100 * VEL_TOL * max(1.0, np.abs(o.p).max()), f"pressure error {perr:.3e}"
+    assert perr <= PRES_TOL * max(1.0, np.abs(o.p).max()), f"pressure error {perr:.3e}"
     div = divergence_error(g, (wl.nx, wl.ny, wl.nz))
     tol = DIV_TOL if precision == "mixed" else DIV_TOL_FAST
     assert div <= tol, f"divergence {div:.3e} U/dx"
