@@ -163,10 +163,10 @@ def stage_kernel(stage: str, tune: dict | None, precision: str, ny: int = 128) -
     T = "float" if precision == "mixed" else "double"
     if stage in ("sweep_y", "sweep_z"):
         sy = t.get("sweep_y", 0)
-        if sy in (1, 2, 3):
+        if sy in (1, 2, 3, 4):
             if stage == "sweep_z":
-                return f"SweepZStream<{T}>"
-            if sy == 3 and precision == "mixed":
+                return f"SweepZTile<{T}>" if sy == 4 else f"SweepZStream<{T}>"
+            if sy in (3, 4) and precision == "mixed":
                 return f"SweepYStretched<{T}>"
             if sy == 2:
                 return f"SweepYTma<{T}>"

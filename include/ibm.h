@@ -297,7 +297,8 @@ typedef struct {
                          lines staged in shared memory by bulk asynchronous copies (where every row
                          starts on a 16-byte boundary and the tile fits; else as 1), 3 as 1 for z,
                          and for y the mixed path's tabulated FP32 rows in register batches (grids of
-                         at most 1024 rows; else as 1) */
+                         at most 1024 rows; else as 1), 4 z from tiles of 32 lines with all their rows
+                         staged in shared memory (nz <= 256; else as 1), y as 3 */
   double ms_per_step; /* set by the autotuners: measured time per step of the chosen shapes */
 } ibm_tune;
 

@@ -156,7 +156,8 @@ struct Tune {
   int fft_plane;  // 1 separate x and z transform kernels; 2 fused per y-plane (when the plane fits)
   int sweep_y;    // z and y sweeps: 0 as sweep_zy; 1 one thread per line, rows streamed through registers;
                   // 2 z as 1, y from tiles staged by bulk asynchronous copies (else as 1);
-                  // 3 z as 1, y from the tabulated FP32 rows in register batches (mixed path, else as 1)
+                  // 3 z as 1, y from the tabulated FP32 rows in register batches (mixed path, else as 1);
+                  // 4 z from shared-memory tiles of whole lines (nz <= 256, else as 1), y as 3
 };
 
 struct Exec {

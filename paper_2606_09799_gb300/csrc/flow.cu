@@ -1455,6 +1455,150 @@ struct SweepZStream {
   __device__ __forceinline__ void operator()(const Blk& bk) const { sweep_z_stream<T>(bk, g, f, flags32, tb, lfirst); }
 };
 
+// z-sweep from a shared-memory tile: a block of ZT_THREADS threads stages the
+// ZT_W z-lines of ZT_W consecutive i at one plane (component bk.z, plane
+// bk.y) -- all n rows, one coalesced 128-byte row segment each, every copy
+// issued before the first wait -- together with the rows' flag bytes (when
+// a line of the tile crosses a body) and the z tables.  One warp then runs
+// the same recurrences as the streamed z-sweep (same operations in the same
+// order; a multiply-add may be fused differently) from shared memory, one
+// lane per line; lane t reads row r at r * ZT_W + t, so the lanes never share a bank
+// whatever rotation their lines take.  The block writes the tile back
+// coalesced.  The forward pass keeps each row's position in its segment in
+// the flag byte (0 on a forcing row), from which the backward pass reads c'.
+constexpr int ZT_W = 32, ZT_THREADS = 128;
+template <typename T>
+__host__ __device__ inline size_t sweep_z_tile_smem(int n) {
+  return (size_t)n * ZT_W * sizeof(T) + (size_t)6 * n * sizeof(T) + (size_t)n * ZT_W;
+}
+template <typename T>
+__device__ __forceinline__ void sweep_z_tile(const Blk& bk, const Geo& g, const Fields<T>& f,
+                                             const unsigned* __restrict__ flags32, const SweepTables<T>& tb,
+                                             const int* __restrict__ lfirst) {
+  extern __shared__ unsigned char smem_raw[];
+  const int c = bk.z;
+  const int nplanes = c == 1 ? g.ny - 1 : g.ny;    // v: interior planes j = 1 .. ny-1
+  if ((int)bk.y >= nplanes) return;
+  const int j = (c == 1 ? 1 : 0) + bk.y;
+  const int i0 = bk.x * ZT_W;
+  const int w = min(ZT_W, g.nx - i0);
+  const int n = g.nz;
+  const long long sn = (long long)planes(g, c) * g.nx;   // row stride along z
+  const long long fs = (long long)g.ny * g.nx;           // flag-byte stride along z
+  T* tile = reinterpret_cast<T*>(smem_raw);               // [n][ZT_W]
+  T* tabs = tile + (size_t)n * ZT_W;                      // inv, cp, g0, zv, invR, cpR (n each)
+  unsigned char* fl = reinterpret_cast<unsigned char*>(tabs + (size_t)6 * n);   // [n][ZT_W]
+  T* __restrict__ Rl = f.R[c] + fidx(g, c, i0, j, 0);
+  const unsigned char* __restrict__ Fl = reinterpret_cast<const unsigned char*>(flags32) + cidx(g, i0, j, 0);
+  const int tid = threadIdx.x;
+  __shared__ int any_s;
+  if (tid == 0) any_s = 0;
+  __syncthreads();
+  int f0 = n;
+  if (tid < w) {
+    f0 = lfirst[line_z(g, c, i0 + tid, j)];
+    if (f0 < n) atomicOr(&any_s, 1);
+  }
+  // every row of the tile, then the tables
+  for (int e = tid; e < n * ZT_W; e += ZT_THREADS) {
+    const int r = e / ZT_W, t = e - r * ZT_W;
+    if (t < w) cp_async<sizeof(T)>(tile + e, Rl + r * sn + t);
+  }
+  for (int e = tid; e < n; e += ZT_THREADS) {
+    tabs[e] = tb.inv[1][e];
+    tabs[n + e] = e < n - 1 ? tb.cp[1][e] : (T)0;
+    tabs[2 * n + e] = tb.g0[1][e];
+    tabs[3 * n + e] = tb.zv[1][e];
+    tabs[4 * n + e] = tb.invR[1][e];
+    tabs[5 * n + e] = tb.cpR[1][e];
+  }
+  __syncthreads();   // any_s
+  const bool tile_any = any_s != 0;
+  if (tile_any) {
+    for (int e = tid; e < n * ZT_W; e += ZT_THREADS) {
+      const int r = e / ZT_W, t = e - r * ZT_W;
+      fl[e] = t < w ? Fl[r * fs + t] : (unsigned char)0;
+    }
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  if (tid < w) {
+    const int t = tid;
+    const bool any = f0 < n;
+    const T a = -tb.off[2];
+    const T* inv = tabs;
+    const T* cpt = tabs + n;
+    const T* g0 = tabs + 2 * n;
+    const T* zv = tabs + 3 * n;
+    const T* invR = tabs + 4 * n;
+    const T* cpR = tabs + 5 * n;
+    const int r0 = any ? f0 : 0;
+    auto rot = [&](int q) { const int r = r0 + q; return r >= n ? r - n : r; };
+    const T x0 = any ? tile[r0 * ZT_W + t] : (T)0;
+    // ---- forward
+    T prev = (T)0, acc = (T)0;
+    int m = 0;
+    if (any) {
+      for (int q = 0; q < n; ++q) {
+        const int r = rot(q);
+        const bool frc = (fl[r * ZT_W + t] >> c) & 1;
+        T iv = (T)1, am = (T)0;
+        if (!frc) {
+          iv = invR[m];
+          am = a;
+        }
+        T dq = tile[r * ZT_W + t];
+        if (q == n - 1 && am != (T)0) dq -= a * x0;
+        prev = (dq - am * prev) * iv;
+        tile[r * ZT_W + t] = prev;
+        // the row's c' is cpR[m] (0 on a forcing row and on the last row):
+        // keep m + 1 (at most n - 1, since row q = 0 is a forcing row)
+        fl[r * ZT_W + t] = frc || q == n - 1 ? (unsigned char)0 : (unsigned char)(m + 1);
+        m = frc ? 0 : m + 1;
+      }
+    } else {
+      for (int q = 0; q < n; ++q) {
+        const T dq = tile[q * ZT_W + t];
+        acc += g0[q] * dq;
+        prev = (dq - a * prev) * inv[q];
+        tile[q * ZT_W + t] = prev;
+      }
+    }
+    const T fact = any ? (T)0 : (acc + (a / tb.gam[1]) * prev) / tb.smden[1];
+    // ---- backward
+    T x = (T)0;
+    if (any) {
+      for (int q = n - 1; q >= 0; --q) {
+        const int r = rot(q);
+        const int mq = fl[r * ZT_W + t];
+        const T cv = mq ? cpR[mq - 1] : (T)0;
+        x = tile[r * ZT_W + t] - cv * x;
+        tile[r * ZT_W + t] = x;
+      }
+    } else {
+      for (int q = n - 1; q >= 0; --q) {
+        x = tile[q * ZT_W + t] - cpt[q] * x;
+        tile[q * ZT_W + t] = x - fact * zv[q];
+      }
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < n * ZT_W; e += ZT_THREADS) {
+    const int r = e / ZT_W, t = e - r * ZT_W;
+    if (t < w) Rl[r * sn + t] = tile[e];
+  }
+}
+template <typename T>
+struct SweepZTile {
+  static constexpr int kThreads = ZT_THREADS;
+  Geo g;
+  Fields<T> f;
+  const unsigned* flags32;
+  SweepTables<T> tb;
+  const int* lfirst;
+  __device__ __forceinline__ void operator()(const Blk& bk) const { sweep_z_tile<T>(bk, g, f, flags32, tb, lfirst); }
+};
+
 // y-sweep on a non-uniform wall-normal grid, one thread per line: the rows'
 // coefficients are those of the y part of the Laplacian of the right-hand
 // side, from the spacing table, and a forcing node's row is the identity;
@@ -1987,7 +2131,10 @@ void launch_sweeps(const Geo& g, const Fields<T>& f, const TagBuffers& b, const 
   // tuning asks for the shared-memory tile with one thread per line
   const bool lanes = sizeof(T) == 4 && ex.tune.sweep_zy != 1;
   ex.mark(ST_SWEEP_Z);
-  if (ex.tune.sweep_y >= 1) {
+  if (ex.tune.sweep_y == 4 && sh.nz <= 256) {
+    ex.launch(dim3((unsigned)((g.nx + ZT_W - 1) / ZT_W), (unsigned)g.ny, 3), dim3(ZT_THREADS),
+              sweep_z_tile_smem<T>(sh.nz), SweepZTile<T>{g, f, b.flags32, tb, b.lines.z});
+  } else if (ex.tune.sweep_y >= 1) {
     const long long lines = (long long)g.nx * g.ny;
     ex.launch(dim3((unsigned)((lines + 127) / 128), 3), dim3(128), 0, SweepZStream<T>{g, f, b.flags32, tb, b.lines.z});
   } else if (!(lanes && sweep_lanes_launch(g, f, b, tb, ex, sh.nz, 2, g.ny))) {
@@ -2004,7 +2151,7 @@ void launch_sweeps(const Geo& g, const Fields<T>& f, const TagBuffers& b, const 
               SweepYStretched<T>{g, f, b.flags32, b.lines.y, (double)tb.off[0] * g.dx * g.dx});
   } else if (ex.tune.sweep_y == 2 && !ex.rec && sweep_y_tma_ok<T>(g, f, b, tb, ds, sh.ny, ex)) {
     // (launched inside the check: the op carries its tensor maps)
-  } else if (ex.tune.sweep_y == 3 && sizeof(T) == 4 && sh.ny <= 1024 && g.yt.yswf && g.yt.ysw2f) {
+  } else if (ex.tune.sweep_y >= 3 && sizeof(T) == 4 && sh.ny <= 1024 && g.yt.yswf && g.yt.ysw2f) {
     // the tabulated FP32 rows (uniform spacing written as the non-uniform
     // grid's tables; built for every mixed grid of at most 1024 rows)
     const long long lines = (long long)g.nx * g.nz;
@@ -2027,6 +2174,7 @@ static void sweep_attrs() {
   op_smem_limit<SweepX<T>>(200 * 1024);
   op_smem_limit<SweepZY<T>>(200 * 1024);
   op_smem_limit<SweepYTma<T>>(200 * 1024);
+  op_smem_limit<SweepZTile<T>>((int)sweep_z_tile_smem<T>(256));
 }
 
 void init_sweep_attributes() {

@@ -916,7 +916,7 @@ struct Knob {
 };
 
 static std::vector<Knob> tune_knobs() {
-  return {{&Tune::fft_plane, {2, 1}}, {&Tune::sweep_zy, {2, 1}}, {&Tune::sweep_y, {1, 2, 3}}, {&Tune::tri_y, {1, 2, 3}},
+  return {{&Tune::fft_plane, {2, 1}}, {&Tune::sweep_zy, {2, 1}}, {&Tune::sweep_y, {1, 2, 3, 4}}, {&Tune::tri_y, {1, 2, 3}},
           {&Tune::sweep_w, {64, 32, 16}},
           {&Tune::fft_lpb, {0, 8, 4, 2}},
           {&Tune::fft_cols, {16, 8, 4}}};
@@ -1756,7 +1756,7 @@ static bool tune_valid(const ibm_tune* t) {
   if (t->fft_cols < 0 || t->fft_cols > 16 || (t->fft_cols & (t->fft_cols - 1))) return false;
   if (t->sweep_zy < 0 || t->sweep_zy > 2) return false;
   if (t->fft_plane < 0 || t->fft_plane > 2) return false;
-  if (t->sweep_y < 0 || t->sweep_y > 3) return false;
+  if (t->sweep_y < 0 || t->sweep_y > 4) return false;
   return true;
 }
 

@@ -181,14 +181,15 @@ def test_batch_autotune_leaves_state():
 
 
 @pytest.mark.parametrize("tune", [dict(tri_y=1, sweep_y=2, fft_plane=2), dict(tri_y=1, sweep_y=3, fft_plane=2),
-                                  dict(tri_y=2, sweep_y=3, fft_plane=2)])
+                                  dict(tri_y=2, sweep_y=3, fft_plane=2), dict(tri_y=1, sweep_y=4, fft_plane=2)])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_batch_bulk_copy_y_tiles_equal_solo(precision, tune):
-    """Launch-shape choices sweep_y = 2 and 3 (with either Thomas variant)
-    in a batch of uneven instances and alone: the same fields, bit for bit
-    in FP64.  (With 2 a batch keeps the streamed y sweep: its ops live in
-    global memory, not in kernel parameters where tensor maps must be; 3 is
-    the mixed path's tabulated rows in both.)"""
+    """Launch-shape choices sweep_y = 2, 3 and 4 (with either Thomas
+    variant) in a batch of uneven instances and alone: the same fields, bit
+    for bit in FP64.  (With 2 a batch keeps the streamed y sweep: its ops
+    live in global memory, not in kernel parameters where tensor maps must
+    be; 3 is the mixed path's tabulated rows in both; 4 adds the z sweep
+    from shared-memory tiles.)"""
     wls = small_batch()
     sims = [make(w, precision) for w in wls]
     b = ibm.Batch(sims)
@@ -221,6 +222,6 @@ def test_tune_values_are_validated():
     with pytest.raises(ibm.IbmError):
         ibm.ibm_set_tune(g.h, fft_cols=3)
     with pytest.raises(ibm.IbmError):
-        ibm.ibm_set_tune(g.h, sweep_y=4)
+        ibm.ibm_set_tune(g.h, sweep_y=5)
     ibm.ibm_set_tune(g.h, tri_y=2, sweep_w=16, fft_lpb=4, fft_cols=4)
     assert ibm.ibm_get_tune(g.h)["sweep_w"] == 16

@@ -284,12 +284,15 @@ def test_stretched_mixed_channel_matches_oracle(precision, scheme, ybc):
     assert divergence_error(g, yf, NX, NZ) <= DIV_TOL[precision] * max(1.0, np.abs(o.u).max())
 
 
-@pytest.mark.parametrize("precision", ["mixed", "mixed_fast"])
-def test_stretched_mixed_moving_sphere_matches_oracle(precision):
+@pytest.mark.parametrize("precision,sweep_y", [("mixed", 0), ("mixed_fast", 0), ("mixed", 4), ("mixed_fast", 4)])
+def test_stretched_mixed_moving_sphere_matches_oracle(precision, sweep_y):
+    """sweep_y = 4: the z sweep from shared-memory tiles."""
     wl = inputs.oscillating_sphere(n=32, steps=8, subdiv=2)
     yf = inputs.stretched_faces(40)
     o = OracleSim(32, 40, 32, re=wl.re, dt=wl.dt, yfaces=yf)
     g = ibm.Simulation(32, 40, 32, re=wl.re, dt=wl.dt, precision=precision, y_faces=yf)
+    if sweep_y:
+        ibm.ibm_set_tune(g.h, sweep_y=sweep_y)
     for s in range(8):
         xyz, vel = wl.surface(s)
         for sim in (o, g):
@@ -305,12 +308,15 @@ def test_stretched_mixed_moving_sphere_matches_oracle(precision):
     assert abs(slip - o.last["slip"]) <= 0.05 * o.last["slip"]
 
 
-def test_stretched_mixed_immersed_wall_channel_matches_oracle():
+@pytest.mark.parametrize("sweep_y", [0, 4])
+def test_stretched_mixed_immersed_wall_channel_matches_oracle(sweep_y):
     wl = inputs.immersed_wall_channel(nx=32, ny=48, nz=32, y_wall=0.1213, steps=6)
     yf = inputs.stretched_faces(48)
     init = inputs.random_fields(32, 48, 32, seed=5, amp=0.1)
     o = OracleSim(32, 48, 32, re=wl.re, dt=wl.dt, yfaces=yf)
     g = ibm.Simulation(32, 48, 32, re=wl.re, dt=wl.dt, precision="mixed", y_faces=yf)
+    if sweep_y:
+        ibm.ibm_set_tune(g.h, sweep_y=sweep_y)
     for sim in (o, g):
         sim.set_fields(*init)
     for s in range(6):
