@@ -1556,6 +1556,18 @@ __device__ __forceinline__ void sweep_z_tile(const Blk& bk, const Geo& g, const 
         fl[r * ZT_W + t] = frc || q == n - 1 ? (unsigned char)0 : (unsigned char)(m + 1);
         m = frc ? 0 : m + 1;
       }
+    } else if ((n & 7) == 0) {
+      // rows in batches of 8 through registers, every shared-memory load of
+      // a batch issued before its recurrence
+      for (int q0 = 0; q0 < n; q0 += 8) {
+        T e[8], gg[8], vv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) { e[u] = tile[(q0 + u) * ZT_W + t]; gg[u] = g0[q0 + u]; vv[u] = inv[q0 + u]; }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) { acc += gg[u] * e[u]; prev = (e[u] - a * prev) * vv[u]; e[u] = prev; }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) tile[(q0 + u) * ZT_W + t] = e[u];
+      }
     } else {
       for (int q = 0; q < n; ++q) {
         const T dq = tile[q * ZT_W + t];
@@ -1574,6 +1586,16 @@ __device__ __forceinline__ void sweep_z_tile(const Blk& bk, const Geo& g, const 
         const T cv = mq ? cpR[mq - 1] : (T)0;
         x = tile[r * ZT_W + t] - cv * x;
         tile[r * ZT_W + t] = x;
+      }
+    } else if ((n & 7) == 0) {
+      for (int q1 = n - 8; q1 >= 0; q1 -= 8) {
+        T e[8], cc[8], zz[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) { e[u] = tile[(q1 + u) * ZT_W + t]; cc[u] = cpt[q1 + u]; zz[u] = zv[q1 + u]; }
+#pragma unroll
+        for (int u = 7; u >= 0; --u) { x = e[u] - cc[u] * x; e[u] = x - fact * zz[u]; }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) tile[(q1 + u) * ZT_W + t] = e[u];
       }
     } else {
       for (int q = n - 1; q >= 0; --q) {
