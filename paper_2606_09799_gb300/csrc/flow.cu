@@ -1538,7 +1538,45 @@ __device__ __forceinline__ void sweep_z_tile(const Blk& bk, const Geo& g, const 
     // ---- forward
     T prev = (T)0, acc = (T)0;
     int m = 0;
-    if (any) {
+    if (any && (n & 7) == 0) {
+      // rows in batches of 8: the batch's rows and flags first, then the
+      // segment positions and pivots (they depend on the flags alone), then
+      // the recurrence.  A row keeps m + 1 for its c' = cpR[m] (0: a forcing
+      // row or the last row, c' = 0); m + 1 <= n - 1 since row q = 0 is a
+      // forcing row
+      for (int q0 = 0; q0 < n; q0 += 8) {
+        T e[8], iv[8], am[8];
+        int rr[8];
+        unsigned char fb[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          rr[u] = rot(q0 + u);
+          e[u] = tile[rr[u] * ZT_W + t];
+          fb[u] = fl[rr[u] * ZT_W + t];
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int q = q0 + u;
+          const bool frc = (fb[u] >> c) & 1;
+          iv[u] = frc ? (T)1 : invR[m];
+          am[u] = frc ? (T)0 : a;
+          fb[u] = frc || q == n - 1 ? (unsigned char)0 : (unsigned char)(m + 1);
+          m = frc ? 0 : m + 1;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          T dq = e[u];
+          if (q0 + u == n - 1 && am[u] != (T)0) dq -= a * x0;
+          prev = (dq - am[u] * prev) * iv[u];
+          e[u] = prev;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          tile[rr[u] * ZT_W + t] = e[u];
+          fl[rr[u] * ZT_W + t] = fb[u];
+        }
+      }
+    } else if (any) {
       for (int q = 0; q < n; ++q) {
         const int r = rot(q);
         const bool frc = (fl[r * ZT_W + t] >> c) & 1;
@@ -1551,8 +1589,6 @@ __device__ __forceinline__ void sweep_z_tile(const Blk& bk, const Geo& g, const 
         if (q == n - 1 && am != (T)0) dq -= a * x0;
         prev = (dq - am * prev) * iv;
         tile[r * ZT_W + t] = prev;
-        // the row's c' is cpR[m] (0 on a forcing row and on the last row):
-        // keep m + 1 (at most n - 1, since row q = 0 is a forcing row)
         fl[r * ZT_W + t] = frc || q == n - 1 ? (unsigned char)0 : (unsigned char)(m + 1);
         m = frc ? 0 : m + 1;
       }
@@ -1579,7 +1615,26 @@ __device__ __forceinline__ void sweep_z_tile(const Blk& bk, const Geo& g, const 
     const T fact = any ? (T)0 : (acc + (a / tb.gam[1]) * prev) / tb.smden[1];
     // ---- backward
     T x = (T)0;
-    if (any) {
+    if (any && (n & 7) == 0) {
+      for (int q1 = n - 8; q1 >= 0; q1 -= 8) {
+        T e[8], cv[8];
+        int rr[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          rr[u] = rot(q1 + u);
+          e[u] = tile[rr[u] * ZT_W + t];
+          const int mq = fl[rr[u] * ZT_W + t];
+          cv[u] = mq ? cpR[mq - 1] : (T)0;
+        }
+#pragma unroll
+        for (int u = 7; u >= 0; --u) {
+          x = e[u] - cv[u] * x;
+          e[u] = x;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) tile[rr[u] * ZT_W + t] = e[u];
+      }
+    } else if (any) {
       for (int q = n - 1; q >= 0; --q) {
         const int r = rot(q);
         const int mq = fl[r * ZT_W + t];
