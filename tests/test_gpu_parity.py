@@ -322,23 +322,28 @@ def test_tile_z_sweep_equals_streamed_to_rounding(precision):
     z sweep's recurrences in the same order (the compiler may fuse a
     multiply-add differently): fields equal to rounding after 3 steps (FP32
     rounding of the state in the mixed path) with a moving sphere (lines
-    with and without forcing rows, a partial tile of 16 lines at nx = 48)."""
+    with and without forcing rows, a partial tile of 16 lines at nx = 48;
+    nz = 96, so the lines' rows move in the register batches of 8)."""
     wl = inputs.oscillating_sphere(n=48, steps=3, subdiv=2)
-    sims = []
-    for sy in (3, 4):
-        g = ibm.Simulation(48, 37, 96, 1.0, 0.9, 1.6, re=150.0, dt=2e-3, precision=precision)
-        ibm.ibm_set_tune(g.h, tri_y=1, sweep_y=sy, fft_plane=2)
-        sims.append(g)
-    for s in range(3):
-        xyz, vel = wl.surface(s)
-        for g in sims:
-            g.set_surface(xyz, vel, wl.tri)
-            g.step()
-    # FP64: rounding of the state; mixed: once one FP32 rounding differs, the
-    # FP32 arithmetic from the hi parts carries an FP32 rounding of the state
-    tol = 1e-14 if precision == "fp64" else 1e-6
-    for a, b in zip(sims[0].fields(), sims[1].fields()):
-        assert np.abs(a - b).max() <= tol * max(1.0, np.abs(a).max())
+    for ny in (37, 48):
+        sims = []
+        for sy in (3, 4):
+            g = ibm.Simulation(48, ny, 96, 1.0, 0.9, 1.6, re=150.0, dt=2e-3, precision=precision)
+            ibm.ibm_set_tune(g.h, tri_y=1, sweep_y=sy, fft_plane=2)
+            sims.append(g)
+        for s in range(3):
+            xyz, vel = wl.surface(s)
+            for g in sims:
+                g.set_surface(xyz, vel, wl.tri)
+                g.step()
+        # FP64: rounding of the state; mixed: once one FP32 rounding differs,
+        # the FP32 arithmetic from the hi parts carries an FP32 rounding of the
+        # state
+        tol = 1e-14 if precision == "fp64" else 1e-6
+        ref = sims[0].fields()
+        for g in sims[1:]:
+            for a, b in zip(ref, g.fields()):
+                assert np.abs(a - b).max() <= tol * max(1.0, np.abs(a).max()), ny
 
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-5)])
