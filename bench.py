@@ -156,7 +156,18 @@ def algorithmic_bytes_per_cell(stage: str, word: int, pairs: bool = False) -> fl
 TRAFFIC_SUMMARY = os.path.join(ROOT, "profiles", "traffic_plate128.md")
 
 
-def stage_kernel(stage: str, tune: dict | None, precision: str, ny: int = 128) -> str | None:
+def fft_form(tune: dict | None, nz: int = 128) -> str:
+    """How the launch shapes run the x and z transforms of one simulation:
+    "cluster" (fused per y-plane over a cluster of 4 blocks: fft_plane 3, and
+    the built-in choice, when nz is a multiple of 8), "plane" (fused per
+    y-plane in one block: fft_plane 2) or "split" (separate x and z kernels)."""
+    v = (tune or {}).get("fft_plane", 0)
+    if v in (0, 3) and nz % 8 == 0:
+        return "cluster"
+    return "plane" if v == 2 else "split"
+
+
+def stage_kernel(stage: str, tune: dict | None, precision: str, ny: int = 128, nz: int = 128) -> str | None:
     """Kernel that the given launch shapes run for a stage of the 128^3 step
     (the name the ncu summaries use), or None when it is not recorded."""
     t = tune or {}
@@ -177,10 +188,12 @@ def stage_kernel(stage: str, tune: dict | None, precision: str, ny: int = 128) -
     if stage == "tri_y":
         v = t.get("tri_y", 0)
         lanes = 8 if ny <= 64 else (16 if ny <= 128 else 32)     # 8 rows per lane
-        warp = f"TriYWarp<{T}, {lanes}>" if ny <= 256 else f"TriY<{T}>"
-        return {0: warp, 1: warp, 2: f"TriY<{T}>", 3: f"TriYSmem<{T}>"}[v]
+        warp = f"TriYWarp<{T}, {lanes}, 7>" if ny <= 256 else f"TriY<{T}>"
+        uncapped = f"TriYWarp<{T}, {lanes}, 1>" if ny <= 256 else f"TriY<{T}>"
+        return {0: warp, 4: warp, 1: uncapped, 2: f"TriY<{T}>", 3: f"TriYSmem<{T}>"}[v]
     if stage == "fft_x_fwd":
-        return f"FftPlaneFwd<{T}>" if t.get("fft_plane", 0) == 2 else f"FftXFwd<{T}>"
+        form = fft_form(t, nz)
+        return {"cluster": f"FftPlaneFwdCl<{T}, 4>", "plane": f"FftPlaneFwd<{T}>"}.get(form, f"FftXFwd<{T}>")
     if stage == "rhs":
         return f"Rhs<{T}>"
     if stage == "project":
@@ -392,7 +405,7 @@ def gpu_arm(args):
     hbm = peaks.get("hbm_gbs", 6800.0)
     groups = {}
     tune_h = head["tune"] or {}
-    plane = tune_h.get("fft_plane", 0) == 2
+    plane = fft_form(tune_h, wl.nz) != "split"
     merged = {"tri_y": ("tri_y", "correction_tri")}
     if plane:
         merged["fft_x_fwd"] = ("fft_x_fwd", "correction")
@@ -434,7 +447,7 @@ def gpu_arm(args):
         g["share"] = g["ms_per_step"] / tot_all
     top = max(groups, key=lambda k: groups[k]["ms_per_step"])
     tg = groups[top]
-    kname = stage_kernel(top, head["tune"], args.precision, wl.ny)
+    kname = stage_kernel(top, head["tune"], args.precision, wl.ny, wl.nz)
     roof = {"bound": tg["bound"], "achieved": tg["achieved"], "peak": tg["peak"], "unit": tg["unit"],
             "frac": tg["frac"], "traffic": ncu_traffic(top, kname), "kernel": top, "kernel_name": kname,
             "ms_per_step": tg["ms_per_step"], "launches_per_step": tg["launches_per_step"],

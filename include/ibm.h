@@ -284,14 +284,18 @@ ibm_status ibm_tag_noalloc(const ibm_grid_desc* desc, int nverts, const double* 
  * rounding order only).  0 in any field means the built-in heuristic. */
 typedef struct {
   int tri_y;          /* per-wavenumber Thomas in y: 1 warp-cooperative scan, 2 one thread per real or
-                         imaginary part, 3 the same with its forward values in shared memory */
+                         imaginary part, 3 the same with its forward values in shared memory, 4 as 1
+                         with its registers capped so that 7 blocks of 128 threads fit an SM (the
+                         built-in choice) */
   int sweep_w;        /* grid lines per block of the z and y sweeps: 16, 32 or 64 */
   int fft_lpb;        /* complex lines per block of the x transforms (capped by shared memory) */
   int fft_cols;       /* kx columns per block of the z transforms: a power of two up to 16 */
   int sweep_zy;       /* z and y sweeps of the FP32 path: 1 shared-memory tile with one thread per line,
                          2 several lanes per line (affine-map scans) */
   int fft_plane;      /* 1 separate x and z transform kernels, 2 both fused per y-plane (when its
-                         half-spectrum fits shared memory) */
+                         half-spectrum fits shared memory), 3 both fused per y-plane over a cluster
+                         of 4 blocks that share the plane through distributed shared memory (one
+                         simulation with nz a multiple of 8; the built-in choice there) */
   int sweep_y;        /* z and y sweeps: 0 as sweep_zy, 1 one thread per line with its rows streamed
                          through registers (any line length), 2 as 1 for z, and for y tiles of 32
                          lines staged in shared memory by bulk asynchronous copies (where every row

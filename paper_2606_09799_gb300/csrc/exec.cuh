@@ -19,6 +19,7 @@
 #include <string.h>
 
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -44,8 +45,22 @@ __device__ __forceinline__ void pdl_enter() {
   asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
 }
 
+// An op may ask the compiler to fit kMinBlocks of its blocks on one SM
+// (registers capped to suit); its kernels are then the _occ forms.  Ops
+// without it keep a plain thread bound (an explicit minimum of 1 would let
+// the compiler spend more registers than its own default).
+template <class Op, class = void>
+struct HasMinBlocks : std::false_type {};
+template <class Op>
+struct HasMinBlocks<Op, std::void_t<decltype(Op::kMinBlocks)>> : std::true_type {};
+
 template <class Op>
 __global__ void __launch_bounds__(Op::kThreads) k_run(const __grid_constant__ Op op) {
+  pdl_enter();
+  op(blk_builtin());
+}
+template <class Op>
+__global__ void __launch_bounds__(Op::kThreads, Op::kMinBlocks) k_run_occ(const __grid_constant__ Op op) {
   pdl_enter();
   op(blk_builtin());
 }
@@ -57,8 +72,7 @@ struct GroupEntry {
 };
 
 template <class Op>
-__global__ void __launch_bounds__(Op::kThreads) k_run_group(const Op* __restrict__ ops,
-                                                            const GroupEntry* __restrict__ ge, int n) {
+__device__ __forceinline__ void run_group(const Op* __restrict__ ops, const GroupEntry* __restrict__ ge, int n) {
   pdl_enter();
   const unsigned b = blockIdx.x;
   int lo = 0, hi = n - 1;   // last instance whose start <= b (empty instances are skipped)
@@ -78,6 +92,29 @@ __global__ void __launch_bounds__(Op::kThreads) k_run_group(const Op* __restrict
   bk.y = r % e.gy;
   bk.z = r / e.gy;
   ops[lo](bk);   // the op stays in global memory (a copy would go to local memory)
+}
+template <class Op>
+__global__ void __launch_bounds__(Op::kThreads) k_run_group(const Op* __restrict__ ops,
+                                                            const GroupEntry* __restrict__ ge, int n) {
+  run_group<Op>(ops, ge, n);
+}
+template <class Op>
+__global__ void __launch_bounds__(Op::kThreads, Op::kMinBlocks) k_run_group_occ(const Op* __restrict__ ops,
+                                                                               const GroupEntry* __restrict__ ge,
+                                                                               int n) {
+  run_group<Op>(ops, ge, n);
+}
+
+// The kernels that run an op: alone and in a batch.
+template <class Op>
+constexpr auto run_kernel() {
+  if constexpr (HasMinBlocks<Op>::value) return &k_run_occ<Op>;
+  else return &k_run<Op>;
+}
+template <class Op>
+constexpr auto group_kernel() {
+  if constexpr (HasMinBlocks<Op>::value) return &k_run_group_occ<Op>;
+  else return &k_run_group<Op>;
 }
 
 // One recorded launch of one instance.
@@ -112,7 +149,7 @@ template <class Op>
 void group_launch(const void* ops, const GroupEntry* ge, int n, unsigned blocks, dim3 block, size_t smem,
                   cudaStream_t st) {
   PdlConfig pc(dim3(blocks), block, smem, st);
-  cudaLaunchKernelEx(&pc.cfg, k_run_group<Op>, static_cast<const Op*>(ops), ge, n);
+  cudaLaunchKernelEx(&pc.cfg, group_kernel<Op>(), static_cast<const Op*>(ops), ge, n);
 }
 
 // Raise the dynamic shared-memory limit of both launch forms of an op on the
@@ -128,9 +165,9 @@ cudaError_t op_smem_limit(int bytes) {
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lk(mu);
   if (bytes <= high[dev]) return cudaSuccess;
-  e = cudaFuncSetAttribute(k_run<Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  e = cudaFuncSetAttribute(run_kernel<Op>(), cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_run_group<Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  e = cudaFuncSetAttribute(group_kernel<Op>(), cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e != cudaSuccess) return e;
   high[dev] = bytes;
   return cudaSuccess;
@@ -153,7 +190,8 @@ struct Tune {
   int fft_lpb;    // complex lines per block of the x transforms
   int fft_cols;   // kx columns per block of the z transforms (power of two)
   int sweep_zy;   // z and y sweeps (FP32): 1 shared-memory tile, one thread per line; 2 several lanes per line
-  int fft_plane;  // 1 separate x and z transform kernels; 2 fused per y-plane (when the plane fits)
+  int fft_plane;  // 1 separate x and z transform kernels; 2 fused per y-plane (when the plane fits);
+                  // 3 fused per y-plane over a cluster of 4 blocks (one simulation, nz a multiple of 8)
   int sweep_y;    // z and y sweeps: 0 as sweep_zy; 1 one thread per line, rows streamed through registers;
                   // 2 z as 1, y from tiles staged by bulk asynchronous copies (else as 1);
                   // 3 z as 1, y from the tabulated FP32 rows in register batches (mixed path, else as 1);
@@ -174,12 +212,43 @@ struct Exec {
     else stage_mark(st, stage);
   }
 
+  // A launch in thread-block clusters of `csize` blocks along x (the op's
+  // blocks then share their shared memory within a cluster).  One simulation
+  // only: a batch records plain launches, whose block offsets would split
+  // the clusters, so its callers choose a plain op instead.
+  template <class Op>
+  void launch_cluster(dim3 grid, dim3 block, size_t smem, const Op& op, int csize) {
+    if (rec) {
+      if (first_err == cudaSuccess) {
+        first_err = cudaErrorNotSupported;
+        first_op = op_name<Op>();
+      }
+      return;
+    }
+    if ((unsigned long long)grid.x * grid.y * grid.z == 0) return;
+    PdlConfig pc(grid, block, smem, st);
+    cudaLaunchAttribute at[2];
+    at[0] = pc.attr[0];
+    at[1].id = cudaLaunchAttributeClusterDimension;
+    at[1].val.clusterDim.x = (unsigned)csize;
+    at[1].val.clusterDim.y = 1;
+    at[1].val.clusterDim.z = 1;
+    pc.cfg.attrs = at;
+    pc.cfg.numAttrs = 2;
+    cudaError_t e = cudaLaunchKernelEx(&pc.cfg, run_kernel<Op>(), op);
+    if (e == cudaSuccess) e = cudaPeekAtLastError();
+    if (e != cudaSuccess && first_err == cudaSuccess) {
+      first_err = e;
+      first_op = op_name<Op>();
+    }
+  }
+
   template <class Op>
   void launch(dim3 grid, dim3 block, size_t smem, const Op& op) {
     if (!rec) {
       if ((unsigned long long)grid.x * grid.y * grid.z == 0) return;
       PdlConfig pc(grid, block, smem, st);
-      cudaError_t e = cudaLaunchKernelEx(&pc.cfg, k_run<Op>, op);
+      cudaError_t e = cudaLaunchKernelEx(&pc.cfg, run_kernel<Op>(), op);
       if (e == cudaSuccess) e = cudaPeekAtLastError();
       if (e != cudaSuccess && first_err == cudaSuccess) {
         first_err = e;

@@ -151,6 +151,8 @@ struct SpecTables {
   const double* inv;     // Thomas 1/pivot per (kz, j, kx)
   const double* segf;    // products of the forward multipliers per (kz, segment of TRI_SEG rows, kx)
   const double* segb;    // ... and of the backward multipliers
+  const int* jc;         // per (kz, kx): first row of the stationary run of the factorisation (rows
+                         // jc .. ny-2 hold the same 1/pivot and c' bit for bit); ny - 1 if none
   const double* pal;     // non-uniform wall-normal grid: forward multipliers (inv then holds
                          // height / pivot and cp the c' of the height-scaled rows); null if uniform
 };
@@ -173,7 +175,7 @@ void launch_pressure_recon(const Geo& g, const Surf& s, const Fields<T>& f, cons
 void launch_build_poisson_tables_nu(const Geo& g, const double* lamx, const double* lamz, double* cp, double* ivh,
                                     double* al, cudaStream_t st);
 void launch_build_poisson_tables(const Geo& g, const double* lamx, const double* lamz, double* cp, double* inv,
-                                 double* segf, double* segb,
+                                 double* segf, double* segb, int* jc,
                                  cudaStream_t st);
 
 }  // namespace ibm

@@ -16,6 +16,8 @@
 #include <algorithm>
 #include <type_traits>
 
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "launch.h"
 
@@ -922,6 +924,217 @@ struct FftPlaneInv {
   }
 };
 
+// ---------------------------------------------------------------------------
+// The per-plane transforms split over a cluster of CL blocks (distributed
+// shared memory).  Block r of a plane's cluster holds rows k of
+// [r nzc, (r + 1) nzc), nzc = nz / CL, of the plane's half-spectrum in its own
+// shared memory.  Forward: each block forms and x-transforms its own rows,
+// then, after a cluster barrier, z-transforms its share of the kx columns,
+// reading every column's rows from the blocks that hold them.  Inverse: the
+// z transforms write their columns' rows into the holders' shared memory,
+// and after the barrier each block x-transforms its own rows.  A 128^3 plane
+// then runs as 4 blocks of 256 threads with 52 KB each, several clusters
+// per SM, so one block's global loads overlap another's transforms, on
+// every SM.
+// ---------------------------------------------------------------------------
+template <typename T, int CL>
+__device__ __forceinline__ void fft_plane_fwd_cl(const Blk& bk, const Geo& g, const Fields<T>& f,
+                                                 const unsigned* __restrict__ flags32, const T* __restrict__ twx,
+                                                 const T* __restrict__ twz, const FftPlan& px, const FftPlan& pz,
+                                                 int wbuf, int cz, const DevState* ds, int s, int use_q,
+                                                 double scale, int mode, const ProjCoef<T>& cf, unsigned* res1) {
+  using C = typename Cplx<T>::type;
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ unsigned char smem_raw[];
+  const int nx = g.nx, nz = g.nz, nkx = g.nkx, ny = g.ny;
+  const int r = (int)cl.block_rank();
+  const int j = (int)(bk.x / CL);
+  const int nzc = nz / CL;
+  C* S = reinterpret_cast<C*>(smem_raw);   // [k - r nzc][kx]
+  C* bufa = S + (size_t)nzc * nkx;
+  C* bufb = bufa + wbuf;
+  const int lc = max(1, wbuf / nx);
+  const T qf = use_q ? (T)ds->qf[s] : (T)0;
+  const T qa = use_q == 2 ? (T)ds->qa[s] : (T)0, qb = use_q == 2 ? (T)ds->qb[s] : (T)0;
+  const int nlines = nzc / 2;
+  const RowY<T> ry = row_y<T>(g, f, cf, j);
+  if (mode == 0) clear_residual(bk, res1);
+  unsigned rmax = 0u;
+  // x: this block's rows, lc complex lines (row pairs) at a time
+  for (int l0 = 0; l0 < nlines; l0 += lc) {
+    const int nl = min(lc, nlines - l0);
+    __syncthreads();
+#pragma unroll 4
+    for (int t = threadIdx.x; t < nl * nx; t += blockDim.x) {
+      const int l = t / nx, i = t - l * nx;
+      const int k0 = r * nzc + 2 * (l0 + l);
+      C z;
+      z.x = poisson_rhs<T>(g, f, flags32, ds, s, use_q, scale, mode, cf, ry, qf, qa, qb, i, j, k0, rmax);
+      z.y = poisson_rhs<T>(g, f, flags32, ds, s, use_q, scale, mode, cf, ry, qf, qa, qb, i, j, k0 + 1, rmax);
+      bufa[t] = z;
+    }
+    const int res = fft_lines<T, false>(bufa, bufb, nl, px, reinterpret_cast<const C*>(twx));
+    const C* out = res == 0 ? bufa : bufb;
+    for (int t = threadIdx.x; t < nl * nkx; t += blockDim.x) {
+      const int l = t / nkx, kx = t - l * nkx;
+      const C Z = out[l * nx + kx];
+      const C Zc = cconj(out[l * nx + (kx == 0 ? 0 : nx - kx)]);
+      C Xa, Xb;
+      Xa.x = (T)0.5 * (Z.x + Zc.x);
+      Xa.y = (T)0.5 * (Z.y + Zc.y);
+      Xb.x = (T)0.5 * (Z.y - Zc.y);   // Xb = (Z - Zc) / (2 i)
+      Xb.y = (T)-0.5 * (Z.x - Zc.x);
+      const int kl = 2 * (l0 + l);
+      S[kl * nkx + kx] = Xa;
+      S[(kl + 1) * nkx + kx] = Xb;
+    }
+  }
+  if (mode == 3) fold_residual(res1, rmax);
+  cl.sync();   // every block's rows are in its shared memory
+  // z: this block's columns [c0, c1), cz at a time, gathered from the holders
+  const int cw = (nkx + CL - 1) / CL;
+  const int c0 = r * cw, c1 = min(nkx, c0 + cw);
+  const unsigned mcz = magic_div_dev(cz);
+  C* spec = reinterpret_cast<C*>(f.spec);
+  for (int kx0 = c0; kx0 < c1; kx0 += cz) {
+    const int w = min(cz, c1 - kx0);
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < CL; ++q) {
+      const C* Sq = cl.map_shared_rank(S, q);
+      C* dst = bufa + (size_t)q * nzc * cz;
+      for (int t = threadIdx.x; t < nzc * cz; t += blockDim.x) {
+        const int kl = (int)fdiv((unsigned)t, mcz), c = t - kl * cz;
+        C z;
+        z.x = z.y = (T)0;
+        if (c < w) z = Sq[kl * nkx + kx0 + c];
+        dst[t] = z;
+      }
+    }
+    const int res = fft_lines<T, false>(bufa, bufb, cz, pz, reinterpret_cast<const C*>(twz), cz, 1, mcz);
+    const C* out = res == 0 ? bufa : bufb;
+#pragma unroll 4
+    for (int t = threadIdx.x; t < nz * cz; t += blockDim.x) {
+      const int k = (int)fdiv((unsigned)t, mcz), c = t - k * cz;
+      if (c < w) spec[((long long)k * ny + j) * nkx + kx0 + c] = out[t];
+    }
+  }
+  cl.sync();   // no block leaves while a peer may still read its rows
+}
+template <typename T, int CL>
+struct FftPlaneFwdCl {
+  static constexpr int kThreads = 256;
+  static constexpr int kMinBlocks = 4;
+  Geo g;
+  Fields<T> f;
+  const unsigned* flags32;
+  const T* twx;
+  const T* twz;
+  FftPlan px, pz;
+  int wbuf, cz;
+  const DevState* ds;
+  int s, use_q;
+  double scale;
+  int mode;
+  ProjCoef<T> cf;
+  unsigned* res1;
+  __device__ __forceinline__ void operator()(const Blk& bk) const {
+    fft_plane_fwd_cl<T, CL>(bk, g, f, flags32, twx, twz, px, pz, wbuf, cz, ds, s, use_q, scale, mode, cf, res1);
+  }
+};
+
+template <typename T, int CL>
+__device__ __forceinline__ void fft_plane_inv_cl(const Blk& bk, const Geo& g, const Fields<T>& f,
+                                                 const T* __restrict__ twx, const T* __restrict__ twz,
+                                                 const FftPlan& px, const FftPlan& pz, int wbuf, int cz,
+                                                 T* __restrict__ out_phi) {
+  using C = typename Cplx<T>::type;
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ unsigned char smem_raw[];
+  const int nx = g.nx, nz = g.nz, nkx = g.nkx, ny = g.ny;
+  const int r = (int)cl.block_rank();
+  const int j = (int)(bk.x / CL);
+  const int nzc = nz / CL;
+  C* S = reinterpret_cast<C*>(smem_raw);   // [k - r nzc][kx]
+  C* bufa = S + (size_t)nzc * nkx;
+  C* bufb = bufa + wbuf;
+  const C* spec = reinterpret_cast<const C*>(f.spec);
+  // z inverse: this block's columns from global, into the holders' rows
+  const int cw = (nkx + CL - 1) / CL;
+  const int c0 = r * cw, c1 = min(nkx, c0 + cw);
+  const unsigned mcz = magic_div_dev(cz);
+  for (int kx0 = c0; kx0 < c1; kx0 += cz) {
+    const int w = min(cz, c1 - kx0);
+    __syncthreads();
+#pragma unroll 4
+    for (int t = threadIdx.x; t < nz * cz; t += blockDim.x) {
+      const int k = (int)fdiv((unsigned)t, mcz), c = t - k * cz;
+      C z;
+      z.x = z.y = (T)0;
+      if (c < w) z = spec[((long long)k * ny + j) * nkx + kx0 + c];
+      bufa[t] = z;
+    }
+    const int res = fft_lines<T, true>(bufa, bufb, cz, pz, reinterpret_cast<const C*>(twz), cz, 1, mcz);
+    const C* out = res == 0 ? bufa : bufb;
+#pragma unroll
+    for (int q = 0; q < CL; ++q) {
+      C* Sq = cl.map_shared_rank(S, q);
+      const C* src = out + (size_t)q * nzc * cz;
+      for (int t = threadIdx.x; t < nzc * cz; t += blockDim.x) {
+        const int kl = (int)fdiv((unsigned)t, mcz), c = t - kl * cz;
+        if (c < w) Sq[kl * nkx + kx0 + c] = src[t];
+      }
+    }
+  }
+  cl.sync();   // every block's rows are complete (written by the whole cluster)
+  // x inverse: two half-spectra (rows k, k + 1) -> one complex line -> two real rows
+  const int lc = max(1, wbuf / nx);
+  const int nlines = nzc / 2;
+  for (int l0 = 0; l0 < nlines; l0 += lc) {
+    const int nl = min(lc, nlines - l0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < nl * nx; t += blockDim.x) {
+      const int l = t / nx, kx = t - l * nx;
+      const int kl = 2 * (l0 + l);
+      const bool mirror = kx >= nkx;
+      const int q = mirror ? nx - kx : kx;
+      C A = S[kl * nkx + q], B = S[(kl + 1) * nkx + q];
+      if (q == 0 || 2 * q == nx) { A.y = (T)0; B.y = (T)0; }   // real DC / Nyquist bins
+      if (mirror) { A = cconj(A); B = cconj(B); }
+      C z;  // A + i B
+      z.x = A.x - B.y;
+      z.y = A.y + B.x;
+      bufa[t] = z;
+    }
+    const int res = fft_lines<T, true>(bufa, bufb, nl, px, reinterpret_cast<const C*>(twx));
+    const C* out = res == 0 ? bufa : bufb;
+#pragma unroll 4
+    for (int t = threadIdx.x; t < nl * nx; t += blockDim.x) {
+      const int l = t / nx, i = t - l * nx;
+      const int k0 = r * nzc + 2 * (l0 + l);
+      out_phi[((long long)k0 * ny + j) * nx + i] = out[t].x;
+      out_phi[((long long)(k0 + 1) * ny + j) * nx + i] = out[t].y;
+    }
+  }
+}
+template <typename T, int CL>
+struct FftPlaneInvCl {
+  static constexpr int kThreads = 256;
+  static constexpr int kMinBlocks = 4;
+  Geo g;
+  Fields<T> f;
+  const T* twx;
+  const T* twz;
+  FftPlan px, pz;
+  int wbuf, cz;
+  T* out_phi;
+  __device__ __forceinline__ void operator()(const Blk& bk) const {
+    fft_plane_inv_cl<T, CL>(bk, g, f, twx, twz, px, pz, wbuf, cz, out_phi);
+  }
+};
+
 // z transform of the half-spectrum, in place; a block takes `cols` adjacent
 // kx columns of one y-plane (coalesced rows of `cols` complex values), kept
 // in shared memory in load order [k][column] and transformed as strided
@@ -1335,7 +1548,7 @@ struct TriY {
 template <typename T, int L>
 __device__ __forceinline__ void tri_y_warp(const Blk& bk, const Geo& g, const Fields<T>& f, const double* __restrict__ cp,
                                            const double* __restrict__ inv, const double* __restrict__ segf,
-                                           const double* __restrict__ segb) {
+                                           const double* __restrict__ segb, const int* __restrict__ jcv) {
   using C = typename Cplx<T>::type;
   constexpr int Rr = TRI_SEG;
   constexpr int G = 32 / L;
@@ -1357,6 +1570,14 @@ __device__ __forceinline__ void tri_y_warp(const Blk& bk, const Geo& g, const Fi
   const int j0 = sl * Rr;
   const bool rows = live && j0 < ny;            // the lane holds at least one row
   const unsigned FULL = 0xFFFFFFFFu;
+  // rows jc .. ny-2 share one (1/pivot, c') pair, read once
+  const int jc = live ? __ldg(jcv + (long long)kz * nkx + kx) : ny;
+  double ivc = 0.0, cpc = 0.0;
+  if (live && jc < ny - 1 && j0 + Rr > jc) {
+    const long long idc = base + (long long)jc * stride;
+    ivc = __ldg(inv + idc);
+    cpc = __ldg(cp + idc);
+  }
   // ---- every load of the lane's rows, issued together; br = r / piv
   double br[Rr], bi[Rr], cq[Rr];
   bool special = false;   // an FP32 input the integer conversion leaves to the hardware
@@ -1367,8 +1588,9 @@ __device__ __forceinline__ void tri_y_warp(const Blk& bk, const Geo& g, const Fi
     if (live && j < ny) {
       const long long id = base + (long long)j * stride;
       const C z = spec[id];
-      const double iv = __ldg(inv + id);
-      cq[u] = __ldg(cp + id);
+      const bool tab = j < jc || j == ny - 1;
+      const double iv = tab ? __ldg(inv + id) : ivc;
+      cq[u] = tab ? __ldg(cp + id) : cpc;
       if constexpr (sizeof(T) == 4) {
         br[u] = f2d_int(z.x, special) * iv;
         bi[u] = f2d_int(z.y, special) * iv;
@@ -1385,7 +1607,7 @@ __device__ __forceinline__ void tri_y_warp(const Blk& bk, const Geo& g, const Fi
       if (live && j < ny) {
         const long long id = base + (long long)j * stride;
         const C z = spec[id];
-        const double iv = __ldg(inv + id);
+        const double iv = (j < jc || j == ny - 1) ? __ldg(inv + id) : ivc;
         br[u] = (double)z.x * iv;
         bi[u] = (double)z.y * iv;
       }
@@ -1520,16 +1742,18 @@ __device__ __forceinline__ void tri_y_warp(const Blk& bk, const Geo& g, const Fi
     }
   }
 }
-template <typename T, int L>
+template <typename T, int L, int MB = 1>
 struct TriYWarp {
   static constexpr int kThreads = 128;
+  static constexpr int kMinBlocks = MB;   // 7: registers capped so 7 blocks fit an SM
   Geo g;
   Fields<T> f;
   const double* cp;
   const double* inv;
   const double* segf;
   const double* segb;
-  __device__ __forceinline__ void operator()(const Blk& bk) const { tri_y_warp<T, L>(bk, g, f, cp, inv, segf, segb); }
+  const int* jc;
+  __device__ __forceinline__ void operator()(const Blk& bk) const { tri_y_warp<T, L>(bk, g, f, cp, inv, segf, segb, jc); }
 };
 
 // Sequential Thomas per (kx, kz, part) with the forward values in shared
@@ -1611,7 +1835,7 @@ struct TriYSmem {
 
 // Tabulate the pivots of every (kx, kz) system once per grid.
 __global__ void k_build_tri_tables(Geo g, const double* __restrict__ lamx, const double* __restrict__ lamz,
-                                   double* cp, double* inv, double* segf, double* segb) {
+                                   double* cp, double* inv, double* segf, double* segb, int* jc) {
   const int nkx = g.nkx;
   const long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (l >= (long long)nkx * g.nz) return;
@@ -1635,6 +1859,21 @@ __global__ void k_build_tri_tables(Geo g, const double* __restrict__ lamx, const
     // multiplier of its forward step (no backward step reads it)
     cp[base + (long long)j * stride] = j == g.ny - 1 ? a * iv : cprev;
   }
+  // With lam > 0 the pivots of the constant-coefficient rows converge
+  // geometrically in j and reach a fixed point in FP64 well before the last
+  // row for all but the smallest wavenumbers.  The run of rows that repeat
+  // row ny - 2's pair exactly, bit for bit, is found here; the solve holds
+  // that pair in registers instead of reading it per row.
+  int j1 = g.ny - 1;
+  if (g.ny >= 3) {
+    const long long e = base + (long long)(g.ny - 2) * stride;
+    const long long ive = __double_as_longlong(inv[e]), cpe = __double_as_longlong(cp[e]);
+    j1 = g.ny - 2;
+    while (j1 > 1 && __double_as_longlong(inv[base + (long long)(j1 - 1) * stride]) == ive &&
+           __double_as_longlong(cp[base + (long long)(j1 - 1) * stride]) == cpe)
+      --j1;
+  }
+  jc[l] = j1;
   // products of the forward (-c'_j, j > 0) and backward (-c'_j, j < ny - 1)
   // multipliers over each segment of TRI_SEG rows, in the order in which the
   // warp-cooperative solve composes them
@@ -1693,9 +1932,9 @@ void launch_build_poisson_tables_nu(const Geo& g, const double* lamx, const doub
 }
 
 void launch_build_poisson_tables(const Geo& g, const double* lamx, const double* lamz, double* cp, double* inv,
-                                 double* segf, double* segb, cudaStream_t st) {
+                                 double* segf, double* segb, int* jc, cudaStream_t st) {
   const long long lines = (long long)g.nkx * g.nz;
-  k_build_tri_tables<<<(unsigned)((lines + 127) / 128), 128, 0, st>>>(g, lamx, lamz, cp, inv, segf, segb);
+  k_build_tri_tables<<<(unsigned)((lines + 127) / 128), 128, 0, st>>>(g, lamx, lamz, cp, inv, segf, segb, jc);
 }
 
 // ---------------------------------------------------------------------------
@@ -1817,8 +2056,14 @@ struct Project {
 // A kernel of the correction solve: does its work only when the first
 // solve's residual exceeds the budget (every block reads the decision the
 // correction's forward transform completed before this launch).
+template <class Op, bool = HasMinBlocks<Op>::value>
+struct MinBlocksOf {};
 template <class Op>
-struct Gated {
+struct MinBlocksOf<Op, true> {
+  static constexpr int kMinBlocks = Op::kMinBlocks;
+};
+template <class Op>
+struct Gated : MinBlocksOf<Op> {
   static constexpr int kThreads = Op::kThreads;
   Op op;
   const DevState* ds;
@@ -2095,7 +2340,7 @@ void launch_poisson(const Geo& g, const Fields<T>& f, const TagBuffers& b, const
     using Op = std::decay_t<decltype(op)>;
     if constexpr (sizeof(T) == 4) {
       if (gate) {
-        ex.launch(gr, bl, sm, Gated<Op>{op, ds, sg.s});
+        ex.launch(gr, bl, sm, Gated<Op>{{}, op, ds, sg.s});
         return;
       }
     }
@@ -2123,15 +2368,23 @@ void launch_poisson(const Geo& g, const Fields<T>& f, const TagBuffers& b, const
     if (tri == 3) {
       glaunch(dim3((unsigned)((2 * tlines + tsm - 1) / tsm)), dim3(tsm), (size_t)tsm * 8 * sh.ny,
                 TriYSmem<T>{g, f, tb.cp, tb.inv});
-    } else if (tri == 1 && sh.ny <= 8 * TRI_SEG) {
-      const long long warps = (long long)((g.nkx + 3) / 4) * g.nz;
-      glaunch(dim3((unsigned)((warps * 32 + 127) / 128)), dim3(128), 0, TriYWarp<T, 8>{g, f, tb.cp, tb.inv, tb.segf, tb.segb});
-    } else if (tri == 1 && sh.ny <= 16 * TRI_SEG) {
-      const long long warps = (long long)((g.nkx + 1) / 2) * g.nz;
-      glaunch(dim3((unsigned)((warps * 32 + 127) / 128)), dim3(128), 0, TriYWarp<T, 16>{g, f, tb.cp, tb.inv, tb.segf, tb.segb});
     } else if (tri == 1) {
-      const long long warps = (long long)g.nkx * g.nz;
-      glaunch(dim3((unsigned)((warps * 32 + 127) / 128)), dim3(128), 0, TriYWarp<T, 32>{g, f, tb.cp, tb.inv, tb.segf, tb.segb});
+      // L lanes per system: G = 32 / L systems per warp.  Unless the tuning
+      // asks for the uncapped form (1), registers are capped so that 7
+      // blocks fit an SM (a 128^2-wavenumber grid then runs in one wave)
+      const bool cap = tu.tri_y != 1;
+      const int L = sh.ny <= 8 * TRI_SEG ? 8 : (sh.ny <= 16 * TRI_SEG ? 16 : 32);
+      const long long warps = (long long)((g.nkx + 32 / L - 1) / (32 / L)) * g.nz;
+      const dim3 gr((unsigned)((warps * 32 + 127) / 128)), bl(128);
+      auto warp_op = [&](auto lanes, auto mb) {
+        glaunch(gr, bl, 0, TriYWarp<T, decltype(lanes)::value, decltype(mb)::value>{g, f, tb.cp, tb.inv, tb.segf,
+                                                                                    tb.segb, tb.jc});
+      };
+      using I1 = std::integral_constant<int, 1>;
+      using I7 = std::integral_constant<int, 7>;
+      if (L == 8) cap ? warp_op(std::integral_constant<int, 8>{}, I7{}) : warp_op(std::integral_constant<int, 8>{}, I1{});
+      else if (L == 16) cap ? warp_op(std::integral_constant<int, 16>{}, I7{}) : warp_op(std::integral_constant<int, 16>{}, I1{});
+      else cap ? warp_op(std::integral_constant<int, 32>{}, I7{}) : warp_op(std::integral_constant<int, 32>{}, I1{});
     } else {
       // blocks of two warps: the systems of a 128^3 grid then spread over
       // every SM, about one warp per SM sub-partition
@@ -2157,17 +2410,54 @@ void launch_poisson(const Geo& g, const Fields<T>& f, const TagBuffers& b, const
   // (opt-in: on a 128^3 plate one block per plane is latency-bound and
   // slower than the separate x and z kernels, which stay the default)
   const bool plane = tu.fft_plane == 2 && lcp >= 1 && (long long)czp * sh.nz <= wmax && smp <= 200 * 1024;
+  // the per-plane transforms split over a cluster of CLN blocks (one
+  // simulation, nz a multiple of 2 CLN; the built-in choice where it fits):
+  // each block's rows and work buffers within 100 KB of shared memory, so at
+  // least two blocks share an SM
+  constexpr int CLN = 4;
+  bool cluster = false;
+  int wbc = 0, czc = 0;
+  size_t smc = 0;
+  if (!ex.rec && (tu.fft_plane == 3 || tu.fft_plane == 0) && sh.nz % (2 * CLN) == 0 && sh.nkx >= CLN) {
+    const int nzc = sh.nz / CLN, cw = (sh.nkx + CLN - 1) / CLN;
+    const long long sb = (long long)nzc * sh.nkx * (long long)sizeof(C);
+    const long long wm = (100ll * 1024 - sb) / (2 * (long long)sizeof(C));
+    const long long lcc = std::min<long long>(nzc / 2, wm / sh.nx);
+    const long long cmax = std::min<long long>(cw, wm / sh.nz);
+    if (lcc >= 1 && cmax >= 1) {
+      const long long nch = (cw + cmax - 1) / cmax;
+      czc = (int)((cw + nch - 1) / nch);
+      wbc = (int)std::max<long long>(lcc * sh.nx, (long long)czc * sh.nz);
+      smc = (size_t)sb + 2ull * wbc * sizeof(C);
+      cluster = true;
+    }
+  }
+  auto glaunch_cl = [&](dim3 gr, dim3 bl, size_t sm, const auto& op) {
+    using Op = std::decay_t<decltype(op)>;
+    if constexpr (sizeof(T) == 4) {
+      if (gate) {
+        ex.launch_cluster(gr, bl, sm, Gated<Op>{{}, op, ds, sg.s}, CLN);
+        return;
+      }
+    }
+    ex.launch_cluster(gr, bl, sm, op, CLN);
+  };
   // the rest of one solve: z transform, wall-normal Thomas, inverse z and x
   // (the first solve marks each kernel group; the correction solve keeps its
   // forward transforms in one group and marks its Thomas and inverse
   // transforms separately)
   auto solve_rest = [&](T* out, bool first) {
-    if (!plane) {
+    if (!plane && !cluster) {
       if (first) ex.mark(ST_FFT_Z_FWD);
       glaunch(dim3(g.ny * ntile), dim3(256), smz, FftZ<T, false>{g, f, tb.twz, pz, cols});
     }
     ex.mark(first ? ST_TRI_Y : ST_CORR_TRI);
     tri_solve();
+    if (cluster) {
+      ex.mark(first ? ST_FFT_X_INV : ST_CORR_INV);
+      glaunch_cl(dim3(g.ny * CLN), dim3(256), smc, FftPlaneInvCl<T, CLN>{g, f, tb.twx, tb.twz, px, pz, wbc, czc, out});
+      return;
+    }
     if (plane) {
       ex.mark(first ? ST_FFT_X_INV : ST_CORR_INV);
       glaunch(dim3(g.ny), dim3(1024), smp, FftPlaneInv<T>{g, f, tb.twx, tb.twz, px, pz, wbuf, czp, out});
@@ -2185,7 +2475,12 @@ void launch_poisson(const Geo& g, const Fields<T>& f, const TagBuffers& b, const
   cf.bx = (T)(bb * g.idx * g.idx); cf.by = (T)(bb * g.idy * g.idy); cf.bz = (T)(bb * g.idz * g.idz);
   cf.adt = (T)adt; cf.bb = (T)bb;
   auto forward = [&](int mode) {
-    if (plane)
+    if (cluster)
+      ex.launch_cluster(dim3(g.ny * CLN), dim3(256), smc,
+                        FftPlaneFwdCl<T, CLN>{g, f, b.flags32, tb.twx, tb.twz, px, pz, wbc, czc, ds, sg.s, use_q,
+                                              scale, mode, cf, ds->res1 + sg.s},
+                        CLN);
+    else if (plane)
       ex.launch(dim3(g.ny), dim3(1024), smp,
                 FftPlaneFwd<T>{g, f, b.flags32, tb.twx, tb.twz, px, pz, wbuf, czp, ds, sg.s, use_q, scale, mode, cf,
                                ds->res1 + sg.s});
@@ -2226,7 +2521,10 @@ void set_fft_smem_limits() {
   op_smem_limit<TriYSmem<T>>(160 * 1024);
   op_smem_limit<FftPlaneFwd<T>>(200 * 1024);
   op_smem_limit<FftPlaneInv<T>>(200 * 1024);
+  op_smem_limit<FftPlaneFwdCl<T, 4>>(100 * 1024);
+  op_smem_limit<FftPlaneInvCl<T, 4>>(100 * 1024);
   if constexpr (sizeof(T) == 4) {   // the correction solve's kernels (mixed path)
+    op_smem_limit<Gated<FftPlaneInvCl<T, 4>>>(100 * 1024);
     op_smem_limit<Gated<FftXInv<T>>>(maxsm);
     op_smem_limit<Gated<FftZ<T, false>>>(maxsm);
     op_smem_limit<Gated<FftZ<T, true>>>(maxsm);

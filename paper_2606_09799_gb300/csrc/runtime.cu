@@ -181,7 +181,7 @@ struct ibm_grid {
   void* qk;                  // q_F per cell (energy-conserving shape)
   // tables
   void* sweep_mem[24];
-  double* pcp; double* pinv; double* psegf; double* psegb; double* lamx; double* lamz;
+  double* pcp; double* pinv; double* psegf; double* psegb; int* pjc; double* lamx; double* lamz;
   double* pal;     // non-uniform wall-normal grid: forward multipliers of the Poisson rows, else null
   double* ytab;    // non-uniform wall-normal grid: 1/heights (ny), 1/centre distances (ny+1), heights (ny),
                    // centre distances (ny+1), centre rows (ny+2), face rows (ny+3)
@@ -477,6 +477,7 @@ static SpecTables<T> spec_tables(ibm_handle h) {
   s.inv = h->pinv;
   s.segf = h->psegf;
   s.segb = h->psegb;
+  s.jc = h->pjc;
   s.pal = h->pal;
   return s;
 }
@@ -916,7 +917,7 @@ struct Knob {
 };
 
 static std::vector<Knob> tune_knobs() {
-  return {{&Tune::fft_plane, {2, 1}}, {&Tune::sweep_zy, {2, 1}}, {&Tune::sweep_y, {1, 2, 3, 4}}, {&Tune::tri_y, {1, 2, 3}},
+  return {{&Tune::fft_plane, {3, 2, 1}}, {&Tune::sweep_zy, {2, 1}}, {&Tune::sweep_y, {1, 2, 3, 4}}, {&Tune::tri_y, {1, 4, 2, 3}},
           {&Tune::sweep_w, {64, 32, 16}},
           {&Tune::fft_lpb, {0, 8, 4, 2}},
           {&Tune::fft_cols, {16, 8, 4}}};
@@ -1198,13 +1199,15 @@ ibm_status ibm_create_grid(const ibm_grid_desc* desc, void* stream, ibm_handle* 
   const size_t nsegs = (size_t)g.nz * ((g.ny + TRI_SEG - 1) / TRI_SEG) * g.nkx;
   h->psegf = (double*)dalloc(h, nsegs * 8);
   h->psegb = (double*)dalloc(h, nsegs * 8);
-  if (!ok || !h->lamx || !h->lamz || !h->twx || !h->twz || !h->pcp || !h->pinv || !h->psegf || !h->psegb) {
+  h->pjc = (int*)dalloc(h, (size_t)g.nz * g.nkx * sizeof(int));
+  if (!ok || !h->lamx || !h->lamz || !h->twx || !h->twz || !h->pcp || !h->pinv || !h->psegf || !h->psegb ||
+      !h->pjc) {
     release_all(h);
     delete h;
     return IBM_ERR_OOM;
   }
   cudaStream_t st = h->user;
-  launch_build_poisson_tables(g, h->lamx, h->lamz, h->pcp, h->pinv, h->psegf, h->psegb, st);
+  launch_build_poisson_tables(g, h->lamx, h->lamz, h->pcp, h->pinv, h->psegf, h->psegb, h->pjc, st);
   // state at rest
   cudaMemsetAsync(h->u, 0, ncell * es, st);
   cudaMemsetAsync(h->v, 0, nvf * es, st);
@@ -1750,12 +1753,12 @@ ibm_status ibm_profile_stages(ibm_handle h, int nsteps, double* ms, int64_t* ker
 // ---- tuning -------------------------------------------------------------------
 static bool tune_valid(const ibm_tune* t) {
   if (!t) return false;
-  if (t->tri_y < 0 || t->tri_y > 3) return false;
+  if (t->tri_y < 0 || t->tri_y > 4) return false;
   if (t->sweep_w != 0 && t->sweep_w != 16 && t->sweep_w != 32 && t->sweep_w != 64) return false;
   if (t->fft_lpb < 0 || t->fft_lpb > 2048) return false;
   if (t->fft_cols < 0 || t->fft_cols > 16 || (t->fft_cols & (t->fft_cols - 1))) return false;
   if (t->sweep_zy < 0 || t->sweep_zy > 2) return false;
-  if (t->fft_plane < 0 || t->fft_plane > 2) return false;
+  if (t->fft_plane < 0 || t->fft_plane > 3) return false;
   if (t->sweep_y < 0 || t->sweep_y > 4) return false;
   return true;
 }

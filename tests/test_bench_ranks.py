@@ -76,4 +76,8 @@ def test_traffic_lookup_follows_the_kernel_source(tmp_path):
     assert bench.ncu_traffic("sweep_y", "SweepYStream<float>", str(summary), str(tmp_path)) is None
     assert bench.stage_kernel("sweep_y", {"sweep_y": 1}, "mixed") == "SweepYStream<float>"
     assert bench.stage_kernel("tri_y", {"tri_y": 3}, "fp64") == "TriYSmem<double>"
-    assert bench.stage_kernel("tri_y", {"tri_y": 0}, "mixed", 128) == "TriYWarp<float, 16>"
+    assert bench.stage_kernel("tri_y", {"tri_y": 0}, "mixed", 128) == "TriYWarp<float, 16, 7>"
+    assert bench.stage_kernel("tri_y", {"tri_y": 1}, "mixed", 128) == "TriYWarp<float, 16, 1>"
+    assert bench.stage_kernel("fft_x_fwd", {}, "mixed") == "FftPlaneFwdCl<float, 4>"
+    assert bench.stage_kernel("fft_x_fwd", {"fft_plane": 0}, "mixed", 37, 60) == "FftXFwd<float>"
+    assert bench.stage_kernel("fft_x_fwd", {"fft_plane": 2}, "fp64") == "FftPlaneFwd<double>"

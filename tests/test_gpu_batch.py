@@ -28,8 +28,10 @@ def make(wl, precision):
     return ibm.Simulation(wl.nx, wl.ny, wl.nz, wl.lx, wl.ly, wl.lz, re=wl.re, dt=wl.dt, precision=precision)
 
 
-def run_solo(wl, nsteps, precision):
+def run_solo(wl, nsteps, precision, **tune):
     g = make(wl, precision)
+    if tune:
+        ibm.ibm_set_tune(g.h, **tune)
     for s in range(nsteps):
         xyz, vel = wl.surface(s)
         g.set_surface(xyz, vel, wl.tri)
@@ -62,7 +64,9 @@ def test_batch_fp64_bit_identical_to_solo():
     assert info["cells"] == sum(w.cells for w in wls)
     assert info["launches_per_step"] < info["launches_per_step_solo"]
     for w, g in zip(wls, sims):
-        ref = run_solo(w, 3, "fp64")
+        # the batch's built-in transforms are the separate x and z kernels (a
+        # cluster of blocks per plane is a one-simulation form): the same here
+        ref = run_solo(w, 3, "fp64", fft_plane=1)
         for a, r in zip(g.fields(), ref.fields()):
             np.testing.assert_array_equal(a, r)
         for a, r in zip(g.tags(), ref.tags()):
@@ -120,6 +124,8 @@ def test_batch_rebuilds_when_a_surface_changes_size():
     sims = [make(w, "fp64") for w in wls]
     b = ibm.Batch(sims)
     refs = [make(w, "fp64") for w in wls]
+    for r in refs:       # the batch's built-in transforms: separate x and z kernels
+        ibm.ibm_set_tune(r.h, fft_plane=1)
     alt_xyz, alt_tri = inputs.icosphere(2, 0.12, (0.5, 0.5, 0.5))     # 320 triangles
     for s in range(4):
         for k, (w, g, r) in enumerate(zip(wls, sims, refs)):
@@ -223,5 +229,9 @@ def test_tune_values_are_validated():
         ibm.ibm_set_tune(g.h, fft_cols=3)
     with pytest.raises(ibm.IbmError):
         ibm.ibm_set_tune(g.h, sweep_y=5)
+    with pytest.raises(ibm.IbmError):
+        ibm.ibm_set_tune(g.h, fft_plane=4)
+    with pytest.raises(ibm.IbmError):
+        ibm.ibm_set_tune(g.h, tri_y=5)
     ibm.ibm_set_tune(g.h, tri_y=2, sweep_w=16, fft_lpb=4, fft_cols=4)
     assert ibm.ibm_get_tune(g.h)["sweep_w"] == 16

@@ -292,7 +292,9 @@ def test_candidate_capacity_grows_for_large_triangles():
                                   dict(tri_y=1, sweep_y=3, fft_plane=2),
                                   dict(tri_y=2, sweep_y=3, fft_plane=2),
                                   dict(tri_y=1, sweep_y=4, fft_plane=2),
-                                  dict(tri_y=3, sweep_y=4, fft_plane=1)])
+                                  dict(tri_y=3, sweep_y=4, fft_plane=1),
+                                  dict(tri_y=4, sweep_y=4, fft_plane=3),
+                                  dict(tri_y=0, fft_plane=0)])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-5)])
 def test_every_launch_shape_matches_oracle(tune, precision, tol):
     """Every choice the autotuner can make (Thomas variant, sweep form and
@@ -314,6 +316,55 @@ def test_every_launch_shape_matches_oracle(tune, precision, tol):
     assert err <= tol, err
     for c, own in enumerate(g.tags()):
         np.testing.assert_array_equal(own, o.owners[c])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_cluster_plane_transforms_and_capped_thomas_equal_the_plain_forms(precision):
+    """The per-plane transforms split over a cluster of 4 blocks (fft_plane 3)
+    and the register-capped warp Thomas (tri_y 4) do the arithmetic of the
+    one-block plane transform (fft_plane 2) and the uncapped Thomas (tri_y 1)
+    element by element, only on other threads: the fields agree to rounding
+    after 3 steps with a moving sphere (48 x 37 x 96: 25 kx columns split
+    7/7/7/4 over the cluster; 24 rows per block)."""
+    wl = inputs.oscillating_sphere(n=48, steps=3, subdiv=2)
+    sims = []
+    for tune in (dict(tri_y=1, fft_plane=2), dict(tri_y=4, fft_plane=3)):
+        g = ibm.Simulation(48, 37, 96, 1.0, 0.9, 1.6, re=150.0, dt=2e-3, precision=precision)
+        ibm.ibm_set_tune(g.h, sweep_y=4, **tune)
+        sims.append(g)
+    for s in range(3):
+        xyz, vel = wl.surface(s)
+        for g in sims:
+            g.set_surface(xyz, vel, wl.tri)
+            g.step()
+    tol = 1e-14 if precision == "fp64" else 1e-6
+    for a, b in zip(sims[0].fields(), sims[1].fields()):
+        assert np.abs(a - b).max() <= tol * max(1.0, np.abs(a).max())
+    for a, b in zip(sims[0].tags(), sims[1].tags()):
+        np.testing.assert_array_equal(a, b)
+
+
+def test_cluster_plane_transforms_in_chunks_match_the_plane_form():
+    """A 256 x 12 x 256 mixed grid: the cluster's rows (64 per block) and
+    columns (33) no longer fit its 100 KB of shared memory at once, so both
+    directions go in chunks (8 lines, 7 columns).  A random divergent start,
+    no body, 2 steps: fields equal to rounding to the one-block plane form."""
+    rng = np.random.default_rng(7)
+    nx, ny, nz = 256, 12, 256
+    u0 = rng.standard_normal((nz, ny, nx))
+    v0 = rng.standard_normal((nz, ny + 1, nx))
+    v0[:, 0, :] = 0.0
+    v0[:, ny, :] = 0.0
+    w0 = rng.standard_normal((nz, ny, nx))
+    out = []
+    for fp in (2, 3):
+        g = ibm.Simulation(nx, ny, nz, 1.0, 0.05, 1.0, re=100.0, dt=1e-5, precision="mixed")
+        ibm.ibm_set_tune(g.h, fft_plane=fp)
+        g.set_fields(u0, v0, w0, np.zeros((nz, ny, nx)))
+        g.step(2)
+        out.append(g.fields())
+    for a, b in zip(*out):
+        assert np.abs(a - b).max() <= 1e-6 * max(1.0, np.abs(a).max())
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
