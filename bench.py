@@ -156,15 +156,28 @@ def algorithmic_bytes_per_cell(stage: str, word: int, pairs: bool = False) -> fl
 TRAFFIC_SUMMARY = os.path.join(ROOT, "profiles", "traffic_plate128.md")
 
 
-def fft_form(tune: dict | None, nz: int = 128) -> str:
+def fft_form(tune: dict | None, nx: int = 128, nz: int = 128, word: int = 4) -> str:
     """How the launch shapes run the x and z transforms of one simulation:
-    "cluster" (fused per y-plane over a cluster of 4 blocks: fft_plane 3, and
-    the built-in choice, when nz is a multiple of 8), "plane" (fused per
-    y-plane in one block: fft_plane 2) or "split" (separate x and z kernels)."""
+    "plane" (fused per y-plane in one block: fft_plane 2, and the built-in
+    choice where the plane and its work buffers fit 200 KB of shared memory),
+    "cluster" (fused per y-plane over a cluster of 4 blocks, each within
+    100 KB: fft_plane 3, and the built-in choice where the plane does not
+    fit) or "split" (separate x and z kernels)."""
     v = (tune or {}).get("fft_plane", 0)
-    if v in (0, 3) and nz % 8 == 0:
-        return "cluster"
-    return "plane" if v == 2 else "split"
+    nkx, c = nx // 2 + 1, 2 * word          # complex word
+    plane_b = nz * nkx * c
+    wmax = (200 * 1024 - plane_b) // (2 * c)
+    lcp, cmax = min(nz // 2, wmax // nx), max(1, min(nkx, wmax // nz))
+    czp = -(-nkx // -(-nkx // cmax))
+    plane_fits = lcp >= 1 and czp * nz <= wmax and plane_b + 2 * max(lcp * nx, czp * nz) * c <= 200 * 1024
+    if v in (0, 2) and plane_fits:
+        return "plane"
+    if v in (0, 3) and nz % 8 == 0 and nkx >= 4:
+        nzc, cw = nz // 4, -(-nkx // 4)
+        wm = (100 * 1024 - nzc * nkx * c) // (2 * c)
+        if min(nzc // 2, wm // nx) >= 1 and min(cw, wm // nz) >= 1:
+            return "cluster"
+    return "split"
 
 
 def stage_kernel(stage: str, tune: dict | None, precision: str, ny: int = 128, nz: int = 128) -> str | None:
@@ -192,10 +205,10 @@ def stage_kernel(stage: str, tune: dict | None, precision: str, ny: int = 128, n
         uncapped = f"TriYWarp<{T}, {lanes}, 1>" if ny <= 256 else f"TriY<{T}>"
         return {0: warp, 4: warp, 1: uncapped, 2: f"TriY<{T}>", 3: f"TriYSmem<{T}>"}[v]
     if stage == "fft_x_fwd":
-        form = fft_form(t, nz)
+        form = fft_form(t, nz=nz, word=4 if precision == "mixed" else 8)
         return {"cluster": f"FftPlaneFwdCl<{T}, 4>", "plane": f"FftPlaneFwd<{T}>"}.get(form, f"FftXFwd<{T}>")
     if stage == "rhs":
-        return f"Rhs<{T}>"
+        return f"RhsTile<{T}, 0>" if t.get("rhs", 0) == 2 else f"Rhs<{T}, 0>"
     if stage == "project":
         return f"Project<{T}>"
     return None
@@ -405,7 +418,7 @@ def gpu_arm(args):
     hbm = peaks.get("hbm_gbs", 6800.0)
     groups = {}
     tune_h = head["tune"] or {}
-    plane = fft_form(tune_h, wl.nz) != "split"
+    plane = fft_form(tune_h, wl.nx, wl.nz, 4 if args.precision == "mixed" else 8) != "split"
     merged = {"tri_y": ("tri_y", "correction_tri")}
     if plane:
         merged["fft_x_fwd"] = ("fft_x_fwd", "correction")

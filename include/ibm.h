@@ -295,7 +295,8 @@ typedef struct {
   int fft_plane;      /* 1 separate x and z transform kernels, 2 both fused per y-plane (when its
                          half-spectrum fits shared memory), 3 both fused per y-plane over a cluster
                          of 4 blocks that share the plane through distributed shared memory (one
-                         simulation with nz a multiple of 8; the built-in choice there) */
+                         simulation with nz a multiple of 8).  Built-in: 2 where it fits, else 3,
+                         else 1 (a batch: 1) */
   int sweep_y;        /* z and y sweeps: 0 as sweep_zy, 1 one thread per line with its rows streamed
                          through registers (any line length), 2 as 1 for z, and for y tiles of 32
                          lines staged in shared memory by bulk asynchronous copies (where every row
@@ -303,6 +304,10 @@ typedef struct {
                          and for y the mixed path's tabulated FP32 rows in register batches (grids of
                          at most 1024 rows; else as 1), 4 z from tiles of 32 lines with all their rows
                          staged in shared memory (nz <= 256; else as 1), y as 3 */
+  int rhs;            /* explicit right-hand side: 1 one thread per cell reading its neighbours from
+                         global memory (the built-in choice), 2 tiles of 32 x 4 cells marching in z
+                         with the three planes of u, v, w (and two of p) and their halos staged in
+                         shared memory */
   double ms_per_step; /* set by the autotuners: measured time per step of the chosen shapes */
 } ibm_tune;
 

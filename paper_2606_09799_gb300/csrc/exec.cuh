@@ -191,11 +191,14 @@ struct Tune {
   int fft_cols;   // kx columns per block of the z transforms (power of two)
   int sweep_zy;   // z and y sweeps (FP32): 1 shared-memory tile, one thread per line; 2 several lanes per line
   int fft_plane;  // 1 separate x and z transform kernels; 2 fused per y-plane (when the plane fits);
-                  // 3 fused per y-plane over a cluster of 4 blocks (one simulation, nz a multiple of 8)
+                  // 3 fused per y-plane over a cluster of 4 blocks (one simulation, nz a multiple of 8);
+                  // 0: 2 where it fits, else 3, else 1 (a batch: 1)
   int sweep_y;    // z and y sweeps: 0 as sweep_zy; 1 one thread per line, rows streamed through registers;
                   // 2 z as 1, y from tiles staged by bulk asynchronous copies (else as 1);
                   // 3 z as 1, y from the tabulated FP32 rows in register batches (mixed path, else as 1);
                   // 4 z from shared-memory tiles of whole lines (nz <= 256, else as 1), y as 3
+  int rhs;        // explicit right-hand side: 1 (and 0) one thread per cell from global memory; 2 tiles
+                  // marching in z with planes and halos staged in shared memory
 };
 
 struct Exec {

@@ -351,6 +351,232 @@ struct Rhs {
   __device__ __forceinline__ void operator()(const Blk& bk) const { rhs<T, NU>(bk, g, f, flags32, cf, use_hp, write_h, ds); }
 };
 
+// Tiled form of the same right-hand side: a block of 32 x 4 threads takes a
+// tile of 32 x 4 cells in (i, j) and marches through RT_KC planes of k.  The
+// planes k-1, k, k+1 of u, v, w and k-1, k of p, each with a one-cell halo in
+// i and j, sit in shared memory rings, so a step loads one new plane per
+// field (its own cell plus a share of the halo) and every neighbour the
+// stencil takes comes from shared memory.  The arithmetic is the per-cell
+// kernel's, term by term, so both give the same values.
+constexpr int RT_TI = 32, RT_TJ = 4, RT_KC = 16;
+constexpr int RT_W = RT_TI + 2, RT_H = RT_TJ + 2, RT_P = RT_W * RT_H;   // one staged plane
+
+template <typename T, bool NU>
+__device__ __forceinline__ void rhs_tile(const Blk& bk, const Geo& g, const Fields<T>& f,
+                                         const unsigned* __restrict__ flags32, const RhsCoef<T>& cf, int use_hp,
+                                         int write_h, const DevState* ds) {
+  __shared__ T su[3][RT_P], sv[3][RT_P], sw[3][RT_P], sp[2][RT_P];
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const T idx = cf.idx, idy = cf.idy, idz = cf.idz;
+  const T idx2 = cf.idx2, idy2 = cf.idy2, idz2 = cf.idz2;
+  const T gs = cf.gs;
+  const T q = (T)0.25;
+  const T cg = cf.cg, cr = cf.cr, ca = cf.ca, cv = cf.cv, tdt = cf.dt;
+  T fbx, fby, fbz;
+  if constexpr (sizeof(T) == 4) {
+    fbx = cf.fba * ds->fbf[0];
+    fby = cf.fba * ds->fbf[1];
+    fbz = cf.fba * ds->fbf[2];
+  } else {
+    fbx = cf.fba * (T)ds->fb[0];
+    fby = cf.fba * (T)ds->fb[1];
+    fbz = cf.fba * (T)ds->fb[2];
+  }
+  const long long pv = (long long)(ny + 1) * nx;
+  const long long pu = (long long)ny * nx;
+  const int i0 = bk.x * RT_TI, j0 = bk.y * RT_TJ, k0 = bk.z * RT_KC;
+  const int k1 = min(nz, k0 + RT_KC);
+  const int tid = threadIdx.y * RT_TI + threadIdx.x;
+  // the (at most two) staged elements this thread loads per plane: tile
+  // column c (-1 .. RT_TI, periodic in x) and row r (-1 .. RT_TJ); rows
+  // outside a field's grid are never read by the stencil and not loaded
+  long long ou[2], ov[2];
+  bool lu[2], lv[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int e = tid + h * RT_TI * RT_TJ;
+    const int r = e / RT_W, c = e - r * RT_W;
+    const int gi = ((i0 + c - 1) % nx + nx) % nx;
+    const int gj = j0 + r - 1;
+    lu[h] = e < RT_P && gj >= 0 && gj < ny;
+    lv[h] = e < RT_P && gj >= 0 && gj <= ny;
+    ou[h] = (long long)gj * nx + gi;
+    ov[h] = ou[h];
+  }
+  auto stage = [&](T (*dst)[RT_P], const T* __restrict__ src, int slot, int k, long long pstride, const bool* live,
+                   const long long* off) {
+    const long long base = (long long)k * pstride;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int e = tid + h * RT_TI * RT_TJ;
+      if (live[h]) dst[slot][e] = src[base + off[h]];
+    }
+  };
+  // the next plane's elements travel in registers while a step computes
+  T nu[2], nv[2], nw[2], np[2];
+  auto fetch = [&](T* reg, const T* __restrict__ src, int k, long long pstride, const bool* live,
+                   const long long* off) {
+    const long long base = (long long)k * pstride;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) reg[h] = live[h] ? src[base + off[h]] : (T)0;
+  };
+  auto put = [&](T (*dst)[RT_P], int slot, const T* reg, const bool* live) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+      if (live[h]) dst[slot][tid + h * RT_TI * RT_TJ] = reg[h];
+  };
+  const T* __restrict__ U = f.u;
+  const T* __restrict__ V = f.v;
+  const T* __restrict__ W = f.w;
+  const T* __restrict__ P = f.p;
+  auto wrapk = [&](int k) { return k < 0 ? k + nz : (k >= nz ? k - nz : k); };
+  // planes k0 - 1 and k0 of u, v, w, and k0 - 1 of p staged; plane k0 + 1
+  // of u, v, w and plane k0 of p in registers
+  {
+    const int km = wrapk(k0 - 1);
+    stage(su, U, (k0 + 2) % 3, km, pu, lu, ou);
+    stage(sv, V, (k0 + 2) % 3, km, pv, lv, ov);
+    stage(sw, W, (k0 + 2) % 3, km, pu, lu, ou);
+    stage(sp, P, (k0 + 1) % 2, km, pu, lu, ou);
+    stage(su, U, k0 % 3, k0, pu, lu, ou);
+    stage(sv, V, k0 % 3, k0, pv, lv, ov);
+    stage(sw, W, k0 % 3, k0, pu, lu, ou);
+    const int kp = wrapk(k0 + 1);
+    fetch(nu, U, kp, pu, lu, ou);
+    fetch(nv, V, kp, pv, lv, ov);
+    fetch(nw, W, kp, pu, lu, ou);
+    fetch(np, P, k0, pu, lu, ou);
+  }
+  const int ti = threadIdx.x, tj = threadIdx.y;
+  const int i = i0 + ti, j = j0 + tj;
+  const bool live = i < nx && j < ny;
+  const bool jlo = j == 0, jhi = j + 1 == ny;
+  constexpr bool nun = NU;
+  T ihc = idy, ihs = idy, ihn = idy, ihcm = idy;
+  if (nun && live) {
+    ihc = (T)g.yt.ihc[j];
+    ihs = (T)g.yt.ihf[j];
+    ihn = (T)g.yt.ihf[j + 1];
+    if (j >= 1) ihcm = (T)g.yt.ihc[j - 1];
+  }
+  const int s0 = (tj + 1) * RT_W + (ti + 1);   // this cell in a staged plane
+  for (int k = k0; k < k1; ++k) {
+    const int sm = (k + 2) % 3, sc = k % 3, sf = (k + 1) % 3;   // planes k - 1, k, k + 1
+    const int pm = (k + 1) % 2, pc0 = k % 2;                     // p planes k - 1, k
+    __syncthreads();   // the ring slots about to be refilled are no longer read
+    put(su, sf, nu, lu);
+    put(sv, sf, nv, lv);
+    put(sw, sf, nw, lu);
+    put(sp, pc0, np, lu);
+    if (k + 1 < k1) {   // the following plane, in flight during this step
+      const int kq = wrapk(k + 2);
+      fetch(nu, U, kq, pu, lu, ou);
+      fetch(nv, V, kq, pv, lv, ov);
+      fetch(nw, W, kq, pu, lu, ou);
+      fetch(np, P, k + 1, pu, lu, ou);
+    }
+    __syncthreads();
+    if (!live) continue;
+    // neighbour (di, dj) of this cell in a staged plane
+    auto at = [&](const T* pl, int di, int dj) { return pl[s0 + dj * RT_W + di]; };
+    const T* um = su[sm]; const T* uk = su[sc]; const T* uq = su[sf];
+    const T* vm = sv[sm]; const T* vk = sv[sc]; const T* vq = sv[sf];
+    const T* wm = sw[sm]; const T* wk = sw[sc]; const T* wq = sw[sf];
+    const T* pm_ = sp[pm]; const T* pk = sp[pc0];
+    const long long r0 = (long long)k * pu + (long long)j * nx;
+    const long long v0 = (long long)k * pv + (long long)j * nx;
+    const long long cell = r0 + i;
+    const unsigned fl = (flags32[cell >> 2] >> (8 * (cell & 3))) & 0xFFu;
+    const T pcv = at(pk, 0, 0);
+    // ---------------- u ----------------
+    {
+      const T uc = at(uk, 0, 0), ue = at(uk, 1, 0), uw = at(uk, -1, 0);
+      const T un = jhi ? gs * uc : at(uk, 0, 1);
+      const T us = jlo ? gs * uc : at(uk, 0, -1);
+      const T uf = at(uq, 0, 0), ub = at(um, 0, 0);
+      const T adx = ((uc + ue) * (uc + ue) - (uw + uc) * (uw + uc)) * q * idx;
+      const T vt = jhi ? (T)0 : (at(vk, -1, 1) + at(vk, 0, 1)) * (uc + un);
+      const T vb = jlo ? (T)0 : (at(vk, -1, 0) + at(vk, 0, 0)) * (us + uc);
+      const T ady = (vt - vb) * q * ihc;
+      const T wf = (at(wq, -1, 0) + at(wq, 0, 0)) * (uc + uf);
+      const T wb = (at(wk, -1, 0) + at(wk, 0, 0)) * (ub + uc);
+      const T adz = (wf - wb) * q * idz;
+      const T H = -(adx + ady + adz);
+      const T lapy = nun ? ((un - uc) * ihn - (uc - us) * ihs) * ihc : (un - (T)2 * uc + us) * idy2;
+      const T lap = (ue - (T)2 * uc + uw) * idx2 + lapy + (uf - (T)2 * uc + ub) * idz2;
+      const T G = (pcv - at(pk, -1, 0)) * idx;
+      T r = cg * H - ca * G + cv * lap + fbx;
+      if (use_hp) r += cr * f.Hp[0][cell];
+      if (write_h) f.H[0][cell] = H;
+      f.R[0][cell] = (fl & FLAG_U) ? (T)0 : tdt * r;
+    }
+    // ---------------- w ----------------
+    {
+      const T wc = at(wk, 0, 0), we = at(wk, 1, 0), ww = at(wk, -1, 0);
+      const T wn = jhi ? gs * wc : at(wk, 0, 1);
+      const T ws = jlo ? gs * wc : at(wk, 0, -1);
+      const T wf = at(wq, 0, 0), wb = at(wm, 0, 0);
+      const T ue = (at(um, 1, 0) + at(uk, 1, 0)) * (wc + we);
+      const T uw = (at(um, 0, 0) + at(uk, 0, 0)) * (ww + wc);
+      const T adx = (ue - uw) * q * idx;
+      const T vt = jhi ? (T)0 : (at(vm, 0, 1) + at(vk, 0, 1)) * (wc + wn);
+      const T vb = jlo ? (T)0 : (at(vm, 0, 0) + at(vk, 0, 0)) * (ws + wc);
+      const T ady = (vt - vb) * q * ihc;
+      const T adz = ((wc + wf) * (wc + wf) - (wb + wc) * (wb + wc)) * q * idz;
+      const T H = -(adx + ady + adz);
+      const T lapy = nun ? ((wn - wc) * ihn - (wc - ws) * ihs) * ihc : (wn - (T)2 * wc + ws) * idy2;
+      const T lap = (we - (T)2 * wc + ww) * idx2 + lapy + (wf - (T)2 * wc + wb) * idz2;
+      const T G = (pcv - at(pm_, 0, 0)) * idz;
+      T r = cg * H - ca * G + cv * lap + fbz;
+      if (use_hp) r += cr * f.Hp[2][cell];
+      if (write_h) f.H[2][cell] = H;
+      f.R[2][cell] = (fl & FLAG_W) ? (T)0 : tdt * r;
+    }
+    // ---------------- v, 1 <= j <= ny-1 ----------------
+    if (j >= 1) {
+      const T vc = at(vk, 0, 0), ve = at(vk, 1, 0), vw = at(vk, -1, 0);
+      const T vn = at(vk, 0, 1), vs = at(vk, 0, -1);
+      const T vf = at(vq, 0, 0), vbk = at(vm, 0, 0);
+      const T ue = (at(uk, 1, -1) + at(uk, 1, 0)) * (vc + ve);
+      const T uw = (at(uk, 0, -1) + at(uk, 0, 0)) * (vw + vc);
+      const T adx = (ue - uw) * q * idx;
+      const T ady = ((vc + vn) * (vc + vn) - (vs + vc) * (vs + vc)) * q * ihs;
+      const T wf = (at(wq, 0, -1) + at(wq, 0, 0)) * (vc + vf);
+      const T wb = (at(wk, 0, -1) + at(wk, 0, 0)) * (vbk + vc);
+      const T adz = (wf - wb) * q * idz;
+      const T H = -(adx + ady + adz);
+      const T lapy = nun ? ((vn - vc) * ihc - (vc - vs) * ihcm) * ihs : (vn - (T)2 * vc + vs) * idy2;
+      const T lap = (ve - (T)2 * vc + vw) * idx2 + lapy + (vf - (T)2 * vc + vbk) * idz2;
+      const T G = (pcv - at(pk, 0, -1)) * ihs;
+      T r = cg * H - ca * G + cv * lap + fby;
+      if (use_hp) r += cr * f.Hp[1][v0 + i];
+      if (write_h) f.H[1][v0 + i] = H;
+      f.R[1][v0 + i] = (fl & FLAG_V) ? (T)0 : tdt * r;
+    } else {
+      f.R[1][v0 + i] = (T)0;
+      f.R[1][(long long)k * pv + (long long)ny * nx + i] = (T)0;
+      if (write_h) {
+        f.H[1][v0 + i] = (T)0;
+        f.H[1][(long long)k * pv + (long long)ny * nx + i] = (T)0;
+      }
+    }
+  }
+}
+template <typename T, bool NU>
+struct RhsTile {
+  static constexpr int kThreads = RT_TI * RT_TJ;
+  Geo g;
+  Fields<T> f;
+  const unsigned* flags32;
+  RhsCoef<T> cf;
+  int use_hp;
+  int write_h;
+  const DevState* ds;
+  __device__ __forceinline__ void operator()(const Blk& bk) const {
+    rhs_tile<T, NU>(bk, g, f, flags32, cf, use_hp, write_h, ds);
+  }
+};
+
 template <typename T>
 void launch_rhs(const Geo& g, const Fields<T>& f, const TagBuffers& b, const Stage& sg, double dt, double re,
                 bool use_hp, bool write_h, DevState* ds, Exec& ex) {
@@ -362,11 +588,21 @@ void launch_rhs(const Geo& g, const Fields<T>& f, const TagBuffers& b, const Sta
   cf.dt = (T)dt;
   cf.fba = (T)sg.alp;
   ex.mark(ST_RHS);
+  const int hp = use_hp ? 1 : 0, wh = write_h ? 1 : 0;
+  if (ex.tune.rhs == 2) {   // tiles marching in z (measured slower than one thread per cell at 128^3)
+    const dim3 grid((g.nx + RT_TI - 1) / RT_TI, (g.ny + RT_TJ - 1) / RT_TJ, (g.nz + RT_KC - 1) / RT_KC),
+        blk(RT_TI, RT_TJ);
+    if (g.yt.ihc)
+      ex.launch(grid, blk, 0, RhsTile<T, true>{g, f, b.flags32, cf, hp, wh, ds});
+    else
+      ex.launch(grid, blk, 0, RhsTile<T, false>{g, f, b.flags32, cf, hp, wh, ds});
+    return;
+  }
   const dim3 grid((g.nx + 31) / 32, (g.ny + 3) / 4, g.nz), blk(32, 4);
   if (g.yt.ihc)   // non-uniform wall-normal spacing
-    ex.launch(grid, blk, 0, Rhs<T, true>{g, f, b.flags32, cf, use_hp ? 1 : 0, write_h ? 1 : 0, ds});
+    ex.launch(grid, blk, 0, Rhs<T, true>{g, f, b.flags32, cf, hp, wh, ds});
   else
-    ex.launch(grid, blk, 0, Rhs<T, false>{g, f, b.flags32, cf, use_hp ? 1 : 0, write_h ? 1 : 0, ds});
+    ex.launch(grid, blk, 0, Rhs<T, false>{g, f, b.flags32, cf, hp, wh, ds});
 }
 
 // ---------------------------------------------------------------------------

@@ -7,8 +7,9 @@
 //   update_pressure).
 //
 // The FFTs are hand-written self-sorting (Stockham) transforms in shared
-// memory with radix-4, -2 and -3 butterflies, so every size 2^a 3^b up to
-// 1024 is supported.  Two real rows are packed into one complex transform.
+// memory with radix-8 (FP32 path), -4, -2, -3 and -5 butterflies, so every
+// size 2^a 3^b 5^c up to 1024 is supported.  Two real rows are packed into
+// one complex transform.
 // The wall-normal Thomas solve always runs in FP64 with pivots tabulated
 // once per grid (they depend only on the wavenumber pair).
 #include <math.h>
@@ -68,12 +69,13 @@ __device__ __forceinline__ unsigned magic_div_dev(unsigned d) {
 // m = 0) and is taken as the identity.
 __device__ __forceinline__ unsigned fdiv(unsigned x, unsigned m) { return m ? __umulhi(x, m) : x; }
 
-static FftPlan make_plan(int n) {
+static FftPlan make_plan(int n, bool radix8) {
   FftPlan p;
   p.n = n;
   p.nst = 0;
   int m = n, Ns = 1;
   int rad[12], nr = 0;
+  while (radix8 && m % 8 == 0) { rad[nr++] = 8; m /= 8; }
   while (m % 4 == 0) { rad[nr++] = 4; m /= 4; }
   while (m % 2 == 0) { rad[nr++] = 2; m /= 2; }
   while (m % 3 == 0) { rad[nr++] = 3; m /= 3; }
@@ -109,6 +111,37 @@ __device__ __forceinline__ void butterfly(typename Cplx<T>::type (&v)[R]) {
     v[2] = csub(s02, s13);
     v[1] = cadd(d02, jd13);
     v[3] = csub(d02, jd13);
+  } else if constexpr (R == 8) {
+    // 4-point transforms of the even and the odd inputs, then
+    // X_k = E_k + w^k O_k and X_{k+4} = E_k - w^k O_k, w = exp(-+ 2 pi i / 8)
+    C e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
+    butterfly<T, INV, 4>(e);
+    butterfly<T, INV, 4>(o);
+    const T h = (T)0.70710678118654752440;   // 1 / sqrt(2)
+    C t1, t2, t3;   // w O_1, w^2 O_2, w^3 O_3
+    if (INV) {      // w = (1 + i) / sqrt2, w^2 = i, w^3 = (-1 + i) / sqrt2
+      t1.x = h * (o[1].x - o[1].y);
+      t1.y = h * (o[1].x + o[1].y);
+      t2.x = -o[2].y;
+      t2.y = o[2].x;
+      t3.x = -h * (o[3].x + o[3].y);
+      t3.y = h * (o[3].x - o[3].y);
+    } else {        // w = (1 - i) / sqrt2, w^2 = -i, w^3 = (-1 - i) / sqrt2
+      t1.x = h * (o[1].x + o[1].y);
+      t1.y = h * (o[1].y - o[1].x);
+      t2.x = o[2].y;
+      t2.y = -o[2].x;
+      t3.x = h * (o[3].y - o[3].x);
+      t3.y = -h * (o[3].x + o[3].y);
+    }
+    v[0] = cadd(e[0], o[0]);
+    v[4] = csub(e[0], o[0]);
+    v[1] = cadd(e[1], t1);
+    v[5] = csub(e[1], t1);
+    v[2] = cadd(e[2], t2);
+    v[6] = csub(e[2], t2);
+    v[3] = cadd(e[3], t3);
+    v[7] = csub(e[3], t3);
   } else if constexpr (R == 5) {
     // X_k = sum_r v_r w^{rk}, w = exp(-+ 2 pi i / 5): pair the inputs
     // symmetric about r = 0 (t1 = v1 + v4, t2 = v2 + v3, t3 = v1 - v4,
@@ -204,6 +237,7 @@ __device__ __forceinline__ void fft_pass(const typename Cplx<T>::type* src, type
                                          const typename Cplx<T>::type* __restrict__ tw, int es, int ls,
                                          unsigned mlines) {
   switch (S.R) {
+    case 8: fft_pass_r<T, INV, 8>(src, dst, lines, S, tw, es, ls, mlines); break;
     case 4: fft_pass_r<T, INV, 4>(src, dst, lines, S, tw, es, ls, mlines); break;
     case 2: fft_pass_r<T, INV, 2>(src, dst, lines, S, tw, es, ls, mlines); break;
     case 3: fft_pass_r<T, INV, 3>(src, dst, lines, S, tw, es, ls, mlines); break;
@@ -2309,7 +2343,9 @@ void launch_poisson(const Geo& g, const Fields<T>& f, const TagBuffers& b, const
     ex.launch(dim3(1), dim3(32), 0, QEnergyFinal{g, partial, ds, sg.s, nq});
   }
   const double scale = 1.0 / (sg.alp * dt * (double)g.nx * (double)g.nz);
-  const FftPlan px = make_plan(g.nx), pz = make_plan(g.nz);
+  // radix-8 passes in the FP32 path (the FP64 path keeps radix 4 and 2: eight
+  // FP64 complex values per thread would crowd the capped registers)
+  const FftPlan px = make_plan(g.nx, sizeof(T) == 4), pz = make_plan(g.nz, sizeof(T) == 4);
   // launch shapes from the batch shape (tiles sized for its largest extents)
   int cols = 16;
   while (cols > 1 && cols * sh.nz > 2048) cols >>= 1;
@@ -2407,18 +2443,19 @@ void launch_poisson(const Geo& g, const Fields<T>& f, const TagBuffers& b, const
   }
   const int wbuf = std::max(lcp * sh.nx, czp * sh.nz);
   const size_t smp = (size_t)plane_b + 2ull * wbuf * sizeof(C);
-  // (opt-in: on a 128^3 plate one block per plane is latency-bound and
-  // slower than the separate x and z kernels, which stay the default)
-  const bool plane = tu.fft_plane == 2 && lcp >= 1 && (long long)czp * sh.nz <= wmax && smp <= 200 * 1024;
+  // the built-in choice for one simulation: one block per plane where the
+  // plane fits, else a cluster of blocks per plane (below), else the
+  // separate kernels; a batch keeps the separate kernels unless asked
+  const bool plane_fits = lcp >= 1 && (long long)czp * sh.nz <= wmax && smp <= 200 * 1024;
+  const bool plane = (tu.fft_plane == 2 || (tu.fft_plane == 0 && !ex.rec)) && plane_fits;
   // the per-plane transforms split over a cluster of CLN blocks (one
-  // simulation, nz a multiple of 2 CLN; the built-in choice where it fits):
-  // each block's rows and work buffers within 100 KB of shared memory, so at
-  // least two blocks share an SM
+  // simulation, nz a multiple of 2 CLN): each block's rows and work buffers
+  // within 100 KB of shared memory, so at least two blocks share an SM
   constexpr int CLN = 4;
   bool cluster = false;
   int wbc = 0, czc = 0;
   size_t smc = 0;
-  if (!ex.rec && (tu.fft_plane == 3 || tu.fft_plane == 0) && sh.nz % (2 * CLN) == 0 && sh.nkx >= CLN) {
+  if (!ex.rec && !plane && (tu.fft_plane == 3 || tu.fft_plane == 0) && sh.nz % (2 * CLN) == 0 && sh.nkx >= CLN) {
     const int nzc = sh.nz / CLN, cw = (sh.nkx + CLN - 1) / CLN;
     const long long sb = (long long)nzc * sh.nkx * (long long)sizeof(C);
     const long long wm = (100ll * 1024 - sb) / (2 * (long long)sizeof(C));

@@ -917,7 +917,7 @@ struct Knob {
 };
 
 static std::vector<Knob> tune_knobs() {
-  return {{&Tune::fft_plane, {3, 2, 1}}, {&Tune::sweep_zy, {2, 1}}, {&Tune::sweep_y, {1, 2, 3, 4}}, {&Tune::tri_y, {1, 4, 2, 3}},
+  return {{&Tune::fft_plane, {3, 2, 1}}, {&Tune::sweep_zy, {2, 1}}, {&Tune::sweep_y, {1, 2, 3, 4}}, {&Tune::tri_y, {1, 4, 2, 3}}, {&Tune::rhs, {1, 2}},
           {&Tune::sweep_w, {64, 32, 16}},
           {&Tune::fft_lpb, {0, 8, 4, 2}},
           {&Tune::fft_cols, {16, 8, 4}}};
@@ -980,6 +980,7 @@ static void tune_out(const Tune& t, double ms, ibm_tune* out) {
   out->sweep_zy = t.sweep_zy;
   out->fft_plane = t.fft_plane;
   out->sweep_y = t.sweep_y;
+  out->rhs = t.rhs;
   out->ms_per_step = ms;
 }
 
@@ -989,8 +990,9 @@ static void tune_log(const Tune& t, double ms) {
   static const bool on = getenv("IBM_AUTOTUNE_LOG") != nullptr;
   if (on)
     fprintf(stderr,
-            "ibm autotune: tri_y %d sweep_w %d fft_lpb %d fft_cols %d sweep_zy %d fft_plane %d sweep_y %d -> %.4f ms/step\n",
-            t.tri_y, t.sweep_w, t.fft_lpb, t.fft_cols, t.sweep_zy, t.fft_plane, t.sweep_y, ms);
+            "ibm autotune: tri_y %d sweep_w %d fft_lpb %d fft_cols %d sweep_zy %d fft_plane %d sweep_y %d rhs %d"
+            " -> %.4f ms/step\n",
+            t.tri_y, t.sweep_w, t.fft_lpb, t.fft_cols, t.sweep_zy, t.fft_plane, t.sweep_y, t.rhs, ms);
 }
 
 template <class Trial>
@@ -1760,12 +1762,13 @@ static bool tune_valid(const ibm_tune* t) {
   if (t->sweep_zy < 0 || t->sweep_zy > 2) return false;
   if (t->fft_plane < 0 || t->fft_plane > 3) return false;
   if (t->sweep_y < 0 || t->sweep_y > 4) return false;
+  if (t->rhs < 0 || t->rhs > 2) return false;
   return true;
 }
 
 ibm_status ibm_set_tune(ibm_handle h, const ibm_tune* t) {
   if (!h || !tune_valid(t)) return IBM_ERR_ARG;
-  h->tune = Tune{t->tri_y, t->sweep_w, t->fft_lpb, t->fft_cols, t->sweep_zy, t->fft_plane, t->sweep_y};
+  h->tune = Tune{t->tri_y, t->sweep_w, t->fft_lpb, t->fft_cols, t->sweep_zy, t->fft_plane, t->sweep_y, t->rhs};
   invalidate(h);
   return IBM_OK;
 }
@@ -1927,7 +1930,7 @@ ibm_status ibm_batch_profile_stages(ibm_batch_handle b, int nsteps, double* ms, 
 
 ibm_status ibm_batch_set_tune(ibm_batch_handle b, const ibm_tune* t) {
   if (!b || !tune_valid(t)) return IBM_ERR_ARG;
-  b->tune = Tune{t->tri_y, t->sweep_w, t->fft_lpb, t->fft_cols, t->sweep_zy, t->fft_plane, t->sweep_y};
+  b->tune = Tune{t->tri_y, t->sweep_w, t->fft_lpb, t->fft_cols, t->sweep_zy, t->fft_plane, t->sweep_y, t->rhs};
   b->built = false;
   return IBM_OK;
 }

@@ -78,6 +78,11 @@ def test_traffic_lookup_follows_the_kernel_source(tmp_path):
     assert bench.stage_kernel("tri_y", {"tri_y": 3}, "fp64") == "TriYSmem<double>"
     assert bench.stage_kernel("tri_y", {"tri_y": 0}, "mixed", 128) == "TriYWarp<float, 16, 7>"
     assert bench.stage_kernel("tri_y", {"tri_y": 1}, "mixed", 128) == "TriYWarp<float, 16, 1>"
-    assert bench.stage_kernel("fft_x_fwd", {}, "mixed") == "FftPlaneFwdCl<float, 4>"
-    assert bench.stage_kernel("fft_x_fwd", {"fft_plane": 0}, "mixed", 37, 60) == "FftXFwd<float>"
+    assert bench.stage_kernel("fft_x_fwd", {}, "mixed") == "FftPlaneFwd<float>"
+    assert bench.stage_kernel("fft_x_fwd", {"fft_plane": 3}, "mixed") == "FftPlaneFwdCl<float, 4>"
     assert bench.stage_kernel("fft_x_fwd", {"fft_plane": 2}, "fp64") == "FftPlaneFwd<double>"
+    assert bench.stage_kernel("fft_x_fwd", {"fft_plane": 1}, "mixed") == "FftXFwd<float>"
+    # the 256 x 192 x 256 channel: its plane does not fit one block, a cluster of 4 takes it
+    assert bench.fft_form({}, 256, 256, 4) == "cluster"
+    assert bench.fft_form({}, 256, 256, 8) == "split"
+    assert bench.fft_form({}, 48, 60, 4) == "plane"
