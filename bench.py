@@ -138,16 +138,19 @@ def algorithmic_bytes_per_cell(stage: str, word: int, pairs: bool = False) -> fl
         "sweep_z": (3, 3),
         "sweep_y": (6, 3),          # du x3 and u^s x3 -> uhat x3
         "fft_x_fwd": (3, 1),        # uhat x3 -> half spectrum (2 words x (nx/2+1)/nx)
+        "correction": (3, 1),       # the correction's forward transform: projected state x3 -> half spectrum
         "fft_z_fwd": (1, 1),
         "tri_y": (1, 1),
         "fft_z_inv": (1, 1),
         "fft_x_inv": (1, 1),
+        "correction_inv": (1, 1),
         "project": (5, 4),          # uhat x3, phi, p -> u x3, p
     }
     if pairs:
         reads_writes.update({
             "sweep_y": (9, 6),      # du x3 and u^s x3 as (hi, lo) -> uhat x3 as (hi, lo)
             "project": (9, 7),      # uhat x3 (hi, lo), p, phi, phi2 -> u x3 (hi, lo), p
+            "correction": (7, 1),   # uhat x3 (hi, lo), phi -> half spectrum of the residual divergence
         })
     r, w = reads_writes.get(stage, (0, 0))
     return (r + w) * word
@@ -237,6 +240,14 @@ def ncu_traffic(stage: str, kernel: str | None, summary: str = TRAFFIC_SUMMARY, 
         except ValueError:
             return None
     return None
+
+
+def group_traffic(stages, kernel: str | None) -> float | None:
+    """DRAM bytes per launch of a kernel group (stages that run the same
+    kernel, launched alike often): the mean of its stages' recorded figures,
+    or None when any of them is missing or stale."""
+    tr = [ncu_traffic(s2, kernel) for s2 in stages]
+    return sum(tr) / len(tr) if tr and all(t is not None for t in tr) else None
 
 
 TAG_FLOPS_PER_PAIR = 100.0   # closest point ~73, N and |N|^2 8, neighbour tests up to ~36 (FP64, counted from source)
@@ -447,7 +458,11 @@ def gpu_arm(args):
             work = fp64_flops_per_cell(name) * cells
             g = dict(bound="alu", achieved=work / (avg_ms / 1e3) / 1e12, peak=fp64_peak, unit="TFLOP/s")
         elif algorithmic_bytes_per_cell(name, 4) > 0:
-            work = algorithmic_bytes_per_cell(name, 4, pairs=args.precision == "mixed") * cells
+            # bytes of an average launch of the group (the correction's forward
+            # transform reads more than the first solve's)
+            nl = [prof[s2][1] for s2 in stages if s2 in prof]
+            work = sum(algorithmic_bytes_per_cell(s2, 4, pairs=args.precision == "mixed") * prof[s2][1]
+                       for s2 in stages if s2 in prof) / sum(nl) * cells
             g = dict(bound="hbm", achieved=work / (avg_ms / 1e3) / 1e9, peak=hbm, unit="GB/s")
         else:
             continue
@@ -462,7 +477,7 @@ def gpu_arm(args):
     tg = groups[top]
     kname = stage_kernel(top, head["tune"], args.precision, wl.ny, wl.nz)
     roof = {"bound": tg["bound"], "achieved": tg["achieved"], "peak": tg["peak"], "unit": tg["unit"],
-            "frac": tg["frac"], "traffic": ncu_traffic(top, kname), "kernel": top, "kernel_name": kname,
+            "frac": tg["frac"], "traffic": group_traffic(tg["stages"], kname), "kernel": top, "kernel_name": kname,
             "ms_per_step": tg["ms_per_step"], "launches_per_step": tg["launches_per_step"],
             "peak_source": ("FP64 FMA-chain probe ibm_measure_alu_peaks, this run (of measured)"
                             if tg["bound"] == "alu" else "MEASURED_PEAKS.json hbm_gbs (of measured)")}

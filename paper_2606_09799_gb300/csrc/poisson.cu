@@ -498,6 +498,14 @@ struct ProjCoef {
   T cx, cy, cz;          // alpha dt / d
   T bx, by, bz;          // alpha dt / (2 Re d^2)
   T adt, bb;             // alpha dt and alpha dt / (2 Re), for a non-uniform wall-normal spacing
+  // the right-hand side's constants in the bulk type, converted once on the
+  // host: a conversion from FP64 inside the per-cell arithmetic would run on
+  // the narrow FP64 pipe (or be repeated there when the compiler
+  // rematerialises it)
+  T sc;                  // 1 / (alpha dt nx nz)
+  T idx, idy, idz;       // 1 / d
+  float scf;             // sc in FP32
+  float ih[3][2];        // 1 / d as FP32 (hi, lo) pairs
 };
 
 // One face of the projected state held as a (hi, lo) pair: the projection's
@@ -559,7 +567,7 @@ struct RowY {
 };
 template <typename T>
 __device__ __forceinline__ RowY<T> row_y(const Geo& g, const Fields<T>& f, const ProjCoef<T>& cf, int j) {
-  RowY<T> r{cf.cy, cf.cy, (T)g.idy, (float)f.idh[1][0], (float)f.idh[1][1]};
+  RowY<T> r{cf.cy, cf.cy, cf.idy, cf.ih[1][0], cf.ih[1][1]};
   if (g.yt.ihc) {
     r.cy0 = mul_rn(cf.adt, (T)g.yt.ihf[j]);
     r.cy1 = mul_rn(cf.adt, (T)g.yt.ihf[j + 1]);
@@ -578,7 +586,7 @@ __device__ __forceinline__ T poisson_rhs(const Geo& g, const Fields<T>& f, const
                                          int k, unsigned& rmax) {
   const int n = g.nx, ny = g.ny;
   const long long pu = (long long)ny * n, pv = (long long)(ny + 1) * n;
-  const T sc = (T)scale, idx = (T)g.idx, idy = (T)g.idy, idz = (T)g.idz;
+  const T sc = cf.sc, idx = cf.idx, idz = cf.idz;
   const int ip = i + 1 == n ? 0 : i + 1;
   const int kp = k + 1 == g.nz ? 0 : k + 1;
   const long long r0 = (long long)k * pu + (long long)j * n;
@@ -612,9 +620,9 @@ __device__ __forceinline__ T poisson_rhs(const Geo& g, const Fields<T>& f, const
         float wh1 = (float)f.w[wk], wl1 = (float)f.lo[2][wk];
         proj_face(wh0, wl0, (float)mul_rn(cf.cz, (T)p0 - ph[rkm + i]));
         proj_face(wh1, wl1, (float)mul_rn(cf.cz, ph[rkp + i] - (T)p0));
-        pair_diff_v(uh1, ul1, uh0, ul0, (float)f.idh[0][0], (float)f.idh[0][1], bx, sx);
+        pair_diff_v(uh1, ul1, uh0, ul0, cf.ih[0][0], cf.ih[0][1], bx, sx);
         pair_diff_v(vh1, vl1, vh0, vl0, ry.ihh, ry.ihl, by, sy);
-        pair_diff_v(wh1, wl1, wh0, wl0, (float)f.idh[2][0], (float)f.idh[2][1], bz, sz);
+        pair_diff_v(wh1, wl1, wh0, wl0, cf.ih[2][0], cf.ih[2][1], bz, sz);
       }
       two_sum(bx, by, a1, e1);
       two_sum(a1, bz, a2, e2);
@@ -625,7 +633,7 @@ __device__ __forceinline__ T poisson_rhs(const Geo& g, const Fields<T>& f, const
       two_sum(a2, -qh, a3, e3);
       const float d = a3 + (((e1 + e2) + e3) + ((sx + sy) + sz) - ql);   // D u' - q
       rmax = max(rmax, __float_as_uint(d) & 0x7FFFFFFFu);                 // |d| (NaN above every number)
-      r = (T)(d * (float)scale);
+      r = (T)(d * cf.scf);
     }
   } else if (!(use_q && (fl & FLAG_B))) {
     const long long v0 = (long long)k * pv + (long long)j * n + i;
@@ -2511,6 +2519,13 @@ void launch_poisson(const Geo& g, const Fields<T>& f, const TagBuffers& b, const
   cf.cx = (T)(adt * g.idx); cf.cy = (T)(adt * g.idy); cf.cz = (T)(adt * g.idz);
   cf.bx = (T)(bb * g.idx * g.idx); cf.by = (T)(bb * g.idy * g.idy); cf.bz = (T)(bb * g.idz * g.idz);
   cf.adt = (T)adt; cf.bb = (T)bb;
+  cf.sc = (T)scale;
+  cf.idx = (T)g.idx; cf.idy = (T)g.idy; cf.idz = (T)g.idz;
+  cf.scf = (float)scale;
+  for (int d = 0; d < 3; ++d) {
+    cf.ih[d][0] = (float)f.idh[d][0];
+    cf.ih[d][1] = (float)f.idh[d][1];
+  }
   auto forward = [&](int mode) {
     if (cluster)
       ex.launch_cluster(dim3(g.ny * CLN), dim3(256), smc,
