@@ -977,8 +977,9 @@ def main():
                     help="also record the no-slip error series of the heaving/pitching plate (opt-in)")
     ap.add_argument("--tune", default="", help="fixed launch shapes instead of autotuning, e.g. tri_y=3,sweep_zy=2")
     ap.add_argument("--batch-steps", type=int, default=20)
-    ap.add_argument("--div-budget", type=float, default=5e-8,
-                    help="mixed path: correction-solve budget on max |D u - q| in U_ref/dx (0: always correct)")
+    ap.add_argument("--div-budget", type=float, default=1e-7,
+                    help="mixed path: correction-solve budget on max |D u - q| in U_ref/dx, by default the "
+                         "1e-7 bound the mixed path must meet (0: always correct)")
     ap.add_argument("--fp64-peak-tflops", type=float, default=0.0,
                     help="FP64 roof in TFLOP/s; 0 (default) measures it on the device (ibm_measure_alu_peaks)")
     args = ap.parse_args()
