@@ -170,15 +170,15 @@ def fft_form(tune: dict | None, nx: int = 128, nz: int = 128, word: int = 4) -> 
     nkx, c = nx // 2 + 1, 2 * word          # complex word
     plane_b = nz * nkx * c
     wmax = (200 * 1024 - plane_b) // (2 * c)
-    lcp, cmax = min(nz // 2, wmax // nx), max(1, min(nkx, wmax // nz))
+    lcp, cmax = min(nz // 2, wmax // (nx + 1)), max(1, min(nkx, wmax // nz))   # x lines padded to nx + 1
     czp = -(-nkx // -(-nkx // cmax))
-    plane_fits = lcp >= 1 and czp * nz <= wmax and plane_b + 2 * max(lcp * nx, czp * nz) * c <= 200 * 1024
+    plane_fits = lcp >= 1 and czp * nz <= wmax and plane_b + 2 * max(lcp * (nx + 1), czp * nz) * c <= 200 * 1024
     if v in (0, 2) and plane_fits:
         return "plane"
     if v in (0, 3) and nz % 8 == 0 and nkx >= 4:
         nzc, cw = nz // 4, -(-nkx // 4)
         wm = (100 * 1024 - nzc * nkx * c) // (2 * c)
-        if min(nzc // 2, wm // nx) >= 1 and min(cw, wm // nz) >= 1:
+        if min(nzc // 2, wm // (nx + 1)) >= 1 and min(cw, wm // nz) >= 1:
             return "cluster"
     return "split"
 

@@ -188,13 +188,15 @@ __device__ __forceinline__ void butterfly(typename Cplx<T>::type (&v)[R]) {
 // e of line l sits at l * ls + e * es (src and dst alike).
 // tw[m] = exp(-2 pi i m/n).  Threads take butterflies (line, j) with the
 // line index fastest when es > 1 (column tiles: neighbouring lines are
-// neighbouring words) and j fastest otherwise.  R is a template parameter
-// so the butterfly's values stay in registers.
+// neighbouring words) or when lfast is set (rows padded to an odd number of
+// words' pairs, ls = n + 1: neighbouring lines then fall in neighbouring
+// banks, whatever stride the pass writes with), and j fastest otherwise.
+// R is a template parameter so the butterfly's values stay in registers.
 template <typename T, bool INV, int R>
 __device__ __forceinline__ void fft_pass_r(const typename Cplx<T>::type* src, typename Cplx<T>::type* dst,
                                            int lines, const FftStage& S,
                                            const typename Cplx<T>::type* __restrict__ tw, int es, int ls,
-                                           unsigned mlines) {
+                                           unsigned mlines, bool lfast) {
   using C = typename Cplx<T>::type;
   const int Ns = S.Ns, nb = S.nb, scale = S.scale;
   const unsigned mNs = S.mNs, mnb = S.mnb;
@@ -202,7 +204,7 @@ __device__ __forceinline__ void fft_pass_r(const typename Cplx<T>::type* src, ty
   const int total = lines * nb;
   for (int t = tid; t < total; t += nth) {
     int line, j;
-    if (es > 1) {
+    if (es > 1 || lfast) {
       j = (int)fdiv((unsigned)t, mlines);
       line = t - j * lines;
     } else {
@@ -235,13 +237,13 @@ template <typename T, bool INV>
 __device__ __forceinline__ void fft_pass(const typename Cplx<T>::type* src, typename Cplx<T>::type* dst,
                                          int lines, const FftStage& S,
                                          const typename Cplx<T>::type* __restrict__ tw, int es, int ls,
-                                         unsigned mlines) {
+                                         unsigned mlines, bool lfast) {
   switch (S.R) {
-    case 8: fft_pass_r<T, INV, 8>(src, dst, lines, S, tw, es, ls, mlines); break;
-    case 4: fft_pass_r<T, INV, 4>(src, dst, lines, S, tw, es, ls, mlines); break;
-    case 2: fft_pass_r<T, INV, 2>(src, dst, lines, S, tw, es, ls, mlines); break;
-    case 3: fft_pass_r<T, INV, 3>(src, dst, lines, S, tw, es, ls, mlines); break;
-    default: fft_pass_r<T, INV, 5>(src, dst, lines, S, tw, es, ls, mlines); break;
+    case 8: fft_pass_r<T, INV, 8>(src, dst, lines, S, tw, es, ls, mlines, lfast); break;
+    case 4: fft_pass_r<T, INV, 4>(src, dst, lines, S, tw, es, ls, mlines, lfast); break;
+    case 2: fft_pass_r<T, INV, 2>(src, dst, lines, S, tw, es, ls, mlines, lfast); break;
+    case 3: fft_pass_r<T, INV, 3>(src, dst, lines, S, tw, es, ls, mlines, lfast); break;
+    default: fft_pass_r<T, INV, 5>(src, dst, lines, S, tw, es, ls, mlines, lfast); break;
   }
 }
 
@@ -249,13 +251,13 @@ __device__ __forceinline__ void fft_pass(const typename Cplx<T>::type* src, type
 template <typename T, bool INV>
 __device__ int fft_lines(typename Cplx<T>::type* a, typename Cplx<T>::type* b, int lines, const FftPlan& p,
                          const typename Cplx<T>::type* __restrict__ tw, int es = 1, int ls = -1,
-                         unsigned mlines = 0) {
+                         unsigned mlines = 0, bool lfast = false) {
   if (ls < 0) ls = p.n;
   int cur = 0;
   for (int s = 0; s < p.nst; ++s) {
     __syncthreads();
-    if (cur == 0) fft_pass<T, INV>(a, b, lines, p.st[s], tw, es, ls, mlines);
-    else fft_pass<T, INV>(b, a, lines, p.st[s], tw, es, ls, mlines);
+    if (cur == 0) fft_pass<T, INV>(a, b, lines, p.st[s], tw, es, ls, mlines, lfast);
+    else fft_pass<T, INV>(b, a, lines, p.st[s], tw, es, ls, mlines, lfast);
     cur ^= 1;
   }
   __syncthreads();
@@ -808,7 +810,8 @@ __device__ __forceinline__ void fft_plane_fwd(const Blk& bk, const Geo& g, const
   C* bufa = S + (size_t)nz * nkx;
   C* bufb = bufa + wbuf;
   const int j = bk.x;
-  const int lc = max(1, wbuf / nx);
+  const int xs = nx + 1;   // padded line stride of the x transforms (see fft_pass_r)
+  const int lc = max(1, wbuf / xs);
   const T qf = use_q ? (T)ds->qf[s] : (T)0;
   const T qa = use_q == 2 ? (T)ds->qa[s] : (T)0, qb = use_q == 2 ? (T)ds->qb[s] : (T)0;
   const int nlines = nz / 2;
@@ -826,14 +829,15 @@ __device__ __forceinline__ void fft_plane_fwd(const Blk& bk, const Geo& g, const
       C z;
       z.x = poisson_rhs<T>(g, f, flags32, ds, s, use_q, scale, mode, cf, ry, qf, qa, qb, i, j, k0, rmax);
       z.y = poisson_rhs<T>(g, f, flags32, ds, s, use_q, scale, mode, cf, ry, qf, qa, qb, i, j, k0 + 1, rmax);
-      bufa[t] = z;
+      bufa[l * xs + i] = z;
     }
-    const int res = fft_lines<T, false>(bufa, bufb, nl, px, reinterpret_cast<const C*>(twx));
+    const int res = fft_lines<T, false>(bufa, bufb, nl, px, reinterpret_cast<const C*>(twx), 1, xs,
+                                        magic_div_dev((unsigned)nl), true);
     const C* out = res == 0 ? bufa : bufb;
     for (int t = threadIdx.x; t < nl * nkx; t += blockDim.x) {
       const int l = t / nkx, kx = t - l * nkx;
-      const C Z = out[l * nx + kx];
-      const C Zc = cconj(out[l * nx + (kx == 0 ? 0 : nx - kx)]);
+      const C Z = out[l * xs + kx];
+      const C Zc = cconj(out[l * xs + (kx == 0 ? 0 : nx - kx)]);
       C Xa, Xb;
       Xa.x = (T)0.5 * (Z.x + Zc.x);
       Xa.y = (T)0.5 * (Z.y + Zc.y);
@@ -922,7 +926,8 @@ __device__ __forceinline__ void fft_plane_inv(const Blk& bk, const Geo& g, const
     }
   }
   // x inverse: two half-spectra (rows k, k + 1) -> one complex line -> two real rows
-  const int lc = max(1, wbuf / nx);
+  const int xs = nx + 1;   // padded line stride of the x transforms (see fft_pass_r)
+  const int lc = max(1, wbuf / xs);
   const int nlines = nz / 2;
   for (int l0 = 0; l0 < nlines; l0 += lc) {
     const int nl = min(lc, nlines - l0);
@@ -938,16 +943,17 @@ __device__ __forceinline__ void fft_plane_inv(const Blk& bk, const Geo& g, const
       C z;  // A + i B
       z.x = A.x - B.y;
       z.y = A.y + B.x;
-      bufa[t] = z;
+      bufa[l * xs + kx] = z;
     }
-    const int res = fft_lines<T, true>(bufa, bufb, nl, px, reinterpret_cast<const C*>(twx));
+    const int res = fft_lines<T, true>(bufa, bufb, nl, px, reinterpret_cast<const C*>(twx), 1, xs,
+                                       magic_div_dev((unsigned)nl), true);
     const C* out = res == 0 ? bufa : bufb;
 #pragma unroll 4
     for (int t = threadIdx.x; t < nl * nx; t += blockDim.x) {
       const int l = t / nx, i = t - l * nx;
       const int k0 = 2 * (l0 + l);
-      out_phi[((long long)k0 * ny + j) * nx + i] = out[t].x;
-      out_phi[((long long)(k0 + 1) * ny + j) * nx + i] = out[t].y;
+      out_phi[((long long)k0 * ny + j) * nx + i] = out[l * xs + i].x;
+      out_phi[((long long)(k0 + 1) * ny + j) * nx + i] = out[l * xs + i].y;
     }
   }
 }
@@ -996,7 +1002,8 @@ __device__ __forceinline__ void fft_plane_fwd_cl(const Blk& bk, const Geo& g, co
   C* S = reinterpret_cast<C*>(smem_raw);   // [k - r nzc][kx]
   C* bufa = S + (size_t)nzc * nkx;
   C* bufb = bufa + wbuf;
-  const int lc = max(1, wbuf / nx);
+  const int xs = nx + 1;   // padded line stride of the x transforms (see fft_pass_r)
+  const int lc = max(1, wbuf / xs);
   const T qf = use_q ? (T)ds->qf[s] : (T)0;
   const T qa = use_q == 2 ? (T)ds->qa[s] : (T)0, qb = use_q == 2 ? (T)ds->qb[s] : (T)0;
   const int nlines = nzc / 2;
@@ -1014,14 +1021,15 @@ __device__ __forceinline__ void fft_plane_fwd_cl(const Blk& bk, const Geo& g, co
       C z;
       z.x = poisson_rhs<T>(g, f, flags32, ds, s, use_q, scale, mode, cf, ry, qf, qa, qb, i, j, k0, rmax);
       z.y = poisson_rhs<T>(g, f, flags32, ds, s, use_q, scale, mode, cf, ry, qf, qa, qb, i, j, k0 + 1, rmax);
-      bufa[t] = z;
+      bufa[l * xs + i] = z;
     }
-    const int res = fft_lines<T, false>(bufa, bufb, nl, px, reinterpret_cast<const C*>(twx));
+    const int res = fft_lines<T, false>(bufa, bufb, nl, px, reinterpret_cast<const C*>(twx), 1, xs,
+                                        magic_div_dev((unsigned)nl), true);
     const C* out = res == 0 ? bufa : bufb;
     for (int t = threadIdx.x; t < nl * nkx; t += blockDim.x) {
       const int l = t / nkx, kx = t - l * nkx;
-      const C Z = out[l * nx + kx];
-      const C Zc = cconj(out[l * nx + (kx == 0 ? 0 : nx - kx)]);
+      const C Z = out[l * xs + kx];
+      const C Zc = cconj(out[l * xs + (kx == 0 ? 0 : nx - kx)]);
       C Xa, Xb;
       Xa.x = (T)0.5 * (Z.x + Zc.x);
       Xa.y = (T)0.5 * (Z.y + Zc.y);
@@ -1132,7 +1140,8 @@ __device__ __forceinline__ void fft_plane_inv_cl(const Blk& bk, const Geo& g, co
   }
   cl.sync();   // every block's rows are complete (written by the whole cluster)
   // x inverse: two half-spectra (rows k, k + 1) -> one complex line -> two real rows
-  const int lc = max(1, wbuf / nx);
+  const int xs = nx + 1;   // padded line stride of the x transforms (see fft_pass_r)
+  const int lc = max(1, wbuf / xs);
   const int nlines = nzc / 2;
   for (int l0 = 0; l0 < nlines; l0 += lc) {
     const int nl = min(lc, nlines - l0);
@@ -1148,16 +1157,17 @@ __device__ __forceinline__ void fft_plane_inv_cl(const Blk& bk, const Geo& g, co
       C z;  // A + i B
       z.x = A.x - B.y;
       z.y = A.y + B.x;
-      bufa[t] = z;
+      bufa[l * xs + kx] = z;
     }
-    const int res = fft_lines<T, true>(bufa, bufb, nl, px, reinterpret_cast<const C*>(twx));
+    const int res = fft_lines<T, true>(bufa, bufb, nl, px, reinterpret_cast<const C*>(twx), 1, xs,
+                                       magic_div_dev((unsigned)nl), true);
     const C* out = res == 0 ? bufa : bufb;
 #pragma unroll 4
     for (int t = threadIdx.x; t < nl * nx; t += blockDim.x) {
       const int l = t / nx, i = t - l * nx;
       const int k0 = r * nzc + 2 * (l0 + l);
-      out_phi[((long long)k0 * ny + j) * nx + i] = out[t].x;
-      out_phi[((long long)(k0 + 1) * ny + j) * nx + i] = out[t].y;
+      out_phi[((long long)k0 * ny + j) * nx + i] = out[l * xs + i].x;
+      out_phi[((long long)(k0 + 1) * ny + j) * nx + i] = out[l * xs + i].y;
     }
   }
 }
@@ -2440,7 +2450,7 @@ void launch_poisson(const Geo& g, const Fields<T>& f, const TagBuffers& b, const
   // a small plane goes through each direction in one or two chunks
   const long long plane_b = (long long)sh.nz * sh.nkx * (long long)sizeof(C);
   const long long wmax = (200ll * 1024 - plane_b) / (2 * (long long)sizeof(C));
-  int lcp = (int)std::min<long long>(sh.nz / 2, wmax / sh.nx);
+  int lcp = (int)std::min<long long>(sh.nz / 2, wmax / (sh.nx + 1));   // x lines padded to nx + 1
   // z columns per chunk: the fewest chunks that fit the work buffers, of
   // equal width (65 columns of a 128^3 grid go in one chunk, not 64 + 1)
   int czp = 1;
@@ -2449,7 +2459,7 @@ void launch_poisson(const Geo& g, const Fields<T>& f, const TagBuffers& b, const
     const long long nch = (sh.nkx + cmax - 1) / cmax;
     czp = (int)((sh.nkx + nch - 1) / nch);
   }
-  const int wbuf = std::max(lcp * sh.nx, czp * sh.nz);
+  const int wbuf = std::max(lcp * (sh.nx + 1), czp * sh.nz);
   const size_t smp = (size_t)plane_b + 2ull * wbuf * sizeof(C);
   // the built-in choice for one simulation: one block per plane where the
   // plane fits, else a cluster of blocks per plane (below), else the
@@ -2467,12 +2477,12 @@ void launch_poisson(const Geo& g, const Fields<T>& f, const TagBuffers& b, const
     const int nzc = sh.nz / CLN, cw = (sh.nkx + CLN - 1) / CLN;
     const long long sb = (long long)nzc * sh.nkx * (long long)sizeof(C);
     const long long wm = (100ll * 1024 - sb) / (2 * (long long)sizeof(C));
-    const long long lcc = std::min<long long>(nzc / 2, wm / sh.nx);
+    const long long lcc = std::min<long long>(nzc / 2, wm / (sh.nx + 1));
     const long long cmax = std::min<long long>(cw, wm / sh.nz);
     if (lcc >= 1 && cmax >= 1) {
       const long long nch = (cw + cmax - 1) / cmax;
       czc = (int)((cw + nch - 1) / nch);
-      wbc = (int)std::max<long long>(lcc * sh.nx, (long long)czc * sh.nz);
+      wbc = (int)std::max<long long>(lcc * (sh.nx + 1), (long long)czc * sh.nz);
       smc = (size_t)sb + 2ull * wbc * sizeof(C);
       cluster = true;
     }
