@@ -143,7 +143,6 @@ def algorithmic_bytes_per_cell(stage: str, word: int, pairs: bool = False) -> fl
         "tri_y": (1, 1),
         "fft_z_inv": (1, 1),
         "fft_x_inv": (1, 1),
-        "correction_inv": (1, 1),
         "project": (5, 4),          # uhat x3, phi, p -> u x3, p
     }
     if pairs:
@@ -430,11 +429,15 @@ def gpu_arm(args):
     groups = {}
     tune_h = head["tune"] or {}
     plane = fft_form(tune_h, wl.nx, wl.nz, 4 if args.precision == "mixed" else 8) != "split"
-    merged = {"tri_y": ("tri_y", "correction_tri")}
+    # the correction solve's Thomas and inverse transforms are gated: a launch
+    # whose sub-stage met the divergence budget returns at entry, so their
+    # per-launch rates would count launches that did no work; they are left
+    # out here (their time is in stages_ms_per_step), and the Thomas and the
+    # inverse transforms are rated on the first solve's launches alone
+    merged = {}
     if plane:
         merged["fft_x_fwd"] = ("fft_x_fwd", "correction")
-        merged["fft_x_inv"] = ("fft_x_inv", "correction_inv")
-    skip = {s2 for k, v in merged.items() for s2 in v if s2 != k}
+    skip = {s2 for k, v in merged.items() for s2 in v if s2 != k} | {"correction_tri", "correction_inv"}
     for name, (tot_ms, ngroups) in prof.items():
         if name in ("other",) or name in skip or ngroups == 0 or tot_ms <= 0:
             continue
