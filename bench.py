@@ -746,7 +746,8 @@ def large_leg(args, dev, stream, flush):
 def cpu_baseline_extra():
     """The oracle's other timings: one thread on the 64^3 oscillating sphere
     (all 10 steps), and all host cores on the 256x192x256 channel with 16
-    bodies (2 whole steps, reported per step as cell updates/s)."""
+    bodies (2 whole steps) and on the 512x384x512 leaflet tube (1 whole
+    step), reported as cell updates/s."""
     from oracle import oracle as orc
     from oracle.oracle import OracleSim
     from paper_2606_09799_gb300 import inputs
@@ -782,6 +783,24 @@ def cpu_baseline_extra():
     out["channel256"] = {"value": cells * 2 / dt / 1e9, "unit": UNIT, "cores": ncores, "kind": "oracle",
                          "sample": "2 whole time steps of the 256x192x256 channel with 16 moving bodies (FP64)",
                          "seconds_per_step": dt / 2}
+    del sim
+    # the 512x384x512 tube: one whole step (about 18 GB of host memory and
+    # half a minute on 16 cores)
+    wl = inputs.workload("leaflet512")
+    sim = OracleSim(wl.nx, wl.ny, wl.nz, wl.lx, wl.ly, wl.lz, re=wl.re, dt=wl.dt)
+    if wl.initial is not None:
+        sim.set_fields(*wl.initial())
+    sim.set_body_force(*wl.body_force_at(0.0))
+    t0 = time.perf_counter()
+    xyz, vel = wl.surface(0)
+    sim.set_surface(xyz, vel, wl.tri)
+    sim.step()
+    dt = time.perf_counter() - t0
+    cells = wl.nx * wl.ny * wl.nz
+    out["leaflet512"] = {"value": cells / dt / 1e9, "unit": UNIT, "cores": ncores, "kind": "oracle",
+                         "sample": "1 whole time step of the 512x384x512 tube with three leaflets (FP64)",
+                         "seconds_per_step": dt}
+    del sim
     return out
 
 
