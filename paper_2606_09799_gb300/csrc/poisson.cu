@@ -665,8 +665,8 @@ __device__ __forceinline__ void fft_x_fwd(const Blk& bk, const Geo& g, const Fie
   using C = typename Cplx<T>::type;
   extern __shared__ unsigned char smem_raw[];
   C* bufa = reinterpret_cast<C*>(smem_raw);
-  C* bufb = bufa + lines_per_block * g.nx;
-  const int n = g.nx, ny = g.ny;
+  C* bufb = bufa + lines_per_block * (g.nx + 1);   // lines padded to nx + 1 words (see fft_pass_r)
+  const int n = g.nx, ny = g.ny, xs = n + 1;
   const int rows = g.ny * g.nz;
   const int line0 = bk.x * lines_per_block;
   const T qf = use_q ? (T)ds->qf[s] : (T)0;
@@ -696,18 +696,19 @@ __device__ __forceinline__ void fft_x_fwd(const Blk& bk, const Geo& g, const Fie
         if (hh == 0) z.x = r;
         else z.y = r;
       }
-      bufa[l * n + i] = z;
+      bufa[l * xs + i] = z;
     }
   }
   if (mode == 3) fold_residual(res1, rmax);
-  const int res = fft_lines<T, false>(bufa, bufb, lines_per_block, plan, reinterpret_cast<const C*>(tw));
+  const int res = fft_lines<T, false>(bufa, bufb, lines_per_block, plan, reinterpret_cast<const C*>(tw), 1, xs,
+                                      magic_div_dev((unsigned)lines_per_block), true);
   const C* out = res == 0 ? bufa : bufb;
   C* spec = reinterpret_cast<C*>(f.spec);
   const int nkx = g.nkx;
   for (int l = threadIdx.y; l < lines_per_block; l += blockDim.y)
   for (int kx = threadIdx.x; kx < nkx; kx += blockDim.x) {
-    const C Z = out[l * n + kx];
-    const C Zc = cconj(out[l * n + (kx == 0 ? 0 : n - kx)]);
+    const C Z = out[l * xs + kx];
+    const C Zc = cconj(out[l * xs + (kx == 0 ? 0 : n - kx)]);
     C Xa, Xb;
     Xa.x = (T)0.5 * (Z.x + Zc.x);
     Xa.y = (T)0.5 * (Z.y + Zc.y);
@@ -745,14 +746,14 @@ __device__ __forceinline__ void fft_x_inv(const Blk& bk, const Geo& g, const Fie
   using C = typename Cplx<T>::type;
   extern __shared__ unsigned char smem_raw[];
   C* bufa = reinterpret_cast<C*>(smem_raw);
-  C* bufb = bufa + lines_per_block * g.nx;
-  const int n = g.nx, nkx = g.nkx;
+  C* bufb = bufa + lines_per_block * (g.nx + 1);   // lines padded to nx + 1 words (see fft_pass_r)
+  const int n = g.nx, nkx = g.nkx, xs = n + 1;
   const long long rows = (long long)g.ny * g.nz;
   const long long line0 = (long long)bk.x * lines_per_block;
   const C* spec = reinterpret_cast<const C*>(f.spec);
   for (int l = threadIdx.y; l < lines_per_block; l += blockDim.y)
   for (int kx = threadIdx.x; kx < n; kx += blockDim.x) {
-    const int t = l * n + kx;
+    const int t = l * xs + kx;
     const long long ra = 2 * (line0 + l), rb = ra + 1;
     const bool mirror = kx >= nkx;
     const int q = mirror ? n - kx : kx;
@@ -767,11 +768,12 @@ __device__ __forceinline__ void fft_x_inv(const Blk& bk, const Geo& g, const Fie
     z.y = A.y + B.x;
     bufa[t] = z;
   }
-  const int res = fft_lines<T, true>(bufa, bufb, lines_per_block, plan, reinterpret_cast<const C*>(tw));
+  const int res = fft_lines<T, true>(bufa, bufb, lines_per_block, plan, reinterpret_cast<const C*>(tw), 1, xs,
+                                     magic_div_dev((unsigned)lines_per_block), true);
   const C* out = res == 0 ? bufa : bufb;
   for (int l = threadIdx.y; l < lines_per_block; l += blockDim.y)
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const int t = l * n + i;
+    const int t = l * xs + i;
     const long long ra = 2 * (line0 + l), rb = ra + 1;
     if (ra < rows) out_phi[ra * n + i] = out[t].x;
     if (rb < rows) out_phi[rb * n + i] = out[t].y;
@@ -2374,7 +2376,7 @@ void launch_poisson(const Geo& g, const Fields<T>& f, const TagBuffers& b, const
   int lpb = lines_for(sh.nx);
   if (tu.fft_lpb > 0 && tu.fft_lpb < lpb) lpb = tu.fft_lpb;
   const long long xlines = ((long long)g.ny * g.nz + 1) / 2;
-  const size_t smx = 2ull * lpb * sh.nx * sizeof(C);
+  const size_t smx = 2ull * lpb * (sh.nx + 1) * sizeof(C);   // lines padded to nx + 1 words
   const int tx = sh.nx < 128 ? sh.nx : 128;
   const dim3 xblk(tx, 256 / tx);
   const dim3 xgrid((unsigned)((xlines + lpb - 1) / lpb));
@@ -2575,7 +2577,7 @@ void launch_poisson(const Geo& g, const Fields<T>& f, const TagBuffers& b, const
 template <typename T>
 void set_fft_smem_limits() {
   using C = typename Cplx<T>::type;
-  const int maxsm = 2 * 2048 * (int)sizeof(C) + 1024;
+  const int maxsm = 2 * 4096 * (int)sizeof(C);   // x lines padded to nx + 1 words
   op_smem_limit<FftXFwd<T>>(maxsm);
   op_smem_limit<FftXInv<T>>(maxsm);
   op_smem_limit<FftZ<T, false>>(maxsm);
