@@ -216,7 +216,10 @@ struct RhsCoef {
   T fba;                // alpha, multiplying the body force read from the device state
 };
 
-template <typename T, bool NU>
+// I: the index type -- int where every field has fewer than 2^31 entries
+// (the 64-bit address arithmetic would otherwise take a large share of this
+// issue-bound kernel's instructions), else long long.
+template <typename T, bool NU, typename I>
 __device__ __forceinline__ void rhs(const Blk& bk, const Geo& g, const Fields<T>& f, const unsigned* __restrict__ flags32, const RhsCoef<T>& cf,
                                              int use_hp, int write_h, const DevState* ds) {
   const int nx = g.nx, ny = g.ny, nz = g.nz;
@@ -237,8 +240,8 @@ __device__ __forceinline__ void rhs(const Blk& bk, const Geo& g, const Fields<T>
     fby = cf.fba * (T)ds->fb[1];
     fbz = cf.fba * (T)ds->fb[2];
   }
-  const long long pv = (long long)(ny + 1) * nx;   // v plane stride (k)
-  const long long pu = (long long)ny * nx;         // u, w, p plane stride
+  const I pv = (I)(ny + 1) * nx;   // v plane stride (k)
+  const I pu = (I)ny * nx;         // u, w, p plane stride
   const T* __restrict__ U = f.u;
   const T* __restrict__ V = f.v;
   const T* __restrict__ W = f.w;
@@ -248,14 +251,14 @@ __device__ __forceinline__ void rhs(const Blk& bk, const Geo& g, const Fields<T>
     const int j = bk.y * blockDim.y + threadIdx.y;
     const int k = bk.z;
     if (i >= nx || j >= ny) return;
-    const long long cell = (long long)k * pu + (long long)j * nx + i;
+    const I cell = (I)k * pu + (I)j * nx + i;
     const int ip = i + 1 == nx ? 0 : i + 1, im = i == 0 ? nx - 1 : i - 1;
     const int kp = k + 1 == nz ? 0 : k + 1, km = k == 0 ? nz - 1 : k - 1;
-    const long long r0 = (long long)k * pu + (long long)j * nx;      // row (j,k) of u, w, p
-    const long long rkp = (long long)kp * pu + (long long)j * nx, rkm = (long long)km * pu + (long long)j * nx;
-    const long long v0 = (long long)k * pv + (long long)j * nx;      // row (j,k) of v
-    const long long v1 = v0 + nx;                                    // row (j+1,k) of v
-    const long long vkm0 = (long long)km * pv + (long long)j * nx, vkp0 = (long long)kp * pv + (long long)j * nx;
+    const I r0 = (I)k * pu + (I)j * nx;      // row (j,k) of u, w, p
+    const I rkp = (I)kp * pu + (I)j * nx, rkm = (I)km * pu + (I)j * nx;
+    const I v0 = (I)k * pv + (I)j * nx;      // row (j,k) of v
+    const I v1 = v0 + nx;                    // row (j+1,k) of v
+    const I vkm0 = (I)km * pv + (I)j * nx, vkp0 = (I)kp * pv + (I)j * nx;
     const unsigned fl = (flags32[cell >> 2] >> (8 * (cell & 3))) & 0xFFu;
     const bool jlo = j == 0, jhi = j + 1 == ny;
     const T pc = P[r0 + i];
@@ -330,15 +333,15 @@ __device__ __forceinline__ void rhs(const Blk& bk, const Geo& g, const Fields<T>
     } else {
       // wall planes of v carry no unknown
       f.R[1][v0 + i] = (T)0;
-      f.R[1][(long long)k * pv + (long long)ny * nx + i] = (T)0;
+      f.R[1][(I)k * pv + (I)ny * nx + i] = (T)0;
       if (write_h) {
         f.H[1][v0 + i] = (T)0;
-        f.H[1][(long long)k * pv + (long long)ny * nx + i] = (T)0;
+        f.H[1][(I)k * pv + (I)ny * nx + i] = (T)0;
       }
     }
   }
 }
-template <typename T, bool NU>
+template <typename T, bool NU, typename I = long long>
 struct Rhs {
   static constexpr int kThreads = 128;
   Geo g;
@@ -348,7 +351,7 @@ struct Rhs {
   int use_hp;
   int write_h;
   const DevState* ds;
-  __device__ __forceinline__ void operator()(const Blk& bk) const { rhs<T, NU>(bk, g, f, flags32, cf, use_hp, write_h, ds); }
+  __device__ __forceinline__ void operator()(const Blk& bk) const { rhs<T, NU, I>(bk, g, f, flags32, cf, use_hp, write_h, ds); }
 };
 
 // Tiled form of the same right-hand side: a block of 32 x 4 threads takes a
@@ -599,10 +602,16 @@ void launch_rhs(const Geo& g, const Fields<T>& f, const TagBuffers& b, const Sta
     return;
   }
   const dim3 grid((g.nx + 31) / 32, (g.ny + 3) / 4, g.nz), blk(32, 4);
-  if (g.yt.ihc)   // non-uniform wall-normal spacing
-    ex.launch(grid, blk, 0, Rhs<T, true>{g, f, b.flags32, cf, hp, wh, ds});
-  else
-    ex.launch(grid, blk, 0, Rhs<T, false>{g, f, b.flags32, cf, hp, wh, ds});
+  // 32-bit indices when every field (the largest: v, with ny + 1 planes)
+  // has fewer than 2^31 entries; a batch decides by its largest instance
+  const bool i32 = (long long)(ex.shape.ny + 1) * ex.shape.nx * ex.shape.nz < (1ll << 31);
+  if (g.yt.ihc) {   // non-uniform wall-normal spacing
+    if (i32) ex.launch(grid, blk, 0, Rhs<T, true, int>{g, f, b.flags32, cf, hp, wh, ds});
+    else ex.launch(grid, blk, 0, Rhs<T, true>{g, f, b.flags32, cf, hp, wh, ds});
+  } else {
+    if (i32) ex.launch(grid, blk, 0, Rhs<T, false, int>{g, f, b.flags32, cf, hp, wh, ds});
+    else ex.launch(grid, blk, 0, Rhs<T, false>{g, f, b.flags32, cf, hp, wh, ds});
+  }
 }
 
 // ---------------------------------------------------------------------------
