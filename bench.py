@@ -435,9 +435,12 @@ def gpu_arm(args):
     # out here (their time is in stages_ms_per_step), and the Thomas and the
     # inverse transforms are rated on the first solve's launches alone
     merged = {}
-    if plane:
+    fused_check = tune_h.get("corr_check", 0) != 2   # else a residual pass shares the correction's stage
+    if plane and fused_check:
         merged["fft_x_fwd"] = ("fft_x_fwd", "correction")
     skip = {s2 for k, v in merged.items() for s2 in v if s2 != k} | {"correction_tri", "correction_inv"}
+    if not fused_check:   # the residual pass and the gated forward transform share a stage
+        skip.add("correction")
     for name, (tot_ms, ngroups) in prof.items():
         if name in ("other",) or name in skip or ngroups == 0 or tot_ms <= 0:
             continue

@@ -308,6 +308,12 @@ typedef struct {
                          global memory (the built-in choice), 2 tiles of 32 x 4 cells marching in z
                          with the three planes of u, v, w (and two of p) and their halos staged in
                          shared memory */
+  int corr_check;     /* mixed path, the first solve's residual against the divergence budget: 1 formed
+                         inside the correction's forward transform (the built-in choice), 2 by a pass
+                         of its own, the correction's forward transform then skipped with the rest of
+                         the correction solve when the budget is met (faster where the budget is met
+                         in most sub-stages; the autotuner leaves it alone: how often the correction
+                         runs changes along a run) */
   double ms_per_step; /* set by the autotuners: measured time per step of the chosen shapes */
 } ibm_tune;
 

@@ -199,6 +199,8 @@ struct Tune {
                   // 4 z from shared-memory tiles of whole lines (nz <= 256, else as 1), y as 3
   int rhs;        // explicit right-hand side: 1 (and 0) one thread per cell from global memory; 2 tiles
                   // marching in z with planes and halos staged in shared memory
+  int corr_check; // mixed path: 1 (and 0) the first solve's residual formed inside the correction's forward
+                  // transform; 2 a residual pass of its own, the whole correction solve gated (not autotuned)
 };
 
 struct Exec {

@@ -1992,6 +1992,46 @@ void launch_build_poisson_tables(const Geo& g, const double* lamx, const double*
 }
 
 // ---------------------------------------------------------------------------
+// Residual check of the mixed path's first solve on its own (launch shape
+// corr_check = 2): max |D u' - q| over the fluid cells of the projected (hi,
+// lo) state u' = uhat - G phi, with the arithmetic of the correction's
+// right-hand side (poisson_rhs, mode 3), folded into the sub-stage's
+// residual word; the correction's forward transform then runs gated, like
+// its Thomas and inverse transforms.  Where the first solve usually meets
+// the budget, this pass (no transform, no spectrum written) replaces the
+// correction's forward transform.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void residual_check(const Blk& bk, const Geo& g, const Fields<T>& f,
+                                               const unsigned* __restrict__ flags32, const DevState* ds, int s,
+                                               int use_q, const ProjCoef<T>& cf, unsigned* res1) {
+  const int i = bk.x * blockDim.x + threadIdx.x;
+  const int j = bk.y * blockDim.y + threadIdx.y;
+  const int k = bk.z;
+  unsigned rmax = 0u;
+  if (i < g.nx && j < g.ny) {
+    const RowY<T> ry = row_y<T>(g, f, cf, j);
+    const T qz = (T)0;
+    (void)poisson_rhs<T>(g, f, flags32, ds, s, use_q, 0.0, 3, cf, ry, qz, qz, qz, i, j, k, rmax);
+  }
+  fold_residual(res1, rmax);
+}
+template <typename T>
+struct ResidualCheck {
+  static constexpr int kThreads = 128;
+  Geo g;
+  Fields<T> f;
+  const unsigned* flags32;
+  const DevState* ds;
+  int s, use_q;
+  ProjCoef<T> cf;
+  unsigned* res1;
+  __device__ __forceinline__ void operator()(const Blk& bk) const {
+    residual_check<T>(bk, g, f, flags32, ds, s, use_q, cf, res1);
+  }
+};
+
+// ---------------------------------------------------------------------------
 // projection (Eq. projection) and pressure update (Eq. update_pressure):
 //   u <- uhat - alpha dt G phi   (v on the wall planes untouched)
 //   p <- p + phi - alpha dt / (2 Re) L_c phi,  L_c with Neumann walls
@@ -2127,7 +2167,6 @@ struct Gated : MinBlocksOf<Op> {
     op(bk);
   }
 };
-
 // ---------------------------------------------------------------------------
 // State diagnostics of a step, after its last projection:
 //   div_max = max over C_F of |D u - q| (Eq. mod_div: the projected field
@@ -2391,11 +2430,12 @@ void launch_poisson(const Geo& g, const Fields<T>& f, const TagBuffers& b, const
   if (tu.tri_y == 3 && tsm > 0) tri = 3;
   // the kernels of the correction solve after its forward transform run
   // gated: they return at once when the first solve met the budget
-  bool gate = false;
+  // gate: 0 none, 1 the correction solve's gate (Gated)
+  int gate = 0;
   auto glaunch = [&](dim3 gr, dim3 bl, size_t sm, const auto& op) {
     using Op = std::decay_t<decltype(op)>;
     if constexpr (sizeof(T) == 4) {
-      if (gate) {
+      if (gate == 1) {
         ex.launch(gr, bl, sm, Gated<Op>{{}, op, ds, sg.s});
         return;
       }
@@ -2492,7 +2532,7 @@ void launch_poisson(const Geo& g, const Fields<T>& f, const TagBuffers& b, const
   auto glaunch_cl = [&](dim3 gr, dim3 bl, size_t sm, const auto& op) {
     using Op = std::decay_t<decltype(op)>;
     if constexpr (sizeof(T) == 4) {
-      if (gate) {
+      if (gate == 1) {
         ex.launch_cluster(gr, bl, sm, Gated<Op>{{}, op, ds, sg.s}, CLN);
         return;
       }
@@ -2538,19 +2578,18 @@ void launch_poisson(const Geo& g, const Fields<T>& f, const TagBuffers& b, const
     cf.ih[d][0] = (float)f.idh[d][0];
     cf.ih[d][1] = (float)f.idh[d][1];
   }
-  auto forward = [&](int mode) {
+  auto forward = [&](int mode) {   // (gated while `gate` is set)
     if (cluster)
-      ex.launch_cluster(dim3(g.ny * CLN), dim3(256), smc,
-                        FftPlaneFwdCl<T, CLN>{g, f, b.flags32, tb.twx, tb.twz, px, pz, wbc, czc, ds, sg.s, use_q,
-                                              scale, mode, cf, ds->res1 + sg.s},
-                        CLN);
+      glaunch_cl(dim3(g.ny * CLN), dim3(256), smc,
+                 FftPlaneFwdCl<T, CLN>{g, f, b.flags32, tb.twx, tb.twz, px, pz, wbc, czc, ds, sg.s, use_q, scale,
+                                       mode, cf, ds->res1 + sg.s});
     else if (plane)
-      ex.launch(dim3(g.ny), dim3(1024), smp,
-                FftPlaneFwd<T>{g, f, b.flags32, tb.twx, tb.twz, px, pz, wbuf, czp, ds, sg.s, use_q, scale, mode, cf,
-                               ds->res1 + sg.s});
+      glaunch(dim3(g.ny), dim3(1024), smp,
+              FftPlaneFwd<T>{g, f, b.flags32, tb.twx, tb.twz, px, pz, wbuf, czp, ds, sg.s, use_q, scale, mode, cf,
+                             ds->res1 + sg.s});
     else
-      ex.launch(xgrid, xblk, smx,
-                FftXFwd<T>{g, f, b.flags32, tb.twx, px, lpb, ds, sg.s, use_q, scale, mode, cf, ds->res1 + sg.s});
+      glaunch(xgrid, xblk, smx,
+              FftXFwd<T>{g, f, b.flags32, tb.twx, px, lpb, ds, sg.s, use_q, scale, mode, cf, ds->res1 + sg.s});
   };
   const dim3 pgrid((g.nx + 31) / 32, (g.ny + 3) / 4, g.nz), pblk(32, 4);
   ex.mark(ST_FFT_X_FWD);
@@ -2566,10 +2605,16 @@ void launch_poisson(const Geo& g, const Fields<T>& f, const TagBuffers& b, const
   // right-hand side, mode 3), then apply both projections and the pressure
   // update in one pass
   ex.mark(ST_CORRECT);
-  forward(3);
-  gate = true;
+  if (tu.corr_check == 2) {   // the residual alone, then the whole correction solve gated
+    ex.launch(pgrid, pblk, 0, ResidualCheck<T>{g, f, b.flags32, ds, sg.s, use_q, cf, ds->res1 + sg.s});
+    gate = 1;
+    forward(3);
+  } else {                    // the correction's forward transform forms the residual (built-in)
+    forward(3);
+    gate = 1;
+  }
   solve_rest(f.phi2, false);
-  gate = false;
+  gate = 0;
   ex.mark(ST_PROJECT);
   ex.launch(pgrid, pblk, 0, Project<T>{g, f, cf, 3, ds, sg.s});
 }
@@ -2589,6 +2634,9 @@ void set_fft_smem_limits() {
   op_smem_limit<FftPlaneInvCl<T, 4>>(100 * 1024);
   if constexpr (sizeof(T) == 4) {   // the correction solve's kernels (mixed path)
     op_smem_limit<Gated<FftPlaneInvCl<T, 4>>>(100 * 1024);
+    op_smem_limit<Gated<FftPlaneFwdCl<T, 4>>>(100 * 1024);
+    op_smem_limit<Gated<FftPlaneFwd<T>>>(200 * 1024);
+    op_smem_limit<Gated<FftXFwd<T>>>(maxsm);
     op_smem_limit<Gated<FftXInv<T>>>(maxsm);
     op_smem_limit<Gated<FftZ<T, false>>>(maxsm);
     op_smem_limit<Gated<FftZ<T, true>>>(maxsm);

@@ -981,6 +981,7 @@ static void tune_out(const Tune& t, double ms, ibm_tune* out) {
   out->fft_plane = t.fft_plane;
   out->sweep_y = t.sweep_y;
   out->rhs = t.rhs;
+  out->corr_check = t.corr_check;
   out->ms_per_step = ms;
 }
 
@@ -991,8 +992,8 @@ static void tune_log(const Tune& t, double ms) {
   if (on)
     fprintf(stderr,
             "ibm autotune: tri_y %d sweep_w %d fft_lpb %d fft_cols %d sweep_zy %d fft_plane %d sweep_y %d rhs %d"
-            " -> %.4f ms/step\n",
-            t.tri_y, t.sweep_w, t.fft_lpb, t.fft_cols, t.sweep_zy, t.fft_plane, t.sweep_y, t.rhs, ms);
+            " corr_check %d -> %.4f ms/step\n",
+            t.tri_y, t.sweep_w, t.fft_lpb, t.fft_cols, t.sweep_zy, t.fft_plane, t.sweep_y, t.rhs, t.corr_check, ms);
 }
 
 template <class Trial>
@@ -1763,12 +1764,14 @@ static bool tune_valid(const ibm_tune* t) {
   if (t->fft_plane < 0 || t->fft_plane > 3) return false;
   if (t->sweep_y < 0 || t->sweep_y > 4) return false;
   if (t->rhs < 0 || t->rhs > 2) return false;
+  if (t->corr_check < 0 || t->corr_check > 2) return false;
   return true;
 }
 
 ibm_status ibm_set_tune(ibm_handle h, const ibm_tune* t) {
   if (!h || !tune_valid(t)) return IBM_ERR_ARG;
-  h->tune = Tune{t->tri_y, t->sweep_w, t->fft_lpb, t->fft_cols, t->sweep_zy, t->fft_plane, t->sweep_y, t->rhs};
+  h->tune = Tune{t->tri_y, t->sweep_w, t->fft_lpb, t->fft_cols, t->sweep_zy, t->fft_plane, t->sweep_y, t->rhs,
+                 t->corr_check};
   invalidate(h);
   return IBM_OK;
 }
@@ -1930,7 +1933,8 @@ ibm_status ibm_batch_profile_stages(ibm_batch_handle b, int nsteps, double* ms, 
 
 ibm_status ibm_batch_set_tune(ibm_batch_handle b, const ibm_tune* t) {
   if (!b || !tune_valid(t)) return IBM_ERR_ARG;
-  b->tune = Tune{t->tri_y, t->sweep_w, t->fft_lpb, t->fft_cols, t->sweep_zy, t->fft_plane, t->sweep_y, t->rhs};
+  b->tune = Tune{t->tri_y, t->sweep_w, t->fft_lpb, t->fft_cols, t->sweep_zy, t->fft_plane, t->sweep_y, t->rhs,
+                 t->corr_check};
   b->built = false;
   return IBM_OK;
 }

@@ -60,7 +60,8 @@ IBM_NSTAGES = 19
 class ibm_tune(ctypes.Structure):
     _fields_ = [("tri_y", ctypes.c_int), ("sweep_w", ctypes.c_int), ("fft_lpb", ctypes.c_int),
                 ("fft_cols", ctypes.c_int), ("sweep_zy", ctypes.c_int), ("fft_plane", ctypes.c_int),
-                ("sweep_y", ctypes.c_int), ("rhs", ctypes.c_int), ("ms_per_step", ctypes.c_double)]
+                ("sweep_y", ctypes.c_int), ("rhs", ctypes.c_int), ("corr_check", ctypes.c_int),
+                ("ms_per_step", ctypes.c_double)]
 
 
 class ibm_batch_info(ctypes.Structure):
@@ -314,12 +315,13 @@ def ibm_tag_noalloc(nx, ny, nz, xyz, tri, owners, lx=1.0, ly=1.0, lz=1.0, ybc=IB
 def _tune_dict(t: ibm_tune) -> dict:
     return {"tri_y": t.tri_y, "sweep_w": t.sweep_w, "fft_lpb": t.fft_lpb, "fft_cols": t.fft_cols,
             "sweep_zy": t.sweep_zy, "fft_plane": t.fft_plane, "sweep_y": t.sweep_y, "rhs": t.rhs,
-            "ms_per_step": t.ms_per_step}
+            "corr_check": t.corr_check, "ms_per_step": t.ms_per_step}
 
 
-def ibm_set_tune(h, tri_y=0, sweep_w=0, fft_lpb=0, fft_cols=0, sweep_zy=0, fft_plane=0, sweep_y=0, rhs=0):
+def ibm_set_tune(h, tri_y=0, sweep_w=0, fft_lpb=0, fft_cols=0, sweep_zy=0, fft_plane=0, sweep_y=0, rhs=0,
+                 corr_check=0):
     _check(h, load().ibm_set_tune(h, ctypes.byref(ibm_tune(tri_y, sweep_w, fft_lpb, fft_cols, sweep_zy, fft_plane,
-                                                           sweep_y, rhs, 0.0))))
+                                                           sweep_y, rhs, corr_check, 0.0))))
 
 
 def ibm_get_tune(h) -> dict:
@@ -378,9 +380,10 @@ def ibm_batch_profile_stages(b, nsteps=1) -> dict:
     return {ibm_stage_name(i): (ms[i], kn[i]) for i in range(IBM_NSTAGES)}
 
 
-def ibm_batch_set_tune(b, tri_y=0, sweep_w=0, fft_lpb=0, fft_cols=0, sweep_zy=0, fft_plane=0, sweep_y=0, rhs=0):
+def ibm_batch_set_tune(b, tri_y=0, sweep_w=0, fft_lpb=0, fft_cols=0, sweep_zy=0, fft_plane=0, sweep_y=0, rhs=0,
+                       corr_check=0):
     _bcheck(b, load().ibm_batch_set_tune(b, ctypes.byref(ibm_tune(tri_y, sweep_w, fft_lpb, fft_cols, sweep_zy,
-                                                                   fft_plane, sweep_y, rhs, 0.0))))
+                                                                   fft_plane, sweep_y, rhs, corr_check, 0.0))))
 
 
 def ibm_batch_autotune(b, steps=3) -> dict:

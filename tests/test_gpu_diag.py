@@ -190,15 +190,19 @@ def test_save_restore_mixed_ab_close():
     assert dist[False] > 10.0 * max(dist[True], 1e-9), dist
 
 
-def test_correction_solve_runs_only_above_the_budget():
+@pytest.mark.parametrize("corr_check", [1, 2])
+def test_correction_solve_runs_only_above_the_budget(corr_check):
     """IBM_MIXED: the correction solve runs in a sub-stage only when the
     first solve's max |D u' - q| over C_F exceeds the budget (Eq. mod_div);
-    skipped, the step keeps the once-projected state."""
+    skipped, the step keeps the once-projected state.  corr_check 1 forms the
+    residual inside the correction's forward transform, 2 in a pass of its
+    own with the whole correction solve gated."""
     wl = inputs.oscillating_sphere(n=32, steps=6, subdiv=2)
     ud = 32.0                                    # U / dx of the unit box
     runs = {}
     for budget in (0.0, 1e30, None):
         g = ibm.Simulation(32, 32, 32, re=wl.re, dt=wl.dt, precision="mixed")
+        ibm.ibm_set_tune(g.h, corr_check=corr_check)
         if budget is None:                       # one of the first run's residuals (an FP32 value)
             budget = sorted(runs[0.0]["first"])[2]
         g.set_div_budget(budget)
@@ -232,6 +236,34 @@ def test_correction_solve_runs_only_above_the_budget():
     # the skipped corrections stay within the velocity bar of the mixed path
     for a, b in zip(always["fields"][:3], never["fields"][:3]):
         assert np.abs(a - b).max() <= 1e-5
+
+
+@pytest.mark.parametrize("budget", [0.0, 1e30, 2.0e-6])
+def test_residual_pass_of_its_own_equals_the_fused_residual(budget):
+    """The residual pass (corr_check 2) and the correction's forward transform
+    (corr_check 1) form the same residual with the same arithmetic, so the
+    decisions, the residuals and the fields agree bit for bit, with the
+    correction always, never and sometimes taken (48 x 37 x 96, a moving
+    sphere, 4 steps)."""
+    wl = inputs.oscillating_sphere(n=48, steps=4, subdiv=2)
+    out = []
+    for cc in (1, 2):
+        g = ibm.Simulation(48, 37, 96, 1.0, 0.9, 1.6, re=150.0, dt=2e-3, precision="mixed")
+        ibm.ibm_set_tune(g.h, corr_check=cc)
+        g.set_div_budget(budget * 48.0)
+        first, taken = [], []
+        for s in range(4):
+            xyz, vel = wl.surface(s)
+            g.set_surface(xyz, vel, wl.tri)
+            g.step()
+            d = g.diag()
+            first.append(d["div_first"])
+            taken.append(d["corr_solves"])
+        out.append((first, taken, g.fields()))
+    for o in out[1:]:
+        assert out[0][0] == o[0] and out[0][1] == o[1]
+        for a, b in zip(out[0][2], o[2]):
+            np.testing.assert_array_equal(a, b)
 
 
 def test_div_budget_rejects_negative_and_nan():

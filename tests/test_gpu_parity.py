@@ -294,7 +294,7 @@ def test_candidate_capacity_grows_for_large_triangles():
                                   dict(tri_y=1, sweep_y=4, fft_plane=2),
                                   dict(tri_y=3, sweep_y=4, fft_plane=1),
                                   dict(tri_y=4, sweep_y=4, fft_plane=3),
-                                  dict(tri_y=0, fft_plane=0, rhs=2),
+                                  dict(tri_y=0, fft_plane=0, rhs=2, corr_check=2),
                                   dict(tri_y=0, fft_plane=0)])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-5)])
 def test_every_launch_shape_matches_oracle(tune, precision, tol):
