@@ -210,7 +210,12 @@ def stage_kernel(stage: str, tune: dict | None, precision: str, ny: int = 128, n
         form = fft_form(t, nz=nz, word=4 if precision == "mixed" else 8)
         return {"cluster": f"FftPlaneFwdCl<{T}, 4>", "plane": f"FftPlaneFwd<{T}>"}.get(form, f"FftXFwd<{T}>")
     if stage == "rhs":
-        return f"RhsTile<{T}, 0>" if t.get("rhs", 0) == 2 else f"Rhs<{T}, 0, int>"
+        v = t.get("rhs", 0)
+        if v == 2:
+            return f"RhsTile<{T}, 0>"
+        if precision == "mixed" and v in (0, 3):
+            return "RhsVec<false>"
+        return f"Rhs<{T}, 0, int>"
     if stage == "project":
         return f"Project<{T}>"
     return None

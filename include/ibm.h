@@ -305,9 +305,10 @@ typedef struct {
                          at most 1024 rows; else as 1), 4 z from tiles of 32 lines with all their rows
                          staged in shared memory (nz <= 256; else as 1), y as 3 */
   int rhs;            /* explicit right-hand side: 1 one thread per cell reading its neighbours from
-                         global memory (the built-in choice), 2 tiles of 32 x 4 cells marching in z
-                         with the three planes of u, v, w (and two of p) and their halos staged in
-                         shared memory */
+                         global memory (the built-in choice of the FP64 path), 2 tiles of 32 x 4 cells
+                         marching in z with the three planes of u, v, w (and two of p) and their halos
+                         staged in shared memory, 3 two cells per thread along x with paired (float2)
+                         row loads (the built-in choice of the FP32 path; the FP64 path runs 1) */
   int corr_check;     /* mixed path, the first solve's residual against the divergence budget: 1 formed
                          inside the correction's forward transform (the built-in choice), 2 by a pass
                          of its own, the correction's forward transform then skipped with the rest of

@@ -197,8 +197,9 @@ struct Tune {
                   // 2 z as 1, y from tiles staged by bulk asynchronous copies (else as 1);
                   // 3 z as 1, y from the tabulated FP32 rows in register batches (mixed path, else as 1);
                   // 4 z from shared-memory tiles of whole lines (nz <= 256, else as 1), y as 3
-  int rhs;        // explicit right-hand side: 1 (and 0) one thread per cell from global memory; 2 tiles
-                  // marching in z with planes and halos staged in shared memory
+  int rhs;        // explicit right-hand side: 1 one thread per cell from global memory; 2 tiles marching
+                  // in z with planes and halos staged in shared memory; 3 two cells per thread along x
+                  // with float2 row loads (FP32); 0: 3 in FP32, 1 in FP64
   int corr_check; // mixed path: 1 (and 0) the first solve's residual formed inside the correction's forward
                   // transform; 2 a residual pass of its own, the whole correction solve gated (not autotuned)
 };

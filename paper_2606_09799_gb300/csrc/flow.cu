@@ -580,6 +580,197 @@ struct RhsTile {
   }
 };
 
+// Two cells per thread along x (launch shape rhs = 3, FP32 path; nx is even
+// on every grid): every row the stencil reads is loaded as one float2 for
+// the thread's cells i0, i0 + 1 plus a scalar on either side where an
+// x-neighbour is needed, so the loads, their address arithmetic and the
+// stores are shared by the two cells.  Each cell's arithmetic is the
+// per-cell kernel's, term by term.
+template <bool NU>
+__device__ __forceinline__ void rhs_vec(const Blk& bk, const Geo& g, const Fields<float>& f,
+                                        const unsigned* __restrict__ flags32, const RhsCoef<float>& cf, int use_hp,
+                                        int write_h, const DevState* ds) {
+  using T = float;
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const T idx = cf.idx, idy = cf.idy, idz = cf.idz;
+  const T idx2 = cf.idx2, idy2 = cf.idy2, idz2 = cf.idz2;
+  const T gs = cf.gs;
+  const T q = (T)0.25;
+  const T cg = cf.cg, cr = cf.cr, ca = cf.ca, cv = cf.cv, tdt = cf.dt;
+  const T fbx = cf.fba * ds->fbf[0], fby = cf.fba * ds->fbf[1], fbz = cf.fba * ds->fbf[2];
+  const int i0 = 2 * (int)(bk.x * blockDim.x + threadIdx.x);
+  const int j = bk.y * blockDim.y + threadIdx.y;
+  const int k = bk.z;
+  if (i0 >= nx || j >= ny) return;
+  const int pv = (ny + 1) * nx, pu = ny * nx;
+  const int im = i0 == 0 ? nx - 1 : i0 - 1;        // left of cell a = i0
+  const int ip2 = i0 + 2 == nx ? 0 : i0 + 2;       // right of cell b = i0 + 1
+  const int kp = k + 1 == nz ? 0 : k + 1, km = k == 0 ? nz - 1 : k - 1;
+  const int r0 = k * pu + j * nx, rkp = kp * pu + j * nx, rkm = km * pu + j * nx;
+  const int v0 = k * pv + j * nx, v1 = v0 + nx;
+  const int vkm0 = km * pv + j * nx, vkp0 = kp * pv + j * nx;
+  const bool jlo = j == 0, jhi = j + 1 == ny;
+  const T* __restrict__ U = f.u;
+  const T* __restrict__ V = f.v;
+  const T* __restrict__ W = f.w;
+  const T* __restrict__ P = f.p;
+  auto ld2 = [](const T* p, int o) { return *reinterpret_cast<const float2*>(p + o); };
+  const float2 zero2 = make_float2(0.0f, 0.0f);
+  // rows of u
+  const float2 Ur = ld2(U, r0 + i0);
+  const T Ur_m = U[r0 + im], Ur_p = U[r0 + ip2];
+  const float2 Un2 = jhi ? zero2 : ld2(U, r0 + nx + i0);
+  const float2 Us2 = jlo ? zero2 : ld2(U, r0 - nx + i0);
+  const T Us_p = jlo ? (T)0 : U[r0 - nx + ip2];
+  const float2 Uf2 = ld2(U, rkp + i0), Ub2 = ld2(U, rkm + i0);
+  const T Ub_p = U[rkm + ip2];
+  // rows of v
+  const float2 V1 = ld2(V, v1 + i0);
+  const T V1_m = V[v1 + im];
+  const float2 V0 = ld2(V, v0 + i0);
+  const T V0_m = V[v0 + im], V0_p = V[v0 + ip2];
+  const float2 Vs2 = jlo ? zero2 : ld2(V, v0 - nx + i0);
+  const float2 Vf2 = ld2(V, vkp0 + i0), Vb2 = ld2(V, vkm0 + i0), Vbn2 = ld2(V, vkm0 + nx + i0);
+  // rows of w
+  const float2 W0 = ld2(W, r0 + i0);
+  const T W0_m = W[r0 + im], W0_p = W[r0 + ip2];
+  const float2 Wn2 = jhi ? zero2 : ld2(W, r0 + nx + i0);
+  const float2 Ws2 = jlo ? zero2 : ld2(W, r0 - nx + i0);
+  const float2 Wf2 = ld2(W, rkp + i0), Wb2 = ld2(W, rkm + i0);
+  const T Wf_m = W[rkp + im];
+  const float2 Wfs2 = jlo ? zero2 : ld2(W, rkp - nx + i0);
+  // rows of p
+  const float2 P0 = ld2(P, r0 + i0), Pb2 = ld2(P, rkm + i0);
+  const T P0_m = P[r0 + im];
+  const float2 Ps2 = jlo ? zero2 : ld2(P, r0 - nx + i0);
+  // flags of both cells (one word: i0 even)
+  const unsigned fw = flags32[(r0 + i0) >> 2];
+  const unsigned sh = 8u * (unsigned)((r0 + i0) & 3);
+  const unsigned fla = (fw >> sh) & 0xFFu, flb = (fw >> (sh + 8u)) & 0xFFu;
+  constexpr bool nun = NU;
+  const T ihc = nun ? (T)g.yt.ihc[j] : idy, ihs = nun ? (T)g.yt.ihf[j] : idy, ihn = nun ? (T)g.yt.ihf[j + 1] : idy;
+  const T ihcm = (nun && j >= 1) ? (T)g.yt.ihc[j - 1] : idy;
+  // ---------------- u ----------------
+  auto ucomp = [&](T uc, T ue, T uw, T unr, T usr, T uf, T ub, T v1m, T v1c, T v0m, T v0c, T wpm, T wpc, T w0m,
+                   T w0c, T pc, T pm, T& H) {
+    const T un = jhi ? gs * uc : unr;
+    const T us = jlo ? gs * uc : usr;
+    const T adx = ((uc + ue) * (uc + ue) - (uw + uc) * (uw + uc)) * q * idx;
+    const T vt = jhi ? (T)0 : (v1m + v1c) * (uc + un);
+    const T vb = jlo ? (T)0 : (v0m + v0c) * (us + uc);
+    const T ady = (vt - vb) * q * ihc;
+    const T wf = (wpm + wpc) * (uc + uf);
+    const T wb = (w0m + w0c) * (ub + uc);
+    const T adz = (wf - wb) * q * idz;
+    H = -(adx + ady + adz);
+    const T lapy = nun ? ((un - uc) * ihn - (uc - us) * ihs) * ihc : (un - (T)2 * uc + us) * idy2;
+    const T lap = (ue - (T)2 * uc + uw) * idx2 + lapy + (uf - (T)2 * uc + ub) * idz2;
+    const T G = (pc - pm) * idx;
+    return cg * H - ca * G + cv * lap + fbx;
+  };
+  {
+    T Ha, Hb;
+    T ra = ucomp(Ur.x, Ur.y, Ur_m, Un2.x, Us2.x, Uf2.x, Ub2.x, V1_m, V1.x, V0_m, V0.x, Wf_m, Wf2.x, W0_m, W0.x, P0.x,
+                 P0_m, Ha);
+    T rb = ucomp(Ur.y, Ur_p, Ur.x, Un2.y, Us2.y, Uf2.y, Ub2.y, V1.x, V1.y, V0.x, V0.y, Wf2.x, Wf2.y, W0.x, W0.y, P0.y,
+                 P0.x, Hb);
+    if (use_hp) {
+      const float2 hp = ld2(f.Hp[0], r0 + i0);
+      ra += cr * hp.x;
+      rb += cr * hp.y;
+    }
+    if (write_h) *reinterpret_cast<float2*>(f.H[0] + r0 + i0) = make_float2(Ha, Hb);
+    *reinterpret_cast<float2*>(f.R[0] + r0 + i0) =
+        make_float2((fla & FLAG_U) ? (T)0 : tdt * ra, (flb & FLAG_U) ? (T)0 : tdt * rb);
+  }
+  // ---------------- w ----------------
+  auto wcomp = [&](T wc, T we, T ww, T wnr, T wsr, T wf, T wb, T ukmp, T u0p, T ukm, T u0, T vkmn, T v1c, T vkm, T v0c,
+                   T pc, T pkm, T& H) {
+    const T wn = jhi ? gs * wc : wnr;
+    const T ws = jlo ? gs * wc : wsr;
+    const T ue = (ukmp + u0p) * (wc + we);
+    const T uw = (ukm + u0) * (ww + wc);
+    const T adx = (ue - uw) * q * idx;
+    const T vt = jhi ? (T)0 : (vkmn + v1c) * (wc + wn);
+    const T vb = jlo ? (T)0 : (vkm + v0c) * (ws + wc);
+    const T ady = (vt - vb) * q * ihc;
+    const T adz = ((wc + wf) * (wc + wf) - (wb + wc) * (wb + wc)) * q * idz;
+    H = -(adx + ady + adz);
+    const T lapy = nun ? ((wn - wc) * ihn - (wc - ws) * ihs) * ihc : (wn - (T)2 * wc + ws) * idy2;
+    const T lap = (we - (T)2 * wc + ww) * idx2 + lapy + (wf - (T)2 * wc + wb) * idz2;
+    const T G = (pc - pkm) * idz;
+    return cg * H - ca * G + cv * lap + fbz;
+  };
+  {
+    T Ha, Hb;
+    T ra = wcomp(W0.x, W0.y, W0_m, Wn2.x, Ws2.x, Wf2.x, Wb2.x, Ub2.y, Ur.y, Ub2.x, Ur.x, Vbn2.x, V1.x, Vb2.x, V0.x,
+                 P0.x, Pb2.x, Ha);
+    T rb = wcomp(W0.y, W0_p, W0.x, Wn2.y, Ws2.y, Wf2.y, Wb2.y, Ub_p, Ur_p, Ub2.y, Ur.y, Vbn2.y, V1.y, Vb2.y, V0.y,
+                 P0.y, Pb2.y, Hb);
+    if (use_hp) {
+      const float2 hp = ld2(f.Hp[2], r0 + i0);
+      ra += cr * hp.x;
+      rb += cr * hp.y;
+    }
+    if (write_h) *reinterpret_cast<float2*>(f.H[2] + r0 + i0) = make_float2(Ha, Hb);
+    *reinterpret_cast<float2*>(f.R[2] + r0 + i0) =
+        make_float2((fla & FLAG_W) ? (T)0 : tdt * ra, (flb & FLAG_W) ? (T)0 : tdt * rb);
+  }
+  // ---------------- v, 1 <= j <= ny-1 ----------------
+  if (j >= 1) {
+    auto vcomp = [&](T vc, T ve, T vw, T vn, T vs, T vf, T vbk, T usp, T u0p, T us, T u0, T wps, T wp0, T w0s, T w00,
+                     T pc, T ps, T& H) {
+      const T ue = (usp + u0p) * (vc + ve);
+      const T uw = (us + u0) * (vw + vc);
+      const T adx = (ue - uw) * q * idx;
+      const T ady = ((vc + vn) * (vc + vn) - (vs + vc) * (vs + vc)) * q * ihs;
+      const T wf = (wps + wp0) * (vc + vf);
+      const T wb = (w0s + w00) * (vbk + vc);
+      const T adz = (wf - wb) * q * idz;
+      H = -(adx + ady + adz);
+      const T lapy = nun ? ((vn - vc) * ihc - (vc - vs) * ihcm) * ihs : (vn - (T)2 * vc + vs) * idy2;
+      const T lap = (ve - (T)2 * vc + vw) * idx2 + lapy + (vf - (T)2 * vc + vbk) * idz2;
+      const T G = (pc - ps) * ihs;
+      return cg * H - ca * G + cv * lap + fby;
+    };
+    T Ha, Hb;
+    T ra = vcomp(V0.x, V0.y, V0_m, V1.x, Vs2.x, Vf2.x, Vb2.x, Us2.y, Ur.y, Us2.x, Ur.x, Wfs2.x, Wf2.x, Ws2.x, W0.x,
+                 P0.x, Ps2.x, Ha);
+    T rb = vcomp(V0.y, V0_p, V0.x, V1.y, Vs2.y, Vf2.y, Vb2.y, Us_p, Ur_p, Us2.y, Ur.y, Wfs2.y, Wf2.y, Ws2.y, W0.y,
+                 P0.y, Ps2.y, Hb);
+    if (use_hp) {
+      const float2 hp = ld2(f.Hp[1], v0 + i0);
+      ra += cr * hp.x;
+      rb += cr * hp.y;
+    }
+    if (write_h) *reinterpret_cast<float2*>(f.H[1] + v0 + i0) = make_float2(Ha, Hb);
+    *reinterpret_cast<float2*>(f.R[1] + v0 + i0) =
+        make_float2((fla & FLAG_V) ? (T)0 : tdt * ra, (flb & FLAG_V) ? (T)0 : tdt * rb);
+  } else {
+    // wall planes of v carry no unknown
+    *reinterpret_cast<float2*>(f.R[1] + v0 + i0) = zero2;
+    *reinterpret_cast<float2*>(f.R[1] + k * pv + ny * nx + i0) = zero2;
+    if (write_h) {
+      *reinterpret_cast<float2*>(f.H[1] + v0 + i0) = zero2;
+      *reinterpret_cast<float2*>(f.H[1] + k * pv + ny * nx + i0) = zero2;
+    }
+  }
+}
+template <bool NU>
+struct RhsVec {
+  static constexpr int kThreads = 128;
+  Geo g;
+  Fields<float> f;
+  const unsigned* flags32;
+  RhsCoef<float> cf;
+  int use_hp;
+  int write_h;
+  const DevState* ds;
+  __device__ __forceinline__ void operator()(const Blk& bk) const {
+    rhs_vec<NU>(bk, g, f, flags32, cf, use_hp, write_h, ds);
+  }
+};
+
 template <typename T>
 void launch_rhs(const Geo& g, const Fields<T>& f, const TagBuffers& b, const Stage& sg, double dt, double re,
                 bool use_hp, bool write_h, DevState* ds, Exec& ex) {
@@ -605,6 +796,17 @@ void launch_rhs(const Geo& g, const Fields<T>& f, const TagBuffers& b, const Sta
   // 32-bit indices when every field (the largest: v, with ny + 1 planes)
   // has fewer than 2^31 entries; a batch decides by its largest instance
   const bool i32 = (long long)(ex.shape.ny + 1) * ex.shape.nx * ex.shape.nz < (1ll << 31);
+  if constexpr (sizeof(T) == 4) {
+    // two cells per thread along x (FP32; the built-in choice there)
+    if ((ex.tune.rhs == 3 || ex.tune.rhs == 0) && i32 && g.nx % 2 == 0 && ex.shape.nx % 2 == 0) {
+      const dim3 gv((g.nx / 2 + 31) / 32, (g.ny + 3) / 4, g.nz);
+      if (g.yt.ihc)
+        ex.launch(gv, blk, 0, RhsVec<true>{g, f, b.flags32, cf, hp, wh, ds});
+      else
+        ex.launch(gv, blk, 0, RhsVec<false>{g, f, b.flags32, cf, hp, wh, ds});
+      return;
+    }
+  }
   if (g.yt.ihc) {   // non-uniform wall-normal spacing
     if (i32) ex.launch(grid, blk, 0, Rhs<T, true, int>{g, f, b.flags32, cf, hp, wh, ds});
     else ex.launch(grid, blk, 0, Rhs<T, true>{g, f, b.flags32, cf, hp, wh, ds});

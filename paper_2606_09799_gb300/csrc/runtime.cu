@@ -917,7 +917,7 @@ struct Knob {
 };
 
 static std::vector<Knob> tune_knobs() {
-  return {{&Tune::fft_plane, {3, 2, 1}}, {&Tune::sweep_zy, {2, 1}}, {&Tune::sweep_y, {1, 2, 3, 4}}, {&Tune::tri_y, {1, 4, 2, 3}}, {&Tune::rhs, {1, 2}},
+  return {{&Tune::fft_plane, {3, 2, 1}}, {&Tune::sweep_zy, {2, 1}}, {&Tune::sweep_y, {1, 2, 3, 4}}, {&Tune::tri_y, {1, 4, 2, 3}}, {&Tune::rhs, {3, 1, 2}},
           {&Tune::sweep_w, {64, 32, 16}},
           {&Tune::fft_lpb, {0, 8, 4, 2}},
           {&Tune::fft_cols, {16, 8, 4}}};
@@ -1763,7 +1763,7 @@ static bool tune_valid(const ibm_tune* t) {
   if (t->sweep_zy < 0 || t->sweep_zy > 2) return false;
   if (t->fft_plane < 0 || t->fft_plane > 3) return false;
   if (t->sweep_y < 0 || t->sweep_y > 4) return false;
-  if (t->rhs < 0 || t->rhs > 2) return false;
+  if (t->rhs < 0 || t->rhs > 3) return false;
   if (t->corr_check < 0 || t->corr_check > 2) return false;
   return true;
 }

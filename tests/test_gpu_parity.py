@@ -323,8 +323,10 @@ def test_every_launch_shape_matches_oracle(tune, precision, tol):
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_tiled_rhs_equals_the_per_cell_rhs(precision, stretched):
     """The right-hand side from z-marching tiles with shared-memory halos
-    (rhs 2) takes every neighbour the per-cell kernel (rhs 1, the built-in
-    choice) reads from global memory and does the same arithmetic: fields
+    (rhs 2) and the one with two cells per thread and paired row loads
+    (rhs 3, the built-in choice of the FP32 path) take every neighbour the
+    per-cell kernel (rhs 1) reads from global memory and do the same
+    arithmetic: fields
     equal to rounding after 3 steps with a moving sphere, on the uniform and
     on a stretched wall-normal grid, AB+CN (the previous sub-stage's H too).
     48 x 37 x 40: ragged tiles in i (48 = 32 + 16), j (37 = 9 x 4 + 1) and k
@@ -332,7 +334,7 @@ def test_tiled_rhs_equals_the_per_cell_rhs(precision, stretched):
     wl = inputs.oscillating_sphere(n=48, steps=3, subdiv=2)
     yf = inputs.stretched_faces(37, ly=0.9) if stretched else None
     sims = []
-    for rhs in (1, 2):
+    for rhs in (1, 2, 3):   # 3: two cells per thread (FP32 path only; the FP64 path falls back to 1)
         g = ibm.Simulation(48, 37, 40, 1.0, 0.9, 1.6, re=150.0, dt=2e-3, scheme="ab", precision=precision,
                            y_faces=yf)
         ibm.ibm_set_tune(g.h, rhs=rhs)
@@ -343,10 +345,12 @@ def test_tiled_rhs_equals_the_per_cell_rhs(precision, stretched):
             g.set_surface(xyz, vel, wl.tri)
             g.step()
     tol = 1e-14 if precision == "fp64" else 1e-6
-    for a, b in zip(sims[0].fields(), sims[1].fields()):
-        assert np.abs(a - b).max() <= tol * max(1.0, np.abs(a).max())
-    for a, b in zip(sims[0].history(), sims[1].history()):
-        assert np.abs(a - b).max() <= tol * max(1.0, np.abs(a).max())
+    for other in sims[1:]:
+        for a, b in zip(sims[0].fields(), other.fields()):
+            assert np.abs(a - b).max() <= tol * max(1.0, np.abs(a).max())
+        for a, b in zip(sims[0].history(), other.history()):
+            assert np.abs(a - b).max() <= tol * max(1.0, np.abs(a).max())
+
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
