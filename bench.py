@@ -214,7 +214,7 @@ def stage_kernel(stage: str, tune: dict | None, precision: str, ny: int = 128, n
         if v == 2:
             return f"RhsTile<{T}, 0>"
         if precision == "mixed" and v in (0, 3):
-            return "RhsVec<false>"
+            return "RhsVec<0>"
         return f"Rhs<{T}, 0, int>"
     if stage == "project":
         return f"Project<{T}>"
