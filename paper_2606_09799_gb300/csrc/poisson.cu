@@ -654,6 +654,42 @@ __device__ __forceinline__ T poisson_rhs(const Geo& g, const Fields<T>& f, const
   return r;
 }
 
+// Mode 0 of poisson_rhs for the FP32 cells (i, j, k) and (i + 1, j, k), i even
+// (nx is even on every grid, so the pairs are 8-byte aligned; every field has
+// fewer than 2^30 entries): each row is read as one float2, with the x-
+// neighbour i + 2 of the second cell as a scalar, and each cell takes
+// poisson_rhs's operations in the same order.
+__device__ __forceinline__ void rhs_pair0(const Geo& g, const Fields<float>& f, const unsigned* __restrict__ flags32,
+                                          int use_q, const ProjCoef<float>& cf, const RowY<float>& ry, float qf,
+                                          int i, int j, int k, float& ra, float& rb) {
+  const int n = g.nx, ny = g.ny;
+  const int pu = ny * n, pv = (ny + 1) * n;
+  const int kp = k + 1 == g.nz ? 0 : k + 1;
+  const int ip2 = i + 2 == n ? 0 : i + 2;
+  const int r0 = k * pu + j * n, cell = r0 + i;
+  const int v0 = k * pv + j * n + i, wk = kp * pu + j * n + i;
+  const float2 uu = *reinterpret_cast<const float2*>(f.u + cell);
+  const float u2 = f.u[r0 + ip2];
+  const float2 va = *reinterpret_cast<const float2*>(f.v + v0), vb = *reinterpret_cast<const float2*>(f.v + v0 + n);
+  const float2 w0 = *reinterpret_cast<const float2*>(f.w + cell), w1 = *reinterpret_cast<const float2*>(f.w + wk);
+  const unsigned fw = flags32[cell >> 2];
+  const unsigned sh = 8u * (unsigned)(cell & 3);
+  const unsigned fla = (fw >> sh) & 0xFFu, flb = (fw >> (sh + 8u)) & 0xFFu;
+  const float sc = cf.sc, idx = cf.idx, idz = cf.idz;
+  {
+    const float du = mul_rn(uu.y - uu.x, idx);
+    const float dv = mul_rn(vb.x - va.x, ry.ih);
+    const float dw = mul_rn(w1.x - w0.x, idz);
+    ra = (use_q && (fla & FLAG_B)) ? 0.0f : mul_rn(add_rn(add_rn(du, dv), dw) - qf, sc);
+  }
+  {
+    const float du = mul_rn(u2 - uu.y, idx);
+    const float dv = mul_rn(vb.y - va.y, ry.ih);
+    const float dw = mul_rn(w1.y - w0.y, idz);
+    rb = (use_q && (flb & FLAG_B)) ? 0.0f : mul_rn(add_rn(add_rn(du, dv), dw) - qf, sc);
+  }
+}
+
 // mode 0: rhs = (D uhat - q)/(alpha dt) from the (hi part of the) state;
 // mode 3: rhs of the correction solve, (D u' - q_F)/(alpha dt) on fluid
 // cells from the projected state u' = uhat - G phi as (hi, lo) pairs, in
@@ -824,14 +860,39 @@ __device__ __forceinline__ void fft_plane_fwd(const Blk& bk, const Geo& g, const
   for (int l0 = 0; l0 < nlines; l0 += lc) {
     const int nl = min(lc, nlines - l0);
     __syncthreads();
+    bool paired = false;
+    if constexpr (sizeof(T) == 4) {
+      // first solve (FP32): two cells per thread along x, paired row loads
+      if (mode == 0 && use_q != 2) {
+        paired = true;
+        const int hx = nx / 2;
+#pragma unroll 2
+        for (int t = threadIdx.x; t < nl * hx; t += blockDim.x) {
+          const int l = t / hx, i = 2 * (t - l * hx);
+          const int k0 = 2 * (l0 + l);
+          float a0, b0, a1, b1;
+          rhs_pair0(g, f, flags32, use_q, cf, ry, qf, i, j, k0, a0, b0);
+          rhs_pair0(g, f, flags32, use_q, cf, ry, qf, i, j, k0 + 1, a1, b1);
+          C za, zb;
+          za.x = a0;
+          za.y = a1;
+          zb.x = b0;
+          zb.y = b1;
+          bufa[l * xs + i] = za;
+          bufa[l * xs + i + 1] = zb;
+        }
+      }
+    }
+    if (!paired) {
 #pragma unroll 4
-    for (int t = threadIdx.x; t < nl * nx; t += blockDim.x) {
-      const int l = t / nx, i = t - l * nx;
-      const int k0 = 2 * (l0 + l);
-      C z;
-      z.x = poisson_rhs<T>(g, f, flags32, ds, s, use_q, scale, mode, cf, ry, qf, qa, qb, i, j, k0, rmax);
-      z.y = poisson_rhs<T>(g, f, flags32, ds, s, use_q, scale, mode, cf, ry, qf, qa, qb, i, j, k0 + 1, rmax);
-      bufa[l * xs + i] = z;
+      for (int t = threadIdx.x; t < nl * nx; t += blockDim.x) {
+        const int l = t / nx, i = t - l * nx;
+        const int k0 = 2 * (l0 + l);
+        C z;
+        z.x = poisson_rhs<T>(g, f, flags32, ds, s, use_q, scale, mode, cf, ry, qf, qa, qb, i, j, k0, rmax);
+        z.y = poisson_rhs<T>(g, f, flags32, ds, s, use_q, scale, mode, cf, ry, qf, qa, qb, i, j, k0 + 1, rmax);
+        bufa[l * xs + i] = z;
+      }
     }
     const int res = fft_lines<T, false>(bufa, bufb, nl, px, reinterpret_cast<const C*>(twx), 1, xs,
                                         magic_div_dev((unsigned)nl), true);
