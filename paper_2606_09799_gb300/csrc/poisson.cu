@@ -690,6 +690,66 @@ __device__ __forceinline__ void rhs_pair0(const Geo& g, const Fields<float>& f, 
   }
 }
 
+// Mode 3 of poisson_rhs (the correction's right-hand side from the projected
+// (hi, lo) state) for the FP32 cells (i, j, k) and (i + 1, j, k), i even:
+// phi, the state's hi and lo words and the rows above, below and beside are
+// read as float2 pairs (scalars for the x-neighbours i - 1 and i + 2), and
+// each cell takes poisson_rhs's operations in the same order.
+__device__ __forceinline__ void rhs_pair3(const Geo& g, const Fields<float>& f, const unsigned* __restrict__ flags32,
+                                          const DevState* ds, int s, int use_q, const ProjCoef<float>& cf,
+                                          const RowY<float>& ry, int i, int j, int k, float& ra, float& rb,
+                                          unsigned& rmax) {
+  const int n = g.nx, ny = g.ny;
+  const int pu = ny * n, pv = (ny + 1) * n;
+  const int kp = k + 1 == g.nz ? 0 : k + 1, km = k == 0 ? g.nz - 1 : k - 1;
+  const int im = i == 0 ? n - 1 : i - 1, ip2 = i + 2 == n ? 0 : i + 2;
+  const int r0 = k * pu + j * n, cell = r0 + i;
+  const int v0 = k * pv + j * n + i, wk = kp * pu + j * n + i;
+  const int rkm = km * pu + j * n, rkp = kp * pu + j * n;
+  auto ld2 = [](const float* p) { return *reinterpret_cast<const float2*>(p); };
+  const float* __restrict__ ph = f.phi;
+  const float2 P0 = ld2(ph + cell);
+  const float Pm = ph[r0 + im], Pp = ph[r0 + ip2];
+  const float2 Ps = j > 0 ? ld2(ph + cell - n) : make_float2(0.0f, 0.0f);
+  const float2 Pn = j + 1 < ny ? ld2(ph + cell + n) : make_float2(0.0f, 0.0f);
+  const float2 Pkm = ld2(ph + rkm + i), Pkp = ld2(ph + rkp + i);
+  const float2 Uh = ld2(f.u + cell), Ul = ld2(f.lo[0] + cell);
+  const float Uhp = f.u[r0 + ip2], Ulp = f.lo[0][r0 + ip2];
+  const float2 V0h = ld2(f.v + v0), V0l = ld2(f.lo[1] + v0), V1h = ld2(f.v + v0 + n), V1l = ld2(f.lo[1] + v0 + n);
+  const float2 W0h = ld2(f.w + cell), W0l = ld2(f.lo[2] + cell), W1h = ld2(f.w + wk), W1l = ld2(f.lo[2] + wk);
+  const unsigned fw = flags32[cell >> 2];
+  const unsigned sh = 8u * (unsigned)(cell & 3);
+  const unsigned fla = (fw >> sh) & 0xFFu, flb = (fw >> (sh + 8u)) & 0xFFu;
+  const float2 Qk = use_q == 2 ? ld2(f.qk + cell) : make_float2(0.0f, 0.0f);
+  const float qh1 = use_q ? ds->qf_hi[s] : 0.0f, ql = use_q == 1 ? ds->qf_lo[s] : 0.0f;
+  auto one = [&](unsigned fl, float p0, float pw, float pe, float pso, float pno, float pkm, float pkp, float uh0,
+                 float ul0, float uh1, float ul1, float vh0, float vl0, float vh1, float vl1, float wh0, float wl0,
+                 float wh1, float wl1, float qk) {
+    if (use_q && (fl & FLAG_B)) return 0.0f;
+    float bx, sx, by, sy, bz, sz, a1, e1, a2, e2, a3, e3;
+    proj_face(uh0, ul0, mul_rn(cf.cx, p0 - pw));
+    proj_face(uh1, ul1, mul_rn(cf.cx, pe - p0));
+    if (j > 0) proj_face(vh0, vl0, mul_rn(ry.cy0, p0 - pso));
+    if (j + 1 < ny) proj_face(vh1, vl1, mul_rn(ry.cy1, pno - p0));
+    proj_face(wh0, wl0, mul_rn(cf.cz, p0 - pkm));
+    proj_face(wh1, wl1, mul_rn(cf.cz, pkp - p0));
+    pair_diff_v(uh1, ul1, uh0, ul0, cf.ih[0][0], cf.ih[0][1], bx, sx);
+    pair_diff_v(vh1, vl1, vh0, vl0, ry.ihh, ry.ihl, by, sy);
+    pair_diff_v(wh1, wl1, wh0, wl0, cf.ih[2][0], cf.ih[2][1], bz, sz);
+    two_sum(bx, by, a1, e1);
+    two_sum(a1, bz, a2, e2);
+    const float qh = use_q == 2 ? qk : qh1;
+    two_sum(a2, -qh, a3, e3);
+    const float d = a3 + (((e1 + e2) + e3) + ((sx + sy) + sz) - ql);   // D u' - q
+    rmax = max(rmax, __float_as_uint(d) & 0x7FFFFFFF);
+    return d * cf.scf;
+  };
+  ra = one(fla, P0.x, Pm, P0.y, Ps.x, Pn.x, Pkm.x, Pkp.x, Uh.x, Ul.x, Uh.y, Ul.y, V0h.x, V0l.x, V1h.x, V1l.x, W0h.x,
+           W0l.x, W1h.x, W1l.x, Qk.x);
+  rb = one(flb, P0.y, P0.x, Pp, Ps.y, Pn.y, Pkm.y, Pkp.y, Uh.y, Ul.y, Uhp, Ulp, V0h.y, V0l.y, V1h.y, V1l.y, W0h.y,
+           W0l.y, W1h.y, W1l.y, Qk.y);
+}
+
 // mode 0: rhs = (D uhat - q)/(alpha dt) from the (hi part of the) state;
 // mode 3: rhs of the correction solve, (D u' - q_F)/(alpha dt) on fluid
 // cells from the projected state u' = uhat - G phi as (hi, lo) pairs, in
@@ -862,8 +922,9 @@ __device__ __forceinline__ void fft_plane_fwd(const Blk& bk, const Geo& g, const
     __syncthreads();
     bool paired = false;
     if constexpr (sizeof(T) == 4) {
-      // first solve (FP32): two cells per thread along x, paired row loads
-      if (mode == 0 && use_q != 2) {
+      // FP32: two cells per thread along x, paired row loads (the first
+      // solve's right-hand side, or the correction's from the (hi, lo) state)
+      if ((mode == 0 && use_q != 2) || (mode == 3 && f.lo[0])) {
         paired = true;
         const int hx = nx / 2;
 #pragma unroll 2
@@ -871,8 +932,13 @@ __device__ __forceinline__ void fft_plane_fwd(const Blk& bk, const Geo& g, const
           const int l = t / hx, i = 2 * (t - l * hx);
           const int k0 = 2 * (l0 + l);
           float a0, b0, a1, b1;
-          rhs_pair0(g, f, flags32, use_q, cf, ry, qf, i, j, k0, a0, b0);
-          rhs_pair0(g, f, flags32, use_q, cf, ry, qf, i, j, k0 + 1, a1, b1);
+          if (mode == 0) {
+            rhs_pair0(g, f, flags32, use_q, cf, ry, qf, i, j, k0, a0, b0);
+            rhs_pair0(g, f, flags32, use_q, cf, ry, qf, i, j, k0 + 1, a1, b1);
+          } else {
+            rhs_pair3(g, f, flags32, ds, s, use_q, cf, ry, i, j, k0, a0, b0, rmax);
+            rhs_pair3(g, f, flags32, ds, s, use_q, cf, ry, i, j, k0 + 1, a1, b1, rmax);
+          }
           C za, zb;
           za.x = a0;
           za.y = a1;
